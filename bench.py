@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the FastLSQ hot path on GB300 (one JSON line on rank 0).
+
+Workload: the 2-D Helmholtz problem (Lap u + 16 u = f on [0,1]^2, manufactured
+u* = sin(pi x) sin(2 pi y) + 0.3 cos(3 pi x + pi y), 8192 uniform-random interior
+points + 1024 boundary points (256 per edge, weight 100), 2048 frozen features
+W ~ N(0, 64 I), b ~ U(0, 2 pi)).  One step = one whole linear PDE solve (Alg. 1):
+right-hand side, operator assembly (FP32 for the factor, FP64 for the refinement
+residual), blocked Householder QR, triangular solve and two steps of FP64
+iterative refinement, all in libfastlsq kernels through the C ABI.
+
+`value` is device-timed solves/s with inputs resident in HBM (L2 flushed between
+steps, outside the per-step events); `e2e` is the same metric through the C ABI
+with host buffers (H2D of the points and features, D2H of beta inside the timed
+step).  The roofline object describes the kernel class with the largest device
+time, measured with CUDA events inside the timed region.  `--impl reference`
+times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PDE solves/s at <=1e-6 rel L2 err vs FP64 GPU path; assembly Gentries/s"
+WORKLOAD = ("helmholtz2d: Lap u + k^2 u = f, k=4, [0,1]^2, 8192 interior + 1024 boundary rows "
+            "(weight 100), 2048 features sigma=8")
+# the CPU oracle runs a sample with half the rows and half the features (1/8 of the
+# dominant m n^2 QR work) or a quarter of each (1/64); times are scaled by that ratio
+SAMPLE_CPU = dict(n_int=4096, n_bc=512, n_feat=1024)
+SAMPLE_REF = dict(n_int=2048, n_bc=256, n_feat=512)
+
+
+def _scale_ratio(sample):
+    full = (8192 + 1024) * 2048 ** 2
+    return full / ((sample["n_int"] + sample["n_bc"]) * sample["n_feat"] ** 2)
+
+
+def _oracle_solve_seconds(sample):
+    """One oracle solve of the sampled Helmholtz problem (assembly, rhs, QR, solve)."""
+    import oracle
+    from paper_2602_10541_gb300 import workloads as wl
+    w = wl.helmholtz2d(**sample)
+    t0 = time.perf_counter()
+    A_int = oracle.assemble(w.x_int, w.alpha, w.coef, w.W, w.b, w.scale)
+    A_bc = oracle.assemble(w.x_bc, np.zeros((1, 2), np.int32), [1.0], w.W, w.b, w.scale,
+                           row_weight=w.lam_bc)
+    f = oracle.problem_source(w.problem, w.x_int, w.params)
+    g = oracle.problem_exact(w.problem, w.x_bc, w.params)
+    oracle.lstsq(np.vstack([A_int, A_bc]), np.concatenate([f, w.lam_bc * g]))
+    return time.perf_counter() - t0
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    ratio = _scale_ratio(SAMPLE_REF)
+    for _ in range(max(0, args.warmup)):
+        _oracle_solve_seconds(SAMPLE_REF)
+    ts = [_oracle_solve_seconds(SAMPLE_REF) for _ in range(args.steps)]
+    total = sum(ts) * ratio
+    value = args.steps / total
+    sample = (f"helmholtz2d with {SAMPLE_REF['n_int']}+{SAMPLE_REF['n_bc']} rows x "
+              f"{SAMPLE_REF['n_feat']} features per step, time x{ratio:.0f} (m n^2 ratio)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (plain C, 1 thread)"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _src_sha(name):
+    with open(os.path.join(ROOT, "paper_2602_10541_gb300", "csrc", name), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+KERNEL_SRC = {"panel": "qr.cu", "trail_simt": "qr.cu", "trail_tc": "tc_update.cu",
+              "apply_q": "qr.cu", "trsv": "qr.cu", "residual": "qr.cu", "assemble_f32": "assemble.cu",
+              "assemble_f64": "assemble.cu", "copy_in": "qr.cu"}
+
+
+def _algorithmic(kernel, m, n, m_aug, nb, nrhs, refine, nb_elem):
+    """(unit, amount per solve) of the algorithmic cost of one kernel class in one
+    step; bytes for memory-bound kernels (each operand moved once), flops for
+    arithmetic-bound ones.  Per-unit figures are stated in the design doc."""
+    e = nb_elem
+    panels = [(k, min(nb, n - k)) for k in range(0, n, nb)]
+    if kernel == "assemble_f32":
+        return "bytes", 4.0 * m * n                     # each entry written once
+    if kernel == "assemble_f64":
+        return "bytes", 8.0 * m * n
+    if kernel == "panel":                              # slice read + written once per panel
+        return "bytes", sum(2.0 * (m_aug - k) * c * e for k, c in panels)
+    if kernel in ("trail_simt", "trail_tc"):           # C read twice, written once; V twice
+        tot = 0.0
+        for k, c in panels:
+            nct = n + nrhs - (k + c)
+            tot += (3.0 * nct + 2.0 * c) * (m_aug - k) * e
+        return "bytes", tot
+    if kernel == "apply_q":                            # V read twice per application
+        return "bytes", refine * sum(2.0 * (m_aug - k) * c * e for k, c in panels)
+    if kernel == "trsv":                               # upper triangle read once per solve
+        return "bytes", (1 + refine) * 0.5 * n * n * e
+    if kernel == "residual":                           # FP64 operator read once per residual
+        return "bytes", refine * 8.0 * m * n
+    if kernel == "copy_in":
+        return "bytes", (4.0 + e) * m * n
+    return "bytes", 0.0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--refine", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2602_10541_gb300 import _build
+    from paper_2602_10541_gb300 import fastlsq as fl
+    from paper_2602_10541_gb300 import pipeline as pl
+    from paper_2602_10541_gb300 import workloads as wl
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    if not _build.up_to_date():
+        _build.build()
+    ctx = fl.Context(local)
+    stream = torch.cuda.current_stream(local)
+
+    # each rank solves its own instance (replicas: the solve does not shard)
+    w = wl.helmholtz2d(seed_offset=rank)
+    dp = pl.upload(w, dev)
+    solver = pl.LinearSolver(ctx, dp, prec=fl.PREC_MIXED, max_refine=args.refine)
+    m, n = w.n_rows, w.n_feat
+
+    for _ in range(args.warmup):
+        solver.step()
+    torch.cuda.synchronize()
+
+    # which kernel class dominates (pre-pass with events on every class)
+    fl.fastlsq_profile_enable(ctx, None)
+    for _ in range(2):
+        solver.step()
+    prof_pre = fl.fastlsq_profile_read(ctx)
+    dominant = max(prof_pre, key=lambda k: prof_pre[k][1])
+    fl.fastlsq_profile_enable(ctx, [dominant])     # only the dominant class inside the timed region
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))                         # evict L2 (outside the step events)
+        ev_s[i].record(stream)
+        solver.step()
+        ev_e[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [ev_s[i].elapsed_time(ev_e[i]) for i in range(args.steps)]
+    total_ms = sum(step_ms)
+    prof = fl.fastlsq_profile_read(ctx)
+    fl.fastlsq_profile_enable(ctx, [])
+    launches = sum(v[0] for v in prof.values())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel class (events recorded in the timed region)
+    dom_launches, dom_ms = prof[dominant]
+    elem = 4
+    solver.solve(stats=True)
+    solve_stats = solver.stats
+    nb = solve_stats.nb
+    unit_kind, per_step = _algorithmic(dominant, m, n, m + (n if w.mu > 0 else 0), nb, 1,
+                                       args.refine, elem)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = per_step * args.steps / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tpath):
+        tinfo = json.load(open(tpath)).get(dominant)
+        if tinfo and tinfo.get("src_sha") == _src_sha(KERNEL_SRC.get(dominant, "qr.cu")):
+            traffic = tinfo.get("bytes_per_launch")
+    roofline = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                "launches": dom_launches, "avg_launch_us": 1e3 * dom_ms / max(1, dom_launches),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+    breakdown = {k: {"launches_per_step": v[0] / 2.0, "ms_per_step": v[1] / 2.0}
+                 for k, v in prof_pre.items() if v[0]}
+
+    # accuracy: mixed result vs the plain FP64 GPU path and vs the exact solution
+    u_mixed = solver.u_test()
+    s64 = pl.LinearSolver(ctx, dp, prec=fl.PREC_FP64)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter()
+    s64.step()
+    torch.cuda.synchronize()
+    fp64_ms = 1e3 * (time.perf_counter() - t64)
+    u64 = s64.u_test()
+    ue = solver.u_exact_test()
+    accuracy = {"rel_l2_vs_fp64_gpu": pl.rel_l2(u_mixed, u64), "rel_l2_vs_exact": pl.rel_l2(u_mixed, ue),
+                "fp64_gpu_rel_l2_vs_exact": pl.rel_l2(u64, ue), "fp64_gpu_ms_per_solve": fp64_ms,
+                "fp64_gpu_solves_per_s": 1e3 / fp64_ms,
+                "resid_norms": list(solve_stats.resid_norm[: args.refine + 1])}
+    del s64
+
+    # assembly alone (FP32 operator, both row blocks), Gentries/s
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    asm_ms = 0.0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ea.record(stream)
+        fl.fastlsq_assemble(ctx, fl.F32, dp.x_int, dp.op_int, 1.0, dp.W, dp.b, w.scale, solver.A32, 0)
+        fl.fastlsq_assemble(ctx, fl.F32, dp.x_bc, dp.op_bc, w.lam_bc, dp.W, dp.b, w.scale,
+                            solver.A32, w.n_int)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        asm_ms += ea.elapsed_time(eb)
+    asm_rate = args.steps * m * n / (asm_ms / 1e3)
+    assembly = {"gentries_per_s": asm_rate / 1e9, "entries": m * n,
+                "hbm_write_gbs": 4 * asm_rate / 1e9, "hbm_frac": 4 * asm_rate / 1e9 / hbm,
+                "sfu_bound_gentries_per_s": None}
+
+    # end to end through the C ABI with host buffers
+    pin = lambda t: t.detach().cpu().pin_memory()
+    h_x_int, h_x_bc, h_W, h_b = pin(dp.x_int), pin(dp.x_bc), pin(dp.W), pin(dp.b)
+    h_beta = torch.empty_like(solver.beta, device="cpu").pin_memory()
+    bi = sum(t.numel() * t.element_size() for t in (h_x_int, h_x_bc, h_W, h_b))
+    bo = h_beta.numel() * h_beta.element_size()
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        dp.x_int.copy_(h_x_int, non_blocking=True)
+        dp.x_bc.copy_(h_x_bc, non_blocking=True)
+        dp.W.copy_(h_W, non_blocking=True)
+        dp.b.copy_(h_b, non_blocking=True)
+        solver.step()
+        h_beta.copy_(solver.beta, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": bi,
+           "d2h_bytes_per_step": bo}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        ratio = _scale_ratio(SAMPLE_CPU)
+        t = _oracle_solve_seconds(SAMPLE_CPU)
+        cpu = {"value": 1.0 / (t * ratio), "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": (f"one oracle solve of helmholtz2d with {SAMPLE_CPU['n_int']}+"
+                          f"{SAMPLE_CPU['n_bc']} rows x {SAMPLE_CPU['n_feat']} features "
+                          f"({t:.1f} s), time x{ratio:.0f} (m n^2 ratio to the full workload)")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_rows": m, "n_feat": n,
+                           "precision": f"mixed: FP32 assembly and Householder QR, FP64 residual, "
+                                        f"{args.refine} refinement steps",
+                           "tensor_core_updates": bool(solve_stats.tensor_core),
+                           "panel_nb": nb, "l2": "flushed between steps (256 MiB write outside the step events)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+                "clocks": clk, "accuracy": accuracy, "assembly": assembly, "kernels": breakdown,
+                "wall_s_timed": wall}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

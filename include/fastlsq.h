@@ -1,0 +1,331 @@
+/*
+ * fastlsq.h -- C ABI of the GB300 (sm_103a) FastLSQ hot path.
+ *
+ * The method (arXiv 2602.10541): u(x) = s * sum_j beta_j sin(W_j.x + b_j) with
+ * s = 1/sqrt(N) (Sec. 2.1, eq. approximation); every linear operator applied to
+ * a feature has the closed form D^alpha phi_j = (prod_k W_jk^alpha_k) *
+ * Phi_{|alpha| mod 4}(W_j.x + b_j), Phi = (sin, cos, -sin, -cos) (Sec. 2.2,
+ * eq. cyclic); a linear PDE becomes the least-squares problem
+ * [A_pde; lambda A_bc] beta = [f; lambda g] (Sec. 2.3, eq. linear_system,
+ * Alg. 1); a nonlinear one is solved by Newton-Raphson with Tikhonov-regularised
+ * least-squares steps (Sec. 2.4, eq. newton); gradients flow through the
+ * pre-factored solve (Sec. 2.5, Sec. 4.4).
+ *
+ * Conventions for every entry point:
+ *  - All array arguments are DEVICE pointers on the context's device unless the
+ *    argument says "host".  The caller owns every array; the library owns only
+ *    the context and factor handles, released by their _destroy calls.
+ *  - Matrices are column-major with a leading dimension ld >= rows; vectors are
+ *    contiguous.  Points x are row-major [n][d]; feature weights W are row-major
+ *    [n_feat][d]; biases b are [n_feat].  x, W, b, right-hand sides and
+ *    coefficients are double precision; the operator matrix may be float or
+ *    double (fastlsq_dtype).
+ *  - Work is queued on the context's stream and is asynchronous unless the call
+ *    documents a host read-back (the stats structs).
+ *  - Return value: 0 success; negative = error (-1 invalid argument, -2 out of
+ *    memory, -3 CUDA error, -4 device-side wait timed out, -5 non-finite value);
+ *    positive = warning (1 Newton reached max_iter, 2 line search failed,
+ *    3 numerically rank-deficient R).  No exception or abort crosses the ABI;
+ *    fastlsq_last_error() gives a message.
+ *  - Sizes: n_feat <= 16384, d <= 8, at most 32 operator terms, per-point terms
+ *    <= 4; n_rows is limited by device memory and by the panel kernel's on-chip
+ *    capacity (fastlsq_lstsq returns -1 with a message when exceeded).
+ */
+#ifndef FASTLSQ_H
+#define FASTLSQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define FASTLSQ_API __attribute__((visibility("default")))
+#else
+#define FASTLSQ_API
+#endif
+
+#define FASTLSQ_OK 0
+#define FASTLSQ_ERR_INVALID (-1)
+#define FASTLSQ_ERR_NOMEM (-2)
+#define FASTLSQ_ERR_CUDA (-3)
+#define FASTLSQ_ERR_TIMEOUT (-4)
+#define FASTLSQ_ERR_NONFINITE (-5)
+#define FASTLSQ_WARN_MAXITER 1
+#define FASTLSQ_WARN_LINESEARCH 2
+#define FASTLSQ_WARN_RANKDEF 3
+
+typedef struct fastlsq_ctx fastlsq_ctx;        /* device, stream, workspace, tile table */
+typedef struct fastlsq_factor fastlsq_factor;  /* checkpointed QR factors (reusable)    */
+
+typedef enum { FASTLSQ_F32 = 0, FASTLSQ_F64 = 1 } fastlsq_dtype;
+
+/* Solve precision.  FP64: FP64 operator, FP64 Householder QR (panel and trailing
+ * updates), FP64 triangular solve.  MIXED: FP32 operator, FP32 panels, trailing
+ * updates as split TF32x3 tensor-core products with FP32 accumulation (SIMT FP32
+ * when tensor-core updates are disabled), then classical iterative refinement:
+ * FP64 residual r = rhs - A64 beta against a caller-supplied FP64 operator, the
+ * correction R^{-1} Q^T r solved with the FP32 factors, beta accumulated in
+ * FP64. */
+typedef enum { FASTLSQ_PREC_FP64 = 0, FASTLSQ_PREC_MIXED = 1 } fastlsq_prec;
+
+/* A linear operator as a list of terms sum_t coef[t] D^{alpha_t} (the paper's Op,
+ * App. B).  alpha: host [n_terms][d] multi-indices; coef: host [n_terms].
+ * pp_*: optional per-point terms (at most 4) whose coefficient varies by row:
+ * term q adds pp_coef[q][i] * D^{pp_alpha_q} phi_j(x_i), pp_coef[q] a DEVICE
+ * double array of n_rows entries (the rows of this call).  This is how the
+ * Newton Jacobian's N'(u_i) phi_j enters (eq. newton). */
+typedef struct {
+    int32_t d;
+    int32_t n_terms;
+    const int32_t *alpha;          /* host [n_terms * d] */
+    const double *coef;            /* host [n_terms]     */
+    int32_t n_pp;                  /* number of per-point terms (0..4) */
+    const int32_t *pp_alpha;       /* host [n_pp * d]    */
+    const double *const *pp_coef;  /* host array of n_pp DEVICE pointers */
+} fastlsq_op;
+
+/* Create a context on `device` that queues work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  Returns 0 or an error. */
+FASTLSQ_API int fastlsq_create(fastlsq_ctx **ctx, int device, void *cuda_stream);
+/* Release the context and its workspace (waits for its stream first). */
+FASTLSQ_API int fastlsq_destroy(fastlsq_ctx *ctx);
+/* Replace the stream the context queues work on. */
+FASTLSQ_API int fastlsq_set_stream(fastlsq_ctx *ctx, void *cuda_stream);
+/* Message describing the last error on this context ("" if none). Owned by ctx. */
+FASTLSQ_API const char *fastlsq_last_error(const fastlsq_ctx *ctx);
+/* Synchronise the context's stream and return the first device-side error flag
+ * raised since the last call (0 if none), then clear it. */
+FASTLSQ_API int fastlsq_sync(fastlsq_ctx *ctx);
+
+/*
+ * Assemble one row block of the operator matrix (Sec. 2.3 eq. linear_system,
+ * Alg. 1 steps 3-4) with the cyclic-derivative closed form (eq. cyclic):
+ *
+ *   A[(row_offset + i) + j*ldA] = row_weight * scale *
+ *        sum_t (coef_t + pp) * (prod_k W_jk^alpha_tk) * Phi_{|alpha_t| mod 4}(W_j.x_i + b_j)
+ *
+ * for i < n_rows, j < n_feat.  x: [n_rows][op->d] (double), W: [n_feat][d]
+ * (double), b: [n_feat] (double).  A: dtype F32 or F64, column-major, ldA >=
+ * row_offset + n_rows; rows outside [row_offset, row_offset + n_rows) are not
+ * touched.  The F32 path rounds x, W, b to float, reduces the argument with a
+ * three-part 2 pi (Cody-Waite) and evaluates sin/cos on the SFU; the F64 path
+ * uses double-precision sin/cos.  Interior rows use the PDE operator with
+ * row_weight 1; boundary rows the boundary operator with row_weight = lambda.
+ */
+FASTLSQ_API int fastlsq_assemble(fastlsq_ctx *ctx, fastlsq_dtype dtype,
+                     const double *x, int64_t n_rows, const fastlsq_op *op,
+                     double row_weight, const double *W, const double *b,
+                     int64_t n_feat, double scale,
+                     void *A, int64_t ldA, int64_t row_offset);
+
+/* Problem ids for fastlsq_rhs (the manufactured and synthetic problems). */
+typedef enum {
+    FASTLSQ_PROBLEM_POISSON_1D = 1,    /* -u'' = f, u* = sin(2 pi x) + 0.5 sin(6 pi x)              */
+    FASTLSQ_PROBLEM_HELMHOLTZ_2D = 2,  /* Lap u + k^2 u = f, params[0] = k,                         */
+                                       /* u* = sin(pi x) sin(2 pi y) + 0.3 cos(3 pi x + pi y)       */
+    FASTLSQ_PROBLEM_POISSON_5D = 3,    /* -Lap u = f, u* = sum_k sin(pi x_k) + prod_k x_k           */
+    FASTLSQ_PROBLEM_BRATU_2D = 4,      /* Lap u + lam e^u = 0, u = 0 on the boundary (f = g = 0)    */
+    FASTLSQ_PROBLEM_GAUSS_SOURCE_2D = 5 /* -Lap u = sum_k a_k exp(-|x-c_k|^2/(2 w_k^2)), params =   */
+                                       /* theta [n_src][4] = (c_x, c_y, w, a)                      */
+} fastlsq_problem;
+
+typedef enum { FASTLSQ_RHS_SOURCE = 0, FASTLSQ_RHS_EXACT = 1 } fastlsq_rhs_kind;
+
+/*
+ * Right-hand side entries (eq. linear_system): out[i] = weight * f(x_i)
+ * (kind SOURCE, the interior equation's source) or weight * u*(x_i) (kind EXACT,
+ * the Dirichlet data g and the reference solution for error measurement; 0 for
+ * problems without a closed form).  params: host [n_params].  x: [n][d].
+ */
+FASTLSQ_API int fastlsq_rhs(fastlsq_ctx *ctx, fastlsq_problem problem, fastlsq_rhs_kind kind,
+                const double *params, int32_t n_params, const double *x, int64_t n,
+                int32_t d, double weight, double *out);
+
+/*
+ * Evaluate the approximation at points (eq. approximation, Alg. 1 return line):
+ * u[e] = scale * sum_j beta[j] sin(W_j.x_e + b_j) for e < n_eval, in FP64.
+ * x: [n_eval][d].  Used for test-set errors and sensor readouts.
+ */
+FASTLSQ_API int fastlsq_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int32_t d,
+                 const double *W, const double *b, int64_t n_feat, double scale,
+                 const double *beta, double *u);
+
+/*
+ * Adjoint of fastlsq_eval (the sensor readout u_s = H_s beta of Sec. 4.4):
+ * grad_beta[j] = scale * sum_e g[e] sin(W_j.x_e + b_j), FP64.  x: [n_eval][d],
+ * g: [n_eval], grad_beta: [n_feat].
+ */
+FASTLSQ_API int fastlsq_eval_adjoint(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int32_t d,
+                                     const double *W, const double *b, int64_t n_feat, double scale,
+                                     const double *g, double *grad_beta);
+
+typedef struct {
+    int32_t refine_steps;      /* refinement steps performed                       */
+    int32_t nb;                /* panel width used                                 */
+    int32_t tensor_core;       /* 1 if trailing updates ran on tcgen05              */
+    int32_t status;            /* as the return value of the call                  */
+    double resid_norm[8];      /* ||rhs - A beta|| (incl. sqrt(mu) rows) after the  */
+                               /* first solve and after each refinement step (FP64) */
+} fastlsq_solve_stats;
+
+/*
+ * beta = argmin ||A beta - rhs||^2 + mu ||beta||^2 (Sec. 2.3: QR; Sec. 2.4:
+ * Tikhonov with mu > 0, realised as the augmented rows sqrt(mu) I).
+ *
+ * A: n_rows x n_feat, dtype a_dtype, column-major with ldA (not modified; it is
+ * copied into the factor's storage, FP32 for MIXED, FP64 for FP64).  rhs:
+ * n_rows x nrhs (ld_rhs), beta: n_feat x nrhs (ld_beta), both double.
+ * prec FP64 requires a_dtype F64.  prec MIXED refines each rhs max_refine times
+ * (0..7) with the FP64 residual against A_refine (double, n_rows x n_feat,
+ * ld_refine), which must equal A to double precision (assemble it with dtype
+ * F64); A_refine may be NULL only when max_refine is 0.
+ * keep: if non-NULL, receives the factor handle (Householder reflectors, T
+ * blocks, R) for fastlsq_factor_solve / fastlsq_backward; the handle keeps the
+ * A_refine pointer, which must then outlive it.  stats may be NULL; if given,
+ * the call synchronises the stream to fill it.
+ * Requires n_rows + (mu > 0 ? n_feat : 0) >= n_feat.
+ */
+FASTLSQ_API int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec,
+                  const void *A, fastlsq_dtype a_dtype, int64_t ldA,
+                  int64_t n_rows, int64_t n_feat, double mu,
+                  const double *rhs, int32_t nrhs, int64_t ld_rhs,
+                  double *beta, int64_t ld_beta,
+                  const double *A_refine, int64_t ld_refine, int32_t max_refine,
+                  fastlsq_factor **keep, fastlsq_solve_stats *stats);
+
+/* Solve again with checkpointed factors for new right-hand sides (the paper's
+ * matrix caching, App. F.4): beta = R^{-1} Q^T [rhs; 0], refined as in
+ * fastlsq_lstsq when the factor is MIXED and was given A_refine. */
+FASTLSQ_API int fastlsq_factor_solve(fastlsq_ctx *ctx, const fastlsq_factor *f,
+                         const double *rhs, int32_t nrhs, int64_t ld_rhs,
+                         double *beta, int64_t ld_beta, int32_t max_refine,
+                         fastlsq_solve_stats *stats);
+
+/* Release a factor handle (stream-ordered). */
+FASTLSQ_API int fastlsq_factor_destroy(fastlsq_factor *f);
+
+/*
+ * Adjoint of the regularised solve beta = (A^T A + mu I)^{-1} A^T rhs
+ * (Sec. 2.5; Sec. 4.4: "each evaluation costs two triangular back-substitutions"),
+ * with R^T R = A^T A + mu I from the checkpointed factor:
+ *   v = R^{-1} R^{-T} grad_beta                      (n_feat, double, out)
+ *   grad_rhs = A v                                   (n_rows, double, out; NULL to skip)
+ * A_op is the FP64 operator (n_rows x n_feat, ld) used for A v; NULL uses the
+ * factor's A_refine.  Loss gradients with respect to a source parameter theta
+ * follow as sum_i grad_rhs[i] d rhs_i / d theta (fastlsq_source_grad), and with
+ * respect to operator coefficients from fastlsq_coef_grad.
+ */
+FASTLSQ_API int fastlsq_backward(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *grad_beta,
+                     double *v, double *grad_rhs, const double *A_op, int64_t ld_op);
+
+/*
+ * dL/dtheta for the Gaussian source (problem GAUSS_SOURCE_2D):
+ *   dtheta[q] = sum_i w[i] * d s(x_i; theta) / d theta_q,  x: [n][2], w = dL/df at x.
+ * theta: host [n_src * 4]; dtheta: host [n_src * 4] (the call synchronises).
+ */
+FASTLSQ_API int fastlsq_source_grad(fastlsq_ctx *ctx, const double *x, int64_t n, const double *theta,
+                        int32_t n_src, const double *w, double *dtheta);
+
+/*
+ * Gradient of the loss with respect to the coefficients of the interior operator
+ * terms (PDE-coefficient parameters).  Differentiating the normal equations
+ * (A^T A + mu I) beta = A^T rhs gives
+ *   dL/dc_t = sum_ij (r_i v_j - (A v)_i beta_j) * scale * D^{alpha_t} phi_j(x_i)
+ * with r = rhs - A beta.  Entries of each term are assembled on the fly in FP64
+ * (never stored).  x: [n_rows][d] (the rows the terms act on), r, Av: [n_rows],
+ * v, beta: [n_feat]; grad: host [op->n_terms] (the call synchronises).
+ */
+FASTLSQ_API int fastlsq_coef_grad(fastlsq_ctx *ctx, const double *x, int64_t n_rows, const fastlsq_op *op,
+                      const double *W, const double *b, int64_t n_feat, double scale,
+                      const double *r, const double *Av, const double *v,
+                      const double *beta, double *grad);
+
+/* Nonlinearities N(u) of the Newton problems (Sec. 3.3). */
+typedef enum { FASTLSQ_NL_NONE = 0, FASTLSQ_NL_EXP = 1, FASTLSQ_NL_CUBIC = 2 } fastlsq_nl;
+
+typedef struct {
+    int32_t d;
+    int64_t n_int, n_bc;
+    const double *x_int;      /* [n_int][d] */
+    const double *x_bc;       /* [n_bc][d]  */
+    fastlsq_op op;            /* interior linear operator L (no per-point terms) */
+    int32_t nl_kind;          /* fastlsq_nl: N(u) = nl_lam e^u or nl_lam u^3     */
+    double nl_lam;
+    double bc_weight;         /* boundary rows bc_weight * (u - g) (Dirichlet)   */
+    const double *f;          /* [n_int] */
+    const double *g;          /* [n_bc]  */
+} fastlsq_newton_problem;
+
+typedef struct {
+    int32_t max_iter;         /* <= 64                                           */
+    double tol;               /* stop when ||a J_u delta|| / ||u|| <= tol        */
+    double mu;                /* Tikhonov parameter of each step                 */
+    double armijo_c;          /* accept a when ||R(beta+a delta)||^2 <= (1-2ca)||R||^2 */
+    int32_t max_halvings;     /* backtracking halvings before giving up          */
+    int32_t prec;             /* fastlsq_prec of each step's solve               */
+    int32_t max_refine;       /* refinement steps per solve (MIXED)              */
+} fastlsq_newton_opts;
+
+typedef struct {
+    int32_t iters;
+    int32_t status;
+    double res_norm[65];      /* ||R|| before each iteration and after the last  */
+    double step_rel[64];      /* ||a J_u delta|| / ||u|| per iteration            */
+    double alpha[64];         /* accepted step length per iteration              */
+} fastlsq_newton_stats;
+
+/*
+ * Newton-Raphson for L[u] + N[u] = f with Dirichlet rows (Sec. 2.4, eq. newton):
+ * R_i = L[u](x_i) + N(u_i) - f_i (interior), bc_weight (u_i - g_i) (boundary);
+ * J_ij = L[phi_j](x_i) + N'(u_i) phi_j(x_i) reassembled on the GPU every
+ * iteration; delta = argmin ||J delta + R||^2 + mu ||delta||^2; Armijo
+ * backtracking on ||R||; solution-level stopping test.  beta_inout: [n_feat]
+ * (start value in, solution out; a warm start from the linear part is the
+ * caller's choice).  The residuals and the refinement operator are FP64.  The
+ * call synchronises once per iteration to take the line-search decisions and
+ * fills stats (may be NULL).  Returns 0 converged, 1 max_iter, 2 line search
+ * failed, or an error.
+ */
+FASTLSQ_API int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *prob,
+                   const double *W, const double *b, int64_t n_feat, double scale,
+                   const fastlsq_newton_opts *opts, double *beta_inout,
+                   fastlsq_newton_stats *stats);
+
+/* Kernel classes for profiling (launch counts are always kept; device times are
+ * recorded with CUDA events around each launch only while profiling is on). */
+typedef enum {
+    FASTLSQ_K_PREFACTOR = 0,   /* column prefactors P, Q                          */
+    FASTLSQ_K_ASSEMBLE_F32,    /* operator assembly, FP32 (SFU)                   */
+    FASTLSQ_K_ASSEMBLE_F64,    /* operator assembly, FP64                         */
+    FASTLSQ_K_RHS,             /* right-hand sides                                */
+    FASTLSQ_K_EVAL,            /* u at points                                     */
+    FASTLSQ_K_COPY_IN,         /* matrix into factor storage (+ Tikhonov rows)    */
+    FASTLSQ_K_PANEL,           /* Householder panel (cluster)                     */
+    FASTLSQ_K_TRAIL_SIMT,      /* trailing update, SIMT                           */
+    FASTLSQ_K_TRAIL_TC,        /* trailing update, tcgen05 TF32x3                 */
+    FASTLSQ_K_APPLY_Q,         /* Q^T y / Q y                                     */
+    FASTLSQ_K_TRSV,            /* triangular solves                               */
+    FASTLSQ_K_RESIDUAL,        /* FP64 residual / matvec                          */
+    FASTLSQ_K_VECTOR,          /* small vector kernels                            */
+    FASTLSQ_K_NEWTON,          /* Newton pointwise kernels                        */
+    FASTLSQ_K_ADJOINT,         /* adjoint contractions                            */
+    FASTLSQ_K_COUNT
+} fastlsq_kernel;
+
+/* Record per-launch CUDA-event times on the context's stream for the kernel
+ * classes whose bit (1 << fastlsq_kernel) is set in `mask` (0 stops recording,
+ * -1 records every class); any call clears all counters.  Must be 0 while the
+ * stream is being captured into a CUDA graph. */
+FASTLSQ_API int fastlsq_profile_enable(fastlsq_ctx *ctx, int mask);
+/* Launches of kernel class `kernel` since the last reset, and (if profiling was
+ * on) their summed device time in milliseconds.  Synchronises the stream. */
+FASTLSQ_API int fastlsq_profile_read(fastlsq_ctx *ctx, int kernel, int64_t *launches,
+                                     double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTLSQ_H */

@@ -1,0 +1,146 @@
+// Shared internals of libfastlsq (GB300, sm_103a): context, workspace, error
+// handling and the operator parameter block passed to kernels by value.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/fastlsq.h"
+
+#define FL_MAX_D 8
+#define FL_MAX_TERMS 32
+#define FL_MAX_PP 4
+#define FL_MAX_FEAT 16384
+
+// Device error flag codes (first one raised wins).
+#define FL_DEVERR_NONFINITE 1
+#define FL_DEVERR_BOUNDS 2
+#define FL_DEVERR_TIMEOUT 3
+
+struct fl_buffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Workspace slots (grow-only device buffers owned by the context).
+enum fl_slot {
+    FL_WS_PREFACTOR = 0,   // column prefactors P, Q and per-point multipliers
+    FL_WS_PARTIAL,         // split-K / split-column partial sums
+    FL_WS_VEC0,            // FP64 vectors for refinement
+    FL_WS_VEC1,
+    FL_WS_VEC2,
+    FL_WS_SCALARS,         // small FP64 scratch (norms)
+    FL_WS_NEWTON_J,        // Newton: FP32 Jacobian
+    FL_WS_NEWTON_L64,      // Newton: FP64 linear operator rows
+    FL_WS_NEWTON_H64,      // Newton: FP64 basis at interior rows
+    FL_WS_NEWTON_VEC,      // Newton: vectors
+    FL_WS_GRAM,            // panel Gram partials
+    FL_WS_NORMS,           // residual norms for solve stats
+    FL_WS_COUNT
+};
+
+struct fl_prof_state {
+    bool enabled = false;
+    unsigned mask = 0;
+    long long launches[FASTLSQ_K_COUNT] = {};
+    std::vector<cudaEvent_t> ev[FASTLSQ_K_COUNT];   // start/end pairs
+    size_t used[FASTLSQ_K_COUNT] = {};
+    double ms[FASTLSQ_K_COUNT] = {};
+};
+
+struct fastlsq_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    std::string last_error;
+    fl_buffer ws[FL_WS_COUNT];
+    int *d_flag = nullptr;          // device error flag (int)
+    int use_tensor_core = 0;        // tcgen05 trailing updates for the MIXED path
+    // Cody-Waite split of 2 pi for the FP32 argument reduction (host-derived)
+    float cw2pi[3] = {0.f, 0.f, 0.f};
+    fl_prof_state prof;
+};
+
+// Records CUDA events around the launches in its scope (when profiling is on) and
+// counts one launch per kernel launched in the scope.
+struct fl_prof_scope {
+    fastlsq_ctx *ctx;
+    int id;
+    cudaEvent_t end = nullptr;
+    fl_prof_scope(fastlsq_ctx *c, int kid, int n_launches = 1);
+    ~fl_prof_scope();
+};
+#define FL_PROF(ctx, kid) fl_prof_scope _fl_prof_scope((ctx), (kid))
+#define FL_PROF_N(ctx, kid, n) fl_prof_scope _fl_prof_scope((ctx), (kid), (n))
+
+struct fastlsq_factor {
+    fastlsq_ctx *ctx = nullptr;
+    int prec = 0;              // fastlsq_prec
+    int64_t m = 0, n = 0;      // rows of A and features
+    int64_t m_aug = 0, ld = 0; // factored rows (m + n when mu > 0), leading dimension
+    double mu = 0.0;
+    int nb = 32;
+    void *F = nullptr;         // factor storage m_aug x n (float or double)
+    void *tau = nullptr;       // n
+    void *T = nullptr;         // (n / nb) blocks of nb x nb (column-major)
+    const double *A_refine = nullptr;
+    int64_t ld_refine = 0;
+    int tensor_core = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+int fl_fail(fastlsq_ctx *ctx, int code, const char *fmt, ...);
+int fl_cuda(fastlsq_ctx *ctx, cudaError_t e, const char *what);
+void *fl_ws(fastlsq_ctx *ctx, int slot, size_t bytes);   // nullptr on failure (error set)
+
+#define FL_CHECK_LAUNCH(ctx, what)                                          \
+    do {                                                                    \
+        cudaError_t _e = cudaGetLastError();                                \
+        if (_e != cudaSuccess) return fl_cuda((ctx), _e, (what));           \
+    } while (0)
+
+#define FL_TRY(expr)                                                        \
+    do {                                                                    \
+        int _rc = (expr);                                                   \
+        if (_rc < 0) return _rc;                                            \
+    } while (0)
+
+__host__ __device__ __forceinline__ int64_t fl_min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t fl_max64(int64_t a, int64_t b) { return a > b ? a : b; }
+static inline int64_t fl_cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static inline int64_t fl_round_up(int64_t a, int64_t b) { return fl_cdiv(a, b) * b; }
+
+// ---------------------------------------------------------------------------
+// Operator parameter block (by value into kernels)
+// ---------------------------------------------------------------------------
+struct fl_op_params {
+    int d;
+    int n_terms;
+    int alpha[FL_MAX_TERMS][FL_MAX_D];
+    double coef[FL_MAX_TERMS];
+    int n_pp;
+    int pp_alpha[FL_MAX_PP][FL_MAX_D];
+    const double *pp_coef[FL_MAX_PP];
+};
+
+int fl_pack_op(fastlsq_ctx *ctx, const fastlsq_op *op, fl_op_params *out);
+
+// Kernels / launchers implemented in the .cu files ---------------------------
+int fl_prefactors(fastlsq_ctx *ctx, const fl_op_params &op, const double *W, int64_t n_feat,
+                  double scale, double row_weight, double *pref);
+int fl_launch_assemble_f32(fastlsq_ctx *ctx, const fl_op_params &op, const double *x,
+                           int64_t n_rows, const double *W, const double *b, int64_t n_feat,
+                           const double *pref, float *A, int64_t ldA, int64_t row_offset,
+                           double row_weight);
+int fl_launch_assemble_f64(fastlsq_ctx *ctx, const fl_op_params &op, const double *x,
+                           int64_t n_rows, const double *W, const double *b, int64_t n_feat,
+                           const double *pref, double *A, int64_t ldA, int64_t row_offset,
+                           double row_weight);

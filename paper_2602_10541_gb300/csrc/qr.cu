@@ -1,0 +1,880 @@
+// Blocked Householder QR and the solves built on it (Sec. 2.3: "beta* = A^+ b
+// via QR"; Sec. 2.4: Tikhonov rows sqrt(mu) I; Sec. 4.4: pre-factored solves).
+//
+// Layout: the factor F is column-major (ld), rows [0, m_aug), columns [0, n)
+// hold the matrix, columns [n, n + nrhs) hold right-hand sides that ride along
+// with the trailing updates (so Q^T b comes out of the factorisation).  After
+// factorisation F holds R on and above the diagonal and the Householder vectors
+// (unit diagonal implied) below it; tau[j] are the reflector scalars and, per
+// panel p of width NB, T_p is the upper-triangular NB x NB matrix of the compact
+// WY form H_k ... H_{k+NB-1} = I - V T V^T.
+//
+// Reflector convention (as LAPACK): beta = -sign(a_jj) ||a_j(j:)||,
+// tau = (beta - a_jj) / beta, v = a_j(j+1:) / (a_jj - beta), v_j = 1.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "common.cuh"
+#include "qr.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int PANEL_THREADS = 512;
+constexpr int PANEL_WARPS = PANEL_THREADS / 32;
+constexpr int CL_MAX = 16;
+
+template <typename T> __device__ __forceinline__ T fl_sqrt(T v);
+template <> __device__ __forceinline__ float fl_sqrt<float>(float v) { return sqrtf(v); }
+template <> __device__ __forceinline__ double fl_sqrt<double>(double v) { return sqrt(v); }
+
+template <typename T> __device__ __forceinline__ bool fl_isfinite(T v) { return isfinite(v); }
+
+__device__ __forceinline__ void raise_flag(int *flag, int code)
+{
+    if (flag) atomicCAS(flag, 0, code);
+}
+
+template <typename T, int NB>
+struct PanelSmem {
+    static constexpr int LD = NB + 1;   // padded row stride of the panel slice
+    static size_t bytes(int rpc)
+    {
+        return sizeof(T) * ((size_t)rpc * LD + PANEL_WARPS * 32 + 2 * (CL_MAX + 1) * NB +
+                            NB * (NB + 1) + NB);
+    }
+};
+
+// Panel factorisation on a cluster of CL CTAs.  CTA `rank` owns panel rows
+// [rank * rpc, min((rank+1) * rpc, mp)) in shared memory; rpc >= ncols so rank 0
+// owns every diagonal row.  For each column j one cluster-wide exchange (DSMEM
+// stores + one cluster barrier) delivers: the dot products of column j with
+// every column l > j below the diagonal (sum over rows i > j of a_ij a_il), the
+// diagonal row a_j., and the Gram entries v_l^T v_{j-1} (l < j-1) needed by the
+// T recurrence T(0:c, c) = -tau_c T(0:c, 0:c) V(:, 0:c)^T v_c.  The update pass
+// that applies H_j to the rows also accumulates the next column's dots and this
+// column's Gram entries, so each column costs one pass over the slice.
+template <typename T, int NB>
+__global__ void __launch_bounds__(PANEL_THREADS, 1)
+k_panel(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int rpc,
+        T *__restrict__ tau_out, T *__restrict__ T_out, int *flag)
+{
+    constexpr int LDP = PanelSmem<T, NB>::LD;
+    constexpr int RPW = 32 / NB;           // rows per warp step
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *P = reinterpret_cast<T *>(smem_raw);
+    T *red = P + (size_t)rpc * LDP;                 // [PANEL_WARPS][32]
+    T *xbuf = red + PANEL_WARPS * 32;               // [2][CL_MAX + 1][NB]
+    T *Tm = xbuf + 2 * (CL_MAX + 1) * NB;           // [NB][NB + 1] (row-major, T[row][col])
+    T *tauv = Tm + NB * (NB + 1);                   // [NB]
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int CL = (int)cluster.num_blocks();
+    const int64_t mp = m - k;
+    const int64_t c0 = (int64_t)rank * rpc;
+    const int nown = (int)fl_max64(0, fl_min64(rpc, mp - c0));
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int l = lane % NB;       // column handled by this lane
+    const int sub = lane / NB;     // row sub-slot within the warp step
+    const unsigned FULL = 0xffffffffu;
+
+    // load the slice (coalesced: consecutive threads take consecutive rows of a column)
+    for (int idx = threadIdx.x; idx < nown * NB; idx += PANEL_THREADS) {
+        int c = idx / nown, r = idx % nown;
+        P[r * LDP + c] = (c < ncols) ? F[(k + c0 + r) + (k + c) * ld] : T(0);
+    }
+    for (int idx = threadIdx.x; idx < NB * (NB + 1); idx += PANEL_THREADS) Tm[idx] = T(0);
+    __syncthreads();
+
+    // dots of column 0 with every column, rows i > 0
+    T acc = T(0);
+    for (int rb = warp * RPW; rb < nown; rb += PANEL_WARPS * RPW) {
+        const int r = rb + sub;
+        if (r < nown && c0 + r > 0) acc += P[r * LDP] * P[r * LDP + l];
+    }
+
+    for (int j = 0; j <= ncols; ++j) {
+        const int par = j & 1;
+        // block reduction of acc over warps and row sub-slots -> warp 0 lane l
+        red[warp * 32 + lane] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            T part = T(0);
+            if (lane < NB)
+                for (int w = 0; w < PANEL_WARPS; ++w)
+                    for (int s = 0; s < RPW; ++s) part += red[w * 32 + s * NB + lane];
+            T top = (rank == 0 && j < ncols && lane < NB) ? P[j * LDP + lane] : T(0);
+            if (lane < NB) {
+                for (int dst = 0; dst < CL; ++dst) {
+                    T *rb = cluster.map_shared_rank(xbuf, dst);
+                    rb[(par * (CL_MAX + 1) + rank) * NB + lane] = part;
+                    if (rank == 0) rb[(par * (CL_MAX + 1) + CL_MAX) * NB + lane] = top;
+                }
+            }
+        }
+        cluster.sync();
+        const T *xb = xbuf + par * (CL_MAX + 1) * NB;
+        T dl = T(0);
+        for (int s = 0; s < CL; ++s) dl += xb[s * NB + l];   // fixed order: same sum everywhere
+
+        // T column j-1 from the Gram entries G(q, j-1) = dl on lanes q < j-1
+        if (j >= 1 && warp == 0 && rank == 0) {
+            const int c = j - 1;
+            T tc = tauv[c];
+            T sum = T(0);
+            for (int q = 0; q < c; ++q) {
+                T gq = __shfl_sync(FULL, dl, q);       // lanes 0..NB-1 carry columns
+                if (lane < c && q >= lane) sum += Tm[lane * (NB + 1) + q] * gq;
+            }
+            if (lane < c) Tm[lane * (NB + 1) + c] = -tc * sum;
+            if (lane == c) Tm[c * (NB + 1) + c] = tc;
+        }
+        if (j == ncols) break;
+
+        // reflector for column j (every thread computes the same scalars)
+        T ss = T(0);
+        for (int s = 0; s < CL; ++s) ss += xb[s * NB + j];
+        const T ajj = xb[CL_MAX * NB + j];
+        const T topl = xb[CL_MAX * NB + l];
+        T beta = ajj, tauj = T(0), inv = T(0);
+        if (!fl_isfinite(ss) || !fl_isfinite(ajj)) {
+            raise_flag(flag, FL_DEVERR_NONFINITE);
+        } else if (ss > T(0)) {
+            T nrm = fl_sqrt<T>(ajj * ajj + ss);
+            beta = (ajj >= T(0)) ? -nrm : nrm;
+            tauj = (beta - ajj) / beta;
+            inv = T(1) / (ajj - beta);
+        }
+        const T wl = (l > j) ? tauj * (topl + inv * dl) : T(0);
+        if (threadIdx.x == 0) tauv[j] = tauj;
+
+        // apply H_j to the owned rows; accumulate next-column dots (l > j) and
+        // Gram entries v_l^T v_j (l < j)
+        acc = T(0);
+        for (int rb = warp * RPW; rb < nown; rb += PANEL_WARPS * RPW) {   // warp-uniform bound
+            const int r = rb + sub;
+            const bool valid = r < nown;
+            const int64_t gi = c0 + r;
+            T pj = valid ? P[r * LDP + j] : T(0);
+            T pl = valid ? P[r * LDP + l] : T(0);
+            __syncwarp();
+            T nl = pl;
+            if (valid && gi >= j) {          // rows gi < j hold finished R rows
+                if (gi == j) {
+                    if (l > j) { nl = pl - wl; P[r * LDP + l] = nl; }
+                    if (l == j) P[r * LDP + j] = beta;
+                    if (l < j) acc += pl;    // v_j has a unit entry in row j
+                } else {
+                    T vj = pj * inv;
+                    if (l > j) { nl = pl - wl * vj; P[r * LDP + l] = nl; }
+                    else if (l == j) P[r * LDP + j] = vj;
+                    if (l < j) acc += pl * vj;
+                }
+            }
+            T nxt = __shfl_sync(FULL, nl, sub * NB + ((j + 1) % NB));
+            if (valid && gi > j + 1 && l > j) acc += nxt * nl;
+        }
+    }
+
+    // write back the slice, tau and T
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nown * NB; idx += PANEL_THREADS) {
+        int c = idx / nown, r = idx % nown;
+        if (c < ncols) F[(k + c0 + r) + (k + c) * ld] = P[r * LDP + c];
+    }
+    if (rank == 0) {
+        for (int idx = threadIdx.x; idx < NB; idx += PANEL_THREADS)
+            tau_out[idx] = (idx < ncols) ? tauv[idx] : T(0);
+        // T stored column-major NB x NB
+        for (int idx = threadIdx.x; idx < NB * NB; idx += PANEL_THREADS) {
+            int col = idx / NB, row = idx % NB;
+            T_out[idx] = (col < ncols && row < ncols) ? Tm[row * (NB + 1) + col] : T(0);
+        }
+    }
+}
+
+// V(i, l) for panel-local row i of panel starting at column k (unit lower trapezoid)
+template <typename T>
+__device__ __forceinline__ T v_at(const T *__restrict__ F, int64_t ld, int64_t k, int64_t i,
+                                  int l, int ncols)
+{
+    if (l >= ncols || i < l) return T(0);
+    if (i == l) return T(1);
+    return F[(k + i) + (k + l) * ld];
+}
+
+// Y partials: Ypart[s][l][c] = sum over rows of split s of V(i,l) C(i,c) for the
+// trailing columns c (global column k + ncols + c).
+constexpr int TY_COLS = 64;
+constexpr int TY_ROWS = 32;
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct,
+          int64_t rows_per_split, T *__restrict__ Ypart)
+{
+    __shared__ T sV[TY_ROWS][NB + 1];
+    __shared__ T sC[TY_COLS][TY_ROWS + 1];
+    const int64_t mp = m - k;
+    const int64_t cbase = (int64_t)blockIdx.x * TY_COLS;
+    const int64_t rs0 = (int64_t)blockIdx.y * rows_per_split;
+    const int64_t rs1 = fl_min64(mp, rs0 + rows_per_split);
+    constexpr int GROUPS = 256 / NB;
+    constexpr int CPT = TY_COLS / GROUPS;   // columns per thread
+    const int l = threadIdx.x % NB;
+    const int g = threadIdx.x / NB;
+    T acc[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) acc[q] = T(0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t r0 = rs0; r0 < rs1; r0 += TY_ROWS) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < TY_ROWS * NB; idx += 256) {
+            int rr = idx % TY_ROWS, ll = idx / TY_ROWS;
+            int64_t i = r0 + rr;
+            sV[rr][ll] = (i < rs1) ? v_at(F, ld, k, i, ll, ncols) : T(0);
+        }
+        for (int cc = warp; cc < TY_COLS; cc += 8) {
+            int64_t c = cbase + cc;
+            int64_t i = r0 + lane;
+            sC[cc][lane] = (c < nct && i < rs1) ? F[(k + i) + (k + ncols + c) * ld] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < TY_ROWS; ++rr) {
+            T v = sV[rr][l];
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) acc[q] += v * sC[g + q * GROUPS][rr];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        int64_t c = cbase + g + q * GROUPS;
+        if (c < nct) Ypart[((int64_t)blockIdx.y * NB + l) * nct + c] = acc[q];
+    }
+}
+
+// C(i, c) -= sum_l V(i, l) Z(l, c) with Z = T^T Y, Y = sum_s Ypart[s].
+constexpr int TC_ROWS = 64;
+constexpr int TC_COLS = 64;
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+k_trail_c(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct,
+          const T *__restrict__ Ypart, int nsplit, const T *__restrict__ Tblk)
+{
+    __shared__ T sZ[NB][TC_COLS];      // holds Y, then Z = T^T Y in place
+    __shared__ T sV[TC_ROWS][NB + 1];
+    __shared__ T sT[NB][NB];
+    const int64_t mp = m - k;
+    const int64_t rbase = (int64_t)blockIdx.x * TC_ROWS;
+    const int64_t cbase = (int64_t)blockIdx.y * TC_COLS;
+    for (int idx = threadIdx.x; idx < NB * NB; idx += 256) sT[idx % NB][idx / NB] = Tblk[idx];
+    for (int idx = threadIdx.x; idx < NB * TC_COLS; idx += 256) {
+        int ll = idx / TC_COLS, cc = idx % TC_COLS;
+        int64_t c = cbase + cc;
+        T s = T(0);
+        if (c < nct)
+            for (int sp = 0; sp < nsplit; ++sp) s += Ypart[((int64_t)sp * NB + ll) * nct + c];
+        sZ[ll][cc] = s;
+    }
+    for (int idx = threadIdx.x; idx < TC_ROWS * NB; idx += 256) {
+        int rr = idx % TC_ROWS, ll = idx / TC_ROWS;
+        int64_t i = rbase + rr;
+        sV[rr][ll] = (i < mp) ? v_at(F, ld, k, i, ll, ncols) : T(0);
+    }
+    __syncthreads();
+    // Z(l, c) = sum_q T(q, l) Y(q, c)  (T upper triangular: q <= l), one column per thread
+    if (threadIdx.x < TC_COLS) {
+        const int cc = threadIdx.x;
+        T y[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) y[q] = sZ[q][cc];
+#pragma unroll
+        for (int ll = 0; ll < NB; ++ll) {
+            T s = T(0);
+#pragma unroll
+            for (int q = 0; q <= ll; ++q) s += sT[q][ll] * y[q];
+            sZ[ll][cc] = s;
+        }
+    }
+    __syncthreads();
+    const int rr = threadIdx.x % TC_ROWS;
+    const int cg4 = threadIdx.x / TC_ROWS;       // 4 groups of 16 columns
+    T acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = T(0);
+#pragma unroll 4
+    for (int ll = 0; ll < NB; ++ll) {
+        T v = sV[rr][ll];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] += v * sZ[ll][cg4 * 16 + q];
+    }
+    const int64_t i = rbase + rr;
+    if (i < mp) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            int64_t c = cbase + cg4 * 16 + q;
+            if (c < nct) {
+                T *p = F + (k + i) + (k + ncols + c) * ld;
+                *p -= acc[q];
+            }
+        }
+    }
+}
+
+// y <- Q^T y (forward) or Q y (backward) for vectors y [m_aug] of type T, on one
+// cluster: per panel, dots s_l = sum_i V(i,l) y_i (cluster exchange), then
+// w = T^T s (Q^T) or T s (Q), then y_i -= sum_l V(i,l) w_l.
+template <typename T, int NB>
+__global__ void __launch_bounds__(PANEL_THREADS, 1)
+k_apply_q(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n, const T *__restrict__ Tall,
+          T *__restrict__ y, int transpose)
+{
+    __shared__ T red[PANEL_WARPS][NB];
+    __shared__ T xbuf[2][CL_MAX][NB];
+    __shared__ T w[NB];
+    __shared__ T sT[NB][NB];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int CL = (int)cluster.num_blocks();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t rows_per = fl_cdiv_dev(m_aug, CL);
+    const int64_t r_lo = rank * rows_per, r_hi = fl_min64(m_aug, r_lo + rows_per);
+    const int npanels = (int)((n + NB - 1) / NB);
+    for (int step = 0; step < npanels; ++step) {
+        const int p = transpose ? step : (npanels - 1 - step);
+        const int64_t k = (int64_t)p * NB;
+        const int ncols = (int)fl_min64(NB, n - k);
+        const int par = step & 1;
+        T acc[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) acc[q] = T(0);
+        for (int64_t i = fl_max64(r_lo, k) + threadIdx.x; i < r_hi; i += PANEL_THREADS) {
+            T yi = y[i];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) acc[q] += v_at(F, ld, k, i - k, q, ncols) * yi;
+        }
+        // reduce acc over the block: warp shuffle then smem across warps
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            T v = acc[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][q] = v;
+        }
+        for (int idx = threadIdx.x; idx < NB * NB; idx += PANEL_THREADS)
+            sT[idx % NB][idx / NB] = Tall[(int64_t)p * NB * NB + idx];
+        __syncthreads();
+        if (warp == 0 && lane < NB) {
+            T s = T(0);
+            for (int ww = 0; ww < PANEL_WARPS; ++ww) s += red[ww][lane];
+            for (int dst = 0; dst < CL; ++dst) {
+                T *rb = cluster.map_shared_rank(&xbuf[0][0][0], dst);
+                rb[(par * CL_MAX + rank) * NB + lane] = s;
+            }
+        }
+        cluster.sync();
+        if (warp == 0) {
+            T s = T(0);
+            if (lane < NB)
+                for (int src = 0; src < CL; ++src) s += xbuf[par][src][lane];
+            T wl = T(0);
+            for (int q = 0; q < NB; ++q) {
+                T sq = __shfl_sync(0xffffffffu, s, q);
+                if (lane < NB) {
+                    // Q^T: w = T^T s -> w_l = sum_{q <= l} T(q,l) s_q ; Q: w = T s -> w_l = sum_{q >= l} T(l,q) s_q
+                    if (transpose) { if (q <= lane) wl += sT[q][lane] * sq; }
+                    else { if (q >= lane) wl += sT[lane][q] * sq; }
+                }
+            }
+            if (lane < NB) w[lane] = wl;
+        }
+        __syncthreads();
+        for (int64_t i = fl_max64(r_lo, k) + threadIdx.x; i < r_hi; i += PANEL_THREADS) {
+            T s = T(0);
+#pragma unroll
+            for (int q = 0; q < NB; ++q) s += v_at(F, ld, k, i - k, q, ncols) * w[q];
+            y[i] -= s;
+        }
+        __syncthreads();
+    }
+}
+
+// Back substitution R x = y (R: upper triangle of F, n x n) on one CTA of 1024
+// threads, 32-row blocks bottom-up.  y: [n] in, x: [n] out (may alias y).
+template <typename T>
+__global__ void __launch_bounds__(1024, 1)
+k_trsv_upper(const T *__restrict__ F, int64_t ld, int64_t n, const T *y, T *x, int *flag)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sx = reinterpret_cast<T *>(smem_raw);   // [n]
+    __shared__ T red[32][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nblk = (n + 31) / 32;
+    for (int64_t bi = nblk - 1; bi >= 0; --bi) {
+        const int64_t r0 = bi * 32, r1 = fl_min64(n, r0 + 32);
+        const int64_t row = r0 + lane;
+        T acc = T(0);
+        if (row < r1)
+            for (int64_t c = r1 + warp; c < n; c += 32) acc += F[row + c * ld] * sx[c];
+        red[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            T s = T(0);
+            for (int ww = 0; ww < 32; ++ww) s += red[ww][lane];
+            if (row < r1) s = y[row] - s;
+            for (int64_t rr = r1 - 1; rr >= r0; --rr) {
+                const int li = (int)(rr - r0);
+                T diag = F[rr + rr * ld];
+                T xv = __shfl_sync(0xffffffffu, s, li) / diag;
+                if (!fl_isfinite(xv)) raise_flag(flag, FL_DEVERR_NONFINITE);
+                if (lane == li) s = xv;
+                if (lane < li && row < r1) s -= F[row + rr * ld] * xv;
+            }
+            if (row < r1) sx[row] = s;
+        }
+        __syncthreads();
+    }
+    for (int64_t i = threadIdx.x; i < n; i += 1024) x[i] = sx[i];
+}
+
+// Forward substitution R^T x = y, 32-row blocks top-down (same launch shape).
+template <typename T>
+__global__ void __launch_bounds__(1024, 1)
+k_trsv_upper_t(const T *__restrict__ F, int64_t ld, int64_t n, const T *y, T *x, int *flag)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sx = reinterpret_cast<T *>(smem_raw);
+    __shared__ T sdot[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nblk = (n + 31) / 32;
+    for (int64_t bi = 0; bi < nblk; ++bi) {
+        const int64_t r0 = bi * 32, r1 = fl_min64(n, r0 + 32);
+        // warp w computes sum_{c < r0} R(c, r0 + w) x_c (column r0 + w of R)
+        const int64_t col = r0 + warp;
+        T acc = T(0);
+        if (col < r1)
+            for (int64_t c = lane; c < r0; c += 32) acc += F[c + col * ld] * sx[c];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) sdot[warp] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            const int64_t row = r0 + lane;
+            T s = (row < r1) ? y[row] - sdot[lane] : T(0);
+            for (int64_t rr = r0; rr < r1; ++rr) {
+                const int li = (int)(rr - r0);
+                T diag = F[rr + rr * ld];
+                T xv = __shfl_sync(0xffffffffu, s, li) / diag;
+                if (!fl_isfinite(xv)) raise_flag(flag, FL_DEVERR_NONFINITE);
+                if (lane == li) s = xv;
+                if (lane > li && row < r1) s -= F[rr + row * ld] * xv;
+            }
+            if (row < r1) sx[row] = s;
+        }
+        __syncthreads();
+    }
+    for (int64_t i = threadIdx.x; i < n; i += 1024) x[i] = sx[i];
+}
+
+// Copy A (and the rhs columns) into the factor storage, writing the Tikhonov
+// rows sqrt(mu) I below the m real rows when mu > 0.
+template <typename TA, typename T>
+__global__ void k_copy_in(const TA *__restrict__ A, int64_t ldA, int64_t m, int64_t n,
+                          double sqrt_mu, int64_t m_aug, const double *__restrict__ rhs,
+                          int64_t ld_rhs, int nrhs, T *__restrict__ F, int64_t ld)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t c = blockIdx.y;
+    if (i >= m_aug) return;
+    T v;
+    if (c < n) v = (i < m) ? (T)A[i + c * ldA] : ((i - m == c) ? (T)sqrt_mu : T(0));
+    else v = (i < m) ? (T)rhs[i + (c - n) * ld_rhs] : T(0);
+    F[i + c * ld] = v;
+}
+
+// Residual of the augmented system in FP64:  r_i = rhs_i - sum_j A_ij beta_j
+// (i < m), r_{m+j} = -sqrt(mu) beta_j.  Column-split partial sums, fixed-order
+// reduction; the second kernel also rounds r to the factor type for the
+// correction solve and accumulates ||r||^2 per block.
+constexpr int RES_ROWS = 256;
+constexpr int RES_COLS = 128;
+
+__global__ void __launch_bounds__(RES_ROWS)
+k_resid_partial(const double *__restrict__ A, int64_t ldA, int64_t m, int64_t n,
+                const double *__restrict__ beta, double *__restrict__ part)
+{
+    __shared__ double sb[RES_COLS];
+    const int64_t j0 = (int64_t)blockIdx.y * RES_COLS;
+    const int nc = (int)fl_min64(RES_COLS, n - j0);
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) sb[t] = beta[j0 + t];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * RES_ROWS + threadIdx.x;
+    if (i >= m) return;
+    double acc = 0.0;
+    const double *a = A + i + j0 * ldA;
+#pragma unroll 8
+    for (int c = 0; c < nc; ++c) acc = fma(a[(int64_t)c * ldA], sb[c], acc);
+    part[(int64_t)blockIdx.y * m + i] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_resid_finish(const double *__restrict__ part, int nsplit, const double *__restrict__ rhs,
+               const double *__restrict__ beta, int64_t m, int64_t n, double sqrt_mu,
+               int64_t m_aug, T *__restrict__ r_out, double *__restrict__ norm_part)
+{
+    __shared__ double red[256];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double r = 0.0;
+    if (i < m) {
+        double s = 0.0;
+        for (int sp = 0; sp < nsplit; ++sp) s += part[(int64_t)sp * m + i];
+        r = rhs[i] - s;
+    } else if (i < m_aug) {
+        r = -sqrt_mu * beta[i - m];
+    }
+    if (i < m_aug) r_out[i] = (T)r;
+    red[threadIdx.x] = r * r;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) norm_part[blockIdx.x] = red[0];
+}
+
+template <typename T>
+__global__ void k_extract_rhs(const T *__restrict__ F, int64_t ld, int64_t n, int r,
+                              T *__restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = F[i + (n + r) * ld];
+}
+
+template <typename T>
+__global__ void k_to_f64(const T *__restrict__ src, int64_t n, double *__restrict__ dst, int add)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (add) dst[i] += (double)src[i];
+    else dst[i] = (double)src[i];
+}
+
+template <typename T>
+__global__ void k_from_f64(const double *__restrict__ src, int64_t n, int64_t n_total,
+                           T *__restrict__ dst)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_total) dst[i] = (i < n) ? (T)src[i] : T(0);
+}
+
+__global__ void k_sum_norm(const double *__restrict__ part, int n, double *__restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += part[i];
+        *out = sqrt(s);
+    }
+}
+
+// Allow the largest dynamic shared memory the kernel can take next to its static part.
+template <typename K>
+cudaError_t set_max_dynamic_smem(K kernel, int optin)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)a.sharedSizeBytes);
+}
+
+template <typename T>
+int trsv_dynamic_limit(fastlsq_ctx *ctx, int transpose)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = transpose ? cudaFuncGetAttributes(&a, k_trsv_upper_t<T>)
+                              : cudaFuncGetAttributes(&a, k_trsv_upper<T>);
+    if (e != cudaSuccess) return 0;
+    return ctx->max_smem_optin - (int)a.sharedSizeBytes;
+}
+
+template <typename T, int NB>
+int set_panel_attrs(fastlsq_ctx *ctx)
+{
+    static bool done = false;   // per process; attributes are per function
+    if (done) return 0;
+    cudaError_t e = set_max_dynamic_smem(k_panel<T, NB>, ctx->max_smem_optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_panel<T, NB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply_q<T, NB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = set_max_dynamic_smem(k_trsv_upper<T>, ctx->max_smem_optin);
+    if (e == cudaSuccess) e = set_max_dynamic_smem(k_trsv_upper_t<T>, ctx->max_smem_optin);
+    if (e != cudaSuccess) return fl_cuda(ctx, e, "cudaFuncSetAttribute");
+    done = true;
+    return 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+
+int fl_panel_capacity_nb(fastlsq_ctx *ctx, int64_t m_aug, size_t elem)
+{
+    // largest NB in {32, 16, 8} whose panel slice fits on a 16-CTA cluster
+    for (int nb = 32; nb >= 8; nb /= 2) {
+        int64_t rpc = fl_cdiv(m_aug, CL_MAX);
+        size_t bytes = elem * ((size_t)rpc * (nb + 1) + PANEL_WARPS * 32 + 2 * (CL_MAX + 1) * nb +
+                               nb * (nb + 1) + nb);
+        if (bytes <= (size_t)ctx->max_smem_optin) return nb;
+    }
+    return 0;
+}
+
+template <typename T, int NB>
+static int launch_panel(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
+                        T *tau, T *Tblk)
+{
+    FL_TRY((set_panel_attrs<T, NB>(ctx)));
+    const int64_t mp = m_aug - k;
+    int CL = CL_MAX;
+    while (CL > 1 && fl_cdiv(mp, CL) < NB) CL >>= 1;
+    int rpc = (int)fl_cdiv(mp, CL);
+    if (rpc < ncols) rpc = ncols;
+    size_t smem = PanelSmem<T, NB>::bytes(rpc);
+    if (smem > (size_t)ctx->max_smem_optin)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "panel of %lld rows exceeds the on-chip capacity",
+                       (long long)mp);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(PANEL_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FL_PROF(ctx, FASTLSQ_K_PANEL);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_panel<T, NB>, F, ld, k, m_aug, ncols, rpc, tau, Tblk,
+                                       ctx->d_flag);
+    if (e != cudaSuccess) return fl_cuda(ctx, e, "panel launch");
+    return 0;
+}
+
+template <typename T, int NB>
+static int launch_trailing(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m_aug,
+                           int ncols, int64_t nct, const T *Tblk)
+{
+    if (nct <= 0) return 0;
+    const int64_t mp = m_aug - k;
+    const int64_t ctiles = fl_cdiv(nct, TY_COLS);
+    // split the long row dimension so the grid covers the GPU about twice
+    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(fl_cdiv(2 * ctx->num_sms, ctiles),
+                                                            fl_cdiv(mp, 256)));
+    int64_t rows_per_split = fl_round_up(fl_cdiv(mp, nsplit), TY_ROWS);
+    nsplit = fl_cdiv(mp, rows_per_split);
+    T *Ypart = (T *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(T) * nsplit * NB * nct);
+    if (!Ypart) return FASTLSQ_ERR_NOMEM;
+    FL_PROF_N(ctx, FASTLSQ_K_TRAIL_SIMT, 2);
+    k_trail_y<T, NB><<<dim3((unsigned)ctiles, (unsigned)nsplit), 256, 0, ctx->stream>>>(
+        F, ld, k, m_aug, ncols, nct, rows_per_split, Ypart);
+    FL_CHECK_LAUNCH(ctx, "trail_y");
+    k_trail_c<T, NB><<<dim3((unsigned)fl_cdiv(mp, TC_ROWS), (unsigned)fl_cdiv(nct, TC_COLS)), 256, 0,
+                       ctx->stream>>>(F, ld, k, m_aug, ncols, nct, Ypart, (int)nsplit, Tblk);
+    FL_CHECK_LAUNCH(ctx, "trail_c");
+    return 0;
+}
+
+template <typename T, int NB>
+static int factor_t(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n, int nrhs,
+                    T *tau, T *Tall, int use_tc)
+{
+    const int64_t ntot = n + nrhs;
+    for (int64_t k = 0; k < n; k += NB) {
+        const int ncols = (int)std::min<int64_t>(NB, n - k);
+        T *Tblk = Tall + (k / NB) * NB * NB;
+        FL_TRY((launch_panel<T, NB>(ctx, F, ld, k, m_aug, ncols, tau + k, Tblk)));
+        const int64_t nct = ntot - (k + ncols);
+        if constexpr (std::is_same<T, float>::value) {
+            if (use_tc) {
+                FL_TRY((fl_trailing_tc_f32(ctx, F, ld, k, m_aug, ncols, NB, nct, Tblk)));
+                continue;
+            }
+        }
+        FL_TRY((launch_trailing<T, NB>(ctx, F, ld, k, m_aug, ncols, nct, Tblk)));
+    }
+    return 0;
+}
+
+template <typename T>
+int fl_factor(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n, int nrhs, int nb,
+              T *tau, T *Tall, int use_tc)
+{
+    switch (nb) {
+    case 32: return factor_t<T, 32>(ctx, F, ld, m_aug, n, nrhs, tau, Tall, use_tc);
+    case 16: return factor_t<T, 16>(ctx, F, ld, m_aug, n, nrhs, tau, Tall, use_tc);
+    case 8: return factor_t<T, 8>(ctx, F, ld, m_aug, n, nrhs, tau, Tall, use_tc);
+    default: return fl_fail(ctx, FASTLSQ_ERR_INVALID, "panel width %d", nb);
+    }
+}
+template int fl_factor<float>(fastlsq_ctx *, float *, int64_t, int64_t, int64_t, int, int, float *,
+                              float *, int);
+template int fl_factor<double>(fastlsq_ctx *, double *, int64_t, int64_t, int64_t, int, int,
+                               double *, double *, int);
+
+template <typename T>
+int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
+               const T *Tall, T *y, int transpose)
+{
+    cudaLaunchConfig_t cfg = {};
+    int CL = CL_MAX;
+    while (CL > 1 && fl_cdiv(m_aug, CL) < 256) CL >>= 1;
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(PANEL_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
+    FL_PROF(ctx, FASTLSQ_K_APPLY_Q);
+    switch (nb) {
+    case 32:
+        FL_TRY((set_panel_attrs<T, 32>(ctx)));
+        e = cudaLaunchKernelEx(&cfg, k_apply_q<T, 32>, F, ld, m_aug, n, Tall, y, transpose);
+        break;
+    case 16:
+        FL_TRY((set_panel_attrs<T, 16>(ctx)));
+        e = cudaLaunchKernelEx(&cfg, k_apply_q<T, 16>, F, ld, m_aug, n, Tall, y, transpose);
+        break;
+    case 8:
+        FL_TRY((set_panel_attrs<T, 8>(ctx)));
+        e = cudaLaunchKernelEx(&cfg, k_apply_q<T, 8>, F, ld, m_aug, n, Tall, y, transpose);
+        break;
+    default:
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "panel width %d", nb);
+    }
+    if (e != cudaSuccess) return fl_cuda(ctx, e, "apply_q launch");
+    return 0;
+}
+template int fl_apply_q<float>(fastlsq_ctx *, const float *, int64_t, int64_t, int64_t, int,
+                               const float *, float *, int);
+template int fl_apply_q<double>(fastlsq_ctx *, const double *, int64_t, int64_t, int64_t, int,
+                                const double *, double *, int);
+
+template <typename T>
+int fl_trsv(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const T *y, T *x, int transpose)
+{
+    FL_TRY((set_panel_attrs<T, 32>(ctx)));
+    size_t smem = sizeof(T) * (size_t)n;
+    if ((int64_t)smem > (int64_t)trsv_dynamic_limit<T>(ctx, transpose))
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "triangular solve: n_feat %lld too large",
+                       (long long)n);
+    FL_PROF(ctx, FASTLSQ_K_TRSV);
+    if (transpose)
+        k_trsv_upper_t<T><<<1, 1024, smem, ctx->stream>>>(F, ld, n, y, x, ctx->d_flag);
+    else
+        k_trsv_upper<T><<<1, 1024, smem, ctx->stream>>>(F, ld, n, y, x, ctx->d_flag);
+    FL_CHECK_LAUNCH(ctx, "trsv");
+    return 0;
+}
+template int fl_trsv<float>(fastlsq_ctx *, const float *, int64_t, int64_t, const float *,
+                            float *, int);
+template int fl_trsv<double>(fastlsq_ctx *, const double *, int64_t, int64_t, const double *,
+                             double *, int);
+
+template <typename TA, typename T>
+int fl_copy_in(fastlsq_ctx *ctx, const TA *A, int64_t ldA, int64_t m, int64_t n, double mu,
+               int64_t m_aug, const double *rhs, int64_t ld_rhs, int nrhs, T *F, int64_t ld)
+{
+    dim3 grid((unsigned)fl_cdiv(m_aug, 256), (unsigned)(n + nrhs));
+    FL_PROF(ctx, FASTLSQ_K_COPY_IN);
+    k_copy_in<TA, T><<<grid, 256, 0, ctx->stream>>>(A, ldA, m, n, mu > 0 ? sqrt(mu) : 0.0, m_aug,
+                                                    rhs, ld_rhs, nrhs, F, ld);
+    FL_CHECK_LAUNCH(ctx, "copy_in");
+    return 0;
+}
+template int fl_copy_in<float, float>(fastlsq_ctx *, const float *, int64_t, int64_t, int64_t,
+                                      double, int64_t, const double *, int64_t, int, float *,
+                                      int64_t);
+template int fl_copy_in<double, float>(fastlsq_ctx *, const double *, int64_t, int64_t, int64_t,
+                                       double, int64_t, const double *, int64_t, int, float *,
+                                       int64_t);
+template int fl_copy_in<double, double>(fastlsq_ctx *, const double *, int64_t, int64_t, int64_t,
+                                        double, int64_t, const double *, int64_t, int, double *,
+                                        int64_t);
+
+template <typename T>
+int fl_residual(fastlsq_ctx *ctx, const double *A, int64_t ldA, int64_t m, int64_t n, double mu,
+                int64_t m_aug, const double *rhs, const double *beta, T *r_out, double *norm_out)
+{
+    int nsplit = (int)fl_cdiv(n, RES_COLS);
+    double *part = (double *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(double) * nsplit * m);
+    int nblk = (int)fl_cdiv(m_aug, 256);
+    double *npart = (double *)fl_ws(ctx, FL_WS_SCALARS, sizeof(double) * (nblk + 8));
+    if (!part || !npart) return FASTLSQ_ERR_NOMEM;
+    FL_PROF_N(ctx, FASTLSQ_K_RESIDUAL, norm_out ? 3 : 2);
+    k_resid_partial<<<dim3((unsigned)fl_cdiv(m, RES_ROWS), (unsigned)nsplit), RES_ROWS, 0,
+                      ctx->stream>>>(A, ldA, m, n, beta, part);
+    FL_CHECK_LAUNCH(ctx, "resid_partial");
+    k_resid_finish<T><<<nblk, 256, 0, ctx->stream>>>(part, nsplit, rhs, beta, m, n,
+                                                     mu > 0 ? sqrt(mu) : 0.0, m_aug, r_out, npart);
+    FL_CHECK_LAUNCH(ctx, "resid_finish");
+    if (norm_out) {
+        k_sum_norm<<<1, 32, 0, ctx->stream>>>(npart, nblk, norm_out);
+        FL_CHECK_LAUNCH(ctx, "sum_norm");
+    }
+    return 0;
+}
+template int fl_residual<float>(fastlsq_ctx *, const double *, int64_t, int64_t, int64_t, double,
+                                int64_t, const double *, const double *, float *, double *);
+template int fl_residual<double>(fastlsq_ctx *, const double *, int64_t, int64_t, int64_t, double,
+                                 int64_t, const double *, const double *, double *, double *);
+
+template <typename T>
+int fl_extract_rhs(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, int r, T *out)
+{
+    FL_PROF(ctx, FASTLSQ_K_VECTOR);
+    k_extract_rhs<T><<<(unsigned)fl_cdiv(n, 256), 256, 0, ctx->stream>>>(F, ld, n, r, out);
+    FL_CHECK_LAUNCH(ctx, "extract_rhs");
+    return 0;
+}
+template int fl_extract_rhs<float>(fastlsq_ctx *, const float *, int64_t, int64_t, int, float *);
+template int fl_extract_rhs<double>(fastlsq_ctx *, const double *, int64_t, int64_t, int, double *);
+
+template <typename T>
+int fl_to_f64(fastlsq_ctx *ctx, const T *src, int64_t n, double *dst, int add)
+{
+    FL_PROF(ctx, FASTLSQ_K_VECTOR);
+    k_to_f64<T><<<(unsigned)fl_cdiv(n, 256), 256, 0, ctx->stream>>>(src, n, dst, add);
+    FL_CHECK_LAUNCH(ctx, "to_f64");
+    return 0;
+}
+template int fl_to_f64<float>(fastlsq_ctx *, const float *, int64_t, double *, int);
+template int fl_to_f64<double>(fastlsq_ctx *, const double *, int64_t, double *, int);
+
+template <typename T>
+int fl_from_f64(fastlsq_ctx *ctx, const double *src, int64_t n, int64_t n_total, T *dst)
+{
+    FL_PROF(ctx, FASTLSQ_K_VECTOR);
+    k_from_f64<T><<<(unsigned)fl_cdiv(n_total, 256), 256, 0, ctx->stream>>>(src, n, n_total, dst);
+    FL_CHECK_LAUNCH(ctx, "from_f64");
+    return 0;
+}
+template int fl_from_f64<float>(fastlsq_ctx *, const double *, int64_t, int64_t, float *);
+template int fl_from_f64<double>(fastlsq_ctx *, const double *, int64_t, int64_t, double *);

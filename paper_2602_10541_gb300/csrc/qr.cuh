@@ -1,0 +1,33 @@
+// Launchers of the blocked Householder QR and its solves (qr.cu, tc_update.cu).
+#pragma once
+#include "common.cuh"
+
+__host__ __device__ __forceinline__ int64_t fl_cdiv_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int fl_panel_capacity_nb(fastlsq_ctx *ctx, int64_t m_aug, size_t elem);
+
+template <typename T>
+int fl_factor(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n, int nrhs, int nb,
+              T *tau, T *Tall, int use_tc);
+template <typename T>
+int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
+               const T *Tall, T *y, int transpose);
+template <typename T>
+int fl_trsv(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const T *y, T *x, int transpose);
+template <typename TA, typename T>
+int fl_copy_in(fastlsq_ctx *ctx, const TA *A, int64_t ldA, int64_t m, int64_t n, double mu,
+               int64_t m_aug, const double *rhs, int64_t ld_rhs, int nrhs, T *F, int64_t ld);
+template <typename T>
+int fl_residual(fastlsq_ctx *ctx, const double *A, int64_t ldA, int64_t m, int64_t n, double mu,
+                int64_t m_aug, const double *rhs, const double *beta, T *r_out, double *norm_out);
+template <typename T>
+int fl_extract_rhs(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, int r, T *out);
+template <typename T>
+int fl_to_f64(fastlsq_ctx *ctx, const T *src, int64_t n, double *dst, int add);
+template <typename T>
+int fl_from_f64(fastlsq_ctx *ctx, const double *src, int64_t n, int64_t n_total, T *dst);
+
+// tcgen05 (TF32x3 split precision) trailing update; tc_update.cu.  Returns a
+// negative status when the tensor-core path cannot handle the shape.
+int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
+                       int nb, int64_t nct, const float *Tblk);

@@ -1,0 +1,103 @@
+"""Compose the C-ABI calls into the paper's pipelines (Alg. 1; Sec. 2.4; Sec. 4.4).
+
+Orchestration only: every number is produced by libfastlsq kernels through the
+binding in ``fastlsq.py``.  Used by the tests, ``bench.py`` and the smoke check.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import fastlsq as fl
+from .workloads import Workload
+
+
+@dataclass
+class DeviceProblem:
+    """A workload's inputs resident on the GPU (float64)."""
+    w: Workload
+    x_int: torch.Tensor
+    x_bc: torch.Tensor
+    W: torch.Tensor
+    b: torch.Tensor
+    x_test: torch.Tensor
+    op_int: fl.Op
+    op_bc: fl.Op
+
+
+def upload(w: Workload, device="cuda:0") -> DeviceProblem:
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+    return DeviceProblem(w, t(w.x_int), t(w.x_bc), t(w.W), t(w.b), t(w.x_test),
+                         fl.Op(w.alpha, w.coef), fl.Op.identity(w.d))
+
+
+class LinearSolver:
+    """One linear PDE solve (Alg. 1): rhs, operator assembly (FP32 for the factor,
+    FP64 for the refinement residual) and the least-squares solve.  Buffers are
+    allocated once so that repeated solves (and CUDA-graph capture) reuse them."""
+
+    def __init__(self, ctx: fl.Context, dp: DeviceProblem, prec=fl.PREC_MIXED, max_refine=2,
+                 mu=None):
+        self.ctx, self.dp, self.prec, self.max_refine = ctx, dp, prec, max_refine
+        w = dp.w
+        self.m, self.n = w.n_rows, w.n_feat
+        self.mu = w.mu if mu is None else mu
+        dev = dp.W.device
+        self.A64 = fl.colmajor(self.m, self.n, torch.float64, dev)
+        self.A32 = fl.colmajor(self.m, self.n, torch.float32, dev) if prec == fl.PREC_MIXED else None
+        self.rhs = torch.empty((1, self.A64.shape[1]), dtype=torch.float64, device=dev)
+        self.beta = torch.zeros((1, self.n), dtype=torch.float64, device=dev)
+        self.stats = None
+
+    def assemble(self):
+        ctx, dp, w = self.ctx, self.dp, self.dp.w
+        targets = [(fl.F64, self.A64)]
+        if self.A32 is not None:
+            targets.insert(0, (fl.F32, self.A32))
+        for dtype, A in targets:
+            fl.fastlsq_assemble(ctx, dtype, dp.x_int, dp.op_int, 1.0, dp.W, dp.b, w.scale, A, 0)
+            fl.fastlsq_assemble(ctx, dtype, dp.x_bc, dp.op_bc, w.lam_bc, dp.W, dp.b, w.scale, A,
+                                w.n_int)
+
+    def build_rhs(self):
+        ctx, dp, w = self.ctx, self.dp, self.dp.w
+        r = self.rhs[0]
+        fl.fastlsq_rhs(ctx, w.problem, fl.RHS_SOURCE, w.params, dp.x_int, 1.0, r[: w.n_int])
+        fl.fastlsq_rhs(ctx, w.problem, fl.RHS_EXACT, w.params, dp.x_bc, w.lam_bc,
+                       r[w.n_int: w.n_rows])
+
+    def solve(self, stats=False, keep=False):
+        A = self.A32 if self.prec == fl.PREC_MIXED else self.A64
+        rc, fac, st = fl.fastlsq_lstsq(self.ctx, self.prec, A, self.m, self.mu, self.rhs, self.beta,
+                                       A_refine=self.A64,
+                                       max_refine=self.max_refine if self.prec == fl.PREC_MIXED else 0,
+                                       keep=keep, stats=stats)
+        self.stats = st
+        return fac
+
+    def step(self, stats=False):
+        self.build_rhs()
+        self.assemble()
+        return self.solve(stats=stats)
+
+    def u_test(self, beta=None):
+        dp = self.dp
+        u = torch.empty(dp.x_test.shape[0], dtype=torch.float64, device=dp.W.device)
+        fl.fastlsq_eval(self.ctx, dp.x_test, dp.W, dp.b, dp.w.scale,
+                        self.beta[0] if beta is None else beta, u)
+        return u
+
+    def u_exact_test(self):
+        dp = self.dp
+        u = torch.empty(dp.x_test.shape[0], dtype=torch.float64, device=dp.W.device)
+        fl.fastlsq_rhs(self.ctx, dp.w.problem, fl.RHS_EXACT, dp.w.params, dp.x_test, 1.0, u)
+        return u
+
+
+def rel_l2(a, b) -> float:
+    """Relative L2 difference ||a - b|| / ||b||, computed on the host."""
+    a = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else np.asarray(a)
+    b = b.detach().cpu().numpy() if isinstance(b, torch.Tensor) else np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
