@@ -70,6 +70,15 @@ typedef enum { FASTLSQ_F32 = 0, FASTLSQ_F64 = 1 } fastlsq_dtype;
  * FP64. */
 typedef enum { FASTLSQ_PREC_FP64 = 0, FASTLSQ_PREC_MIXED = 1 } fastlsq_prec;
 
+/* Refinement of a MIXED solve.  CLASSICAL: beta += R^{-1} Q^T (rhs - A64 beta),
+ * max_refine times (0..7); converges when the least-squares residual is small
+ * (consistent systems such as the manufactured linear PDEs).  CGLS: CGLS on the
+ * FP64 operator right-preconditioned by the factor's R, started from the direct
+ * solve, at most max_refine iterations (0..64) or until the preconditioned
+ * normal-equation residual falls by refine_tol; converges also for
+ * large-residual and ill-conditioned systems (Newton steps, inverse problems). */
+typedef enum { FASTLSQ_REFINE_CLASSICAL = 0, FASTLSQ_REFINE_CGLS = 1 } fastlsq_refine;
+
 /* A linear operator as a list of terms sum_t coef[t] D^{alpha_t} (the paper's Op,
  * App. B).  alpha: host [n_terms][d] multi-indices; coef: host [n_terms].
  * pp_*: optional per-point terms (at most 4) whose coefficient varies by row:
@@ -162,11 +171,11 @@ FASTLSQ_API int fastlsq_eval_adjoint(fastlsq_ctx *ctx, const double *x, int64_t 
                                      const double *g, double *grad_beta);
 
 typedef struct {
-    int32_t refine_steps;      /* refinement steps performed                       */
+    int32_t refine_steps;      /* refinement steps / CGLS iterations performed     */
     int32_t nb;                /* panel width used                                 */
     int32_t tensor_core;       /* 1 if trailing updates ran on tcgen05              */
     int32_t status;            /* as the return value of the call                  */
-    double resid_norm[8];      /* ||rhs - A beta|| (incl. sqrt(mu) rows) after the  */
+    double resid_norm[65];     /* ||rhs - A beta|| (incl. sqrt(mu) rows) after the  */
                                /* first solve and after each refinement step (FP64) */
 } fastlsq_solve_stats;
 
@@ -178,9 +187,10 @@ typedef struct {
  * copied into the factor's storage, FP32 for MIXED, FP64 for FP64).  rhs:
  * n_rows x nrhs (ld_rhs), beta: n_feat x nrhs (ld_beta), both double.
  * prec FP64 requires a_dtype F64.  prec MIXED refines each rhs max_refine times
- * (0..7) with the FP64 residual against A_refine (double, n_rows x n_feat,
- * ld_refine), which must equal A to double precision (assemble it with dtype
- * F64); A_refine may be NULL only when max_refine is 0.
+ * with the FP64 residual against A_refine (double, n_rows x n_feat, ld_refine),
+ * which must equal A to double precision (assemble it with dtype F64), in the
+ * given refine_mode (fastlsq_refine) with max_refine steps and refine_tol (CGLS);
+ * A_refine may be NULL only when max_refine is 0.
  * keep: if non-NULL, receives the factor handle (Householder reflectors, T
  * blocks, R) for fastlsq_factor_solve / fastlsq_backward; the handle keeps the
  * A_refine pointer, which must then outlive it.  stats may be NULL; if given,
@@ -193,6 +203,7 @@ FASTLSQ_API int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec,
                   const double *rhs, int32_t nrhs, int64_t ld_rhs,
                   double *beta, int64_t ld_beta,
                   const double *A_refine, int64_t ld_refine, int32_t max_refine,
+                  int32_t refine_mode, double refine_tol,
                   fastlsq_factor **keep, fastlsq_solve_stats *stats);
 
 /* Solve again with checkpointed factors for new right-hand sides (the paper's
@@ -201,6 +212,7 @@ FASTLSQ_API int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec,
 FASTLSQ_API int fastlsq_factor_solve(fastlsq_ctx *ctx, const fastlsq_factor *f,
                          const double *rhs, int32_t nrhs, int64_t ld_rhs,
                          double *beta, int64_t ld_beta, int32_t max_refine,
+                         int32_t refine_mode, double refine_tol,
                          fastlsq_solve_stats *stats);
 
 /* Release a factor handle (stream-ordered). */
@@ -213,12 +225,16 @@ FASTLSQ_API int fastlsq_factor_destroy(fastlsq_factor *f);
  *   v = R^{-1} R^{-T} grad_beta                      (n_feat, double, out)
  *   grad_rhs = A v                                   (n_rows, double, out; NULL to skip)
  * A_op is the FP64 operator (n_rows x n_feat, ld) used for A v; NULL uses the
- * factor's A_refine.  Loss gradients with respect to a source parameter theta
+ * factor's A_refine.  For a MIXED factor, max_iter > 0 refines v by
+ * preconditioned CG on (A^T A + mu I) v = grad_beta with FP64 operator products
+ * (M = R^T R), up to max_iter iterations or a residual reduction by tol; this
+ * needs the factor's A_refine.  Loss gradients with respect to a source parameter theta
  * follow as sum_i grad_rhs[i] d rhs_i / d theta (fastlsq_source_grad), and with
  * respect to operator coefficients from fastlsq_coef_grad.
  */
 FASTLSQ_API int fastlsq_backward(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *grad_beta,
-                     double *v, double *grad_rhs, const double *A_op, int64_t ld_op);
+                     double *v, double *grad_rhs, const double *A_op, int64_t ld_op,
+                     int32_t max_iter, double tol);
 
 /*
  * dL/dtheta for the Gaussian source (problem GAUSS_SOURCE_2D):
@@ -265,7 +281,8 @@ typedef struct {
     double armijo_c;          /* accept a when ||R(beta+a delta)||^2 <= (1-2ca)||R||^2 */
     int32_t max_halvings;     /* backtracking halvings before giving up          */
     int32_t prec;             /* fastlsq_prec of each step's solve               */
-    int32_t max_refine;       /* refinement steps per solve (MIXED)              */
+    int32_t max_refine;       /* CGLS refinement iterations per step (MIXED)     */
+    double refine_tol;        /* CGLS tolerance per step (0: 1e-10)              */
 } fastlsq_newton_opts;
 
 typedef struct {
@@ -311,6 +328,7 @@ typedef enum {
     FASTLSQ_K_VECTOR,          /* small vector kernels                            */
     FASTLSQ_K_NEWTON,          /* Newton pointwise kernels                        */
     FASTLSQ_K_ADJOINT,         /* adjoint contractions                            */
+    FASTLSQ_K_KRYLOV,          /* Krylov refinement (FP64 products, scalars)      */
     FASTLSQ_K_COUNT
 } fastlsq_kernel;
 

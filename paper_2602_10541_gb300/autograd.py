@@ -21,8 +21,11 @@ class Factorization:
     with Tikhonov mu; A_op is the FP64 operator used for grad_rhs = A v (and for
     refinement when prec is MIXED)."""
 
-    def __init__(self, ctx, A, n_rows, mu, prec=fl.PREC_FP64, A_op=None, max_refine=0):
+    def __init__(self, ctx, A, n_rows, mu, prec=fl.PREC_FP64, A_op=None, max_refine=0,
+                 refine_mode=fl.REFINE_CGLS, refine_tol=1e-13, adjoint_iters=0, adjoint_tol=1e-13):
         self.ctx, self.n_rows, self.mu, self.prec = ctx, n_rows, mu, prec
+        self.refine_mode, self.refine_tol = refine_mode, refine_tol
+        self.adjoint_iters, self.adjoint_tol = adjoint_iters, adjoint_tol
         self.n_feat = A.shape[0]
         self.A_op = A_op if A_op is not None else (A if A.dtype == torch.float64 else None)
         self.max_refine = max_refine
@@ -34,9 +37,11 @@ class Factorization:
         return _Solve.apply(rhs, self)
 
     def close(self):
-        if self.handle is not None:
+        # the factor's memory belongs to the device pool; once the context is gone
+        # (interpreter shutdown) it is released with the process
+        if self.handle is not None and getattr(self.ctx, "handle", None):
             fl.fastlsq_factor_destroy(self.ctx, self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -52,7 +57,8 @@ class _Solve(torch.autograd.Function):
         r = torch.zeros((1, ld), dtype=torch.float64, device=fac.device)
         r[0, : fac.n_rows] = rhs
         beta = torch.empty((1, fac.n_feat), dtype=torch.float64, device=fac.device)
-        fl.fastlsq_factor_solve(fac.ctx, fac.handle, r, beta, max_refine=fac.max_refine)
+        fl.fastlsq_factor_solve(fac.ctx, fac.handle, r, beta, max_refine=fac.max_refine,
+                                refine_mode=fac.refine_mode, refine_tol=fac.refine_tol)
         actx.fac = fac
         return beta[0]
 
@@ -62,7 +68,7 @@ class _Solve(torch.autograd.Function):
         v = torch.empty(fac.n_feat, dtype=torch.float64, device=fac.device)
         grad_rhs = torch.empty(fac.n_rows, dtype=torch.float64, device=fac.device)
         fl.fastlsq_backward(fac.ctx, fac.handle, grad_beta.contiguous().to(torch.float64), v,
-                            grad_rhs, fac.A_op)
+                            grad_rhs, fac.A_op, max_iter=fac.adjoint_iters, tol=fac.adjoint_tol)
         return grad_rhs, None
 
 

@@ -138,6 +138,8 @@ extern "C" int fastlsq_create(fastlsq_ctx **out, int device, void *stream)
         e = cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_grid_bar, 64);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_grid_bar, 0, 64, ctx->stream);
     if (e == cudaSuccess) {
         // keep freed stream-ordered memory cached in the pool (no per-call OS round trips)
         cudaMemPool_t pool;
@@ -149,6 +151,7 @@ extern "C" int fastlsq_create(fastlsq_ctx **out, int device, void *stream)
     if (e != cudaSuccess) {
         int rc = (e == cudaErrorMemoryAllocation) ? FASTLSQ_ERR_NOMEM : FASTLSQ_ERR_CUDA;
         if (ctx->d_flag) cudaFree(ctx->d_flag);
+        if (ctx->d_grid_bar) cudaFree(ctx->d_grid_bar);
         delete ctx;
         return rc;
     }
@@ -233,6 +236,7 @@ extern "C" int fastlsq_destroy(fastlsq_ctx *ctx)
     for (int s = 0; s < FL_WS_COUNT; ++s)
         if (ctx->ws[s].ptr) cudaFree(ctx->ws[s].ptr);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
+    if (ctx->d_grid_bar) cudaFree(ctx->d_grid_bar);
     delete ctx;
     return 0;
 }
@@ -258,6 +262,8 @@ extern "C" int fastlsq_sync(fastlsq_ctx *ctx)
     if (e != cudaSuccess) return fl_cuda(ctx, e, "sync");
     if (flag) {
         cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
+        // a barrier that timed out may have left arrivals counted: start it afresh
+        if (flag == FL_DEVERR_TIMEOUT) cudaMemsetAsync(ctx->d_grid_bar, 0, 64, ctx->stream);
         if (flag == FL_DEVERR_NONFINITE) return fl_fail(ctx, FASTLSQ_ERR_NONFINITE, "non-finite value on the device");
         if (flag == FL_DEVERR_TIMEOUT) return fl_fail(ctx, FASTLSQ_ERR_TIMEOUT, "device-side wait timed out");
         return fl_fail(ctx, FASTLSQ_ERR_CUDA, "device error flag %d", flag);
@@ -337,7 +343,7 @@ extern "C" int fastlsq_eval_adjoint(fastlsq_ctx *ctx, const double *x, int64_t n
 static void factor_free(fastlsq_factor *f)
 {
     if (!f) return;
-    cudaStream_t s = f->ctx ? f->ctx->stream : nullptr;
+    cudaStream_t s = f->stream;
     if (f->F) cudaFreeAsync(f->F, s);
     if (f->tau) cudaFreeAsync(f->tau, s);
     if (f->T) cudaFreeAsync(f->T, s);
@@ -348,7 +354,8 @@ static void factor_free(fastlsq_factor *f)
 // either already in column n + r of F (from_factor) or computed from rhs64.
 template <typename T>
 static int solve_one(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, int r,
-                     const double *rhs64, double *beta64, int max_refine, double *norms_dev)
+                     const double *rhs64, double *beta64, int max_refine, int mode, double tol,
+                     double *norms_dev)
 {
     const int64_t n = f->n, m = f->m, m_aug = f->m_aug;
     const T *F = (const T *)f->F;
@@ -363,6 +370,10 @@ static int solve_one(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, i
     }
     FL_TRY(fl_trsv<T>(ctx, F, f->ld, n, y, dx, 0));
     FL_TRY(fl_to_f64<T>(ctx, dx, n, beta64, 0));
+    if (mode == FASTLSQ_REFINE_CGLS) {
+        if (max_refine > 0) return fl_refine_cgls(ctx, f, rhs64, beta64, max_refine, tol, norms_dev);
+        return 0;
+    }
     // classical iterative refinement: FP64 residual, correction with the factors
     for (int it = 0; it < max_refine; ++it) {
         FL_TRY(fl_residual<T>(ctx, f->A_refine, f->ld_refine, m, n, f->mu, m_aug, rhs64, beta64, y,
@@ -380,30 +391,34 @@ static int solve_one(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, i
 
 static int solve_all(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, const double *rhs,
                      int nrhs, int64_t ld_rhs, double *beta, int64_t ld_beta, int max_refine,
-                     fastlsq_solve_stats *stats)
+                     int mode, double tol, fastlsq_solve_stats *stats)
 {
     double *norms = nullptr;
     if (stats) {
-        norms = (double *)fl_ws(ctx, FL_WS_NORMS, sizeof(double) * 8);
+        norms = (double *)fl_ws(ctx, FL_WS_NORMS, sizeof(double) * 65);
         if (!norms) return FASTLSQ_ERR_NOMEM;
-        cudaMemsetAsync(norms, 0, sizeof(double) * 8, ctx->stream);
+        cudaMemsetAsync(norms, 0, sizeof(double) * 65, ctx->stream);
     }
     for (int r = 0; r < nrhs; ++r) {
         double *nr = (stats && r == 0) ? norms : nullptr;
-        if (f->prec == FASTLSQ_PREC_FP64)
-            FL_TRY(solve_one<double>(ctx, f, nrhs_in_F, r, rhs + r * ld_rhs, beta + r * ld_beta, 0, nr));
+        if (f->prec == FASTLSQ_PREC_FP64 && mode != FASTLSQ_REFINE_CGLS)
+            FL_TRY(solve_one<double>(ctx, f, nrhs_in_F, r, rhs + r * ld_rhs, beta + r * ld_beta, 0,
+                                     mode, tol, nr));
+        else if (f->prec == FASTLSQ_PREC_FP64)
+            FL_TRY(solve_one<double>(ctx, f, nrhs_in_F, r, rhs + r * ld_rhs, beta + r * ld_beta,
+                                     max_refine, mode, tol, nr));
         else
             FL_TRY(solve_one<float>(ctx, f, nrhs_in_F, r, rhs + r * ld_rhs, beta + r * ld_beta,
-                                    max_refine, nr));
+                                    max_refine, mode, tol, nr));
     }
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         int rc = fastlsq_sync(ctx);
-        double h[8] = {0};
+        double h[65] = {0};
         cudaError_t e = cudaMemcpy(h, norms, sizeof(h), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return fl_cuda(ctx, e, "stats readback");
-        for (int i = 0; i < 8; ++i) stats->resid_norm[i] = h[i];
-        stats->refine_steps = (f->prec == FASTLSQ_PREC_MIXED) ? max_refine : 0;
+        for (int i = 0; i < 65; ++i) stats->resid_norm[i] = h[i];
+        stats->refine_steps = (f->prec == FASTLSQ_PREC_MIXED || mode == FASTLSQ_REFINE_CGLS) ? max_refine : 0;
         stats->nb = f->nb;
         stats->tensor_core = f->tensor_core;
         stats->status = rc;
@@ -416,8 +431,8 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
                              fastlsq_dtype a_dtype, int64_t ldA, int64_t n_rows, int64_t n_feat,
                              double mu, const double *rhs, int32_t nrhs, int64_t ld_rhs,
                              double *beta, int64_t ld_beta, const double *A_refine,
-                             int64_t ld_refine, int32_t max_refine, fastlsq_factor **keep,
-                             fastlsq_solve_stats *stats)
+                             int64_t ld_refine, int32_t max_refine, int32_t refine_mode,
+                             double refine_tol, fastlsq_factor **keep, fastlsq_solve_stats *stats)
 {
     if (!ctx) return FASTLSQ_ERR_INVALID;
     if (keep) *keep = nullptr;
@@ -428,13 +443,17 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
     if (n_rows < 0 || n_feat < 1 || n_feat > FL_MAX_FEAT || ldA < n_rows || nrhs < 0 ||
         (nrhs > 0 && (ld_rhs < n_rows || ld_beta < n_feat)) || mu < 0 || !std::isfinite(mu))
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "lstsq: bad sizes");
-    if (max_refine < 0 || max_refine > 7) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "lstsq: max_refine 0..7");
+    if (refine_mode != FASTLSQ_REFINE_CLASSICAL && refine_mode != FASTLSQ_REFINE_CGLS)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "lstsq: refine_mode");
+    if (max_refine < 0 || max_refine > (refine_mode == FASTLSQ_REFINE_CGLS ? 64 : 7))
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "lstsq: max_refine out of range");
     const int64_t m_aug = n_rows + (mu > 0 ? n_feat : 0);
     if (m_aug < n_feat)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "lstsq: %lld rows < %lld features needs mu > 0",
                        (long long)n_rows, (long long)n_feat);
     if (!A || (nrhs > 0 && (!rhs || !beta))) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "lstsq: null array");
-    if (prec == FASTLSQ_PREC_MIXED && max_refine > 0 && !A_refine)
+    if ((prec == FASTLSQ_PREC_MIXED || refine_mode == FASTLSQ_REFINE_CGLS) && max_refine > 0 &&
+        !A_refine && !(prec == FASTLSQ_PREC_FP64))
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "lstsq: refinement needs the FP64 operator");
     if (A_refine && ld_refine < n_rows) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "lstsq: ld_refine");
 
@@ -446,6 +465,7 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
     fastlsq_factor *f = new (std::nothrow) fastlsq_factor();
     if (!f) return FASTLSQ_ERR_NOMEM;
     f->ctx = ctx;
+    f->stream = ctx->stream;
     f->prec = prec;
     f->m = n_rows;
     f->n = n_feat;
@@ -485,7 +505,8 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
     }
     if (rc == 0 && nrhs > 0)
         rc = solve_all(ctx, f, nrhs, rhs, nrhs, ld_rhs, beta, ld_beta,
-                       prec == FASTLSQ_PREC_MIXED ? max_refine : 0, stats);
+                       (prec == FASTLSQ_PREC_MIXED || refine_mode == FASTLSQ_REFINE_CGLS) ? max_refine : 0,
+                       refine_mode, refine_tol, stats);
     if (rc < 0 || !keep) {
         factor_free(f);
         return rc;
@@ -496,16 +517,21 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
 
 extern "C" int fastlsq_factor_solve(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs,
                                     int32_t nrhs, int64_t ld_rhs, double *beta, int64_t ld_beta,
-                                    int32_t max_refine, fastlsq_solve_stats *stats)
+                                    int32_t max_refine, int32_t refine_mode, double refine_tol,
+                                    fastlsq_solve_stats *stats)
 {
     if (!ctx || !f) return FASTLSQ_ERR_INVALID;
     if (nrhs < 0 || (nrhs > 0 && (!rhs || !beta || ld_rhs < f->m || ld_beta < f->n)))
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "factor_solve: bad arguments");
-    if (max_refine < 0 || max_refine > 7) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "max_refine 0..7");
-    if (f->prec == FASTLSQ_PREC_MIXED && max_refine > 0 && !f->A_refine)
+    if (refine_mode != FASTLSQ_REFINE_CLASSICAL && refine_mode != FASTLSQ_REFINE_CGLS)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "factor_solve: refine_mode");
+    if (max_refine < 0 || max_refine > (refine_mode == FASTLSQ_REFINE_CGLS ? 64 : 7))
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "factor_solve: max_refine out of range");
+    const bool refine = (f->prec == FASTLSQ_PREC_MIXED || refine_mode == FASTLSQ_REFINE_CGLS);
+    if (refine && max_refine > 0 && !f->A_refine)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "factor_solve: factor has no FP64 operator");
-    return solve_all(ctx, f, 0, rhs, nrhs, ld_rhs, beta, ld_beta,
-                     f->prec == FASTLSQ_PREC_MIXED ? max_refine : 0, stats);
+    return solve_all(ctx, f, 0, rhs, nrhs, ld_rhs, beta, ld_beta, refine ? max_refine : 0,
+                     refine_mode, refine_tol, stats);
 }
 
 extern "C" int fastlsq_factor_destroy(fastlsq_factor *f)
@@ -533,11 +559,19 @@ static int backward_t(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *g
 }
 
 extern "C" int fastlsq_backward(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *grad_beta,
-                                double *v, double *grad_rhs, const double *A_op, int64_t ld_op)
+                                double *v, double *grad_rhs, const double *A_op, int64_t ld_op,
+                                int32_t max_iter, double tol)
 {
     if (!ctx || !f || !grad_beta || !v) return FASTLSQ_ERR_INVALID;
-    if (f->prec == FASTLSQ_PREC_FP64) FL_TRY(backward_t<double>(ctx, f, grad_beta, v));
-    else FL_TRY(backward_t<float>(ctx, f, grad_beta, v));
+    if (max_iter < 0 || max_iter > 64) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "backward: max_iter 0..64");
+    if (f->prec == FASTLSQ_PREC_FP64) {
+        FL_TRY(backward_t<double>(ctx, f, grad_beta, v));
+    } else if (max_iter > 0) {
+        if (!f->A_refine) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "backward: PCG needs the FP64 operator");
+        FL_TRY(fl_normal_pcg(ctx, f, grad_beta, v, max_iter, tol));
+    } else {
+        FL_TRY(backward_t<float>(ctx, f, grad_beta, v));
+    }
     if (grad_rhs) {
         const double *Aop = A_op ? A_op : f->A_refine;
         int64_t ld = A_op ? ld_op : f->ld_refine;

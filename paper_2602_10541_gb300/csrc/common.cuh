@@ -41,6 +41,7 @@ enum fl_slot {
     FL_WS_NEWTON_VEC,      // Newton: vectors
     FL_WS_GRAM,            // panel Gram partials
     FL_WS_NORMS,           // residual norms for solve stats
+    FL_WS_KRYLOV,          // Krylov refinement vectors and scalars
     FL_WS_COUNT
 };
 
@@ -61,6 +62,7 @@ struct fastlsq_ctx {
     std::string last_error;
     fl_buffer ws[FL_WS_COUNT];
     int *d_flag = nullptr;          // device error flag (int)
+    void *d_grid_bar = nullptr;     // grid barrier state (count, generation) of this context
     int use_tensor_core = 0;        // tcgen05 trailing updates for the MIXED path
     // Cody-Waite split of 2 pi for the FP32 argument reduction (host-derived)
     float cw2pi[3] = {0.f, 0.f, 0.f};
@@ -80,7 +82,8 @@ struct fl_prof_scope {
 #define FL_PROF_N(ctx, kid, n) fl_prof_scope _fl_prof_scope((ctx), (kid), (n))
 
 struct fastlsq_factor {
-    fastlsq_ctx *ctx = nullptr;
+    fastlsq_ctx *ctx = nullptr;  // creating context (not dereferenced by _destroy)
+    cudaStream_t stream = nullptr;
     int prec = 0;              // fastlsq_prec
     int64_t m = 0, n = 0;      // rows of A and features
     int64_t m_aug = 0, ld = 0; // factored rows (m + n when mu > 0), leading dimension

@@ -271,10 +271,12 @@ extern "C" int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p,
             NT_TRY(fl_launch_assemble_f32(ctx, opI, p->x_bc, n_bc, W, b, n, pref, B.J32, m, n_int,
                                           p->bc_weight));
             NT_TRY(fastlsq_lstsq(ctx, FASTLSQ_PREC_MIXED, B.J32, FASTLSQ_F32, m, m, n, o->mu, B.negR,
-                                 1, m, B.delta, n, B.J64, m, o->max_refine, nullptr, nullptr));
+                                 1, m, B.delta, n, B.J64, m, o->max_refine, FASTLSQ_REFINE_CGLS,
+                                 o->refine_tol > 0 ? o->refine_tol : 1e-10, nullptr, nullptr));
         } else {
             NT_TRY(fastlsq_lstsq(ctx, FASTLSQ_PREC_FP64, B.J64, FASTLSQ_F64, m, m, n, o->mu, B.negR,
-                                 1, m, B.delta, n, nullptr, 0, 0, nullptr, nullptr));
+                                 1, m, B.delta, n, nullptr, 0, 0, FASTLSQ_REFINE_CLASSICAL, 0.0,
+                                 nullptr, nullptr));
         }
         // backtracking line search on ||R||
         double a = 1.0, rr_new = 0.0;

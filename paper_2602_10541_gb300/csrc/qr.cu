@@ -24,8 +24,10 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int PANEL_THREADS = 512;
+constexpr int PANEL_THREADS = 1024;
 constexpr int PANEL_WARPS = PANEL_THREADS / 32;
+constexpr int APPLY_THREADS = 512;
+constexpr int APPLY_WARPS = APPLY_THREADS / 32;
 constexpr int CL_MAX = 16;
 
 template <typename T> __device__ __forceinline__ T fl_sqrt(T v);
@@ -45,7 +47,7 @@ struct PanelSmem {
     static size_t bytes(int rpc)
     {
         return sizeof(T) * ((size_t)rpc * LD + PANEL_WARPS * 32 + 2 * (CL_MAX + 1) * NB +
-                            NB * (NB + 1) + NB);
+                            2 * NB * (NB + 1) + NB);
     }
 };
 
@@ -54,23 +56,28 @@ struct PanelSmem {
 // owns every diagonal row.  For each column j one cluster-wide exchange (DSMEM
 // stores + one cluster barrier) delivers: the dot products of column j with
 // every column l > j below the diagonal (sum over rows i > j of a_ij a_il), the
-// diagonal row a_j., and the Gram entries v_l^T v_{j-1} (l < j-1) needed by the
-// T recurrence T(0:c, c) = -tau_c T(0:c, 0:c) V(:, 0:c)^T v_c.  The update pass
-// that applies H_j to the rows also accumulates the next column's dots and this
-// column's Gram entries, so each column costs one pass over the slice.
+// diagonal row a_j., and the Gram entries v_l^T v_{j-1} (l < j-1) that the
+// compact-WY recurrence T(0:c, c) = -tau_c T(0:c, 0:c) V(:, 0:c)^T v_c needs
+// (T is formed once at the end).  The update pass that applies H_j to the rows
+// also accumulates the next column's dots and this column's Gram entries, so a
+// column costs one pass over the slice; each thread updates four independent
+// rows per iteration and the two rows next to the diagonal are handled apart.
 template <typename T, int NB>
 __global__ void __launch_bounds__(PANEL_THREADS, 1)
 k_panel(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int rpc,
         T *__restrict__ tau_out, T *__restrict__ T_out, int *flag)
 {
     constexpr int LDP = PanelSmem<T, NB>::LD;
-    constexpr int RPW = 32 / NB;           // rows per warp step
+    constexpr int RPW = 32 / NB;                 // rows per warp step
+    constexpr int RSTEP = PANEL_WARPS * RPW;     // rows per block step
+    constexpr int U = 4;                         // rows per thread per iteration
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *P = reinterpret_cast<T *>(smem_raw);
     T *red = P + (size_t)rpc * LDP;                 // [PANEL_WARPS][32]
     T *xbuf = red + PANEL_WARPS * 32;               // [2][CL_MAX + 1][NB]
-    T *Tm = xbuf + 2 * (CL_MAX + 1) * NB;           // [NB][NB + 1] (row-major, T[row][col])
-    T *tauv = Tm + NB * (NB + 1);                   // [NB]
+    T *Tm = xbuf + 2 * (CL_MAX + 1) * NB;           // [NB][NB + 1] T(row, col)
+    T *G = Tm + NB * (NB + 1);                      // [NB][NB + 1] G(q, c) = v_q^T v_c
+    T *tauv = G + NB * (NB + 1);                    // [NB]
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -82,32 +89,30 @@ k_panel(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int rpc,
     const int warp = threadIdx.x >> 5;
     const int l = lane % NB;       // column handled by this lane
     const int sub = lane / NB;     // row sub-slot within the warp step
+    const int rb0 = warp * RPW + sub;
     const unsigned FULL = 0xffffffffu;
 
-    // load the slice (coalesced: consecutive threads take consecutive rows of a column)
     for (int idx = threadIdx.x; idx < nown * NB; idx += PANEL_THREADS) {
         int c = idx / nown, r = idx % nown;
         P[r * LDP + c] = (c < ncols) ? F[(k + c0 + r) + (k + c) * ld] : T(0);
     }
-    for (int idx = threadIdx.x; idx < NB * (NB + 1); idx += PANEL_THREADS) Tm[idx] = T(0);
+    for (int idx = threadIdx.x; idx < 2 * NB * (NB + 1); idx += PANEL_THREADS) Tm[idx] = T(0);
     __syncthreads();
 
     // dots of column 0 with every column, rows i > 0
     T acc = T(0);
-    for (int rb = warp * RPW; rb < nown; rb += PANEL_WARPS * RPW) {
-        const int r = rb + sub;
-        if (r < nown && c0 + r > 0) acc += P[r * LDP] * P[r * LDP + l];
-    }
+    for (int r = rb0; r < nown; r += RSTEP)
+        if (c0 + r > 0) acc += P[r * LDP] * P[r * LDP + l];
 
     for (int j = 0; j <= ncols; ++j) {
         const int par = j & 1;
-        // block reduction of acc over warps and row sub-slots -> warp 0 lane l
         red[warp * 32 + lane] = acc;
         __syncthreads();
         if (warp == 0) {
             T part = T(0);
             if (lane < NB)
                 for (int w = 0; w < PANEL_WARPS; ++w)
+#pragma unroll
                     for (int s = 0; s < RPW; ++s) part += red[w * 32 + s * NB + lane];
             T top = (rank == 0 && j < ncols && lane < NB) ? P[j * LDP + lane] : T(0);
             if (lane < NB) {
@@ -122,19 +127,8 @@ k_panel(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int rpc,
         const T *xb = xbuf + par * (CL_MAX + 1) * NB;
         T dl = T(0);
         for (int s = 0; s < CL; ++s) dl += xb[s * NB + l];   // fixed order: same sum everywhere
-
-        // T column j-1 from the Gram entries G(q, j-1) = dl on lanes q < j-1
-        if (j >= 1 && warp == 0 && rank == 0) {
-            const int c = j - 1;
-            T tc = tauv[c];
-            T sum = T(0);
-            for (int q = 0; q < c; ++q) {
-                T gq = __shfl_sync(FULL, dl, q);       // lanes 0..NB-1 carry columns
-                if (lane < c && q >= lane) sum += Tm[lane * (NB + 1) + q] * gq;
-            }
-            if (lane < c) Tm[lane * (NB + 1) + c] = -tc * sum;
-            if (lane == c) Tm[c * (NB + 1) + c] = tc;
-        }
+        // Gram column j-1 (lanes l < j-1), kept for the T recurrence at the end
+        if (j >= 1 && warp == 0 && lane < NB && rank == 0 && l < j - 1) G[l * (NB + 1) + (j - 1)] = dl;
         if (j == ncols) break;
 
         // reflector for column j (every thread computes the same scalars)
@@ -153,46 +147,79 @@ k_panel(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int rpc,
         }
         const T wl = (l > j) ? tauj * (topl + inv * dl) : T(0);
         if (threadIdx.x == 0) tauv[j] = tauj;
+        const int jn = (j + 1) % NB;
 
-        // apply H_j to the owned rows; accumulate next-column dots (l > j) and
-        // Gram entries v_l^T v_j (l < j)
+        // apply H_j to the owned rows below j+1: next-column dots (l > j) and Gram
+        // entries v_l^T v_j (l < j); U independent rows per iteration
         acc = T(0);
-        for (int rb = warp * RPW; rb < nown; rb += PANEL_WARPS * RPW) {   // warp-uniform bound
-            const int r = rb + sub;
-            const bool valid = r < nown;
-            const int64_t gi = c0 + r;
-            T pj = valid ? P[r * LDP + j] : T(0);
-            T pl = valid ? P[r * LDP + l] : T(0);
+        for (int r0 = rb0 - sub; r0 < nown; r0 += U * RSTEP) {      // warp-uniform bound
+            T pj[U], pl[U];
+            bool ok[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = r0 + sub + u * RSTEP;
+                ok[u] = (r < nown) && (c0 + r > j + 1);
+                pj[u] = ok[u] ? P[r * LDP + j] : T(0);
+                pl[u] = ok[u] ? P[r * LDP + l] : T(0);
+            }
             __syncwarp();
-            T nl = pl;
-            if (valid && gi >= j) {          // rows gi < j hold finished R rows
-                if (gi == j) {
-                    if (l > j) { nl = pl - wl; P[r * LDP + l] = nl; }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = r0 + sub + u * RSTEP;
+                const T vj = pj[u] * inv;
+                const T nl = (l > j) ? pl[u] - wl * vj : pl[u];
+                if (ok[u]) P[r * LDP + l] = (l == j) ? vj : nl;
+                const T nxt = __shfl_sync(FULL, nl, sub * NB + jn);
+                const T add = (l < j) ? pl[u] * vj : ((l > j) ? nxt * nl : T(0));
+                acc += ok[u] ? add : T(0);
+            }
+        }
+        // the diagonal row j and the next row j + 1, on the rank that owns each
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int64_t g = j + q;                         // panel-local row
+            const int r = (int)(g - c0);
+            if (g >= mp || g >= ncols + 1 || r < 0 || r >= nown) continue;   // uniform per CTA
+            if (warp != (r % RSTEP) / RPW) continue;        // owner warp (uniform)
+            const bool mine = (sub == (r % RSTEP) % RPW);
+            T pj = mine ? P[r * LDP + j] : T(0);
+            T pl = mine ? P[r * LDP + l] : T(0);
+            __syncwarp();
+            if (mine) {
+                if (q == 0) {                     // diagonal row: H_j maps it to (beta, a - w)
+                    if (l > j) P[r * LDP + l] = pl - wl;
                     if (l == j) P[r * LDP + j] = beta;
-                    if (l < j) acc += pl;    // v_j has a unit entry in row j
-                } else {
-                    T vj = pj * inv;
-                    if (l > j) { nl = pl - wl * vj; P[r * LDP + l] = nl; }
-                    else if (l == j) P[r * LDP + j] = vj;
+                    if (l < j) acc += pl;         // v_j has a unit entry in row j
+                } else {                          // row j + 1: update, Gram only
+                    const T vj = pj * inv;
+                    if (l > j) P[r * LDP + l] = pl - wl * vj;
+                    if (l == j) P[r * LDP + j] = vj;
                     if (l < j) acc += pl * vj;
                 }
             }
-            T nxt = __shfl_sync(FULL, nl, sub * NB + ((j + 1) % NB));
-            if (valid && gi > j + 1 && l > j) acc += nxt * nl;
         }
     }
 
-    // write back the slice, tau and T
+    // write back the slice; rank 0 forms T and writes tau, T
     __syncthreads();
     for (int idx = threadIdx.x; idx < nown * NB; idx += PANEL_THREADS) {
         int c = idx / nown, r = idx % nown;
         if (c < ncols) F[(k + c0 + r) + (k + c) * ld] = P[r * LDP + c];
     }
-    if (rank == 0) {
-        for (int idx = threadIdx.x; idx < NB; idx += PANEL_THREADS)
-            tau_out[idx] = (idx < ncols) ? tauv[idx] : T(0);
-        // T stored column-major NB x NB
-        for (int idx = threadIdx.x; idx < NB * NB; idx += PANEL_THREADS) {
+    if (rank == 0 && warp == 0) {
+        // T(c, c) = tau_c ; T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c)   (lane = row)
+        for (int c = 0; c < ncols; ++c) {
+            const T tc = tauv[c];
+            T sum = T(0);
+            if (lane < c)
+                for (int q = lane; q < c; ++q) sum += Tm[lane * (NB + 1) + q] * G[q * (NB + 1) + c];
+            __syncwarp();
+            if (lane < c) Tm[lane * (NB + 1) + c] = -tc * sum;
+            if (lane == c) Tm[c * (NB + 1) + c] = tc;
+            __syncwarp();
+        }
+        for (int idx = lane; idx < NB; idx += 32) tau_out[idx] = (idx < ncols) ? tauv[idx] : T(0);
+        for (int idx = lane; idx < NB * NB; idx += 32) {
             int col = idx / NB, row = idx % NB;
             T_out[idx] = (col < ncols && row < ncols) ? Tm[row * (NB + 1) + col] : T(0);
         }
@@ -329,18 +356,42 @@ k_trail_c(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_
     }
 }
 
-// y <- Q^T y (forward) or Q y (backward) for vectors y [m_aug] of type T, on one
-// cluster: per panel, dots s_l = sum_i V(i,l) y_i (cluster exchange), then
-// w = T^T s (Q^T) or T s (Q), then y_i -= sum_l V(i,l) w_l.
+// Sum of vals[0..NB) over the 32 lanes, scattered: on exit lane L holds the sum for
+// index L % NB in vals[0] (butterfly for the lane bits above NB, then a
+// reduce-scatter with NB - 1 shuffles).
 template <typename T, int NB>
-__global__ void __launch_bounds__(PANEL_THREADS, 1)
+__device__ __forceinline__ T warp_reduce_scatter(T (&vals)[NB], int lane)
+{
+#pragma unroll
+    for (int s = 16; s >= NB; s >>= 1)
+#pragma unroll
+        for (int i = 0; i < NB; ++i) vals[i] += __shfl_xor_sync(0xffffffffu, vals[i], s);
+#pragma unroll
+    for (int s = NB / 2; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            T send = up ? vals[i] : vals[i + s];
+            T keep = up ? vals[i + s] : vals[i];
+            vals[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return vals[0];
+}
+
+// y <- Q^T y (transpose) or Q y for a vector y [m_aug] of type T, on one cluster:
+// per panel, dots s_l = sum_i V(i,l) y_i (cluster exchange), w = T^T s (Q^T) or
+// T s (Q), then y_i -= sum_l V(i,l) w_l.  Rows below the unit-diagonal block read
+// V without masking.
+template <typename T, int NB>
+__global__ void __launch_bounds__(APPLY_THREADS, 1)
 k_apply_q(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n, const T *__restrict__ Tall,
           T *__restrict__ y, int transpose)
 {
-    __shared__ T red[PANEL_WARPS][NB];
+    __shared__ T red[APPLY_WARPS][NB];
     __shared__ T xbuf[2][CL_MAX][NB];
     __shared__ T w[NB];
-    __shared__ T sT[NB][NB];
+    __shared__ T sT[NB][NB + 1];
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int CL = (int)cluster.num_blocks();
@@ -353,27 +404,30 @@ k_apply_q(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n, const T
         const int64_t k = (int64_t)p * NB;
         const int ncols = (int)fl_min64(NB, n - k);
         const int par = step & 1;
+        const T *Vp = F + k + k * ld;              // V(i, q) = Vp[i + q * ld] below the block
         T acc[NB];
 #pragma unroll
         for (int q = 0; q < NB; ++q) acc[q] = T(0);
-        for (int64_t i = fl_max64(r_lo, k) + threadIdx.x; i < r_hi; i += PANEL_THREADS) {
-            T yi = y[i];
+        for (int64_t i = fl_max64(r_lo, k) + threadIdx.x; i < r_hi; i += APPLY_THREADS) {
+            const int64_t li = i - k;
+            const T yi = y[i];
+            if (li >= NB) {
 #pragma unroll
-            for (int q = 0; q < NB; ++q) acc[q] += v_at(F, ld, k, i - k, q, ncols) * yi;
-        }
-        // reduce acc over the block: warp shuffle then smem across warps
+                for (int q = 0; q < NB; ++q)
+                    if (q < ncols) acc[q] += Vp[li + q * ld] * yi;
+            } else {
 #pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            T v = acc[q];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][q] = v;
+                for (int q = 0; q < NB; ++q) acc[q] += v_at(F, ld, k, li, q, ncols) * yi;
+            }
         }
-        for (int idx = threadIdx.x; idx < NB * NB; idx += PANEL_THREADS)
+        const T part = warp_reduce_scatter<T, NB>(acc, lane);
+        if (lane < NB) red[warp][lane] = part;
+        for (int idx = threadIdx.x; idx < NB * NB; idx += APPLY_THREADS)
             sT[idx % NB][idx / NB] = Tall[(int64_t)p * NB * NB + idx];
         __syncthreads();
         if (warp == 0 && lane < NB) {
             T s = T(0);
-            for (int ww = 0; ww < PANEL_WARPS; ++ww) s += red[ww][lane];
+            for (int ww = 0; ww < APPLY_WARPS; ++ww) s += red[ww][lane];
             for (int dst = 0; dst < CL; ++dst) {
                 T *rb = cluster.map_shared_rank(&xbuf[0][0][0], dst);
                 rb[(par * CL_MAX + rank) * NB + lane] = s;
@@ -396,10 +450,17 @@ k_apply_q(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n, const T
             if (lane < NB) w[lane] = wl;
         }
         __syncthreads();
-        for (int64_t i = fl_max64(r_lo, k) + threadIdx.x; i < r_hi; i += PANEL_THREADS) {
+        for (int64_t i = fl_max64(r_lo, k) + threadIdx.x; i < r_hi; i += APPLY_THREADS) {
+            const int64_t li = i - k;
             T s = T(0);
+            if (li >= NB) {
 #pragma unroll
-            for (int q = 0; q < NB; ++q) s += v_at(F, ld, k, i - k, q, ncols) * w[q];
+                for (int q = 0; q < NB; ++q)
+                    if (q < ncols) s += Vp[li + q * ld] * w[q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < NB; ++q) s += v_at(F, ld, k, li, q, ncols) * w[q];
+            }
             y[i] -= s;
         }
         __syncthreads();
@@ -407,73 +468,101 @@ k_apply_q(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n, const T
 }
 
 // Back substitution R x = y (R: upper triangle of F, n x n) on one CTA of 1024
-// threads, 32-row blocks bottom-up.  y: [n] in, x: [n] out (may alias y).
+// threads, 32-row blocks bottom-up.  Per block: the 32 x (n - r1) strip right of
+// the block is contracted with the solved x (32 warps, 4 independent loads in
+// flight per thread), the 32 x 32 diagonal block is staged in shared memory, and
+// warp 0 substitutes from shared memory.  y: [n] in, x: [n] out (may alias y).
 template <typename T>
 __global__ void __launch_bounds__(1024, 1)
-k_trsv_upper(const T *__restrict__ F, int64_t ld, int64_t n, const T *y, T *x, int *flag)
+k_trsv_upper(const T *__restrict__ F, int64_t ld, int64_t n, const T *y, T *x, int *flag,
+             const int *skip)
 {
+    if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sx = reinterpret_cast<T *>(smem_raw);   // [n]
     __shared__ T red[32][33];
+    __shared__ T D[32][33];                     // diagonal block D(row, col)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nblk = (n + 31) / 32;
     for (int64_t bi = nblk - 1; bi >= 0; --bi) {
         const int64_t r0 = bi * 32, r1 = fl_min64(n, r0 + 32);
         const int64_t row = r0 + lane;
-        T acc = T(0);
-        if (row < r1)
-            for (int64_t c = r1 + warp; c < n; c += 32) acc += F[row + c * ld] * sx[c];
-        red[warp][lane] = acc;
+        const bool rv = row < r1;
+        // diagonal block: thread (warp = column, lane = row)
+        D[lane][warp] = (rv && r0 + warp < r1) ? F[row + (r0 + warp) * ld] : T(0);
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        if (rv) {
+            int64_t c = r1 + warp;
+            for (; c + 96 < n; c += 128) {
+                a0 += F[row + c * ld] * sx[c];
+                a1 += F[row + (c + 32) * ld] * sx[c + 32];
+                a2 += F[row + (c + 64) * ld] * sx[c + 64];
+                a3 += F[row + (c + 96) * ld] * sx[c + 96];
+            }
+            for (; c < n; c += 32) a0 += F[row + c * ld] * sx[c];
+        }
+        red[warp][lane] = (a0 + a1) + (a2 + a3);
         __syncthreads();
         if (warp == 0) {
             T s = T(0);
             for (int ww = 0; ww < 32; ++ww) s += red[ww][lane];
-            if (row < r1) s = y[row] - s;
-            for (int64_t rr = r1 - 1; rr >= r0; --rr) {
-                const int li = (int)(rr - r0);
-                T diag = F[rr + rr * ld];
-                T xv = __shfl_sync(0xffffffffu, s, li) / diag;
+            if (rv) s = y[row] - s;
+            const int nr = (int)(r1 - r0);
+            for (int li = nr - 1; li >= 0; --li) {
+                T xv = __shfl_sync(0xffffffffu, s, li) / D[li][li];
                 if (!fl_isfinite(xv)) raise_flag(flag, FL_DEVERR_NONFINITE);
                 if (lane == li) s = xv;
-                if (lane < li && row < r1) s -= F[row + rr * ld] * xv;
+                if (lane < li) s -= D[lane][li] * xv;
             }
-            if (row < r1) sx[row] = s;
+            if (rv) sx[row] = s;
         }
         __syncthreads();
     }
     for (int64_t i = threadIdx.x; i < n; i += 1024) x[i] = sx[i];
 }
 
-// Forward substitution R^T x = y, 32-row blocks top-down (same launch shape).
+// Forward substitution R^T x = y, 32-row blocks top-down (same launch shape):
+// warp w contracts column r0 + w of R above the block with the solved x.
 template <typename T>
 __global__ void __launch_bounds__(1024, 1)
-k_trsv_upper_t(const T *__restrict__ F, int64_t ld, int64_t n, const T *y, T *x, int *flag)
+k_trsv_upper_t(const T *__restrict__ F, int64_t ld, int64_t n, const T *y, T *x, int *flag,
+               const int *skip)
 {
+    if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sx = reinterpret_cast<T *>(smem_raw);
     __shared__ T sdot[32];
+    __shared__ T D[32][33];                     // D(row, col) of the diagonal block of R
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nblk = (n + 31) / 32;
     for (int64_t bi = 0; bi < nblk; ++bi) {
         const int64_t r0 = bi * 32, r1 = fl_min64(n, r0 + 32);
-        // warp w computes sum_{c < r0} R(c, r0 + w) x_c (column r0 + w of R)
         const int64_t col = r0 + warp;
-        T acc = T(0);
-        if (col < r1)
-            for (int64_t c = lane; c < r0; c += 32) acc += F[c + col * ld] * sx[c];
+        D[lane][warp] = (r0 + lane < r1 && col < r1) ? F[(r0 + lane) + col * ld] : T(0);
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        if (col < r1) {
+            int64_t c = lane;
+            for (; c + 96 < r0; c += 128) {
+                a0 += F[c + col * ld] * sx[c];
+                a1 += F[c + 32 + col * ld] * sx[c + 32];
+                a2 += F[c + 64 + col * ld] * sx[c + 64];
+                a3 += F[c + 96 + col * ld] * sx[c + 96];
+            }
+            for (; c < r0; c += 32) a0 += F[c + col * ld] * sx[c];
+        }
+        T acc = (a0 + a1) + (a2 + a3);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) sdot[warp] = acc;
         __syncthreads();
         if (warp == 0) {
             const int64_t row = r0 + lane;
             T s = (row < r1) ? y[row] - sdot[lane] : T(0);
-            for (int64_t rr = r0; rr < r1; ++rr) {
-                const int li = (int)(rr - r0);
-                T diag = F[rr + rr * ld];
-                T xv = __shfl_sync(0xffffffffu, s, li) / diag;
+            const int nr = (int)(r1 - r0);
+            for (int li = 0; li < nr; ++li) {
+                T xv = __shfl_sync(0xffffffffu, s, li) / D[li][li];
                 if (!fl_isfinite(xv)) raise_flag(flag, FL_DEVERR_NONFINITE);
                 if (lane == li) s = xv;
-                if (lane > li && row < r1) s -= F[rr + row * ld] * xv;
+                if (lane > li) s -= D[li][lane] * xv;
             }
             if (row < r1) sx[row] = s;
         }
@@ -558,8 +647,10 @@ __global__ void k_extract_rhs(const T *__restrict__ F, int64_t ld, int64_t n, in
 }
 
 template <typename T>
-__global__ void k_to_f64(const T *__restrict__ src, int64_t n, double *__restrict__ dst, int add)
+__global__ void k_to_f64(const T *__restrict__ src, int64_t n, double *__restrict__ dst, int add,
+                         const int *skip)
 {
+    if (skip && *skip) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (add) dst[i] += (double)src[i];
@@ -568,8 +659,9 @@ __global__ void k_to_f64(const T *__restrict__ src, int64_t n, double *__restric
 
 template <typename T>
 __global__ void k_from_f64(const double *__restrict__ src, int64_t n, int64_t n_total,
-                           T *__restrict__ dst)
+                           T *__restrict__ dst, const int *skip)
 {
+    if (skip && *skip) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_total) dst[i] = (i < n) ? (T)src[i] : T(0);
 }
@@ -633,7 +725,7 @@ int fl_panel_capacity_nb(fastlsq_ctx *ctx, int64_t m_aug, size_t elem)
     for (int nb = 32; nb >= 8; nb /= 2) {
         int64_t rpc = fl_cdiv(m_aug, CL_MAX);
         size_t bytes = elem * ((size_t)rpc * (nb + 1) + PANEL_WARPS * 32 + 2 * (CL_MAX + 1) * nb +
-                               nb * (nb + 1) + nb);
+                               2 * nb * (nb + 1) + nb);
         if (bytes <= (size_t)ctx->max_smem_optin) return nb;
     }
     return 0;
@@ -741,7 +833,7 @@ int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t 
     int CL = CL_MAX;
     while (CL > 1 && fl_cdiv(m_aug, CL) < 256) CL >>= 1;
     cfg.gridDim = dim3(CL);
-    cfg.blockDim = dim3(PANEL_THREADS);
+    cfg.blockDim = dim3(APPLY_THREADS);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = ctx->stream;
     cudaLaunchAttribute at[1];
@@ -778,7 +870,8 @@ template int fl_apply_q<double>(fastlsq_ctx *, const double *, int64_t, int64_t,
                                 const double *, double *, int);
 
 template <typename T>
-int fl_trsv(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const T *y, T *x, int transpose)
+int fl_trsv(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const T *y, T *x, int transpose,
+            const int *skip)
 {
     FL_TRY((set_panel_attrs<T, 32>(ctx)));
     size_t smem = sizeof(T) * (size_t)n;
@@ -787,16 +880,16 @@ int fl_trsv(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const T *y, T *
                        (long long)n);
     FL_PROF(ctx, FASTLSQ_K_TRSV);
     if (transpose)
-        k_trsv_upper_t<T><<<1, 1024, smem, ctx->stream>>>(F, ld, n, y, x, ctx->d_flag);
+        k_trsv_upper_t<T><<<1, 1024, smem, ctx->stream>>>(F, ld, n, y, x, ctx->d_flag, skip);
     else
-        k_trsv_upper<T><<<1, 1024, smem, ctx->stream>>>(F, ld, n, y, x, ctx->d_flag);
+        k_trsv_upper<T><<<1, 1024, smem, ctx->stream>>>(F, ld, n, y, x, ctx->d_flag, skip);
     FL_CHECK_LAUNCH(ctx, "trsv");
     return 0;
 }
 template int fl_trsv<float>(fastlsq_ctx *, const float *, int64_t, int64_t, const float *,
-                            float *, int);
+                            float *, int, const int *);
 template int fl_trsv<double>(fastlsq_ctx *, const double *, int64_t, int64_t, const double *,
-                             double *, int);
+                             double *, int, const int *);
 
 template <typename TA, typename T>
 int fl_copy_in(fastlsq_ctx *ctx, const TA *A, int64_t ldA, int64_t m, int64_t n, double mu,
@@ -858,23 +951,26 @@ template int fl_extract_rhs<float>(fastlsq_ctx *, const float *, int64_t, int64_
 template int fl_extract_rhs<double>(fastlsq_ctx *, const double *, int64_t, int64_t, int, double *);
 
 template <typename T>
-int fl_to_f64(fastlsq_ctx *ctx, const T *src, int64_t n, double *dst, int add)
+int fl_to_f64(fastlsq_ctx *ctx, const T *src, int64_t n, double *dst, int add, const int *skip)
 {
     FL_PROF(ctx, FASTLSQ_K_VECTOR);
-    k_to_f64<T><<<(unsigned)fl_cdiv(n, 256), 256, 0, ctx->stream>>>(src, n, dst, add);
+    k_to_f64<T><<<(unsigned)fl_cdiv(n, 256), 256, 0, ctx->stream>>>(src, n, dst, add, skip);
     FL_CHECK_LAUNCH(ctx, "to_f64");
     return 0;
 }
-template int fl_to_f64<float>(fastlsq_ctx *, const float *, int64_t, double *, int);
-template int fl_to_f64<double>(fastlsq_ctx *, const double *, int64_t, double *, int);
+template int fl_to_f64<float>(fastlsq_ctx *, const float *, int64_t, double *, int, const int *);
+template int fl_to_f64<double>(fastlsq_ctx *, const double *, int64_t, double *, int, const int *);
 
 template <typename T>
-int fl_from_f64(fastlsq_ctx *ctx, const double *src, int64_t n, int64_t n_total, T *dst)
+int fl_from_f64(fastlsq_ctx *ctx, const double *src, int64_t n, int64_t n_total, T *dst,
+                const int *skip)
 {
     FL_PROF(ctx, FASTLSQ_K_VECTOR);
-    k_from_f64<T><<<(unsigned)fl_cdiv(n_total, 256), 256, 0, ctx->stream>>>(src, n, n_total, dst);
+    k_from_f64<T><<<(unsigned)fl_cdiv(n_total, 256), 256, 0, ctx->stream>>>(src, n, n_total, dst, skip);
     FL_CHECK_LAUNCH(ctx, "from_f64");
     return 0;
 }
-template int fl_from_f64<float>(fastlsq_ctx *, const double *, int64_t, int64_t, float *);
-template int fl_from_f64<double>(fastlsq_ctx *, const double *, int64_t, int64_t, double *);
+template int fl_from_f64<float>(fastlsq_ctx *, const double *, int64_t, int64_t, float *,
+                                const int *);
+template int fl_from_f64<double>(fastlsq_ctx *, const double *, int64_t, int64_t, double *,
+                                 const int *);

@@ -13,7 +13,8 @@ template <typename T>
 int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
                const T *Tall, T *y, int transpose);
 template <typename T>
-int fl_trsv(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const T *y, T *x, int transpose);
+int fl_trsv(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const T *y, T *x, int transpose,
+            const int *skip = nullptr);
 template <typename TA, typename T>
 int fl_copy_in(fastlsq_ctx *ctx, const TA *A, int64_t ldA, int64_t m, int64_t n, double mu,
                int64_t m_aug, const double *rhs, int64_t ld_rhs, int nrhs, T *F, int64_t ld);
@@ -23,11 +24,19 @@ int fl_residual(fastlsq_ctx *ctx, const double *A, int64_t ldA, int64_t m, int64
 template <typename T>
 int fl_extract_rhs(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, int r, T *out);
 template <typename T>
-int fl_to_f64(fastlsq_ctx *ctx, const T *src, int64_t n, double *dst, int add);
+int fl_to_f64(fastlsq_ctx *ctx, const T *src, int64_t n, double *dst, int add,
+              const int *skip = nullptr);
 template <typename T>
-int fl_from_f64(fastlsq_ctx *ctx, const double *src, int64_t n, int64_t n_total, T *dst);
+int fl_from_f64(fastlsq_ctx *ctx, const double *src, int64_t n, int64_t n_total, T *dst,
+                const int *skip = nullptr);
 
 // tcgen05 (TF32x3 split precision) trailing update; tc_update.cu.  Returns a
 // negative status when the tensor-core path cannot handle the shape.
 int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
                        int nb, int64_t nct, const float *Tblk);
+
+// Krylov refinement with the factor's R as preconditioner (refine.cu)
+int fl_refine_cgls(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs64, double *beta64,
+                   int max_iter, double tol, double *norms_dev);
+int fl_normal_pcg(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *c64, double *v64,
+                  int max_iter, double tol);

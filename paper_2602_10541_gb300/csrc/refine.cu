@@ -1,0 +1,462 @@
+// Krylov refinement of least-squares solutions with a low-precision QR factor as
+// preconditioner (mixed-precision iterative refinement in the style of
+// LSQR/GMRES-IR, Carson & Higham): the operator products and the residual are
+// FP64 against the FP64 operator, the preconditioner applies the factor's R.
+//
+//  * fl_refine_cgls: CGLS on min ||A~ x - b~|| (A~ = [A; sqrt(mu) I], b~ = [b; 0])
+//    right-preconditioned by R (x = R^{-1} y), started from the direct solve.
+//    Converges to the FP64 least-squares solution also when the residual is large
+//    or kappa(A) eps32 > 1, where classical refinement stagnates.
+//  * fl_normal_pcg: preconditioned CG on (A~^T A~) v = c with M = R^T R; this is
+//    the adjoint solve v = (A^T A + mu I)^{-1} grad_beta of Sec. 2.5 / Sec. 4.4.
+//
+// Every kernel reads a device flag and returns at once after convergence, so a
+// fixed number of launches can be queued (and captured in a CUDA graph) without
+// host round trips.
+#include <cmath>
+
+#include "common.cuh"
+#include "qr.cuh"
+
+namespace {
+
+struct KryScalars {
+    double gamma, gamma0, qq, alpha, beta;
+    int done;
+    int iters;
+};
+
+constexpr int KV_ROWS = 256;
+constexpr int KV_COLS = 128;
+
+// partial sums of A~ v over column chunks (rows < m)
+__global__ void __launch_bounds__(KV_ROWS)
+k_kry_mv_partial(const double *__restrict__ A, int64_t ld, int64_t m, int64_t n,
+                 const double *__restrict__ v, double *__restrict__ part, const KryScalars *st)
+{
+    if (st && st->done) return;
+    __shared__ double sv[KV_COLS];
+    const int64_t j0 = (int64_t)blockIdx.y * KV_COLS;
+    const int nc = (int)fl_min64(KV_COLS, n - j0);
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) sv[t] = v[j0 + t];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * KV_ROWS + threadIdx.x;
+    if (i >= m) return;
+    double acc = 0.0;
+    const double *a = A + i + j0 * ld;
+#pragma unroll 8
+    for (int c = 0; c < nc; ++c) acc = fma(a[(int64_t)c * ld], sv[c], acc);
+    part[(int64_t)blockIdx.y * m + i] = acc;
+}
+
+// out = A~ v (rhs == nullptr) or out = rhs~ - A~ v
+__global__ void k_kry_mv_finish(const double *__restrict__ part, int nsplit, const double *__restrict__ v,
+                                const double *__restrict__ rhs, int64_t m, int64_t m_aug,
+                                double sqrt_mu, double *__restrict__ out, const KryScalars *st)
+{
+    if (st && st->done) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m_aug) return;
+    double s;
+    if (i < m) {
+        s = 0.0;
+        for (int sp = 0; sp < nsplit; ++sp) s += part[(int64_t)sp * m + i];
+    } else {
+        s = sqrt_mu * v[i - m];
+    }
+    out[i] = rhs ? ((i < m ? rhs[i] : 0.0) - s) : s;
+}
+
+// z_j = sum_i A_ij r_i + sqrt(mu) r_{m+j}: one warp per column (columns are contiguous)
+__global__ void __launch_bounds__(256)
+k_kry_mvt(const double *__restrict__ A, int64_t ld, int64_t m, int64_t n,
+          const double *__restrict__ r, double sqrt_mu, int64_t m_aug, double *__restrict__ z,
+          const KryScalars *st)
+{
+    if (st && st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const double *a = A + j * ld;
+    double acc0 = 0.0, acc1 = 0.0;
+    int64_t i = lane;
+    for (; i + 32 < m; i += 64) {
+        acc0 = fma(a[i], r[i], acc0);
+        acc1 = fma(a[i + 32], r[i + 32], acc1);
+    }
+    for (; i < m; i += 32) acc0 = fma(a[i], r[i], acc0);
+    double acc = acc0 + acc1;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) z[j] = acc + ((m_aug > m) ? sqrt_mu * r[m + j] : 0.0);
+}
+
+constexpr int DOT_THREADS = 256;
+constexpr int DOT_BLOCKS = 128;
+
+__global__ void __launch_bounds__(DOT_THREADS)
+k_kry_dot_partial(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
+                  double *__restrict__ part, const KryScalars *st)
+{
+    if (st && st->done) return;
+    __shared__ double red[DOT_THREADS];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * DOT_THREADS + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * DOT_THREADS)
+        acc = fma(a[i], b[i], acc);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = DOT_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+enum { OP_INIT = 0, OP_ALPHA = 1, OP_BETA = 2, OP_NORM = 3 };
+
+// sums the dot partials in a fixed order and advances the scalar recurrence
+__global__ void k_kry_scalar(const double *__restrict__ part, int nblk, KryScalars *st, int op,
+                             double tol, double *norm_out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (op != OP_INIT && st->done) return;
+    double d = 0.0;
+    for (int b = 0; b < nblk; ++b) d += part[b];
+    if (op == OP_INIT) {
+        st->gamma = d;
+        st->gamma0 = d;
+        st->iters = 0;
+        st->done = !(d > 0.0) || !isfinite(d);
+    } else if (op == OP_ALPHA) {
+        st->qq = d;
+        if (!(d > 0.0) || !isfinite(d)) {
+            st->alpha = 0.0;
+            st->done = 1;
+        } else {
+            st->alpha = st->gamma / d;
+        }
+    } else if (op == OP_BETA) {
+        st->beta = d / st->gamma;
+        st->gamma = d;
+        st->iters += 1;
+        if (!(d > tol * tol * st->gamma0) || !isfinite(d)) st->done = 1;
+    } else if (op == OP_NORM) {
+        if (norm_out) *norm_out = sqrt(d);
+    }
+}
+
+// y += sign * alpha * x
+__global__ void k_kry_axpy(double *__restrict__ y, const double *__restrict__ x, int64_t n,
+                           const KryScalars *st, double sign)
+{
+    if (st->done) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = fma(sign * st->alpha, x[i], y[i]);
+}
+
+// p = s + beta * p
+__global__ void k_kry_xpby(double *__restrict__ p, const double *__restrict__ s, int64_t n,
+                           const KryScalars *st)
+{
+    if (st->done) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = fma(st->beta, p[i], s[i]);
+}
+
+__global__ void k_kry_copy_sub(double *__restrict__ dst, const double *__restrict__ a,
+                               const double *__restrict__ b, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = b ? a[i] - b[i] : a[i];
+}
+
+// ---------------------------------------------------------------------------
+// Grid-wide FP64 triangular solve with the factor's R (entries of type T promoted
+// to double): R x = y (transpose 0) or R^T x = y.  Applying R^{-1} in FP64 keeps
+// the preconditioner a fixed linear operator even when kappa(R) eps32 >> 1.
+// One CTA per SM (cooperative launch, so all CTAs are resident), 64-row blocks:
+// CTA 0 substitutes within the block from shared memory, then every CTA removes
+// the block's contribution from its share of the remaining rows.  The grid
+// barrier spins a bounded number of times; on timeout it raises the device flag
+// and the kernel returns.
+// ---------------------------------------------------------------------------
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+};
+
+constexpr long long BAR_SPIN_LIMIT = 1ll << 24;
+
+__device__ bool grid_sync(GridBar *bar, unsigned nblocks, int *flag, volatile int *s_abort)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && !*s_abort) {
+        volatile unsigned *vgen = &bar->gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
+        if (arrived == nblocks) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > BAR_SPIN_LIMIT) {
+                    atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
+                    *s_abort = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *s_abort == 0;
+}
+
+constexpr int TG_BS = 64;
+constexpr int TG_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(TG_THREADS, 1)
+k_trsv_grid(const T *__restrict__ F, int64_t ld, int64_t n, const double *__restrict__ y,
+            double *__restrict__ x, double *__restrict__ work, int transpose, GridBar *bar,
+            int *flag, const KryScalars *st)
+{
+    if (st && st->done) return;              // same value in every CTA
+    __shared__ double D[TG_BS][TG_BS + 1];
+    __shared__ volatile int s_abort;
+    const unsigned G = gridDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_abort = 0;
+    for (int64_t i = (int64_t)blockIdx.x * TG_THREADS + threadIdx.x; i < n; i += (int64_t)G * TG_THREADS)
+        work[i] = y[i];
+    if (!grid_sync(bar, G, flag, &s_abort)) return;
+    const int64_t nblk = (n + TG_BS - 1) / TG_BS;
+    for (int64_t step = 0; step < nblk; ++step) {
+        const int64_t b = transpose ? step : nblk - 1 - step;
+        const int64_t r0 = b * TG_BS, r1 = fl_min64(n, r0 + TG_BS);
+        const int nb = (int)(r1 - r0);
+        if (blockIdx.x == 0) {
+            for (int idx = threadIdx.x; idx < TG_BS * TG_BS; idx += TG_THREADS) {
+                const int i = idx % TG_BS, j = idx / TG_BS;   // D(i, j) = R(r0 + i, r0 + j)
+                D[i][j] = (i < nb && j < nb) ? (double)F[(r0 + i) + (r0 + j) * ld] : 0.0;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                double s0 = (lane < nb) ? work[r0 + lane] : 0.0;
+                double s1 = (lane + 32 < nb) ? work[r0 + lane + 32] : 0.0;
+                for (int t = 0; t < nb; ++t) {
+                    const int c = transpose ? t : nb - 1 - t;
+                    const double sc = __shfl_sync(0xffffffffu, c < 32 ? s0 : s1, c & 31);
+                    const double xv = sc / D[c][c];
+                    if (!isfinite(xv)) atomicCAS(flag, 0, FL_DEVERR_NONFINITE);
+                    if (lane == c) s0 = xv;
+                    if (lane + 32 == c) s1 = xv;
+                    if (!transpose) {            // rows above c: s_i -= R(i, c) x_c
+                        if (lane < c) s0 -= D[lane][c] * xv;
+                        if (lane + 32 < c) s1 -= D[lane + 32][c] * xv;
+                    } else {                     // rows below c: s_i -= R(c, i) x_c
+                        if (lane > c && lane < nb) s0 -= D[c][lane] * xv;
+                        if (lane + 32 > c && lane + 32 < nb) s1 -= D[c][lane + 32] * xv;
+                    }
+                }
+                if (lane < nb) x[r0 + lane] = s0;
+                if (lane + 32 < nb) x[r0 + lane + 32] = s1;
+            }
+        }
+        if (!grid_sync(bar, G, flag, &s_abort)) return;
+        if (!transpose) {
+            // rows i < r0: work_i -= sum_c R(i, r0 + c) x_{r0 + c}   (thread per row, coalesced)
+            for (int64_t i = (int64_t)blockIdx.x * TG_THREADS + threadIdx.x; i < r0;
+                 i += (int64_t)G * TG_THREADS) {
+                double acc = 0.0;
+                for (int c = 0; c < nb; ++c) acc = fma((double)F[i + (r0 + c) * ld], x[r0 + c], acc);
+                work[i] -= acc;
+            }
+        } else {
+            // rows i >= r1: work_i -= sum_c R(r0 + c, i) x_{r0 + c}   (warp per row, coalesced)
+            for (int64_t i = r1 + (int64_t)blockIdx.x * (TG_THREADS / 32) + warp; i < n;
+                 i += (int64_t)G * (TG_THREADS / 32)) {
+                double acc = 0.0;
+                for (int c = lane; c < nb; c += 32) acc = fma((double)F[(r0 + c) + i * ld], x[r0 + c], acc);
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) work[i] -= acc;
+            }
+        }
+        if (!grid_sync(bar, G, flag, &s_abort)) return;
+    }
+}
+
+struct KryBufs {
+    double *r, *s, *p, *t, *q, *z, *part;
+    KryScalars *st;
+    void *tf;   // factor-type temporary [n]
+    double *work;
+    GridBar *bar;
+};
+
+int kry_bufs(fastlsq_ctx *ctx, const fastlsq_factor *f, KryBufs *B)
+{
+    const int64_t n = f->n, m_aug = f->m_aug;
+    const int nsplit = (int)fl_cdiv(n, KV_COLS);
+    size_t nd = (size_t)(2 * m_aug + 5 * n) + (size_t)nsplit * f->m + DOT_BLOCKS + 64;
+    double *base = (double *)fl_ws(ctx, FL_WS_KRYLOV, sizeof(double) * nd + sizeof(KryScalars) + 64);
+    void *tf = fl_ws(ctx, FL_WS_VEC1, 8 * (size_t)n + 64);
+    if (!base || !tf) return FASTLSQ_ERR_NOMEM;
+    B->r = base;
+    B->q = B->r + m_aug;
+    B->s = B->q + m_aug;
+    B->p = B->s + n;
+    B->t = B->p + n;
+    B->z = B->t + n;
+    B->part = B->z + n;
+    B->work = B->part + (size_t)nsplit * f->m + DOT_BLOCKS + 8;
+    B->st = (KryScalars *)(B->work + n + 8);
+    B->tf = tf;
+    B->bar = (GridBar *)ctx->d_grid_bar;
+    return 0;
+}
+
+int kry_mv(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *v, const double *rhs,
+           double *out, const KryBufs &B, const KryScalars *st)
+{
+    const int nsplit = (int)fl_cdiv(f->n, KV_COLS);
+    FL_PROF_N(ctx, FASTLSQ_K_KRYLOV, 2);
+    k_kry_mv_partial<<<dim3((unsigned)fl_cdiv(f->m, KV_ROWS), (unsigned)nsplit), KV_ROWS, 0, ctx->stream>>>(
+        f->A_refine, f->ld_refine, f->m, f->n, v, B.part, st);
+    k_kry_mv_finish<<<(unsigned)fl_cdiv(f->m_aug, 256), 256, 0, ctx->stream>>>(
+        B.part, nsplit, v, rhs, f->m, f->m_aug, f->mu > 0 ? sqrt(f->mu) : 0.0, out, st);
+    FL_CHECK_LAUNCH(ctx, "krylov mv");
+    return 0;
+}
+
+int kry_mvt(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *r, double *z, const KryScalars *st)
+{
+    FL_PROF(ctx, FASTLSQ_K_KRYLOV);
+    k_kry_mvt<<<(unsigned)fl_cdiv(f->n, 8), 256, 0, ctx->stream>>>(
+        f->A_refine, f->ld_refine, f->m, f->n, r, f->mu > 0 ? sqrt(f->mu) : 0.0, f->m_aug, z, st);
+    FL_CHECK_LAUNCH(ctx, "krylov mvt");
+    return 0;
+}
+
+int kry_dot(fastlsq_ctx *ctx, const double *a, const double *b, int64_t n, const KryBufs &B, int op,
+            double tol, double *norm_out, const KryScalars *skip)
+{
+    FL_PROF_N(ctx, FASTLSQ_K_KRYLOV, 2);
+    k_kry_dot_partial<<<DOT_BLOCKS, DOT_THREADS, 0, ctx->stream>>>(a, b, n, B.part, skip);
+    k_kry_scalar<<<1, 32, 0, ctx->stream>>>(B.part, DOT_BLOCKS, B.st, op, tol, norm_out);
+    FL_CHECK_LAUNCH(ctx, "krylov dot");
+    return 0;
+}
+
+// out = R^{-1} in (transpose = 0) or R^{-T} in, in FP64 with the factor's R
+template <typename T>
+int kry_prec(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *in, double *out, int transpose,
+             const KryBufs &B)
+{
+    FL_PROF(ctx, FASTLSQ_K_TRSV);
+    const T *F = (const T *)f->F;
+    int64_t ld = f->ld, n = f->n;
+    int *flag = ctx->d_flag;
+    const KryScalars *st = B.st;
+    GridBar *bar = B.bar;
+    double *work = B.work;
+    void *args[] = {(void *)&F, (void *)&ld, (void *)&n, (void *)&in, (void *)&out, (void *)&work,
+                    (void *)&transpose, (void *)&bar, (void *)&flag, (void *)&st};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_trsv_grid<T>, dim3(ctx->num_sms),
+                                                dim3(TG_THREADS), args, 0, ctx->stream);
+    if (e != cudaSuccess) return fl_cuda(ctx, e, "grid triangular solve");
+    return 0;
+}
+
+template <typename T>
+int refine_cgls_t(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs64, double *x,
+                  int max_iter, double tol, double *norms)
+{
+    KryBufs B;
+    FL_TRY(kry_bufs(ctx, f, &B));
+    const int64_t n = f->n, m_aug = f->m_aug;
+    const unsigned gn = (unsigned)fl_cdiv(n, 256), gm = (unsigned)fl_cdiv(m_aug, 256);
+    cudaMemsetAsync(B.st, 0, sizeof(KryScalars), ctx->stream);
+    // r = b~ - A~ x ; s = R^{-T} A~^T r ; p = s ; gamma = s.s
+    FL_TRY(kry_mv(ctx, f, x, rhs64, B.r, B, nullptr));
+    if (norms) FL_TRY(kry_dot(ctx, B.r, B.r, m_aug, B, OP_NORM, 0.0, norms, nullptr));
+    FL_TRY(kry_mvt(ctx, f, B.r, B.z, nullptr));
+    FL_TRY(kry_prec<T>(ctx, f, B.z, B.s, 1, B));
+    k_kry_copy_sub<<<gn, 256, 0, ctx->stream>>>(B.p, B.s, nullptr, n);
+    ctx->prof.launches[FASTLSQ_K_KRYLOV] += 1;
+    FL_TRY(kry_dot(ctx, B.s, B.s, n, B, OP_INIT, tol, nullptr, nullptr));
+    for (int it = 0; it < max_iter; ++it) {
+        FL_TRY(kry_prec<T>(ctx, f, B.p, B.t, 0, B));                 // t = R^{-1} p
+        FL_TRY(kry_mv(ctx, f, B.t, nullptr, B.q, B, B.st));           // q = A~ t
+        FL_TRY(kry_dot(ctx, B.q, B.q, m_aug, B, OP_ALPHA, tol, nullptr, B.st));
+        k_kry_axpy<<<gn, 256, 0, ctx->stream>>>(x, B.t, n, B.st, 1.0);
+        k_kry_axpy<<<gm, 256, 0, ctx->stream>>>(B.r, B.q, m_aug, B.st, -1.0);
+        FL_TRY(kry_mvt(ctx, f, B.r, B.z, B.st));                      // z = A~^T r
+        FL_TRY(kry_prec<T>(ctx, f, B.z, B.s, 1, B));                  // s = R^{-T} z
+        FL_TRY(kry_dot(ctx, B.s, B.s, n, B, OP_BETA, tol, nullptr, B.st));
+        k_kry_xpby<<<gn, 256, 0, ctx->stream>>>(B.p, B.s, n, B.st);
+        ctx->prof.launches[FASTLSQ_K_KRYLOV] += 3;
+        if (norms && it + 1 < 64) FL_TRY(kry_dot(ctx, B.r, B.r, m_aug, B, OP_NORM, 0.0, norms + it + 1, B.st));
+        FL_CHECK_LAUNCH(ctx, "cgls");
+    }
+    return 0;
+}
+
+template <typename T>
+int normal_pcg_t(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *c, double *v, int max_iter,
+                 double tol)
+{
+    KryBufs B;
+    FL_TRY(kry_bufs(ctx, f, &B));
+    const int64_t n = f->n;
+    const unsigned gn = (unsigned)fl_cdiv(n, 256);
+    cudaMemsetAsync(B.st, 0, sizeof(KryScalars), ctx->stream);
+    // v0 = M^{-1} c ; z = c - A~^T A~ v0 ; y(=s) = M^{-1} z ; p = y ; rho = z.y
+    FL_TRY(kry_prec<T>(ctx, f, c, B.t, 1, B));
+    FL_TRY(kry_prec<T>(ctx, f, B.t, v, 0, B));
+    FL_TRY(kry_mv(ctx, f, v, nullptr, B.q, B, nullptr));
+    FL_TRY(kry_mvt(ctx, f, B.q, B.r, nullptr));                       // r (n-space) = A~^T A~ v0
+    k_kry_copy_sub<<<gn, 256, 0, ctx->stream>>>(B.z, c, B.r, n);      // z = c - A~^T A~ v0
+    FL_TRY(kry_prec<T>(ctx, f, B.z, B.t, 1, B));
+    FL_TRY(kry_prec<T>(ctx, f, B.t, B.s, 0, B));
+    k_kry_copy_sub<<<gn, 256, 0, ctx->stream>>>(B.p, B.s, nullptr, n);
+    ctx->prof.launches[FASTLSQ_K_KRYLOV] += 2;
+    FL_TRY(kry_dot(ctx, B.z, B.s, n, B, OP_INIT, tol, nullptr, nullptr));
+    for (int it = 0; it < max_iter; ++it) {
+        FL_TRY(kry_mv(ctx, f, B.p, nullptr, B.q, B, B.st));
+        FL_TRY(kry_mvt(ctx, f, B.q, B.r, B.st));                      // w = A~^T A~ p (in r)
+        FL_TRY(kry_dot(ctx, B.p, B.r, n, B, OP_ALPHA, tol, nullptr, B.st));
+        k_kry_axpy<<<gn, 256, 0, ctx->stream>>>(v, B.p, n, B.st, 1.0);
+        k_kry_axpy<<<gn, 256, 0, ctx->stream>>>(B.z, B.r, n, B.st, -1.0);
+        FL_TRY(kry_prec<T>(ctx, f, B.z, B.t, 1, B));
+        FL_TRY(kry_prec<T>(ctx, f, B.t, B.s, 0, B));
+        FL_TRY(kry_dot(ctx, B.z, B.s, n, B, OP_BETA, tol, nullptr, B.st));
+        k_kry_xpby<<<gn, 256, 0, ctx->stream>>>(B.p, B.s, n, B.st);
+        ctx->prof.launches[FASTLSQ_K_KRYLOV] += 3;
+        FL_CHECK_LAUNCH(ctx, "normal pcg");
+    }
+    return 0;
+}
+
+}  // namespace
+
+int fl_refine_cgls(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs64, double *beta64,
+                   int max_iter, double tol, double *norms_dev)
+{
+    if (!f->A_refine) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "CGLS refinement needs the FP64 operator");
+    if (f->prec == FASTLSQ_PREC_FP64)
+        return refine_cgls_t<double>(ctx, f, rhs64, beta64, max_iter, tol, norms_dev);
+    return refine_cgls_t<float>(ctx, f, rhs64, beta64, max_iter, tol, norms_dev);
+}
+
+int fl_normal_pcg(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *c64, double *v64,
+                  int max_iter, double tol)
+{
+    if (!f->A_refine) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "PCG adjoint needs the FP64 operator");
+    if (f->prec == FASTLSQ_PREC_FP64) return normal_pcg_t<double>(ctx, f, c64, v64, max_iter, tol);
+    return normal_pcg_t<float>(ctx, f, c64, v64, max_iter, tol);
+}

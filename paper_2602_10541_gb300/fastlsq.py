@@ -20,6 +20,7 @@ _lib = None
 
 F32, F64 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+REFINE_CLASSICAL, REFINE_CGLS = 0, 1
 RHS_SOURCE, RHS_EXACT = 0, 1
 POISSON_1D, HELMHOLTZ_2D, POISSON_5D, BRATU_2D, GAUSS_SOURCE_2D = 1, 2, 3, 4, 5
 NL_NONE, NL_EXP, NL_CUBIC = 0, 1, 2
@@ -38,7 +39,7 @@ class fastlsq_op(ctypes.Structure):
 
 class fastlsq_solve_stats(ctypes.Structure):
     _fields_ = [("refine_steps", _i32), ("nb", _i32), ("tensor_core", _i32), ("status", _i32),
-                ("resid_norm", _dbl * 8)]
+                ("resid_norm", _dbl * 65)]
 
 
 class fastlsq_newton_problem(ctypes.Structure):
@@ -49,7 +50,7 @@ class fastlsq_newton_problem(ctypes.Structure):
 
 class fastlsq_newton_opts(ctypes.Structure):
     _fields_ = [("max_iter", _i32), ("tol", _dbl), ("mu", _dbl), ("armijo_c", _dbl),
-                ("max_halvings", _i32), ("prec", _i32), ("max_refine", _i32)]
+                ("max_halvings", _i32), ("prec", _i32), ("max_refine", _i32), ("refine_tol", _dbl)]
 
 
 class fastlsq_newton_stats(ctypes.Structure):
@@ -70,12 +71,12 @@ _SIGNATURES = {
     "fastlsq_eval": [_vp, _vp, _i64, _i32, _vp, _vp, _i64, _dbl, _vp, _vp],
     "fastlsq_eval_adjoint": [_vp, _vp, _i64, _i32, _vp, _vp, _i64, _dbl, _vp, _vp],
     "fastlsq_lstsq": [_vp, ctypes.c_int, _vp, ctypes.c_int, _i64, _i64, _i64, _dbl, _vp, _i32, _i64,
-                      _vp, _i64, _vp, _i64, _i32, ctypes.POINTER(_vp),
+                      _vp, _i64, _vp, _i64, _i32, _i32, _dbl, ctypes.POINTER(_vp),
                       ctypes.POINTER(fastlsq_solve_stats)],
-    "fastlsq_factor_solve": [_vp, _vp, _vp, _i32, _i64, _vp, _i64, _i32,
+    "fastlsq_factor_solve": [_vp, _vp, _vp, _i32, _i64, _vp, _i64, _i32, _i32, _dbl,
                              ctypes.POINTER(fastlsq_solve_stats)],
     "fastlsq_factor_destroy": [_vp],
-    "fastlsq_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _i64],
+    "fastlsq_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _i32, _dbl],
     "fastlsq_source_grad": [_vp, _vp, _i64, ctypes.POINTER(_dbl), _i32, _vp, ctypes.POINTER(_dbl)],
     "fastlsq_coef_grad": [_vp, _vp, _i64, ctypes.POINTER(fastlsq_op), _vp, _vp, _i64, _dbl, _vp,
                           _vp, _vp, _vp, ctypes.POINTER(_dbl)],
@@ -87,7 +88,8 @@ _SIGNATURES = {
 }
 
 KERNELS = ["prefactor", "assemble_f32", "assemble_f64", "rhs", "eval", "copy_in", "panel",
-           "trail_simt", "trail_tc", "apply_q", "trsv", "residual", "vector", "newton", "adjoint"]
+           "trail_simt", "trail_tc", "apply_q", "trsv", "residual", "vector", "newton", "adjoint",
+           "krylov"]
 
 
 def library_path() -> str:
@@ -194,6 +196,8 @@ class Op:
 
 def fastlsq_assemble(ctx, dtype, x, op, row_weight, W, b, scale, A, row_offset=0, n_rows=None):
     n_rows = x.shape[0] if n_rows is None else n_rows
+    if n_rows > x.shape[0] or x.shape[1] != op.d or W.shape[1] != op.d or b.numel() < W.shape[0]:
+        raise ValueError("fastlsq_assemble: array shapes do not match the sizes")
     return ctx.check(ctx.lib.fastlsq_assemble(
         ctx.handle, dtype, _ptr(x), n_rows, ctypes.byref(op.struct), float(row_weight), _ptr(W),
         _ptr(b), W.shape[0], float(scale), _ptr(A), A.shape[1], row_offset))
@@ -218,7 +222,7 @@ def fastlsq_eval_adjoint(ctx, x, W, b, scale, g, grad_beta):
 
 
 def fastlsq_lstsq(ctx, prec, A, n_rows, mu, rhs, beta, A_refine=None, max_refine=0, keep=False,
-                  stats=False):
+                  stats=False, refine_mode=REFINE_CLASSICAL, refine_tol=1e-10):
     """A: (n_feat, ldA) float32/float64 column-major; rhs: (nrhs, ld_rhs) float64;
     beta: (nrhs, n_feat) float64.  Returns (status, factor handle or None, stats or None)."""
     import torch
@@ -230,17 +234,19 @@ def fastlsq_lstsq(ctx, prec, A, n_rows, mu, rhs, beta, A_refine=None, max_refine
     rc = ctx.lib.fastlsq_lstsq(
         ctx.handle, prec, _ptr(A), a_dtype, A.shape[1], n_rows, n_feat, float(mu), _ptr(rhs),
         nrhs, rhs.shape[1] if nrhs else 0, _ptr(beta), beta.shape[1] if nrhs else 0, _ptr(A_refine),
-        A_refine.shape[1] if A_refine is not None else 0, int(max_refine),
-        ctypes.byref(handle) if keep else None, ctypes.byref(st) if stats else None)
+        A_refine.shape[1] if A_refine is not None else 0, int(max_refine), int(refine_mode),
+        float(refine_tol), ctypes.byref(handle) if keep else None,
+        ctypes.byref(st) if stats else None)
     ctx.check(rc)
     return rc, (handle if keep else None), st
 
 
-def fastlsq_factor_solve(ctx, factor, rhs, beta, max_refine=0, stats=False):
+def fastlsq_factor_solve(ctx, factor, rhs, beta, max_refine=0, stats=False,
+                         refine_mode=REFINE_CLASSICAL, refine_tol=1e-10):
     st = fastlsq_solve_stats() if stats else None
     rc = ctx.lib.fastlsq_factor_solve(ctx.handle, factor, _ptr(rhs), rhs.shape[0], rhs.shape[1],
-                                      _ptr(beta), beta.shape[1], int(max_refine),
-                                      ctypes.byref(st) if stats else None)
+                                      _ptr(beta), beta.shape[1], int(max_refine), int(refine_mode),
+                                      float(refine_tol), ctypes.byref(st) if stats else None)
     ctx.check(rc)
     return rc, st
 
@@ -249,10 +255,11 @@ def fastlsq_factor_destroy(ctx, factor):
     return ctx.lib.fastlsq_factor_destroy(factor)
 
 
-def fastlsq_backward(ctx, factor, grad_beta, v, grad_rhs=None, A_op=None):
+def fastlsq_backward(ctx, factor, grad_beta, v, grad_rhs=None, A_op=None, max_iter=0, tol=1e-12):
     return ctx.check(ctx.lib.fastlsq_backward(ctx.handle, factor, _ptr(grad_beta), _ptr(v),
                                               _ptr(grad_rhs), _ptr(A_op),
-                                              A_op.shape[1] if A_op is not None else 0))
+                                              A_op.shape[1] if A_op is not None else 0,
+                                              int(max_iter), float(tol)))
 
 
 def fastlsq_source_grad(ctx, x, theta, w):
@@ -275,12 +282,12 @@ def fastlsq_coef_grad(ctx, x, op, W, b, scale, r, Av, v, beta):
 
 def fastlsq_newton(ctx, x_int, x_bc, op, nl_kind, nl_lam, bc_weight, f, g, W, b, scale, beta,
                    max_iter=15, tol=1e-10, mu=1e-10, armijo_c=1e-4, max_halvings=20,
-                   prec=PREC_MIXED, max_refine=2):
+                   prec=PREC_MIXED, max_refine=30, refine_tol=1e-10):
     prob = fastlsq_newton_problem(x_int.shape[1], x_int.shape[0], x_bc.shape[0], x_int.data_ptr(),
                                   x_bc.data_ptr(), op.struct, nl_kind, float(nl_lam),
                                   float(bc_weight), f.data_ptr(), g.data_ptr())
     opts = fastlsq_newton_opts(max_iter, float(tol), float(mu), float(armijo_c), max_halvings,
-                               prec, max_refine)
+                               prec, max_refine, float(refine_tol))
     st = fastlsq_newton_stats()
     rc = ctx.lib.fastlsq_newton(ctx.handle, ctypes.byref(prob), _ptr(W), _ptr(b), W.shape[0],
                                 float(scale), ctypes.byref(opts), _ptr(beta), ctypes.byref(st))

@@ -39,8 +39,9 @@ class LinearSolver:
     allocated once so that repeated solves (and CUDA-graph capture) reuse them."""
 
     def __init__(self, ctx: fl.Context, dp: DeviceProblem, prec=fl.PREC_MIXED, max_refine=2,
-                 mu=None):
+                 mu=None, refine_mode=fl.REFINE_CLASSICAL, refine_tol=1e-10):
         self.ctx, self.dp, self.prec, self.max_refine = ctx, dp, prec, max_refine
+        self.refine_mode, self.refine_tol = refine_mode, refine_tol
         w = dp.w
         self.m, self.n = w.n_rows, w.n_feat
         self.mu = w.mu if mu is None else mu
@@ -73,7 +74,8 @@ class LinearSolver:
         rc, fac, st = fl.fastlsq_lstsq(self.ctx, self.prec, A, self.m, self.mu, self.rhs, self.beta,
                                        A_refine=self.A64,
                                        max_refine=self.max_refine if self.prec == fl.PREC_MIXED else 0,
-                                       keep=keep, stats=stats)
+                                       keep=keep, stats=stats, refine_mode=self.refine_mode,
+                                       refine_tol=self.refine_tol)
         self.stats = st
         return fac
 

@@ -127,6 +127,20 @@ def test_mixed_refinement_on_large_residual_problem_never_hurts(ctx):
     assert errs[1] <= errs[0] * 1.5 and errs[1] < 1e-5, errs
 
 
+@pytest.mark.parametrize("mu", [0.0, 1e-2])
+def test_mixed_cgls_refinement_reaches_fp64_on_large_residual(ctx, mu):
+    rng = np.random.default_rng(23)
+    m, n = 517, 77
+    A = rng.standard_normal((m, n))
+    B = rng.standard_normal((m, 1))
+    ref = oracle.lstsq(A, B, mu=mu).reshape(-1)
+    beta = torch.zeros((1, n), dtype=torch.float64, device=DEV)
+    _, _, st = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, mu, _rhs(B), beta,
+                                A_refine=_cm(A, torch.float64), max_refine=30,
+                                refine_mode=fl.REFINE_CGLS, refine_tol=1e-14, stats=True)
+    np.testing.assert_allclose(beta.cpu().numpy()[0], ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+
+
 def _oracle_solution(w):
     A_int = oracle.assemble(w.x_int, w.alpha, w.coef, w.W, w.b, w.scale)
     A_bc = oracle.assemble(w.x_bc, np.zeros((1, w.d), np.int32), [1.0], w.W, w.b, w.scale,

@@ -31,7 +31,7 @@ def _gpu_newton(ctx, w, prec, max_iter, tol=1e-10):
     rc, st = fl.fastlsq_newton(ctx, _t(w.x_int), _t(w.x_bc), fl.Op(w.alpha, w.coef), fl.NL_EXP,
                                w.nl_lam, w.lam_bc, _t(np.zeros(w.n_int)), _t(np.zeros(w.n_bc)),
                                _t(w.W), _t(w.b), w.scale, beta, max_iter=max_iter, tol=tol,
-                               mu=w.mu, prec=prec, max_refine=2)
+                               mu=w.mu, prec=prec, max_refine=30)
     return beta, rc, st
 
 
