@@ -215,6 +215,17 @@ FASTLSQ_API int fastlsq_factor_solve(fastlsq_ctx *ctx, const fastlsq_factor *f,
                          int32_t refine_mode, double refine_tol,
                          fastlsq_solve_stats *stats);
 
+/* Copy the triangular factor R (n_feat x n_feat, upper; zeros below) of a
+ * checkpointed factorisation into R_out (double, column-major, ld_r >= n_feat). */
+FASTLSQ_API int fastlsq_factor_get_r(fastlsq_ctx *ctx, const fastlsq_factor *f, double *R_out,
+                                     int64_t ld_r);
+
+/* x = R^{-1} y (transpose 0) or R^{-T} y (transpose 1) in FP64 arithmetic with the
+ * factor's R, by the grid-wide substitution kernel used as the Krylov
+ * preconditioner.  y, x: [n_feat] double (may alias). */
+FASTLSQ_API int fastlsq_factor_trsv(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *y,
+                                    double *x, int32_t transpose);
+
 /* Release a factor handle (stream-ordered). */
 FASTLSQ_API int fastlsq_factor_destroy(fastlsq_factor *f);
 

@@ -360,27 +360,30 @@ static int solve_one(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, i
     const int64_t n = f->n, m = f->m, m_aug = f->m_aug;
     const T *F = (const T *)f->F;
     T *y = (T *)fl_ws(ctx, FL_WS_VEC0, sizeof(T) * m_aug);
-    T *dx = (T *)fl_ws(ctx, FL_WS_VEC1, sizeof(T) * n);
-    if (!y || !dx) return FASTLSQ_ERR_NOMEM;
+    double *v64 = (double *)fl_ws(ctx, FL_WS_SOLVE64, sizeof(double) * 3 * n + 64);
+    if (!y || !v64) return FASTLSQ_ERR_NOMEM;
+    double *y64 = v64, *dx64 = v64 + n, *work = v64 + 2 * n;
     if (r < nrhs_in_F) {
         FL_TRY(fl_extract_rhs<T>(ctx, F, f->ld, n, r, y));
     } else {
         FL_TRY(fl_from_f64<T>(ctx, rhs64, m, m_aug, y));
         FL_TRY(fl_apply_q<T>(ctx, F, f->ld, m_aug, n, f->nb, (const T *)f->T, y, 1));
     }
-    FL_TRY(fl_trsv<T>(ctx, F, f->ld, n, y, dx, 0));
-    FL_TRY(fl_to_f64<T>(ctx, dx, n, beta64, 0));
+    FL_TRY(fl_to_f64<T>(ctx, y, n, y64, 0));
+    FL_TRY(fl_trsv_grid<T>(ctx, F, f->ld, n, y64, beta64, work, 0));
     if (mode == FASTLSQ_REFINE_CGLS) {
         if (max_refine > 0) return fl_refine_cgls(ctx, f, rhs64, beta64, max_refine, tol, norms_dev);
         return 0;
     }
-    // classical iterative refinement: FP64 residual, correction with the factors
+    // classical iterative refinement: FP64 residual, correction R^{-1} Q^T r with the
+    // factors (Q^T in the factor's type, R^{-1} in FP64)
     for (int it = 0; it < max_refine; ++it) {
         FL_TRY(fl_residual<T>(ctx, f->A_refine, f->ld_refine, m, n, f->mu, m_aug, rhs64, beta64, y,
                               norms_dev ? norms_dev + it : nullptr));
         FL_TRY(fl_apply_q<T>(ctx, F, f->ld, m_aug, n, f->nb, (const T *)f->T, y, 1));
-        FL_TRY(fl_trsv<T>(ctx, F, f->ld, n, y, dx, 0));
-        FL_TRY(fl_to_f64<T>(ctx, dx, n, beta64, 1));
+        FL_TRY(fl_to_f64<T>(ctx, y, n, y64, 0));
+        FL_TRY(fl_trsv_grid<T>(ctx, F, f->ld, n, y64, dx64, work, 0));
+        FL_TRY(fl_to_f64<double>(ctx, dx64, n, beta64, 1));
     }
     if (norms_dev && f->A_refine) {
         FL_TRY(fl_residual<T>(ctx, f->A_refine, f->ld_refine, m, n, f->mu, m_aug, rhs64, beta64, y,
@@ -534,6 +537,22 @@ extern "C" int fastlsq_factor_solve(fastlsq_ctx *ctx, const fastlsq_factor *f, c
                      refine_mode, refine_tol, stats);
 }
 
+int fl_factor_get_r(fastlsq_ctx *ctx, const fastlsq_factor *f, double *R, int64_t ldr);
+int fl_factor_trsv64(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *y, double *x, int transpose);
+
+extern "C" int fastlsq_factor_get_r(fastlsq_ctx *ctx, const fastlsq_factor *f, double *R_out, int64_t ld_r)
+{
+    if (!ctx || !f || !R_out || ld_r < f->n) return FASTLSQ_ERR_INVALID;
+    return fl_factor_get_r(ctx, f, R_out, ld_r);
+}
+
+extern "C" int fastlsq_factor_trsv(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *y, double *x,
+                                   int32_t transpose)
+{
+    if (!ctx || !f || !y || !x) return FASTLSQ_ERR_INVALID;
+    return fl_factor_trsv64(ctx, f, y, x, transpose ? 1 : 0);
+}
+
 extern "C" int fastlsq_factor_destroy(fastlsq_factor *f)
 {
     factor_free(f);
@@ -550,12 +569,10 @@ template <typename T>
 static int backward_t(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *grad_beta, double *v)
 {
     const int64_t n = f->n;
-    T *y = (T *)fl_ws(ctx, FL_WS_VEC0, sizeof(T) * f->m_aug);
-    if (!y) return FASTLSQ_ERR_NOMEM;
-    FL_TRY(fl_from_f64<T>(ctx, grad_beta, n, n, y));
-    FL_TRY(fl_trsv<T>(ctx, (const T *)f->F, f->ld, n, y, y, 1));   // R^{-T} grad_beta
-    FL_TRY(fl_trsv<T>(ctx, (const T *)f->F, f->ld, n, y, y, 0));   // R^{-1} (...)
-    return fl_to_f64<T>(ctx, y, n, v, 0);
+    double *v64 = (double *)fl_ws(ctx, FL_WS_SOLVE64, sizeof(double) * 3 * n + 64);
+    if (!v64) return FASTLSQ_ERR_NOMEM;
+    FL_TRY(fl_trsv_grid<T>(ctx, (const T *)f->F, f->ld, n, grad_beta, v64, v64 + 2 * n, 1));  // R^{-T} g
+    return fl_trsv_grid<T>(ctx, (const T *)f->F, f->ld, n, v64, v, v64 + 2 * n, 0);           // R^{-1} (.)
 }
 
 extern "C" int fastlsq_backward(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *grad_beta,

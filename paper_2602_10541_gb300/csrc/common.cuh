@@ -42,6 +42,8 @@ enum fl_slot {
     FL_WS_GRAM,            // panel Gram partials
     FL_WS_NORMS,           // residual norms for solve stats
     FL_WS_KRYLOV,          // Krylov refinement vectors and scalars
+    FL_WS_APPLYQ,          // Q application partial sums
+    FL_WS_SOLVE64,         // FP64 vectors of the triangular solves
     FL_WS_COUNT
 };
 

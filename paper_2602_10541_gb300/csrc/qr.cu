@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "gridsync.cuh"
 #include "qr.cuh"
 
 namespace cg = cooperative_groups;
@@ -46,7 +47,7 @@ struct PanelSmem {
     static constexpr int LD = NB + 1;   // padded row stride of the panel slice
     static size_t bytes(int rpc)
     {
-        return sizeof(T) * ((size_t)rpc * LD + PANEL_WARPS * 32 + 2 * (CL_MAX + 1) * NB +
+        return sizeof(T) * ((size_t)rpc * LD + PANEL_WARPS * 33 + 2 * (CL_MAX + 1) * NB +
                             2 * NB * (NB + 1) + NB);
     }
 };
@@ -73,8 +74,8 @@ k_panel(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int rpc,
     constexpr int U = 4;                         // rows per thread per iteration
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *P = reinterpret_cast<T *>(smem_raw);
-    T *red = P + (size_t)rpc * LDP;                 // [PANEL_WARPS][32]
-    T *xbuf = red + PANEL_WARPS * 32;               // [2][CL_MAX + 1][NB]
+    T *red = P + (size_t)rpc * LDP;                 // [PANEL_WARPS][33]
+    T *xbuf = red + PANEL_WARPS * 33;               // [2][CL_MAX + 1][NB]
     T *Tm = xbuf + 2 * (CL_MAX + 1) * NB;           // [NB][NB + 1] T(row, col)
     T *G = Tm + NB * (NB + 1);                      // [NB][NB + 1] G(q, c) = v_q^T v_c
     T *tauv = G + NB * (NB + 1);                    // [NB]
@@ -106,34 +107,44 @@ k_panel(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int rpc,
 
     for (int j = 0; j <= ncols; ++j) {
         const int par = j & 1;
-        red[warp * 32 + lane] = acc;
+        // block reduction, transposed: warp c sums column c over the 32 warps (and
+        // row sub-slots), then its lane 0 sends the CTA's partial to every rank
+        red[warp * 33 + lane] = acc;
         __syncthreads();
-        if (warp == 0) {
+        if (warp < NB) {
             T part = T(0);
-            if (lane < NB)
-                for (int w = 0; w < PANEL_WARPS; ++w)
 #pragma unroll
-                    for (int s = 0; s < RPW; ++s) part += red[w * 32 + s * NB + lane];
-            T top = (rank == 0 && j < ncols && lane < NB) ? P[j * LDP + lane] : T(0);
-            if (lane < NB) {
-                for (int dst = 0; dst < CL; ++dst) {
-                    T *rb = cluster.map_shared_rank(xbuf, dst);
-                    rb[(par * (CL_MAX + 1) + rank) * NB + lane] = part;
-                    if (rank == 0) rb[(par * (CL_MAX + 1) + CL_MAX) * NB + lane] = top;
-                }
+            for (int s = 0; s < RPW; ++s) part += red[lane * 33 + s * NB + warp];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+            if (lane < CL) {
+                T *rb = cluster.map_shared_rank(xbuf, lane);
+                rb[(par * (CL_MAX + 1) + rank) * NB + warp] = part;
+                if (rank == 0) rb[(par * (CL_MAX + 1) + CL_MAX) * NB + warp] =
+                    (j < ncols) ? P[j * LDP + warp] : T(0);
             }
         }
         cluster.sync();
         const T *xb = xbuf + par * (CL_MAX + 1) * NB;
-        T dl = T(0);
-        for (int s = 0; s < CL; ++s) dl += xb[s * NB + l];   // fixed order: same sum everywhere
+        // cross-CTA sums: four interleaved chains, the same order on every rank
+        T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        const int jc = (j < ncols) ? j : 0;
+        for (int q = 0; q < CL; q += 4) {
+            d0 += xb[q * NB + l];
+            s0 += xb[q * NB + jc];
+            if (q + 1 < CL) { d1 += xb[(q + 1) * NB + l]; s1 += xb[(q + 1) * NB + jc]; }
+            if (q + 2 < CL) { d2 += xb[(q + 2) * NB + l]; s2 += xb[(q + 2) * NB + jc]; }
+            if (q + 3 < CL) { d3 += xb[(q + 3) * NB + l]; s3 += xb[(q + 3) * NB + jc]; }
+        }
+        const T dl = (d0 + d1) + (d2 + d3);
+        const T ssum = (s0 + s1) + (s2 + s3);
         // Gram column j-1 (lanes l < j-1), kept for the T recurrence at the end
         if (j >= 1 && warp == 0 && lane < NB && rank == 0 && l < j - 1) G[l * (NB + 1) + (j - 1)] = dl;
         if (j == ncols) break;
 
         // reflector for column j (every thread computes the same scalars)
-        T ss = T(0);
-        for (int s = 0; s < CL; ++s) ss += xb[s * NB + j];
+        const T ss = ssum;
         const T ajj = xb[CL_MAX * NB + j];
         const T topl = xb[CL_MAX * NB + l];
         T beta = ajj, tauj = T(0), inv = T(0);
@@ -237,58 +248,84 @@ __device__ __forceinline__ T v_at(const T *__restrict__ F, int64_t ld, int64_t k
 }
 
 // Y partials: Ypart[s][l][c] = sum over rows of split s of V(i,l) C(i,c) for the
-// trailing columns c (global column k + ncols + c).
-constexpr int TY_COLS = 64;
+// trailing columns c (global column k + ncols + c).  CTA tile: all NB rows of Y
+// x TY_COLS columns; rows streamed in chunks of TY_ROWS through shared memory
+// stored row-major ([row][l], [row][c]) so each thread reads its 4 l-values and 4
+// c-values as vectors: 16 FMAs per two shared-memory loads.
+constexpr int TY_COLS = 128;
 constexpr int TY_ROWS = 32;
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
 k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct,
           int64_t rows_per_split, T *__restrict__ Ypart)
 {
-    __shared__ T sV[TY_ROWS][NB + 1];
-    __shared__ T sC[TY_COLS][TY_ROWS + 1];
+    using V4 = typename Vec4<T>::type;
+    constexpr int LG = NB / 4;                 // l-groups of 4
+    constexpr int CG = 256 / LG;               // c-groups
+    constexpr int CPT = TY_COLS / CG;          // columns per thread (4 for NB = 32)
+    static_assert(CPT == 4 || CPT == 2 || CPT == 1, "tile");
+    __shared__ __align__(16) T sV[TY_ROWS][NB];
+    __shared__ __align__(16) T sC[TY_ROWS][TY_COLS + 4];
     const int64_t mp = m - k;
     const int64_t cbase = (int64_t)blockIdx.x * TY_COLS;
     const int64_t rs0 = (int64_t)blockIdx.y * rows_per_split;
     const int64_t rs1 = fl_min64(mp, rs0 + rows_per_split);
-    constexpr int GROUPS = 256 / NB;
-    constexpr int CPT = TY_COLS / GROUPS;   // columns per thread
-    const int l = threadIdx.x % NB;
-    const int g = threadIdx.x / NB;
-    T acc[CPT];
+    const int lg = threadIdx.x % LG, cg = threadIdx.x / LG;
+    T acc[4][CPT];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) acc[q] = T(0);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < CPT; ++b) acc[a][b] = T(0);
+    const int lr = threadIdx.x & 31, lq = threadIdx.x >> 5;   // loader: row, group
     for (int64_t r0 = rs0; r0 < rs1; r0 += TY_ROWS) {
         __syncthreads();
-        for (int idx = threadIdx.x; idx < TY_ROWS * NB; idx += 256) {
-            int rr = idx % TY_ROWS, ll = idx / TY_ROWS;
-            int64_t i = r0 + rr;
-            sV[rr][ll] = (i < rs1) ? v_at(F, ld, k, i, ll, ncols) : T(0);
+        const int64_t i = r0 + lr;
+        const bool iv = i < rs1;
+        for (int l0 = lq * 4; l0 < NB; l0 += 32) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sV[lr][l0 + u] = iv ? v_at(F, ld, k, i, l0 + u, ncols) : T(0);
         }
-        for (int cc = warp; cc < TY_COLS; cc += 8) {
-            int64_t c = cbase + cc;
-            int64_t i = r0 + lane;
-            sC[cc][lane] = (c < nct && i < rs1) ? F[(k + i) + (k + ncols + c) * ld] : T(0);
+        for (int c0 = lq * 4; c0 < TY_COLS; c0 += 32) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t c = cbase + c0 + u;
+                sC[lr][c0 + u] = (iv && c < nct) ? F[(k + i) + (k + ncols + c) * ld] : T(0);
+            }
         }
         __syncthreads();
 #pragma unroll 4
         for (int rr = 0; rr < TY_ROWS; ++rr) {
-            T v = sV[rr][l];
+            const V4 v = *reinterpret_cast<const V4 *>(&sV[rr][lg * 4]);
+            T cv[CPT];
 #pragma unroll
-            for (int q = 0; q < CPT; ++q) acc[q] += v * sC[g + q * GROUPS][rr];
+            for (int b = 0; b < CPT; ++b) cv[b] = sC[rr][cg * CPT + b];
+#pragma unroll
+            for (int b = 0; b < CPT; ++b) {
+                acc[0][b] += v.x * cv[b];
+                acc[1][b] += v.y * cv[b];
+                acc[2][b] += v.z * cv[b];
+                acc[3][b] += v.w * cv[b];
+            }
         }
     }
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-        int64_t c = cbase + g + q * GROUPS;
-        if (c < nct) Ypart[((int64_t)blockIdx.y * NB + l) * nct + c] = acc[q];
-    }
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < CPT; ++b) {
+            const int64_t c = cbase + cg * CPT + b;
+            if (c < nct) Ypart[((int64_t)blockIdx.y * NB + lg * 4 + a) * nct + c] = acc[a][b];
+        }
 }
 
-// C(i, c) -= sum_l V(i, l) Z(l, c) with Z = T^T Y, Y = sum_s Ypart[s].
-constexpr int TC_ROWS = 64;
+// C(i, c) -= sum_l V(i, l) Z(l, c) with Z = T^T Y, Y = sum_s Ypart[s].  CTA tile
+// TC_ROWS x TC_COLS; each thread owns 4 consecutive rows x 8 columns and reads and
+// writes C as 4-row vectors (coalesced along the column).
+constexpr int TC_ROWS = 128;
 constexpr int TC_COLS = 64;
 
 template <typename T, int NB>
@@ -296,9 +333,11 @@ __global__ void __launch_bounds__(256)
 k_trail_c(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct,
           const T *__restrict__ Ypart, int nsplit, const T *__restrict__ Tblk)
 {
-    __shared__ T sZ[NB][TC_COLS];      // holds Y, then Z = T^T Y in place
-    __shared__ T sV[TC_ROWS][NB + 1];
-    __shared__ T sT[NB][NB];
+    using V4 = typename Vec4<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*sZ)[TC_COLS] = reinterpret_cast<T (*)[TC_COLS]>(smem_raw);                   // [NB][TC_COLS]: Y, then Z
+    T (*sV)[TC_ROWS] = reinterpret_cast<T (*)[TC_ROWS]>(smem_raw + sizeof(T) * NB * TC_COLS);   // V(l, row)
+    T (*sT)[NB] = reinterpret_cast<T (*)[NB]>(smem_raw + sizeof(T) * NB * (TC_COLS + TC_ROWS));
     const int64_t mp = m - k;
     const int64_t rbase = (int64_t)blockIdx.x * TC_ROWS;
     const int64_t cbase = (int64_t)blockIdx.y * TC_COLS;
@@ -314,7 +353,7 @@ k_trail_c(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_
     for (int idx = threadIdx.x; idx < TC_ROWS * NB; idx += 256) {
         int rr = idx % TC_ROWS, ll = idx / TC_ROWS;
         int64_t i = rbase + rr;
-        sV[rr][ll] = (i < mp) ? v_at(F, ld, k, i, ll, ncols) : T(0);
+        sV[ll][rr] = (i < mp) ? v_at(F, ld, k, i, ll, ncols) : T(0);
     }
     __syncthreads();
     // Z(l, c) = sum_q T(q, l) Y(q, c)  (T upper triangular: q <= l), one column per thread
@@ -332,26 +371,45 @@ k_trail_c(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_
         }
     }
     __syncthreads();
-    const int rr = threadIdx.x % TC_ROWS;
-    const int cg4 = threadIdx.x / TC_ROWS;       // 4 groups of 16 columns
-    T acc[16];
+    const int r4 = (threadIdx.x & 31) * 4;     // 4 consecutive rows
+    const int c8 = (threadIdx.x >> 5) * 8;     // 8 columns
+    T acc[4][8];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = T(0);
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = T(0);
 #pragma unroll 4
     for (int ll = 0; ll < NB; ++ll) {
-        T v = sV[rr][ll];
+        const V4 v = *reinterpret_cast<const V4 *>(&sV[ll][r4]);
+        const V4 z0 = *reinterpret_cast<const V4 *>(&sZ[ll][c8]);
+        const V4 z1 = *reinterpret_cast<const V4 *>(&sZ[ll][c8 + 4]);
+        const T zz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] += v * sZ[ll][cg4 * 16 + q];
+        for (int b = 0; b < 8; ++b) {
+            acc[0][b] += v.x * zz[b];
+            acc[1][b] += v.y * zz[b];
+            acc[2][b] += v.z * zz[b];
+            acc[3][b] += v.w * zz[b];
+        }
     }
-    const int64_t i = rbase + rr;
-    if (i < mp) {
+    const int64_t i0 = rbase + r4;
+    const bool vec = (i0 + 3 < mp) && (((k + i0) & 3) == 0) && ((ld & 3) == 0);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            int64_t c = cbase + cg4 * 16 + q;
-            if (c < nct) {
-                T *p = F + (k + i) + (k + ncols + c) * ld;
-                *p -= acc[q];
-            }
+    for (int b = 0; b < 8; ++b) {
+        const int64_t c = cbase + c8 + b;
+        if (c >= nct) break;
+        T *p = F + (k + i0) + (k + ncols + c) * ld;
+        if (vec) {
+            V4 cur = *reinterpret_cast<V4 *>(p);
+            cur.x -= acc[0][b];
+            cur.y -= acc[1][b];
+            cur.z -= acc[2][b];
+            cur.w -= acc[3][b];
+            *reinterpret_cast<V4 *>(p) = cur;
+        } else {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (i0 + a < mp) p[a] -= acc[a][b];
         }
     }
 }
@@ -379,36 +437,42 @@ __device__ __forceinline__ T warp_reduce_scatter(T (&vals)[NB], int lane)
     return vals[0];
 }
 
-// y <- Q^T y (transpose) or Q y for a vector y [m_aug] of type T, on one cluster:
-// per panel, dots s_l = sum_i V(i,l) y_i (cluster exchange), w = T^T s (Q^T) or
-// T s (Q), then y_i -= sum_l V(i,l) w_l.  Rows below the unit-diagonal block read
-// V without masking.
+// y <- Q^T y (transpose) or Q y for a vector y [m_aug] of type T, grid-wide: one
+// CTA per SM (cooperative launch) owns a contiguous chunk of rows.  Per panel p:
+// dots s_l = sum_i V(i,l) y_i (CTA partials, double-buffered in global memory,
+// one grid barrier), w = T^T s (Q^T) or T s (Q), then y_i -= sum_l V(i,l) w_l on
+// the owned rows.  Rows below the unit-diagonal block read V without masking.
+constexpr int AQ_THREADS = 256;
+
 template <typename T, int NB>
-__global__ void __launch_bounds__(APPLY_THREADS, 1)
-k_apply_q(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n, const T *__restrict__ Tall,
-          T *__restrict__ y, int transpose)
+__global__ void __launch_bounds__(AQ_THREADS, 1)
+k_apply_q_grid(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n,
+               const T *__restrict__ Tall, T *__restrict__ y, int transpose, T *__restrict__ part,
+               GridBar *bar, int *flag)
 {
-    __shared__ T red[APPLY_WARPS][NB];
-    __shared__ T xbuf[2][CL_MAX][NB];
+    constexpr int NW = AQ_THREADS / 32;
+    constexpr int GROUPS = AQ_THREADS / NB;
+    __shared__ T red[NW][NB];
+    __shared__ T red2[GROUPS][NB];
     __shared__ T w[NB];
     __shared__ T sT[NB][NB + 1];
-    cg::cluster_group cluster = cg::this_cluster();
-    const int rank = (int)cluster.block_rank();
-    const int CL = (int)cluster.num_blocks();
+    __shared__ volatile int s_abort;
+    const unsigned G = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t rows_per = fl_cdiv_dev(m_aug, CL);
-    const int64_t r_lo = rank * rows_per, r_hi = fl_min64(m_aug, r_lo + rows_per);
+    if (threadIdx.x == 0) s_abort = 0;
+    const int64_t rows_per = fl_cdiv_dev(m_aug, G);
+    const int64_t r_lo = (int64_t)blockIdx.x * rows_per, r_hi = fl_min64(m_aug, r_lo + rows_per);
     const int npanels = (int)((n + NB - 1) / NB);
     for (int step = 0; step < npanels; ++step) {
         const int p = transpose ? step : (npanels - 1 - step);
         const int64_t k = (int64_t)p * NB;
         const int ncols = (int)fl_min64(NB, n - k);
         const int par = step & 1;
-        const T *Vp = F + k + k * ld;              // V(i, q) = Vp[i + q * ld] below the block
+        const T *Vp = F + k + k * ld;
         T acc[NB];
 #pragma unroll
         for (int q = 0; q < NB; ++q) acc[q] = T(0);
-        for (int64_t i = fl_max64(r_lo, k) + threadIdx.x; i < r_hi; i += APPLY_THREADS) {
+        for (int64_t i = fl_max64(r_lo, k) + threadIdx.x; i < r_hi; i += AQ_THREADS) {
             const int64_t li = i - k;
             const T yi = y[i];
             if (li >= NB) {
@@ -420,27 +484,39 @@ k_apply_q(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n, const T
                 for (int q = 0; q < NB; ++q) acc[q] += v_at(F, ld, k, li, q, ncols) * yi;
             }
         }
-        const T part = warp_reduce_scatter<T, NB>(acc, lane);
-        if (lane < NB) red[warp][lane] = part;
-        for (int idx = threadIdx.x; idx < NB * NB; idx += APPLY_THREADS)
-            sT[idx % NB][idx / NB] = Tall[(int64_t)p * NB * NB + idx];
+        const T partial = warp_reduce_scatter<T, NB>(acc, lane);
+        if (lane < NB) red[warp][lane] = partial;
         __syncthreads();
         if (warp == 0 && lane < NB) {
             T s = T(0);
-            for (int ww = 0; ww < APPLY_WARPS; ++ww) s += red[ww][lane];
-            for (int dst = 0; dst < CL; ++dst) {
-                T *rb = cluster.map_shared_rank(&xbuf[0][0][0], dst);
-                rb[(par * CL_MAX + rank) * NB + lane] = s;
-            }
+#pragma unroll
+            for (int ww = 0; ww < NW; ++ww) s += red[ww][lane];
+            part[((int64_t)par * G + blockIdx.x) * NB + lane] = s;
         }
-        cluster.sync();
+        if (!grid_sync(bar, G, flag, &s_abort)) return;
+        for (int idx = threadIdx.x; idx < NB * NB; idx += AQ_THREADS)
+            sT[idx % NB][idx / NB] = Tall[(int64_t)p * NB * NB + idx];
+        {   // sum the G partials: thread (group g, column l) takes CTAs g, g + GROUPS, ...
+            const int l = threadIdx.x % NB, g = threadIdx.x / NB;
+            T s0 = T(0), s1 = T(0);
+            unsigned c = g;
+            for (; c + GROUPS < G; c += 2 * GROUPS) {
+                s0 += part[((int64_t)par * G + c) * NB + l];
+                s1 += part[((int64_t)par * G + c + GROUPS) * NB + l];
+            }
+            for (; c < G; c += GROUPS) s0 += part[((int64_t)par * G + c) * NB + l];
+            red2[g][l] = s0 + s1;
+        }
+        __syncthreads();
         if (warp == 0) {
             T s = T(0);
             if (lane < NB)
-                for (int src = 0; src < CL; ++src) s += xbuf[par][src][lane];
+#pragma unroll
+                for (int g = 0; g < GROUPS; ++g) s += red2[g][lane];
             T wl = T(0);
+#pragma unroll
             for (int q = 0; q < NB; ++q) {
-                T sq = __shfl_sync(0xffffffffu, s, q);
+                const T sq = __shfl_sync(0xffffffffu, s, q);
                 if (lane < NB) {
                     // Q^T: w = T^T s -> w_l = sum_{q <= l} T(q,l) s_q ; Q: w = T s -> w_l = sum_{q >= l} T(l,q) s_q
                     if (transpose) { if (q <= lane) wl += sT[q][lane] * sq; }
@@ -450,7 +526,7 @@ k_apply_q(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n, const T
             if (lane < NB) w[lane] = wl;
         }
         __syncthreads();
-        for (int64_t i = fl_max64(r_lo, k) + threadIdx.x; i < r_hi; i += APPLY_THREADS) {
+        for (int64_t i = fl_max64(r_lo, k) + threadIdx.x; i < r_hi; i += AQ_THREADS) {
             const int64_t li = i - k;
             T s = T(0);
             if (li >= NB) {
@@ -465,110 +541,6 @@ k_apply_q(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n, const T
         }
         __syncthreads();
     }
-}
-
-// Back substitution R x = y (R: upper triangle of F, n x n) on one CTA of 1024
-// threads, 32-row blocks bottom-up.  Per block: the 32 x (n - r1) strip right of
-// the block is contracted with the solved x (32 warps, 4 independent loads in
-// flight per thread), the 32 x 32 diagonal block is staged in shared memory, and
-// warp 0 substitutes from shared memory.  y: [n] in, x: [n] out (may alias y).
-template <typename T>
-__global__ void __launch_bounds__(1024, 1)
-k_trsv_upper(const T *__restrict__ F, int64_t ld, int64_t n, const T *y, T *x, int *flag,
-             const int *skip)
-{
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sx = reinterpret_cast<T *>(smem_raw);   // [n]
-    __shared__ T red[32][33];
-    __shared__ T D[32][33];                     // diagonal block D(row, col)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t nblk = (n + 31) / 32;
-    for (int64_t bi = nblk - 1; bi >= 0; --bi) {
-        const int64_t r0 = bi * 32, r1 = fl_min64(n, r0 + 32);
-        const int64_t row = r0 + lane;
-        const bool rv = row < r1;
-        // diagonal block: thread (warp = column, lane = row)
-        D[lane][warp] = (rv && r0 + warp < r1) ? F[row + (r0 + warp) * ld] : T(0);
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        if (rv) {
-            int64_t c = r1 + warp;
-            for (; c + 96 < n; c += 128) {
-                a0 += F[row + c * ld] * sx[c];
-                a1 += F[row + (c + 32) * ld] * sx[c + 32];
-                a2 += F[row + (c + 64) * ld] * sx[c + 64];
-                a3 += F[row + (c + 96) * ld] * sx[c + 96];
-            }
-            for (; c < n; c += 32) a0 += F[row + c * ld] * sx[c];
-        }
-        red[warp][lane] = (a0 + a1) + (a2 + a3);
-        __syncthreads();
-        if (warp == 0) {
-            T s = T(0);
-            for (int ww = 0; ww < 32; ++ww) s += red[ww][lane];
-            if (rv) s = y[row] - s;
-            const int nr = (int)(r1 - r0);
-            for (int li = nr - 1; li >= 0; --li) {
-                T xv = __shfl_sync(0xffffffffu, s, li) / D[li][li];
-                if (!fl_isfinite(xv)) raise_flag(flag, FL_DEVERR_NONFINITE);
-                if (lane == li) s = xv;
-                if (lane < li) s -= D[lane][li] * xv;
-            }
-            if (rv) sx[row] = s;
-        }
-        __syncthreads();
-    }
-    for (int64_t i = threadIdx.x; i < n; i += 1024) x[i] = sx[i];
-}
-
-// Forward substitution R^T x = y, 32-row blocks top-down (same launch shape):
-// warp w contracts column r0 + w of R above the block with the solved x.
-template <typename T>
-__global__ void __launch_bounds__(1024, 1)
-k_trsv_upper_t(const T *__restrict__ F, int64_t ld, int64_t n, const T *y, T *x, int *flag,
-               const int *skip)
-{
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sx = reinterpret_cast<T *>(smem_raw);
-    __shared__ T sdot[32];
-    __shared__ T D[32][33];                     // D(row, col) of the diagonal block of R
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t nblk = (n + 31) / 32;
-    for (int64_t bi = 0; bi < nblk; ++bi) {
-        const int64_t r0 = bi * 32, r1 = fl_min64(n, r0 + 32);
-        const int64_t col = r0 + warp;
-        D[lane][warp] = (r0 + lane < r1 && col < r1) ? F[(r0 + lane) + col * ld] : T(0);
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        if (col < r1) {
-            int64_t c = lane;
-            for (; c + 96 < r0; c += 128) {
-                a0 += F[c + col * ld] * sx[c];
-                a1 += F[c + 32 + col * ld] * sx[c + 32];
-                a2 += F[c + 64 + col * ld] * sx[c + 64];
-                a3 += F[c + 96 + col * ld] * sx[c + 96];
-            }
-            for (; c < r0; c += 32) a0 += F[c + col * ld] * sx[c];
-        }
-        T acc = (a0 + a1) + (a2 + a3);
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) sdot[warp] = acc;
-        __syncthreads();
-        if (warp == 0) {
-            const int64_t row = r0 + lane;
-            T s = (row < r1) ? y[row] - sdot[lane] : T(0);
-            const int nr = (int)(r1 - r0);
-            for (int li = 0; li < nr; ++li) {
-                T xv = __shfl_sync(0xffffffffu, s, li) / D[li][li];
-                if (!fl_isfinite(xv)) raise_flag(flag, FL_DEVERR_NONFINITE);
-                if (lane == li) s = xv;
-                if (lane > li) s -= D[li][lane] * xv;
-            }
-            if (row < r1) sx[row] = s;
-        }
-        __syncthreads();
-    }
-    for (int64_t i = threadIdx.x; i < n; i += 1024) x[i] = sx[i];
 }
 
 // Copy A (and the rhs columns) into the factor storage, writing the Tikhonov
@@ -686,16 +658,6 @@ cudaError_t set_max_dynamic_smem(K kernel, int optin)
                                 optin - (int)a.sharedSizeBytes);
 }
 
-template <typename T>
-int trsv_dynamic_limit(fastlsq_ctx *ctx, int transpose)
-{
-    cudaFuncAttributes a;
-    cudaError_t e = transpose ? cudaFuncGetAttributes(&a, k_trsv_upper_t<T>)
-                              : cudaFuncGetAttributes(&a, k_trsv_upper<T>);
-    if (e != cudaSuccess) return 0;
-    return ctx->max_smem_optin - (int)a.sharedSizeBytes;
-}
-
 template <typename T, int NB>
 int set_panel_attrs(fastlsq_ctx *ctx)
 {
@@ -704,10 +666,7 @@ int set_panel_attrs(fastlsq_ctx *ctx)
     cudaError_t e = set_max_dynamic_smem(k_panel<T, NB>, ctx->max_smem_optin);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_panel<T, NB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_apply_q<T, NB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess) e = set_max_dynamic_smem(k_trsv_upper<T>, ctx->max_smem_optin);
-    if (e == cudaSuccess) e = set_max_dynamic_smem(k_trsv_upper_t<T>, ctx->max_smem_optin);
+
     if (e != cudaSuccess) return fl_cuda(ctx, e, "cudaFuncSetAttribute");
     done = true;
     return 0;
@@ -724,7 +683,7 @@ int fl_panel_capacity_nb(fastlsq_ctx *ctx, int64_t m_aug, size_t elem)
     // largest NB in {32, 16, 8} whose panel slice fits on a 16-CTA cluster
     for (int nb = 32; nb >= 8; nb /= 2) {
         int64_t rpc = fl_cdiv(m_aug, CL_MAX);
-        size_t bytes = elem * ((size_t)rpc * (nb + 1) + PANEL_WARPS * 32 + 2 * (CL_MAX + 1) * nb +
+        size_t bytes = elem * ((size_t)rpc * (nb + 1) + PANEL_WARPS * 33 + 2 * (CL_MAX + 1) * nb +
                                2 * nb * (nb + 1) + nb);
         if (bytes <= (size_t)ctx->max_smem_optin) return nb;
     }
@@ -778,11 +737,19 @@ static int launch_trailing(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_
     nsplit = fl_cdiv(mp, rows_per_split);
     T *Ypart = (T *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(T) * nsplit * NB * nct);
     if (!Ypart) return FASTLSQ_ERR_NOMEM;
+    static bool attr_done = false;
+    const size_t smem_c = sizeof(T) * NB * (TC_COLS + TC_ROWS + NB);
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_trail_c<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_c);
+        if (e != cudaSuccess) return fl_cuda(ctx, e, "trail_c attribute");
+        attr_done = true;
+    }
     FL_PROF_N(ctx, FASTLSQ_K_TRAIL_SIMT, 2);
     k_trail_y<T, NB><<<dim3((unsigned)ctiles, (unsigned)nsplit), 256, 0, ctx->stream>>>(
         F, ld, k, m_aug, ncols, nct, rows_per_split, Ypart);
     FL_CHECK_LAUNCH(ctx, "trail_y");
-    k_trail_c<T, NB><<<dim3((unsigned)fl_cdiv(mp, TC_ROWS), (unsigned)fl_cdiv(nct, TC_COLS)), 256, 0,
+    k_trail_c<T, NB><<<dim3((unsigned)fl_cdiv(mp, TC_ROWS), (unsigned)fl_cdiv(nct, TC_COLS)), 256, smem_c,
                        ctx->stream>>>(F, ld, k, m_aug, ncols, nct, Ypart, (int)nsplit, Tblk);
     FL_CHECK_LAUNCH(ctx, "trail_c");
     return 0;
@@ -829,38 +796,22 @@ template <typename T>
 int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
                const T *Tall, T *y, int transpose)
 {
-    cudaLaunchConfig_t cfg = {};
-    int CL = CL_MAX;
-    while (CL > 1 && fl_cdiv(m_aug, CL) < 256) CL >>= 1;
-    cfg.gridDim = dim3(CL);
-    cfg.blockDim = dim3(APPLY_THREADS);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = ctx->stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CL;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaSuccess;
-    FL_PROF(ctx, FASTLSQ_K_APPLY_Q);
+    const unsigned G = (unsigned)ctx->num_sms;
+    T *part = (T *)fl_ws(ctx, FL_WS_APPLYQ, sizeof(T) * 2 * G * 32);
+    if (!part) return FASTLSQ_ERR_NOMEM;
+    GridBar *bar = (GridBar *)ctx->d_grid_bar;
+    int *flag = ctx->d_flag;
+    void *args[] = {(void *)&F, (void *)&ld, (void *)&m_aug, (void *)&n, (void *)&Tall, (void *)&y,
+                    (void *)&transpose, (void *)&part, (void *)&bar, (void *)&flag};
+    const void *fn = nullptr;
     switch (nb) {
-    case 32:
-        FL_TRY((set_panel_attrs<T, 32>(ctx)));
-        e = cudaLaunchKernelEx(&cfg, k_apply_q<T, 32>, F, ld, m_aug, n, Tall, y, transpose);
-        break;
-    case 16:
-        FL_TRY((set_panel_attrs<T, 16>(ctx)));
-        e = cudaLaunchKernelEx(&cfg, k_apply_q<T, 16>, F, ld, m_aug, n, Tall, y, transpose);
-        break;
-    case 8:
-        FL_TRY((set_panel_attrs<T, 8>(ctx)));
-        e = cudaLaunchKernelEx(&cfg, k_apply_q<T, 8>, F, ld, m_aug, n, Tall, y, transpose);
-        break;
-    default:
-        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "panel width %d", nb);
+    case 32: fn = (const void *)k_apply_q_grid<T, 32>; break;
+    case 16: fn = (const void *)k_apply_q_grid<T, 16>; break;
+    case 8: fn = (const void *)k_apply_q_grid<T, 8>; break;
+    default: return fl_fail(ctx, FASTLSQ_ERR_INVALID, "panel width %d", nb);
     }
+    FL_PROF(ctx, FASTLSQ_K_APPLY_Q);
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(AQ_THREADS), args, 0, ctx->stream);
     if (e != cudaSuccess) return fl_cuda(ctx, e, "apply_q launch");
     return 0;
 }
@@ -868,28 +819,6 @@ template int fl_apply_q<float>(fastlsq_ctx *, const float *, int64_t, int64_t, i
                                const float *, float *, int);
 template int fl_apply_q<double>(fastlsq_ctx *, const double *, int64_t, int64_t, int64_t, int,
                                 const double *, double *, int);
-
-template <typename T>
-int fl_trsv(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const T *y, T *x, int transpose,
-            const int *skip)
-{
-    FL_TRY((set_panel_attrs<T, 32>(ctx)));
-    size_t smem = sizeof(T) * (size_t)n;
-    if ((int64_t)smem > (int64_t)trsv_dynamic_limit<T>(ctx, transpose))
-        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "triangular solve: n_feat %lld too large",
-                       (long long)n);
-    FL_PROF(ctx, FASTLSQ_K_TRSV);
-    if (transpose)
-        k_trsv_upper_t<T><<<1, 1024, smem, ctx->stream>>>(F, ld, n, y, x, ctx->d_flag, skip);
-    else
-        k_trsv_upper<T><<<1, 1024, smem, ctx->stream>>>(F, ld, n, y, x, ctx->d_flag, skip);
-    FL_CHECK_LAUNCH(ctx, "trsv");
-    return 0;
-}
-template int fl_trsv<float>(fastlsq_ctx *, const float *, int64_t, int64_t, const float *,
-                            float *, int, const int *);
-template int fl_trsv<double>(fastlsq_ctx *, const double *, int64_t, int64_t, const double *,
-                             double *, int, const int *);
 
 template <typename TA, typename T>
 int fl_copy_in(fastlsq_ctx *ctx, const TA *A, int64_t ldA, int64_t m, int64_t n, double mu,

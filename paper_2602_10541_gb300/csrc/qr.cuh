@@ -12,9 +12,6 @@ int fl_factor(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n, int 
 template <typename T>
 int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
                const T *Tall, T *y, int transpose);
-template <typename T>
-int fl_trsv(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const T *y, T *x, int transpose,
-            const int *skip = nullptr);
 template <typename TA, typename T>
 int fl_copy_in(fastlsq_ctx *ctx, const TA *A, int64_t ldA, int64_t m, int64_t n, double mu,
                int64_t m_aug, const double *rhs, int64_t ld_rhs, int nrhs, T *F, int64_t ld);
@@ -40,3 +37,8 @@ int fl_refine_cgls(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs6
                    int max_iter, double tol, double *norms_dev);
 int fl_normal_pcg(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *c64, double *v64,
                   int max_iter, double tol);
+
+// grid-wide FP64 triangular solve with R of type T (refine.cu)
+template <typename T>
+int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const double *y, double *x,
+                 double *work, int transpose, const void *skip_scalars = nullptr);

@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "gridsync.cuh"
 #include "qr.cuh"
 
 namespace {
@@ -180,42 +181,6 @@ __global__ void k_kry_copy_sub(double *__restrict__ dst, const double *__restric
 // barrier spins a bounded number of times; on timeout it raises the device flag
 // and the kernel returns.
 // ---------------------------------------------------------------------------
-struct GridBar {
-    unsigned count;
-    unsigned gen;
-};
-
-constexpr long long BAR_SPIN_LIMIT = 1ll << 24;
-
-__device__ bool grid_sync(GridBar *bar, unsigned nblocks, int *flag, volatile int *s_abort)
-{
-    __syncthreads();
-    if (threadIdx.x == 0 && !*s_abort) {
-        volatile unsigned *vgen = &bar->gen;
-        const unsigned g = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
-        if (arrived == nblocks) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == g) {
-                if (++spins > BAR_SPIN_LIMIT) {
-                    atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
-                    *s_abort = 1;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return *s_abort == 0;
-}
-
 constexpr int TG_BS = 64;
 constexpr int TG_THREADS = 256;
 
@@ -352,24 +317,38 @@ int kry_dot(fastlsq_ctx *ctx, const double *a, const double *b, int64_t n, const
     return 0;
 }
 
-// out = R^{-1} in (transpose = 0) or R^{-T} in, in FP64 with the factor's R
+}  // namespace
+
+// x = R^{-1} y (transpose 0) or R^{-T} y in FP64 with the factor's R (type T);
+// work: [n] FP64 scratch; skip: optional device flag that makes the call a no-op.
 template <typename T>
-int kry_prec(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *in, double *out, int transpose,
-             const KryBufs &B)
+int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const double *y, double *x,
+                 double *work, int transpose, const void *skip_scalars)
 {
     FL_PROF(ctx, FASTLSQ_K_TRSV);
-    const T *F = (const T *)f->F;
-    int64_t ld = f->ld, n = f->n;
     int *flag = ctx->d_flag;
-    const KryScalars *st = B.st;
-    GridBar *bar = B.bar;
-    double *work = B.work;
-    void *args[] = {(void *)&F, (void *)&ld, (void *)&n, (void *)&in, (void *)&out, (void *)&work,
+    const KryScalars *st = (const KryScalars *)skip_scalars;
+    GridBar *bar = (GridBar *)ctx->d_grid_bar;
+    void *args[] = {(void *)&F, (void *)&ld, (void *)&n, (void *)&y, (void *)&x, (void *)&work,
                     (void *)&transpose, (void *)&bar, (void *)&flag, (void *)&st};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_trsv_grid<T>, dim3(ctx->num_sms),
                                                 dim3(TG_THREADS), args, 0, ctx->stream);
     if (e != cudaSuccess) return fl_cuda(ctx, e, "grid triangular solve");
     return 0;
+}
+template int fl_trsv_grid<float>(fastlsq_ctx *, const float *, int64_t, int64_t, const double *,
+                                 double *, double *, int, const void *);
+template int fl_trsv_grid<double>(fastlsq_ctx *, const double *, int64_t, int64_t, const double *,
+                                  double *, double *, int, const void *);
+
+namespace {
+
+// out = R^{-1} in (transpose = 0) or R^{-T} in, in FP64 with the factor's R
+template <typename T>
+int kry_prec(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *in, double *out, int transpose,
+             const KryBufs &B)
+{
+    return fl_trsv_grid<T>(ctx, (const T *)f->F, f->ld, f->n, in, out, B.work, transpose, B.st);
 }
 
 template <typename T>
@@ -459,4 +438,36 @@ int fl_normal_pcg(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *c64, 
     if (!f->A_refine) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "PCG adjoint needs the FP64 operator");
     if (f->prec == FASTLSQ_PREC_FP64) return normal_pcg_t<double>(ctx, f, c64, v64, max_iter, tol);
     return normal_pcg_t<float>(ctx, f, c64, v64, max_iter, tol);
+}
+
+namespace {
+template <typename T>
+__global__ void k_get_r(const T *__restrict__ F, int64_t ld, int64_t n, double *__restrict__ R, int64_t ldr)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = blockIdx.y;
+    if (i >= n || j >= n) return;
+    R[i + j * ldr] = (i <= j) ? (double)F[i + j * ld] : 0.0;
+}
+}  // namespace
+
+int fl_factor_get_r(fastlsq_ctx *ctx, const fastlsq_factor *f, double *R, int64_t ldr)
+{
+    FL_PROF(ctx, FASTLSQ_K_VECTOR);
+    dim3 grid((unsigned)fl_cdiv(f->n, 256), (unsigned)f->n);
+    if (f->prec == FASTLSQ_PREC_FP64)
+        k_get_r<double><<<grid, 256, 0, ctx->stream>>>((const double *)f->F, f->ld, f->n, R, ldr);
+    else
+        k_get_r<float><<<grid, 256, 0, ctx->stream>>>((const float *)f->F, f->ld, f->n, R, ldr);
+    FL_CHECK_LAUNCH(ctx, "get_r");
+    return 0;
+}
+
+int fl_factor_trsv64(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *y, double *x, int transpose)
+{
+    KryBufs B;
+    FL_TRY(kry_bufs(ctx, f, &B));
+    cudaMemsetAsync(B.st, 0, sizeof(KryScalars), ctx->stream);
+    if (f->prec == FASTLSQ_PREC_FP64) return kry_prec<double>(ctx, f, y, x, transpose, B);
+    return kry_prec<float>(ctx, f, y, x, transpose, B);
 }

@@ -76,6 +76,8 @@ _SIGNATURES = {
     "fastlsq_factor_solve": [_vp, _vp, _vp, _i32, _i64, _vp, _i64, _i32, _i32, _dbl,
                              ctypes.POINTER(fastlsq_solve_stats)],
     "fastlsq_factor_destroy": [_vp],
+    "fastlsq_factor_get_r": [_vp, _vp, _vp, _i64],
+    "fastlsq_factor_trsv": [_vp, _vp, _vp, _vp, _i32],
     "fastlsq_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _i32, _dbl],
     "fastlsq_source_grad": [_vp, _vp, _i64, ctypes.POINTER(_dbl), _i32, _vp, ctypes.POINTER(_dbl)],
     "fastlsq_coef_grad": [_vp, _vp, _i64, ctypes.POINTER(fastlsq_op), _vp, _vp, _i64, _dbl, _vp,
@@ -249,6 +251,16 @@ def fastlsq_factor_solve(ctx, factor, rhs, beta, max_refine=0, stats=False,
                                       float(refine_tol), ctypes.byref(st) if stats else None)
     ctx.check(rc)
     return rc, st
+
+
+def fastlsq_factor_get_r(ctx, factor, R):
+    """R: (n_feat, ld >= n_feat) float64 column-major tensor."""
+    return ctx.check(ctx.lib.fastlsq_factor_get_r(ctx.handle, factor, _ptr(R), R.shape[1]))
+
+
+def fastlsq_factor_trsv(ctx, factor, y, x, transpose=False):
+    return ctx.check(ctx.lib.fastlsq_factor_trsv(ctx.handle, factor, _ptr(y), _ptr(x),
+                                                 1 if transpose else 0))
 
 
 def fastlsq_factor_destroy(ctx, factor):

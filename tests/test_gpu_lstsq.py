@@ -141,6 +141,36 @@ def test_mixed_cgls_refinement_reaches_fp64_on_large_residual(ctx, mu):
     np.testing.assert_allclose(beta.cpu().numpy()[0], ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("prec,dt,tol", [(fl.PREC_FP64, torch.float64, 1e-11),
+                                          (fl.PREC_MIXED, torch.float32, 2e-5)])
+@pytest.mark.parametrize("m,n", [(700, 130), (200, 64), (3000, 257)])
+def test_factor_r_matches_householder_and_trsv_inverts_it(ctx, prec, dt, tol, m, n):
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n))
+    beta = torch.zeros((1, n), dtype=torch.float64, device=DEV)
+    Ad = _cm(A, dt)
+    _, fac, _ = fl.fastlsq_lstsq(ctx, prec, Ad, m, 0.0, None, None, A_refine=_cm(A, torch.float64),
+                                 keep=True)
+    R = torch.zeros((n, n), dtype=torch.float64, device=DEV)
+    fl.fastlsq_factor_get_r(ctx, fac, R)
+    Rg = R.cpu().numpy().T
+    packed, _ = oracle.qr(A)
+    Ro = np.triu(packed[:n])
+    # same reflector sign convention: R agrees entry for entry (relative to its scale)
+    assert np.abs(Rg - Ro).max() <= tol * np.abs(Ro).max()
+    y = rng.standard_normal(n)
+    for tr in (False, True):
+        x = torch.empty(n, dtype=torch.float64, device=DEV)
+        fl.fastlsq_factor_trsv(ctx, fac, _t1(y), x, transpose=tr)
+        ref = np.linalg.solve(Rg.T if tr else Rg, y)          # the exported R, FP64
+        np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+    fl.fastlsq_factor_destroy(ctx, fac)
+
+
+def _t1(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
 def _oracle_solution(w):
     A_int = oracle.assemble(w.x_int, w.alpha, w.coef, w.W, w.b, w.scale)
     A_bc = oracle.assemble(w.x_bc, np.zeros((1, w.d), np.int32), [1.0], w.W, w.b, w.scale,
