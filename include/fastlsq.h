@@ -269,6 +269,50 @@ FASTLSQ_API int fastlsq_coef_grad(fastlsq_ctx *ctx, const double *x, int64_t n_r
                       const double *r, const double *Av, const double *v,
                       const double *beta, double *grad);
 
+/* One instance of the steady inverse heat-source problem (Sec. 4.4, App. F.2 in
+ * steady form): -L u = s(x; theta) in the domain (interior operator from the
+ * batch call), u = 0 on the boundary rows, sensors u_s = u(x_s), loss
+ * L = mean_s (u_s - y_s)^2.  All pointers are DEVICE pointers. */
+typedef struct {
+    int64_t n_int, n_bc, n_feat, n_sens;
+    const double *x_int;      /* [n_int][2]  */
+    const double *x_bc;       /* [n_bc][2]   */
+    const double *W;          /* [n_feat][2] */
+    const double *b;          /* [n_feat]    */
+    const double *sensors;    /* [n_sens][2] */
+    const double *y_obs;      /* [n_sens]    */
+    const double *theta;      /* [n_src * 4] evaluation point (c_x, c_y, w, a) per source */
+    double *beta;             /* out [n_feat]      */
+    double *loss;             /* out [1]           */
+    double *dtheta;           /* out [n_src * 4]   */
+} fastlsq_inverse_instance;
+
+typedef struct {
+    int32_t prec;             /* fastlsq_prec of the factorisation                    */
+    int32_t refine_iters;     /* CGLS iterations of the forward solve (MIXED)         */
+    double refine_tol;
+    int32_t adjoint_iters;    /* PCG iterations of the adjoint solve (MIXED)          */
+    double adjoint_tol;
+    double mu;                /* Tikhonov parameter (rows sqrt(mu) I)                 */
+    double bc_weight;         /* boundary penalty lambda                              */
+} fastlsq_inverse_opts;
+
+/*
+ * Loss and gradient dL/dtheta for a batch of instances of uneven size (the
+ * differentiable solve of Sec. 2.5 applied to the inverse problem of Sec. 4.4):
+ * per instance, assemble the operator (FP64, plus FP32 for a MIXED factor),
+ * factor it, solve for beta with the source s(x; theta), read the sensors, form
+ * the loss, and run the adjoint: grad_beta = H_s^T dL/du_s,
+ * v = (A^T A + mu I)^{-1} grad_beta, dL/ds = A v, dL/dtheta = sum_i (A v)_i
+ * ds(x_i)/dtheta.  op is the interior operator (e.g. -Lap); n_src Gaussian
+ * sources.  Queued on the context's stream without host synchronisation (the
+ * whole batch can be captured in a CUDA graph once the workspace has been sized
+ * by a first call).
+ */
+FASTLSQ_API int fastlsq_inverse_batch(fastlsq_ctx *ctx, const fastlsq_inverse_instance *inst,
+                                      int32_t n_inst, const fastlsq_op *op, int32_t n_src,
+                                      const fastlsq_inverse_opts *opts);
+
 /* Nonlinearities N(u) of the Newton problems (Sec. 3.3). */
 typedef enum { FASTLSQ_NL_NONE = 0, FASTLSQ_NL_EXP = 1, FASTLSQ_NL_CUBIC = 2 } fastlsq_nl;
 
@@ -320,6 +364,14 @@ FASTLSQ_API int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p
                    const double *W, const double *b, int64_t n_feat, double scale,
                    const fastlsq_newton_opts *opts, double *beta_inout,
                    fastlsq_newton_stats *stats);
+
+/* Context options for fastlsq_set_option. */
+typedef enum {
+    FASTLSQ_OPT_TENSOR_CORE = 0   /* 1: MIXED trailing updates on tcgen05 (TF32x3), 0: SIMT FP32 */
+} fastlsq_option;
+
+/* Set a context option (see fastlsq_option).  Returns 0 or -1 for an unknown option. */
+FASTLSQ_API int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value);
 
 /* Kernel classes for profiling (launch counts are always kept; device times are
  * recorded with CUDA events around each launch only while profiling is on). */

@@ -248,6 +248,16 @@ extern "C" int fastlsq_set_stream(fastlsq_ctx *ctx, void *stream)
     return 0;
 }
 
+extern "C" int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value)
+{
+    if (!ctx) return FASTLSQ_ERR_INVALID;
+    if (option == FASTLSQ_OPT_TENSOR_CORE) {
+        ctx->use_tensor_core = value ? 1 : 0;
+        return 0;
+    }
+    return fl_fail(ctx, FASTLSQ_ERR_INVALID, "unknown option %d", option);
+}
+
 extern "C" const char *fastlsq_last_error(const fastlsq_ctx *ctx)
 {
     return ctx ? ctx->last_error.c_str() : "null context";
@@ -510,6 +520,12 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
         rc = solve_all(ctx, f, nrhs, rhs, nrhs, ld_rhs, beta, ld_beta,
                        (prec == FASTLSQ_PREC_MIXED || refine_mode == FASTLSQ_REFINE_CGLS) ? max_refine : 0,
                        refine_mode, refine_tol, stats);
+    if (rc == 0 && nrhs == 0 && stats) {            // factor only: report the factor's shape
+        memset(stats, 0, sizeof(*stats));
+        stats->nb = f->nb;
+        stats->tensor_core = f->tensor_core;
+        stats->status = rc = fastlsq_sync(ctx);
+    }
     if (rc < 0 || !keep) {
         factor_free(f);
         return rc;

@@ -796,8 +796,9 @@ template <typename T>
 int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
                const T *Tall, T *y, int transpose)
 {
-    const unsigned G = (unsigned)ctx->num_sms;
-    T *part = (T *)fl_ws(ctx, FL_WS_APPLYQ, sizeof(T) * 2 * G * 32);
+    // about 512 rows per CTA keeps the partial sums few (one L2 round trip to combine)
+    const unsigned G = (unsigned)std::min<int64_t>(ctx->num_sms, std::max<int64_t>(4, fl_cdiv(m_aug, 512)));
+    T *part = (T *)fl_ws(ctx, FL_WS_APPLYQ, sizeof(T) * 2 * ctx->num_sms * 32);
     if (!part) return FASTLSQ_ERR_NOMEM;
     GridBar *bar = (GridBar *)ctx->d_grid_bar;
     int *flag = ctx->d_flag;

@@ -13,7 +13,10 @@
 // Every kernel reads a device flag and returns at once after convergence, so a
 // fixed number of launches can be queued (and captured in a CUDA graph) without
 // host round trips.
+#include <algorithm>
 #include <cmath>
+
+#include <cooperative_groups.h>
 
 #include "common.cuh"
 #include "gridsync.cuh"
@@ -172,26 +175,203 @@ __global__ void k_kry_copy_sub(double *__restrict__ dst, const double *__restric
 }
 
 // ---------------------------------------------------------------------------
-// Grid-wide FP64 triangular solve with the factor's R (entries of type T promoted
-// to double): R x = y (transpose 0) or R^T x = y.  Applying R^{-1} in FP64 keeps
-// the preconditioner a fixed linear operator even when kappa(R) eps32 >> 1.
-// One CTA per SM (cooperative launch, so all CTAs are resident), 64-row blocks:
-// CTA 0 substitutes within the block from shared memory, then every CTA removes
-// the block's contribution from its share of the remaining rows.  The grid
-// barrier spins a bounded number of times; on timeout it raises the device flag
-// and the kernel returns.
+// FP64 triangular solves with the factor's R (entries of type T promoted to
+// double): R x = y (transpose 0) or R^T x = y.  Applying R^{-1} in FP64 keeps the
+// preconditioner a fixed linear operator even when kappa(R) eps32 >> 1, and the
+// FP64 path gets LAPACK-grade backward stability: every 64 x 64 diagonal block is
+// solved by substitution (no explicit inverse, whose error grows with the block's
+// condition number), the off-diagonal blocks are applied as FP64 mat-vecs.
+//
+//  * k_trsv_cluster: one cluster of up to 16 CTAs.  64-row block b belongs to
+//    rank b % CS, which keeps its diagonal block and its rows of the running
+//    right-hand side w in shared memory.  Per block: the owner's warp 0 solves the
+//    diagonal block and writes x_b into every rank's shared copy of x (DSMEM);
+//    one cluster barrier; every rank removes x_b's contribution from its own
+//    remaining rows.  No grid barrier and no global scratch.
+//  * k_trsv_grid: the same blocked substitution on a cooperative grid for R too
+//    large for the cluster's shared memory (two grid barriers per block; each
+//    barrier spins for at most about a second, then raises the device flag and
+//    the kernel returns).
 // ---------------------------------------------------------------------------
 constexpr int TG_BS = 64;
 constexpr int TG_THREADS = 256;
+constexpr int TC_THREADS = 512;
+constexpr int TS_LD = TG_BS + 1;        // padded column stride of a staged diagonal block
+constexpr int TC_MAX_CS = 16;
+
+// Stage diagonal block b as the "effective" triangle E in column-major layout
+// E[j * TS_LD + i]: E = D (upper) or D^T (lower, transpose).  Ragged rows/cols
+// beyond n become the identity so that the padded unknowns solve to zero.
+template <typename T>
+__device__ __forceinline__ void trsv_stage_diag(const T *__restrict__ F, int64_t ld, int64_t n, int64_t r0,
+                                                int transpose, double *E, int tid, int nthreads)
+{
+    const int nb = (int)fl_min64(TG_BS, n - r0);
+    for (int idx = tid; idx < TG_BS * TG_BS; idx += nthreads) {
+        // consecutive threads read consecutive addresses of F in both cases
+        const int a = idx % TG_BS, c = idx / TG_BS;          // F row r0 + a, F column r0 + c
+        double v;
+        if (a < nb && c < nb) v = (a <= c) ? (double)F[(r0 + a) + (r0 + c) * ld] : 0.0;   // R is D's upper triangle
+        else v = (a == c) ? 1.0 : 0.0;
+        if (!transpose) E[c * TS_LD + a] = v;                // E(i=a, j=c) = D(a, c)
+        else E[a * TS_LD + c] = v;                           // E(i=c, j=a) = D(a, c)
+    }
+}
+
+// Substitution on one staged 64 x 64 triangle by one warp.  Lane l holds rows l
+// and l + 32 of the running right-hand side (w0, w1) and returns x in (w0, w1).
+// Upper: j = 63..0, x_j = w_j / E_jj, w_i -= E_ij x_j (i < j).  Lower: j = 0..63,
+// i > j.  x_j is formed as w_j * (1 / E_jj) (at most two roundings) so that the
+// dependent chain per unknown is one multiply, one shuffle and one FMA.
+__device__ __forceinline__ void trsv_diag_warp(const double *E, int lower, int lane, double &w0, double &w1)
+{
+    const double rinv0 = 1.0 / E[lane * TS_LD + lane];
+    const double rinv1 = 1.0 / E[(lane + 32) * TS_LD + lane + 32];
+    double x0 = 0.0, x1 = 0.0;
+    if (!lower) {
+#pragma unroll
+        for (int j = TG_BS - 1; j >= 0; --j) {
+            const double t = (j < 32) ? w0 * rinv0 : w1 * rinv1;
+            const double xj = __shfl_sync(0xffffffffu, t, j & 31);
+            if (lane == (j & 31)) { if (j < 32) x0 = xj; else x1 = xj; }
+            const double *col = E + j * TS_LD;
+            if (lane < j) w0 = fma(-col[lane], xj, w0);
+            if (lane + 32 < j) w1 = fma(-col[lane + 32], xj, w1);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < TG_BS; ++j) {
+            const double t = (j < 32) ? w0 * rinv0 : w1 * rinv1;
+            const double xj = __shfl_sync(0xffffffffu, t, j & 31);
+            if (lane == (j & 31)) { if (j < 32) x0 = xj; else x1 = xj; }
+            const double *col = E + j * TS_LD;
+            if (lane > j) w0 = fma(-col[lane], xj, w0);
+            if (lane + 32 > j) w1 = fma(-col[lane + 32], xj, w1);
+        }
+    }
+    w0 = x0;
+    w1 = x1;
+}
+
+struct TrsvClusterSmem {
+    // [nown][TG_BS * TS_LD] staged diagonal blocks, [nown][TG_BS] w, [nblk * TG_BS] x
+    static __host__ __device__ size_t bytes(int nown, int64_t nblk)
+    {
+        return sizeof(double) * ((size_t)nown * (TG_BS * TS_LD + TG_BS) + (size_t)nblk * TG_BS);
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_trsv_cluster(const T *__restrict__ F, int64_t ld, int64_t n, const double *__restrict__ y,
+               double *__restrict__ x, int transpose, int *flag, const KryScalars *st)
+{
+    if (st && st->done) return;              // same value in every CTA of the cluster
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) double tsm[];
+    __shared__ double red[2][4 * TG_BS];
+    const int rank = (int)cluster.block_rank();
+    const int CS = (int)cluster.num_blocks();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t nblk = (n + TG_BS - 1) / TG_BS;
+    const int nown = (int)((nblk - rank + CS - 1) / CS);
+    const int nown_max = (int)((nblk + CS - 1) / CS);
+    double *Es = tsm;
+    double *ws = Es + (size_t)nown_max * TG_BS * TS_LD;
+    double *xs = ws + (size_t)nown_max * TG_BS;
+    for (int lb = 0; lb < nown; ++lb) {
+        const int64_t r0 = (int64_t)(rank + lb * CS) * TG_BS;
+        trsv_stage_diag(F, ld, n, r0, transpose, Es + (size_t)lb * TG_BS * TS_LD, tid, TC_THREADS);
+        for (int i = tid; i < TG_BS; i += TC_THREADS) ws[lb * TG_BS + i] = (r0 + i < n) ? y[r0 + i] : 0.0;
+    }
+    cluster.sync();                          // every rank resident before the first DSMEM store
+    for (int64_t s = 0; s < nblk; ++s) {
+        const int64_t b = transpose ? s : nblk - 1 - s;
+        const int64_t r0 = b * TG_BS;
+        const int nb = (int)fl_min64(TG_BS, n - r0);
+        if ((int)(b % CS) == rank && warp == 0) {
+            const int lb = (int)(b / CS);
+            double w0 = ws[lb * TG_BS + lane], w1 = ws[lb * TG_BS + lane + 32];
+            trsv_diag_warp(Es + (size_t)lb * TG_BS * TS_LD, transpose, lane, w0, w1);
+            if (!isfinite(w0) || !isfinite(w1)) atomicCAS(flag, 0, FL_DEVERR_NONFINITE);
+            for (int rr = 0; rr < CS; ++rr) {
+                double *dst = cluster.map_shared_rank(xs, rr);
+                dst[r0 + lane] = w0;
+                dst[r0 + lane + 32] = w1;
+            }
+        }
+        cluster.sync();
+        const double *xb = xs + r0;
+        if (!transpose) {
+            // owned rows of blocks b' < b: w_i -= sum_c R(i, r0 + c) x_c; two column halves
+            const int row = tid & (4 * TG_BS - 1), half = tid / (4 * TG_BS);
+            const int lb = row / TG_BS, ri = row % TG_BS;
+            const int64_t bb = (int64_t)rank + (int64_t)lb * CS;
+            double acc = 0.0;
+            if (lb < nown && bb < b) {
+                const T *a = F + (bb * TG_BS + ri) + (r0 + half * 32) * ld;
+                const int c1 = fl_min64(32, nb - half * 32);
+                T v[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) v[c] = (c < c1) ? a[(int64_t)c * ld] : (T)0;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) acc = fma((double)v[c], xb[half * 32 + c], acc);
+            }
+            red[half][row] = acc;
+            __syncthreads();
+            if (tid < 4 * TG_BS && lb < nown && bb < b) ws[row] -= red[0][row] + red[1][row];
+        } else {
+            // owned rows i of blocks b' > b: w_i -= sum_c R(r0 + c, i) x_c; warp per 16 rows,
+            // lanes over c (contiguous in column i of F)
+            const int nrow_own = nown * TG_BS;
+            for (int base = warp * 16; base < nrow_own; base += (TC_THREADS / 32) * 16) {
+                double acc[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int row = base + q;
+                    const int lb = row / TG_BS, ri = row % TG_BS;
+                    const int64_t bb = (int64_t)rank + (int64_t)lb * CS;
+                    const int64_t i = bb * TG_BS + ri;
+                    acc[q] = 0.0;
+                    if (row < nrow_own && bb > b && i < n) {
+                        const T *a = F + r0 + i * ld;
+                        const double v0 = (lane < nb) ? (double)a[lane] : 0.0;
+                        const double v1 = (lane + 32 < nb) ? (double)a[lane + 32] : 0.0;
+                        acc[q] = fma(v0, xb[lane], v1 * xb[lane + 32]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+                if (lane < 16) {
+                    double mine = acc[0];
+#pragma unroll
+                    for (int q = 1; q < 16; ++q) if (lane == q) mine = acc[q];
+                    const int row = base + lane;
+                    const int lb = row / TG_BS;
+                    const int64_t bb = (int64_t)rank + (int64_t)lb * CS;
+                    if (row < nrow_own && bb > b) ws[row] -= mine;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int lb = 0; lb < nown; ++lb) {
+        const int64_t r0 = (int64_t)(rank + lb * CS) * TG_BS;
+        for (int i = tid; i < TG_BS; i += TC_THREADS)
+            if (r0 + i < n) x[r0 + i] = xs[r0 + i];
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(TG_THREADS, 1)
 k_trsv_grid(const T *__restrict__ F, int64_t ld, int64_t n, const double *__restrict__ y,
-            double *__restrict__ x, double *__restrict__ work, int transpose, GridBar *bar,
-            int *flag, const KryScalars *st)
+            double *__restrict__ x, double *__restrict__ work, int transpose, GridBar *bar, int *flag,
+            const KryScalars *st)
 {
     if (st && st->done) return;              // same value in every CTA
-    __shared__ double D[TG_BS][TG_BS + 1];
+    __shared__ double E[TG_BS * TS_LD];
     __shared__ volatile int s_abort;
     const unsigned G = gridDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -205,31 +385,15 @@ k_trsv_grid(const T *__restrict__ F, int64_t ld, int64_t n, const double *__rest
         const int64_t r0 = b * TG_BS, r1 = fl_min64(n, r0 + TG_BS);
         const int nb = (int)(r1 - r0);
         if (blockIdx.x == 0) {
-            for (int idx = threadIdx.x; idx < TG_BS * TG_BS; idx += TG_THREADS) {
-                const int i = idx % TG_BS, j = idx / TG_BS;   // D(i, j) = R(r0 + i, r0 + j)
-                D[i][j] = (i < nb && j < nb) ? (double)F[(r0 + i) + (r0 + j) * ld] : 0.0;
-            }
+            trsv_stage_diag(F, ld, n, r0, transpose, E, threadIdx.x, TG_THREADS);
             __syncthreads();
             if (warp == 0) {
-                double s0 = (lane < nb) ? work[r0 + lane] : 0.0;
-                double s1 = (lane + 32 < nb) ? work[r0 + lane + 32] : 0.0;
-                for (int t = 0; t < nb; ++t) {
-                    const int c = transpose ? t : nb - 1 - t;
-                    const double sc = __shfl_sync(0xffffffffu, c < 32 ? s0 : s1, c & 31);
-                    const double xv = sc / D[c][c];
-                    if (!isfinite(xv)) atomicCAS(flag, 0, FL_DEVERR_NONFINITE);
-                    if (lane == c) s0 = xv;
-                    if (lane + 32 == c) s1 = xv;
-                    if (!transpose) {            // rows above c: s_i -= R(i, c) x_c
-                        if (lane < c) s0 -= D[lane][c] * xv;
-                        if (lane + 32 < c) s1 -= D[lane + 32][c] * xv;
-                    } else {                     // rows below c: s_i -= R(c, i) x_c
-                        if (lane > c && lane < nb) s0 -= D[c][lane] * xv;
-                        if (lane + 32 > c && lane + 32 < nb) s1 -= D[c][lane + 32] * xv;
-                    }
-                }
-                if (lane < nb) x[r0 + lane] = s0;
-                if (lane + 32 < nb) x[r0 + lane + 32] = s1;
+                double w0 = (lane < nb) ? work[r0 + lane] : 0.0;
+                double w1 = (lane + 32 < nb) ? work[r0 + lane + 32] : 0.0;
+                trsv_diag_warp(E, transpose, lane, w0, w1);
+                if (!isfinite(w0) || !isfinite(w1)) atomicCAS(flag, 0, FL_DEVERR_NONFINITE);
+                if (lane < nb) x[r0 + lane] = w0;
+                if (lane + 32 < nb) x[r0 + lane + 32] = w1;
             }
         }
         if (!grid_sync(bar, G, flag, &s_abort)) return;
@@ -238,6 +402,7 @@ k_trsv_grid(const T *__restrict__ F, int64_t ld, int64_t n, const double *__rest
             for (int64_t i = (int64_t)blockIdx.x * TG_THREADS + threadIdx.x; i < r0;
                  i += (int64_t)G * TG_THREADS) {
                 double acc = 0.0;
+#pragma unroll 16
                 for (int c = 0; c < nb; ++c) acc = fma((double)F[i + (r0 + c) * ld], x[r0 + c], acc);
                 work[i] -= acc;
             }
@@ -320,7 +485,8 @@ int kry_dot(fastlsq_ctx *ctx, const double *a, const double *b, int64_t n, const
 }  // namespace
 
 // x = R^{-1} y (transpose 0) or R^{-T} y in FP64 with the factor's R (type T);
-// work: [n] FP64 scratch; skip: optional device flag that makes the call a no-op.
+// work: [n] FP64 scratch (grid variant only); skip: optional device flag that
+// makes the call a no-op.
 template <typename T>
 int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const double *y, double *x,
                  double *work, int transpose, const void *skip_scalars)
@@ -328,10 +494,42 @@ int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const doub
     FL_PROF(ctx, FASTLSQ_K_TRSV);
     int *flag = ctx->d_flag;
     const KryScalars *st = (const KryScalars *)skip_scalars;
+    const int64_t nblk = fl_cdiv(n, TG_BS);
+    const int CS = (int)std::min<int64_t>(TC_MAX_CS, nblk);
+    const int nown_max = (int)fl_cdiv(nblk, CS);
+    const size_t smem = TrsvClusterSmem::bytes(nown_max, nblk);
+    static bool attr_done = false;   // per process; attributes are per function
+    if (nown_max <= 4 && smem + sizeof(double) * 2 * 4 * TG_BS <= (size_t)ctx->max_smem_optin) {
+        if (!attr_done) {
+            cudaError_t e = cudaFuncSetAttribute(k_trsv_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 ctx->max_smem_optin - (int)(sizeof(double) * 2 * 4 * TG_BS));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_trsv_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return fl_cuda(ctx, e, "cudaFuncSetAttribute");
+            attr_done = true;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CS);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CS;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_trsv_cluster<T>, F, ld, n, y, x, transpose, flag, st);
+        if (e != cudaSuccess) return fl_cuda(ctx, e, "cluster triangular solve");
+        return 0;
+    }
     GridBar *bar = (GridBar *)ctx->d_grid_bar;
     void *args[] = {(void *)&F, (void *)&ld, (void *)&n, (void *)&y, (void *)&x, (void *)&work,
                     (void *)&transpose, (void *)&bar, (void *)&flag, (void *)&st};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_trsv_grid<T>, dim3(ctx->num_sms),
+    // a few dozen CTAs: the per-block updates are small and barrier cost grows with the grid
+    const unsigned G = (unsigned)std::min<int64_t>(ctx->num_sms, std::max<int64_t>(8, nblk));
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_trsv_grid<T>, dim3(G),
                                                 dim3(TG_THREADS), args, 0, ctx->stream);
     if (e != cudaSuccess) return fl_cuda(ctx, e, "grid triangular solve");
     return 0;

@@ -1,0 +1,146 @@
+// Inline-PTX helpers for the 5th-generation tensor cores (tcgen05) on sm_103a:
+// TMEM allocation, shared-memory matrix descriptors, the kind::tf32 MMA, commit
+// to an mbarrier, TMEM loads and the async-proxy fences, written from the PTX ISA.
+#pragma once
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---- TMEM -----------------------------------------------------------------
+// One full warp allocates ncols (power of two >= 32) columns; the TMEM address is
+// written to *slot in shared memory.
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 :: "r"(smem_addr(slot)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_after_sync()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+// generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// ---- mbarrier ---------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+// Waits for the phase with the given parity; gives up after max_spins polls and
+// returns false (the caller raises the device flag and skips the dependent work).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long max_spins)
+{
+    uint32_t done = 0;
+    for (long long it = 0; it < max_spins; ++it) {
+        asm volatile("{\n.reg .pred p;\n"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// ---- descriptors ------------------------------------------------------------
+// Shared-memory matrix descriptor, K-major operand in the 128-byte-swizzle
+// canonical layout: rows of 128 bytes (32 fp32), 8-row atoms of 1024 bytes,
+// stride between atoms (SBO) 1024 bytes, base 1024-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void *base)
+{
+    const uint64_t addr = smem_addr(base);
+    uint64_t d = 0;
+    d |= (addr >> 4) & 0x3FFFull;            // start address
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+    d |= (uint64_t)1 << 46;                  // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                  // swizzle: 128 bytes
+    return d;
+}
+
+// Instruction descriptor of kind::tf32: D fp32, A and B tf32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4)                       // D format: f32
+         | (2u << 7)                       // A format: tf32
+         | (2u << 10)                      // B format: tf32
+         | ((uint32_t)(N >> 3) << 17)      // N
+         | ((uint32_t)(M >> 4) << 24);     // M
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile("{\n.reg .pred p;\n"
+                 "setp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+
+// arrive on the mbarrier once all previously issued MMAs of this thread complete
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                 :: "r"(smem_addr(bar)) : "memory");
+}
+
+// 32 lanes x 16 consecutive fp32 columns: thread t of the warp gets lane (base + t)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---- split precision ----------------------------------------------------------
+// x = hi + lo with hi the round-to-nearest tf32 value and lo = x - hi (exact in fp32)
+__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
+{
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(x));
+    hi = __uint_as_float(h);
+    lo = x - hi;
+}
+
+// byte offset of element (row, k) (k < 32 fp32) in a K-major 128B-swizzled tile
+__device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t k)
+{
+    const uint32_t chunk = k >> 2;                       // 16-byte chunk within the 128-byte row
+    return row * 128u + (((chunk ^ (row & 7u)) << 4) | ((k & 3u) << 2));
+}
+
+}  // namespace tc

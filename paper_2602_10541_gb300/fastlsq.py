@@ -58,12 +58,24 @@ class fastlsq_newton_stats(ctypes.Structure):
                 ("step_rel", _dbl * 64), ("alpha", _dbl * 64)]
 
 
+class fastlsq_inverse_instance(ctypes.Structure):
+    _fields_ = [("n_int", _i64), ("n_bc", _i64), ("n_feat", _i64), ("n_sens", _i64),
+                ("x_int", _vp), ("x_bc", _vp), ("W", _vp), ("b", _vp), ("sensors", _vp),
+                ("y_obs", _vp), ("theta", _vp), ("beta", _vp), ("loss", _vp), ("dtheta", _vp)]
+
+
+class fastlsq_inverse_opts(ctypes.Structure):
+    _fields_ = [("prec", _i32), ("refine_iters", _i32), ("refine_tol", _dbl),
+                ("adjoint_iters", _i32), ("adjoint_tol", _dbl), ("mu", _dbl), ("bc_weight", _dbl)]
+
+
 _SIGNATURES = {
     "fastlsq_create": [ctypes.POINTER(_vp), ctypes.c_int, _vp],
     "fastlsq_destroy": [_vp],
     "fastlsq_set_stream": [_vp, _vp],
     "fastlsq_last_error": [_vp],
     "fastlsq_sync": [_vp],
+    "fastlsq_set_option": [_vp, ctypes.c_int, ctypes.c_int],
     "fastlsq_assemble": [_vp, ctypes.c_int, _vp, _i64, ctypes.POINTER(fastlsq_op), _dbl, _vp, _vp,
                          _i64, _dbl, _vp, _i64, _i64],
     "fastlsq_rhs": [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_dbl), _i32, _vp, _i64, _i32,
@@ -85,6 +97,8 @@ _SIGNATURES = {
     "fastlsq_newton": [_vp, ctypes.POINTER(fastlsq_newton_problem), _vp, _vp, _i64, _dbl,
                        ctypes.POINTER(fastlsq_newton_opts), _vp,
                        ctypes.POINTER(fastlsq_newton_stats)],
+    "fastlsq_inverse_batch": [_vp, ctypes.POINTER(fastlsq_inverse_instance), _i32,
+                              ctypes.POINTER(fastlsq_op), _i32, ctypes.POINTER(fastlsq_inverse_opts)],
     "fastlsq_profile_enable": [_vp, ctypes.c_int],
     "fastlsq_profile_read": [_vp, ctypes.c_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)],
 }
@@ -161,6 +175,13 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+OPT_TENSOR_CORE = 0
+
+
+def fastlsq_set_option(ctx, option, value):
+    return ctx.check(ctx.lib.fastlsq_set_option(ctx.handle, int(option), int(value)))
 
 
 def colmajor(n_rows, n_cols, dtype, device, ld=None, zero=False):
@@ -327,3 +348,22 @@ def fastlsq_profile_read(ctx):
         ctx.check(ctx.lib.fastlsq_profile_read(ctx.handle, k, ctypes.byref(n), ctypes.byref(ms)))
         out[name] = (int(n.value), float(ms.value))
     return out
+
+
+def fastlsq_inverse_batch(ctx, instances, op, n_src, prec=PREC_MIXED, refine_iters=64,
+                          refine_tol=1e-13, adjoint_iters=64, adjoint_tol=1e-13, mu=1e-10,
+                          bc_weight=100.0):
+    """instances: sequence of dicts with device tensors x_int, x_bc, W, b, sensors, y_obs,
+    theta and output tensors beta, loss (1), dtheta (4 n_src)."""
+    arr = (fastlsq_inverse_instance * len(instances))()
+    for q, d in enumerate(instances):
+        arr[q] = fastlsq_inverse_instance(
+            d["x_int"].shape[0], d["x_bc"].shape[0], d["W"].shape[0], d["sensors"].shape[0],
+            d["x_int"].data_ptr(), d["x_bc"].data_ptr(), d["W"].data_ptr(), d["b"].data_ptr(),
+            d["sensors"].data_ptr(), d["y_obs"].data_ptr(), d["theta"].data_ptr(),
+            d["beta"].data_ptr(), d["loss"].data_ptr(), d["dtheta"].data_ptr())
+    opts = fastlsq_inverse_opts(prec, refine_iters, float(refine_tol), adjoint_iters,
+                                float(adjoint_tol), float(mu), float(bc_weight))
+    return ctx.check(ctx.lib.fastlsq_inverse_batch(ctx.handle, arr, len(instances),
+                                                   ctypes.byref(op.struct), n_src,
+                                                   ctypes.byref(opts)))

@@ -103,3 +103,37 @@ def rel_l2(a, b) -> float:
     a = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else np.asarray(a)
     b = b.detach().cpu().numpy() if isinstance(b, torch.Tensor) else np.asarray(b)
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def main(argv=None):
+    """Command line: run a few linear solves of a named workload and print the error
+    of the last one on the test set, e.g. as the program under a profiler:
+    ``python -m paper_2602_10541_gb300.pipeline helmholtz2d --prec mixed --steps 2``."""
+    import argparse
+
+    from . import workloads as wl
+
+    ap = argparse.ArgumentParser(prog="python -m paper_2602_10541_gb300.pipeline")
+    ap.add_argument("workload", choices=["poisson1d", "helmholtz2d", "poisson5d"])
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--refine", type=int, default=2)
+    ap.add_argument("--refine-mode", choices=["classical", "cgls"], default="classical")
+    ap.add_argument("--tensor-core", action="store_true", help="tcgen05 trailing updates (MIXED)")
+    a = ap.parse_args(argv)
+    ctx = fl.Context(0)
+    if a.tensor_core:
+        fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
+    dp = upload(wl.CONFIGS[a.workload]())
+    s = LinearSolver(ctx, dp, prec=fl.PREC_MIXED if a.prec == "mixed" else fl.PREC_FP64,
+                     max_refine=a.refine,
+                     refine_mode=fl.REFINE_CGLS if a.refine_mode == "cgls" else fl.REFINE_CLASSICAL)
+    for _ in range(a.steps):
+        s.step()
+    torch.cuda.synchronize()
+    print(f"{a.workload} {a.prec}: rel L2 error vs exact on the test set "
+          f"{rel_l2(s.u_test(), s.u_exact_test()):.3e}")
+
+
+if __name__ == "__main__":
+    main()

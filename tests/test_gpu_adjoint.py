@@ -141,3 +141,34 @@ def test_backward_pieces_match_oracle(ctx):
     fl.fastlsq_eval_adjoint(ctx, _t(w.sensors), _t(w.W), _t(w.b), w.scale, _t(g), gbeta)
     np.testing.assert_allclose(gbeta.cpu().numpy(), ref["Hs"].T @ g, rtol=1e-12, atol=1e-12)
     fac.close()
+
+
+def _device_instance(w, y, theta):
+    n_src = len(theta) // 4
+    return dict(x_int=_t(w.x_int), x_bc=_t(w.x_bc), W=_t(w.W), b=_t(w.b), sensors=_t(w.sensors),
+                y_obs=_t(y), theta=_t(theta),
+                beta=torch.zeros(w.n_feat, dtype=torch.float64, device=DEV),
+                loss=torch.zeros(1, dtype=torch.float64, device=DEV),
+                dtheta=torch.zeros(4 * n_src, dtype=torch.float64, device=DEV))
+
+
+@pytest.mark.parametrize("prec", [fl.PREC_FP64, fl.PREC_MIXED])
+def test_inverse_batch_matches_oracle(ctx, prec):
+    """Uneven instances through the batched entry point: loss and dL/dtheta of every
+    instance against the oracle's forward map and adjoint."""
+    mu = 1e-10
+    shapes = [(600, 160), (401, 97), (800, 210)]
+    cases, dev = [], []
+    for q, (ni, nf) in enumerate(shapes):
+        w = wl.inverse_instance(q, n_int=ni, n_feat=nf)
+        w.W = w.W * (6.0 / 8.0)
+        y = _oracle_pieces(w, w.params, np.zeros(64), mu)["u_s"] + w.noise
+        ref = _oracle_pieces(w, w.theta0, y, mu)
+        cases.append(ref)
+        dev.append(_device_instance(w, y, w.theta0))
+    fl.fastlsq_inverse_batch(ctx, dev, fl.Op([[2, 0], [0, 2]], [-1.0, -1.0]), 4, prec=prec, mu=mu)
+    torch.cuda.synchronize()
+    for ref, d in zip(cases, dev):
+        assert abs(d["loss"].item() - ref["loss"]) <= 1e-6 * ref["loss"]
+        g = d["dtheta"].cpu().numpy()
+        assert np.abs(g - ref["dtheta"]).max() <= 2e-5 * np.abs(ref["dtheta"]).max(), (g, ref["dtheta"])

@@ -219,3 +219,24 @@ def test_helmholtz2d_full_size(ctx):
     assert pl.rel_l2(umx, ue) <= 1e-6
     st = smx.stats
     assert st.resid_norm[2] <= st.resid_norm[0]
+
+
+@pytest.mark.parametrize("m,n", [(2200, 2050), (4200, 4096), (4400, 4200)])
+def test_trsv_large_and_ragged(ctx, m, n):
+    """The triangular solves at sizes that take the cluster kernel with 1 to 4 owned
+    diagonal blocks per CTA (n <= 4096) and the grid kernel (n > 4096), against a
+    substitution in FP64 on the exported R (scipy's LAPACK dtrtrs)."""
+    sla = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((m, n))
+    _, fac, _ = fl.fastlsq_lstsq(ctx, fl.PREC_FP64, _cm(A, torch.float64), m, 0.0, None, None, keep=True)
+    R = torch.zeros((n, n), dtype=torch.float64, device=DEV)
+    fl.fastlsq_factor_get_r(ctx, fac, R)
+    Rg = R.cpu().numpy().T
+    y = rng.standard_normal(n)
+    for tr in (False, True):
+        x = torch.empty(n, dtype=torch.float64, device=DEV)
+        fl.fastlsq_factor_trsv(ctx, fac, _t1(y), x, transpose=tr)
+        ref = sla.solve_triangular(Rg, y, trans=1 if tr else 0, lower=False)
+        np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=1e-9, atol=1e-11 * np.abs(ref).max())
+    fl.fastlsq_factor_destroy(ctx, fac)
