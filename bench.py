@@ -195,6 +195,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--refine", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tensor-core", type=int, default=0, choices=[0, 1],
+                    help="1: trailing QR updates on tcgen05 (TF32x3), 0: SIMT FP32")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -215,6 +217,7 @@ def main():
     if not _build.up_to_date():
         _build.build()
     ctx = fl.Context(local)
+    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, args.tensor_core)
     stream = torch.cuda.current_stream(local)
 
     # each rank solves its own instance (replicas: the solve does not shard)

@@ -255,6 +255,10 @@ extern "C" int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value)
         ctx->use_tensor_core = value ? 1 : 0;
         return 0;
     }
+    if (option == FASTLSQ_OPT_REGISTER_PANEL) {
+        ctx->panel_reg = value ? 1 : 0;
+        return 0;
+    }
     return fl_fail(ctx, FASTLSQ_ERR_INVALID, "unknown option %d", option);
 }
 

@@ -66,6 +66,7 @@ struct fastlsq_ctx {
     int *d_flag = nullptr;          // device error flag (int)
     void *d_grid_bar = nullptr;     // grid barrier state (count, generation) of this context
     int use_tensor_core = 0;        // tcgen05 trailing updates for the MIXED path
+    int panel_reg = 1;              // register-resident FP32 panel (width 32) where it fits
     // Cody-Waite split of 2 pi for the FP32 argument reduction (host-derived)
     float cw2pi[3] = {0.f, 0.f, 0.f};
     fl_prof_state prof;

@@ -552,9 +552,10 @@ __global__ void k_copy_in(const TA *__restrict__ A, int64_t ldA, int64_t m, int6
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t c = blockIdx.y;
-    if (i >= m_aug) return;
+    if (i >= ld) return;
     T v;
-    if (c < n) v = (i < m) ? (T)A[i + c * ldA] : ((i - m == c) ? (T)sqrt_mu : T(0));
+    if (i >= m_aug) v = T(0);          // padding rows stay zero through the factorisation
+    else if (c < n) v = (i < m) ? (T)A[i + c * ldA] : ((i - m == c) ? (T)sqrt_mu : T(0));
     else v = (i < m) ? (T)rhs[i + (c - n) * ld_rhs] : T(0);
     F[i + c * ld] = v;
 }
@@ -763,7 +764,14 @@ static int factor_t(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n
     for (int64_t k = 0; k < n; k += NB) {
         const int ncols = (int)std::min<int64_t>(NB, n - k);
         T *Tblk = Tall + (k / NB) * NB * NB;
-        FL_TRY((launch_panel<T, NB>(ctx, F, ld, k, m_aug, ncols, tau + k, Tblk)));
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value && NB == 32) {
+            if (ctx->panel_reg && fl_panel_reg_fits(m_aug - k)) {
+                FL_TRY(fl_panel_reg_f32(ctx, F, ld, k, m_aug, ncols, tau + k, Tblk));
+                done = true;
+            }
+        }
+        if (!done) FL_TRY((launch_panel<T, NB>(ctx, F, ld, k, m_aug, ncols, tau + k, Tblk)));
         const int64_t nct = ntot - (k + ncols);
         if constexpr (std::is_same<T, float>::value) {
             if (use_tc) {
@@ -825,7 +833,7 @@ template <typename TA, typename T>
 int fl_copy_in(fastlsq_ctx *ctx, const TA *A, int64_t ldA, int64_t m, int64_t n, double mu,
                int64_t m_aug, const double *rhs, int64_t ld_rhs, int nrhs, T *F, int64_t ld)
 {
-    dim3 grid((unsigned)fl_cdiv(m_aug, 256), (unsigned)(n + nrhs));
+    dim3 grid((unsigned)fl_cdiv(ld, 256), (unsigned)(n + nrhs));
     FL_PROF(ctx, FASTLSQ_K_COPY_IN);
     k_copy_in<TA, T><<<grid, 256, 0, ctx->stream>>>(A, ldA, m, n, mu > 0 ? sqrt(mu) : 0.0, m_aug,
                                                     rhs, ld_rhs, nrhs, F, ld);

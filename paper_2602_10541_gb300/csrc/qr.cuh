@@ -27,6 +27,11 @@ template <typename T>
 int fl_from_f64(fastlsq_ctx *ctx, const double *src, int64_t n, int64_t n_total, T *dst,
                 const int *skip = nullptr);
 
+// Register-resident FP32 panel of width 32 (panel_reg.cu); fits: rows per warp <= 24.
+bool fl_panel_reg_fits(int64_t mp);
+int fl_panel_reg_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
+                     float *tau, float *Tblk);
+
 // tcgen05 (TF32x3 split precision) trailing update; tc_update.cu.  Returns a
 // negative status when the tensor-core path cannot handle the shape.
 int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,

@@ -178,6 +178,7 @@ class Context:
 
 
 OPT_TENSOR_CORE = 0
+OPT_REGISTER_PANEL = 1
 
 
 def fastlsq_set_option(ctx, option, value):

@@ -240,3 +240,30 @@ def test_trsv_large_and_ragged(ctx, m, n):
         ref = sla.solve_triangular(Rg, y, trans=1 if tr else 0, lower=False)
         np.testing.assert_allclose(x.cpu().numpy(), ref, rtol=1e-9, atol=1e-11 * np.abs(ref).max())
     fl.fastlsq_factor_destroy(ctx, fac)
+
+
+@pytest.mark.parametrize("m,n", [(700, 130), (300, 40), (9000, 96), (12000, 64), (13000, 40)])
+def test_register_panel_matches_oracle_and_shared_memory_panel(ctx, m, n):
+    """The FP32 panel with the slice in registers (1 to 24 rows per warp, 1 to 16
+    CTAs; 13000 rows take the shared-memory kernel) against the oracle's Householder
+    R and the shared-memory panel kernel."""
+    rng = np.random.default_rng(3 * m + n)
+    A = rng.standard_normal((m, n))
+    Rs = {}
+    for reg in (1, 0):
+        fl.fastlsq_set_option(ctx, fl.OPT_REGISTER_PANEL, reg)
+        try:
+            _, fac, st = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, 0.0, None, None,
+                                          keep=True, stats=True)
+        finally:
+            fl.fastlsq_set_option(ctx, fl.OPT_REGISTER_PANEL, 1)
+        assert st.nb == 32
+        R = torch.zeros((n, n), dtype=torch.float64, device=DEV)
+        fl.fastlsq_factor_get_r(ctx, fac, R)
+        fl.fastlsq_factor_destroy(ctx, fac)
+        Rs[reg] = R.cpu().numpy().T
+    packed, _ = oracle.qr(A)
+    Ro = np.triu(packed[:n])
+    scale = np.abs(Ro).max()
+    assert np.abs(Rs[1] - Ro).max() <= 2e-5 * scale
+    assert np.abs(Rs[1] - Rs[0]).max() <= 2e-5 * scale
