@@ -197,6 +197,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tensor-core", type=int, default=0, choices=[0, 1],
                     help="1: trailing QR updates on tcgen05 (TF32x3), 0: SIMT FP32")
+    ap.add_argument("--trsv-fp32", type=int, default=1, choices=[0, 1],
+                    help="1: FP32 substitution in the triangular solves of classical refinement")
+    ap.add_argument("--lookahead", type=int, default=1, choices=[0, 1],
+                    help="1: factor the next panel on a second stream during the trailing update")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -218,6 +222,8 @@ def main():
         _build.build()
     ctx = fl.Context(local)
     fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, args.tensor_core)
+    fl.fastlsq_set_option(ctx, fl.OPT_TRSV_FP32, args.trsv_fp32)
+    fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, args.lookahead)
     stream = torch.cuda.current_stream(local)
 
     # each rank solves its own instance (replicas: the solve does not shard)

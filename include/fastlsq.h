@@ -368,9 +368,18 @@ FASTLSQ_API int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p
 /* Context options for fastlsq_set_option. */
 typedef enum {
     FASTLSQ_OPT_TENSOR_CORE = 0,  /* 1: MIXED trailing updates on tcgen05 (TF32x3), 0: SIMT FP32 */
-    FASTLSQ_OPT_REGISTER_PANEL = 1 /* 1 (default): FP32 panels of width 32 factor with the
+    FASTLSQ_OPT_REGISTER_PANEL = 1, /* 1 (default): FP32 panels of width 32 factor with the
                                       slice in registers where rows per warp <= 24;
                                       0: the shared-memory panel kernel everywhere */
+    FASTLSQ_OPT_LOOKAHEAD = 2,     /* 1 (default): panel p+1 is factored on the caller's
+                                      stream while the rest of panel p's trailing update runs
+                                      on a second, low-priority stream of the context (joined
+                                      back into the caller's stream before the next panel's
+                                      update); 0: everything on the caller's stream */
+    FASTLSQ_OPT_TRSV_FP32 = 3      /* 1 (default): the triangular solves of classical
+                                      refinement (MIXED) substitute in FP32 arithmetic
+                                      (backward stable like the FP32 factor); 0: FP64
+                                      arithmetic.  CGLS and the adjoint always use FP64. */
 } fastlsq_option;
 
 /* Set a context option (see fastlsq_option).  Returns 0 or -1 for an unknown option. */

@@ -148,8 +148,19 @@ extern "C" int fastlsq_create(fastlsq_ctx **out, int device, void *stream)
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
         }
     }
+    if (e == cudaSuccess) {
+        // low-priority stream for the trailing updates that run beside a look-ahead panel
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->aux_stream, cudaStreamNonBlocking, lo);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         int rc = (e == cudaErrorMemoryAllocation) ? FASTLSQ_ERR_NOMEM : FASTLSQ_ERR_CUDA;
+        if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+        if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+        if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
         if (ctx->d_flag) cudaFree(ctx->d_flag);
         if (ctx->d_grid_bar) cudaFree(ctx->d_grid_bar);
         delete ctx;
@@ -192,6 +203,7 @@ fl_prof_scope::~fl_prof_scope()
 static void prof_collect(fastlsq_ctx *ctx)
 {
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->aux_stream) cudaStreamSynchronize(ctx->aux_stream);
     for (int k = 0; k < FASTLSQ_K_COUNT; ++k) {
         for (size_t i = 0; i + 1 < ctx->prof.used[k]; i += 2) {
             float ms = 0.f;
@@ -231,6 +243,10 @@ extern "C" int fastlsq_destroy(fastlsq_ctx *ctx)
     if (!ctx) return 0;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->aux_stream) cudaStreamSynchronize(ctx->aux_stream);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
     for (int k = 0; k < FASTLSQ_K_COUNT; ++k)
         for (cudaEvent_t e : ctx->prof.ev[k]) cudaEventDestroy(e);
     for (int s = 0; s < FL_WS_COUNT; ++s)
@@ -257,6 +273,14 @@ extern "C" int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value)
     }
     if (option == FASTLSQ_OPT_REGISTER_PANEL) {
         ctx->panel_reg = value ? 1 : 0;
+        return 0;
+    }
+    if (option == FASTLSQ_OPT_LOOKAHEAD) {
+        ctx->lookahead = value ? 1 : 0;
+        return 0;
+    }
+    if (option == FASTLSQ_OPT_TRSV_FP32) {
+        ctx->trsv32 = value ? 1 : 0;
         return 0;
     }
     return fl_fail(ctx, FASTLSQ_ERR_INVALID, "unknown option %d", option);
@@ -384,7 +408,10 @@ static int solve_one(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, i
         FL_TRY(fl_apply_q<T>(ctx, F, f->ld, m_aug, n, f->nb, (const T *)f->T, y, 1));
     }
     FL_TRY(fl_to_f64<T>(ctx, y, n, y64, 0));
-    FL_TRY(fl_trsv_grid<T>(ctx, F, f->ld, n, y64, beta64, work, 0));
+    // FP32 substitution (backward stable, like the FP32 factor itself) is an option for
+    // classical refinement; CGLS needs R^{-1} as a fixed linear operator: FP64
+    const int a32 = (mode == FASTLSQ_REFINE_CLASSICAL) ? ctx->trsv32 : 0;
+    FL_TRY(fl_trsv_grid<T>(ctx, F, f->ld, n, y64, beta64, work, 0, nullptr, a32));
     if (mode == FASTLSQ_REFINE_CGLS) {
         if (max_refine > 0) return fl_refine_cgls(ctx, f, rhs64, beta64, max_refine, tol, norms_dev);
         return 0;
@@ -396,7 +423,7 @@ static int solve_one(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, i
                               norms_dev ? norms_dev + it : nullptr));
         FL_TRY(fl_apply_q<T>(ctx, F, f->ld, m_aug, n, f->nb, (const T *)f->T, y, 1));
         FL_TRY(fl_to_f64<T>(ctx, y, n, y64, 0));
-        FL_TRY(fl_trsv_grid<T>(ctx, F, f->ld, n, y64, dx64, work, 0));
+        FL_TRY(fl_trsv_grid<T>(ctx, F, f->ld, n, y64, dx64, work, 0, nullptr, a32));
         FL_TRY(fl_to_f64<double>(ctx, dx64, n, beta64, 1));
     }
     if (norms_dev && f->A_refine) {

@@ -44,6 +44,8 @@ enum fl_slot {
     FL_WS_KRYLOV,          // Krylov refinement vectors and scalars
     FL_WS_APPLYQ,          // Q application partial sums
     FL_WS_SOLVE64,         // FP64 vectors of the triangular solves
+    FL_WS_ZBUF,            // Z = T^T V^T C of the current trailing update
+    FL_WS_COUNTERS,        // completion counters of the trailing-update column tiles
     FL_WS_COUNT
 };
 
@@ -67,6 +69,10 @@ struct fastlsq_ctx {
     void *d_grid_bar = nullptr;     // grid barrier state (count, generation) of this context
     int use_tensor_core = 0;        // tcgen05 trailing updates for the MIXED path
     int panel_reg = 1;              // register-resident FP32 panel (width 32) where it fits
+    int lookahead = 1;              // panel p+1 beside the rest of panel p's update (on aux_stream)
+    int trsv32 = 1;                 // FP32 arithmetic in the triangular solves of classical refinement
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // Cody-Waite split of 2 pi for the FP32 argument reduction (host-derived)
     float cw2pi[3] = {0.f, 0.f, 0.f};
     fl_prof_state prof;

@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "qr.cuh"
+#include "tc_common.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -30,7 +31,30 @@ namespace {
 constexpr int PR_NB = 32;
 constexpr int PR_THREADS = 1024;
 constexpr int PR_CL_MAX = 16;
-constexpr int PR_XLD = 33;                   // padded stride of the exchange buffer
+constexpr int PR_XLD = 36;                   // row stride of the exchange buffer (16-byte rows)
+constexpr long long PR_SPIN = 2000000000ll;  // SM cycles (about a second) before an exchange wait gives up
+
+// shared::cluster address of the same shared-memory object in CTA `rank`
+__device__ __forceinline__ uint32_t map_rank(const void *p, int rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(tc::smem_addr(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                 :: "r"(tc::smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// bulk copy of `bytes` (multiple of 16) from this CTA's shared memory into another
+// CTA's, counted down on the receiver's barrier
+__device__ __forceinline__ void bulk_to_rank(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 :: "r"(dst), "r"(tc::smem_addr(src)), "r"(bytes), "r"(bar) : "memory");
+}
 
 struct PrLayout {
     // offsets in floats
@@ -56,12 +80,14 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
     float *S = psm;
     float *red = psm + PrLayout::red(rpc);
     float *xbuf = psm + PrLayout::xbuf(rpc);
-    float *dsum = psm + PrLayout::dsum(rpc);
-    float *sc = psm + PrLayout::sc(rpc);
     float *diag = psm + PrLayout::diag(rpc);
     float *Tm = psm + PrLayout::Tm(rpc);
     float *G = psm + PrLayout::G(rpc);
     float *tauv = psm + PrLayout::tauv(rpc);
+    __shared__ uint64_t xbar[2];
+    __shared__ __align__(16) float part[2][32];      // this CTA's partials, by column parity
+    __shared__ __align__(16) float pdiag[2][32];     // rank 0: the diagonal row, by parity
+    __shared__ volatile int s_abort;
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -92,58 +118,68 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
         if (g0 + r > 0) acc = fmaf(a0, p[r], acc);
     }
 
+    // one exchange barrier per parity; per phase one local arrival (with the expected
+    // byte count) plus the byte counts of the CL x 32 partials and rank 0's diagonal row
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&xbar[0], 1);
+        tc::mbar_init(&xbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (threadIdx.x == 0) s_abort = 0;
+    cluster.sync();                                  // barriers ready before any remote signal
+    const uint32_t xbytes = (uint32_t)(CL + 1) * 32u * (uint32_t)sizeof(float);
+
     for (int j = 0; j <= ncols; ++j) {
         const int par = j & 1;
         float *xb = xbuf + par * (PR_CL_MAX + 1) * PR_XLD;
+        if (threadIdx.x == 0) arrive_expect_tx(&xbar[par], xbytes);
         red[warp * 33 + lane] = acc;
         __syncthreads();
+        if (s_abort) break;                          // uniform: read after the barrier
         {
-            // warp c reduces column c over the 32 warps and sends the CTA's partial
+            // warp c reduces column c over the 32 warps; the CTA's 32 partials (and rank
+            // 0's diagonal row) then go to every rank as one 128-byte bulk copy each,
+            // counted down on the receiver's barrier
             const int c = warp;
             float s = red[lane * 33 + c];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-            s = __shfl_sync(FULL, s, 0);
-            if (lane < CL) {
-                float *rb = cluster.map_shared_rank(xb, lane);
-                rb[rank * PR_XLD + c] = s;
-                if (rank == 0) rb[PR_CL_MAX * PR_XLD + c] = (j < ncols) ? diag[c] : 0.f;
-            }
-        }
-        cluster.sync();
-        {
-            // warp c sums the CL partials of column c (fixed order, same on every rank)
-            const int c = warp;
-            float v = (lane < CL) ? xb[lane * PR_XLD + c] : 0.f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-            v = __shfl_sync(FULL, v, 0);
             if (lane == 0) {
-                dsum[c] = v;
-                if (rank == 0 && j >= 1 && c < j - 1) G[c * 33 + (j - 1)] = v;
-                if (c == j && j < ncols) {
-                    // reflector of column j: v = 1 at row j, a(j+1:)/(a_jj - beta) below
-                    const float ss = v, ajj = xb[PR_CL_MAX * PR_XLD + j];
-                    float beta = ajj, tj = 0.f, inv = 0.f;
-                    if (!isfinite(ss) || !isfinite(ajj)) {
-                        atomicCAS(flag, 0, FL_DEVERR_NONFINITE);
-                    } else if (ss > 0.f) {
-                        const float nrm = sqrtf(ajj * ajj + ss);
-                        beta = (ajj >= 0.f) ? -nrm : nrm;
-                        tj = (beta - ajj) / beta;
-                        inv = 1.f / (ajj - beta);
-                    }
-                    sc[0] = beta;
-                    sc[1] = tj;
-                    sc[2] = inv;
-                    if (rank == 0) tauv[j] = tj;
-                }
+                part[par][c] = s;
+                if (rank == 0) pdiag[par][c] = (j < ncols) ? diag[c] : 0.f;
+                tc::fence_proxy_async_smem();        // visible to the bulk copies below
             }
         }
-        if (j == ncols) break;
         __syncthreads();
-        const float beta = sc[0], tj = sc[1], inv = sc[2];
-        const float wl = (l > j) ? tj * (xb[PR_CL_MAX * PR_XLD + l] + inv * dsum[l]) : 0.f;
+        if (warp == 0 && lane < CL) {
+            const uint32_t rbar = map_rank(&xbar[par], lane);
+            bulk_to_rank(map_rank(xb + rank * PR_XLD, lane), part[par], 32 * sizeof(float), rbar);
+            if (rank == 0) bulk_to_rank(map_rank(xb + PR_CL_MAX * PR_XLD, lane), pdiag[par], 32 * sizeof(float), rbar);
+        }
+        if (!tc::mbar_wait(&xbar[par], (uint32_t)(j >> 1) & 1u, PR_SPIN)) {
+            s_abort = 1;                             // every warp leaves at the next barrier
+            atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
+        }
+        // every warp sums the CL partials of every column in the same order, so all
+        // warps of all ranks hold bit-identical sums and reflector scalars
+        float dl = 0.f;
+        for (int q = 0; q < CL; ++q) dl += xb[q * PR_XLD + l];
+        if (rank == 0 && warp == 0 && j >= 1 && l < j - 1) G[l * 33 + (j - 1)] = dl;
+        if (j == ncols) break;
+        const float ss = __shfl_sync(FULL, dl, j);
+        const float ajj = xb[PR_CL_MAX * PR_XLD + j];
+        float beta = ajj, tj = 0.f, inv = 0.f;
+        if (!isfinite(ss) || !isfinite(ajj)) {
+            if (lane == 0) atomicCAS(flag, 0, FL_DEVERR_NONFINITE);
+        } else if (ss > 0.f) {
+            // reflector of column j: v = 1 at row j, a(j+1:)/(a_jj - beta) below
+            const float nrm = sqrtf(ajj * ajj + ss);
+            beta = (ajj >= 0.f) ? -nrm : nrm;
+            tj = (beta - ajj) / beta;
+            inv = 1.f / (ajj - beta);
+        }
+        if (rank == 0 && warp == 0 && lane == 0) tauv[j] = tj;
+        const float wl = (l > j) ? tj * (xb[PR_CL_MAX * PR_XLD + l] + inv * dl) : 0.f;
         const int jn = (j + 1) & 31;
         acc = 0.f;
         if (g0 >= j + 2) {

@@ -20,6 +20,7 @@
 #include "common.cuh"
 #include "gridsync.cuh"
 #include "qr.cuh"
+#include "trail_z.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -247,71 +248,126 @@ __device__ __forceinline__ T v_at(const T *__restrict__ F, int64_t ld, int64_t k
     return F[(k + i) + (k + l) * ld];
 }
 
-// Y partials: Ypart[s][l][c] = sum over rows of split s of V(i,l) C(i,c) for the
-// trailing columns c (global column k + ncols + c).  CTA tile: all NB rows of Y
-// x TY_COLS columns; rows streamed in chunks of TY_ROWS through shared memory
-// stored row-major ([row][l], [row][c]) so each thread reads its 4 l-values and 4
-// c-values as vectors: 16 FMAs per two shared-memory loads.
+// Trailing update C -= V (T^T (V^T C)) of one panel (C: the columns right of the
+// panel, right-hand sides included), in two kernels:
+//  * k_trail_y: Y partials over row splits, Ypart[s][l][c] = sum over the rows of
+//    split s of V(i,l) C(i,c); CTA tile = all NB rows of Y x TY_COLS columns, rows
+//    streamed in chunks of TY_ROWS.  Chunks are read as 4-row vectors along the
+//    columns of F (coalesced) into registers one chunk ahead of the one being
+//    multiplied from shared memory.  The last CTA of a column tile forms Z = T^T Y.
+//  * k_trail_c: C -= V Z on TC_ROWS x TC_COLS tiles; the tile of C is requested
+//    first so its loads overlap the staging of V and Z.
+// Rows past the end of the panel (up to the factor's 4-row padding) are zero in F,
+// so 4-row vectors never need masking below row m_aug.
 constexpr int TY_COLS = 128;
 constexpr int TY_ROWS = 32;
+constexpr int TY_LDS = TY_ROWS + 4;     // padded stride of a staged column (keeps 16-byte alignment)
+constexpr int TY_THREADS = 256;
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4; };
 
-template <typename T, int NB>
-__global__ void __launch_bounds__(256)
-k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct,
-          int64_t rows_per_split, T *__restrict__ Ypart)
+template <typename T>
+__device__ __forceinline__ typename Vec4<T>::type v4_zero()
+{
+    typename Vec4<T>::type z;
+    z.x = z.y = z.z = z.w = T(0);
+    return z;
+}
+
+// V(i..i+3, l) as a vector, with the unit-lower-trapezoid mask on the top rows
+template <typename T>
+__device__ __forceinline__ typename Vec4<T>::type v_quad(const T *__restrict__ F, int64_t ld, int64_t k,
+                                                          int64_t i, int l, int ncols)
 {
     using V4 = typename Vec4<T>::type;
-    constexpr int LG = NB / 4;                 // l-groups of 4
-    constexpr int CG = 256 / LG;               // c-groups
-    constexpr int CPT = TY_COLS / CG;          // columns per thread (4 for NB = 32)
-    static_assert(CPT == 4 || CPT == 2 || CPT == 1, "tile");
-    __shared__ __align__(16) T sV[TY_ROWS][NB];
-    __shared__ __align__(16) T sC[TY_ROWS][TY_COLS + 4];
+    if (l >= ncols) return v4_zero<T>();
+    V4 v = *reinterpret_cast<const V4 *>(F + (k + i) + (k + l) * ld);
+    if (i <= l) {                       // rows at or above the diagonal of column l
+        v.x = (i + 0 < l) ? T(0) : (i + 0 == l ? T(1) : v.x);
+        v.y = (i + 1 < l) ? T(0) : (i + 1 == l ? T(1) : v.y);
+        v.z = (i + 2 < l) ? T(0) : (i + 2 == l ? T(1) : v.z);
+        v.w = (i + 3 < l) ? T(0) : (i + 3 == l ? T(1) : v.w);
+    }
+    return v;
+}
+
+template <typename T, int NB>
+struct TrailYSmem {
+    static constexpr size_t stage = sizeof(T) * (size_t)(TY_COLS + NB) * TY_LDS;
+    static constexpr size_t zscr = sizeof(T) * (size_t)(NB * TY_COLS + NB * NB);
+    static constexpr size_t bytes = stage > zscr ? stage : zscr;
+};
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(TY_THREADS)
+k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct, int64_t coff,
+          int64_t rows_per_split, T *__restrict__ Ypart, T *__restrict__ Z, const T *__restrict__ Tblk,
+          int *__restrict__ counters)
+{
+    using V4 = typename Vec4<T>::type;
+    constexpr int LG = NB / 4;                       // l-groups of 4
+    constexpr int CG = TY_THREADS / LG;              // c-groups
+    constexpr int CPT = TY_COLS / CG;                // columns per thread
+    constexpr int QPC = TY_ROWS / 4;                 // 4-row quads per chunk column
+    constexpr int CQ = TY_COLS * QPC / TY_THREADS;   // C quads per thread per chunk
+    static_assert(CPT >= 1 && CQ >= 1, "tile");
+    extern __shared__ __align__(16) unsigned char ty_raw[];
+    T *sC = reinterpret_cast<T *>(ty_raw);           // [TY_COLS][TY_LDS]
+    T *sV = sC + TY_COLS * TY_LDS;                   // [NB][TY_LDS]
     const int64_t mp = m - k;
     const int64_t cbase = (int64_t)blockIdx.x * TY_COLS;
     const int64_t rs0 = (int64_t)blockIdx.y * rows_per_split;
     const int64_t rs1 = fl_min64(mp, rs0 + rows_per_split);
-    const int lg = threadIdx.x % LG, cg = threadIdx.x / LG;
+    const int tid = threadIdx.x;
+    const int lq = tid % QPC;                         // loader: quad within the chunk
+    const int lc = tid / QPC;                         // loader: column (plus pass * 32)
+    V4 rc[CQ], rv;
+
+    auto load = [&](int64_t r0) {
+        const int64_t i = r0 + 4 * lq;
+#pragma unroll
+        for (int ps = 0; ps < CQ; ++ps) {
+            const int64_t c = cbase + lc + ps * (TY_THREADS / QPC);
+            rc[ps] = (i < rs1 && c < nct) ? *reinterpret_cast<const V4 *>(F + (k + i) + (k + ncols + coff + c) * ld)
+                                         : v4_zero<T>();
+        }
+        rv = (lc < NB && i < rs1) ? v_quad(F, ld, k, i, lc, ncols) : v4_zero<T>();
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int ps = 0; ps < CQ; ++ps)
+            *reinterpret_cast<V4 *>(sC + (lc + ps * (TY_THREADS / QPC)) * TY_LDS + 4 * lq) = rc[ps];
+        if (lc < NB) *reinterpret_cast<V4 *>(sV + lc * TY_LDS + 4 * lq) = rv;
+    };
+
+    const int lg = tid % LG, cg = tid / LG;
     T acc[4][CPT];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < CPT; ++b) acc[a][b] = T(0);
-    const int lr = threadIdx.x & 31, lq = threadIdx.x >> 5;   // loader: row, group
+
+    if (rs0 < rs1) load(rs0);
     for (int64_t r0 = rs0; r0 < rs1; r0 += TY_ROWS) {
+        store();
         __syncthreads();
-        const int64_t i = r0 + lr;
-        const bool iv = i < rs1;
-        for (int l0 = lq * 4; l0 < NB; l0 += 32) {
+        if (r0 + TY_ROWS < rs1) load(r0 + TY_ROWS);          // next chunk in flight
 #pragma unroll
-            for (int u = 0; u < 4; ++u) sV[lr][l0 + u] = iv ? v_at(F, ld, k, i, l0 + u, ncols) : T(0);
-        }
-        for (int c0 = lq * 4; c0 < TY_COLS; c0 += 32) {
+        for (int rg = 0; rg < QPC; ++rg) {
+            V4 v[4], cv[CPT];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t c = cbase + c0 + u;
-                sC[lr][c0 + u] = (iv && c < nct) ? F[(k + i) + (k + ncols + c) * ld] : T(0);
-            }
+            for (int a = 0; a < 4; ++a) v[a] = *reinterpret_cast<const V4 *>(sV + (lg * 4 + a) * TY_LDS + 4 * rg);
+#pragma unroll
+            for (int b = 0; b < CPT; ++b) cv[b] = *reinterpret_cast<const V4 *>(sC + (cg * CPT + b) * TY_LDS + 4 * rg);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < CPT; ++b)
+                    acc[a][b] += v[a].x * cv[b].x + v[a].y * cv[b].y + v[a].z * cv[b].z + v[a].w * cv[b].w;
         }
         __syncthreads();
-#pragma unroll 4
-        for (int rr = 0; rr < TY_ROWS; ++rr) {
-            const V4 v = *reinterpret_cast<const V4 *>(&sV[rr][lg * 4]);
-            T cv[CPT];
-#pragma unroll
-            for (int b = 0; b < CPT; ++b) cv[b] = sC[rr][cg * CPT + b];
-#pragma unroll
-            for (int b = 0; b < CPT; ++b) {
-                acc[0][b] += v.x * cv[b];
-                acc[1][b] += v.y * cv[b];
-                acc[2][b] += v.z * cv[b];
-                acc[3][b] += v.w * cv[b];
-            }
-        }
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -320,59 +376,49 @@ k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, 
             const int64_t c = cbase + cg * CPT + b;
             if (c < nct) Ypart[((int64_t)blockIdx.y * NB + lg * 4 + a) * nct + c] = acc[a][b];
         }
+    trail_finish_z<T, NB, TY_COLS, TY_THREADS>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Z,
+                                               counters + blockIdx.x, reinterpret_cast<T *>(ty_raw));
 }
 
-// C(i, c) -= sum_l V(i, l) Z(l, c) with Z = T^T Y, Y = sum_s Ypart[s].  CTA tile
-// TC_ROWS x TC_COLS; each thread owns 4 consecutive rows x 8 columns and reads and
-// writes C as 4-row vectors (coalesced along the column).
+// C(i, c) -= sum_l V(i, l) Z(l, c).  CTA tile TC_ROWS x TC_COLS; each thread owns 4
+// consecutive rows x 8 columns and reads and writes C as 4-row vectors.
 constexpr int TC_ROWS = 128;
 constexpr int TC_COLS = 64;
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(256)
-k_trail_c(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct,
-          const T *__restrict__ Ypart, int nsplit, const T *__restrict__ Tblk)
+k_trail_c(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct, int64_t coff,
+          const T *__restrict__ Z)
 {
     using V4 = typename Vec4<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T (*sZ)[TC_COLS] = reinterpret_cast<T (*)[TC_COLS]>(smem_raw);                   // [NB][TC_COLS]: Y, then Z
-    T (*sV)[TC_ROWS] = reinterpret_cast<T (*)[TC_ROWS]>(smem_raw + sizeof(T) * NB * TC_COLS);   // V(l, row)
-    T (*sT)[NB] = reinterpret_cast<T (*)[NB]>(smem_raw + sizeof(T) * NB * (TC_COLS + TC_ROWS));
+    T (*sZ)[TC_COLS] = reinterpret_cast<T (*)[TC_COLS]>(smem_raw);                                // [NB][TC_COLS]
+    T (*sV)[TC_ROWS] = reinterpret_cast<T (*)[TC_ROWS]>(smem_raw + sizeof(T) * NB * TC_COLS);    // [NB][TC_ROWS]
     const int64_t mp = m - k;
     const int64_t rbase = (int64_t)blockIdx.x * TC_ROWS;
     const int64_t cbase = (int64_t)blockIdx.y * TC_COLS;
-    for (int idx = threadIdx.x; idx < NB * NB; idx += 256) sT[idx % NB][idx / NB] = Tblk[idx];
-    for (int idx = threadIdx.x; idx < NB * TC_COLS; idx += 256) {
-        int ll = idx / TC_COLS, cc = idx % TC_COLS;
-        int64_t c = cbase + cc;
-        T s = T(0);
-        if (c < nct)
-            for (int sp = 0; sp < nsplit; ++sp) s += Ypart[((int64_t)sp * NB + ll) * nct + c];
-        sZ[ll][cc] = s;
-    }
-    for (int idx = threadIdx.x; idx < TC_ROWS * NB; idx += 256) {
-        int rr = idx % TC_ROWS, ll = idx / TC_ROWS;
-        int64_t i = rbase + rr;
-        sV[ll][rr] = (i < mp) ? v_at(F, ld, k, i, ll, ncols) : T(0);
-    }
-    __syncthreads();
-    // Z(l, c) = sum_q T(q, l) Y(q, c)  (T upper triangular: q <= l), one column per thread
-    if (threadIdx.x < TC_COLS) {
-        const int cc = threadIdx.x;
-        T y[NB];
-#pragma unroll
-        for (int q = 0; q < NB; ++q) y[q] = sZ[q][cc];
-#pragma unroll
-        for (int ll = 0; ll < NB; ++ll) {
-            T s = T(0);
-#pragma unroll
-            for (int q = 0; q <= ll; ++q) s += sT[q][ll] * y[q];
-            sZ[ll][cc] = s;
-        }
-    }
-    __syncthreads();
     const int r4 = (threadIdx.x & 31) * 4;     // 4 consecutive rows
     const int c8 = (threadIdx.x >> 5) * 8;     // 8 columns
+    const int64_t i0 = rbase + r4;
+    // the thread's C tile first: its loads overlap the staging below
+    V4 cur[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int64_t c = cbase + c8 + b;
+        cur[b] = (i0 < mp && c < nct) ? *reinterpret_cast<const V4 *>(F + (k + i0) + (k + ncols + coff + c) * ld)
+                                      : v4_zero<T>();
+    }
+    for (int idx = threadIdx.x; idx < NB * (TC_ROWS / 4); idx += 256) {
+        const int ll = idx / (TC_ROWS / 4), q = idx % (TC_ROWS / 4);
+        const int64_t i = rbase + 4 * q;
+        *reinterpret_cast<V4 *>(&sV[ll][4 * q]) = (i < mp) ? v_quad(F, ld, k, i, ll, ncols) : v4_zero<T>();
+    }
+    for (int idx = threadIdx.x; idx < NB * TC_COLS; idx += 256) {
+        const int ll = idx / TC_COLS, cc = idx % TC_COLS;
+        const int64_t c = cbase + cc;
+        sZ[ll][cc] = (c < nct) ? Z[(int64_t)ll * nct + c] : T(0);
+    }
+    __syncthreads();
     T acc[4][8];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -392,25 +438,17 @@ k_trail_c(T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_
             acc[3][b] += v.w * zz[b];
         }
     }
-    const int64_t i0 = rbase + r4;
-    const bool vec = (i0 + 3 < mp) && (((k + i0) & 3) == 0) && ((ld & 3) == 0);
+    if (i0 >= mp) return;
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
         const int64_t c = cbase + c8 + b;
         if (c >= nct) break;
-        T *p = F + (k + i0) + (k + ncols + c) * ld;
-        if (vec) {
-            V4 cur = *reinterpret_cast<V4 *>(p);
-            cur.x -= acc[0][b];
-            cur.y -= acc[1][b];
-            cur.z -= acc[2][b];
-            cur.w -= acc[3][b];
-            *reinterpret_cast<V4 *>(p) = cur;
-        } else {
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                if (i0 + a < mp) p[a] -= acc[a][b];
-        }
+        V4 u = cur[b];
+        u.x -= acc[0][b];
+        u.y -= acc[1][b];
+        u.z -= acc[2][b];
+        u.w -= acc[3][b];
+        *reinterpret_cast<V4 *>(F + (k + i0) + (k + ncols + coff + c) * ld) = u;
     }
 }
 
@@ -726,7 +764,7 @@ static int launch_panel(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m
 
 template <typename T, int NB>
 static int launch_trailing(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m_aug,
-                           int ncols, int64_t nct, const T *Tblk)
+                           int ncols, int64_t nct, int64_t coff, const T *Tblk, int *counters)
 {
     if (nct <= 0) return 0;
     const int64_t mp = m_aug - k;
@@ -737,49 +775,95 @@ static int launch_trailing(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_
     int64_t rows_per_split = fl_round_up(fl_cdiv(mp, nsplit), TY_ROWS);
     nsplit = fl_cdiv(mp, rows_per_split);
     T *Ypart = (T *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(T) * nsplit * NB * nct);
-    if (!Ypart) return FASTLSQ_ERR_NOMEM;
+    T *Z = (T *)fl_ws(ctx, FL_WS_ZBUF, sizeof(T) * NB * nct);
+    if (!Ypart || !Z) return FASTLSQ_ERR_NOMEM;
     static bool attr_done = false;
-    const size_t smem_c = sizeof(T) * NB * (TC_COLS + TC_ROWS + NB);
+    const size_t smem_c = sizeof(T) * NB * (TC_COLS + TC_ROWS);
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_trail_c<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_c);
-        if (e != cudaSuccess) return fl_cuda(ctx, e, "trail_c attribute");
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_trail_y<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TrailYSmem<T, NB>::bytes);
+        if (e != cudaSuccess) return fl_cuda(ctx, e, "trailing-update attributes");
         attr_done = true;
     }
     FL_PROF_N(ctx, FASTLSQ_K_TRAIL_SIMT, 2);
-    k_trail_y<T, NB><<<dim3((unsigned)ctiles, (unsigned)nsplit), 256, 0, ctx->stream>>>(
-        F, ld, k, m_aug, ncols, nct, rows_per_split, Ypart);
+    k_trail_y<T, NB><<<dim3((unsigned)ctiles, (unsigned)nsplit), TY_THREADS, TrailYSmem<T, NB>::bytes,
+                       ctx->stream>>>(F, ld, k, m_aug, ncols, nct, coff, rows_per_split, Ypart, Z, Tblk, counters);
     FL_CHECK_LAUNCH(ctx, "trail_y");
     k_trail_c<T, NB><<<dim3((unsigned)fl_cdiv(mp, TC_ROWS), (unsigned)fl_cdiv(nct, TC_COLS)), 256, smem_c,
-                       ctx->stream>>>(F, ld, k, m_aug, ncols, nct, Ypart, (int)nsplit, Tblk);
+                       ctx->stream>>>(F, ld, k, m_aug, ncols, nct, coff, Z);
     FL_CHECK_LAUNCH(ctx, "trail_c");
     return 0;
 }
 
 template <typename T, int NB>
+static int panel_any(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m_aug, int ncols, T *tau,
+                     T *Tblk)
+{
+    if constexpr (std::is_same<T, float>::value && NB == 32) {
+        if (ctx->panel_reg && fl_panel_reg_fits(m_aug - k))
+            return fl_panel_reg_f32(ctx, F, ld, k, m_aug, ncols, tau, Tblk);
+    }
+    return launch_panel<T, NB>(ctx, F, ld, k, m_aug, ncols, tau, Tblk);
+}
+
+// trailing columns [k + ncols + coff, k + ncols + coff + nct) updated by panel k
+template <typename T, int NB>
+static int trailing_any(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
+                        int64_t nct, int64_t coff, const T *Tblk, int *counters, int use_tc)
+{
+    if (nct <= 0) return 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (use_tc) return fl_trailing_tc_f32(ctx, F, ld, k, m_aug, ncols, NB, nct, coff, Tblk, counters);
+    }
+    return launch_trailing<T, NB>(ctx, F, ld, k, m_aug, ncols, nct, coff, Tblk, counters);
+}
+
+// Blocked right-looking Householder QR.  With look-ahead, panel p's update of the
+// next panel's columns runs first; the rest of panel p's update is then handed to
+// the auxiliary stream while the next panel is factored right away on the caller's
+// stream (so the panel's cluster is placed before the update's CTAs fill the GPU),
+// and the two join before panel p+1's own update.
+template <typename T, int NB>
 static int factor_t(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n, int nrhs,
                     T *tau, T *Tall, int use_tc)
 {
     const int64_t ntot = n + nrhs;
-    for (int64_t k = 0; k < n; k += NB) {
+    // one completion counter per column tile of the trailing updates, zero between panels
+    const int64_t max_tiles = fl_cdiv(ntot, 32) + 8;
+    int *counters = (int *)fl_ws(ctx, FL_WS_COUNTERS, sizeof(int) * max_tiles);
+    if (!counters) return FASTLSQ_ERR_NOMEM;
+    cudaMemsetAsync(counters, 0, sizeof(int) * max_tiles, ctx->stream);
+    const int64_t npan = fl_cdiv(n, NB);
+    const bool la = ctx->lookahead && ctx->aux_stream && npan > 1;
+    for (int64_t p = 0; p < npan; ++p) {
+        const int64_t k = p * NB;
         const int ncols = (int)std::min<int64_t>(NB, n - k);
-        T *Tblk = Tall + (k / NB) * NB * NB;
-        bool done = false;
-        if constexpr (std::is_same<T, float>::value && NB == 32) {
-            if (ctx->panel_reg && fl_panel_reg_fits(m_aug - k)) {
-                FL_TRY(fl_panel_reg_f32(ctx, F, ld, k, m_aug, ncols, tau + k, Tblk));
-                done = true;
-            }
-        }
-        if (!done) FL_TRY((launch_panel<T, NB>(ctx, F, ld, k, m_aug, ncols, tau + k, Tblk)));
+        T *Tblk = Tall + p * NB * NB;
+        if (!la || p == 0) FL_TRY((panel_any<T, NB>(ctx, F, ld, k, m_aug, ncols, tau + k, Tblk)));
         const int64_t nct = ntot - (k + ncols);
-        if constexpr (std::is_same<T, float>::value) {
-            if (use_tc) {
-                FL_TRY((fl_trailing_tc_f32(ctx, F, ld, k, m_aug, ncols, NB, nct, Tblk)));
-                continue;
-            }
+        if (la && p + 1 < npan) {
+            const int ncn = (int)std::min<int64_t>(NB, n - (k + NB));
+            FL_TRY((trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, ncn, 0, Tblk, counters, use_tc)));
+            cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0);
+            if (e != cudaSuccess) return fl_cuda(ctx, e, "look-ahead fork");
+            cudaStream_t main_stream = ctx->stream;
+            ctx->stream = ctx->aux_stream;
+            const int rc = trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, nct - ncn, ncn, Tblk, counters,
+                                               use_tc);
+            if (rc == 0) e = cudaEventRecord(ctx->ev_join, ctx->aux_stream);
+            ctx->stream = main_stream;
+            FL_TRY(rc);
+            if (e != cudaSuccess) return fl_cuda(ctx, e, "look-ahead join");
+            FL_TRY((panel_any<T, NB>(ctx, F, ld, k + NB, m_aug, ncn, tau + k + NB, Tblk + NB * NB)));
+            e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+            if (e != cudaSuccess) return fl_cuda(ctx, e, "look-ahead join");
+        } else {
+            FL_TRY((trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, nct, 0, Tblk, counters, use_tc)));
         }
-        FL_TRY((launch_trailing<T, NB>(ctx, F, ld, k, m_aug, ncols, nct, Tblk)));
     }
     return 0;
 }
@@ -804,6 +888,10 @@ template <typename T>
 int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
                const T *Tall, T *y, int transpose)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        const int rc = fl_apply_q_cluster<float>(ctx, F, ld, m_aug, n, nb, Tall, y, transpose);
+        if (rc <= 0) return rc;          // 1: shape not taken by the cluster kernel
+    }
     // about 512 rows per CTA keeps the partial sums few (one L2 round trip to combine)
     const unsigned G = (unsigned)std::min<int64_t>(ctx->num_sms, std::max<int64_t>(4, fl_cdiv(m_aug, 512)));
     T *part = (T *)fl_ws(ctx, FL_WS_APPLYQ, sizeof(T) * 2 * ctx->num_sms * 32);

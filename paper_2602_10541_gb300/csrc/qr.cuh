@@ -9,6 +9,11 @@ int fl_panel_capacity_nb(fastlsq_ctx *ctx, int64_t m_aug, size_t elem);
 template <typename T>
 int fl_factor(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n, int nrhs, int nb,
               T *tau, T *Tall, int use_tc);
+// Q^T y / Q y on one cluster, FP32 factor with panel width 32 (apply_q.cu); returns 1
+// when the shape is not taken (more than 16 x 640 rows or another panel width)
+template <typename T>
+int fl_apply_q_cluster(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
+                       const T *Tall, T *y, int transpose);
 template <typename T>
 int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
                const T *Tall, T *y, int transpose);
@@ -35,7 +40,7 @@ int fl_panel_reg_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t 
 // tcgen05 (TF32x3 split precision) trailing update; tc_update.cu.  Returns a
 // negative status when the tensor-core path cannot handle the shape.
 int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
-                       int nb, int64_t nct, const float *Tblk);
+                       int nb, int64_t nct, int64_t coff, const float *Tblk, int *counters);
 
 // Krylov refinement with the factor's R as preconditioner (refine.cu)
 int fl_refine_cgls(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs64, double *beta64,
@@ -46,4 +51,4 @@ int fl_normal_pcg(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *c64, 
 // grid-wide FP64 triangular solve with R of type T (refine.cu)
 template <typename T>
 int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const double *y, double *x,
-                 double *work, int transpose, const void *skip_scalars = nullptr);
+                 double *work, int transpose, const void *skip_scalars = nullptr, int arith32 = 0);

@@ -15,6 +15,7 @@
 // host round trips.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 
@@ -202,17 +203,17 @@ constexpr int TC_MAX_CS = 16;
 // Stage diagonal block b as the "effective" triangle E in column-major layout
 // E[j * TS_LD + i]: E = D (upper) or D^T (lower, transpose).  Ragged rows/cols
 // beyond n become the identity so that the padded unknowns solve to zero.
-template <typename T>
+template <typename T, typename A>
 __device__ __forceinline__ void trsv_stage_diag(const T *__restrict__ F, int64_t ld, int64_t n, int64_t r0,
-                                                int transpose, double *E, int tid, int nthreads)
+                                                int transpose, A *E, int tid, int nthreads)
 {
     const int nb = (int)fl_min64(TG_BS, n - r0);
     for (int idx = tid; idx < TG_BS * TG_BS; idx += nthreads) {
         // consecutive threads read consecutive addresses of F in both cases
         const int a = idx % TG_BS, c = idx / TG_BS;          // F row r0 + a, F column r0 + c
-        double v;
-        if (a < nb && c < nb) v = (a <= c) ? (double)F[(r0 + a) + (r0 + c) * ld] : 0.0;   // R is D's upper triangle
-        else v = (a == c) ? 1.0 : 0.0;
+        A v;
+        if (a < nb && c < nb) v = (a <= c) ? (A)F[(r0 + a) + (r0 + c) * ld] : A(0);   // R is D's upper triangle
+        else v = (a == c) ? A(1) : A(0);
         if (!transpose) E[c * TS_LD + a] = v;                // E(i=a, j=c) = D(a, c)
         else E[a * TS_LD + c] = v;                           // E(i=c, j=a) = D(a, c)
     }
@@ -223,28 +224,29 @@ __device__ __forceinline__ void trsv_stage_diag(const T *__restrict__ F, int64_t
 // Upper: j = 63..0, x_j = w_j / E_jj, w_i -= E_ij x_j (i < j).  Lower: j = 0..63,
 // i > j.  x_j is formed as w_j * (1 / E_jj) (at most two roundings) so that the
 // dependent chain per unknown is one multiply, one shuffle and one FMA.
-__device__ __forceinline__ void trsv_diag_warp(const double *E, int lower, int lane, double &w0, double &w1)
+template <typename A>
+__device__ __forceinline__ void trsv_diag_warp(const A *E, int lower, int lane, A &w0, A &w1)
 {
-    const double rinv0 = 1.0 / E[lane * TS_LD + lane];
-    const double rinv1 = 1.0 / E[(lane + 32) * TS_LD + lane + 32];
-    double x0 = 0.0, x1 = 0.0;
+    const A rinv0 = A(1) / E[lane * TS_LD + lane];
+    const A rinv1 = A(1) / E[(lane + 32) * TS_LD + lane + 32];
+    A x0 = A(0), x1 = A(0);
     if (!lower) {
 #pragma unroll
         for (int j = TG_BS - 1; j >= 0; --j) {
-            const double t = (j < 32) ? w0 * rinv0 : w1 * rinv1;
-            const double xj = __shfl_sync(0xffffffffu, t, j & 31);
+            const A t = (j < 32) ? w0 * rinv0 : w1 * rinv1;
+            const A xj = __shfl_sync(0xffffffffu, t, j & 31);
             if (lane == (j & 31)) { if (j < 32) x0 = xj; else x1 = xj; }
-            const double *col = E + j * TS_LD;
+            const A *col = E + j * TS_LD;
             if (lane < j) w0 = fma(-col[lane], xj, w0);
             if (lane + 32 < j) w1 = fma(-col[lane + 32], xj, w1);
         }
     } else {
 #pragma unroll
         for (int j = 0; j < TG_BS; ++j) {
-            const double t = (j < 32) ? w0 * rinv0 : w1 * rinv1;
-            const double xj = __shfl_sync(0xffffffffu, t, j & 31);
+            const A t = (j < 32) ? w0 * rinv0 : w1 * rinv1;
+            const A xj = __shfl_sync(0xffffffffu, t, j & 31);
             if (lane == (j & 31)) { if (j < 32) x0 = xj; else x1 = xj; }
-            const double *col = E + j * TS_LD;
+            const A *col = E + j * TS_LD;
             if (lane > j) w0 = fma(-col[lane], xj, w0);
             if (lane + 32 > j) w1 = fma(-col[lane + 32], xj, w1);
         }
@@ -255,13 +257,13 @@ __device__ __forceinline__ void trsv_diag_warp(const double *E, int lower, int l
 
 struct TrsvClusterSmem {
     // [nown][TG_BS * TS_LD] staged diagonal blocks, [nown][TG_BS] w, [nblk * TG_BS] x
-    static __host__ __device__ size_t bytes(int nown, int64_t nblk)
+    static __host__ __device__ size_t bytes(int nown, int64_t nblk, size_t elem)
     {
-        return sizeof(double) * ((size_t)nown * (TG_BS * TS_LD + TG_BS) + (size_t)nblk * TG_BS);
+        return elem * ((size_t)nown * (TG_BS * TS_LD + TG_BS) + (size_t)nblk * TG_BS);
     }
 };
 
-template <typename T>
+template <typename T, typename A>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_trsv_cluster(const T *__restrict__ F, int64_t ld, int64_t n, const double *__restrict__ y,
                double *__restrict__ x, int transpose, int *flag, const KryScalars *st)
@@ -269,21 +271,22 @@ k_trsv_cluster(const T *__restrict__ F, int64_t ld, int64_t n, const double *__r
     if (st && st->done) return;              // same value in every CTA of the cluster
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ __align__(16) double tsm[];
-    __shared__ double red[2][4 * TG_BS];
+    extern __shared__ __align__(16) unsigned char tsm_raw[];
+    A *tsm = reinterpret_cast<A *>(tsm_raw);
+    __shared__ A red[2][4 * TG_BS];
     const int rank = (int)cluster.block_rank();
     const int CS = (int)cluster.num_blocks();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t nblk = (n + TG_BS - 1) / TG_BS;
     const int nown = (int)((nblk - rank + CS - 1) / CS);
     const int nown_max = (int)((nblk + CS - 1) / CS);
-    double *Es = tsm;
-    double *ws = Es + (size_t)nown_max * TG_BS * TS_LD;
-    double *xs = ws + (size_t)nown_max * TG_BS;
+    A *Es = tsm;
+    A *ws = Es + (size_t)nown_max * TG_BS * TS_LD;
+    A *xs = ws + (size_t)nown_max * TG_BS;
     for (int lb = 0; lb < nown; ++lb) {
         const int64_t r0 = (int64_t)(rank + lb * CS) * TG_BS;
         trsv_stage_diag(F, ld, n, r0, transpose, Es + (size_t)lb * TG_BS * TS_LD, tid, TC_THREADS);
-        for (int i = tid; i < TG_BS; i += TC_THREADS) ws[lb * TG_BS + i] = (r0 + i < n) ? y[r0 + i] : 0.0;
+        for (int i = tid; i < TG_BS; i += TC_THREADS) ws[lb * TG_BS + i] = (r0 + i < n) ? (A)y[r0 + i] : A(0);
     }
     cluster.sync();                          // every rank resident before the first DSMEM store
     for (int64_t s = 0; s < nblk; ++s) {
@@ -292,23 +295,23 @@ k_trsv_cluster(const T *__restrict__ F, int64_t ld, int64_t n, const double *__r
         const int nb = (int)fl_min64(TG_BS, n - r0);
         if ((int)(b % CS) == rank && warp == 0) {
             const int lb = (int)(b / CS);
-            double w0 = ws[lb * TG_BS + lane], w1 = ws[lb * TG_BS + lane + 32];
+            A w0 = ws[lb * TG_BS + lane], w1 = ws[lb * TG_BS + lane + 32];
             trsv_diag_warp(Es + (size_t)lb * TG_BS * TS_LD, transpose, lane, w0, w1);
             if (!isfinite(w0) || !isfinite(w1)) atomicCAS(flag, 0, FL_DEVERR_NONFINITE);
             for (int rr = 0; rr < CS; ++rr) {
-                double *dst = cluster.map_shared_rank(xs, rr);
+                A *dst = cluster.map_shared_rank(xs, rr);
                 dst[r0 + lane] = w0;
                 dst[r0 + lane + 32] = w1;
             }
         }
         cluster.sync();
-        const double *xb = xs + r0;
+        const A *xb = xs + r0;
         if (!transpose) {
             // owned rows of blocks b' < b: w_i -= sum_c R(i, r0 + c) x_c; two column halves
             const int row = tid & (4 * TG_BS - 1), half = tid / (4 * TG_BS);
             const int lb = row / TG_BS, ri = row % TG_BS;
             const int64_t bb = (int64_t)rank + (int64_t)lb * CS;
-            double acc = 0.0;
+            A acc = A(0);
             if (lb < nown && bb < b) {
                 const T *a = F + (bb * TG_BS + ri) + (r0 + half * 32) * ld;
                 const int c1 = fl_min64(32, nb - half * 32);
@@ -316,7 +319,7 @@ k_trsv_cluster(const T *__restrict__ F, int64_t ld, int64_t n, const double *__r
 #pragma unroll
                 for (int c = 0; c < 32; ++c) v[c] = (c < c1) ? a[(int64_t)c * ld] : (T)0;
 #pragma unroll
-                for (int c = 0; c < 32; ++c) acc = fma((double)v[c], xb[half * 32 + c], acc);
+                for (int c = 0; c < 32; ++c) acc = fma((A)v[c], xb[half * 32 + c], acc);
             }
             red[half][row] = acc;
             __syncthreads();
@@ -326,18 +329,18 @@ k_trsv_cluster(const T *__restrict__ F, int64_t ld, int64_t n, const double *__r
             // lanes over c (contiguous in column i of F)
             const int nrow_own = nown * TG_BS;
             for (int base = warp * 16; base < nrow_own; base += (TC_THREADS / 32) * 16) {
-                double acc[16];
+                A acc[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int row = base + q;
                     const int lb = row / TG_BS, ri = row % TG_BS;
                     const int64_t bb = (int64_t)rank + (int64_t)lb * CS;
                     const int64_t i = bb * TG_BS + ri;
-                    acc[q] = 0.0;
+                    acc[q] = A(0);
                     if (row < nrow_own && bb > b && i < n) {
                         const T *a = F + r0 + i * ld;
-                        const double v0 = (lane < nb) ? (double)a[lane] : 0.0;
-                        const double v1 = (lane + 32 < nb) ? (double)a[lane + 32] : 0.0;
+                        const A v0 = (lane < nb) ? (A)a[lane] : A(0);
+                        const A v1 = (lane + 32 < nb) ? (A)a[lane + 32] : A(0);
                         acc[q] = fma(v0, xb[lane], v1 * xb[lane + 32]);
                     }
                 }
@@ -345,7 +348,7 @@ k_trsv_cluster(const T *__restrict__ F, int64_t ld, int64_t n, const double *__r
                 for (int q = 0; q < 16; ++q)
                     for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
                 if (lane < 16) {
-                    double mine = acc[0];
+                    A mine = acc[0];
 #pragma unroll
                     for (int q = 1; q < 16; ++q) if (lane == q) mine = acc[q];
                     const int row = base + lane;
@@ -489,7 +492,7 @@ int kry_dot(fastlsq_ctx *ctx, const double *a, const double *b, int64_t n, const
 // makes the call a no-op.
 template <typename T>
 int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const double *y, double *x,
-                 double *work, int transpose, const void *skip_scalars)
+                 double *work, int transpose, const void *skip_scalars, int arith32)
 {
     FL_PROF(ctx, FASTLSQ_K_TRSV);
     int *flag = ctx->d_flag;
@@ -497,16 +500,21 @@ int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const doub
     const int64_t nblk = fl_cdiv(n, TG_BS);
     const int CS = (int)std::min<int64_t>(TC_MAX_CS, nblk);
     const int nown_max = (int)fl_cdiv(nblk, CS);
-    const size_t smem = TrsvClusterSmem::bytes(nown_max, nblk);
-    static bool attr_done = false;   // per process; attributes are per function
-    if (nown_max <= 4 && smem + sizeof(double) * 2 * 4 * TG_BS <= (size_t)ctx->max_smem_optin) {
-        if (!attr_done) {
-            cudaError_t e = cudaFuncSetAttribute(k_trsv_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 ctx->max_smem_optin - (int)(sizeof(double) * 2 * 4 * TG_BS));
+    // FP32 arithmetic only on request and only for an FP32 factor
+    const bool a32 = arith32 && std::is_same<T, float>::value;
+    const size_t elem = a32 ? sizeof(float) : sizeof(double);
+    const size_t smem = TrsvClusterSmem::bytes(nown_max, nblk, elem);
+    using K = void (*)(const T *, int64_t, int64_t, const double *, double *, int, int *, const KryScalars *);
+    K kern = a32 ? (K)k_trsv_cluster<T, float> : (K)k_trsv_cluster<T, double>;
+    static bool attr_done[2] = {false, false};   // per process; attributes are per function
+    if (nown_max <= 4 && smem + elem * 2 * 4 * TG_BS <= (size_t)ctx->max_smem_optin) {
+        if (!attr_done[a32]) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 ctx->max_smem_optin - (int)(elem * 2 * 4 * TG_BS));
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_trsv_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return fl_cuda(ctx, e, "cudaFuncSetAttribute");
-            attr_done = true;
+            attr_done[a32] = true;
         }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(CS);
@@ -520,7 +528,7 @@ int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const doub
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, k_trsv_cluster<T>, F, ld, n, y, x, transpose, flag, st);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, F, ld, n, y, x, transpose, flag, st);
         if (e != cudaSuccess) return fl_cuda(ctx, e, "cluster triangular solve");
         return 0;
     }
@@ -535,9 +543,9 @@ int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const doub
     return 0;
 }
 template int fl_trsv_grid<float>(fastlsq_ctx *, const float *, int64_t, int64_t, const double *,
-                                 double *, double *, int, const void *);
+                                 double *, double *, int, const void *, int);
 template int fl_trsv_grid<double>(fastlsq_ctx *, const double *, int64_t, int64_t, const double *,
-                                  double *, double *, int, const void *);
+                                  double *, double *, int, const void *, int);
 
 namespace {
 

@@ -52,19 +52,21 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
                  : "memory");
 }
 
-// Waits for the phase with the given parity; gives up after max_spins polls and
-// returns false (the caller raises the device flag and skips the dependent work).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long max_spins)
+// Waits for the phase with the given parity; gives up once max_cycles SM clock
+// cycles have passed and returns false (the caller raises the device flag and
+// skips the dependent work).  Each poll suspends for at most 1 us.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long max_cycles)
 {
+    const long long t0 = clock64();
     uint32_t done = 0;
-    for (long long it = 0; it < max_spins; ++it) {
+    for (;;) {
         asm volatile("{\n.reg .pred p;\n"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
                      "selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+                     : "=r"(done) : "r"(smem_addr(bar)), "r"(parity), "r"(1000u) : "memory");
         if (done) return true;
+        if (clock64() - t0 > max_cycles) return false;
     }
-    return false;
 }
 
 // ---- descriptors ------------------------------------------------------------

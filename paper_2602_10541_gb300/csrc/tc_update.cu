@@ -17,6 +17,7 @@
 #include "common.cuh"
 #include "qr.cuh"
 #include "tc_common.cuh"
+#include "trail_z.cuh"
 
 namespace {
 
@@ -24,7 +25,7 @@ constexpr int TCY_COLS = 128;      // columns of C per CTA (M of the MMA)
 constexpr int TCY_CHUNK = 32;      // rows per K-chunk
 constexpr int TCU_ROWS = 128;      // rows of C per CTA in the update (M)
 constexpr int TCU_COLS = 128;      // columns of C per CTA in the update (N)
-constexpr long long TC_SPIN = 1ll << 26;
+constexpr long long TC_SPIN = 2000000000ll;   // SM cycles (about a second) before an mbarrier wait gives up
 
 __device__ __forceinline__ float v_at_f(const float *__restrict__ F, int64_t ld, int64_t k, int64_t i,
                                         int l, int ncols)
@@ -45,8 +46,9 @@ __device__ __forceinline__ unsigned char *align1024(unsigned char *p)
 // ---------------------------------------------------------------------------
 template <int NB>
 __global__ void __launch_bounds__(128, 1)
-k_tc_y(const float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct,
-       int64_t rows_per_split, float *__restrict__ Ypart, int *flag)
+k_tc_y(const float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct, int64_t coff,
+       int64_t rows_per_split, float *__restrict__ Ypart, float *__restrict__ Z,
+       const float *__restrict__ Tblk, int *__restrict__ counters, int *flag)
 {
     constexpr int N = NB < 16 ? 16 : NB;                 // MMA N (multiple of 16 for M = 128)
     constexpr uint32_t A_BYTES = TCY_COLS * 128;         // 128 rows x 32 fp32
@@ -94,7 +96,7 @@ k_tc_y(const float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
         for (int cl = 0; cl < 32; ++cl) {
             const int cr = warp * 32 + cl;
             const int64_t c = cbase + cr;
-            const float x = (iv && c < nct) ? F[(k + i) + (k + ncols + c) * ld] : 0.f;
+            const float x = (iv && c < nct) ? F[(k + i) + (k + ncols + coff + c) * ld] : 0.f;
             float h, lo;
             tc::split_tf32(x, h, lo);
             const uint32_t off = tc::sw128_offset(cr, lane);
@@ -160,6 +162,9 @@ k_tc_y(const float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 32);
+    if (ok)   // uniform; the stage buffers are free once the last MMA has completed
+        trail_finish_z<float, NB, TCY_COLS, 128>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Z,
+                                                 counters + blockIdx.x, reinterpret_cast<float *>(base));
 }
 
 // ---------------------------------------------------------------------------
@@ -167,15 +172,14 @@ k_tc_y(const float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
 // ---------------------------------------------------------------------------
 template <int NB>
 __global__ void __launch_bounds__(128, 1)
-k_tc_update(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct,
-            const float *__restrict__ Ypart, int nsplit, const float *__restrict__ Tblk, int *flag)
+k_tc_update(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct, int64_t coff,
+            const float *__restrict__ Z, int *flag)
 {
     constexpr uint32_t A_BYTES = TCU_ROWS * 128;     // 128 rows x 32 fp32 (K = l, padded to 32)
     constexpr uint32_t B_BYTES = TCU_COLS * 128;     // 128 columns x 32 fp32
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = align1024(smem_raw);
     unsigned char *Ah = base, *Al = Ah + A_BYTES, *Bh = Al + A_BYTES, *Bl = Bh + B_BYTES;
-    __shared__ float sT[NB][NB + 1];
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -188,24 +192,15 @@ k_tc_update(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, 
         tc::mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    for (int idx = threadIdx.x; idx < NB * NB; idx += 128) sT[idx % NB][idx / NB] = Tblk[idx];
-    __syncthreads();
     // B = Z: thread t owns column c = cbase + t; smem row t, k = l
     {
         const int64_t c = cbase + threadIdx.x;
-        float y[NB];
+        float zl[NB];
 #pragma unroll
-        for (int q = 0; q < NB; ++q) y[q] = 0.f;
-        if (c < nct)
-            for (int sp = 0; sp < nsplit; ++sp)
-#pragma unroll
-                for (int q = 0; q < NB; ++q) y[q] += Ypart[((int64_t)sp * NB + q) * nct + c];
+        for (int l = 0; l < NB; ++l) zl[l] = (c < nct) ? Z[(int64_t)l * nct + c] : 0.f;
 #pragma unroll
         for (int l = 0; l < 32; ++l) {
-            float z = 0.f;
-            if (l < NB)
-#pragma unroll
-                for (int q = 0; q <= l && q < NB; ++q) z += sT[q][l] * y[q];
+            const float z = (l < NB) ? zl[l] : 0.f;
             float h, lo;
             tc::split_tf32(z, h, lo);
             const uint32_t off = tc::sw128_offset(threadIdx.x, l);
@@ -263,7 +258,7 @@ k_tc_update(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, 
                 for (int j = 0; j < 16; ++j) {
                     const int64_t c = cbase + cc + j;
                     if (c < nct) {
-                        float *p = F + (k + i) + (k + ncols + c) * ld;
+                        float *p = F + (k + i) + (k + ncols + coff + c) * ld;
                         *p -= v[j];
                     }
                 }
@@ -277,7 +272,7 @@ k_tc_update(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, 
 
 template <int NB>
 int launch_tc(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols, int64_t nct,
-              const float *Tblk)
+              int64_t coff, const float *Tblk, int *counters)
 {
     constexpr int N = NB < 16 ? 16 : NB;
     const size_t smem_y = 2 * (2 * TCY_COLS * 128 + 2 * N * 128) + 1024;
@@ -296,13 +291,14 @@ int launch_tc(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, 
     int64_t rows_per_split = fl_round_up(fl_cdiv(mp, nsplit), TCY_CHUNK);
     nsplit = fl_cdiv(mp, rows_per_split);
     float *Ypart = (float *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(float) * nsplit * NB * nct);
-    if (!Ypart) return FASTLSQ_ERR_NOMEM;
+    float *Z = (float *)fl_ws(ctx, FL_WS_ZBUF, sizeof(float) * NB * nct);
+    if (!Ypart || !Z) return FASTLSQ_ERR_NOMEM;
     FL_PROF_N(ctx, FASTLSQ_K_TRAIL_TC, 2);
     k_tc_y<NB><<<dim3((unsigned)ctiles, (unsigned)nsplit), 128, smem_y, ctx->stream>>>(
-        F, ld, k, m_aug, ncols, nct, rows_per_split, Ypart, ctx->d_flag);
+        F, ld, k, m_aug, ncols, nct, coff, rows_per_split, Ypart, Z, Tblk, counters, ctx->d_flag);
     FL_CHECK_LAUNCH(ctx, "tc_y");
     k_tc_update<NB><<<dim3((unsigned)fl_cdiv(mp, TCU_ROWS), (unsigned)fl_cdiv(nct, TCU_COLS)), 128, smem_u,
-                      ctx->stream>>>(F, ld, k, m_aug, ncols, nct, Ypart, (int)nsplit, Tblk, ctx->d_flag);
+                      ctx->stream>>>(F, ld, k, m_aug, ncols, nct, coff, Z, ctx->d_flag);
     FL_CHECK_LAUNCH(ctx, "tc_update");
     return 0;
 }
@@ -310,13 +306,13 @@ int launch_tc(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, 
 }  // namespace
 
 int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
-                       int nb, int64_t nct, const float *Tblk)
+                       int nb, int64_t nct, int64_t coff, const float *Tblk, int *counters)
 {
     if (nct <= 0) return 0;
     switch (nb) {
-    case 32: return launch_tc<32>(ctx, F, ld, k, m_aug, ncols, nct, Tblk);
-    case 16: return launch_tc<16>(ctx, F, ld, k, m_aug, ncols, nct, Tblk);
-    case 8: return launch_tc<8>(ctx, F, ld, k, m_aug, ncols, nct, Tblk);
+    case 32: return launch_tc<32>(ctx, F, ld, k, m_aug, ncols, nct, coff, Tblk, counters);
+    case 16: return launch_tc<16>(ctx, F, ld, k, m_aug, ncols, nct, coff, Tblk, counters);
+    case 8: return launch_tc<8>(ctx, F, ld, k, m_aug, ncols, nct, coff, Tblk, counters);
     default: return fl_fail(ctx, FASTLSQ_ERR_INVALID, "tensor-core update: panel width %d", nb);
     }
 }

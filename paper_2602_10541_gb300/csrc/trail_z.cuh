@@ -1,0 +1,52 @@
+// Completion of the Y = V^T C partial sums of a trailing update: the last CTA of a
+// column tile to finish (counted with an atomic per tile) adds the split partials
+// in split order, so the result does not depend on which CTA finishes last, and
+// forms Z = T^T Y (T upper triangular) for the tile.  The counter is reset for the
+// next panel.  Z is stored [l][c] with row stride nct.
+#pragma once
+#include "common.cuh"
+
+template <typename T, int NB, int COLS, int THREADS>
+__device__ __forceinline__ void trail_finish_z(const T *__restrict__ Ypart, int nsplit, int64_t nct,
+                                               int64_t cbase, const T *__restrict__ Tblk,
+                                               T *__restrict__ Z, int *counter, T *scratch)
+{
+    static_assert((NB * COLS) % THREADS == 0, "tile");
+    constexpr int ITEMS = NB * COLS / THREADS;
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1) == nsplit - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    T *sY = scratch;                    // [NB][COLS]
+    T *sT = scratch + NB * COLS;        // [NB * NB], T(q, l) at q + l * NB
+    for (int idx = threadIdx.x; idx < NB * NB; idx += THREADS) sT[idx] = Tblk[idx];
+    T acc[ITEMS];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) acc[it] = T(0);
+    for (int sp = 0; sp < nsplit; ++sp) {
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            const int idx = it * THREADS + threadIdx.x;
+            const int l = idx / COLS, cc = idx % COLS;
+            const int64_t c = cbase + cc;
+            if (c < nct) acc[it] += __ldcg(Ypart + ((int64_t)sp * NB + l) * nct + c);
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) sY[it * THREADS + threadIdx.x] = acc[it];
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        const int idx = it * THREADS + threadIdx.x;
+        const int l = idx / COLS, cc = idx % COLS;
+        const int64_t c = cbase + cc;
+        if (c >= nct) continue;
+        T z = T(0);
+        for (int q = 0; q <= l; ++q) z += sT[q + l * NB] * sY[q * COLS + cc];
+        Z[(int64_t)l * nct + c] = z;
+    }
+    if (threadIdx.x == 0) *counter = 0;
+}

@@ -179,6 +179,8 @@ class Context:
 
 OPT_TENSOR_CORE = 0
 OPT_REGISTER_PANEL = 1
+OPT_LOOKAHEAD = 2
+OPT_TRSV_FP32 = 3
 
 
 def fastlsq_set_option(ctx, option, value):

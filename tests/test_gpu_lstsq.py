@@ -267,3 +267,36 @@ def test_register_panel_matches_oracle_and_shared_memory_panel(ctx, m, n):
     scale = np.abs(Ro).max()
     assert np.abs(Rs[1] - Ro).max() <= 2e-5 * scale
     assert np.abs(Rs[1] - Rs[0]).max() <= 2e-5 * scale
+
+
+@pytest.mark.parametrize("tc", [0, 1])
+@pytest.mark.parametrize("m,n", [(700, 130), (3000, 257)])
+def test_lookahead_matches_single_stream(ctx, tc, m, n):
+    """Look-ahead (next panel on the auxiliary stream during the trailing update)
+    gives the same factor as one stream up to FP32 summation order, and the same
+    refined solution."""
+    rng = np.random.default_rng(5 * m + n)
+    A = rng.standard_normal((m, n))
+    B = _nearly_consistent(rng, A)
+    ref = oracle.lstsq(A, B).reshape(-1)
+    packed, _ = oracle.qr(A)
+    Ro = np.triu(packed[:n])
+    scale = np.abs(Ro).max()
+    Rs = {}
+    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, tc)
+    try:
+        for la in (1, 0):
+            fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, la)
+            beta = torch.zeros((1, n), dtype=torch.float64, device=DEV)
+            _, fac, _ = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, 0.0, _rhs(B), beta,
+                                         A_refine=_cm(A, torch.float64), max_refine=4, keep=True)
+            R = torch.zeros((n, n), dtype=torch.float64, device=DEV)
+            fl.fastlsq_factor_get_r(ctx, fac, R)
+            fl.fastlsq_factor_destroy(ctx, fac)
+            Rs[la] = R.cpu().numpy().T
+            np.testing.assert_allclose(beta.cpu().numpy()[0], ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+    finally:
+        fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, 1)
+        fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 0)
+    assert np.abs(Rs[1] - Ro).max() <= 2e-5 * scale
+    assert np.abs(Rs[1] - Rs[0]).max() <= 2e-5 * scale
