@@ -162,6 +162,31 @@ FASTLSQ_API int fastlsq_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, 
                  const double *beta, double *u);
 
 /*
+ * fastlsq_eval without any device allocation.  The paper has no counterpart: this
+ * entry serves callers that must not allocate device memory while they run (code
+ * under a no-allocation policy, or code being captured into a CUDA graph).
+ *
+ * Arguments, layout and result are those of fastlsq_eval, and the result is
+ * bitwise the same (the same kernels in the same order).  The only difference is
+ * where the scratch lives: the FP64 partial sums, ceil(n_feat / 128) x n_eval of
+ * them, are written into a fixed 4 MiB array compiled into this library (524,288
+ * doubles) instead of the context's workspace.  So the call requires
+ * ceil(n_feat / 128) * n_eval <= 524288 (for example 5000 points with up to 13,312
+ * features) and returns FASTLSQ_ERR_INVALID, without launching anything, when the
+ * request is larger.  Nothing in the array needs to start at zero: every entry a
+ * call reads was written earlier in the same call.
+ *
+ * The array's device address is looked up with cudaGetSymbolAddress on the first
+ * call on each device; make that first call before capturing a stream into a
+ * graph.  There is one array per device for the whole process: two calls whose
+ * executions can overlap (different streams, host threads or contexts on the same
+ * device) use the same scratch and give wrong results.  Serialise them.
+ */
+FASTLSQ_API int fastlsq_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int32_t d,
+                         const double *W, const double *b, int64_t n_feat, double scale,
+                         const double *beta, double *u);
+
+/*
  * Adjoint of fastlsq_eval (the sensor readout u_s = H_s beta of Sec. 4.4):
  * grad_beta[j] = scale * sum_e g[e] sin(W_j.x_e + b_j), FP64.  x: [n_eval][d],
  * g: [n_eval], grad_beta: [n_feat].

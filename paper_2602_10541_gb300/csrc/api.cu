@@ -11,6 +11,8 @@
 
 int fl_launch_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, const double *W,
                    const double *b, int64_t n_feat, double scale, const double *beta, double *u);
+int fl_launch_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, const double *W,
+                           const double *b, int64_t n_feat, double scale, const double *beta, double *u);
 int fl_launch_eval_adjoint(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d,
                            const double *W, const double *b, int64_t n_feat, double scale,
                            const double *g, double *grad);
@@ -361,6 +363,18 @@ extern "C" int fastlsq_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, i
     if (n_eval == 0) return 0;
     if (!x || !W || !b || !beta || !u) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval: null array");
     return fl_launch_eval(ctx, x, n_eval, d, W, b, n_feat, scale, beta, u);
+}
+
+extern "C" int fastlsq_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int32_t d,
+                                    const double *W, const double *b, int64_t n_feat, double scale,
+                                    const double *beta, double *u)
+{
+    if (!ctx) return FASTLSQ_ERR_INVALID;
+    if (n_eval < 0 || n_feat < 1 || d < 1 || d > FL_MAX_D)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval_noalloc: bad sizes");
+    if (n_eval == 0) return 0;
+    if (!x || !W || !b || !beta || !u) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval_noalloc: null array");
+    return fl_launch_eval_noalloc(ctx, x, n_eval, d, W, b, n_feat, scale, beta, u);
 }
 
 extern "C" int fastlsq_eval_adjoint(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int32_t d,

@@ -467,6 +467,44 @@ int fl_launch_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, con
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// fastlsq_eval_noalloc: the evaluation of fastlsq_eval with its partial sums in a
+// fixed device array of this library instead of the context's workspace, so the
+// call allocates nothing.  The array is shared by every context on a device; its
+// address is looked up once per device.
+// ---------------------------------------------------------------------------
+constexpr size_t FL_EVAL_STATIC_DOUBLES = (size_t)1 << 19;      // 4 MiB of FP64 partial sums
+static __device__ __align__(256) double g_eval_static[FL_EVAL_STATIC_DOUBLES];
+
+int fl_launch_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, const double *W,
+                           const double *b, int64_t n_feat, double scale, const double *beta, double *u)
+{
+    if (n_eval == 0) return 0;
+    const int64_t nsplit = fl_cdiv(n_feat, EVAL_SPLIT_COLS);
+    if (nsplit * n_eval > (int64_t)FL_EVAL_STATIC_DOUBLES)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID,
+                       "eval_noalloc: ceil(n_feat/%d) * n_eval = %lld exceeds the %lld-entry static scratch",
+                       EVAL_SPLIT_COLS, (long long)(nsplit * n_eval), (long long)FL_EVAL_STATIC_DOUBLES);
+    static double *addr[64] = {};            // per device ordinal; every thread writes the same value
+    if (ctx->device < 0 || ctx->device >= 64)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval_noalloc: device ordinal %d", ctx->device);
+    if (!addr[ctx->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_eval_static);
+        if (e != cudaSuccess) return fl_cuda(ctx, e, "eval_noalloc: scratch address");
+        addr[ctx->device] = (double *)p;
+    }
+    double *part = addr[ctx->device];
+    dim3 grid((unsigned)fl_cdiv(n_eval, 128), (unsigned)nsplit);
+    FL_PROF_N(ctx, FASTLSQ_K_EVAL, 2);
+    k_eval_partial<<<grid, 128, 0, ctx->stream>>>(x, n_eval, d, W, b, n_feat, beta, part);
+    FL_CHECK_LAUNCH(ctx, "eval_partial");
+    k_eval_reduce<<<(unsigned)fl_cdiv(n_eval, 256), 256, 0, ctx->stream>>>(part, (int)nsplit, n_eval,
+                                                                           scale, u);
+    FL_CHECK_LAUNCH(ctx, "eval_reduce");
+    return 0;
+}
+
 int fl_launch_eval_adjoint(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d,
                            const double *W, const double *b, int64_t n_feat, double scale,
                            const double *g, double *grad)

@@ -81,6 +81,7 @@ _SIGNATURES = {
     "fastlsq_rhs": [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_dbl), _i32, _vp, _i64, _i32,
                     _dbl, _vp],
     "fastlsq_eval": [_vp, _vp, _i64, _i32, _vp, _vp, _i64, _dbl, _vp, _vp],
+    "fastlsq_eval_noalloc": [_vp, _vp, _i64, _i32, _vp, _vp, _i64, _dbl, _vp, _vp],
     "fastlsq_eval_adjoint": [_vp, _vp, _i64, _i32, _vp, _vp, _i64, _dbl, _vp, _vp],
     "fastlsq_lstsq": [_vp, ctypes.c_int, _vp, ctypes.c_int, _i64, _i64, _i64, _dbl, _vp, _i32, _i64,
                       _vp, _i64, _vp, _i64, _i32, _i32, _dbl, ctypes.POINTER(_vp),
@@ -239,6 +240,12 @@ def fastlsq_rhs(ctx, problem, kind, params, x, weight, out):
 def fastlsq_eval(ctx, x, W, b, scale, beta, u):
     return ctx.check(ctx.lib.fastlsq_eval(ctx.handle, _ptr(x), x.shape[0], x.shape[1], _ptr(W),
                                           _ptr(b), W.shape[0], float(scale), _ptr(beta), _ptr(u)))
+
+
+def fastlsq_eval_noalloc(ctx, x, W, b, scale, beta, u):
+    """fastlsq_eval with the scratch in the library's fixed device array (no allocation)."""
+    return ctx.check(ctx.lib.fastlsq_eval_noalloc(ctx.handle, _ptr(x), x.shape[0], x.shape[1], _ptr(W),
+                                                  _ptr(b), W.shape[0], float(scale), _ptr(beta), _ptr(u)))
 
 
 def fastlsq_eval_adjoint(ctx, x, W, b, scale, g, grad_beta):
