@@ -63,43 +63,52 @@ struct fl_pp_rows {
 };
 
 // FP32 assembly: z in float FMAs, Cody-Waite reduction to [-pi, pi] with a
-// three-part 2 pi, SFU sin/cos, float4 stores of 4 consecutive rows.
-template <bool NEED_COS>
-__global__ void __launch_bounds__(ASM_THREADS)
-k_assemble_f32(const double *__restrict__ x, int64_t n_rows, int d,
+// three-part 2 pi, SFU sin/cos, float4 stores of 4 consecutive rows.  The point
+// dimension D is a template parameter, so the inner loop holds exactly D FMAs.
+// CTA tile: 128 rows (32 lanes x 4 rows) x 256 columns; the column data (W, b, P,
+// Q) are converted to float once per CTA into shared memory, the thread's 4 points
+// once per thread into registers.
+constexpr int AF_ROWS = 128;
+constexpr int AF_COLS = 256;
+constexpr int AF_THREADS = 256;
+
+template <int D, bool NEED_COS>
+__global__ void __launch_bounds__(AF_THREADS)
+k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
                const double *__restrict__ W, const double *__restrict__ b, int64_t n_feat,
                const double *__restrict__ pref, int n_pp, unsigned pp_cos_mask, fl_pp_rows pp,
                float *__restrict__ A, int64_t ldA, int64_t row_offset,
                float c1, float c2, float c3)
 {
-    __shared__ float sW[ASM_COLS][FL_MAX_D];
-    __shared__ float sB[ASM_COLS], sP[ASM_COLS], sQ[ASM_COLS];
-    __shared__ float sM[FL_MAX_PP][ASM_COLS];
+    __shared__ float sW[D][AF_COLS];
+    __shared__ float sB[AF_COLS], sP[AF_COLS], sQ[NEED_COS ? AF_COLS : 1];
+    __shared__ float sM[FL_MAX_PP][AF_COLS];
 
-    const int64_t col0 = (int64_t)blockIdx.y * ASM_COLS;
-    const int64_t row0 = (int64_t)blockIdx.x * ASM_ROWS;
-    for (int t = threadIdx.x; t < ASM_COLS; t += blockDim.x) {
-        int64_t j = col0 + t;
-        bool ok = j < n_feat;
-        for (int k = 0; k < FL_MAX_D; ++k) sW[t][k] = (ok && k < d) ? (float)W[j * d + k] : 0.f;
-        sB[t] = ok ? (float)b[j] : 0.f;
-        sP[t] = ok ? (float)pref[j] : 0.f;
-        sQ[t] = ok ? (float)pref[n_feat + j] : 0.f;
-        for (int q = 0; q < n_pp; ++q) sM[q][t] = ok ? (float)pref[(2 + q) * n_feat + j] : 0.f;
+    const int64_t col0 = (int64_t)blockIdx.y * AF_COLS;
+    const int64_t row0 = (int64_t)blockIdx.x * AF_ROWS;
+    const int ncol = (int)fl_min64(AF_COLS, n_feat - col0);
+    for (int t = threadIdx.x; t < ncol * D; t += AF_THREADS) {
+        const int c = t / D, k = t % D;                  // consecutive threads: consecutive W
+        sW[k][c] = (float)W[(col0 + c) * D + k];
     }
-    __syncthreads();
+    for (int t = threadIdx.x; t < ncol; t += AF_THREADS) {
+        sB[t] = (float)b[col0 + t];
+        sP[t] = (float)pref[col0 + t];
+        if (NEED_COS) sQ[t] = (float)pref[n_feat + col0 + t];
+        for (int q = 0; q < n_pp; ++q) sM[q][t] = (float)pref[(2 + q) * n_feat + col0 + t];
+    }
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int64_t r0 = row0 + 4 * lane;
-    float xr[4][FL_MAX_D];
+    float xr[4][D];
     float cpt[FL_MAX_PP][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        int64_t i = r0 + u;
-        bool ok = i < n_rows;
+        const int64_t i = r0 + u;
+        const bool ok = i < n_rows;
 #pragma unroll
-        for (int k = 0; k < FL_MAX_D; ++k) xr[u][k] = (ok && k < d) ? (float)x[i * d + k] : 0.f;
+        for (int k = 0; k < D; ++k) xr[u][k] = ok ? (float)x[i * D + k] : 0.f;
 #pragma unroll
         for (int q = 0; q < FL_MAX_PP; ++q) cpt[q][u] = (ok && q < n_pp) ? (float)pp.c[q][i] : 0.f;
     }
@@ -108,36 +117,38 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows, int d,
     const bool vec = full && ((gr & 3) == 0) && ((ldA & 3) == 0) &&
                      ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
     const float inv2pi = 0.159154943091895335768883763372514362f;
+    __syncthreads();
 
-#pragma unroll 2
-    for (int cc = 0; cc < ASM_COLS / 8; ++cc) {
-        const int c = warp * (ASM_COLS / 8) + cc;
-        const int64_t j = col0 + c;
-        if (j >= n_feat) break;
+#pragma unroll 4
+    for (int c = warp; c < ncol; c += AF_THREADS / 32) {
         float v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             float z = sB[c];
 #pragma unroll
-            for (int k = 0; k < FL_MAX_D; ++k)
-                if (k < d) z = fmaf(sW[c][k], xr[u][k], z);
-            float qn = rintf(z * inv2pi);
+            for (int k = 0; k < D; ++k) z = fmaf(sW[k][c], xr[u][k], z);
+            const float qn = rintf(z * inv2pi);
             float r = fmaf(-qn, c1, z);
             r = fmaf(-qn, c2, r);
             r = fmaf(-qn, c3, r);
-            float sn = __sinf(r);
+            const float sn = __sinf(r);
             float val = sP[c] * sn;
             float cs = 0.f;
             if (NEED_COS) {
                 cs = __cosf(r);
                 val = fmaf(sQ[c], cs, val);
             }
+            if (n_pp > 0) {                               // uniform: per-point terms (Newton)
 #pragma unroll
-            for (int q = 0; q < FL_MAX_PP; ++q)
-                if (q < n_pp) val = fmaf(cpt[q][u] * sM[q][c], ((pp_cos_mask >> q) & 1) ? cs : sn, val);
+                for (int q = 0; q < FL_MAX_PP; ++q) {
+                    if (q >= n_pp) break;
+                    const float phi = ((pp_cos_mask >> q) & 1) ? (NEED_COS ? cs : __cosf(r)) : sn;
+                    val = fmaf(cpt[q][u] * sM[q][c], phi, val);
+                }
+            }
             v[u] = val;
         }
-        float *dst = A + j * ldA + gr;
+        float *dst = A + (col0 + c) * ldA + gr;
         if (vec) {
             *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
         } else {
@@ -411,19 +422,26 @@ int fl_launch_assemble_f32(fastlsq_ctx *ctx, const fl_op_params &op, const doubl
 {
     if (n_rows == 0 || n_feat == 0) return 0;
     unsigned mask;
-    bool need_cos = op_needs_cos(op, &mask);
+    const bool need_cos = op_needs_cos(op, &mask);
     fl_pp_rows pp{};
     for (int q = 0; q < op.n_pp; ++q) pp.c[q] = op.pp_coef[q];
-    dim3 grid((unsigned)fl_cdiv(n_rows, ASM_ROWS), (unsigned)fl_cdiv(n_feat, ASM_COLS));
+    const dim3 grid((unsigned)fl_cdiv(n_rows, AF_ROWS), (unsigned)fl_cdiv(n_feat, AF_COLS));
+    const float c1 = ctx->cw2pi[0], c2 = ctx->cw2pi[1], c3 = ctx->cw2pi[2];
     FL_PROF(ctx, FASTLSQ_K_ASSEMBLE_F32);
-    if (need_cos)
-        k_assemble_f32<true><<<grid, ASM_THREADS, 0, ctx->stream>>>(
-            x, n_rows, op.d, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset,
-            ctx->cw2pi[0], ctx->cw2pi[1], ctx->cw2pi[2]);
-    else
-        k_assemble_f32<false><<<grid, ASM_THREADS, 0, ctx->stream>>>(
-            x, n_rows, op.d, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset,
-            ctx->cw2pi[0], ctx->cw2pi[1], ctx->cw2pi[2]);
+#define FL_ASM32(DD)                                                                                 \
+    case DD:                                                                                         \
+        if (need_cos)                                                                                \
+            k_assemble_f32<DD, true><<<grid, AF_THREADS, 0, ctx->stream>>>(                          \
+                x, n_rows, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset, c1, c2, c3);   \
+        else                                                                                         \
+            k_assemble_f32<DD, false><<<grid, AF_THREADS, 0, ctx->stream>>>(                         \
+                x, n_rows, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset, c1, c2, c3);   \
+        break;
+    switch (op.d) {
+        FL_ASM32(1) FL_ASM32(2) FL_ASM32(3) FL_ASM32(4) FL_ASM32(5) FL_ASM32(6) FL_ASM32(7) FL_ASM32(8)
+    default: return fl_fail(ctx, FASTLSQ_ERR_INVALID, "assemble: dimension %d", op.d);
+    }
+#undef FL_ASM32
     FL_CHECK_LAUNCH(ctx, "assemble_f32");
     return 0;
 }

@@ -97,7 +97,9 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
     const int nown = (int)fl_max64(0, fl_min64(rpc, mp - c0));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int l = lane;
-    const int64_t g0 = c0 + (int64_t)warp * RW;    // panel-local row of register row 0
+    // register row r of warp w holds CTA row 32 r + w: the rows next to the diagonal
+    // (panel rows <= 32) are register rows 0 and 1 of rank 0, spread over all warps
+    const int64_t g0 = c0 + warp;                   // panel-local row of register row 0
 
     // stage the slice through shared memory (coalesced along the columns of F)
     for (int idx = threadIdx.x; idx < rpc * 32; idx += PR_THREADS) {
@@ -108,14 +110,14 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
     __syncthreads();
     float p[RW];
 #pragma unroll
-    for (int r = 0; r < RW; ++r) p[r] = S[(warp * RW + r) * 33 + l];
+    for (int r = 0; r < RW; ++r) p[r] = S[(r * 32 + warp) * 33 + l];
     if (g0 == 0) diag[l] = p[0];                    // diagonal row 0 (rank 0, warp 0)
     // dot products of column 0 with every column over rows 1..
     float acc = 0.f;
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
         const float a0 = __shfl_sync(FULL, p[r], 0);
-        if (g0 + r > 0) acc = fmaf(a0, p[r], acc);
+        if (g0 + 32 * r > 0) acc = fmaf(a0, p[r], acc);
     }
 
     // one exchange barrier per parity; per phase one local arrival (with the expected
@@ -182,28 +184,17 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
         const float wl = (l > j) ? tj * (xb[PR_CL_MAX * PR_XLD + l] + inv * dl) : 0.f;
         const int jn = (j + 1) & 31;
         acc = 0.f;
-        if (g0 >= j + 2) {
-            // every row of this warp lies below the next diagonal row
+        // register rows 0 and 1 may be rows at or above j + 1 (rank 0): row j takes beta,
+        // row j + 1 is the next diagonal row and stays out of the next column's dot
+        // products, rows above j are finished rows of R
 #pragma unroll
-            for (int r = 0; r < RW; ++r) {
-                const float vj = __shfl_sync(FULL, p[r], j) * inv;
-                const float nl = fmaf(-wl, vj, p[r]);
-                const float nx = __shfl_sync(FULL, nl, jn);
-                p[r] = (l == j) ? vj : nl;
-                const float f = (l > j) ? nx : ((l < j) ? vj : 0.f);
-                acc = fmaf(f, nl, acc);
-            }
-        } else {
-            // rows at or above j + 1 (rank 0's first warps): row j takes beta, row j + 1
-            // is the next diagonal row and stays out of the next column's dot products
-#pragma unroll
-            for (int r = 0; r < RW; ++r) {
-                const int64_t g = g0 + r;                   // uniform across the warp
-                const float pj = __shfl_sync(FULL, p[r], j);
-                const float vj = (g == j) ? 1.f : pj * inv;
-                const float nl = fmaf(-wl, vj, p[r]);
-                const float nx = __shfl_sync(FULL, nl, jn);
-                if (g < j) continue;
+        for (int r = 0; r < 2; ++r) {
+            const int64_t g = g0 + 32 * r;                 // uniform across the warp
+            const float pj = __shfl_sync(FULL, p[r], j);
+            const float vj = (g == j) ? 1.f : pj * inv;
+            const float nl = fmaf(-wl, vj, p[r]);
+            const float nx = __shfl_sync(FULL, nl, jn);
+            if (g >= j) {
                 const float nv = (l == j) ? ((g == j) ? beta : vj) : nl;
                 p[r] = nv;
                 const float f = (l < j) ? vj : ((l > j && g > j + 1) ? nx : 0.f);
@@ -211,12 +202,22 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
                 if (g == j + 1) diag[l] = nv;
             }
         }
+        // register rows 2.. are panel rows >= 64, always below the next diagonal row
+#pragma unroll
+        for (int r = 2; r < RW; ++r) {
+            const float vj = __shfl_sync(FULL, p[r], j) * inv;
+            const float nl = fmaf(-wl, vj, p[r]);
+            const float nx = __shfl_sync(FULL, nl, jn);
+            p[r] = (l == j) ? vj : nl;
+            const float f = (l > j) ? nx : ((l < j) ? vj : 0.f);
+            acc = fmaf(f, nl, acc);
+        }
     }
 
     // write the slice back (coalesced through shared memory); rank 0 forms T
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < RW; ++r) S[(warp * RW + r) * 33 + l] = p[r];
+    for (int r = 0; r < RW; ++r) S[(r * 32 + warp) * 33 + l] = p[r];
     __syncthreads();
     for (int idx = threadIdx.x; idx < rpc * 32; idx += PR_THREADS) {
         const int c = idx / rpc, r = idx % rpc;
