@@ -153,9 +153,9 @@ def _src_sha(name):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-KERNEL_SRC = {"panel": "qr.cu", "trail_simt": "qr.cu", "trail_tc": "tc_update.cu",
-              "apply_q": "qr.cu", "trsv": "qr.cu", "residual": "qr.cu", "assemble_f32": "assemble.cu",
-              "assemble_f64": "assemble.cu", "copy_in": "qr.cu"}
+KERNEL_SRC = {"panel": "panel_reg.cu", "trail_simt": "qr.cu", "trail_tc": "tc_update.cu",
+              "apply_q": "apply_q.cu", "trsv": "refine.cu", "residual": "qr.cu",
+              "assemble_f32": "assemble.cu", "assemble_f64": "assemble.cu", "copy_in": "qr.cu"}
 
 
 def _algorithmic(kernel, m, n, m_aug, nb, nrhs, refine, nb_elem):
@@ -170,12 +170,8 @@ def _algorithmic(kernel, m, n, m_aug, nb, nrhs, refine, nb_elem):
         return "bytes", 8.0 * m * n
     if kernel == "panel":                              # slice read + written once per panel
         return "bytes", sum(2.0 * (m_aug - k) * c * e for k, c in panels)
-    if kernel in ("trail_simt", "trail_tc"):           # C read twice, written once; V twice
-        tot = 0.0
-        for k, c in panels:
-            nct = n + nrhs - (k + c)
-            tot += (3.0 * nct + 2.0 * c) * (m_aug - k) * e
-        return "bytes", tot
+    if kernel in ("trail_simt", "trail_tc"):           # Y = V^T C and C -= V Z: 4 (m-k) c nct
+        return "flops", sum(4.0 * (m_aug - k) * c * (n + nrhs - (k + c)) for k, c in panels)
     if kernel == "apply_q":                            # V read twice per application
         return "bytes", refine * sum(2.0 * (m_aug - k) * c * e for k, c in panels)
     if kernel == "trsv":                               # upper triangle read once per solve
@@ -285,17 +281,34 @@ def main():
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved = per_step * args.steps / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    if unit_kind == "flops" and dominant == "trail_simt":
+        # FP32 FMA pipe: SMs x 128 lanes x 2 flop x max SM clock
+        bound, unit = "alu", "TFLOP/s"
+        peak = 2.0 * 128 * nsm * sm_mhz * 1e6 / 1e12
+        peak_src = f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"
+    elif unit_kind == "flops":
+        # tcgen05 kind::tf32: measured bf16 dense peak x 1/2 (nominal TF32 : BF16 ratio)
+        bound, unit = "tensor", "TFLOP/s"
+        peak = peaks.get("bf16_tflops", 1900.0) * 0.5
+        peak_src = ("MEASURED_PEAKS.json bf16_tflops x 0.5 (of measured)" if peaks
+                    else "fallback 1900 TF/s bf16 x 0.5")
+    else:
+        bound, unit, peak = "hbm", "GB/s", hbm
+        peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"
+    scale_u = 1e12 if unit == "TFLOP/s" else 1e9
+    achieved = per_step * args.steps / (dom_ms / 1e3) / scale_u if dom_ms > 0 else 0.0
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tpath):
         tinfo = json.load(open(tpath)).get(dominant)
         if tinfo and tinfo.get("src_sha") == _src_sha(KERNEL_SRC.get(dominant, "qr.cu")):
             traffic = tinfo.get("bytes_per_launch")
-    roofline = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+    roofline = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak, "traffic": traffic,
                 "launches": dom_launches, "avg_launch_us": 1e3 * dom_ms / max(1, dom_launches),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+                "peak_source": peak_src}
     breakdown = {k: {"launches_per_step": v[0] / 2.0, "ms_per_step": v[1] / 2.0}
                  for k, v in prof_pre.items() if v[0]}
 

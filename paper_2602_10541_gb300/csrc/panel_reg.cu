@@ -48,12 +48,11 @@ __device__ __forceinline__ void arrive_expect_tx(uint64_t *bar, uint32_t bytes)
                  :: "r"(tc::smem_addr(bar)), "r"(bytes) : "memory");
 }
 
-// bulk copy of `bytes` (multiple of 16) from this CTA's shared memory into another
-// CTA's, counted down on the receiver's barrier
-__device__ __forceinline__ void bulk_to_rank(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+// store 16 bytes to another CTA's shared memory and count them down on its barrier
+__device__ __forceinline__ void st_async_v4(uint32_t addr, float4 v, uint32_t bar)
 {
-    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
-                 :: "r"(dst), "r"(tc::smem_addr(src)), "r"(bytes), "r"(bar) : "memory");
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];\n"
+                 :: "r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar) : "memory");
 }
 
 struct PrLayout {
@@ -139,9 +138,7 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
         __syncthreads();
         if (s_abort) break;                          // uniform: read after the barrier
         {
-            // warp c reduces column c over the 32 warps; the CTA's 32 partials (and rank
-            // 0's diagonal row) then go to every rank as one 128-byte bulk copy each,
-            // counted down on the receiver's barrier
+            // warp c reduces column c over the 32 warps into this CTA's partial vector
             const int c = warp;
             float s = red[lane * 33 + c];
 #pragma unroll
@@ -149,14 +146,21 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
             if (lane == 0) {
                 part[par][c] = s;
                 if (rank == 0) pdiag[par][c] = (j < ncols) ? diag[c] : 0.f;
-                tc::fence_proxy_async_smem();        // visible to the bulk copies below
             }
         }
         __syncthreads();
-        if (warp == 0 && lane < CL) {
-            const uint32_t rbar = map_rank(&xbar[par], lane);
-            bulk_to_rank(map_rank(xb + rank * PR_XLD, lane), part[par], 32 * sizeof(float), rbar);
-            if (rank == 0) bulk_to_rank(map_rank(xb + PR_CL_MAX * PR_XLD, lane), pdiag[par], 32 * sizeof(float), rbar);
+        if (warp < CL) {
+            // warp q sends the 32 partials (lanes 0-7, 16 bytes each) and, on rank 0, the
+            // diagonal row (lanes 8-15) to rank q with asynchronous DSMEM stores that
+            // count the bytes down on rank q's barrier
+            const int q = warp;
+            const uint32_t rbar = map_rank(&xbar[par], q);
+            if (lane < 8)
+                st_async_v4(map_rank(xb + rank * PR_XLD + 4 * lane, q),
+                            *reinterpret_cast<const float4 *>(&part[par][4 * lane]), rbar);
+            else if (lane < 16 && rank == 0)
+                st_async_v4(map_rank(xb + PR_CL_MAX * PR_XLD + 4 * (lane - 8), q),
+                            *reinterpret_cast<const float4 *>(&pdiag[par][4 * (lane - 8)]), rbar);
         }
         if (!tc::mbar_wait(&xbar[par], (uint32_t)(j >> 1) & 1u, PR_SPIN)) {
             s_abort = 1;                             // every warp leaves at the next barrier
@@ -164,8 +168,15 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
         }
         // every warp sums the CL partials of every column in the same order, so all
         // warps of all ranks hold bit-identical sums and reflector scalars
-        float dl = 0.f;
-        for (int q = 0; q < CL; ++q) dl += xb[q * PR_XLD + l];
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;    // four chains, fixed order
+#pragma unroll
+        for (int q = 0; q < PR_CL_MAX; q += 4) {
+            if (q < CL) d0 += xb[q * PR_XLD + l];
+            if (q + 1 < CL) d1 += xb[(q + 1) * PR_XLD + l];
+            if (q + 2 < CL) d2 += xb[(q + 2) * PR_XLD + l];
+            if (q + 3 < CL) d3 += xb[(q + 3) * PR_XLD + l];
+        }
+        const float dl = (d0 + d1) + (d2 + d3);
         if (rank == 0 && warp == 0 && j >= 1 && l < j - 1) G[l * 33 + (j - 1)] = dl;
         if (j == ncols) break;
         const float ss = __shfl_sync(FULL, dl, j);
@@ -177,8 +188,8 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
             // reflector of column j: v = 1 at row j, a(j+1:)/(a_jj - beta) below
             const float nrm = sqrtf(ajj * ajj + ss);
             beta = (ajj >= 0.f) ? -nrm : nrm;
-            tj = (beta - ajj) / beta;
-            inv = 1.f / (ajj - beta);
+            tj = __fdividef(beta - ajj, beta);       // |beta| >= |ajj| > 0: in range, 2 ulp
+            inv = __fdividef(1.f, ajj - beta);
         }
         if (rank == 0 && warp == 0 && lane == 0) tauv[j] = tj;
         const float wl = (l > j) ? tj * (xb[PR_CL_MAX * PR_XLD + l] + inv * dl) : 0.f;
@@ -289,6 +300,7 @@ int fl_panel_reg_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t 
     if (rpw <= 8) return launch_panel_reg<8>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
     if (rpw <= 12) return launch_panel_reg<12>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
     if (rpw <= 16) return launch_panel_reg<16>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
+    if (rpw <= 18) return launch_panel_reg<18>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
     if (rpw <= 20) return launch_panel_reg<20>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
     if (rpw <= 24) return launch_panel_reg<24>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
     return 1;   // too tall for registers: the caller uses the shared-memory panel
