@@ -183,6 +183,66 @@ def _algorithmic(kernel, m, n, m_aug, nb, nrhs, refine, nb_elem):
     return "bytes", 0.0
 
 
+def _secondary(fl, pl, wl, torch, ctx, dev, n_inverse):
+    """The other rows of the hot path, timed outside the headline step: the full-size
+    Bratu Newton run (Jacobian reassembled every step) in MIXED and FP64, and a batch of
+    inverse-problem instances (factor, solve, sensor loss, adjoint gradient)."""
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    out = {}
+    w = wl.bratu2d()
+    xi, xb, W, b = t(w.x_int), t(w.x_bc), t(w.W), t(w.b)
+    zi, zb = torch.zeros(w.n_int, dtype=torch.float64, device=dev), torch.zeros(w.n_bc, dtype=torch.float64, device=dev)
+    xt = t(w.x_test)
+    us = {}
+    for name, prec in (("mixed", fl.PREC_MIXED), ("fp64", fl.PREC_FP64)):
+        beta = torch.zeros(w.n_feat, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = fl.fastlsq_newton(ctx, xi, xb, fl.Op(w.alpha, w.coef), fl.NL_EXP, w.nl_lam, w.lam_bc,
+                                   zi, zb, W, b, w.scale, beta, max_iter=15, tol=1e-10, mu=w.mu,
+                                   prec=prec, max_refine=64, refine_tol=1e-13)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        u = torch.empty(xt.shape[0], dtype=torch.float64, device=dev)
+        fl.fastlsq_eval(ctx, xt, W, b, w.scale, beta, u)
+        us[name] = u
+        out[f"newton_{name}"] = {"seconds": sec, "iters": int(st.iters), "status": int(st.status),
+                                 "res_norm_first": float(st.res_norm[0]),
+                                 "res_norm_last": float(st.res_norm[st.iters]),
+                                 "last_step_rel": float(st.step_rel[max(0, st.iters - 1)])}
+    out["newton_mixed"]["rel_l2_vs_fp64_gpu"] = pl.rel_l2(us["mixed"], us["fp64"])
+    out["newton_workload"] = ("bratu2d: Lap u + e^u = 0, [0,1]^2, 8192 interior + 1024 boundary rows, "
+                              "2048 features sigma=6, mu=1e-10, Newton from beta=0, <=15 iterations")
+    # inverse problem: observations from the forward map at theta_true, gradients at theta_0
+    op = fl.Op([[2, 0], [0, 2]], [-1.0, -1.0])
+    insts, ws = [], []
+    for q in range(n_inverse):
+        wq = wl.inverse_instance(q)
+        ws.append(wq)
+        insts.append(dict(x_int=t(wq.x_int), x_bc=t(wq.x_bc), W=t(wq.W), b=t(wq.b), sensors=t(wq.sensors),
+                          y_obs=torch.zeros(wq.sensors.shape[0], dtype=torch.float64, device=dev),
+                          theta=t(wq.params), beta=torch.zeros(wq.n_feat, dtype=torch.float64, device=dev),
+                          loss=torch.zeros(1, dtype=torch.float64, device=dev),
+                          dtheta=torch.zeros(16, dtype=torch.float64, device=dev)))
+    fl.fastlsq_inverse_batch(ctx, insts, op, 4)
+    for d, wq in zip(insts, ws):
+        u_s = torch.empty(d["sensors"].shape[0], dtype=torch.float64, device=dev)
+        fl.fastlsq_eval(ctx, d["sensors"], d["W"], d["b"], wq.scale, d["beta"], u_s)
+        d["y_obs"].copy_(u_s + t(wq.noise))
+        d["theta"].copy_(t(wq.theta0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fl.fastlsq_inverse_batch(ctx, insts, op, 4)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    out["inverse"] = {"instances": n_inverse, "seconds": sec, "gradient_evals_per_s": n_inverse / sec,
+                      "rows_range": [int(min(wq.n_int for wq in ws)), int(max(wq.n_int for wq in ws))],
+                      "features_range": [int(min(wq.n_feat for wq in ws)), int(max(wq.n_feat for wq in ws))],
+                      "workload": ("steady inverse heat source, 4 Gaussians (16 parameters), MIXED factor + "
+                                   "CGLS/PCG refinement, loss and dL/dtheta per instance")}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -195,6 +255,8 @@ def main():
                     help="1: trailing QR updates on tcgen05 (TF32x3), 0: SIMT FP32")
     ap.add_argument("--trsv-fp32", type=int, default=1, choices=[0, 1],
                     help="1: FP32 substitution in the triangular solves of classical refinement")
+    ap.add_argument("--no-extras", action="store_true", help="skip the Newton and inverse-problem timings")
+    ap.add_argument("--inverse-instances", type=int, default=32)
     ap.add_argument("--lookahead", type=int, default=1, choices=[0, 1],
                     help="1: factor the next panel on a second stream during the trailing update")
     args = ap.parse_args()
@@ -377,6 +439,10 @@ def main():
                           f"{SAMPLE_CPU['n_bc']} rows x {SAMPLE_CPU['n_feat']} features "
                           f"({t:.1f} s), time x{ratio:.0f} (m n^2 ratio to the full workload)")}
 
+    extras = None
+    if rank == 0 and not args.no_extras:
+        extras = _secondary(fl, pl, wl, torch, ctx, dev, args.inverse_instances)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -390,7 +456,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single"},
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
                 "clocks": clk, "accuracy": accuracy, "assembly": assembly, "kernels": breakdown,
-                "wall_s_timed": wall}
+                "other_rows": extras, "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -89,6 +89,7 @@ k_apply_q_cluster(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n,
                                                               // writes step s + 1
     __shared__ __align__(16) T xbuf[2][AQC_CS_MAX][AQC_NB + 4];   // 16-byte rows for bulk copies
     __shared__ __align__(16) T part[2][AQC_NB];
+    __shared__ T sT[2][AQC_NB][AQC_NB + 1];                    // the panel's T block, by parity
     __shared__ uint64_t xbar[2];
     __shared__ volatile int s_abort;
     cg::cluster_group cluster = cg::this_cluster();
@@ -121,6 +122,11 @@ k_apply_q_cluster(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n,
             aq_load_v(F, ld, n, (int64_t)pn * AQC_NB, i, row_ok, vn);
         }
         if (threadIdx.x == 0) aq_expect_tx(&xbar[par], xbytes);
+        {
+            const T *Tb = Tall + (int64_t)p * AQC_NB * AQC_NB;     // T(q, l) at q + 32 l
+            for (int idx = threadIdx.x; idx < AQC_NB * AQC_NB; idx += blockDim.x)
+                sT[par][idx % AQC_NB][idx / AQC_NB] = Tb[idx];
+        }
         // s_l: warp partials, then the CTA's partial sent to every rank
         T prod[AQC_NB];
 #pragma unroll
@@ -145,14 +151,13 @@ k_apply_q_cluster(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n,
         }
         T sl = T(0);
         for (int q = 0; q < CS; ++q) sl += xbuf[par][q][lane];
-        // w = T^T s (Q^T) or T s (Q); T(q, l) at Tblk[q + l * 32]
-        const T *Tb = Tall + (int64_t)p * AQC_NB * AQC_NB;
+        // w = T^T s (Q^T) or T s (Q), T from shared memory
         T wl = T(0);
 #pragma unroll
         for (int q = 0; q < AQC_NB; ++q) {
             const T sq = __shfl_sync(FULL, sl, q);
-            if (transpose) { if (q <= lane) wl += Tb[q + lane * AQC_NB] * sq; }
-            else { if (q >= lane) wl += Tb[lane + q * AQC_NB] * sq; }
+            if (transpose) { if (q <= lane) wl += sT[par][q][lane] * sq; }
+            else { if (q >= lane) wl += sT[par][lane][q] * sq; }
         }
         T upd = T(0);
 #pragma unroll

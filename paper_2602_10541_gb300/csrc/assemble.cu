@@ -83,6 +83,7 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
     __shared__ float sW[D][AF_COLS];
     __shared__ float sB[AF_COLS], sP[AF_COLS], sQ[NEED_COS ? AF_COLS : 1];
     __shared__ float sM[FL_MAX_PP][AF_COLS];
+    __shared__ float sX[AF_ROWS][D];                     // the CTA's points, converted once
 
     const int64_t col0 = (int64_t)blockIdx.y * AF_COLS;
     const int64_t row0 = (int64_t)blockIdx.x * AF_ROWS;
@@ -98,6 +99,11 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
         for (int q = 0; q < n_pp; ++q) sM[q][t] = (float)pref[(2 + q) * n_feat + col0 + t];
     }
 
+    for (int t = threadIdx.x; t < AF_ROWS * D; t += AF_THREADS) {
+        const int64_t i = row0 + t / D;
+        sX[t / D][t % D] = (i < n_rows) ? (float)x[row0 * D + t] : 0.f;   // consecutive reads
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int64_t r0 = row0 + 4 * lane;
@@ -108,7 +114,7 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
         const int64_t i = r0 + u;
         const bool ok = i < n_rows;
 #pragma unroll
-        for (int k = 0; k < D; ++k) xr[u][k] = ok ? (float)x[i * D + k] : 0.f;
+        for (int k = 0; k < D; ++k) xr[u][k] = sX[4 * lane + u][k];
 #pragma unroll
         for (int q = 0; q < FL_MAX_PP; ++q) cpt[q][u] = (ok && q < n_pp) ? (float)pp.c[q][i] : 0.f;
     }
@@ -117,7 +123,6 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
     const bool vec = full && ((gr & 3) == 0) && ((ldA & 3) == 0) &&
                      ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
     const float inv2pi = 0.159154943091895335768883763372514362f;
-    __syncthreads();
 
 #pragma unroll 4
     for (int c = warp; c < ncol; c += AF_THREADS / 32) {

@@ -29,7 +29,6 @@ namespace {
 constexpr int PANEL_THREADS = 1024;
 constexpr int PANEL_WARPS = PANEL_THREADS / 32;
 constexpr int APPLY_THREADS = 512;
-constexpr int APPLY_WARPS = APPLY_THREADS / 32;
 constexpr int CL_MAX = 16;
 
 template <typename T> __device__ __forceinline__ T fl_sqrt(T v);
@@ -261,12 +260,11 @@ __device__ __forceinline__ T v_at(const T *__restrict__ F, int64_t ld, int64_t k
 // so 4-row vectors never need masking below row m_aug.
 constexpr int TY_COLS = 128;
 constexpr int TY_ROWS = 32;
-constexpr int TY_LDS = TY_ROWS + 4;     // padded stride of a staged column (keeps 16-byte alignment)
 constexpr int TY_THREADS = 256;
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
-template <> struct Vec4<double> { using type = double4; };
+template <> struct Vec4<double> { using type = double4_32a; };
 
 template <typename T>
 __device__ __forceinline__ typename Vec4<T>::type v4_zero()
@@ -295,7 +293,9 @@ __device__ __forceinline__ typename Vec4<T>::type v_quad(const T *__restrict__ F
 
 template <typename T, int NB>
 struct TrailYSmem {
-    static constexpr size_t stage = sizeof(T) * (size_t)(TY_COLS + NB) * TY_LDS;
+    // row-major chunks: C [TY_ROWS][TY_COLS + 4], V [TY_ROWS][NB + 4]
+    static constexpr int CLD = TY_COLS + 4, VLD = NB + 4;
+    static constexpr size_t stage = sizeof(T) * (size_t)TY_ROWS * (CLD + VLD);
     static constexpr size_t zscr = sizeof(T) * (size_t)(NB * TY_COLS + NB * NB);
     static constexpr size_t bytes = stage > zscr ? stage : zscr;
 };
@@ -307,20 +307,20 @@ k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, 
           int *__restrict__ counters)
 {
     using V4 = typename Vec4<T>::type;
-    constexpr int LG = NB / 4;                       // l-groups of 4
-    constexpr int CG = TY_THREADS / LG;              // c-groups
-    constexpr int CPT = TY_COLS / CG;                // columns per thread
+    constexpr int CLD = TrailYSmem<T, NB>::CLD, VLD = TrailYSmem<T, NB>::VLD;
+    constexpr int NW = TY_THREADS / 32;              // warps
+    constexpr int LPW = NB / NW;                     // l per warp (4 for NB = 32, 2 for 16, 1 for 8)
     constexpr int QPC = TY_ROWS / 4;                 // 4-row quads per chunk column
     constexpr int CQ = TY_COLS * QPC / TY_THREADS;   // C quads per thread per chunk
-    static_assert(CPT >= 1 && CQ >= 1, "tile");
+    static_assert(LPW >= 1 && CQ >= 1 && TY_COLS == 4 * 32, "tile");
     extern __shared__ __align__(16) unsigned char ty_raw[];
-    T *sC = reinterpret_cast<T *>(ty_raw);           // [TY_COLS][TY_LDS]
-    T *sV = sC + TY_COLS * TY_LDS;                   // [NB][TY_LDS]
+    T *sC = reinterpret_cast<T *>(ty_raw);           // [TY_ROWS][CLD]
+    T *sV = sC + TY_ROWS * CLD;                      // [TY_ROWS][VLD]
     const int64_t mp = m - k;
     const int64_t cbase = (int64_t)blockIdx.x * TY_COLS;
     const int64_t rs0 = (int64_t)blockIdx.y * rows_per_split;
     const int64_t rs1 = fl_min64(mp, rs0 + rows_per_split);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int lq = tid % QPC;                         // loader: quad within the chunk
     const int lc = tid / QPC;                         // loader: column (plus pass * 32)
     V4 rc[CQ], rv;
@@ -335,46 +335,60 @@ k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, 
         }
         rv = (lc < NB && i < rs1) ? v_quad(F, ld, k, i, lc, ncols) : v4_zero<T>();
     };
+    // 4-row vectors of one column land in 4 rows of the row-major chunk
     auto store = [&]() {
 #pragma unroll
-        for (int ps = 0; ps < CQ; ++ps)
-            *reinterpret_cast<V4 *>(sC + (lc + ps * (TY_THREADS / QPC)) * TY_LDS + 4 * lq) = rc[ps];
-        if (lc < NB) *reinterpret_cast<V4 *>(sV + lc * TY_LDS + 4 * lq) = rv;
+        for (int ps = 0; ps < CQ; ++ps) {
+            T *d = sC + (4 * lq) * CLD + lc + ps * (TY_THREADS / QPC);
+            d[0] = rc[ps].x;
+            d[CLD] = rc[ps].y;
+            d[2 * CLD] = rc[ps].z;
+            d[3 * CLD] = rc[ps].w;
+        }
+        if (lc < NB) {
+            T *d = sV + (4 * lq) * VLD + lc;
+            d[0] = rv.x;
+            d[VLD] = rv.y;
+            d[2 * VLD] = rv.z;
+            d[3 * VLD] = rv.w;
+        }
     };
 
-    const int lg = tid % LG, cg = tid / LG;
-    T acc[4][CPT];
+    // warp w owns l = LPW w .. LPW w + LPW - 1 (one broadcast read per row), lane owns
+    // columns 4 lane .. 4 lane + 3 (one conflict-free 16-byte read per row)
+    T acc[LPW][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < LPW; ++a)
 #pragma unroll
-        for (int b = 0; b < CPT; ++b) acc[a][b] = T(0);
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
 
     if (rs0 < rs1) load(rs0);
     for (int64_t r0 = rs0; r0 < rs1; r0 += TY_ROWS) {
         store();
         __syncthreads();
         if (r0 + TY_ROWS < rs1) load(r0 + TY_ROWS);          // next chunk in flight
+#pragma unroll 8
+        for (int r = 0; r < TY_ROWS; ++r) {
+            const V4 cv = *reinterpret_cast<const V4 *>(sC + r * CLD + 4 * lane);
+            T vl[LPW];
 #pragma unroll
-        for (int rg = 0; rg < QPC; ++rg) {
-            V4 v[4], cv[CPT];
+            for (int a = 0; a < LPW; ++a) vl[a] = sV[r * VLD + LPW * warp + a];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) v[a] = *reinterpret_cast<const V4 *>(sV + (lg * 4 + a) * TY_LDS + 4 * rg);
-#pragma unroll
-            for (int b = 0; b < CPT; ++b) cv[b] = *reinterpret_cast<const V4 *>(sC + (cg * CPT + b) * TY_LDS + 4 * rg);
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < CPT; ++b)
-                    acc[a][b] += v[a].x * cv[b].x + v[a].y * cv[b].y + v[a].z * cv[b].z + v[a].w * cv[b].w;
+            for (int a = 0; a < LPW; ++a) {
+                acc[a][0] += vl[a] * cv.x;
+                acc[a][1] += vl[a] * cv.y;
+                acc[a][2] += vl[a] * cv.z;
+                acc[a][3] += vl[a] * cv.w;
+            }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < LPW; ++a)
 #pragma unroll
-        for (int b = 0; b < CPT; ++b) {
-            const int64_t c = cbase + cg * CPT + b;
-            if (c < nct) Ypart[((int64_t)blockIdx.y * NB + lg * 4 + a) * nct + c] = acc[a][b];
+        for (int b = 0; b < 4; ++b) {
+            const int64_t c = cbase + 4 * lane + b;
+            if (c < nct) Ypart[((int64_t)blockIdx.y * NB + LPW * warp + a) * nct + c] = acc[a][b];
         }
     trail_finish_z<T, NB, TY_COLS, TY_THREADS>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Z,
                                                counters + blockIdx.x, reinterpret_cast<T *>(ty_raw));
