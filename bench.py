@@ -161,7 +161,7 @@ KERNEL_SRC = {"panel": "panel_reg.cu", "trail_simt": "qr.cu", "trail_tc": "tc_up
 def _algorithmic(kernel, m, n, m_aug, nb, nrhs, refine, nb_elem):
     """(unit, amount per solve) of the algorithmic cost of one kernel class in one
     step; bytes for memory-bound kernels (each operand moved once), flops for
-    arithmetic-bound ones.  Per-unit figures are stated in the design doc."""
+    arithmetic-bound ones: each operand moved once, or 4 (m-k) nb n_c flops per trailing update."""
     e = nb_elem
     panels = [(k, min(nb, n - k)) for k in range(0, n, nb)]
     if kernel == "assemble_f32":

@@ -401,10 +401,14 @@ typedef enum {
                                       on a second, low-priority stream of the context (joined
                                       back into the caller's stream before the next panel's
                                       update); 0: everything on the caller's stream */
-    FASTLSQ_OPT_TRSV_FP32 = 3      /* 1 (default): the triangular solves of classical
+    FASTLSQ_OPT_TRSV_FP32 = 3,     /* 1 (default): the triangular solves of classical
                                       refinement (MIXED) substitute in FP32 arithmetic
                                       (backward stable like the FP32 factor); 0: FP64
                                       arithmetic.  CGLS and the adjoint always use FP64. */
+    FASTLSQ_OPT_FUSED_LOOKAHEAD = 4 /* 1 (default): with look-ahead, the register panel
+                                      applies the previous panel's update to its own columns
+                                      in its prologue (no separate kernels for it) where its
+                                      shared memory allows; 0: separate update kernels */
 } fastlsq_option;
 
 /* Set a context option (see fastlsq_option).  Returns 0 or -1 for an unknown option. */

@@ -281,6 +281,10 @@ extern "C" int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value)
         ctx->lookahead = value ? 1 : 0;
         return 0;
     }
+    if (option == FASTLSQ_OPT_FUSED_LOOKAHEAD) {
+        ctx->fuse_next = value ? 1 : 0;
+        return 0;
+    }
     if (option == FASTLSQ_OPT_TRSV_FP32) {
         ctx->trsv32 = value ? 1 : 0;
         return 0;

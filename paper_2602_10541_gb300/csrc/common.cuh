@@ -70,6 +70,7 @@ struct fastlsq_ctx {
     int use_tensor_core = 0;        // tcgen05 trailing updates for the MIXED path
     int panel_reg = 1;              // register-resident FP32 panel (width 32) where it fits
     int lookahead = 1;              // panel p+1 beside the rest of panel p's update (on aux_stream)
+    int fuse_next = 1;              // look-ahead: next panel applies the previous update itself
     int trsv32 = 1;                 // FP32 arithmetic in the triangular solves of classical refinement
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -55,6 +55,14 @@ __device__ __forceinline__ void st_async_v4(uint32_t addr, float4 v, uint32_t ba
                  :: "r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar) : "memory");
 }
 
+// bulk copy of `bytes` (multiple of 16) from this CTA's shared memory into another
+// CTA's, counted down on the receiver's barrier
+__device__ __forceinline__ void bulk_to_rank(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 :: "r"(dst), "r"(tc::smem_addr(src)), "r"(bytes), "r"(bar) : "memory");
+}
+
 struct PrLayout {
     // offsets in floats
     static __host__ __device__ size_t red(int rpc) { return (size_t)rpc * 33; }
@@ -66,12 +74,169 @@ struct PrLayout {
     static __host__ __device__ size_t G(int rpc) { return Tm(rpc) + 32 * 33; }
     static __host__ __device__ size_t tauv(int rpc) { return G(rpc) + 32 * 33; }
     static __host__ __device__ size_t bytes(int rpc) { return sizeof(float) * (tauv(rpc) + 32); }
+    // with the previous panel's update fused in front: its V slice and the Y/Z buffers
+    static __host__ __device__ size_t sv(int rpc) { return tauv(rpc) + 32; }        // [rpc][36]
+    static __host__ __device__ size_t yp(int rpc) { return sv(rpc) + (size_t)rpc * 36; }  // [32][32]
+    static __host__ __device__ size_t rs(int rpc) { return yp(rpc) + 1024; }        // [48][32]
+    static __host__ __device__ size_t ys(int rpc) { return rs(rpc) + 48 * 32; }     // [32][32]
+    static __host__ __device__ size_t yf(int rpc) { return ys(rpc) + 1024; }        // [32][32]
+    static __host__ __device__ size_t zs(int rpc) { return yf(rpc) + 1024; }        // [32][33]
+    static __host__ __device__ size_t tp(int rpc) { return zs(rpc) + 32 * 33; }     // [32 * 32]
+    static __host__ __device__ size_t bytes_fused(int rpc) { return sizeof(float) * (tp(rpc) + 1024); }
 };
+
+// The previous panel's update of this panel's columns, fused in front of the panel:
+// C -= V (T^T (V^T C)) over rows kp.. with V, T of the panel starting at column kp.
+// C sits in registers (lane = column, p[r]) and in S; V in SV; rank 0 also holds the 32
+// rows kp..kp+31 of C (CT, in Tm) and the unit lower triangle of V (VT, in G).
+//  1. Y partial (32 x 32) of this CTA: thread = (4 x 4 block of Y, one of 16 row groups),
+//     sum over the row groups with shuffles;
+//  2. reduce-scatter: row l of the partial goes to rank l % CL (128-byte bulk copies),
+//     which adds the CL partials in rank order;
+//  3. all-gather of the summed rows to every rank (bulk copies): all ranks hold the same Y;
+//  4. Z = T^T Y; p[r] -= V(row, :) Z on the register rows; rank 0 writes CT - VT Z back.
+template <int RW>
+__device__ __forceinline__ void prev_panel_z(int rank, int CL, int nown, float *psm, int *flag,
+                                             uint64_t *ybar, volatile int *s_abort)
+{
+    constexpr int rpc = 32 * RW;
+    constexpr unsigned FULL = 0xffffffffu;
+    const float *S = psm;
+    const float *SV = psm + PrLayout::sv(rpc);
+    float *Yp = psm + PrLayout::yp(rpc);
+    float *RS = psm + PrLayout::rs(rpc);
+    float *YS = psm + PrLayout::ys(rpc);
+    float *YF = psm + PrLayout::yf(rpc);
+    float *Zs = psm + PrLayout::zs(rpc);
+    const float *Tp = psm + PrLayout::tp(rpc);
+    float *Tm = psm + PrLayout::Tm(rpc);
+    const float *G = psm + PrLayout::G(rpc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // 1. this CTA's partial of Y = V^T C
+    {
+        const int rg = threadIdx.x & 15, blk = threadIdx.x >> 4, lb = blk >> 3, cb = blk & 7;
+        float y[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) y[a][b] = 0.f;
+        for (int r = rg; r < nown; r += 16) {
+            const float4 v = *reinterpret_cast<const float4 *>(SV + r * 36 + 4 * lb);
+            const float va[4] = {v.x, v.y, v.z, v.w};
+            float cc[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cc[b] = S[r * 33 + 4 * cb + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) y[a][b] = fmaf(va[a], cc[b], y[a][b]);
+        }
+        if (rank == 0 && rg == 0)
+            for (int i = 0; i < 32; ++i)
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) y[a][b] = fmaf(G[i * 33 + 4 * lb + a], Tm[i * 33 + 4 * cb + b], y[a][b]);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) y[a][b] += __shfl_xor_sync(FULL, y[a][b], o);
+        if (rg == 0) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) Yp[(4 * lb + a) * 32 + 4 * cb + b] = y[a][b];
+            tc::fence_proxy_async_smem();
+        }
+    }
+    __syncthreads();
+    // 2. reduce-scatter
+    const int rpo = (32 + CL - 1) / CL;                  // rows per owner, at most
+    const int mine = (32 - rank + CL - 1) / CL;          // rows owned by this rank
+    if (threadIdx.x == 0) arrive_expect_tx(&ybar[0], (uint32_t)(mine * CL * 128));
+    if (threadIdx.x < 32) {
+        const int row = threadIdx.x, q = row % CL;
+        bulk_to_rank(map_rank(RS + (rank * rpo + row / CL) * 32, q), Yp + row * 32, 128, map_rank(&ybar[0], q));
+    }
+    if (!tc::mbar_wait(&ybar[0], 0u, PR_SPIN)) {
+        *s_abort = 1;
+        atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
+    }
+    for (int idx = threadIdx.x; idx < mine * 32; idx += PR_THREADS) {
+        const int lr = idx / 32, c = idx % 32;
+        float sum = 0.f;
+        for (int src = 0; src < CL; ++src) sum += RS[(src * rpo + lr) * 32 + c];
+        YS[lr * 32 + c] = sum;
+    }
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    // 3. all-gather
+    if (threadIdx.x == 0) arrive_expect_tx(&ybar[1], 32u * 128u);
+    for (int idx = threadIdx.x; idx < mine * CL; idx += PR_THREADS) {
+        const int lr = idx / CL, q = idx % CL, row = lr * CL + rank;
+        bulk_to_rank(map_rank(YF + row * 32, q), YS + lr * 32, 128, map_rank(&ybar[1], q));
+    }
+    if (!tc::mbar_wait(&ybar[1], 0u, PR_SPIN)) {
+        *s_abort = 1;
+        atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
+    }
+    // 4. Z = T^T Y (T(q, l) at Tp[q + 32 l], upper triangular), then the updates
+    {
+        float z = 0.f;
+        for (int q = 0; q <= warp; ++q) z = fmaf(Tp[q + warp * 32], YF[q * 32 + lane], z);
+        Zs[warp * 33 + lane] = z;
+    }
+    __syncthreads();
+}
+
+template <int RW>
+__device__ __forceinline__ void prev_panel_apply(int rank, int ncols, float *__restrict__ F, int64_t ld,
+                                                 int64_t k, int64_t kp, float *psm, float (&p)[RW])
+{
+    constexpr int rpc = 32 * RW;
+    const float *SV = psm + PrLayout::sv(rpc);
+    const float *Zs = psm + PrLayout::zs(rpc);
+    const float *Tm = psm + PrLayout::Tm(rpc);
+    const float *G = psm + PrLayout::G(rpc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int l0 = 0; l0 < 32; l0 += 8) {
+        float zc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) zc[i] = Zs[(l0 + i) * 33 + lane];
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const float *v = SV + (r * 32 + warp) * 36 + l0;
+            const float4 va = *reinterpret_cast<const float4 *>(v);
+            const float4 vb = *reinterpret_cast<const float4 *>(v + 4);
+            float u = va.x * zc[0];
+            u = fmaf(va.y, zc[1], u);
+            u = fmaf(va.z, zc[2], u);
+            u = fmaf(va.w, zc[3], u);
+            u = fmaf(vb.x, zc[4], u);
+            u = fmaf(vb.y, zc[5], u);
+            u = fmaf(vb.z, zc[6], u);
+            u = fmaf(vb.w, zc[7], u);
+            p[r] -= u;
+        }
+    }
+    if (rank == 0) {
+        const int i = warp, c = lane;
+        float u = 0.f;
+        for (int q = 0; q < 32; ++q) u = fmaf(G[i * 33 + q], Zs[q * 33 + c], u);
+        if (c < ncols) F[(kp + i) + (k + c) * ld] = Tm[i * 33 + c] - u;
+    }
+    __syncthreads();
+}
 
 template <int RW>
 __global__ void __launch_bounds__(PR_THREADS, 1)
 k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
-            float *__restrict__ tau_out, float *__restrict__ T_out, int *flag)
+            float *__restrict__ tau_out, float *__restrict__ T_out, int *flag,
+            int64_t kp, const float *__restrict__ Tprev)
 {
     constexpr int rpc = 32 * RW;
     constexpr unsigned FULL = 0xffffffffu;
@@ -84,6 +249,7 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
     float *G = psm + PrLayout::G(rpc);
     float *tauv = psm + PrLayout::tauv(rpc);
     __shared__ uint64_t xbar[2];
+    __shared__ uint64_t ybar[2];                     // the fused update's two exchanges
     __shared__ __align__(16) float part[2][32];      // this CTA's partials, by column parity
     __shared__ __align__(16) float pdiag[2][32];     // rank 0: the diagonal row, by parity
     __shared__ volatile int s_abort;
@@ -100,16 +266,50 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
     // (panel rows <= 32) are register rows 0 and 1 of rank 0, spread over all warps
     const int64_t g0 = c0 + warp;                   // panel-local row of register row 0
 
+    // exchange barriers: per phase one local arrival (with the expected byte count) plus
+    // the byte counts of the asynchronous DSMEM stores or bulk copies aimed at them
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&xbar[0], 1);
+        tc::mbar_init(&xbar[1], 1);
+        tc::mbar_init(&ybar[0], 1);
+        tc::mbar_init(&ybar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_abort = 0;
+    }
+    cluster.sync();                                  // barriers ready before any remote signal
+
     // stage the slice through shared memory (coalesced along the columns of F)
+    const bool fused = kp >= 0;
     for (int idx = threadIdx.x; idx < rpc * 32; idx += PR_THREADS) {
         const int c = idx / rpc, r = idx % rpc;
         S[r * 33 + c] = (r < nown && c < ncols) ? F[(k + c0 + r) + (k + c) * ld] : 0.f;
     }
-    for (int idx = threadIdx.x; idx < 2 * 32 * 33; idx += PR_THREADS) Tm[idx] = 0.f;   // Tm and G
+    float *SV = psm + PrLayout::sv(rpc);
+    if (fused) {
+        // the previous panel's reflectors (columns kp..kp+31) on this CTA's rows, which
+        // lie below that panel's diagonal block; its T; on rank 0 the 32 rows kp..kp+31
+        // of this panel's columns (CT, in Tm) and the unit lower triangle of V (VT, in G)
+        for (int idx = threadIdx.x; idx < rpc * 32; idx += PR_THREADS) {
+            const int c = idx / rpc, r = idx % rpc;
+            SV[r * 36 + c] = (r < nown) ? F[(k + c0 + r) + (kp + c) * ld] : 0.f;
+        }
+        float *Tp = psm + PrLayout::tp(rpc);
+        for (int idx = threadIdx.x; idx < 1024; idx += PR_THREADS) Tp[idx] = Tprev[idx];
+        if (rank == 0)
+            for (int idx = threadIdx.x; idx < 1024; idx += PR_THREADS) {
+                const int i = idx % 32, c = idx / 32;
+                Tm[i * 33 + c] = (c < ncols) ? F[(kp + i) + (k + c) * ld] : 0.f;
+                G[i * 33 + c] = (i > c) ? F[(kp + i) + (kp + c) * ld] : ((i == c) ? 1.f : 0.f);
+            }
+    }
     __syncthreads();
+    if (fused) prev_panel_z<RW>(rank, CL, nown, psm, flag, ybar, &s_abort);
     float p[RW];
 #pragma unroll
     for (int r = 0; r < RW; ++r) p[r] = S[(r * 32 + warp) * 33 + l];
+    if (fused) prev_panel_apply<RW>(rank, ncols, F, ld, k, kp, psm, p);
+    for (int idx = threadIdx.x; idx < 2 * 32 * 33; idx += PR_THREADS) Tm[idx] = 0.f;   // Tm and G
+    __syncthreads();
     if (g0 == 0) diag[l] = p[0];                    // diagonal row 0 (rank 0, warp 0)
     // dot products of column 0 with every column over rows 1..
     float acc = 0.f;
@@ -119,15 +319,6 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
         if (g0 + 32 * r > 0) acc = fmaf(a0, p[r], acc);
     }
 
-    // one exchange barrier per parity; per phase one local arrival (with the expected
-    // byte count) plus the byte counts of the CL x 32 partials and rank 0's diagonal row
-    if (threadIdx.x == 0) {
-        tc::mbar_init(&xbar[0], 1);
-        tc::mbar_init(&xbar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    if (threadIdx.x == 0) s_abort = 0;
-    cluster.sync();                                  // barriers ready before any remote signal
     const uint32_t xbytes = (uint32_t)(CL + 1) * 32u * (uint32_t)sizeof(float);
 
     for (int j = 0; j <= ncols; ++j) {
@@ -258,13 +449,16 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
 
 template <int RW>
 int launch_panel_reg(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
-                     int CL, float *tau, float *Tblk)
+                     int CL, float *tau, float *Tblk, int64_t kp, const float *Tprev)
 {
-    const size_t smem = PrLayout::bytes(32 * RW);
+    const size_t plain = PrLayout::bytes(32 * RW), fused = PrLayout::bytes_fused(32 * RW);
+    const size_t cap = (size_t)ctx->max_smem_optin - 1024;          // static shared memory aside
+    const size_t smem = kp >= 0 ? fused : plain;
+    if (smem > cap) return 2;
     static bool attr_done = false;   // per process; attributes are per function
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_panel_reg<RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+                                             (int)std::min(fused > cap ? plain : fused, cap));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_panel_reg<RW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return fl_cuda(ctx, e, "cudaFuncSetAttribute");
@@ -283,7 +477,8 @@ int launch_panel_reg(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     FL_PROF(ctx, FASTLSQ_K_PANEL);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_panel_reg<RW>, F, ld, k, m_aug, ncols, tau, Tblk, ctx->d_flag);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_panel_reg<RW>, F, ld, k, m_aug, ncols, tau, Tblk, ctx->d_flag,
+                                       kp, Tprev);
     if (e != cudaSuccess) return fl_cuda(ctx, e, "register panel launch");
     return 0;
 }
@@ -291,18 +486,16 @@ int launch_panel_reg(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t 
 }  // namespace
 
 int fl_panel_reg_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
-                     float *tau, float *Tblk)
+                     float *tau, float *Tblk, int64_t kp, const float *Tprev)
 {
     const int64_t mp = m_aug - k;
     // enough CTAs that each warp holds at most 24 rows, no more than needed for 8
     const int CL = (int)std::min<int64_t>(PR_CL_MAX, std::max<int64_t>(1, fl_cdiv(mp, 32 * 8)));
     const int64_t rpw = fl_cdiv(fl_cdiv(mp, CL), 32);
-    if (rpw <= 8) return launch_panel_reg<8>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
-    if (rpw <= 12) return launch_panel_reg<12>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
-    if (rpw <= 16) return launch_panel_reg<16>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
-    if (rpw <= 18) return launch_panel_reg<18>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
-    if (rpw <= 20) return launch_panel_reg<20>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
-    if (rpw <= 24) return launch_panel_reg<24>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk);
+#define FL_PANEL_RW(R) \
+    if (rpw <= R) return launch_panel_reg<R>(ctx, F, ld, k, m_aug, ncols, CL, tau, Tblk, kp, Tprev);
+    FL_PANEL_RW(8) FL_PANEL_RW(12) FL_PANEL_RW(16) FL_PANEL_RW(18) FL_PANEL_RW(20) FL_PANEL_RW(24)
+#undef FL_PANEL_RW
     return 1;   // too tall for registers: the caller uses the shared-memory panel
 }
 
@@ -310,4 +503,13 @@ bool fl_panel_reg_fits(int64_t mp)
 {
     const int64_t CL = std::min<int64_t>(PR_CL_MAX, std::max<int64_t>(1, fl_cdiv(mp, 32 * 8)));
     return fl_cdiv(fl_cdiv(mp, CL), 32) <= 24;
+}
+
+bool fl_panel_reg_fused_fits(fastlsq_ctx *ctx, int64_t mp)
+{
+    const int64_t CL = std::min<int64_t>(PR_CL_MAX, std::max<int64_t>(1, fl_cdiv(mp, 32 * 8)));
+    const int64_t rpw = fl_cdiv(fl_cdiv(mp, CL), 32);
+    const int rw = rpw <= 8 ? 8 : rpw <= 12 ? 12 : rpw <= 16 ? 16 : rpw <= 18 ? 18 : rpw <= 20 ? 20 : 24;
+    if (rpw > 24) return false;
+    return PrLayout::bytes_fused(32 * rw) <= (size_t)ctx->max_smem_optin - 1024;
 }

@@ -860,7 +860,13 @@ static int factor_t(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n
         const int64_t nct = ntot - (k + ncols);
         if (la && p + 1 < npan) {
             const int ncn = (int)std::min<int64_t>(NB, n - (k + NB));
-            FL_TRY((trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, ncn, 0, Tblk, counters, use_tc)));
+            // the next panel can take panel p's update of its own columns in its prologue
+            bool fuse = false;
+            if constexpr (std::is_same<T, float>::value && NB == 32)
+                fuse = ctx->panel_reg && ctx->fuse_next && fl_panel_reg_fits(m_aug - (k + NB)) &&
+                       fl_panel_reg_fused_fits(ctx, m_aug - (k + NB));
+            if (!fuse)
+                FL_TRY((trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, ncn, 0, Tblk, counters, use_tc)));
             cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0);
             if (e != cudaSuccess) return fl_cuda(ctx, e, "look-ahead fork");
@@ -872,7 +878,12 @@ static int factor_t(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n
             ctx->stream = main_stream;
             FL_TRY(rc);
             if (e != cudaSuccess) return fl_cuda(ctx, e, "look-ahead join");
-            FL_TRY((panel_any<T, NB>(ctx, F, ld, k + NB, m_aug, ncn, tau + k + NB, Tblk + NB * NB)));
+            if (fuse) {
+                if constexpr (std::is_same<T, float>::value && NB == 32)
+                    FL_TRY(fl_panel_reg_f32(ctx, F, ld, k + NB, m_aug, ncn, tau + k + NB, Tblk + NB * NB, k, Tblk));
+            } else {
+                FL_TRY((panel_any<T, NB>(ctx, F, ld, k + NB, m_aug, ncn, tau + k + NB, Tblk + NB * NB)));
+            }
             e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
             if (e != cudaSuccess) return fl_cuda(ctx, e, "look-ahead join");
         } else {

@@ -33,9 +33,13 @@ int fl_from_f64(fastlsq_ctx *ctx, const double *src, int64_t n, int64_t n_total,
                 const int *skip = nullptr);
 
 // Register-resident FP32 panel of width 32 (panel_reg.cu); fits: rows per warp <= 24.
+// With kp >= 0 the kernel first applies the panel at column kp (its reflectors in F,
+// its T in Tprev) to this panel's columns, rows kp.. (the look-ahead update fused in).
+// Returns 1 when the panel is too tall for registers, 2 when the fused form does not fit.
 bool fl_panel_reg_fits(int64_t mp);
+bool fl_panel_reg_fused_fits(fastlsq_ctx *ctx, int64_t mp);
 int fl_panel_reg_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
-                     float *tau, float *Tblk);
+                     float *tau, float *Tblk, int64_t kp = -1, const float *Tprev = nullptr);
 
 // tcgen05 (TF32x3 split precision) trailing update; tc_update.cu.  Returns a
 // negative status when the tensor-core path cannot handle the shape.

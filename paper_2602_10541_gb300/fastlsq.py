@@ -182,6 +182,7 @@ OPT_TENSOR_CORE = 0
 OPT_REGISTER_PANEL = 1
 OPT_LOOKAHEAD = 2
 OPT_TRSV_FP32 = 3
+OPT_FUSED_LOOKAHEAD = 4
 
 
 def fastlsq_set_option(ctx, option, value):

@@ -4,7 +4,7 @@ The chain theta -> s(x; theta) -> beta = (A^T A + mu I)^{-1} A^T [s; 0] -> u_s =
 beta -> loss = mean (u_s - y)^2 runs through the autograd wrappers over the C ABI
 (FP64 factor, checkpointed).  The bar for dL/dtheta is the accuracy the oracle
 itself reaches against central differences (2e-5 of the largest component; the
-forward map has condition numbers near 1e8, see DESIGN.md); per-kernel pieces with
+forward map has condition numbers near 1e8); per-kernel pieces with
 identical inputs must agree to 1e-10.
 """
 import numpy as np
@@ -168,7 +168,12 @@ def test_inverse_batch_matches_oracle(ctx, prec):
         dev.append(_device_instance(w, y, w.theta0))
     fl.fastlsq_inverse_batch(ctx, dev, fl.Op([[2, 0], [0, 2]], [-1.0, -1.0]), 4, prec=prec, mu=mu)
     torch.cuda.synchronize()
+    # the loss is a mean of squared sensor residuals u_s - y of the size of the noise
+    # (1e-3) while u_s is O(1): an absolute error delta in u_s moves the loss by about
+    # 2 delta / 1e-3 relative.  FP64 solves (delta ~ 1e-12) meet 1e-6; MIXED solves are
+    # refined by CGLS to delta ~ 1e-9 (as in the Newton steps), hence 1e-5
+    loss_bar = 1e-6 if prec == fl.PREC_FP64 else 1e-5
     for ref, d in zip(cases, dev):
-        assert abs(d["loss"].item() - ref["loss"]) <= 1e-6 * ref["loss"]
+        assert abs(d["loss"].item() - ref["loss"]) <= loss_bar * ref["loss"]
         g = d["dtheta"].cpu().numpy()
         assert np.abs(g - ref["dtheta"]).max() <= 2e-5 * np.abs(ref["dtheta"]).max(), (g, ref["dtheta"])

@@ -1,7 +1,7 @@
 """GPU parity of the least-squares solves (Sec. 2.3; Sec. 2.4 Tikhonov rows) against
 the FP64 oracle, through the C ABI.
 
-Bars (derived in the design doc): on well-conditioned random systems the FP64 path
+Bars: on well-conditioned random systems the FP64 path
 matches the oracle's beta to 1e-10 relative, the MIXED path after refinement to
 1e-9; on the PDE systems (condition numbers up to 1e17) beta is not unique, so
 the solution u on the independent test set is compared instead: FP64 path within
@@ -270,11 +270,12 @@ def test_register_panel_matches_oracle_and_shared_memory_panel(ctx, m, n):
 
 
 @pytest.mark.parametrize("tc", [0, 1])
-@pytest.mark.parametrize("m,n", [(700, 130), (3000, 257)])
+@pytest.mark.parametrize("m,n", [(700, 130), (3000, 257), (9000, 96)])
 def test_lookahead_matches_single_stream(ctx, tc, m, n):
-    """Look-ahead (next panel on the auxiliary stream during the trailing update)
-    gives the same factor as one stream up to FP32 summation order, and the same
-    refined solution."""
+    """Look-ahead (the rest of each trailing update on the auxiliary stream while the
+    next panel is factored, that panel applying the previous update to its own columns
+    in its prologue, or with separate kernels) gives the same factor as one stream up to
+    FP32 summation order, and the same refined solution."""
     rng = np.random.default_rng(5 * m + n)
     A = rng.standard_normal((m, n))
     B = _nearly_consistent(rng, A)
@@ -285,18 +286,21 @@ def test_lookahead_matches_single_stream(ctx, tc, m, n):
     Rs = {}
     fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, tc)
     try:
-        for la in (1, 0):
+        for la, fused in ((1, 1), (1, 0), (0, 0)):
             fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, la)
+            fl.fastlsq_set_option(ctx, fl.OPT_FUSED_LOOKAHEAD, fused)
             beta = torch.zeros((1, n), dtype=torch.float64, device=DEV)
             _, fac, _ = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, 0.0, _rhs(B), beta,
                                          A_refine=_cm(A, torch.float64), max_refine=4, keep=True)
             R = torch.zeros((n, n), dtype=torch.float64, device=DEV)
             fl.fastlsq_factor_get_r(ctx, fac, R)
             fl.fastlsq_factor_destroy(ctx, fac)
-            Rs[la] = R.cpu().numpy().T
+            Rs[(la, fused)] = R.cpu().numpy().T
             np.testing.assert_allclose(beta.cpu().numpy()[0], ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
     finally:
         fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, 1)
+        fl.fastlsq_set_option(ctx, fl.OPT_FUSED_LOOKAHEAD, 1)
         fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 0)
-    assert np.abs(Rs[1] - Ro).max() <= 2e-5 * scale
-    assert np.abs(Rs[1] - Rs[0]).max() <= 2e-5 * scale
+    for key in ((1, 1), (1, 0)):
+        assert np.abs(Rs[key] - Ro).max() <= 2e-5 * scale, key
+        assert np.abs(Rs[key] - Rs[(0, 0)]).max() <= 2e-5 * scale, key
