@@ -373,6 +373,19 @@ def main():
                 "peak_source": peak_src}
     breakdown = {k: {"launches_per_step": v[0] / 2.0, "ms_per_step": v[1] / 2.0}
                  for k, v in prof_pre.items() if v[0]}
+    # the same roofline arithmetic for every class of the pre-pass (two steps), for context
+    for kname, v in breakdown.items():
+        ukind, amount = _algorithmic(kname, m, n, m + (n if w.mu > 0 else 0), nb, 1, args.refine, elem)
+        if amount <= 0 or v["ms_per_step"] <= 0:
+            continue
+        if ukind == "flops":
+            pk = 2.0 * 128 * nsm * sm_mhz * 1e6 / 1e12 if kname == "trail_simt" else peaks.get("bf16_tflops", 1900.0) * 0.5
+            v["roofline"] = {"achieved": amount / (v["ms_per_step"] / 1e3) / 1e12, "peak": pk, "unit": "TFLOP/s",
+                             "bound": "alu" if kname == "trail_simt" else "tensor"}
+        else:
+            v["roofline"] = {"achieved": amount / (v["ms_per_step"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "bound": "hbm"}
+        v["roofline"]["frac"] = v["roofline"]["achieved"] / v["roofline"]["peak"]
 
     # accuracy: mixed result vs the plain FP64 GPU path and vs the exact solution
     u_mixed = solver.u_test()

@@ -32,6 +32,7 @@ constexpr int PR_NB = 32;
 constexpr int PR_THREADS = 1024;
 constexpr int PR_CL_MAX = 16;
 constexpr int PR_XLD = 36;                   // row stride of the exchange buffer (16-byte rows)
+constexpr int PR_STAGE_U = 8;                // loads in flight per thread when staging
 constexpr long long PR_SPIN = 2000000000ll;  // SM cycles (about a second) before an exchange wait gives up
 
 // shared::cluster address of the same shared-memory object in CTA `rank`
@@ -121,6 +122,21 @@ __device__ __forceinline__ void prev_panel_z(int rank, int CL, int nown, float *
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) y[a][b] = 0.f;
+        if (rank == 0)          // the 32 rows above the slice: rows rg and rg + 16 of VT, CT
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = rg + 16 * h;
+                float va[4], cc[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) va[a] = G[i * 33 + 4 * lb + a];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) cc[b] = Tm[i * 33 + 4 * cb + b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) y[a][b] = fmaf(va[a], cc[b], y[a][b]);
+            }
+#pragma unroll 4
         for (int r = rg; r < nown; r += 16) {
             const float4 v = *reinterpret_cast<const float4 *>(SV + r * 36 + 4 * lb);
             const float va[4] = {v.x, v.y, v.z, v.w};
@@ -132,12 +148,6 @@ __device__ __forceinline__ void prev_panel_z(int rank, int CL, int nown, float *
 #pragma unroll
                 for (int b = 0; b < 4; ++b) y[a][b] = fmaf(va[a], cc[b], y[a][b]);
         }
-        if (rank == 0 && rg == 0)
-            for (int i = 0; i < 32; ++i)
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) y[a][b] = fmaf(G[i * 33 + 4 * lb + a], Tm[i * 33 + 4 * cb + b], y[a][b]);
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1)
 #pragma unroll
@@ -280,18 +290,39 @@ k_panel_reg(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
 
     // stage the slice through shared memory (coalesced along the columns of F)
     const bool fused = kp >= 0;
-    for (int idx = threadIdx.x; idx < rpc * 32; idx += PR_THREADS) {
-        const int c = idx / rpc, r = idx % rpc;
-        S[r * 33 + c] = (r < nown && c < ncols) ? F[(k + c0 + r) + (k + c) * ld] : 0.f;
+    // (loads in groups of PR_STAGE_U per thread, so that many are in flight at once)
+#pragma unroll 1
+    for (int base = threadIdx.x; base < rpc * 32; base += PR_THREADS * PR_STAGE_U) {
+        float v[PR_STAGE_U];
+#pragma unroll
+        for (int u = 0; u < PR_STAGE_U; ++u) {
+            const int idx = base + u * PR_THREADS, c = idx / rpc, r = idx % rpc;
+            v[u] = (idx < rpc * 32 && r < nown && c < ncols) ? F[(k + c0 + r) + (k + c) * ld] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < PR_STAGE_U; ++u) {
+            const int idx = base + u * PR_THREADS;
+            if (idx < rpc * 32) S[(idx % rpc) * 33 + idx / rpc] = v[u];
+        }
     }
     float *SV = psm + PrLayout::sv(rpc);
     if (fused) {
         // the previous panel's reflectors (columns kp..kp+31) on this CTA's rows, which
         // lie below that panel's diagonal block; its T; on rank 0 the 32 rows kp..kp+31
         // of this panel's columns (CT, in Tm) and the unit lower triangle of V (VT, in G)
-        for (int idx = threadIdx.x; idx < rpc * 32; idx += PR_THREADS) {
-            const int c = idx / rpc, r = idx % rpc;
-            SV[r * 36 + c] = (r < nown) ? F[(k + c0 + r) + (kp + c) * ld] : 0.f;
+#pragma unroll 1
+        for (int base = threadIdx.x; base < rpc * 32; base += PR_THREADS * PR_STAGE_U) {
+            float v[PR_STAGE_U];
+#pragma unroll
+            for (int u = 0; u < PR_STAGE_U; ++u) {
+                const int idx = base + u * PR_THREADS, c = idx / rpc, r = idx % rpc;
+                v[u] = (idx < rpc * 32 && r < nown) ? F[(k + c0 + r) + (kp + c) * ld] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < PR_STAGE_U; ++u) {
+                const int idx = base + u * PR_THREADS;
+                if (idx < rpc * 32) SV[(idx % rpc) * 36 + idx / rpc] = v[u];
+            }
         }
         float *Tp = psm + PrLayout::tp(rpc);
         for (int idx = threadIdx.x; idx < 1024; idx += PR_THREADS) Tp[idx] = Tprev[idx];
