@@ -70,6 +70,18 @@ def _dist_env():
     return rank, world, local
 
 
+def _job_throughput(total_ms, steps, world, device=None):
+    """Whole-job solves/s over `world` replicas: each rank solved `steps` instances in
+    total_ms of device time; the job takes as long as its slowest rank (max over ranks)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1e3), total_ms
+
+
 def run_reference(args):
     rank, world, _ = _dist_env()
     if rank != 0:
@@ -326,11 +338,7 @@ def main():
     prof = fl.fastlsq_profile_read(ctx)
     fl.fastlsq_profile_enable(ctx, [])
     launches = sum(v[0] for v in prof.values())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value, total_ms = _job_throughput(total_ms, args.steps, world, dev)
 
     # roofline of the dominant kernel class (events recorded in the timed region)
     dom_launches, dom_ms = prof[dominant]
