@@ -111,6 +111,17 @@ k_apply_q_cluster(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n,
     const uint32_t xbytes = (uint32_t)CS * AQC_NB * (uint32_t)sizeof(T);
     T vn[AQC_NB];
     if (npan > 0) aq_load_v(F, ld, n, (int64_t)(transpose ? 0 : npan - 1) * AQC_NB, i, row_ok, vn);
+    // the T block of the next panel, prefetched like V (entries tid + h blockDim, blockDim >= 128)
+    T tn[8];
+    auto load_t = [&](int pp) {
+        const T *Tb = Tall + (int64_t)pp * AQC_NB * AQC_NB;        // T(q, l) at q + 32 l
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int idx = threadIdx.x + h * blockDim.x;
+            tn[h] = (idx < AQC_NB * AQC_NB) ? Tb[idx] : T(0);
+        }
+    };
+    if (npan > 0) load_t(transpose ? 0 : npan - 1);
     for (int step = 0; step < npan; ++step) {
         const int p = transpose ? step : npan - 1 - step;
         const int par = step & 1;
@@ -122,11 +133,12 @@ k_apply_q_cluster(const T *__restrict__ F, int64_t ld, int64_t m_aug, int64_t n,
             aq_load_v(F, ld, n, (int64_t)pn * AQC_NB, i, row_ok, vn);
         }
         if (threadIdx.x == 0) aq_expect_tx(&xbar[par], xbytes);
-        {
-            const T *Tb = Tall + (int64_t)p * AQC_NB * AQC_NB;     // T(q, l) at q + 32 l
-            for (int idx = threadIdx.x; idx < AQC_NB * AQC_NB; idx += blockDim.x)
-                sT[par][idx % AQC_NB][idx / AQC_NB] = Tb[idx];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int idx = threadIdx.x + h * blockDim.x;
+            if (idx < AQC_NB * AQC_NB) sT[par][idx % AQC_NB][idx / AQC_NB] = tn[h];
         }
+        if (step + 1 < npan) load_t(transpose ? step + 1 : npan - 2 - step);
         // s_l: warp partials, then the CTA's partial sent to every rank
         T prod[AQC_NB];
 #pragma unroll
@@ -178,7 +190,7 @@ int fl_apply_q_cluster(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, 
     if (nb != AQC_NB) return 1;
     int CS = AQC_CS_MAX;
     while (CS > 1 && fl_cdiv(m_aug, CS) < 128) CS >>= 1;
-    const int64_t threads = fl_round_up(fl_cdiv(m_aug, CS), 32);
+    const int64_t threads = std::max<int64_t>(128, fl_round_up(fl_cdiv(m_aug, CS), 32));   // >= 128: T prefetch
     if (threads > AQC_MAX_THREADS) return 1;
     static bool attr_done = false;
     if (!attr_done) {
