@@ -269,6 +269,8 @@ def main():
                     help="1: FP32 substitution in the triangular solves of classical refinement")
     ap.add_argument("--no-extras", action="store_true", help="skip the Newton and inverse-problem timings")
     ap.add_argument("--inverse-instances", type=int, default=32)
+    ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
+                    help="assemble the FP64 operator on a side stream during the factorisation")
     ap.add_argument("--lookahead", type=int, default=1, choices=[0, 1],
                     help="1: factor the next panel on a second stream during the trailing update")
     args = ap.parse_args()
@@ -299,7 +301,8 @@ def main():
     # each rank solves its own instance (replicas: the solve does not shard)
     w = wl.helmholtz2d(seed_offset=rank)
     dp = pl.upload(w, dev)
-    solver = pl.LinearSolver(ctx, dp, prec=fl.PREC_MIXED, max_refine=args.refine)
+    solver = pl.LinearSolver(ctx, dp, prec=fl.PREC_MIXED, max_refine=args.refine,
+                             overlap=bool(args.overlap))
     m, n = w.n_rows, w.n_feat
 
     for _ in range(args.warmup):

@@ -102,6 +102,15 @@ FASTLSQ_API int fastlsq_create(fastlsq_ctx **ctx, int device, void *cuda_stream)
 FASTLSQ_API int fastlsq_destroy(fastlsq_ctx *ctx);
 /* Replace the stream the context queues work on. */
 FASTLSQ_API int fastlsq_set_stream(fastlsq_ctx *ctx, void *cuda_stream);
+/* Make every later call on this context that reads a factor's FP64 operator
+ * A_refine (the refinement residuals of fastlsq_lstsq / fastlsq_factor_solve, the
+ * PCG products and A v of fastlsq_backward) first make the context's stream wait
+ * for `cuda_event` (a cudaEvent_t), as cudaStreamWaitEvent does at that point:
+ * the wait binds to the event's latest record made before the call.  The FP64
+ * operator can then be assembled on another stream while the FP32 factorisation
+ * runs; only the refinement waits for it.  NULL removes the wait.  The event is
+ * not owned by the context and must outlive its use. */
+FASTLSQ_API int fastlsq_set_refine_event(fastlsq_ctx *ctx, void *cuda_event);
 /* Message describing the last error on this context ("" if none). Owned by ctx. */
 FASTLSQ_API const char *fastlsq_last_error(const fastlsq_ctx *ctx);
 /* Synchronise the context's stream and return the first device-side error flag

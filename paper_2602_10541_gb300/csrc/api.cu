@@ -266,6 +266,21 @@ extern "C" int fastlsq_set_stream(fastlsq_ctx *ctx, void *stream)
     return 0;
 }
 
+extern "C" int fastlsq_set_refine_event(fastlsq_ctx *ctx, void *event)
+{
+    if (!ctx) return FASTLSQ_ERR_INVALID;
+    ctx->refine_event = (cudaEvent_t)event;
+    return 0;
+}
+
+// the stream waits for the caller's event before the first read of A_refine
+static int wait_refine(fastlsq_ctx *ctx)
+{
+    if (!ctx->refine_event) return 0;
+    cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->refine_event, 0);
+    return e == cudaSuccess ? 0 : fl_cuda(ctx, e, "wait for the FP64 operator");
+}
+
 extern "C" int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value)
 {
     if (!ctx) return FASTLSQ_ERR_INVALID;
@@ -430,6 +445,7 @@ static int solve_one(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, i
     // classical refinement; CGLS needs R^{-1} as a fixed linear operator: FP64
     const int a32 = (mode == FASTLSQ_REFINE_CLASSICAL) ? ctx->trsv32 : 0;
     FL_TRY(fl_trsv_grid<T>(ctx, F, f->ld, n, y64, beta64, work, 0, nullptr, a32));
+    if ((max_refine > 0 || norms_dev) && f->A_refine) FL_TRY(wait_refine(ctx));
     if (mode == FASTLSQ_REFINE_CGLS) {
         if (max_refine > 0) return fl_refine_cgls(ctx, f, rhs64, beta64, max_refine, tol, norms_dev);
         return 0;
@@ -650,6 +666,7 @@ extern "C" int fastlsq_backward(fastlsq_ctx *ctx, const fastlsq_factor *f, const
         FL_TRY(backward_t<double>(ctx, f, grad_beta, v));
     } else if (max_iter > 0) {
         if (!f->A_refine) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "backward: PCG needs the FP64 operator");
+        FL_TRY(wait_refine(ctx));
         FL_TRY(fl_normal_pcg(ctx, f, grad_beta, v, max_iter, tol));
     } else {
         FL_TRY(backward_t<float>(ctx, f, grad_beta, v));
@@ -659,6 +676,7 @@ extern "C" int fastlsq_backward(fastlsq_ctx *ctx, const fastlsq_factor *f, const
         int64_t ld = A_op ? ld_op : f->ld_refine;
         if (!Aop) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "backward: no FP64 operator for A v");
         if (ld < f->m) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "backward: ld_op");
+        if (!A_op) FL_TRY(wait_refine(ctx));
         FL_TRY(fl_matvec64(ctx, Aop, ld, f->m, f->n, v, grad_rhs));
     }
     return 0;

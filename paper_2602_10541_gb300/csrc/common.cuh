@@ -74,6 +74,7 @@ struct fastlsq_ctx {
     int trsv32 = 1;                 // FP32 arithmetic in the triangular solves of classical refinement
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t refine_event = nullptr;   // waited on before reads of A_refine (caller's)
     // Cody-Waite split of 2 pi for the FP32 argument reduction (host-derived)
     float cw2pi[3] = {0.f, 0.f, 0.f};
     fl_prof_state prof;

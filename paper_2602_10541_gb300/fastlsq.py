@@ -73,6 +73,7 @@ _SIGNATURES = {
     "fastlsq_create": [ctypes.POINTER(_vp), ctypes.c_int, _vp],
     "fastlsq_destroy": [_vp],
     "fastlsq_set_stream": [_vp, _vp],
+    "fastlsq_set_refine_event": [_vp, _vp],
     "fastlsq_last_error": [_vp],
     "fastlsq_sync": [_vp],
     "fastlsq_set_option": [_vp, ctypes.c_int, ctypes.c_int],
@@ -187,6 +188,19 @@ OPT_FUSED_LOOKAHEAD = 4
 
 def fastlsq_set_option(ctx, option, value):
     return ctx.check(ctx.lib.fastlsq_set_option(ctx.handle, int(option), int(value)))
+
+
+def fastlsq_set_stream(ctx, stream):
+    """Queue the context's later work on `stream` (a torch.cuda.Stream)."""
+    ctx.stream = stream
+    return ctx.check(ctx.lib.fastlsq_set_stream(ctx.handle, ctypes.c_void_p(stream.cuda_stream)))
+
+
+def fastlsq_set_refine_event(ctx, event):
+    """Reads of a factor's FP64 operator wait for `event` (a torch.cuda.Event that has
+    been recorded; None removes the wait)."""
+    h = None if event is None else ctypes.c_void_p(event.cuda_event)
+    return ctx.check(ctx.lib.fastlsq_set_refine_event(ctx.handle, h))
 
 
 def colmajor(n_rows, n_cols, dtype, device, ld=None, zero=False):

@@ -39,7 +39,7 @@ class LinearSolver:
     allocated once so that repeated solves (and CUDA-graph capture) reuse them."""
 
     def __init__(self, ctx: fl.Context, dp: DeviceProblem, prec=fl.PREC_MIXED, max_refine=2,
-                 mu=None, refine_mode=fl.REFINE_CLASSICAL, refine_tol=1e-10):
+                 mu=None, refine_mode=fl.REFINE_CLASSICAL, refine_tol=1e-10, overlap=True):
         self.ctx, self.dp, self.prec, self.max_refine = ctx, dp, prec, max_refine
         self.refine_mode, self.refine_tol = refine_mode, refine_tol
         w = dp.w
@@ -51,16 +51,37 @@ class LinearSolver:
         self.rhs = torch.empty((1, self.A64.shape[1]), dtype=torch.float64, device=dev)
         self.beta = torch.zeros((1, self.n), dtype=torch.float64, device=dev)
         self.stats = None
+        # MIXED: the FP64 operator, read only by the refinement, is assembled on a
+        # side stream while the FP32 factorisation runs
+        self.side = None
+        if overlap and self.A32 is not None:
+            lo, _ = torch.cuda.Stream.priority_range()
+            self.side = torch.cuda.Stream(device=dev, priority=lo)
+            self.ev_fp32 = torch.cuda.Event()
+            self.ev_fp64 = torch.cuda.Event()
+
+    def _assemble_one(self, dtype, A):
+        ctx, dp, w = self.ctx, self.dp, self.dp.w
+        fl.fastlsq_assemble(ctx, dtype, dp.x_int, dp.op_int, 1.0, dp.W, dp.b, w.scale, A, 0)
+        fl.fastlsq_assemble(ctx, dtype, dp.x_bc, dp.op_bc, w.lam_bc, dp.W, dp.b, w.scale, A, w.n_int)
 
     def assemble(self):
-        ctx, dp, w = self.ctx, self.dp, self.dp.w
-        targets = [(fl.F64, self.A64)]
         if self.A32 is not None:
-            targets.insert(0, (fl.F32, self.A32))
-        for dtype, A in targets:
-            fl.fastlsq_assemble(ctx, dtype, dp.x_int, dp.op_int, 1.0, dp.W, dp.b, w.scale, A, 0)
-            fl.fastlsq_assemble(ctx, dtype, dp.x_bc, dp.op_bc, w.lam_bc, dp.W, dp.b, w.scale, A,
-                                w.n_int)
+            self._assemble_one(fl.F32, self.A32)
+        if self.side is None:
+            self._assemble_one(fl.F64, self.A64)
+            return
+        # the side stream starts after the FP32 assembly (the context's column
+        # prefactors are free again, and the previous solve's reads of A64 are done)
+        main = self.ctx.stream
+        self.ev_fp32.record(main)
+        self.side.wait_event(self.ev_fp32)
+        fl.fastlsq_set_stream(self.ctx, self.side)
+        try:
+            self._assemble_one(fl.F64, self.A64)
+        finally:
+            fl.fastlsq_set_stream(self.ctx, main)
+        self.ev_fp64.record(self.side)
 
     def build_rhs(self):
         ctx, dp, w = self.ctx, self.dp, self.dp.w
@@ -71,11 +92,17 @@ class LinearSolver:
 
     def solve(self, stats=False, keep=False):
         A = self.A32 if self.prec == fl.PREC_MIXED else self.A64
-        rc, fac, st = fl.fastlsq_lstsq(self.ctx, self.prec, A, self.m, self.mu, self.rhs, self.beta,
-                                       A_refine=self.A64,
-                                       max_refine=self.max_refine if self.prec == fl.PREC_MIXED else 0,
-                                       keep=keep, stats=stats, refine_mode=self.refine_mode,
-                                       refine_tol=self.refine_tol)
+        if self.side is not None:     # the waits are queued by the call itself
+            fl.fastlsq_set_refine_event(self.ctx, self.ev_fp64)
+        try:
+            rc, fac, st = fl.fastlsq_lstsq(self.ctx, self.prec, A, self.m, self.mu, self.rhs, self.beta,
+                                           A_refine=self.A64,
+                                           max_refine=self.max_refine if self.prec == fl.PREC_MIXED else 0,
+                                           keep=keep, stats=stats, refine_mode=self.refine_mode,
+                                           refine_tol=self.refine_tol)
+        finally:
+            if self.side is not None:
+                fl.fastlsq_set_refine_event(self.ctx, None)
         self.stats = st
         return fac
 
