@@ -414,10 +414,14 @@ typedef enum {
                                       refinement (MIXED) substitute in FP32 arithmetic
                                       (backward stable like the FP32 factor); 0: FP64
                                       arithmetic.  CGLS and the adjoint always use FP64. */
-    FASTLSQ_OPT_FUSED_LOOKAHEAD = 4 /* 1 (default): with look-ahead, the register panel
+    FASTLSQ_OPT_FUSED_LOOKAHEAD = 4,/* 1 (default): with look-ahead, the register panel
                                       applies the previous panel's update to its own columns
                                       in its prologue (no separate kernels for it) where its
                                       shared memory allows; 0: separate update kernels */
+    FASTLSQ_OPT_ROW_PANEL = 5       /* 1 (default): the register panel keeps one or two
+                                      panel rows per thread (updates without shuffles),
+                                      where the panel has at most 768 rows per CTA; 0: one
+                                      column per lane (32 rows per thread at most) */
 } fastlsq_option;
 
 /* Set a context option (see fastlsq_option).  Returns 0 or -1 for an unknown option. */

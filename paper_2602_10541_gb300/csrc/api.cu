@@ -296,6 +296,10 @@ extern "C" int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value)
         ctx->lookahead = value ? 1 : 0;
         return 0;
     }
+    if (option == FASTLSQ_OPT_ROW_PANEL) {
+        ctx->row_panel = value ? 1 : 0;
+        return 0;
+    }
     if (option == FASTLSQ_OPT_FUSED_LOOKAHEAD) {
         ctx->fuse_next = value ? 1 : 0;
         return 0;

@@ -69,6 +69,7 @@ struct fastlsq_ctx {
     void *d_grid_bar = nullptr;     // grid barrier state (count, generation) of this context
     int use_tensor_core = 0;        // tcgen05 trailing updates for the MIXED path
     int panel_reg = 1;              // register-resident FP32 panel (width 32) where it fits
+    int row_panel = 1;              // of which the row layout (one or two rows per thread)
     int lookahead = 1;              // panel p+1 beside the rest of panel p's update (on aux_stream)
     int fuse_next = 1;              // look-ahead: next panel applies the previous update itself
     int trsv32 = 1;                 // FP32 arithmetic in the triangular solves of classical refinement

@@ -519,6 +519,10 @@ int launch_panel_reg(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t 
 int fl_panel_reg_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
                      float *tau, float *Tblk, int64_t kp, const float *Tprev)
 {
+    if (ctx->row_panel) {
+        const int rc = fl_panel_row_f32(ctx, F, ld, k, m_aug, ncols, tau, Tblk, kp, Tprev);
+        if (rc != 1 && rc != 2) return rc;
+    }
     const int64_t mp = m_aug - k;
     // enough CTAs that each warp holds at most 24 rows, no more than needed for 8
     const int CL = (int)std::min<int64_t>(PR_CL_MAX, std::max<int64_t>(1, fl_cdiv(mp, 32 * 8)));
@@ -538,6 +542,7 @@ bool fl_panel_reg_fits(int64_t mp)
 
 bool fl_panel_reg_fused_fits(fastlsq_ctx *ctx, int64_t mp)
 {
+    if (ctx->row_panel && fl_panel_row_fits(ctx, mp, true)) return true;
     const int64_t CL = std::min<int64_t>(PR_CL_MAX, std::max<int64_t>(1, fl_cdiv(mp, 32 * 8)));
     const int64_t rpw = fl_cdiv(fl_cdiv(mp, CL), 32);
     const int rw = rpw <= 8 ? 8 : rpw <= 12 ? 12 : rpw <= 16 ? 16 : rpw <= 18 ? 18 : rpw <= 20 ? 20 : 24;

@@ -184,6 +184,7 @@ OPT_REGISTER_PANEL = 1
 OPT_LOOKAHEAD = 2
 OPT_TRSV_FP32 = 3
 OPT_FUSED_LOOKAHEAD = 4
+OPT_ROW_PANEL = 5
 
 
 def fastlsq_set_option(ctx, option, value):

@@ -288,6 +288,43 @@ def test_register_panel_matches_oracle_and_shared_memory_panel(ctx, m, n):
     assert np.abs(Rs[1] - Rs[0]).max() <= 2e-5 * scale
 
 
+# (m, n): one CTA, two rows per thread (300); 16 CTAs of one row per thread, ragged
+# last panel (1000, 70); two rows per thread (5000); the 768-row limit (12288); past it
+# (12300: another kernel); the headline panel height with the fused look-ahead (11264);
+# a height whose fused form does not fit (11800: separate look-ahead kernels)
+@pytest.mark.parametrize("m,n", [(300, 40), (1000, 70), (5000, 100), (12288, 40), (12300, 40),
+                                 (11264, 96), (11800, 72)])
+def test_row_panel_matches_oracle_and_column_panel(ctx, m, n):
+    """The register panel with one or two rows per thread against the oracle's
+    Householder R and the one-column-per-lane kernel; the refined solution with
+    look-ahead against the oracle's least-squares solution."""
+    rng = np.random.default_rng(11 * m + n)
+    A = rng.standard_normal((m, n))
+    B = _nearly_consistent(rng, A)
+    ref = oracle.lstsq(A, B).reshape(-1)
+    Rs = {}
+    for row in (1, 0):
+        fl.fastlsq_set_option(ctx, fl.OPT_ROW_PANEL, row)
+        try:
+            beta = torch.zeros((1, n), dtype=torch.float64, device=DEV)
+            _, fac, st = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, 0.0, _rhs(B), beta,
+                                          A_refine=_cm(A, torch.float64), max_refine=4, keep=True,
+                                          stats=True)
+        finally:
+            fl.fastlsq_set_option(ctx, fl.OPT_ROW_PANEL, 1)
+        assert st.nb == 32 and st.status == 0
+        R = torch.zeros((n, n), dtype=torch.float64, device=DEV)
+        fl.fastlsq_factor_get_r(ctx, fac, R)
+        fl.fastlsq_factor_destroy(ctx, fac)
+        Rs[row] = R.cpu().numpy().T
+        np.testing.assert_allclose(beta.cpu().numpy()[0], ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+    packed, _ = oracle.qr(A)
+    Ro = np.triu(packed[:n])
+    scale = np.abs(Ro).max()
+    assert np.abs(Rs[1] - Ro).max() <= 2e-5 * scale
+    assert np.abs(Rs[1] - Rs[0]).max() <= 2e-5 * scale
+
+
 @pytest.mark.parametrize("tc", [0, 1])
 @pytest.mark.parametrize("m,n", [(700, 130), (3000, 257), (9000, 96)])
 def test_lookahead_matches_single_stream(ctx, tc, m, n):
