@@ -27,9 +27,17 @@ namespace {
 
 struct KryScalars {
     double gamma, gamma0, qq, alpha, beta;
+    double obj;      // CGLS: ||r||^2 (from r.r, less each step's decrease alpha gamma);
+                     // PCG: the objective decrease accumulated so far
     int done;
     int iters;
+    int accumulate;  // 1: obj accumulates (PCG), 0: obj is what remains (CGLS)
 };
+
+// A step that changes the objective by less than this fraction of it is below the
+// resolution of FP64: iterating further only lets the recurrence drift (kappa ~ 1e8
+// systems stall at a normal-equations residual far above any relative tolerance)
+constexpr double KRY_STALL = 1e-15;
 
 constexpr int KV_ROWS = 256;
 constexpr int KV_COLS = 128;
@@ -117,21 +125,25 @@ k_kry_dot_partial(const double *__restrict__ a, const double *__restrict__ b, in
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-enum { OP_INIT = 0, OP_ALPHA = 1, OP_BETA = 2, OP_NORM = 3 };
+enum { OP_INIT = 0, OP_ALPHA = 1, OP_BETA = 2, OP_NORM = 3, OP_OBJ = 4, OP_INIT_ACC = 5 };
 
 // sums the dot partials in a fixed order and advances the scalar recurrence
 __global__ void k_kry_scalar(const double *__restrict__ part, int nblk, KryScalars *st, int op,
                              double tol, double *norm_out)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (op != OP_INIT && st->done) return;
+    if (op != OP_INIT && op != OP_INIT_ACC && op != OP_OBJ && st->done) return;
     double d = 0.0;
     for (int b = 0; b < nblk; ++b) d += part[b];
-    if (op == OP_INIT) {
+    if (op == OP_INIT || op == OP_INIT_ACC) {
         st->gamma = d;
         st->gamma0 = d;
         st->iters = 0;
         st->done = !(d > 0.0) || !isfinite(d);
+        st->accumulate = (op == OP_INIT_ACC);
+        st->obj = 0.0;
+    } else if (op == OP_OBJ) {
+        st->obj = d;
     } else if (op == OP_ALPHA) {
         st->qq = d;
         if (!(d > 0.0) || !isfinite(d)) {
@@ -141,10 +153,15 @@ __global__ void k_kry_scalar(const double *__restrict__ part, int nblk, KryScala
             st->alpha = st->gamma / d;
         }
     } else if (op == OP_BETA) {
+        // this step lowered the objective by alpha gamma (CGLS: ||r||^2; PCG: twice the
+        // quadratic form's decrease)
+        const double dec = st->alpha * st->gamma;
+        st->obj = st->accumulate ? st->obj + dec : st->obj - dec;
         st->beta = d / st->gamma;
         st->gamma = d;
         st->iters += 1;
         if (!(d > tol * tol * st->gamma0) || !isfinite(d)) st->done = 1;
+        if (!(dec > KRY_STALL * st->obj)) st->done = 1;   // (an estimate <= 0 never fires)
     } else if (op == OP_NORM) {
         if (norm_out) *norm_out = sqrt(d);
     }
@@ -574,6 +591,7 @@ int refine_cgls_t(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs64
     k_kry_copy_sub<<<gn, 256, 0, ctx->stream>>>(B.p, B.s, nullptr, n);
     ctx->prof.launches[FASTLSQ_K_KRYLOV] += 1;
     FL_TRY(kry_dot(ctx, B.s, B.s, n, B, OP_INIT, tol, nullptr, nullptr));
+    FL_TRY(kry_dot(ctx, B.r, B.r, m_aug, B, OP_OBJ, tol, nullptr, nullptr));
     for (int it = 0; it < max_iter; ++it) {
         FL_TRY(kry_prec<T>(ctx, f, B.p, B.t, 0, B));                 // t = R^{-1} p
         FL_TRY(kry_mv(ctx, f, B.t, nullptr, B.q, B, B.st));           // q = A~ t
@@ -610,7 +628,7 @@ int normal_pcg_t(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *c, dou
     FL_TRY(kry_prec<T>(ctx, f, B.t, B.s, 0, B));
     k_kry_copy_sub<<<gn, 256, 0, ctx->stream>>>(B.p, B.s, nullptr, n);
     ctx->prof.launches[FASTLSQ_K_KRYLOV] += 2;
-    FL_TRY(kry_dot(ctx, B.z, B.s, n, B, OP_INIT, tol, nullptr, nullptr));
+    FL_TRY(kry_dot(ctx, B.z, B.s, n, B, OP_INIT_ACC, tol, nullptr, nullptr));
     for (int it = 0; it < max_iter; ++it) {
         FL_TRY(kry_mv(ctx, f, B.p, nullptr, B.q, B, B.st));
         FL_TRY(kry_mvt(ctx, f, B.q, B.r, B.st));                      // w = A~^T A~ p (in r)
