@@ -269,6 +269,8 @@ def main():
                     help="1: FP32 substitution in the triangular solves of classical refinement")
     ap.add_argument("--no-extras", action="store_true", help="skip the Newton and inverse-problem timings")
     ap.add_argument("--inverse-instances", type=int, default=32)
+    ap.add_argument("--instances", type=int, default=4,
+                    help="independent full-size solves per step, each on its own stream")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
                     help="assemble the FP64 operator on a side stream during the factorisation")
     ap.add_argument("--lookahead", type=int, default=1, choices=[0, 1],
@@ -292,27 +294,37 @@ def main():
     dev = f"cuda:{local}"
     if not _build.up_to_date():
         _build.build()
-    ctx = fl.Context(local)
-    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, args.tensor_core)
-    fl.fastlsq_set_option(ctx, fl.OPT_TRSV_FP32, args.trsv_fp32)
-    fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, args.lookahead)
     stream = torch.cuda.current_stream(local)
-
-    # each rank solves its own instance (replicas: the solve does not shard)
-    w = wl.helmholtz2d(seed_offset=rank)
-    dp = pl.upload(w, dev)
-    solver = pl.LinearSolver(ctx, dp, prec=fl.PREC_MIXED, max_refine=args.refine,
-                             overlap=bool(args.overlap))
+    # each rank solves its own instances (replicas: a solve does not shard); a step is
+    # args.instances independent full-size solves, one context and stream each
+    _, hi_prio = torch.cuda.Stream.priority_range()
+    B = max(1, args.instances)
+    ctxs, solvers = [], []
+    for i in range(B):
+        c = fl.Context(local, stream=torch.cuda.Stream(device=local, priority=hi_prio))
+        fl.fastlsq_set_option(c, fl.OPT_TENSOR_CORE, args.tensor_core)
+        fl.fastlsq_set_option(c, fl.OPT_TRSV_FP32, args.trsv_fp32)
+        fl.fastlsq_set_option(c, fl.OPT_LOOKAHEAD, args.lookahead)
+        wi = wl.helmholtz2d(seed_offset=rank * B + i)
+        with torch.cuda.stream(c.stream):
+            dpi = pl.upload(wi, dev)
+            solvers.append(pl.LinearSolver(c, dpi, prec=fl.PREC_MIXED, max_refine=args.refine,
+                                           overlap=bool(args.overlap)))
+        ctxs.append(c)
+    torch.cuda.synchronize()
+    ctx, solver = ctxs[0], solvers[0]          # instance 0: profiles, accuracy, assembly alone
+    dp, w = solver.dp, solver.dp.w
+    batch = pl.ConcurrentSolves(solvers)
     m, n = w.n_rows, w.n_feat
 
     for _ in range(args.warmup):
-        solver.step()
+        batch.step(stream)
     torch.cuda.synchronize()
 
-    # which kernel class dominates (pre-pass with events on every class)
+    # which kernel class dominates (pre-pass with events on every class of instance 0)
     fl.fastlsq_profile_enable(ctx, None)
     for _ in range(2):
-        solver.step()
+        batch.step(stream)
     prof_pre = fl.fastlsq_profile_read(ctx)
     dominant = max(prof_pre, key=lambda k: prof_pre[k][1])
     fl.fastlsq_profile_enable(ctx, [dominant])     # only the dominant class inside the timed region
@@ -329,7 +341,7 @@ def main():
     for i in range(args.steps):
         flush.fill_(float(i))                         # evict L2 (outside the step events)
         ev_s[i].record(stream)
-        solver.step()
+        batch.step(stream)
         ev_e[i].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -340,13 +352,15 @@ def main():
     total_ms = sum(step_ms)
     prof = fl.fastlsq_profile_read(ctx)
     fl.fastlsq_profile_enable(ctx, [])
-    launches = sum(v[0] for v in prof.values())
+    launches = B * sum(v[0] for v in prof.values())     # instances run the same launches
     value, total_ms = _job_throughput(total_ms, args.steps, world, dev)
+    value *= B
 
     # roofline of the dominant kernel class (events recorded in the timed region)
     dom_launches, dom_ms = prof[dominant]
     elem = 4
-    solver.solve(stats=True)
+    with torch.cuda.stream(ctx.stream):
+        solver.solve(stats=True)
     solve_stats = solver.stats
     nb = solve_stats.nb
     unit_kind, per_step = _algorithmic(dominant, m, n, m + (n if w.mu > 0 else 0), nb, 1,
@@ -399,6 +413,10 @@ def main():
         v["roofline"]["frac"] = v["roofline"]["achieved"] / v["roofline"]["peak"]
 
     # accuracy: mixed result vs the plain FP64 GPU path and vs the exact solution
+    # (instance 0, on the default stream from here on except in the end-to-end batch)
+    torch.cuda.synchronize()
+    s0 = ctx.stream
+    fl.fastlsq_set_stream(ctx, stream)
     u_mixed = solver.u_test()
     s64 = pl.LinearSolver(ctx, dp, prec=fl.PREC_FP64)
     torch.cuda.synchronize()
@@ -431,25 +449,29 @@ def main():
                 "hbm_write_gbs": 4 * asm_rate / 1e9, "hbm_frac": 4 * asm_rate / 1e9 / hbm,
                 "sfu_bound_gentries_per_s": None}
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: every instance's inputs from
+    # pinned host memory, its solution back, each step
+    torch.cuda.synchronize()
+    fl.fastlsq_set_stream(ctx, s0)
     pin = lambda t: t.detach().cpu().pin_memory()
-    h_x_int, h_x_bc, h_W, h_b = pin(dp.x_int), pin(dp.x_bc), pin(dp.W), pin(dp.b)
-    h_beta = torch.empty_like(solver.beta, device="cpu").pin_memory()
-    bi = sum(t.numel() * t.element_size() for t in (h_x_int, h_x_bc, h_W, h_b))
-    bo = h_beta.numel() * h_beta.element_size()
+    h_in = [[pin(t) for t in (sv.dp.x_int, sv.dp.x_bc, sv.dp.W, sv.dp.b)] for sv in solvers]
+    h_beta = [torch.empty_like(sv.beta, device="cpu").pin_memory() for sv in solvers]
+    bi = sum(t.numel() * t.element_size() for h in h_in for t in h)
+    bo = sum(t.numel() * t.element_size() for t in h_beta)
     e2e_steps = max(3, args.steps // 2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        dp.x_int.copy_(h_x_int, non_blocking=True)
-        dp.x_bc.copy_(h_x_bc, non_blocking=True)
-        dp.W.copy_(h_W, non_blocking=True)
-        dp.b.copy_(h_b, non_blocking=True)
-        solver.step()
-        h_beta.copy_(solver.beta, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        for sv, h in zip(solvers, h_in):
+            for d, hh in zip((sv.dp.x_int, sv.dp.x_bc, sv.dp.W, sv.dp.b), h):
+                d.copy_(hh, non_blocking=True)
+        batch.step(stream)
+        for sv, hb in zip(solvers, h_beta):
+            hb.copy_(sv.beta, non_blocking=True)
+        stream.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": bi,
+    fl.fastlsq_set_stream(ctx, stream)
+    e2e = {"value": world * B * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": bi,
            "d2h_bytes_per_step": bo}
 
     cpu = None
@@ -477,12 +499,16 @@ def main():
                                         f"{args.refine} refinement steps",
                            "tensor_core_updates": bool(solve_stats.tensor_core),
                            "panel_nb": nb, "l2": "flushed between steps (256 MiB write outside the step events)",
+                           "instances_per_step": B,
+                           "concurrency": (f"{B} independent instances (seeds) of the workload per step, "
+                                           "each on its own context and stream"),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
                 "clocks": clk, "accuracy": accuracy, "assembly": assembly, "kernels": breakdown,
                 "other_rows": extras, "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
-    ctx.close()
+    for c in ctxs:
+        c.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -12,7 +12,8 @@
 //   3. every warp adds the ranks' sums in the same fixed order (all threads of all
 //      ranks hold bit-identical reflector scalars) and forms w_l = tau v_j^T a_l;
 //   4. each thread updates its own row: no shuffles and no shared memory in the
-//      update, the row is in the thread's registers.
+//      update, the row is in the thread's registers (column j picked by selects, so
+//      that the column loop stays a loop).
 // The sums for l < j are the Gram entries v_l^T v_j of the reflectors (less the
 // pivot row's part), from which T = (I + D striu(V^T V))^{-1} D, D = diag(tau), is
 // formed at the end by a triangular inverse (one lane per column of T).
@@ -363,9 +364,10 @@ k_panel_row(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
     if (threadIdx.x < 32) tauv[threadIdx.x] = 0.f;
     const uint32_t xbytes = (uint32_t)(CL + 1) * 32u * (uint32_t)sizeof(float);
 
-#pragma unroll
-    for (int j = 0; j < RP_NB; ++j) {
-        if (j >= ncols) break;                       // uniform
+    // (a loop, not unrolled: 32 unrolled steps do not fit in the instruction caches;
+    // the register column j is picked by selects)
+#pragma unroll 1
+    for (int j = 0; j < ncols; ++j) {
         const int par = j & 1;
         float *xb = xbuf + par * (RP_CL_MAX + 1) * RP_XLD;
         if (threadIdx.x == 0) rp_expect_tx(&xbar[par], xbytes);
@@ -377,7 +379,10 @@ k_panel_row(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
             for (int l = 0; l < RP_NB; ++l) P[l] = 0.f;
 #pragma unroll
             for (int h = 0; h < RPT; ++h) {
-                const float aj = (live[h] && g[h] > j) ? a[h][j] : 0.f;
+                float ajx = 0.f;
+#pragma unroll
+                for (int l = 0; l < RP_NB; ++l) ajx = (l == j) ? a[h][l] : ajx;
+                const float aj = (live[h] && g[h] > j) ? ajx : 0.f;
 #pragma unroll
                 for (int l = 0; l < RP_NB; ++l) P[l] = fmaf(aj, a[h][l], P[l]);
             }
@@ -452,18 +457,19 @@ k_panel_row(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
             w[4 * i + 2] = t.z;
             w[4 * i + 3] = t.w;
         }
+        // rows below the pivot: v = a_j inv into column j, a_l -= w_l v; the pivot row:
+        // beta into column j, a_l -= w_l; rows above: unchanged (w_l = 0 for l <= j)
 #pragma unroll
         for (int h = 0; h < RPT; ++h) {
-            if (live[h] && g[h] > j) {
-                const float v = a[h][j] * inv;
-                a[h][j] = v;
+            const bool below = live[h] && g[h] > j, piv = g[h] == j;
+            float ajx = 0.f;
 #pragma unroll
-                for (int l = j + 1; l < RP_NB; ++l) a[h][l] = fmaf(-w[l], v, a[h][l]);
-            } else if (g[h] == j) {
-                a[h][j] = beta;
+            for (int l = 0; l < RP_NB; ++l) ajx = (l == j) ? a[h][l] : ajx;
+            const float v = ajx * inv;
+            const float vv = below ? v : (piv ? 1.f : 0.f);
+            const float nj = below ? v : (piv ? beta : ajx);
 #pragma unroll
-                for (int l = j + 1; l < RP_NB; ++l) a[h][l] -= w[l];
-            }
+            for (int l = 0; l < RP_NB; ++l) a[h][l] = (l == j) ? nj : fmaf(-w[l], vv, a[h][l]);
         }
     }
 

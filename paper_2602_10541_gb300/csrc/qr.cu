@@ -826,11 +826,14 @@ static int panel_any(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m_au
 // trailing columns [k + ncols + coff, k + ncols + coff + nct) updated by panel k
 template <typename T, int NB>
 static int trailing_any(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
-                        int64_t nct, int64_t coff, const T *Tblk, int *counters, int use_tc)
+                        int64_t nct, int64_t coff, int64_t ntot, const T *Tblk, int *counters, int use_tc)
 {
     if (nct <= 0) return 0;
     if constexpr (std::is_same<T, float>::value) {
-        if (use_tc) return fl_trailing_tc_f32(ctx, F, ld, k, m_aug, ncols, NB, nct, coff, Tblk, counters);
+        if (use_tc) {
+            const int rc = fl_trailing_tc_f32(ctx, F, ld, k, m_aug, ncols, NB, nct, coff, ntot, Tblk, counters);
+            if (rc != 1) return rc;
+        }
     }
     return launch_trailing<T, NB>(ctx, F, ld, k, m_aug, ncols, nct, coff, Tblk, counters);
 }
@@ -866,13 +869,13 @@ static int factor_t(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n
                 fuse = ctx->panel_reg && ctx->fuse_next && fl_panel_reg_fits(m_aug - (k + NB)) &&
                        fl_panel_reg_fused_fits(ctx, m_aug - (k + NB));
             if (!fuse)
-                FL_TRY((trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, ncn, 0, Tblk, counters, use_tc)));
+                FL_TRY((trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, ncn, 0, ntot, Tblk, counters, use_tc)));
             cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0);
             if (e != cudaSuccess) return fl_cuda(ctx, e, "look-ahead fork");
             cudaStream_t main_stream = ctx->stream;
             ctx->stream = ctx->aux_stream;
-            const int rc = trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, nct - ncn, ncn, Tblk, counters,
+            const int rc = trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, nct - ncn, ncn, ntot, Tblk, counters,
                                                use_tc);
             if (rc == 0) e = cudaEventRecord(ctx->ev_join, ctx->aux_stream);
             ctx->stream = main_stream;
@@ -887,7 +890,7 @@ static int factor_t(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n
             e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
             if (e != cudaSuccess) return fl_cuda(ctx, e, "look-ahead join");
         } else {
-            FL_TRY((trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, nct, 0, Tblk, counters, use_tc)));
+            FL_TRY((trailing_any<T, NB>(ctx, F, ld, k, m_aug, ncols, nct, 0, ntot, Tblk, counters, use_tc)));
         }
     }
     return 0;

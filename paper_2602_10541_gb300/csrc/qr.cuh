@@ -46,10 +46,11 @@ bool fl_panel_reg_fused_fits(fastlsq_ctx *ctx, int64_t mp);
 int fl_panel_reg_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
                      float *tau, float *Tblk, int64_t kp = -1, const float *Tprev = nullptr);
 
-// tcgen05 (TF32x3 split precision) trailing update; tc_update.cu.  Returns a
-// negative status when the tensor-core path cannot handle the shape.
+// tcgen05 (TF32x3 split precision) trailing update fed by TMA; tc_update.cu.  ntot:
+// columns of F.  Returns 1 when the tensor-core path does not take the shape (panel
+// width other than 32, unaligned factor), the caller then runs the SIMT update.
 int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
-                       int nb, int64_t nct, int64_t coff, const float *Tblk, int *counters);
+                       int nb, int64_t nct, int64_t coff, int64_t ntot, const float *Tblk, int *counters);
 
 // Krylov refinement with the factor's R as preconditioner (refine.cu)
 int fl_refine_cgls(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs64, double *beta64,

@@ -1,18 +1,27 @@
 // Trailing update of the blocked Householder QR on the tcgen05 tensor cores, in
 // split TF32x3 precision with FP32 accumulation in TMEM:
 //   x = hi + lo (hi = tf32 rounding of x, lo = x - hi), a*b ~ ah*bh + ah*bl + al*bh.
-// For panel k with Householder block V (m_p x nb, unit lower trapezoidal) and
-// compact-WY factor T:
-//   k_tc_y      : Y^T = C^T V over a split of the rows (M = 128 columns of C,
-//                 N = nb, K = rows in chunks of 32), partial sums per split;
-//   k_tc_update : C -= V Z with Z = T^T sum_s Y_s (M = 128 rows, N = 128 columns,
-//                 K = nb).
-// Operands are staged into shared memory by the warps (coalesced 128-byte loads),
-// split into hi/lo and written in the K-major 128-byte-swizzle layout; one thread
-// issues the MMAs and commits them to an mbarrier; the epilogue reads TMEM with
-// tcgen05.ld.  Every mbarrier wait is bounded: on timeout the kernel raises the
-// device flag, waits once more (bounded) and frees its TMEM.
+// For panel k with Householder block V (m_p x 32, unit lower trapezoidal) and
+// compact-WY factor T, C -= V (T^T (V^T C)) in two kernels:
+//   k_tcy : Y^T = C^T V over a split of the rows (MMA M = 128 columns of C, N = 32,
+//           K = rows in chunks of 32).  A ring of 4 stages is filled by TMA: a C chunk
+//           (32 rows x 128 columns) and a V chunk (32 rows x 32 columns) land in the
+//           K-major 128-byte-swizzled layout the MMA reads (the column-major factor is
+//           already K-major for both).  All threads split a landed stage into hi/lo in
+//           place; one thread issues the 12 MMAs of the chunk and commits them to the
+//           stage's "empty" barrier, after which the stage is refilled.  The last CTA of
+//           each column tile forms Z = T^T Y and writes it as the update's operand
+//           image (Z^T hi and lo, swizzled).
+//   k_tcu : C -= V Z on 128 x 128 tiles (M = 128 rows, N = 128 columns, K = 32): the C
+//           tile arrives by TMA and the Z image by one bulk copy while the threads stage
+//           V (hi/lo, swizzled); the epilogue subtracts D (tcgen05.ld) from the staged C
+//           and stores coalesced along the rows.
+// Every mbarrier wait is bounded: on timeout the kernel raises the device flag, waits
+// (bounded) for its copies and MMAs in flight, frees its TMEM and returns.
+#include <cuda.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "qr.cuh"
@@ -21,19 +30,19 @@
 
 namespace {
 
-constexpr int TCY_COLS = 128;      // columns of C per CTA (M of the MMA)
-constexpr int TCY_CHUNK = 32;      // rows per K-chunk
-constexpr int TCU_ROWS = 128;      // rows of C per CTA in the update (M)
-constexpr int TCU_COLS = 128;      // columns of C per CTA in the update (N)
-constexpr long long TC_SPIN = 2000000000ll;   // SM cycles (about a second) before an mbarrier wait gives up
+constexpr int TY_C = 128;          // columns of C per k_tcy CTA (MMA M)
+constexpr int TY_K = 32;           // rows per chunk (MMA K per stage)
+constexpr int TY_STAGES = 4;
+constexpr int TU_R = 128;          // rows per k_tcu tile (MMA M)
+constexpr int TU_C = 128;          // columns per k_tcu tile (MMA N)
+constexpr long long TC_SPIN = 2000000000ll;   // SM cycles (about a second) before a wait gives up
 
-__device__ __forceinline__ float v_at_f(const float *__restrict__ F, int64_t ld, int64_t k, int64_t i,
-                                        int l, int ncols)
-{
-    if (l >= ncols || i < l) return 0.f;
-    if (i == l) return 1.f;
-    return F[(k + i) + (k + l) * ld];
-}
+constexpr uint32_t TY_A = TY_C * 128;            // one 128 x 32 fp32 operand tile (bytes)
+constexpr uint32_t TY_B = 32 * 128;              // one 32 x 32 fp32 operand tile
+constexpr uint32_t TY_STAGE = 2 * TY_A + 2 * TY_B;
+constexpr uint32_t TU_CT = TU_R * TU_C * 4;      // staged C tile
+constexpr uint32_t TU_V = TU_R * 128;            // V hi (or lo)
+constexpr uint32_t TU_Z = TU_C * 128;            // Z^T hi (or lo)
 
 __device__ __forceinline__ unsigned char *align1024(unsigned char *p)
 {
@@ -41,278 +50,407 @@ __device__ __forceinline__ unsigned char *align1024(unsigned char *p)
     return p + ((1024u - (a & 1023u)) & 1023u);
 }
 
+__device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                 :: "r"(tc::smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// 2-D tile of the factor (x = row, y = column) into shared memory, counted on bar
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                 "[%0], [%1, {%2, %3}], [%4];\n"
+                 :: "r"(tc::smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y),
+                    "r"(tc::smem_addr(bar))
+                 : "memory");
+}
+
+// contiguous global -> shared copy (16-byte aligned, multiple of 16 bytes)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 :: "r"(tc::smem_addr(dst)), "l"(src), "r"(bytes), "r"(tc::smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ float v_at(const float *__restrict__ F, int64_t ld, int64_t k, int64_t i, int l,
+                                      int ncols)
+{
+    if (l >= ncols || i < l) return 0.f;
+    if (i == l) return 1.f;
+    return F[(k + i) + (k + l) * ld];
+}
+
+__device__ __forceinline__ float4 split4(float4 &x)
+{
+    float4 lo;
+    tc::split_tf32(x.x, x.x, lo.x);
+    tc::split_tf32(x.y, x.y, lo.y);
+    tc::split_tf32(x.z, x.z, lo.z);
+    tc::split_tf32(x.w, x.w, lo.w);
+    return lo;
+}
+
+}  // namespace
+
+namespace {
+
 // ---------------------------------------------------------------------------
 // Y partials: Ypart[split][l][c] = sum over the split's rows of V(i, l) C(i, c)
 // ---------------------------------------------------------------------------
-template <int NB>
 __global__ void __launch_bounds__(128, 1)
-k_tc_y(const float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct, int64_t coff,
-       int64_t rows_per_split, float *__restrict__ Ypart, float *__restrict__ Z,
-       const float *__restrict__ Tblk, int *__restrict__ counters, int *flag)
+k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMap mV, int64_t k, int ncols,
+      int64_t nct, int64_t coff, int64_t mp, int64_t rows_per_split, float *__restrict__ Ypart,
+      float *__restrict__ Zimg, const float *__restrict__ Tblk, int *__restrict__ counters, int *flag)
 {
-    constexpr int N = NB < 16 ? 16 : NB;                 // MMA N (multiple of 16 for M = 128)
-    constexpr uint32_t A_BYTES = TCY_COLS * 128;         // 128 rows x 32 fp32
-    constexpr uint32_t B_BYTES = N * 128;
-    constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES; // hi/lo of A and B
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = align1024(smem_raw);
-    __shared__ uint64_t bar[2];
+    __shared__ uint64_t full[TY_STAGES], empty[TY_STAGES];
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t mp = m - k;
-    const int64_t cbase = (int64_t)blockIdx.x * TCY_COLS;
+    const int64_t cbase = (int64_t)blockIdx.x * TY_C;
     const int64_t rs0 = (int64_t)blockIdx.y * rows_per_split;
     const int64_t rs1 = fl_min64(mp, rs0 + rows_per_split);
-    const int nchunks = (int)fl_max64(0, fl_cdiv_dev(rs1 - rs0, TCY_CHUNK));
+    const int nchunks = (int)fl_max64(0, fl_cdiv_dev(rs1 - rs0, TY_K));
 
     if (warp == 0) tc::tmem_alloc(&tmem_slot, 32);
     if (threadIdx.x == 0) {
-        tc::mbar_init(&bar[0], 1);
-        tc::mbar_init(&bar[1], 1);
+        for (int s = 0; s < TY_STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
-    constexpr uint32_t idesc = tc::idesc_tf32(128, N);
-    bool ok = true;
-    uint32_t uses[2] = {0u, 0u};
+    constexpr uint32_t idesc = tc::idesc_tf32(TY_C, 32);
+    // TMA coordinates: x = row of the factor, y = column
+    const int x0 = (int)(k + rs0), yc = (int)(k + ncols + coff + cbase), yv = (int)k;
+    // thread 0's record of the last chunk loaded into / committed from each stage
+    int last_load[TY_STAGES], last_commit[TY_STAGES];
+#pragma unroll
+    for (int s = 0; s < TY_STAGES; ++s) last_load[s] = last_commit[s] = -1;
+    auto issue = [&](int ch) {
+        const int s = ch % TY_STAGES;
+        unsigned char *A = base + s * TY_STAGE, *B = A + 2 * TY_A;
+        expect_tx(&full[s], TY_A + TY_B);
+        tma_load_2d(A, &mC, x0 + ch * TY_K, yc, &full[s]);
+        tma_load_2d(B, &mV, x0 + ch * TY_K, yv, &full[s]);
+        last_load[s] = ch;
+    };
+    if (threadIdx.x == 0)
+        for (int ch = 0; ch < nchunks && ch < TY_STAGES; ++ch) issue(ch);
 
-    for (int ch = 0; ch < nchunks && ok; ++ch) {
-        const int buf = ch & 1;
-        unsigned char *Ah = base + buf * STAGE, *Al = Ah + A_BYTES, *Bh = Al + A_BYTES, *Bl = Bh + B_BYTES;
-        if (ch >= 2) {   // the MMAs that read this buffer two chunks ago must be done
-            const bool w = tc::mbar_wait(&bar[buf], (uses[buf] - 1) & 1, TC_SPIN);
-            ok = __syncthreads_and(w) != 0;          // uniform decision for the whole CTA
-            if (!ok) break;
-            tc::fence_after_sync();
-        }
-        const int64_t r0 = rs0 + (int64_t)ch * TCY_CHUNK;
-        const int64_t i = r0 + lane;
-        const bool iv = i < rs1;
-        // A = C^T: smem row = column c (32 per warp), k = row within the chunk
-#pragma unroll 8
-        for (int cl = 0; cl < 32; ++cl) {
-            const int cr = warp * 32 + cl;
-            const int64_t c = cbase + cr;
-            const float x = (iv && c < nct) ? F[(k + i) + (k + ncols + coff + c) * ld] : 0.f;
-            float h, lo;
-            tc::split_tf32(x, h, lo);
-            const uint32_t off = tc::sw128_offset(cr, lane);
-            *reinterpret_cast<float *>(Ah + off) = h;
-            *reinterpret_cast<float *>(Al + off) = lo;
-        }
-        // B = V: smem row = l, k = row within the chunk
-        for (int l = warp; l < N; l += 4) {
-            const float x = (iv && l < NB) ? v_at_f(F, ld, k, i, l, ncols) : 0.f;
-            float h, lo;
-            tc::split_tf32(x, h, lo);
-            const uint32_t off = tc::sw128_offset(l, lane);
-            *reinterpret_cast<float *>(Bh + off) = h;
-            *reinterpret_cast<float *>(Bl + off) = lo;
+    bool ok = true;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int s = ch % TY_STAGES;
+        const uint32_t ph = (uint32_t)(ch / TY_STAGES) & 1u;
+        unsigned char *Ah = base + s * TY_STAGE, *Al = Ah + TY_A, *Bh = Al + TY_A, *Bl = Bh + TY_B;
+        const bool landed = tc::mbar_wait(&full[s], ph, TC_SPIN);
+        if (landed) {
+            // C chunk: split in place (hi) and into the lo tile
+            for (int q = threadIdx.x; q < (int)(TY_A / 16); q += 128) {
+                float4 x = reinterpret_cast<const float4 *>(Ah)[q];
+                const float4 lo = split4(x);
+                reinterpret_cast<float4 *>(Ah)[q] = x;
+                reinterpret_cast<float4 *>(Al)[q] = lo;
+            }
+            // V chunk: smem row l = column l of V, 16-byte pieces of 4 consecutive rows;
+            // zero past the panel's columns, unit lower triangle on its top rows
+            const int64_t r0 = rs0 + (int64_t)ch * TY_K;
+            for (int q = threadIdx.x; q < (int)(TY_B / 16); q += 128) {
+                float4 x = reinterpret_cast<const float4 *>(Bh)[q];
+                const int l = q >> 3;
+                const int64_t i0 = r0 + (((q & 7) ^ (l & 7)) << 2);
+                if (l >= ncols) {
+                    x = make_float4(0.f, 0.f, 0.f, 0.f);
+                } else if (i0 <= l) {
+                    x.x = (i0 + 0 < l) ? 0.f : ((i0 + 0 == l) ? 1.f : x.x);
+                    x.y = (i0 + 1 < l) ? 0.f : ((i0 + 1 == l) ? 1.f : x.y);
+                    x.z = (i0 + 2 < l) ? 0.f : ((i0 + 2 == l) ? 1.f : x.z);
+                    x.w = (i0 + 3 < l) ? 0.f : ((i0 + 3 == l) ? 1.f : x.w);
+                }
+                const float4 lo = split4(x);
+                reinterpret_cast<float4 *>(Bh)[q] = x;
+                reinterpret_cast<float4 *>(Bl)[q] = lo;
+            }
         }
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
-        __syncthreads();
+        ok = __syncthreads_and(landed) != 0;
         tc::fence_after_sync();
+        if (!ok) break;
         if (threadIdx.x == 0) {
             const uint64_t dAh = tc::smem_desc_sw128(Ah), dAl = tc::smem_desc_sw128(Al);
             const uint64_t dBh = tc::smem_desc_sw128(Bh), dBl = tc::smem_desc_sw128(Bl);
 #pragma unroll
-            for (int ks = 0; ks < TCY_CHUNK / 8; ++ks) {
+            for (int ks = 0; ks < TY_K / 8; ++ks) {
                 const uint64_t o = (uint64_t)(ks * 32) >> 4;      // 8 tf32 = 32 bytes along K
                 tc::mma_tf32(tmem, dAh + o, dBh + o, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
                 tc::mma_tf32(tmem, dAh + o, dBl + o, idesc, 1u);
                 tc::mma_tf32(tmem, dAl + o, dBh + o, idesc, 1u);
             }
-            tc::mma_commit(&bar[buf]);
+            tc::mma_commit(&empty[s]);
+            last_commit[s] = ch;
+            // refill the stage once its MMAs have read it
+            if (ch + TY_STAGES < nchunks && tc::mbar_wait(&empty[s], ph, TC_SPIN)) issue(ch + TY_STAGES);
         }
-        uses[buf] += 1;
     }
-    // wait for the last chunk's MMAs (its commit completes after all earlier ones)
-    if (ok && nchunks > 0) {
-        const int lb = (nchunks - 1) & 1;
-        ok = tc::mbar_wait(&bar[lb], (uses[lb] - 1) & 1, TC_SPIN);
+    // the last commit arrives after every earlier MMA of the thread has completed
+    bool done = true;
+    if (threadIdx.x == 0 && ok && nchunks > 0) {
+        const int lc = nchunks - 1;
+        done = tc::mbar_wait(&empty[lc % TY_STAGES], (uint32_t)(lc / TY_STAGES) & 1u, TC_SPIN);
     }
-    ok = __syncthreads_and(ok) != 0;
-    if (!ok) {
-        if (threadIdx.x == 0) atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
-        for (int b2 = 0; b2 < 2; ++b2)
-            if (uses[b2]) tc::mbar_wait(&bar[b2], (uses[b2] - 1) & 1, TC_SPIN);
-    }
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok && done) != 0;
     tc::fence_after_sync();
-    if (ok) {
-        // D: TMEM lane = column c (warp w holds lanes 32w..32w+31), TMEM column = l
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
+            // let the copies and MMAs in flight finish before the CTA leaves (bounded)
+            for (int s = 0; s < TY_STAGES; ++s) {
+                if (last_load[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)(last_load[s] / TY_STAGES) & 1u, TC_SPIN);
+                if (last_commit[s] >= 0)
+                    tc::mbar_wait(&empty[s], (uint32_t)(last_commit[s] / TY_STAGES) & 1u, TC_SPIN);
+            }
+        }
+    } else {
+        // D: TMEM lane = column c (warp w: lanes 32 w ..), TMEM column = l
         const int64_t c = cbase + warp * 32 + lane;
 #pragma unroll
-        for (int lc = 0; lc < N; lc += 16) {
+        for (int lc = 0; lc < 32; lc += 16) {
             float v[16];
-            if (nchunks > 0) tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + lc, v);
-            else
+            if (nchunks > 0) {
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + lc, v);
+            } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = 0.f;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int l = lc + j;
-                if (l < NB && c < nct) Ypart[((int64_t)blockIdx.y * NB + l) * nct + c] = v[j];
             }
+            if (c < nct)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) Ypart[((int64_t)blockIdx.y * 32 + lc + j) * nct + c] = v[j];
         }
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 32);
     if (ok)   // uniform; the stage buffers are free once the last MMA has completed
-        trail_finish_z<float, NB, TCY_COLS, 128>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Z,
-                                                 counters + blockIdx.x, reinterpret_cast<float *>(base));
+        trail_finish_z<float, 32, TY_C, 128, true>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Zimg,
+                                                   counters + blockIdx.x, reinterpret_cast<float *>(base));
 }
 
 // ---------------------------------------------------------------------------
-// C(i, c) -= sum_l V(i, l) Z(l, c), Z = T^T Y
+// C(i, c) -= sum_l V(i, l) Z(l, c) on a 128 x 128 tile
 // ---------------------------------------------------------------------------
-template <int NB>
 __global__ void __launch_bounds__(128, 1)
-k_tc_update(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct, int64_t coff,
-            const float *__restrict__ Z, int *flag)
+k_tcu(const __grid_constant__ CUtensorMap mT, float *__restrict__ F, int64_t ld, int64_t k, int ncols,
+      int64_t nct, int64_t coff, int64_t mp, const float *__restrict__ Zimg, int *flag)
 {
-    constexpr uint32_t A_BYTES = TCU_ROWS * 128;     // 128 rows x 32 fp32 (K = l, padded to 32)
-    constexpr uint32_t B_BYTES = TCU_COLS * 128;     // 128 columns x 32 fp32
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = align1024(smem_raw);
-    unsigned char *Ah = base, *Al = Ah + A_BYTES, *Bh = Al + A_BYTES, *Bl = Bh + B_BYTES;
-    __shared__ uint64_t bar;
+    unsigned char *Vh = base, *Vl = Vh + TU_V, *Zh = Vl + TU_V, *Zl = Zh + TU_Z;
+    const float *Cs = reinterpret_cast<const float *>(Zl + TU_Z);   // [c][r], r contiguous
+    __shared__ uint64_t bar_c, bar_z, bar_m;
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t mp = m - k;
-    const int64_t rbase = (int64_t)blockIdx.x * TCU_ROWS;
-    const int64_t cbase = (int64_t)blockIdx.y * TCU_COLS;
+    const int64_t rbase = (int64_t)blockIdx.x * TU_R;
+    const int64_t cbase = (int64_t)blockIdx.y * TU_C;
 
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, TCU_COLS);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, TU_C);
     if (threadIdx.x == 0) {
-        tc::mbar_init(&bar, 1);
+        tc::mbar_init(&bar_c, 1);
+        tc::mbar_init(&bar_z, 1);
+        tc::mbar_init(&bar_m, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    // B = Z: thread t owns column c = cbase + t; smem row t, k = l
-    {
-        const int64_t c = cbase + threadIdx.x;
-        float zl[NB];
-#pragma unroll
-        for (int l = 0; l < NB; ++l) zl[l] = (c < nct) ? Z[(int64_t)l * nct + c] : 0.f;
-#pragma unroll
-        for (int l = 0; l < 32; ++l) {
-            const float z = (l < NB) ? zl[l] : 0.f;
-            float h, lo;
-            tc::split_tf32(z, h, lo);
-            const uint32_t off = tc::sw128_offset(threadIdx.x, l);
-            *reinterpret_cast<float *>(Bh + off) = h;
-            *reinterpret_cast<float *>(Bl + off) = lo;
-        }
-    }
-    // A = V rows: warp w stages rows 32w..32w+31, lane = row, loop over l (coalesced)
-    {
-        const int r = warp * 32 + lane;
-        const int64_t i = rbase + r;
-#pragma unroll 4
-        for (int l = 0; l < 32; ++l) {
-            const float x = (i < mp && l < NB) ? v_at_f(F, ld, k, i, l, ncols) : 0.f;
-            float h, lo;
-            tc::split_tf32(x, h, lo);
-            const uint32_t off = tc::sw128_offset(r, l);
-            *reinterpret_cast<float *>(Ah + off) = h;
-            *reinterpret_cast<float *>(Al + off) = lo;
-        }
-    }
-    tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     if (threadIdx.x == 0) {
-        constexpr uint32_t idesc = tc::idesc_tf32(TCU_ROWS, TCU_COLS);
-        const uint64_t dAh = tc::smem_desc_sw128(Ah), dAl = tc::smem_desc_sw128(Al);
-        const uint64_t dBh = tc::smem_desc_sw128(Bh), dBl = tc::smem_desc_sw128(Bl);
+        // the C tile (rows k + rbase .., columns of the update) and the tile's Z image
+        expect_tx(&bar_c, TU_CT);
+        tma_load_2d(const_cast<float *>(Cs), &mT, (int)(k + rbase), (int)(k + ncols + coff + cbase), &bar_c);
+        expect_tx(&bar_z, 2 * TU_Z);
+        bulk_load(Zh, Zimg + (cbase / TU_C) * (2 * TU_C * 32), 2 * TU_Z, &bar_z);
+    }
+    // A = V rows: thread = row, one column l at a time (coalesced along the rows)
+    {
+        const int r = threadIdx.x;
+        const int64_t i = rbase + r;
+        float x[32];
 #pragma unroll
-        for (int ks = 0; ks < (NB + 7) / 8; ++ks) {
+        for (int l = 0; l < 32; ++l) x[l] = (i < mp) ? v_at(F, ld, k, i, l, ncols) : 0.f;
+#pragma unroll
+        for (int l = 0; l < 32; ++l) {
+            float h, lo;
+            tc::split_tf32(x[l], h, lo);
+            const uint32_t off = tc::sw128_offset((uint32_t)r, (uint32_t)l);
+            *reinterpret_cast<float *>(Vh + off) = h;
+            *reinterpret_cast<float *>(Vl + off) = lo;
+        }
+    }
+    tc::fence_proxy_async_smem();
+    const bool wz = tc::mbar_wait(&bar_z, 0u, TC_SPIN);
+    tc::fence_before_sync();
+    bool ok = __syncthreads_and(wz) != 0;
+    tc::fence_after_sync();
+    if (ok && threadIdx.x == 0) {
+        constexpr uint32_t idesc = tc::idesc_tf32(TU_R, TU_C);
+        const uint64_t dAh = tc::smem_desc_sw128(Vh), dAl = tc::smem_desc_sw128(Vl);
+        const uint64_t dBh = tc::smem_desc_sw128(Zh), dBl = tc::smem_desc_sw128(Zl);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
             const uint64_t o = (uint64_t)(ks * 32) >> 4;
             tc::mma_tf32(tmem, dAh + o, dBh + o, idesc, ks > 0 ? 1u : 0u);
             tc::mma_tf32(tmem, dAh + o, dBl + o, idesc, 1u);
             tc::mma_tf32(tmem, dAl + o, dBh + o, idesc, 1u);
         }
-        tc::mma_commit(&bar);
+        tc::mma_commit(&bar_m);
     }
-    bool ok = __syncthreads_and(tc::mbar_wait(&bar, 0, TC_SPIN)) != 0;
-    if (!ok) {
-        if (threadIdx.x == 0) atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
-        tc::mbar_wait(&bar, 0, TC_SPIN);
-    }
+    const bool wm = ok ? tc::mbar_wait(&bar_m, 0u, TC_SPIN) : true;
+    const bool wc = tc::mbar_wait(&bar_c, 0u, TC_SPIN);
+    const bool issued = ok;
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok && wm && wc) != 0;
     tc::fence_after_sync();
-    if (ok) {
-        // D: TMEM lane = row (warp w: rows 32w..), column = c; C -= D, coalesced along rows
-        const int64_t i = rbase + warp * 32 + lane;
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
+            tc::mbar_wait(&bar_c, 0u, TC_SPIN);
+            tc::mbar_wait(&bar_z, 0u, TC_SPIN);
+            if (issued) tc::mbar_wait(&bar_m, 0u, TC_SPIN);
+        }
+    } else {
+        // D: TMEM lane = row (warp w: rows 32 w ..), column = c; C - D stored along the rows
+        const int r = warp * 32 + lane;
+        const int64_t i = rbase + r;
 #pragma unroll 1
-        for (int cc = 0; cc < TCU_COLS; cc += 16) {
+        for (int cc = 0; cc < TU_C; cc += 16) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc, v);
             if (i < mp) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int64_t c = cbase + cc + j;
-                    if (c < nct) {
-                        float *p = F + (k + i) + (k + ncols + coff + c) * ld;
-                        *p -= v[j];
-                    }
+                    if (c < nct) F[(k + i) + (k + ncols + coff + c) * ld] = Cs[(cc + j) * TU_R + r] - v[j];
                 }
             }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, TCU_COLS);
-}
-
-template <int NB>
-int launch_tc(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols, int64_t nct,
-              int64_t coff, const float *Tblk, int *counters)
-{
-    constexpr int N = NB < 16 ? 16 : NB;
-    const size_t smem_y = 2 * (2 * TCY_COLS * 128 + 2 * N * 128) + 1024;
-    const size_t smem_u = 2 * TCU_ROWS * 128 + 2 * TCU_COLS * 128 + 1024;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_y<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_tc_update<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u);
-        if (e != cudaSuccess) return fl_cuda(ctx, e, "tensor-core attributes");
-        attr_done = true;
-    }
-    const int64_t mp = m_aug - k;
-    const int64_t ctiles = fl_cdiv(nct, TCY_COLS);
-    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(fl_cdiv(2 * ctx->num_sms, ctiles), fl_cdiv(mp, 256)));
-    int64_t rows_per_split = fl_round_up(fl_cdiv(mp, nsplit), TCY_CHUNK);
-    nsplit = fl_cdiv(mp, rows_per_split);
-    float *Ypart = (float *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(float) * nsplit * NB * nct);
-    float *Z = (float *)fl_ws(ctx, FL_WS_ZBUF, sizeof(float) * NB * nct);
-    if (!Ypart || !Z) return FASTLSQ_ERR_NOMEM;
-    FL_PROF_N(ctx, FASTLSQ_K_TRAIL_TC, 2);
-    k_tc_y<NB><<<dim3((unsigned)ctiles, (unsigned)nsplit), 128, smem_y, ctx->stream>>>(
-        F, ld, k, m_aug, ncols, nct, coff, rows_per_split, Ypart, Z, Tblk, counters, ctx->d_flag);
-    FL_CHECK_LAUNCH(ctx, "tc_y");
-    k_tc_update<NB><<<dim3((unsigned)fl_cdiv(mp, TCU_ROWS), (unsigned)fl_cdiv(nct, TCU_COLS)), 128, smem_u,
-                      ctx->stream>>>(F, ld, k, m_aug, ncols, nct, coff, Z, ctx->d_flag);
-    FL_CHECK_LAUNCH(ctx, "tc_update");
-    return 0;
+    if (warp == 0) tc::tmem_dealloc(tmem, TU_C);
 }
 
 }  // namespace
 
-int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
-                       int nb, int64_t nct, int64_t coff, const float *Tblk, int *counters)
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn()
+{
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+// The factor F (ld rows x ntot columns, column-major fp32) seen as a 2-D tensor
+// (dimension 0 = rows): boxes of box_r rows x box_c columns; out-of-range elements
+// read as zero.
+bool encode_map(CUtensorMap *m, const float *F, int64_t ld, int64_t ntot, uint32_t box_r, uint32_t box_c,
+                bool swizzle128)
+{
+    EncodeTiled fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ntot};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {box_r, box_c};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(F), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the three maps of one factor, cached (a factorisation launches two updates per panel)
+struct FactorMaps {
+    const float *F = nullptr;
+    int64_t ld = 0, ntot = 0;
+    CUtensorMap c, v, t;
+};
+
+bool factor_maps(const float *F, int64_t ld, int64_t ntot, FactorMaps &out)
+{
+    static std::mutex mu;
+    static FactorMaps cache[8];
+    static int next = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const FactorMaps &e : cache)
+        if (e.F == F && e.ld == ld && e.ntot == ntot) {
+            out = e;
+            return true;
+        }
+    FactorMaps e;
+    e.F = F;
+    e.ld = ld;
+    e.ntot = ntot;
+    if (!encode_map(&e.c, F, ld, ntot, TY_K, TY_C, true) || !encode_map(&e.v, F, ld, ntot, TY_K, 32, true) ||
+        !encode_map(&e.t, F, ld, ntot, TU_R, TU_C, false))
+        return false;
+    cache[next] = e;
+    next = (next + 1) % 8;
+    out = e;
+    return true;
+}
+
+}  // namespace
+
+// 1 when the tensor-core path does not take the shape (the caller uses the SIMT update)
+int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols, int nb,
+                       int64_t nct, int64_t coff, int64_t ntot, const float *Tblk, int *counters)
 {
     if (nct <= 0) return 0;
-    switch (nb) {
-    case 32: return launch_tc<32>(ctx, F, ld, k, m_aug, ncols, nct, coff, Tblk, counters);
-    case 16: return launch_tc<16>(ctx, F, ld, k, m_aug, ncols, nct, coff, Tblk, counters);
-    case 8: return launch_tc<8>(ctx, F, ld, k, m_aug, ncols, nct, coff, Tblk, counters);
-    default: return fl_fail(ctx, FASTLSQ_ERR_INVALID, "tensor-core update: panel width %d", nb);
+    if (nb != 32 || ld % 4 != 0 || k % 4 != 0 || (reinterpret_cast<uintptr_t>(F) & 15u) != 0) return 1;
+    FactorMaps maps;
+    if (!factor_maps(F, ld, ntot, maps)) return 1;
+    const size_t smem_y = TY_STAGES * TY_STAGE + 1024;
+    const size_t smem_u = 2 * TU_V + 2 * TU_Z + TU_CT + 1024;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_tcy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tcu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u);
+        if (e != cudaSuccess) return fl_cuda(ctx, e, "tensor-core attributes");
+        attr_done = true;
     }
+    const int64_t mp = m_aug - k;
+    const int64_t ctiles = fl_cdiv(nct, TY_C);
+    // about one wave of k_tcy CTAs, each streaming at least 16 chunks of rows
+    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(fl_cdiv(ctx->num_sms, ctiles), fl_cdiv(mp, 16 * TY_K)));
+    const int64_t rows_per_split = fl_round_up(fl_cdiv(mp, nsplit), TY_K);
+    nsplit = fl_cdiv(mp, rows_per_split);
+    float *Ypart = (float *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(float) * nsplit * 32 * nct);
+    float *Zimg = (float *)fl_ws(ctx, FL_WS_ZBUF, (size_t)ctiles * 2 * TU_Z);
+    if (!Ypart || !Zimg) return FASTLSQ_ERR_NOMEM;
+    FL_PROF_N(ctx, FASTLSQ_K_TRAIL_TC, 2);
+    k_tcy<<<dim3((unsigned)ctiles, (unsigned)nsplit), 128, smem_y, ctx->stream>>>(
+        maps.c, maps.v, k, ncols, nct, coff, mp, rows_per_split, Ypart, Zimg, Tblk, counters, ctx->d_flag);
+    FL_CHECK_LAUNCH(ctx, "tc_y");
+    k_tcu<<<dim3((unsigned)fl_cdiv(mp, TU_R), (unsigned)ctiles), 128, smem_u, ctx->stream>>>(
+        maps.t, F, ld, k, ncols, nct, coff, mp, Zimg, ctx->d_flag);
+    FL_CHECK_LAUNCH(ctx, "tc_update");
+    return 0;
 }

@@ -2,15 +2,19 @@
 // column tile to finish (counted with an atomic per tile) adds the split partials
 // in split order, so the result does not depend on which CTA finishes last, and
 // forms Z = T^T Y (T upper triangular) for the tile.  The counter is reset for the
-// next panel.  Z is stored [l][c] with row stride nct.
+// next panel.  Z is stored [l][c] with row stride nct, or (Zimg) as the tensor-core
+// operand image of the tile: Z^T split into tf32 hi and lo parts, each 128 rows (c)
+// of 128 bytes (l) in the K-major 128-byte-swizzled layout.
 #pragma once
 #include "common.cuh"
+#include "tc_common.cuh"
 
-template <typename T, int NB, int COLS, int THREADS>
+template <typename T, int NB, int COLS, int THREADS, bool IMG = false>
 __device__ __forceinline__ void trail_finish_z(const T *__restrict__ Ypart, int nsplit, int64_t nct,
                                                int64_t cbase, const T *__restrict__ Tblk,
                                                T *__restrict__ Z, int *counter, T *scratch)
 {
+    static_assert(!IMG || (NB == 32 && COLS == 128), "image tiles: 128 columns x 32 l");
     static_assert((NB * COLS) % THREADS == 0, "tile");
     constexpr int ITEMS = NB * COLS / THREADS;
     __shared__ int s_last;
@@ -60,10 +64,22 @@ __device__ __forceinline__ void trail_finish_z(const T *__restrict__ Ypart, int 
         const int idx = it * THREADS + threadIdx.x;
         const int l = idx / COLS, cc = idx % COLS;
         const int64_t c = cbase + cc;
-        if (c >= nct) continue;
-        T z = T(0);
-        for (int q = 0; q <= l; ++q) z += sT[q + l * NB] * sY[q * COLS + cc];
-        Z[(int64_t)l * nct + c] = z;
+        if constexpr (IMG) {
+            T z = T(0);
+            if (c < nct)
+                for (int q = 0; q <= l; ++q) z += sT[q + l * NB] * sY[q * COLS + cc];
+            float h, lo;
+            tc::split_tf32((float)z, h, lo);
+            float *img = reinterpret_cast<float *>(Z) + (cbase / COLS) * (2 * COLS * 32);
+            const uint32_t off = tc::sw128_offset((uint32_t)cc, (uint32_t)l) >> 2;
+            img[off] = h;
+            img[COLS * 32 + off] = lo;
+        } else {
+            if (c >= nct) continue;
+            T z = T(0);
+            for (int q = 0; q <= l; ++q) z += sT[q + l * NB] * sY[q * COLS + cc];
+            Z[(int64_t)l * nct + c] = z;
+        }
     }
     if (threadIdx.x == 0) *counter = 0;
 }

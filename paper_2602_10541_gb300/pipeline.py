@@ -125,6 +125,33 @@ class LinearSolver:
         return u
 
 
+class ConcurrentSolves:
+    """Independent linear solves queued together, each on its own context and stream.
+
+    One solve's critical path is its chain of panel factorisations, each on one
+    cluster of at most 16 SMs; the trailing updates fill part of the rest.  Solves of
+    independent instances (other seeds, parameters or right-hand-side operators) on
+    separate streams fill the remaining SMs.  step() forks from `origin` (a stream)
+    and joins back into it, so events recorded on `origin` around it time the batch."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.ev_fork = torch.cuda.Event()
+        self.ev_done = [torch.cuda.Event() for _ in self.solvers]
+
+    def step(self, origin=None):
+        origin = torch.cuda.current_stream() if origin is None else origin
+        self.ev_fork.record(origin)
+        for sv, ev in zip(self.solvers, self.ev_done):
+            s = sv.ctx.stream
+            s.wait_event(self.ev_fork)
+            with torch.cuda.stream(s):
+                sv.step()
+            ev.record(s)
+        for ev in self.ev_done:
+            origin.wait_event(ev)
+
+
 def rel_l2(a, b) -> float:
     """Relative L2 difference ||a - b|| / ||b||, computed on the host."""
     a = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else np.asarray(a)
