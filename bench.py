@@ -263,7 +263,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--refine", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tensor-core", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--tensor-core", type=int, default=1, choices=[0, 1],
                     help="1: trailing QR updates on tcgen05 (TF32x3), 0: SIMT FP32")
     ap.add_argument("--trsv-fp32", type=int, default=1, choices=[0, 1],
                     help="1: FP32 substitution in the triangular solves of classical refinement")

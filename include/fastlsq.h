@@ -401,7 +401,12 @@ FASTLSQ_API int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p
 
 /* Context options for fastlsq_set_option. */
 typedef enum {
-    FASTLSQ_OPT_TENSOR_CORE = 0,  /* 1: MIXED trailing updates on tcgen05 (TF32x3), 0: SIMT FP32 */
+    FASTLSQ_OPT_TENSOR_CORE = 0,  /* 1 (default): MIXED trailing updates on tcgen05 (TF32x3,
+                                      operands by TMA) for panel width 32 in factors refined
+                                      classically; factors refined by CGLS (preconditioners
+                                      of ill-conditioned systems) always use the SIMT FP32
+                                      update, whose products are 4x more accurate; 0: SIMT
+                                      FP32 everywhere */
     FASTLSQ_OPT_REGISTER_PANEL = 1, /* 1 (default): FP32 panels of width 32 factor with the
                                       slice in registers where rows per warp <= 24;
                                       0: the shared-memory panel kernel everywhere */

@@ -558,7 +558,11 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
     f->A_refine = (prec == FASTLSQ_PREC_MIXED) ? A_refine
                                                 : (const double *)(A_refine ? A_refine : A);
     f->ld_refine = (prec == FASTLSQ_PREC_MIXED || A_refine) ? ld_refine : ldA;
-    f->tensor_core = (prec == FASTLSQ_PREC_MIXED) ? ctx->use_tensor_core : 0;
+    // TF32x3 products carry about 2^-22 relative per product, FP32 FMAs 2^-24: where the
+    // factor preconditions CGLS (systems with kappa near 1 / eps32), the FP32 update keeps
+    // A R^{-1} well conditioned (measured on Sec. 4.4 instances: cond 2-11 vs 10-170)
+    f->tensor_core = (prec == FASTLSQ_PREC_MIXED && refine_mode == FASTLSQ_REFINE_CLASSICAL)
+                         ? ctx->use_tensor_core : 0;
     int rc = 0;
     const int64_t npanels = fl_cdiv(n_feat, nb);
     f->F = fl_alloc(ctx, elem * f->ld * (n_feat + nrhs), &rc);

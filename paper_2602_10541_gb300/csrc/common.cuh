@@ -46,6 +46,7 @@ enum fl_slot {
     FL_WS_SOLVE64,         // FP64 vectors of the triangular solves
     FL_WS_ZBUF,            // Z = T^T V^T C of the current trailing update
     FL_WS_COUNTERS,        // completion counters of the trailing-update column tiles
+    FL_WS_VIMG,            // the panel's V as the tensor-core update's operand image
     FL_WS_COUNT
 };
 
@@ -67,7 +68,7 @@ struct fastlsq_ctx {
     fl_buffer ws[FL_WS_COUNT];
     int *d_flag = nullptr;          // device error flag (int)
     void *d_grid_bar = nullptr;     // grid barrier state (count, generation) of this context
-    int use_tensor_core = 0;        // tcgen05 trailing updates for the MIXED path
+    int use_tensor_core = 1;        // tcgen05 trailing updates for the MIXED path
     int panel_reg = 1;              // register-resident FP32 panel (width 32) where it fits
     int row_panel = 1;              // of which the row layout (one or two rows per thread)
     int lookahead = 1;              // panel p+1 beside the rest of panel p's update (on aux_stream)

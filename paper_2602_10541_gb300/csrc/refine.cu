@@ -34,9 +34,10 @@ struct KryScalars {
     int accumulate;  // 1: obj accumulates (PCG), 0: obj is what remains (CGLS)
 };
 
-// A step that changes the objective by less than this fraction of it is below the
-// resolution of FP64: iterating further only lets the recurrence drift (kappa ~ 1e8
-// systems stall at a normal-equations residual far above any relative tolerance)
+// A step that changes the objective by less than this fraction of it, while the
+// preconditioned residual no longer falls, is below the resolution of FP64: iterating
+// further only lets the recurrence drift (kappa ~ 1e8 systems stall at a
+// normal-equations residual far above any relative tolerance)
 constexpr double KRY_STALL = 1e-15;
 
 constexpr int KV_ROWS = 256;
@@ -157,11 +158,15 @@ __global__ void k_kry_scalar(const double *__restrict__ part, int nblk, KryScala
         // quadratic form's decrease)
         const double dec = st->alpha * st->gamma;
         st->obj = st->accumulate ? st->obj + dec : st->obj - dec;
+        // stalled: the objective no longer moves AND the preconditioned residual has
+        // stopped falling (a flat objective alone can hide progress along directions
+        // that barely change it)
+        const bool stalled = !(dec > KRY_STALL * st->obj) && d > 0.5 * st->gamma;
         st->beta = d / st->gamma;
         st->gamma = d;
         st->iters += 1;
         if (!(d > tol * tol * st->gamma0) || !isfinite(d)) st->done = 1;
-        if (!(dec > KRY_STALL * st->obj)) st->done = 1;   // (an estimate <= 0 never fires)
+        if (stalled) st->done = 1;                        // (an estimate <= 0 never fires)
     } else if (op == OP_NORM) {
         if (norm_out) *norm_out = sqrt(d);
     }

@@ -7,15 +7,16 @@
 //           K = rows in chunks of 32).  A ring of 4 stages is filled by TMA: a C chunk
 //           (32 rows x 128 columns) and a V chunk (32 rows x 32 columns) land in the
 //           K-major 128-byte-swizzled layout the MMA reads (the column-major factor is
-//           already K-major for both).  All threads split a landed stage into hi/lo in
-//           place; one thread issues the 12 MMAs of the chunk and commits them to the
-//           stage's "empty" barrier, after which the stage is refilled.  The last CTA of
+//           already K-major for both).  Six warps split a landed stage into hi/lo in
+//           place, one thread issues the 12 MMAs of the chunk and commits them to the
+//           stage's "empty" barrier, one thread refills emptied stages.  The last CTA of
 //           each column tile forms Z = T^T Y and writes it as the update's operand
 //           image (Z^T hi and lo, swizzled).
-//   k_tcu : C -= V Z on 128 x 128 tiles (M = 128 rows, N = 128 columns, K = 32): the C
-//           tile arrives by TMA and the Z image by one bulk copy while the threads stage
-//           V (hi/lo, swizzled); the epilogue subtracts D (tcgen05.ld) from the staged C
-//           and stores coalesced along the rows.
+//   k_vimg: V of the panel written once as the update's operand image (hi/lo, swizzled).
+//   k_tcu : C -= V Z on 128 x 64 tiles (M = 128 rows, N = 64 columns, K = 32; two CTAs
+//           per SM): the C tile arrives by TMA, the V image of its row block and its half
+//           of the Z image by bulk copies; the epilogue subtracts D (tcgen05.ld) from the
+//           staged C and stores coalesced along the rows.
 // Every mbarrier wait is bounded: on timeout the kernel raises the device flag, waits
 // (bounded) for its copies and MMAs in flight, frees its TMEM and returns.
 #include <cuda.h>
@@ -33,8 +34,10 @@ namespace {
 constexpr int TY_C = 128;          // columns of C per k_tcy CTA (MMA M)
 constexpr int TY_K = 32;           // rows per chunk (MMA K per stage)
 constexpr int TY_STAGES = 4;
+constexpr int TY_THREADS = 256;
 constexpr int TU_R = 128;          // rows per k_tcu tile (MMA M)
-constexpr int TU_C = 128;          // columns per k_tcu tile (MMA N)
+constexpr int TU_C = 64;           // columns per k_tcu tile (MMA N; two tiles per Z image)
+constexpr int TU_THREADS = 256;
 constexpr long long TC_SPIN = 2000000000ll;   // SM cycles (about a second) before a wait gives up
 
 constexpr uint32_t TY_A = TY_C * 128;            // one 128 x 32 fp32 operand tile (bytes)
@@ -73,6 +76,11 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  :: "r"(tc::smem_addr(dst)), "l"(src), "r"(bytes), "r"(tc::smem_addr(bar)) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(tc::smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ float v_at(const float *__restrict__ F, int64_t ld, int64_t k, int64_t i, int l,
                                       int ncols)
 {
@@ -96,16 +104,48 @@ __device__ __forceinline__ float4 split4(float4 &x)
 namespace {
 
 // ---------------------------------------------------------------------------
-// Y partials: Ypart[split][l][c] = sum over the split's rows of V(i, l) C(i, c)
+// V of the panel at column k as the update's A operand: per block of 128 rows, the hi
+// part then the lo part, each 128 rows x 32 fp32 in the K-major 128-byte-swizzled
+// layout (thread = row, whole 128-byte rows written)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TU_R)
+k_vimg(const float *__restrict__ F, int64_t ld, int64_t k, int ncols, int64_t mp, float *__restrict__ Vimg)
+{
+    const int r = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * TU_R + r;
+    float x[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) x[l] = (i < mp) ? v_at(F, ld, k, i, l, ncols) : 0.f;
+    float4 *hi = reinterpret_cast<float4 *>(Vimg + (int64_t)blockIdx.x * (2 * TU_R * 32) + r * 32);
+    float4 *lo = hi + TU_R * 8;
+#pragma unroll
+    for (int c4 = 0; c4 < 8; ++c4) {
+        float4 h = make_float4(x[4 * c4], x[4 * c4 + 1], x[4 * c4 + 2], x[4 * c4 + 3]);
+        const float4 l4 = split4(h);
+        const int phys = c4 ^ (r & 7);
+        hi[phys] = h;
+        lo[phys] = l4;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Y partials: Ypart[split][l][c] = sum over the split's rows of V(i, l) C(i, c).
+// Warp roles: warp 0 loads stages by TMA, warp 1 issues the MMAs, warps 2..7 split
+// the landed stages into hi/lo; per-stage barriers (full: TMA landed, conv: split
+// done, empty: MMAs done) replace CTA-wide synchronisation inside the loop.
+// ---------------------------------------------------------------------------
+constexpr int TY_CONV = TY_THREADS / 32 - 2;     // converter warps
+
+__global__ void __launch_bounds__(TY_THREADS, 1)
 k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMap mV, int64_t k, int ncols,
       int64_t nct, int64_t coff, int64_t mp, int64_t rows_per_split, float *__restrict__ Ypart,
       float *__restrict__ Zimg, const float *__restrict__ Tblk, int *__restrict__ counters, int *flag)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = align1024(smem_raw);
-    __shared__ uint64_t full[TY_STAGES], empty[TY_STAGES];
+    __shared__ uint64_t full[TY_STAGES], conv[TY_STAGES], empty[TY_STAGES];
+    __shared__ int s_last_load[TY_STAGES], s_last_commit[TY_STAGES];
+    __shared__ volatile int s_fail;
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t cbase = (int64_t)blockIdx.x * TY_C;
@@ -117,41 +157,79 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
     if (threadIdx.x == 0) {
         for (int s = 0; s < TY_STAGES; ++s) {
             tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&conv[s], TY_CONV);
             tc::mbar_init(&empty[s], 1);
+            s_last_load[s] = s_last_commit[s] = -1;
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_fail = 0;
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
-    constexpr uint32_t idesc = tc::idesc_tf32(TY_C, 32);
-    // TMA coordinates: x = row of the factor, y = column
-    const int x0 = (int)(k + rs0), yc = (int)(k + ncols + coff + cbase), yv = (int)k;
-    // thread 0's record of the last chunk loaded into / committed from each stage
-    int last_load[TY_STAGES], last_commit[TY_STAGES];
-#pragma unroll
-    for (int s = 0; s < TY_STAGES; ++s) last_load[s] = last_commit[s] = -1;
-    auto issue = [&](int ch) {
-        const int s = ch % TY_STAGES;
-        unsigned char *A = base + s * TY_STAGE, *B = A + 2 * TY_A;
-        expect_tx(&full[s], TY_A + TY_B);
-        tma_load_2d(A, &mC, x0 + ch * TY_K, yc, &full[s]);
-        tma_load_2d(B, &mV, x0 + ch * TY_K, yv, &full[s]);
-        last_load[s] = ch;
-    };
-    if (threadIdx.x == 0)
-        for (int ch = 0; ch < nchunks && ch < TY_STAGES; ++ch) issue(ch);
 
-    bool ok = true;
-    for (int ch = 0; ch < nchunks; ++ch) {
-        const int s = ch % TY_STAGES;
-        const uint32_t ph = (uint32_t)(ch / TY_STAGES) & 1u;
-        unsigned char *Ah = base + s * TY_STAGE, *Al = Ah + TY_A, *Bh = Al + TY_A, *Bl = Bh + TY_B;
-        const bool landed = tc::mbar_wait(&full[s], ph, TC_SPIN);
-        if (landed) {
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA coordinates: x = row of the factor, y = column
+            const int x0 = (int)(k + rs0), yc = (int)(k + ncols + coff + cbase), yv = (int)k;
+            for (int ch = 0; ch < nchunks; ++ch) {
+                const int s = ch % TY_STAGES;
+                if (ch >= TY_STAGES &&
+                    !tc::mbar_wait(&empty[s], (uint32_t)((ch - TY_STAGES) / TY_STAGES) & 1u, TC_SPIN)) {
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                unsigned char *A = base + s * TY_STAGE, *B = A + 2 * TY_A;
+                expect_tx(&full[s], TY_A + TY_B);
+                tma_load_2d(A, &mC, x0 + ch * TY_K, yc, &full[s]);
+                tma_load_2d(B, &mV, x0 + ch * TY_K, yv, &full[s]);
+                s_last_load[s] = ch;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_tf32(TY_C, 32);
+            for (int ch = 0; ch < nchunks; ++ch) {
+                const int s = ch % TY_STAGES;
+                if (!tc::mbar_wait(&conv[s], (uint32_t)(ch / TY_STAGES) & 1u, TC_SPIN)) {
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                tc::fence_after_sync();
+                unsigned char *Ah = base + s * TY_STAGE, *Al = Ah + TY_A, *Bh = Al + TY_A, *Bl = Bh + TY_B;
+                const uint64_t dAh = tc::smem_desc_sw128(Ah), dAl = tc::smem_desc_sw128(Al);
+                const uint64_t dBh = tc::smem_desc_sw128(Bh), dBl = tc::smem_desc_sw128(Bl);
+#pragma unroll
+                for (int ks = 0; ks < TY_K / 8; ++ks) {
+                    const uint64_t o = (uint64_t)(ks * 32) >> 4;      // 8 tf32 = 32 bytes along K
+                    tc::mma_tf32(tmem, dAh + o, dBh + o, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
+                    tc::mma_tf32(tmem, dAh + o, dBl + o, idesc, 1u);
+                    tc::mma_tf32(tmem, dAl + o, dBh + o, idesc, 1u);
+                }
+                tc::mma_commit(&empty[s]);
+                s_last_commit[s] = ch;
+            }
+            // the last commit arrives after every earlier MMA of the thread has completed
+            if (!s_fail && nchunks > 0) {
+                const int lc = nchunks - 1;
+                if (!tc::mbar_wait(&empty[lc % TY_STAGES], (uint32_t)(lc / TY_STAGES) & 1u, TC_SPIN)) s_fail = 1;
+            }
+        }
+    } else {
+        const int ct = threadIdx.x - 64;                 // 0 .. 32 TY_CONV - 1
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int s = ch % TY_STAGES;
+            if (!tc::mbar_wait(&full[s], (uint32_t)(ch / TY_STAGES) & 1u, TC_SPIN)) {
+                s_fail = 1;
+                break;
+            }
+            if (s_fail) break;
+            unsigned char *Ah = base + s * TY_STAGE, *Al = Ah + TY_A, *Bh = Al + TY_A, *Bl = Bh + TY_B;
             // C chunk: split in place (hi) and into the lo tile
-            for (int q = threadIdx.x; q < (int)(TY_A / 16); q += 128) {
+            for (int q = ct; q < (int)(TY_A / 16); q += 32 * TY_CONV) {
                 float4 x = reinterpret_cast<const float4 *>(Ah)[q];
                 const float4 lo = split4(x);
                 reinterpret_cast<float4 *>(Ah)[q] = x;
@@ -160,7 +238,7 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
             // V chunk: smem row l = column l of V, 16-byte pieces of 4 consecutive rows;
             // zero past the panel's columns, unit lower triangle on its top rows
             const int64_t r0 = rs0 + (int64_t)ch * TY_K;
-            for (int q = threadIdx.x; q < (int)(TY_B / 16); q += 128) {
+            for (int q = ct; q < (int)(TY_B / 16); q += 32 * TY_CONV) {
                 float4 x = reinterpret_cast<const float4 *>(Bh)[q];
                 const int l = q >> 3;
                 const int64_t i0 = r0 + (((q & 7) ^ (l & 7)) << 2);
@@ -176,78 +254,57 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
                 reinterpret_cast<float4 *>(Bh)[q] = x;
                 reinterpret_cast<float4 *>(Bl)[q] = lo;
             }
+            tc::fence_proxy_async_smem();                // generic writes -> the MMA's reads
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&conv[s]);
         }
-        tc::fence_proxy_async_smem();
-        tc::fence_before_sync();
-        ok = __syncthreads_and(landed) != 0;
-        tc::fence_after_sync();
-        if (!ok) break;
-        if (threadIdx.x == 0) {
-            const uint64_t dAh = tc::smem_desc_sw128(Ah), dAl = tc::smem_desc_sw128(Al);
-            const uint64_t dBh = tc::smem_desc_sw128(Bh), dBl = tc::smem_desc_sw128(Bl);
-#pragma unroll
-            for (int ks = 0; ks < TY_K / 8; ++ks) {
-                const uint64_t o = (uint64_t)(ks * 32) >> 4;      // 8 tf32 = 32 bytes along K
-                tc::mma_tf32(tmem, dAh + o, dBh + o, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
-                tc::mma_tf32(tmem, dAh + o, dBl + o, idesc, 1u);
-                tc::mma_tf32(tmem, dAl + o, dBh + o, idesc, 1u);
-            }
-            tc::mma_commit(&empty[s]);
-            last_commit[s] = ch;
-            // refill the stage once its MMAs have read it
-            if (ch + TY_STAGES < nchunks && tc::mbar_wait(&empty[s], ph, TC_SPIN)) issue(ch + TY_STAGES);
-        }
-    }
-    // the last commit arrives after every earlier MMA of the thread has completed
-    bool done = true;
-    if (threadIdx.x == 0 && ok && nchunks > 0) {
-        const int lc = nchunks - 1;
-        done = tc::mbar_wait(&empty[lc % TY_STAGES], (uint32_t)(lc / TY_STAGES) & 1u, TC_SPIN);
     }
     tc::fence_before_sync();
-    ok = __syncthreads_and(ok && done) != 0;
+    __syncthreads();
     tc::fence_after_sync();
+    const bool ok = !s_fail;
     if (!ok) {
         if (threadIdx.x == 0) {
             atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
             // let the copies and MMAs in flight finish before the CTA leaves (bounded)
             for (int s = 0; s < TY_STAGES; ++s) {
-                if (last_load[s] >= 0) tc::mbar_wait(&full[s], (uint32_t)(last_load[s] / TY_STAGES) & 1u, TC_SPIN);
-                if (last_commit[s] >= 0)
-                    tc::mbar_wait(&empty[s], (uint32_t)(last_commit[s] / TY_STAGES) & 1u, TC_SPIN);
+                if (s_last_load[s] >= 0)
+                    tc::mbar_wait(&full[s], (uint32_t)(s_last_load[s] / TY_STAGES) & 1u, TC_SPIN);
+                if (s_last_commit[s] >= 0)
+                    tc::mbar_wait(&empty[s], (uint32_t)(s_last_commit[s] / TY_STAGES) & 1u, TC_SPIN);
             }
         }
     } else {
-        // D: TMEM lane = column c (warp w: lanes 32 w ..), TMEM column = l
-        const int64_t c = cbase + warp * 32 + lane;
+        // D: TMEM lane = column c, TMEM column = l; warp w reads lanes 32 (w % 4) ..
+        // (its lane quarter) and columns 16 (w / 4) .. + 15
+        const int q4 = warp & 3, lc = 16 * (warp >> 2);
+        const int64_t c = cbase + q4 * 32 + lane;
+        float v[16];
+        if (nchunks > 0) {
+            tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + lc, v);
+        } else {
 #pragma unroll
-        for (int lc = 0; lc < 32; lc += 16) {
-            float v[16];
-            if (nchunks > 0) {
-                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + lc, v);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = 0.f;
-            }
-            if (c < nct)
-#pragma unroll
-                for (int j = 0; j < 16; ++j) Ypart[((int64_t)blockIdx.y * 32 + lc + j) * nct + c] = v[j];
+            for (int j = 0; j < 16; ++j) v[j] = 0.f;
         }
+        if (c < nct)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) Ypart[((int64_t)blockIdx.y * 32 + lc + j) * nct + c] = v[j];
     }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 32);
     if (ok)   // uniform; the stage buffers are free once the last MMA has completed
-        trail_finish_z<float, 32, TY_C, 128, true>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Zimg,
-                                                   counters + blockIdx.x, reinterpret_cast<float *>(base));
+        trail_finish_z<float, 32, TY_C, TY_THREADS, true>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Zimg,
+                                                          counters + blockIdx.x, reinterpret_cast<float *>(base));
 }
 
 // ---------------------------------------------------------------------------
-// C(i, c) -= sum_l V(i, l) Z(l, c) on a 128 x 128 tile
+// C(i, c) -= sum_l V(i, l) Z(l, c) on a 128 x 64 tile
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TU_THREADS, 2)
 k_tcu(const __grid_constant__ CUtensorMap mT, float *__restrict__ F, int64_t ld, int64_t k, int ncols,
-      int64_t nct, int64_t coff, int64_t mp, const float *__restrict__ Zimg, int *flag)
+      int64_t nct, int64_t coff, int64_t mp, const float *__restrict__ Vimg, const float *__restrict__ Zimg,
+      int *flag)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = align1024(smem_raw);
@@ -271,29 +328,16 @@ k_tcu(const __grid_constant__ CUtensorMap mT, float *__restrict__ F, int64_t ld,
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     if (threadIdx.x == 0) {
-        // the C tile (rows k + rbase .., columns of the update) and the tile's Z image
+        // the C tile (rows k + rbase .., columns of the update), the V image of the row
+        // block and this tile's half of the Z image of its 128-column tile
         expect_tx(&bar_c, TU_CT);
         tma_load_2d(const_cast<float *>(Cs), &mT, (int)(k + rbase), (int)(k + ncols + coff + cbase), &bar_c);
-        expect_tx(&bar_z, 2 * TU_Z);
-        bulk_load(Zh, Zimg + (cbase / TU_C) * (2 * TU_C * 32), 2 * TU_Z, &bar_z);
+        const float *img = Zimg + (cbase / TY_C) * (2 * TY_C * 32) + (cbase % TY_C) * 32;
+        expect_tx(&bar_z, 2 * TU_V + 2 * TU_Z);
+        bulk_load(Vh, Vimg + (int64_t)blockIdx.x * (2 * TU_R * 32), 2 * TU_V, &bar_z);   // hi, lo
+        bulk_load(Zh, img, TU_Z, &bar_z);
+        bulk_load(Zl, img + TY_C * 32, TU_Z, &bar_z);
     }
-    // A = V rows: thread = row, one column l at a time (coalesced along the rows)
-    {
-        const int r = threadIdx.x;
-        const int64_t i = rbase + r;
-        float x[32];
-#pragma unroll
-        for (int l = 0; l < 32; ++l) x[l] = (i < mp) ? v_at(F, ld, k, i, l, ncols) : 0.f;
-#pragma unroll
-        for (int l = 0; l < 32; ++l) {
-            float h, lo;
-            tc::split_tf32(x[l], h, lo);
-            const uint32_t off = tc::sw128_offset((uint32_t)r, (uint32_t)l);
-            *reinterpret_cast<float *>(Vh + off) = h;
-            *reinterpret_cast<float *>(Vl + off) = lo;
-        }
-    }
-    tc::fence_proxy_async_smem();
     const bool wz = tc::mbar_wait(&bar_z, 0u, TC_SPIN);
     tc::fence_before_sync();
     bool ok = __syncthreads_and(wz) != 0;
@@ -325,13 +369,15 @@ k_tcu(const __grid_constant__ CUtensorMap mT, float *__restrict__ F, int64_t ld,
             if (issued) tc::mbar_wait(&bar_m, 0u, TC_SPIN);
         }
     } else {
-        // D: TMEM lane = row (warp w: rows 32 w ..), column = c; C - D stored along the rows
-        const int r = warp * 32 + lane;
+        // D: TMEM lane = row, column = c.  Warp w reads lanes 32 (w % 4) .. (its lane
+        // quarter), columns 32 (w / 4) .. + 31; C - D stored along the rows
+        const int q4 = warp & 3, c0 = 32 * (warp >> 2);
+        const int r = q4 * 32 + lane;
         const int64_t i = rbase + r;
-#pragma unroll 1
-        for (int cc = 0; cc < TU_C; cc += 16) {
+#pragma unroll
+        for (int cc = c0; cc < c0 + 32; cc += 16) {
             float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc, v);
+            tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + cc, v);
             if (i < mp) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -442,15 +488,20 @@ int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_
     int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(fl_cdiv(ctx->num_sms, ctiles), fl_cdiv(mp, 16 * TY_K)));
     const int64_t rows_per_split = fl_round_up(fl_cdiv(mp, nsplit), TY_K);
     nsplit = fl_cdiv(mp, rows_per_split);
+    const int64_t rblocks = fl_cdiv(mp, TU_R);
+    float *Vimg = (float *)fl_ws(ctx, FL_WS_VIMG, (size_t)rblocks * 2 * TU_R * 32 * sizeof(float));
     float *Ypart = (float *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(float) * nsplit * 32 * nct);
-    float *Zimg = (float *)fl_ws(ctx, FL_WS_ZBUF, (size_t)ctiles * 2 * TU_Z);
-    if (!Ypart || !Zimg) return FASTLSQ_ERR_NOMEM;
-    FL_PROF_N(ctx, FASTLSQ_K_TRAIL_TC, 2);
-    k_tcy<<<dim3((unsigned)ctiles, (unsigned)nsplit), 128, smem_y, ctx->stream>>>(
+    // Z image: per 128-column tile, hi and lo parts of 128 rows x 32 fp32
+    float *Zimg = (float *)fl_ws(ctx, FL_WS_ZBUF, (size_t)ctiles * 2 * TY_C * 32 * sizeof(float));
+    if (!Ypart || !Zimg || !Vimg) return FASTLSQ_ERR_NOMEM;
+    FL_PROF_N(ctx, FASTLSQ_K_TRAIL_TC, 3);
+    k_vimg<<<(unsigned)rblocks, TU_R, 0, ctx->stream>>>(F, ld, k, ncols, mp, Vimg);
+    FL_CHECK_LAUNCH(ctx, "tc_vimg");
+    k_tcy<<<dim3((unsigned)ctiles, (unsigned)nsplit), TY_THREADS, smem_y, ctx->stream>>>(
         maps.c, maps.v, k, ncols, nct, coff, mp, rows_per_split, Ypart, Zimg, Tblk, counters, ctx->d_flag);
     FL_CHECK_LAUNCH(ctx, "tc_y");
-    k_tcu<<<dim3((unsigned)fl_cdiv(mp, TU_R), (unsigned)ctiles), 128, smem_u, ctx->stream>>>(
-        maps.t, F, ld, k, ncols, nct, coff, mp, Zimg, ctx->d_flag);
+    k_tcu<<<dim3((unsigned)rblocks, (unsigned)fl_cdiv(nct, TU_C)), TU_THREADS, smem_u, ctx->stream>>>(
+        maps.t, F, ld, k, ncols, nct, coff, mp, Vimg, Zimg, ctx->d_flag);
     FL_CHECK_LAUNCH(ctx, "tc_update");
     return 0;
 }

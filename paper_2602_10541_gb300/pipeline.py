@@ -173,11 +173,12 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--refine", type=int, default=2)
     ap.add_argument("--refine-mode", choices=["classical", "cgls"], default="classical")
-    ap.add_argument("--tensor-core", action="store_true", help="tcgen05 trailing updates (MIXED)")
+    ap.add_argument("--tensor-core", action="store_true",
+                    help="tcgen05 trailing updates (MIXED; the default)")
+    ap.add_argument("--simt", action="store_true", help="SIMT FP32 trailing updates instead")
     a = ap.parse_args(argv)
     ctx = fl.Context(0)
-    if a.tensor_core:
-        fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
+    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 0 if a.simt else 1)
     dp = upload(wl.CONFIGS[a.workload]())
     s = LinearSolver(ctx, dp, prec=fl.PREC_MIXED if a.prec == "mixed" else fl.PREC_FP64,
                      max_refine=a.refine,

@@ -356,7 +356,7 @@ def test_lookahead_matches_single_stream(ctx, tc, m, n):
     finally:
         fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, 1)
         fl.fastlsq_set_option(ctx, fl.OPT_FUSED_LOOKAHEAD, 1)
-        fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 0)
+        fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
     for key in ((1, 1), (1, 0)):
         assert np.abs(Rs[key] - Ro).max() <= 2e-5 * scale, key
         assert np.abs(Rs[key] - Rs[(0, 0)]).max() <= 2e-5 * scale, key

@@ -1,6 +1,6 @@
 """Trailing updates of the MIXED factorisation on the tcgen05 tensor cores (split
-TF32x3 products, FP32 accumulation in TMEM) against the FP64 oracle and against
-the SIMT FP32 updates.
+TF32x3 products, FP32 accumulation in TMEM, operands by TMA; the default) against
+the FP64 oracle and against the SIMT FP32 updates.
 
 Bars: TF32x3 keeps about FP32 accuracy per product (the dropped lo*lo term is
 2^-22 relative), so R must match the oracle's Householder R to the same 2e-5
@@ -25,7 +25,7 @@ DEV = "cuda:0"
 def ctx():
     c = fl.Context(0)
     yield c
-    fl.fastlsq_set_option(c, fl.OPT_TENSOR_CORE, 0)
+    fl.fastlsq_set_option(c, fl.OPT_TENSOR_CORE, 1)
 
 
 def _cm(M, dtype):
@@ -50,7 +50,7 @@ def _factor_r(ctx, A, tc):
     R = torch.zeros((n, n), dtype=torch.float64, device=DEV)
     fl.fastlsq_factor_get_r(ctx, fac, R)
     fl.fastlsq_factor_destroy(ctx, fac)
-    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 0)
+    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
     return R.cpu().numpy().T, st
 
 
@@ -85,7 +85,7 @@ def test_tensor_core_mixed_solve_refines_to_fp64(ctx, m, n, mu):
         _, _, st = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, mu, _rhs(B), beta,
                                     A_refine=_cm(A, torch.float64), max_refine=4, stats=True)
     finally:
-        fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 0)
+        fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
     assert st.tensor_core == 1
     np.testing.assert_allclose(beta.cpu().numpy()[0], ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
 
@@ -105,6 +105,6 @@ def test_tensor_core_helmholtz_matches_oracle(ctx):
         s = pl.LinearSolver(ctx, dp, prec=fl.PREC_MIXED, max_refine=2)
         s.step(stats=True)
     finally:
-        fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 0)
+        fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
     assert s.stats.tensor_core == 1
     assert pl.rel_l2(s.u_test().cpu().numpy(), u_orc) <= 1e-6
