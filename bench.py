@@ -165,7 +165,7 @@ def _src_sha(name):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-KERNEL_SRC = {"panel": "panel_reg.cu", "trail_simt": "qr.cu", "trail_tc": "tc_update.cu",
+KERNEL_SRC = {"panel": "panel_row.cu", "trail_simt": "qr.cu", "trail_tc": "tc_update.cu",
               "apply_q": "apply_q.cu", "trsv": "refine.cu", "residual": "qr.cu",
               "assemble_f32": "assemble.cu", "assemble_f64": "assemble.cu", "copy_in": "qr.cu"}
 

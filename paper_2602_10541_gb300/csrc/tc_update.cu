@@ -4,12 +4,12 @@
 // For panel k with Householder block V (m_p x 32, unit lower trapezoidal) and
 // compact-WY factor T, C -= V (T^T (V^T C)) in two kernels:
 //   k_tcy : Y^T = C^T V over a split of the rows (MMA M = 128 columns of C, N = 32,
-//           K = rows in chunks of 32).  A ring of 4 stages is filled by TMA: a C chunk
-//           (32 rows x 128 columns) and a V chunk (32 rows x 32 columns) land in the
-//           K-major 128-byte-swizzled layout the MMA reads (the column-major factor is
-//           already K-major for both).  Six warps split a landed stage into hi/lo in
-//           place, one thread issues the 12 MMAs of the chunk and commits them to the
-//           stage's "empty" barrier, one thread refills emptied stages.  The last CTA of
+//           K = rows in chunks of 32).  A ring of 6 landing slots is filled by TMA: a C
+//           chunk (32 rows x 128 columns) and a V chunk (32 rows x 32 columns) land in
+//           the K-major 128-byte-swizzled layout the MMA reads (the column-major factor
+//           is already K-major for both).  Six warps split a landed chunk into hi (in
+//           place) and lo (one of 2 lo slots), one thread issues the 12 MMAs of the
+//           chunk and frees both slots by commits, one thread refills landing slots.  The last CTA of
 //           each column tile forms Z = T^T Y and writes it as the update's operand
 //           image (Z^T hi and lo, swizzled).
 //   k_vimg: V of the panel written once as the update's operand image (hi/lo, swizzled).
@@ -33,7 +33,6 @@ namespace {
 
 constexpr int TY_C = 128;          // columns of C per k_tcy CTA (MMA M)
 constexpr int TY_K = 32;           // rows per chunk (MMA K per stage)
-constexpr int TY_STAGES = 4;
 constexpr int TY_THREADS = 256;
 constexpr int TU_R = 128;          // rows per k_tcu tile (MMA M)
 constexpr int TU_C = 64;           // columns per k_tcu tile (MMA N; two tiles per Z image)
@@ -42,7 +41,6 @@ constexpr long long TC_SPIN = 2000000000ll;   // SM cycles (about a second) befo
 
 constexpr uint32_t TY_A = TY_C * 128;            // one 128 x 32 fp32 operand tile (bytes)
 constexpr uint32_t TY_B = 32 * 128;              // one 32 x 32 fp32 operand tile
-constexpr uint32_t TY_STAGE = 2 * TY_A + 2 * TY_B;
 constexpr uint32_t TU_CT = TU_R * TU_C * 4;      // staged C tile
 constexpr uint32_t TU_V = TU_R * 128;            // V hi (or lo)
 constexpr uint32_t TU_Z = TU_C * 128;            // Z^T hi (or lo)
@@ -130,11 +128,18 @@ k_vimg(const float *__restrict__ F, int64_t ld, int64_t k, int ncols, int64_t mp
 
 // ---------------------------------------------------------------------------
 // Y partials: Ypart[split][l][c] = sum over the split's rows of V(i, l) C(i, c).
-// Warp roles: warp 0 loads stages by TMA, warp 1 issues the MMAs, warps 2..7 split
-// the landed stages into hi/lo; per-stage barriers (full: TMA landed, conv: split
-// done, empty: MMAs done) replace CTA-wide synchronisation inside the loop.
+// Warp roles: warp 0 loads chunks by TMA into a ring of TY_LAND landing slots, warps
+// 2..7 split a landed chunk into hi (in place) and lo (into one of TY_LO lo slots),
+// warp 1 issues the MMAs and commits them twice (freeing the landing slot and the lo
+// slot).  Per-slot barriers: full (TMA landed), conv (split done), land_empty and
+// lo_empty (MMAs done); no CTA-wide synchronisation inside the loop.
 // ---------------------------------------------------------------------------
 constexpr int TY_CONV = TY_THREADS / 32 - 2;     // converter warps
+constexpr int TY_LAND = 6;                       // landing slots (raw, then hi)
+constexpr int TY_LO = 2;                         // lo slots
+constexpr uint32_t TY_SLOT = TY_A + TY_B;        // one chunk: C part then V part
+constexpr int TY_QA = TY_A / 16, TY_QB = TY_B / 16;                  // float4 per part
+constexpr int TY_PER = (TY_QA + TY_QB + 32 * TY_CONV - 1) / (32 * TY_CONV);   // per converter thread
 
 __global__ void __launch_bounds__(TY_THREADS, 1)
 k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMap mV, int64_t k, int ncols,
@@ -143,8 +148,9 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = align1024(smem_raw);
-    __shared__ uint64_t full[TY_STAGES], conv[TY_STAGES], empty[TY_STAGES];
-    __shared__ int s_last_load[TY_STAGES], s_last_commit[TY_STAGES];
+    unsigned char *land = base, *lo = base + TY_LAND * TY_SLOT;
+    __shared__ uint64_t full[TY_LAND], land_empty[TY_LAND], conv[TY_LO], lo_empty[TY_LO];
+    __shared__ int s_last_load[TY_LAND], s_last_commit;
     __shared__ volatile int s_fail;
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -155,13 +161,17 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
 
     if (warp == 0) tc::tmem_alloc(&tmem_slot, 32);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TY_STAGES; ++s) {
+        for (int s = 0; s < TY_LAND; ++s) {
             tc::mbar_init(&full[s], 1);
-            tc::mbar_init(&conv[s], TY_CONV);
-            tc::mbar_init(&empty[s], 1);
-            s_last_load[s] = s_last_commit[s] = -1;
+            tc::mbar_init(&land_empty[s], 1);
+            s_last_load[s] = -1;
+        }
+        for (int t = 0; t < TY_LO; ++t) {
+            tc::mbar_init(&conv[t], TY_CONV);
+            tc::mbar_init(&lo_empty[t], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_last_commit = -1;
         s_fail = 0;
     }
     tc::fence_before_sync();
@@ -174,17 +184,17 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
             // TMA coordinates: x = row of the factor, y = column
             const int x0 = (int)(k + rs0), yc = (int)(k + ncols + coff + cbase), yv = (int)k;
             for (int ch = 0; ch < nchunks; ++ch) {
-                const int s = ch % TY_STAGES;
-                if (ch >= TY_STAGES &&
-                    !tc::mbar_wait(&empty[s], (uint32_t)((ch - TY_STAGES) / TY_STAGES) & 1u, TC_SPIN)) {
+                const int s = ch % TY_LAND;
+                if (ch >= TY_LAND &&
+                    !tc::mbar_wait(&land_empty[s], (uint32_t)((ch - TY_LAND) / TY_LAND) & 1u, TC_SPIN)) {
                     s_fail = 1;
                     break;
                 }
                 if (s_fail) break;
-                unsigned char *A = base + s * TY_STAGE, *B = A + 2 * TY_A;
-                expect_tx(&full[s], TY_A + TY_B);
+                unsigned char *A = land + s * TY_SLOT;
+                expect_tx(&full[s], TY_SLOT);
                 tma_load_2d(A, &mC, x0 + ch * TY_K, yc, &full[s]);
-                tma_load_2d(B, &mV, x0 + ch * TY_K, yv, &full[s]);
+                tma_load_2d(A + TY_A, &mV, x0 + ch * TY_K, yv, &full[s]);
                 s_last_load[s] = ch;
             }
         }
@@ -192,14 +202,14 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_tf32(TY_C, 32);
             for (int ch = 0; ch < nchunks; ++ch) {
-                const int s = ch % TY_STAGES;
-                if (!tc::mbar_wait(&conv[s], (uint32_t)(ch / TY_STAGES) & 1u, TC_SPIN)) {
+                const int s = ch % TY_LAND, t = ch % TY_LO;
+                if (!tc::mbar_wait(&conv[t], (uint32_t)(ch / TY_LO) & 1u, TC_SPIN)) {
                     s_fail = 1;
                     break;
                 }
                 if (s_fail) break;
                 tc::fence_after_sync();
-                unsigned char *Ah = base + s * TY_STAGE, *Al = Ah + TY_A, *Bh = Al + TY_A, *Bl = Bh + TY_B;
+                unsigned char *Ah = land + s * TY_SLOT, *Bh = Ah + TY_A, *Al = lo + t * TY_SLOT, *Bl = Al + TY_A;
                 const uint64_t dAh = tc::smem_desc_sw128(Ah), dAl = tc::smem_desc_sw128(Al);
                 const uint64_t dBh = tc::smem_desc_sw128(Bh), dBl = tc::smem_desc_sw128(Bl);
 #pragma unroll
@@ -209,54 +219,66 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
                     tc::mma_tf32(tmem, dAh + o, dBl + o, idesc, 1u);
                     tc::mma_tf32(tmem, dAl + o, dBh + o, idesc, 1u);
                 }
-                tc::mma_commit(&empty[s]);
-                s_last_commit[s] = ch;
+                tc::mma_commit(&land_empty[s]);
+                tc::mma_commit(&lo_empty[t]);
+                s_last_commit = ch;
             }
             // the last commit arrives after every earlier MMA of the thread has completed
             if (!s_fail && nchunks > 0) {
                 const int lc = nchunks - 1;
-                if (!tc::mbar_wait(&empty[lc % TY_STAGES], (uint32_t)(lc / TY_STAGES) & 1u, TC_SPIN)) s_fail = 1;
+                if (!tc::mbar_wait(&lo_empty[lc % TY_LO], (uint32_t)(lc / TY_LO) & 1u, TC_SPIN)) s_fail = 1;
             }
         }
     } else {
         const int ct = threadIdx.x - 64;                 // 0 .. 32 TY_CONV - 1
         for (int ch = 0; ch < nchunks; ++ch) {
-            const int s = ch % TY_STAGES;
-            if (!tc::mbar_wait(&full[s], (uint32_t)(ch / TY_STAGES) & 1u, TC_SPIN)) {
+            const int s = ch % TY_LAND, t = ch % TY_LO;
+            // the lo slot is free once the MMAs of chunk ch - TY_LO have completed
+            if (ch >= TY_LO &&
+                !tc::mbar_wait(&lo_empty[t], (uint32_t)((ch - TY_LO) / TY_LO) & 1u, TC_SPIN)) {
+                s_fail = 1;
+                break;
+            }
+            if (!tc::mbar_wait(&full[s], (uint32_t)(ch / TY_LAND) & 1u, TC_SPIN)) {
                 s_fail = 1;
                 break;
             }
             if (s_fail) break;
-            unsigned char *Ah = base + s * TY_STAGE, *Al = Ah + TY_A, *Bh = Al + TY_A, *Bl = Bh + TY_B;
-            // C chunk: split in place (hi) and into the lo tile
-            for (int q = ct; q < (int)(TY_A / 16); q += 32 * TY_CONV) {
-                float4 x = reinterpret_cast<const float4 *>(Ah)[q];
-                const float4 lo = split4(x);
-                reinterpret_cast<float4 *>(Ah)[q] = x;
-                reinterpret_cast<float4 *>(Al)[q] = lo;
+            float4 *hi = reinterpret_cast<float4 *>(land + s * TY_SLOT);
+            float4 *lq = reinterpret_cast<float4 *>(lo + t * TY_SLOT);
+            // float4 q < TY_QA: the C part; q >= TY_QA: the V part (smem row l = column l
+            // of V, 4 consecutive rows) with zero past the panel's columns and the unit
+            // lower triangle on the panel's top rows
+            float4 x[TY_PER];
+#pragma unroll
+            for (int u = 0; u < TY_PER; ++u) {
+                const int q = ct + u * 32 * TY_CONV;
+                x[u] = (q < TY_QA + TY_QB) ? hi[q] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            // V chunk: smem row l = column l of V, 16-byte pieces of 4 consecutive rows;
-            // zero past the panel's columns, unit lower triangle on its top rows
             const int64_t r0 = rs0 + (int64_t)ch * TY_K;
-            for (int q = ct; q < (int)(TY_B / 16); q += 32 * TY_CONV) {
-                float4 x = reinterpret_cast<const float4 *>(Bh)[q];
-                const int l = q >> 3;
-                const int64_t i0 = r0 + (((q & 7) ^ (l & 7)) << 2);
-                if (l >= ncols) {
-                    x = make_float4(0.f, 0.f, 0.f, 0.f);
-                } else if (i0 <= l) {
-                    x.x = (i0 + 0 < l) ? 0.f : ((i0 + 0 == l) ? 1.f : x.x);
-                    x.y = (i0 + 1 < l) ? 0.f : ((i0 + 1 == l) ? 1.f : x.y);
-                    x.z = (i0 + 2 < l) ? 0.f : ((i0 + 2 == l) ? 1.f : x.z);
-                    x.w = (i0 + 3 < l) ? 0.f : ((i0 + 3 == l) ? 1.f : x.w);
+#pragma unroll
+            for (int u = 0; u < TY_PER; ++u) {
+                const int q = ct + u * 32 * TY_CONV;
+                if (q >= TY_QA + TY_QB) continue;
+                if (q >= TY_QA) {
+                    const int qb = q - TY_QA, l = qb >> 3;
+                    const int64_t i0 = r0 + (((qb & 7) ^ (l & 7)) << 2);
+                    if (l >= ncols) {
+                        x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else if (i0 <= l) {
+                        x[u].x = (i0 + 0 < l) ? 0.f : ((i0 + 0 == l) ? 1.f : x[u].x);
+                        x[u].y = (i0 + 1 < l) ? 0.f : ((i0 + 1 == l) ? 1.f : x[u].y);
+                        x[u].z = (i0 + 2 < l) ? 0.f : ((i0 + 2 == l) ? 1.f : x[u].z);
+                        x[u].w = (i0 + 3 < l) ? 0.f : ((i0 + 3 == l) ? 1.f : x[u].w);
+                    }
                 }
-                const float4 lo = split4(x);
-                reinterpret_cast<float4 *>(Bh)[q] = x;
-                reinterpret_cast<float4 *>(Bl)[q] = lo;
+                const float4 l4 = split4(x[u]);
+                hi[q] = x[u];
+                lq[q] = l4;
             }
             tc::fence_proxy_async_smem();                // generic writes -> the MMA's reads
             __syncwarp();
-            if (lane == 0) mbar_arrive(&conv[s]);
+            if (lane == 0) mbar_arrive(&conv[t]);
         }
     }
     tc::fence_before_sync();
@@ -267,12 +289,11 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
         if (threadIdx.x == 0) {
             atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
             // let the copies and MMAs in flight finish before the CTA leaves (bounded)
-            for (int s = 0; s < TY_STAGES; ++s) {
+            for (int s = 0; s < TY_LAND; ++s)
                 if (s_last_load[s] >= 0)
-                    tc::mbar_wait(&full[s], (uint32_t)(s_last_load[s] / TY_STAGES) & 1u, TC_SPIN);
-                if (s_last_commit[s] >= 0)
-                    tc::mbar_wait(&empty[s], (uint32_t)(s_last_commit[s] / TY_STAGES) & 1u, TC_SPIN);
-            }
+                    tc::mbar_wait(&full[s], (uint32_t)(s_last_load[s] / TY_LAND) & 1u, TC_SPIN);
+            const int lc = s_last_commit;
+            if (lc >= 0) tc::mbar_wait(&lo_empty[lc % TY_LO], (uint32_t)(lc / TY_LO) & 1u, TC_SPIN);
         }
     } else {
         // D: TMEM lane = column c, TMEM column = l; warp w reads lanes 32 (w % 4) ..
@@ -293,7 +314,7 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 32);
-    if (ok)   // uniform; the stage buffers are free once the last MMA has completed
+    if (ok)   // uniform; the ring is free once the last MMA has completed
         trail_finish_z<float, 32, TY_C, TY_THREADS, true>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Zimg,
                                                           counters + blockIdx.x, reinterpret_cast<float *>(base));
 }
@@ -472,7 +493,7 @@ int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_
     if (nb != 32 || ld % 4 != 0 || k % 4 != 0 || (reinterpret_cast<uintptr_t>(F) & 15u) != 0) return 1;
     FactorMaps maps;
     if (!factor_maps(F, ld, ntot, maps)) return 1;
-    const size_t smem_y = TY_STAGES * TY_STAGE + 1024;
+    const size_t smem_y = (TY_LAND + TY_LO) * TY_SLOT + 1024;
     const size_t smem_u = 2 * TU_V + 2 * TU_Z + TU_CT + 1024;
     static bool attr_done = false;
     if (!attr_done) {
