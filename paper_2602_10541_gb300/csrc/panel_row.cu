@@ -64,6 +64,13 @@ __device__ __forceinline__ void rp_st_async_v4(uint32_t addr, float4 v, uint32_t
                  :: "r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(bar) : "memory");
 }
 
+// contiguous global -> own shared memory copy (16-byte aligned, multiple of 16 bytes)
+__device__ __forceinline__ void rp_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 :: "r"(tc::smem_addr(dst)), "l"(src), "r"(bytes), "r"(tc::smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void rp_bulk_to_rank(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
     asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
@@ -237,20 +244,27 @@ __device__ __forceinline__ void rp_prev_y(const RpLayout &L, float *sm, int rank
     __syncthreads();
 }
 
-// c -= V(row, :) Z for one row held in registers; V(row, :) from the staged columns
-__device__ __forceinline__ void rp_apply_row(const float *SVc, int lds, int r, const float *Zs,
-                                             float (&c)[RP_NB])
+// c -= V(row, :) Z for the thread's rows (row t + h NT) held in registers; V(row, :)
+// from the staged columns; each row of Z is read once for all the thread's rows
+template <int RPT>
+__device__ __forceinline__ void rp_apply_rows(const float *SVc, int lds, int NT, const float *Zs,
+                                              float (&c)[RPT][RP_NB])
 {
-#pragma unroll 4
+#pragma unroll 2
     for (int q = 0; q < RP_NB; ++q) {
-        const float v = SVc[q * lds + r];
+        float v[RPT];
+#pragma unroll
+        for (int h = 0; h < RPT; ++h) v[h] = SVc[q * lds + threadIdx.x + h * NT];
 #pragma unroll
         for (int l4 = 0; l4 < 8; ++l4) {
             const float4 z = *reinterpret_cast<const float4 *>(Zs + q * 32 + 4 * l4);
-            c[4 * l4 + 0] = fmaf(-v, z.x, c[4 * l4 + 0]);
-            c[4 * l4 + 1] = fmaf(-v, z.y, c[4 * l4 + 1]);
-            c[4 * l4 + 2] = fmaf(-v, z.z, c[4 * l4 + 2]);
-            c[4 * l4 + 3] = fmaf(-v, z.w, c[4 * l4 + 3]);
+#pragma unroll
+            for (int h = 0; h < RPT; ++h) {
+                c[h][4 * l4 + 0] = fmaf(-v[h], z.x, c[h][4 * l4 + 0]);
+                c[h][4 * l4 + 1] = fmaf(-v[h], z.y, c[h][4 * l4 + 1]);
+                c[h][4 * l4 + 2] = fmaf(-v[h], z.z, c[h][4 * l4 + 2]);
+                c[h][4 * l4 + 3] = fmaf(-v[h], z.w, c[h][4 * l4 + 3]);
+            }
         }
     }
 }
@@ -271,6 +285,7 @@ k_panel_row(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
     extern __shared__ __align__(16) float sm[];
     __shared__ uint64_t xbar[2];
     __shared__ uint64_t ybar[2];
+    __shared__ uint64_t lbar;                        // bulk loads of the staged columns
     __shared__ volatile int s_abort;
 
     cg::cluster_group cluster = cg::this_cluster();
@@ -296,31 +311,47 @@ k_panel_row(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
         tc::mbar_init(&xbar[1], 1);
         tc::mbar_init(&ybar[0], 1);
         tc::mbar_init(&ybar[1], 1);
+        tc::mbar_init(&lbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_abort = 0;
     }
+    __syncthreads();                                 // the bulk loads' barrier is initialised
 
-    // the rows, loaded straight into registers (a warp reads 128 contiguous bytes of
-    // each column); columns past the panel and rows past the matrix are zero
+    // the rows, in registers: loaded straight from F (a warp reads 128 contiguous bytes
+    // of each column) or, with the fused update, from the staged columns after it;
+    // columns past the panel and rows past the matrix are zero
     float a[RPT][RP_NB];
+    if (!fused) {
 #pragma unroll
-    for (int h = 0; h < RPT; ++h)
+        for (int h = 0; h < RPT; ++h)
 #pragma unroll
-        for (int l = 0; l < RP_NB; ++l)
-            a[h][l] = (live[h] && l < ncols) ? F[(k + g[h]) + (k + l) * ld] : 0.f;
+            for (int l = 0; l < RP_NB; ++l)
+                a[h][l] = (live[h] && l < ncols) ? F[(k + g[h]) + (k + l) * ld] : 0.f;
+    }
 
     if (fused) {
-        // the previous panel's reflectors on the same rows; C and V staged column-major
+        // this panel's columns (C) and the previous panel's reflectors (V) on the CTA's
+        // rows, staged column-major by bulk copies of each column's rows.  The factor's
+        // rows are padded with zeros to a multiple of 4 (the copies' 16-byte granule);
+        // the staged rows past those and C's columns past the panel are zeroed here.
         float *Sc = sm + L.Sc(), *SVc = sm + L.SVc();
-#pragma unroll
-        for (int h = 0; h < RPT; ++h) {
-            const int r = threadIdx.x + h * NT;
-#pragma unroll
-            for (int l = 0; l < RP_NB; ++l) Sc[l * rpc + r] = a[h][l];
-#pragma unroll
-            for (int q = 0; q < RP_NB; ++q)
-                SVc[q * rpc + r] = live[h] ? F[(k + g[h]) + (kp + q) * ld] : 0.f;
+        const int nown = (int)fl_max64(0, fl_min64(rpc, M - c0));
+        const int nrow4 = (nown + 3) & ~3;
+        if (threadIdx.x == 0) {
+            const uint32_t bytes = (uint32_t)nrow4 * 4u;
+            rp_expect_tx(&lbar, bytes * (uint32_t)(ncols + RP_NB));
+            if (nrow4 > 0) {
+                for (int l = 0; l < ncols; ++l) rp_bulk_load(Sc + l * rpc, F + (k + c0) + (k + l) * ld, bytes, &lbar);
+                for (int q = 0; q < RP_NB; ++q) rp_bulk_load(SVc + q * rpc, F + (k + c0) + (kp + q) * ld, bytes, &lbar);
+            }
         }
+        for (int idx = threadIdx.x; idx < RP_NB * (rpc - nrow4); idx += NT) {
+            const int l = idx / (rpc - nrow4), r = nrow4 + idx % (rpc - nrow4);
+            Sc[l * rpc + r] = 0.f;
+            SVc[l * rpc + r] = 0.f;
+        }
+        for (int idx = threadIdx.x; idx < (RP_NB - ncols) * nrow4; idx += NT)
+            Sc[(ncols + idx / nrow4) * rpc + idx % nrow4] = 0.f;
         float *Tp = sm + L.Tp();
         for (int idx = threadIdx.x; idx < 1024; idx += NT) Tp[idx] = Tprev[idx];
         if (rank == 0) {
@@ -334,18 +365,20 @@ k_panel_row(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
             }
         }
     }
+    if (fused && !tc::mbar_wait(&lbar, 0u, RP_SPIN)) {
+        s_abort = 1;
+        atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
+    }
     cluster.sync();                                  // barriers ready before any remote signal;
                                                      // staged data visible to the CTA
     if (fused) {
         rp_prev_y<RPT>(L, sm, rank, CL, flag, ybar, &s_abort);
         const float *Sc = sm + L.Sc(), *SVc = sm + L.SVc(), *Zs = sm + L.Zs();
 #pragma unroll
-        for (int h = 0; h < RPT; ++h) {
-            const int r = threadIdx.x + h * NT;
+        for (int h = 0; h < RPT; ++h)
 #pragma unroll
-            for (int l = 0; l < RP_NB; ++l) a[h][l] = Sc[l * rpc + r];   // (registers free above)
-            rp_apply_row(SVc, rpc, r, Zs, a[h]);
-        }
+            for (int l = 0; l < RP_NB; ++l) a[h][l] = Sc[l * rpc + threadIdx.x + h * NT];
+        rp_apply_rows<RPT>(SVc, rpc, NT, Zs, a);
         if (rank == 0) {
             const float *CT = sm + L.CT(), *VT = sm + L.VT();
             for (int idx = threadIdx.x; idx < 1024; idx += NT) {
