@@ -182,8 +182,15 @@ def _algorithmic(kernel, m, n, m_aug, nb, nrhs, refine, nb_elem):
         return "bytes", 8.0 * m * n
     if kernel == "panel":                              # slice read + written once per panel
         return "bytes", sum(2.0 * (m_aug - k) * c * e for k, c in panels)
-    if kernel in ("trail_simt", "trail_tc"):           # Y = V^T C and C -= V Z: 4 (m-k) c nct
+    if kernel == "trail_simt":                         # Y = V^T C and C -= V Z: 4 (m-k) c nct
         return "flops", sum(4.0 * (m_aug - k) * c * (n + nrhs - (k + c)) for k, c in panels)
+    if kernel == "trail_tc":
+        # 128 TF32x3 products (384 tensor flops) per 12 bytes of C (read twice, written
+        # once) is below the tensor ridge (measured TF32 / HBM, about 140 flop per byte):
+        # HBM is the roof.  Bytes: C read twice and written once, V read once and written
+        # once as the operand image (hi, lo), per panel
+        return "bytes", sum((12.0 * (n + nrhs - (k + c)) + 4.0 * c + 8.0 * 32) * (m_aug - k)
+                            for k, c in panels)
     if kernel == "apply_q":                            # V read twice per application
         return "bytes", refine * sum(2.0 * (m_aug - k) * c * e for k, c in panels)
     if kernel == "trsv":                               # upper triangle read once per solve
