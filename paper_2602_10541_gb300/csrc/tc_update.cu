@@ -3,7 +3,7 @@
 //   x = hi + lo (hi = tf32 rounding of x, lo = x - hi), a*b ~ ah*bh + ah*bl + al*bh.
 // For panel k with Householder block V (m_p x 32, unit lower trapezoidal) and
 // compact-WY factor T, C -= V (T^T (V^T C)) in two kernels:
-//   k_tcy : Y^T = C^T V over a split of the rows (MMA M = 128 columns of C, N = 32,
+//   k_tcy : Y^T = C^T V over interleaved row chunks (MMA M = 128 columns of C, N = 32,
 //           K = rows in chunks of 32).  A ring of 6 landing slots is filled by TMA: a C
 //           chunk (32 rows x 128 columns) and a V chunk (32 rows x 32 columns) land in
 //           the K-major 128-byte-swizzled layout the MMA reads (the column-major factor
@@ -143,7 +143,7 @@ constexpr int TY_PER = (TY_QA + TY_QB + 32 * TY_CONV - 1) / (32 * TY_CONV);   //
 
 __global__ void __launch_bounds__(TY_THREADS, 1)
 k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMap mV, int64_t k, int ncols,
-      int64_t nct, int64_t coff, int64_t mp, int64_t rows_per_split, float *__restrict__ Ypart,
+      int64_t nct, int64_t coff, int64_t mp, float *__restrict__ Ypart,
       float *__restrict__ Zimg, const float *__restrict__ Tblk, int *__restrict__ counters, int *flag)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -155,9 +155,11 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t cbase = (int64_t)blockIdx.x * TY_C;
-    const int64_t rs0 = (int64_t)blockIdx.y * rows_per_split;
-    const int64_t rs1 = fl_min64(mp, rs0 + rows_per_split);
-    const int nchunks = (int)fl_max64(0, fl_cdiv_dev(rs1 - rs0, TY_K));
+    // chunk ch of this CTA is the panel's 32-row chunk blockIdx.y + ch * gridDim.y: the
+    // CTAs of a column tile read neighbouring pieces of each column at the same time
+    const int64_t tchunks = fl_cdiv_dev(mp, TY_K), S = gridDim.y;
+    const int nchunks = (int)fl_max64(0, fl_cdiv_dev(tchunks - blockIdx.y, S));
+    auto row0 = [&](int ch) { return ((int64_t)blockIdx.y + (int64_t)ch * S) * TY_K; };
 
     if (warp == 0) tc::tmem_alloc(&tmem_slot, 32);
     if (threadIdx.x == 0) {
@@ -182,7 +184,7 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
     if (warp == 0) {
         if (lane == 0) {
             // TMA coordinates: x = row of the factor, y = column
-            const int x0 = (int)(k + rs0), yc = (int)(k + ncols + coff + cbase), yv = (int)k;
+            const int yc = (int)(k + ncols + coff + cbase), yv = (int)k;
             for (int ch = 0; ch < nchunks; ++ch) {
                 const int s = ch % TY_LAND;
                 if (ch >= TY_LAND &&
@@ -193,8 +195,8 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
                 if (s_fail) break;
                 unsigned char *A = land + s * TY_SLOT;
                 expect_tx(&full[s], TY_SLOT);
-                tma_load_2d(A, &mC, x0 + ch * TY_K, yc, &full[s]);
-                tma_load_2d(A + TY_A, &mV, x0 + ch * TY_K, yv, &full[s]);
+                tma_load_2d(A, &mC, (int)(k + row0(ch)), yc, &full[s]);
+                tma_load_2d(A + TY_A, &mV, (int)(k + row0(ch)), yv, &full[s]);
                 s_last_load[s] = ch;
             }
         }
@@ -255,7 +257,7 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
                 const int q = ct + u * 32 * TY_CONV;
                 x[u] = (q < TY_QA + TY_QB) ? hi[q] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            const int64_t r0 = rs0 + (int64_t)ch * TY_K;
+            const int64_t r0 = row0(ch);
 #pragma unroll
             for (int u = 0; u < TY_PER; ++u) {
                 const int q = ct + u * 32 * TY_CONV;
@@ -505,10 +507,10 @@ int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_
     }
     const int64_t mp = m_aug - k;
     const int64_t ctiles = fl_cdiv(nct, TY_C);
-    // about one wave of k_tcy CTAs, each streaming at least 16 chunks of rows
-    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(fl_cdiv(ctx->num_sms, ctiles), fl_cdiv(mp, 16 * TY_K)));
-    const int64_t rows_per_split = fl_round_up(fl_cdiv(mp, nsplit), TY_K);
-    nsplit = fl_cdiv(mp, rows_per_split);
+    // one wave of k_tcy CTAs (one per SM) beside the 16-SM cluster of the next panel,
+    // each streaming at least 16 chunks of rows
+    const int64_t free_sms = std::max<int64_t>(1, ctx->num_sms - 16);
+    const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(free_sms / ctiles, fl_cdiv(mp, 16 * TY_K)));
     const int64_t rblocks = fl_cdiv(mp, TU_R);
     float *Vimg = (float *)fl_ws(ctx, FL_WS_VIMG, (size_t)rblocks * 2 * TU_R * 32 * sizeof(float));
     float *Ypart = (float *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(float) * nsplit * 32 * nct);
@@ -519,7 +521,7 @@ int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_
     k_vimg<<<(unsigned)rblocks, TU_R, 0, ctx->stream>>>(F, ld, k, ncols, mp, Vimg);
     FL_CHECK_LAUNCH(ctx, "tc_vimg");
     k_tcy<<<dim3((unsigned)ctiles, (unsigned)nsplit), TY_THREADS, smem_y, ctx->stream>>>(
-        maps.c, maps.v, k, ncols, nct, coff, mp, rows_per_split, Ypart, Zimg, Tblk, counters, ctx->d_flag);
+        maps.c, maps.v, k, ncols, nct, coff, mp, Ypart, Zimg, Tblk, counters, ctx->d_flag);
     FL_CHECK_LAUNCH(ctx, "tc_y");
     k_tcu<<<dim3((unsigned)rblocks, (unsigned)fl_cdiv(nct, TU_C)), TU_THREADS, smem_u, ctx->stream>>>(
         maps.t, F, ld, k, ncols, nct, coff, mp, Vimg, Zimg, ctx->d_flag);

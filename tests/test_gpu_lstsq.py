@@ -221,6 +221,38 @@ def test_helmholtz2d_full_size(ctx):
     assert st.resid_norm[2] <= st.resid_norm[0]
 
 
+def test_concurrent_solves_are_bit_identical():
+    """Independent solves queued together, each on its own context and stream (the
+    bench's step), give the same bits as the same solves one after another."""
+    B = 3
+    shapes = [dict(n_int=3000, n_bc=512, n_feat=640), dict(n_int=2500, n_bc=384, n_feat=512),
+              dict(n_int=3500, n_bc=512, n_feat=700)]
+    ref = []
+    for i in range(B):
+        c = fl.Context(0)
+        s = pl.LinearSolver(c, pl.upload(wl.helmholtz2d(seed_offset=i, **shapes[i])), prec=fl.PREC_MIXED,
+                            max_refine=2)
+        s.step()
+        ref.append(s.beta.clone())
+    torch.cuda.synchronize()
+    solvers = []
+    for i in range(B):
+        c = fl.Context(0, stream=torch.cuda.Stream())
+        with torch.cuda.stream(c.stream):
+            solvers.append(pl.LinearSolver(c, pl.upload(wl.helmholtz2d(seed_offset=i, **shapes[i])),
+                                           prec=fl.PREC_MIXED, max_refine=2))
+    torch.cuda.synchronize()
+    batch = pl.ConcurrentSolves(solvers)
+    origin = torch.cuda.current_stream()
+    for _ in range(2):
+        for sv in solvers:
+            sv.beta.zero_()
+        batch.step(origin)
+        origin.synchronize()
+        for sv, r in zip(solvers, ref):
+            assert torch.equal(sv.beta, r)
+
+
 def test_overlapped_fp64_assembly_is_bit_identical(ctx):
     """The FP64 operator assembled on a side stream (the refinement waits on its
     event) gives the same bits as the serial schedule: the same kernels on the same
