@@ -233,6 +233,36 @@ def _secondary(fl, pl, wl, torch, ctx, dev, n_inverse):
     out["newton_workload"] = ("bratu2d: Lap u + e^u = 0, [0,1]^2, 8192 interior + 1024 boundary rows, "
                               "2048 features sigma=6, mu=1e-10, Newton from beta=0, <=15 iterations")
     # inverse problem: observations from the forward map at theta_true, gradients at theta_0
+    # the cubic Newton problems (Sec. 3.3 NL-Poisson, NL-Helmholtz k = 3): N(u) = u^3,
+    # manufactured u*, sources and Dirichlet data from the GPU's problem catalogue
+    for name, precs in (("nlpoisson2d", (("mixed", fl.PREC_MIXED), ("fp64", fl.PREC_FP64))),
+                        ("nlhelmholtz2d", (("mixed", fl.PREC_MIXED),))):
+        wc = getattr(wl, name)()
+        xi, xb, Wc, bc, xt = t(wc.x_int), t(wc.x_bc), t(wc.W), t(wc.b), t(wc.x_test)
+        f = torch.empty(wc.n_int, dtype=torch.float64, device=dev)
+        g = torch.empty(wc.n_bc, dtype=torch.float64, device=dev)
+        ue = torch.empty(xt.shape[0], dtype=torch.float64, device=dev)
+        fl.fastlsq_rhs(ctx, wc.problem, fl.RHS_SOURCE, wc.params, xi, 1.0, f)
+        fl.fastlsq_rhs(ctx, wc.problem, fl.RHS_EXACT, wc.params, xb, 1.0, g)
+        fl.fastlsq_rhs(ctx, wc.problem, fl.RHS_EXACT, wc.params, xt, 1.0, ue)
+        for pname, prec in precs:
+            beta = torch.zeros(wc.n_feat, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, st = fl.fastlsq_newton(ctx, xi, xb, fl.Op(wc.alpha, wc.coef), fl.NL_CUBIC, wc.nl_lam, wc.lam_bc,
+                                       f, g, Wc, bc, wc.scale, beta, max_iter=12, tol=1e-10, mu=wc.mu,
+                                       prec=prec, max_refine=64, refine_tol=1e-13)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            u = torch.empty(xt.shape[0], dtype=torch.float64, device=dev)
+            fl.fastlsq_eval(ctx, xt, Wc, bc, wc.scale, beta, u)
+            out[f"newton_{name}_{pname}"] = {
+                "seconds": sec, "iters": int(st.iters), "status": int(st.status),
+                "seconds_per_iter": sec / max(1, int(st.iters)),
+                "rel_l2_vs_exact": pl.rel_l2(u, ue), "last_step_rel": float(st.step_rel[max(0, st.iters - 1)]),
+                "workload": (f"{name}: 8192 interior + 1024 boundary rows, 2048 features sigma={wc.sigma:g}, "
+                             "u^3 term, manufactured u* = sin(pi x) sin(pi y) + x y / 2, mu=1e-10, <=12 iterations")}
+
     op = fl.Op([[2, 0], [0, 2]], [-1.0, -1.0])
     insts, ws = [], []
     for q in range(n_inverse):

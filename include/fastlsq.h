@@ -145,6 +145,10 @@ typedef enum {
                                        /* u* = sin(pi x) sin(2 pi y) + 0.3 cos(3 pi x + pi y)       */
     FASTLSQ_PROBLEM_POISSON_5D = 3,    /* -Lap u = f, u* = sum_k sin(pi x_k) + prod_k x_k           */
     FASTLSQ_PROBLEM_BRATU_2D = 4,      /* Lap u + lam e^u = 0, u = 0 on the boundary (f = g = 0)    */
+    FASTLSQ_PROBLEM_NLPOISSON_2D = 6,  /* -Lap u + lam u^3 = f, params[0] = lam (Sec. 3.3 NL-Poisson;  */
+                                       /* u* = sin(pi x) sin(pi y) + x y / 2, Dirichlet data u*)      */
+    FASTLSQ_PROBLEM_NLHELMHOLTZ_2D = 7, /* Lap u + k^2 u + lam u^3 = f, params = (k, lam) (Sec. 3.3  */
+                                       /* NL-Helmholtz; the same u*)                                  */
     FASTLSQ_PROBLEM_GAUSS_SOURCE_2D = 5 /* -Lap u = sum_k a_k exp(-|x-c_k|^2/(2 w_k^2)), params =   */
                                        /* theta [n_src][4] = (c_x, c_y, w, a)                      */
 } fastlsq_problem;

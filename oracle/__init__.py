@@ -32,6 +32,8 @@ HELMHOLTZ_2D = 2
 POISSON_5D = 3
 BRATU_2D = 4
 GAUSS_SOURCE_2D = 5
+NLPOISSON_2D = 6
+NLHELMHOLTZ_2D = 7
 
 NL_NONE, NL_EXP, NL_CUBIC = 0, 1, 2
 

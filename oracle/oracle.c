@@ -251,7 +251,11 @@ enum {
                            /* u* = sin(pi x) sin(2 pi y) + 0.3 cos(3 pi x + pi y)               */
     ORC_POISSON_5D = 3,    /* -Lap u = f on [0,1]^5; u* = sum_k sin(pi x_k) + prod_k x_k        */
     ORC_BRATU_2D = 4,      /* Lap u + lam e^u = 0, u = 0 on the boundary (no closed form)       */
-    ORC_GAUSS_SOURCE_2D = 5 /* -Lap u = s(x; theta), u = 0 on the boundary; params = theta      */
+    ORC_GAUSS_SOURCE_2D = 5, /* -Lap u = s(x; theta), u = 0 on the boundary; params = theta     */
+    /* the cubic Newton problems of Sec. 3.3 ("u^3 term"; the equations are this reading):    */
+    /* u* = sin(pi x) sin(pi y) + x y / 2 on [0,1]^2, Dirichlet data u* on the boundary        */
+    ORC_NLPOISSON_2D = 6,  /* -Lap u + lam u^3 = f; params[0] = lam                              */
+    ORC_NLHELMHOLTZ_2D = 7 /* Lap u + k^2 u + lam u^3 = f; params = (k, lam)                     */
 };
 
 /* s(x; theta) = sum_k a_k exp(-|x - c_k|^2 / (2 w_k^2)), theta_k = (c_kx, c_ky, w_k, a_k). */
@@ -283,6 +287,8 @@ void orc_problem_exact(int prob, const double *x, long n, int d,
             double sum = 0.0, prod = 1.0;
             for (int k = 0; k < d; ++k) { sum += sin(pi * p[k]); prod *= p[k]; }
             v = sum + prod;
+        } else if (prob == ORC_NLPOISSON_2D || prob == ORC_NLHELMHOLTZ_2D) {
+            v = sin(pi * p[0]) * sin(pi * p[1]) + 0.5 * p[0] * p[1];
         }
         u[i] = v;
     }
@@ -311,6 +317,14 @@ void orc_problem_source(int prob, const double *x, long n, int d,
             v = pi * pi * sum;
         } else if (prob == ORC_GAUSS_SOURCE_2D) {
             v = orc_gauss(p, params, n_params / 4);
+        } else if (prob == ORC_NLPOISSON_2D || prob == ORC_NLHELMHOLTZ_2D) {
+            /* Lap of sin(pi x) sin(pi y) is -2 pi^2 times it; x y is harmonic */
+            double s = sin(pi * p[0]) * sin(pi * p[1]);
+            double u = s + 0.5 * p[0] * p[1];
+            if (prob == ORC_NLPOISSON_2D)
+                v = 2 * pi * pi * s + params[0] * u * u * u;
+            else
+                v = -2 * pi * pi * s + params[0] * params[0] * u + params[1] * u * u * u;
         }
         f[i] = v;
     }

@@ -369,8 +369,13 @@ extern "C" int fastlsq_rhs(fastlsq_ctx *ctx, fastlsq_problem problem, fastlsq_rh
     if (!ctx) return FASTLSQ_ERR_INVALID;
     if (n < 0 || d < 1 || d > FL_MAX_D || n_params < 0 || (n_params > 0 && !params))
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "rhs: bad arguments");
-    if (problem < FASTLSQ_PROBLEM_POISSON_1D || problem > FASTLSQ_PROBLEM_GAUSS_SOURCE_2D)
+    if (problem < FASTLSQ_PROBLEM_POISSON_1D || problem > FASTLSQ_PROBLEM_NLHELMHOLTZ_2D)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "rhs: unknown problem %d", (int)problem);
+    if (kind == FASTLSQ_RHS_SOURCE &&
+        ((problem == FASTLSQ_PROBLEM_NLPOISSON_2D && n_params < 1) ||
+         (problem == FASTLSQ_PROBLEM_NLHELMHOLTZ_2D && n_params < 2) ||
+         (problem == FASTLSQ_PROBLEM_HELMHOLTZ_2D && n_params < 1)))
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "rhs: problem %d needs more parameters", (int)problem);
     if (n == 0) return 0;
     if (!x || !out) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "rhs: null array");
     return fl_launch_rhs(ctx, problem, kind, params, n_params, x, n, d, weight, out);

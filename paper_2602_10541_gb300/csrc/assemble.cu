@@ -338,6 +338,16 @@ __global__ void k_rhs(int problem, int kind, fl_problem_params prm, const double
         v = (kind == FASTLSQ_RHS_EXACT) ? sum + prod : pi * pi * sum;
         break;
     }
+    case FASTLSQ_PROBLEM_NLPOISSON_2D:
+    case FASTLSQ_PROBLEM_NLHELMHOLTZ_2D: {
+        // u* = sin(pi x) sin(pi y) + x y / 2; Lap u* = -2 pi^2 sin(pi x) sin(pi y)
+        const double sp = sin(pi * p[0]) * sin(pi * p[1]);
+        const double us = sp + 0.5 * p[0] * p[1];
+        if (kind == FASTLSQ_RHS_EXACT) v = us;
+        else if (problem == FASTLSQ_PROBLEM_NLPOISSON_2D) v = 2 * pi * pi * sp + prm.p[0] * us * us * us;
+        else v = -2 * pi * pi * sp + prm.p[0] * prm.p[0] * us + prm.p[1] * us * us * us;
+        break;
+    }
     case FASTLSQ_PROBLEM_GAUSS_SOURCE_2D:
         if (kind == FASTLSQ_RHS_SOURCE) {
             for (int k = 0; k + 3 < prm.n; k += 4) {

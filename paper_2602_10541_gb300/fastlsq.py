@@ -23,6 +23,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 REFINE_CLASSICAL, REFINE_CGLS = 0, 1
 RHS_SOURCE, RHS_EXACT = 0, 1
 POISSON_1D, HELMHOLTZ_2D, POISSON_5D, BRATU_2D, GAUSS_SOURCE_2D = 1, 2, 3, 4, 5
+NLPOISSON_2D, NLHELMHOLTZ_2D = 6, 7
 NL_NONE, NL_EXP, NL_CUBIC = 0, 1, 2
 
 _vp = ctypes.c_void_p

@@ -185,6 +185,36 @@ def bratu2d(n_int=8192, n_bc=1024, n_feat=2048, lam=1.0):
     return w
 
 
+def nlpoisson2d(n_int=8192, n_bc=1024, n_feat=2048, lam=1.0):
+    """-Lap u + lam u^3 = f on [0,1]^2 (Sec. 3.3 NL-Poisson, sigma = 3), manufactured
+    u* = sin(pi x) sin(pi y) + x y / 2 with Dirichlet data u* (problem 6); Newton from
+    beta = 0, mu = 1e-10, boundary weight 100."""
+    s = SEED0 + 6
+    alpha, coef = _laplacian_terms(2, -1.0)
+    w = Workload("nlpoisson2d", 6, 2, n_int, n_bc, n_feat, 3.0, 100.0, alpha, coef,
+                 np.array([lam]), s, mu=1e-10, nl_kind=2, nl_lam=lam)
+    w.x_int = uniform(s + 100, "x_int", n_int * 2).reshape(n_int, 2)
+    w.x_bc = box_boundary(s + 100, "x_bc", n_bc, 2, per_face=True)
+    w.W, w.b = _features(s, n_feat, 2, w.sigma)
+    w.x_test = uniform(s + 200, "test", 5000 * 2).reshape(-1, 2)
+    return w
+
+
+def nlhelmholtz2d(n_int=8192, n_bc=1024, n_feat=2048, k=3.0, lam=1.0):
+    """Lap u + k^2 u + lam u^3 = f on [0,1]^2 (Sec. 3.3 NL-Helmholtz, k = 3, sigma = 5),
+    the same manufactured u* (problem 7); Newton from beta = 0, mu = 1e-10, boundary
+    weight 100."""
+    s = SEED0 + 7
+    alpha = np.array([[2, 0], [0, 2], [0, 0]], np.int32)
+    w = Workload("nlhelmholtz2d", 7, 2, n_int, n_bc, n_feat, 5.0, 100.0, alpha,
+                 np.array([1.0, 1.0, k * k]), np.array([k, lam]), s, mu=1e-10, nl_kind=2, nl_lam=lam)
+    w.x_int = uniform(s + 100, "x_int", n_int * 2).reshape(n_int, 2)
+    w.x_bc = box_boundary(s + 100, "x_bc", n_bc, 2, per_face=True)
+    w.W, w.b = _features(s, n_feat, 2, w.sigma)
+    w.x_test = uniform(s + 200, "test", 5000 * 2).reshape(-1, 2)
+    return w
+
+
 def gauss_theta(seed: int, name: str, n_src: int = 4) -> np.ndarray:
     """theta_k = (c_kx, c_ky, w_k, a_k): centres U(0.2,0.8)^2, widths U(0.05,0.15),
     amplitudes U(0.5,2)."""

@@ -79,3 +79,54 @@ def test_newton_bratu_full_size(ctx):
     uc = torch.empty(1, dtype=torch.float64, device=DEV)
     fl.fastlsq_eval(ctx, _t([[0.5, 0.5]]), _t(w.W), _t(w.b), w.scale, beta_m, uc)
     assert 0.078 < uc.item() < 0.079
+
+
+def _u_star(x):
+    return np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) + 0.5 * x[:, 0] * x[:, 1]
+
+
+def _cubic_newton(ctx, w, prec, max_iter, f, g, tol=1e-10):
+    beta = torch.zeros(w.n_feat, dtype=torch.float64, device=DEV)
+    rc, st = fl.fastlsq_newton(ctx, _t(w.x_int), _t(w.x_bc), fl.Op(w.alpha, w.coef), fl.NL_CUBIC,
+                               w.nl_lam, w.lam_bc, f, g, _t(w.W), _t(w.b), w.scale, beta,
+                               max_iter=max_iter, tol=tol, mu=w.mu, prec=prec, max_refine=64,
+                               refine_tol=1e-13)
+    return beta, rc, st
+
+
+@pytest.mark.parametrize("name", ["nlpoisson2d", "nlhelmholtz2d"])
+@pytest.mark.parametrize("prec,bar", [(fl.PREC_FP64, 1e-9), (fl.PREC_MIXED, 1e-5)])
+def test_newton_cubic_steps_match_oracle(ctx, name, prec, bar):
+    """The cubic Newton problems (N(u) = lam u^3, Jacobian term 3 lam u^2 H): three
+    steps from beta = 0 against the oracle's, with the sources from the oracle."""
+    w = getattr(wl, name)(n_int=1200, n_bc=256, n_feat=320)
+    f = oracle.problem_source(w.problem, w.x_int, w.params)
+    g = _u_star(w.x_bc)
+    iters = 3
+    beta_o, st_o, it_o, hist_o = oracle.newton(w.x_int, w.x_bc, w.alpha, w.coef, oracle.NL_CUBIC, w.nl_lam,
+                                               w.lam_bc, f, g, w.W, w.b, w.scale, mu=w.mu,
+                                               max_iter=iters, tol=0.0)
+    beta, rc, st = _cubic_newton(ctx, w, prec, iters, _t(f), _t(g), tol=0.0)
+    assert st.iters == it_o == iters
+    u_o = oracle.eval_u(w.x_test, w.W, w.b, w.scale, beta_o)
+    u = _u(ctx, w, beta)
+    assert np.linalg.norm(u - u_o) / np.linalg.norm(u_o) <= bar
+    np.testing.assert_allclose(st.res_norm[:2], hist_o[:2], rtol=1e-6 if prec == fl.PREC_FP64 else 1e-4)
+
+
+def test_newton_nlpoisson_full_size(ctx):
+    """NL-Poisson at the Bratu sizes (8192 + 1024 rows, 2048 features), sources from the
+    GPU's problem catalogue: MIXED within 1e-6 of u* and of the FP64 run."""
+    w = wl.nlpoisson2d()
+    f = torch.empty(w.n_int, dtype=torch.float64, device=DEV)
+    g = torch.empty(w.n_bc, dtype=torch.float64, device=DEV)
+    fl.fastlsq_rhs(ctx, fl.NLPOISSON_2D, fl.RHS_SOURCE, w.params, _t(w.x_int), 1.0, f)
+    fl.fastlsq_rhs(ctx, fl.NLPOISSON_2D, fl.RHS_EXACT, w.params, _t(w.x_bc), 1.0, g)
+    np.testing.assert_allclose(g.cpu().numpy(), _u_star(w.x_bc), rtol=0, atol=1e-14)
+    beta_m, rc_m, st_m = _cubic_newton(ctx, w, fl.PREC_MIXED, 12, f, g)
+    beta_d, rc_d, st_d = _cubic_newton(ctx, w, fl.PREC_FP64, 12, f, g)
+    u_m, u_d = _u(ctx, w, beta_m), _u(ctx, w, beta_d)
+    ue = _u_star(w.x_test)
+    assert np.linalg.norm(u_d - ue) / np.linalg.norm(ue) <= 1e-6
+    assert np.linalg.norm(u_m - ue) / np.linalg.norm(ue) <= 1e-6
+    assert np.linalg.norm(u_m - u_d) / np.linalg.norm(u_d) <= 1e-6 + 10 * st_d.step_rel[st_d.iters - 1]

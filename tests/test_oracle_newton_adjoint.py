@@ -155,3 +155,46 @@ def test_adjoint_coefficient_gradient_matches_central_differences():
             losses.append(oracle.inverse_adjoint(Ap, rhs, Hs, y, mu)["loss"])
         fd = (losses[0] - losses[1]) / (2 * h)
         assert abs(g - fd) <= 1e-5 * (abs(fd) + 1e-12), (t, g, fd)
+
+
+def _u_star(x):
+    """u* = sin(pi x) sin(pi y) + x y / 2 of the cubic problems, written out here."""
+    return np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) + 0.5 * x[:, 0] * x[:, 1]
+
+
+@pytest.mark.parametrize("name", ["nlpoisson2d", "nlhelmholtz2d"])
+def test_cubic_sources_match_the_operator_on_u_star(name):
+    """f of the cubic problems = L[u*] + lam u*^3, with L[u*] by central differences
+    of the closed form (h = 1e-4, error O(h^2))."""
+    w = getattr(wl, name)(n_int=200, n_bc=8, n_feat=8)
+    x = w.x_int
+    h = 1e-4
+    lap = np.zeros(len(x))
+    for k in range(2):
+        e = np.zeros(2)
+        e[k] = h
+        lap += (_u_star(x + e) - 2 * _u_star(x) + _u_star(x - e)) / h ** 2
+    u = _u_star(x)
+    lam = w.nl_lam
+    ref = (-lap + lam * u ** 3) if name == "nlpoisson2d" else (lap + 9.0 * u + lam * u ** 3)
+    f = oracle.problem_source(w.problem, x, w.params)
+    np.testing.assert_allclose(f, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+    np.testing.assert_allclose(oracle.problem_exact(w.problem, w.x_bc, w.params), _u_star(w.x_bc),
+                               rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("name", ["nlpoisson2d", "nlhelmholtz2d"])
+def test_newton_cubic_recovers_the_manufactured_solution(name):
+    """Newton from beta = 0 on the cubic problems (Sec. 3.3, mu = 1e-10, backtracking)
+    converges, and u agrees with u* on the test set to the basis' accuracy."""
+    w = getattr(wl, name)(n_int=1200, n_bc=256, n_feat=320)
+    f = oracle.problem_source(w.problem, w.x_int, w.params)
+    g = _u_star(w.x_bc)
+    beta, status, iters, hist = oracle.newton(w.x_int, w.x_bc, w.alpha, w.coef, oracle.NL_CUBIC, w.nl_lam,
+                                              w.lam_bc, f, g, w.W, w.b, w.scale, mu=w.mu, max_iter=20,
+                                              tol=1e-10)
+    assert hist[-1] < 1e-3 * hist[0]
+    u = oracle.eval_u(w.x_test, w.W, w.b, w.scale, beta)
+    ue = _u_star(w.x_test)
+    err = np.linalg.norm(u - ue) / np.linalg.norm(ue)
+    assert err < 1e-6, (status, iters, err)
