@@ -263,6 +263,51 @@ def _secondary(fl, pl, wl, torch, ctx, dev, n_inverse):
                 "workload": (f"{name}: 8192 interior + 1024 boundary rows, 2048 features sigma={wc.sigma:g}, "
                              "u^3 term, manufactured u* = sin(pi x) sin(pi y) + x y / 2, mu=1e-10, <=12 iterations")}
 
+    # cached re-solves (App. F.4): factor the helmholtz2d operator once, then solve for
+    # new right-hand sides (Q^T b, R^{-1}, two refinement steps) against the kept factor
+    wr = wl.helmholtz2d()
+    dpr = pl.upload(wr, dev)
+    sr = pl.LinearSolver(ctx, dpr, prec=fl.PREC_MIXED, max_refine=2)
+    sr.build_rhs()
+    sr.assemble()
+    fac = sr.solve(keep=True)
+    n_resolve = 20
+    rhs = sr.rhs.repeat(n_resolve, 1) * torch.linspace(0.5, 1.5, n_resolve, dtype=torch.float64,
+                                                      device=dev).unsqueeze(1)
+    betas = torch.zeros((n_resolve, wr.n_feat), dtype=torch.float64, device=dev)
+    fl.fastlsq_factor_solve(ctx, fac, rhs[:1], betas[:1], max_refine=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fl.fastlsq_factor_solve(ctx, fac, rhs, betas, max_refine=2)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    # the solution is linear in the right-hand side: u(1.5 b) = 1.5 u(b) on the test set
+    # (beta itself is not determined elementwise: the system's condition number is large)
+    fl.fastlsq_factor_destroy(ctx, fac)
+    u_a = sr.u_test()
+    u_b = sr.u_test(beta=betas[-1])
+    lin = pl.rel_l2(u_b, 1.5 * u_a)
+    out["resolve"] = {"rhs": n_resolve, "seconds": sec, "resolves_per_s": n_resolve / sec,
+                      "u_rel_diff_scaled_rhs": lin,
+                      "workload": ("helmholtz2d (9216 x 2048) MIXED factor kept; 20 right-hand sides, each Q^T b, "
+                                   "R^{-1} and 2 classical refinement steps")}
+    # L u at arbitrary points (the gradient of the helmholtz2d solution at 200,000 points)
+    xg = torch.rand((200000, 2), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(7))
+    gx = torch.empty(200000, dtype=torch.float64, device=dev)
+    ops = [fl.Op([[1, 0]], [1.0]), fl.Op([[0, 1]], [1.0])]
+    for o in ops:
+        fl.fastlsq_eval_op(ctx, xg, o, dpr.W, dpr.b, wr.scale, sr.beta[0], gx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for o in ops:
+        fl.fastlsq_eval_op(ctx, xg, o, dpr.W, dpr.b, wr.scale, sr.beta[0], gx)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    out["eval_grad"] = {"points": 200000, "components": 2, "seconds": sec,
+                        "point_feature_pairs_per_s": 2 * 200000 * wr.n_feat / sec,
+                        "workload": "d u/dx and d u/dy of the helmholtz2d solution (2048 features) at 200,000 points, FP64"}
+    del sr, dpr
+
     op = fl.Op([[2, 0], [0, 2]], [-1.0, -1.0])
     insts, ws = [], []
     for q in range(n_inverse):

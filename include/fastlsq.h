@@ -166,6 +166,19 @@ FASTLSQ_API int fastlsq_rhs(fastlsq_ctx *ctx, fastlsq_problem problem, fastlsq_r
                 int32_t d, double weight, double *out);
 
 /*
+ * Evaluate a linear operator of the approximation at points (eq. cyclic applied to
+ * u = scale * sum_j beta_j sin(W_j.x + b_j)): u[e] = (L u)(x_e) for the operator L of
+ * `op` (terms c_t D^{alpha_t}), e.g. a gradient component (one term, alpha = e_k), the
+ * Laplacian, or the PDE residual's linear part; FP64.  Per-point coefficients
+ * (op->n_pp > 0) are not allowed (they belong to collocation rows).  x: [n_eval][d]
+ * with d = op->d; W: [n_feat][d]; b, beta: [n_feat]; u: [n_eval] (all device).
+ * Errors: FASTLSQ_ERR_INVALID for bad sizes, null arrays or per-point terms.
+ */
+FASTLSQ_API int fastlsq_eval_op(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int32_t d,
+                                const fastlsq_op *op, const double *W, const double *b, int64_t n_feat,
+                                double scale, const double *beta, double *u);
+
+/*
  * Evaluate the approximation at points (eq. approximation, Alg. 1 return line):
  * u[e] = scale * sum_j beta[j] sin(W_j.x_e + b_j) for e < n_eval, in FP64.
  * x: [n_eval][d].  Used for test-set errors and sensor readouts.

@@ -11,6 +11,8 @@
 
 int fl_launch_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, const double *W,
                    const double *b, int64_t n_feat, double scale, const double *beta, double *u);
+int fl_launch_eval_op(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, const double *W,
+                      const double *b, int64_t n_feat, const double *pref, const double *beta, double *u);
 int fl_launch_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, const double *W,
                            const double *b, int64_t n_feat, double scale, const double *beta, double *u);
 int fl_launch_eval_adjoint(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d,
@@ -360,6 +362,24 @@ extern "C" int fastlsq_assemble(fastlsq_ctx *ctx, fastlsq_dtype dtype, const dou
                                       row_offset, row_weight);
     return fl_launch_assemble_f64(ctx, p, x, n_rows, W, b, n_feat, pref, (double *)A, ldA,
                                   row_offset, row_weight);
+}
+
+extern "C" int fastlsq_eval_op(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int32_t d,
+                               const fastlsq_op *op, const double *W, const double *b, int64_t n_feat,
+                               double scale, const double *beta, double *u)
+{
+    if (!ctx) return FASTLSQ_ERR_INVALID;
+    fl_op_params p;
+    FL_TRY(fl_pack_op(ctx, op, &p));
+    if (p.n_pp != 0) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval_op: per-point coefficients are not allowed");
+    if (n_eval < 0 || n_feat < 1 || n_feat > FL_MAX_FEAT || d != p.d)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval_op: bad sizes");
+    if (n_eval == 0) return 0;
+    if (!x || !W || !b || !beta || !u) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval_op: null array");
+    double *pref = (double *)fl_ws(ctx, FL_WS_PREFACTOR, sizeof(double) * (2 + FL_MAX_PP) * n_feat);
+    if (!pref) return FASTLSQ_ERR_NOMEM;
+    FL_TRY(fl_prefactors(ctx, p, W, n_feat, scale, 1.0, pref));
+    return fl_launch_eval_op(ctx, x, n_eval, d, W, b, n_feat, pref, beta, u);
 }
 
 extern "C" int fastlsq_rhs(fastlsq_ctx *ctx, fastlsq_problem problem, fastlsq_rhs_kind kind,

@@ -266,6 +266,40 @@ __global__ void k_eval_reduce(const double *__restrict__ part, int nsplit, int64
     u[e] = scale * acc;
 }
 
+// L[u](x_e) = sum_j beta_j (P_j sin z_ej + Q_j cos z_ej), z_ej = W_j.x_e + b_j, with the
+// operator's column prefactors P, Q (eq. cyclic; scale included): split over feature
+// chunks like k_eval_partial, the partial sums reduced by k_eval_reduce
+__global__ void __launch_bounds__(128)
+k_eval_op_partial(const double *__restrict__ x, int64_t n_eval, int d, const double *__restrict__ W,
+                  const double *__restrict__ b, int64_t n_feat, const double *__restrict__ pref,
+                  const double *__restrict__ beta, double *__restrict__ part)
+{
+    __shared__ double sW[EVAL_SPLIT_COLS][FL_MAX_D];
+    __shared__ double sB[EVAL_SPLIT_COLS], sP[EVAL_SPLIT_COLS], sQ[EVAL_SPLIT_COLS];
+    const int64_t j0 = (int64_t)blockIdx.y * EVAL_SPLIT_COLS;
+    const int ncols = (int)fl_min64(EVAL_SPLIT_COLS, n_feat - j0);
+    for (int t = threadIdx.x; t < ncols; t += blockDim.x) {
+        for (int k = 0; k < d; ++k) sW[t][k] = W[(j0 + t) * d + k];
+        sB[t] = b[j0 + t];
+        sP[t] = beta[j0 + t] * pref[j0 + t];
+        sQ[t] = beta[j0 + t] * pref[n_feat + j0 + t];
+    }
+    __syncthreads();
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_eval) return;
+    double xe[FL_MAX_D];
+    for (int k = 0; k < FL_MAX_D; ++k) xe[k] = (k < d) ? x[e * d + k] : 0.0;
+    double acc = 0.0;
+    for (int c = 0; c < ncols; ++c) {
+        double z = sB[c];
+        for (int k = 0; k < d; ++k) z = fma(sW[c][k], xe[k], z);
+        double sn, cs;
+        sincos(z, &sn, &cs);
+        acc = fma(sP[c], sn, fma(sQ[c], cs, acc));
+    }
+    part[(int64_t)blockIdx.y * n_eval + e] = acc;
+}
+
 // grad_beta_j = scale * sum_e g_e sin(W_j.x_e + b_j): one feature per thread,
 // points staged in shared memory in chunks (FP64).
 constexpr int EA_PTS = 256;
@@ -496,6 +530,22 @@ int fl_launch_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, con
     FL_CHECK_LAUNCH(ctx, "eval_partial");
     k_eval_reduce<<<(unsigned)fl_cdiv(n_eval, 256), 256, 0, ctx->stream>>>(part, nsplit, n_eval,
                                                                            scale, u);
+    FL_CHECK_LAUNCH(ctx, "eval_reduce");
+    return 0;
+}
+
+int fl_launch_eval_op(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, const double *W,
+                      const double *b, int64_t n_feat, const double *pref, const double *beta, double *u)
+{
+    if (n_eval == 0) return 0;
+    int nsplit = (int)fl_cdiv(n_feat, EVAL_SPLIT_COLS);
+    double *part = (double *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(double) * nsplit * n_eval);
+    if (!part) return FASTLSQ_ERR_NOMEM;
+    dim3 grid((unsigned)fl_cdiv(n_eval, 128), (unsigned)nsplit);
+    FL_PROF_N(ctx, FASTLSQ_K_EVAL, 2);
+    k_eval_op_partial<<<grid, 128, 0, ctx->stream>>>(x, n_eval, d, W, b, n_feat, pref, beta, part);
+    FL_CHECK_LAUNCH(ctx, "eval_op_partial");
+    k_eval_reduce<<<(unsigned)fl_cdiv(n_eval, 256), 256, 0, ctx->stream>>>(part, nsplit, n_eval, 1.0, u);
     FL_CHECK_LAUNCH(ctx, "eval_reduce");
     return 0;
 }

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "fastlsq_rhs": [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_dbl), _i32, _vp, _i64, _i32,
                     _dbl, _vp],
     "fastlsq_eval": [_vp, _vp, _i64, _i32, _vp, _vp, _i64, _dbl, _vp, _vp],
+    "fastlsq_eval_op": [_vp, _vp, _i64, _i32, ctypes.POINTER(fastlsq_op), _vp, _vp, _i64, _dbl, _vp, _vp],
     "fastlsq_eval_noalloc": [_vp, _vp, _i64, _i32, _vp, _vp, _i64, _dbl, _vp, _vp],
     "fastlsq_eval_adjoint": [_vp, _vp, _i64, _i32, _vp, _vp, _i64, _dbl, _vp, _vp],
     "fastlsq_lstsq": [_vp, ctypes.c_int, _vp, ctypes.c_int, _i64, _i64, _i64, _dbl, _vp, _i32, _i64,
@@ -257,6 +258,13 @@ def fastlsq_rhs(ctx, problem, kind, params, x, weight, out):
 def fastlsq_eval(ctx, x, W, b, scale, beta, u):
     return ctx.check(ctx.lib.fastlsq_eval(ctx.handle, _ptr(x), x.shape[0], x.shape[1], _ptr(W),
                                           _ptr(b), W.shape[0], float(scale), _ptr(beta), _ptr(u)))
+
+
+def fastlsq_eval_op(ctx, x, op, W, b, scale, beta, u):
+    """(L u)(x_e) for the operator `op` (an Op without per-point terms)."""
+    return ctx.check(ctx.lib.fastlsq_eval_op(ctx.handle, _ptr(x), x.shape[0], x.shape[1],
+                                             ctypes.byref(op.struct), _ptr(W), _ptr(b), W.shape[0],
+                                             float(scale), _ptr(beta), _ptr(u)))
 
 
 def fastlsq_eval_noalloc(ctx, x, W, b, scale, beta, u):

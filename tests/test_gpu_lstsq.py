@@ -253,6 +253,25 @@ def test_concurrent_solves_are_bit_identical():
             assert torch.equal(sv.beta, r)
 
 
+def test_cached_resolves_of_a_pde_system(ctx):
+    """Re-solves against a kept factor (App. F.4) for several right-hand sides at once:
+    u is linear in the right-hand side (checked on the test set; beta itself is not
+    determined elementwise for these condition numbers)."""
+    w = wl.helmholtz2d(n_int=3000, n_bc=512, n_feat=640)
+    s = pl.LinearSolver(ctx, pl.upload(w), prec=fl.PREC_MIXED, max_refine=2)
+    s.build_rhs()
+    s.assemble()
+    fac = s.solve(keep=True)
+    scales = [0.5, 1.0, 2.0]
+    rhs = s.rhs.repeat(3, 1) * torch.tensor(scales, dtype=torch.float64, device=DEV).unsqueeze(1)
+    betas = torch.zeros((3, w.n_feat), dtype=torch.float64, device=DEV)
+    fl.fastlsq_factor_solve(ctx, fac, rhs, betas, max_refine=2)
+    fl.fastlsq_factor_destroy(ctx, fac)
+    u0 = s.u_test()
+    for c, bt in zip(scales, betas):
+        assert pl.rel_l2(s.u_test(beta=bt), c * u0) <= 1e-7
+
+
 def test_overlapped_fp64_assembly_is_bit_identical(ctx):
     """The FP64 operator assembled on a side stream (the refinement waits on its
     event) gives the same bits as the serial schedule: the same kernels on the same
