@@ -263,6 +263,38 @@ def _secondary(fl, pl, wl, torch, ctx, dev, n_inverse):
                 "workload": (f"{name}: 8192 interior + 1024 boundary rows, 2048 features sigma={wc.sigma:g}, "
                              "u^3 term, manufactured u* = sin(pi x) sin(pi y) + x y / 2, mu=1e-10, <=12 iterations")}
 
+    # the 1-D problems of Sec. 3.3 in true solver mode (f = 0, Dirichlet data of the exact
+    # kink): Allen-Cahn eps = 0.1 (30 iterations) and steady Burgers nu = 0.1 with
+    # continuation nu = 1, 0.5, 0.2, 0.1 (12 iterations per stage, 48 in all), both
+    # warm-started from the linear part, 5000 interior points, 1500 features
+    for name, stages, iters in (("allen_cahn1d", None, 30),
+                                ("burgers1d", wl.burgers_stage_coef(0.1), 12)):
+        w1 = getattr(wl, name)()
+        dp1 = pl.upload(w1, dev)
+        f1 = torch.zeros(w1.n_int, dtype=torch.float64, device=dev)
+        g1 = torch.empty(w1.n_bc, dtype=torch.float64, device=dev)
+        ue1 = torch.empty(dp1.x_test.shape[0], dtype=torch.float64, device=dev)
+        fl.fastlsq_rhs(ctx, w1.problem, fl.RHS_EXACT, w1.params, dp1.x_bc, 1.0, g1)
+        fl.fastlsq_rhs(ctx, w1.problem, fl.RHS_EXACT, w1.params, dp1.x_test, 1.0, ue1)
+        for pname, prec in (("mixed", fl.PREC_MIXED), ("fp64", fl.PREC_FP64)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            beta, rc, sts = pl.newton_solve(ctx, dp1, f1, g1, prec=prec, max_iter=iters, tol=1e-10,
+                                            stage_coef=stages)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            u = torch.empty(dp1.x_test.shape[0], dtype=torch.float64, device=dev)
+            fl.fastlsq_eval(ctx, dp1.x_test, dp1.W, dp1.b, w1.scale, beta, u)
+            n_it = sum(int(st.iters) for st in sts) + 1          # + the warm-start solve
+            out[f"newton_{name}_{pname}"] = {
+                "seconds": sec, "iters": n_it, "status": int(rc), "seconds_per_iter": sec / n_it,
+                "rel_l2_vs_exact": pl.rel_l2(u, ue1),
+                "workload": (f"{name}: {w1.n_int} interior + 2 boundary rows, {w1.n_feat} features "
+                             f"sigma={w1.sigma:g}, f = 0, exact kink as Dirichlet data, mu=1e-10, warm start, "
+                             + (f"<= {iters} iterations" if stages is None else
+                                f"continuation nu = {', '.join(f'{-c[0]:g}' for c in stages)}, "
+                                f"<= {iters} iterations per stage"))}
+
     # cached re-solves (App. F.4): factor the helmholtz2d operator once, then solve for
     # new right-hand sides (Q^T b, R^{-1}, two refinement steps) against the kept factor
     wr = wl.helmholtz2d()

@@ -149,6 +149,10 @@ typedef enum {
                                        /* u* = sin(pi x) sin(pi y) + x y / 2, Dirichlet data u*)      */
     FASTLSQ_PROBLEM_NLHELMHOLTZ_2D = 7, /* Lap u + k^2 u + lam u^3 = f, params = (k, lam) (Sec. 3.3  */
                                        /* NL-Helmholtz; the same u*)                                  */
+    FASTLSQ_PROBLEM_ALLEN_CAHN_1D = 8, /* eps u'' + u - u^3 = 0 on [0,1], params[0] = eps (Sec. 3.3   */
+                                       /* Allen-Cahn; f = 0), u* = tanh((x - 1/2) / sqrt(2 eps))     */
+    FASTLSQ_PROBLEM_BURGERS_1D = 9,    /* u u' - nu u'' = 0 on [0,1], params[0] = nu (Sec. 3.3 steady */
+                                       /* Burgers; f = 0), u* = -tanh((x - 1/2) / (2 nu))            */
     FASTLSQ_PROBLEM_GAUSS_SOURCE_2D = 5 /* -Lap u = sum_k a_k exp(-|x-c_k|^2/(2 w_k^2)), params =   */
                                        /* theta [n_src][4] = (c_x, c_y, w, a)                      */
 } fastlsq_problem;
@@ -364,8 +368,10 @@ FASTLSQ_API int fastlsq_inverse_batch(fastlsq_ctx *ctx, const fastlsq_inverse_in
                                       int32_t n_inst, const fastlsq_op *op, int32_t n_src,
                                       const fastlsq_inverse_opts *opts);
 
-/* Nonlinearities N(u) of the Newton problems (Sec. 3.3). */
-typedef enum { FASTLSQ_NL_NONE = 0, FASTLSQ_NL_EXP = 1, FASTLSQ_NL_CUBIC = 2 } fastlsq_nl;
+/* Nonlinearities N(u) of the Newton problems (Sec. 3.3): nl_lam e^u, nl_lam u^3, or the
+ * Burgers advection term nl_lam u du/dx_0 (derivative along the first coordinate). */
+typedef enum { FASTLSQ_NL_NONE = 0, FASTLSQ_NL_EXP = 1, FASTLSQ_NL_CUBIC = 2,
+               FASTLSQ_NL_BURGERS = 3 } fastlsq_nl;
 
 typedef struct {
     int32_t d;
@@ -373,7 +379,8 @@ typedef struct {
     const double *x_int;      /* [n_int][d] */
     const double *x_bc;       /* [n_bc][d]  */
     fastlsq_op op;            /* interior linear operator L (no per-point terms) */
-    int32_t nl_kind;          /* fastlsq_nl: N(u) = nl_lam e^u or nl_lam u^3     */
+    int32_t nl_kind;          /* fastlsq_nl: N(u) = nl_lam e^u, nl_lam u^3 or     */
+                              /* nl_lam u u_{x_0}                                */
     double nl_lam;
     double bc_weight;         /* boundary rows bc_weight * (u - g) (Dirichlet)   */
     const double *f;          /* [n_int] */
@@ -403,7 +410,8 @@ typedef struct {
  * Newton-Raphson for L[u] + N[u] = f with Dirichlet rows (Sec. 2.4, eq. newton):
  * R_i = L[u](x_i) + N(u_i) - f_i (interior), bc_weight (u_i - g_i) (boundary);
  * J_ij = L[phi_j](x_i) + N'(u_i) phi_j(x_i) reassembled on the GPU every
- * iteration; delta = argmin ||J delta + R||^2 + mu ||delta||^2; Armijo
+ * iteration (Burgers: + nl_lam u_{x_0}(x_i) phi_j(x_i) + nl_lam u(x_i) d(phi_j)/dx_0(x_i),
+ * the second a per-point coefficient on a first-derivative feature); delta = argmin ||J delta + R||^2 + mu ||delta||^2; Armijo
  * backtracking on ||R||; solution-level stopping test.  beta_inout: [n_feat]
  * (start value in, solution out; a warm start from the linear part is the
  * caller's choice).  The residuals and the refinement operator are FP64.  The
@@ -414,6 +422,23 @@ typedef struct {
 FASTLSQ_API int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *prob,
                    const double *W, const double *b, int64_t n_feat, double scale,
                    const fastlsq_newton_opts *opts, double *beta_inout,
+                   fastlsq_newton_stats *stats);
+
+/*
+ * Newton with continuation (homotopy, Sec. 2.4, used for steady Burgers): n_stages
+ * fastlsq_newton solves in turn, stage k with the interior operator's term
+ * coefficients replaced by stage_coef[k * prob->op.n_terms + t] (e.g. the viscosity
+ * term -nu D^2 with nu = 1.0, 0.5, 0.2, 0.1), each stage starting from the previous
+ * stage's beta (beta_inout: start value in, last stage's solution out).  The other
+ * fields of prob (nonlinearity, data, weights) stay fixed.  stats: host
+ * [n_stages] (may be NULL).  Returns the last stage's status (0 converged,
+ * 1 max_iter, 2 line search failed); an error of any stage is returned at once.
+ * A stage whose status is 2 ends the continuation.
+ */
+FASTLSQ_API int fastlsq_newton_continuation(fastlsq_ctx *ctx, const fastlsq_newton_problem *prob,
+                   const double *W, const double *b, int64_t n_feat, double scale,
+                   const fastlsq_newton_opts *opts, int32_t n_stages,
+                   const double *stage_coef, double *beta_inout,
                    fastlsq_newton_stats *stats);
 
 /* Context options for fastlsq_set_option. */

@@ -34,8 +34,10 @@ BRATU_2D = 4
 GAUSS_SOURCE_2D = 5
 NLPOISSON_2D = 6
 NLHELMHOLTZ_2D = 7
+ALLEN_CAHN_1D = 8
+BURGERS_1D = 9
 
-NL_NONE, NL_EXP, NL_CUBIC = 0, 1, 2
+NL_NONE, NL_EXP, NL_CUBIC, NL_BURGERS = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:

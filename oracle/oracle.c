@@ -255,7 +255,12 @@ enum {
     /* the cubic Newton problems of Sec. 3.3 ("u^3 term"; the equations are this reading):    */
     /* u* = sin(pi x) sin(pi y) + x y / 2 on [0,1]^2, Dirichlet data u* on the boundary        */
     ORC_NLPOISSON_2D = 6,  /* -Lap u + lam u^3 = f; params[0] = lam                              */
-    ORC_NLHELMHOLTZ_2D = 7 /* Lap u + k^2 u + lam u^3 = f; params = (k, lam)                     */
+    ORC_NLHELMHOLTZ_2D = 7, /* Lap u + k^2 u + lam u^3 = f; params = (k, lam)                    */
+    /* the 1-D Newton problems of Sec. 3.3 in true solver mode (f = 0), each with a kink   */
+    /* that solves the equation exactly on the real line, Dirichlet data u* at x = 0, 1:  */
+    ORC_ALLEN_CAHN_1D = 8, /* eps u'' + u - u^3 = 0; params[0] = eps;                          */
+                           /* u* = tanh((x - 1/2) / sqrt(2 eps))                                */
+    ORC_BURGERS_1D = 9     /* u u' - nu u'' = 0; params[0] = nu; u* = -tanh((x - 1/2) / (2 nu))  */
 };
 
 /* s(x; theta) = sum_k a_k exp(-|x - c_k|^2 / (2 w_k^2)), theta_k = (c_kx, c_ky, w_k, a_k). */
@@ -275,7 +280,6 @@ void orc_problem_exact(int prob, const double *x, long n, int d,
                        const double *params, double *u)
 {
     const double pi = M_PI;
-    (void)params;
     for (long i = 0; i < n; ++i) {
         const double *p = x + i * d;
         double v = 0.0;
@@ -289,6 +293,12 @@ void orc_problem_exact(int prob, const double *x, long n, int d,
             v = sum + prod;
         } else if (prob == ORC_NLPOISSON_2D || prob == ORC_NLHELMHOLTZ_2D) {
             v = sin(pi * p[0]) * sin(pi * p[1]) + 0.5 * p[0] * p[1];
+        } else if (prob == ORC_ALLEN_CAHN_1D) {
+            /* u = tanh(k s): u'' = -2 k^2 u (1 - u^2), so eps u'' + u - u^3 = 0 at k^2 = 1/(2 eps) */
+            v = tanh((p[0] - 0.5) / sqrt(2.0 * params[0]));
+        } else if (prob == ORC_BURGERS_1D) {
+            /* u = -tanh(k s): u u' = k tanh sech^2 and nu u'' = 2 nu k^2 tanh sech^2, equal at k = 1/(2 nu) */
+            v = -tanh((p[0] - 0.5) / (2.0 * params[0]));
         }
         u[i] = v;
     }
@@ -356,20 +366,26 @@ void orc_gauss_source_grad(const double *x, long n, const double *theta, int n_s
 /* Newton-Raphson for L[u] + N[u] = f (Sec. 2.4, eq. newton).                 */
 /* ------------------------------------------------------------------------- */
 
-enum { ORC_NL_NONE = 0, ORC_NL_EXP = 1, ORC_NL_CUBIC = 2 };
+/* N(u) = lam e^u, lam u^3, or (Burgers) lam u du/dx_0, the advection term along the first
+ * coordinate. */
+enum { ORC_NL_NONE = 0, ORC_NL_EXP = 1, ORC_NL_CUBIC = 2, ORC_NL_BURGERS = 3 };
 
-static double orc_nl(int kind, double lam, double u)
+static double orc_nl(int kind, double lam, double u, double ux)
 {
     if (kind == ORC_NL_EXP) return lam * exp(u);
     if (kind == ORC_NL_CUBIC) return lam * u * u * u;
+    if (kind == ORC_NL_BURGERS) return lam * u * ux;
     return 0.0;
 }
 
-static double orc_nl_prime(int kind, double lam, double u)
+/* Derivative of N in the direction phi: c0 phi + c1 d(phi)/dx_0. */
+static void orc_nl_prime(int kind, double lam, double u, double ux, double *c0, double *c1)
 {
-    if (kind == ORC_NL_EXP) return lam * exp(u);
-    if (kind == ORC_NL_CUBIC) return 3.0 * lam * u * u;
-    return 0.0;
+    *c0 = 0.0;
+    *c1 = 0.0;
+    if (kind == ORC_NL_EXP) *c0 = lam * exp(u);
+    if (kind == ORC_NL_CUBIC) *c0 = 3.0 * lam * u * u;
+    if (kind == ORC_NL_BURGERS) { *c0 = lam * ux; *c1 = lam * u; }
 }
 
 static void orc_matvec(const double *M, long m, long n, const double *v, double *out)
@@ -382,16 +398,18 @@ static void orc_matvec(const double *M, long m, long n, const double *v, double 
 /* Residual R(beta): interior rows L[u] + N(u) - f, then boundary rows
  * bc_weight * (u - g).  Also returns u at every collocation row. */
 static double orc_newton_residual(const double *HL, const double *Hi, const double *Hb,
-                                  long n_int, long n_bc, long n, int nl_kind, double nl_lam,
-                                  double bc_weight, const double *f, const double *g,
-                                  const double *beta, double *R, double *u_rows, double *tmp)
+                                  const double *Hd, long n_int, long n_bc, long n, int nl_kind,
+                                  double nl_lam, double bc_weight, const double *f,
+                                  const double *g, const double *beta, double *R, double *u_rows,
+                                  double *ux, double *tmp)
 {
     double rr = 0.0;
     orc_matvec(HL, n_int, n, beta, tmp);          /* L[u] at interior points */
     orc_matvec(Hi, n_int, n, beta, u_rows);       /* u at interior points    */
     orc_matvec(Hb, n_bc, n, beta, u_rows + n_int); /* u at boundary points    */
+    if (Hd) orc_matvec(Hd, n_int, n, beta, ux);   /* du/dx_0 at interior points */
     for (long i = 0; i < n_int; ++i) {
-        R[i] = tmp[i] + orc_nl(nl_kind, nl_lam, u_rows[i]) - f[i];
+        R[i] = tmp[i] + orc_nl(nl_kind, nl_lam, u_rows[i], Hd ? ux[i] : 0.0) - f[i];
         rr += R[i] * R[i];
     }
     for (long i = 0; i < n_bc; ++i) {
@@ -403,8 +421,9 @@ static double orc_newton_residual(const double *HL, const double *Hi, const doub
 
 /*
  * Newton-Raphson with the refinements of Sec. 2.4:
- *   J_ij = L[phi_j](x_i) + N'(u_i) phi_j(x_i) on interior rows, bc_weight phi_j on
- *   boundary rows; delta = argmin ||J delta + R||^2 + mu ||delta||^2 (Tikhonov);
+ *   J_ij = L[phi_j](x_i) + N'(u_i) phi_j(x_i) on interior rows (for Burgers, N = lam u u_x,
+ *   the derivative lam u_x(x_i) phi_j(x_i) + lam u(x_i) d(phi_j)/dx_0(x_i)), bc_weight
+ *   phi_j on boundary rows; delta = argmin ||J delta + R||^2 + mu ||delta||^2 (Tikhonov);
  *   backtracking on the residual norm with the Armijo-type test
  *   ||R(beta + a delta)||^2 <= (1 - 2 c a) ||R(beta)||^2, halving a at most
  *   max_halvings times; stop when ||a J_u delta|| / ||u_new|| <= tol, the change of
@@ -417,7 +436,8 @@ static double orc_newton_residual(const double *HL, const double *Hi, const doub
  * Returns 0 converged, 1 max_iter reached, 2 line search failed, -2 no memory.
  *
  * Pins: for Bratu, an independent second-order finite-difference Newton solve
- * (tests); for a linear problem (N = 0) one step equals the linear solve.
+ * (tests); for a linear problem (N = 0) one step equals the linear solve; for the
+ * problems with a closed-form solution, convergence to it (tests).
  */
 int orc_newton(const double *x_int, long n_int, const double *x_bc, long n_bc, int d,
                int n_terms, const int *alpha, const double *coef,
@@ -428,9 +448,13 @@ int orc_newton(const double *x_int, long n_int, const double *x_bc, long n_bc, i
                double *beta, int *iters_out, double *res_hist)
 {
     long n = n_feat, m = n_int + n_bc;
-    int zero_alpha[16] = {0};
+    int zero_alpha[16] = {0}, dx0_alpha[16] = {1};
     double one = 1.0;
+    const int burgers = (nl_kind == ORC_NL_BURGERS);
     double *HL = malloc(sizeof(double) * n_int * n);
+    double *Hd = burgers ? malloc(sizeof(double) * n_int * n) : NULL;
+    double *ux = calloc(n_int + 1, sizeof(double));
+    double *uxn = calloc(n_int + 1, sizeof(double));
     double *Hi = malloc(sizeof(double) * n_int * n);
     double *Hb = malloc(sizeof(double) * n_bc * n);
     double *J = malloc(sizeof(double) * m * n);
@@ -442,22 +466,28 @@ int orc_newton(const double *x_int, long n_int, const double *x_bc, long n_bc, i
     double *delta = malloc(sizeof(double) * n);
     double *bt = malloc(sizeof(double) * n);
     int status = 1, it = 0;
-    if (!HL || !Hi || !Hb || !J || !R || !Rn || !u || !un || !tmp || !delta || !bt || d > 16) {
+    if (!HL || !Hi || !Hb || !J || !R || !Rn || !u || !un || !tmp || !delta || !bt || !ux || !uxn ||
+        (burgers && !Hd) || d > 16) {
         status = -2;
         goto done;
     }
     orc_assemble(x_int, n_int, d, n_terms, alpha, coef, NULL, 1.0, W, b, n, scale, HL, n_int);
     orc_assemble(x_int, n_int, d, 1, zero_alpha, &one, NULL, 1.0, W, b, n, scale, Hi, n_int);
     orc_assemble(x_bc, n_bc, d, 1, zero_alpha, &one, NULL, 1.0, W, b, n, scale, Hb, n_bc);
+    if (burgers) orc_assemble(x_int, n_int, d, 1, dx0_alpha, &one, NULL, 1.0, W, b, n, scale, Hd, n_int);
 
-    double rr = orc_newton_residual(HL, Hi, Hb, n_int, n_bc, n, nl_kind, nl_lam, bc_weight,
-                                    f, g, beta, R, u, tmp);
+    double rr = orc_newton_residual(HL, Hi, Hb, Hd, n_int, n_bc, n, nl_kind, nl_lam, bc_weight,
+                                    f, g, beta, R, u, ux, tmp);
     for (it = 0; it < max_iter; ++it) {
         if (res_hist) res_hist[it] = sqrt(rr);
         /* Jacobian, eq. newton */
         for (long j = 0; j < n; ++j) {
-            for (long i = 0; i < n_int; ++i)
-                J[i + j * m] = HL[i + j * n_int] + orc_nl_prime(nl_kind, nl_lam, u[i]) * Hi[i + j * n_int];
+            for (long i = 0; i < n_int; ++i) {
+                double c0, c1;
+                orc_nl_prime(nl_kind, nl_lam, u[i], ux[i], &c0, &c1);
+                J[i + j * m] = HL[i + j * n_int] + c0 * Hi[i + j * n_int];
+                if (burgers) J[i + j * m] += c1 * Hd[i + j * n_int];
+            }
             for (long i = 0; i < n_bc; ++i)
                 J[n_int + i + j * m] = bc_weight * Hb[i + j * n_bc];
         }
@@ -468,8 +498,8 @@ int orc_newton(const double *x_int, long n_int, const double *x_bc, long n_bc, i
         int accepted = 0;
         for (int h = 0; h <= max_halvings; ++h) {
             for (long j = 0; j < n; ++j) bt[j] = beta[j] + a * delta[j];
-            rr_new = orc_newton_residual(HL, Hi, Hb, n_int, n_bc, n, nl_kind, nl_lam, bc_weight,
-                                         f, g, bt, Rn, un, tmp);
+            rr_new = orc_newton_residual(HL, Hi, Hb, Hd, n_int, n_bc, n, nl_kind, nl_lam,
+                                         bc_weight, f, g, bt, Rn, un, uxn, tmp);
             if (rr_new <= (1.0 - 2.0 * armijo_c * a) * rr) { accepted = 1; break; }
             a *= 0.5;
         }
@@ -484,13 +514,15 @@ int orc_newton(const double *x_int, long n_int, const double *x_bc, long n_bc, i
         memcpy(beta, bt, sizeof(double) * n);
         memcpy(R, Rn, sizeof(double) * m);
         memcpy(u, un, sizeof(double) * m);
+        memcpy(ux, uxn, sizeof(double) * n_int);
         rr = rr_new;
         if (sqrt(du2) <= tol * sqrt(u2)) { status = 0; ++it; break; }
     }
     if (res_hist) res_hist[it] = sqrt(rr);
 done:
     if (iters_out) *iters_out = it;
-    free(HL); free(Hi); free(Hb); free(J); free(R); free(Rn); free(u); free(un);
+    free(HL); free(Hd); free(ux); free(uxn); free(Hi); free(Hb); free(J); free(R); free(Rn);
+    free(u); free(un);
     free(tmp); free(delta); free(bt);
     return status;
 }

@@ -382,6 +382,14 @@ __global__ void k_rhs(int problem, int kind, fl_problem_params prm, const double
         else v = -2 * pi * pi * sp + prm.p[0] * prm.p[0] * us + prm.p[1] * us * us * us;
         break;
     }
+    case FASTLSQ_PROBLEM_ALLEN_CAHN_1D:
+        // tanh(k s) with k^2 = 1/(2 eps) solves eps u'' + u - u^3 = 0 (f = 0)
+        if (kind == FASTLSQ_RHS_EXACT) v = tanh((p[0] - 0.5) / sqrt(2.0 * prm.p[0]));
+        break;
+    case FASTLSQ_PROBLEM_BURGERS_1D:
+        // -tanh(k s) with k = 1/(2 nu) solves u u' - nu u'' = 0 (f = 0)
+        if (kind == FASTLSQ_RHS_EXACT) v = -tanh((p[0] - 0.5) / (2.0 * prm.p[0]));
+        break;
     case FASTLSQ_PROBLEM_GAUSS_SOURCE_2D:
         if (kind == FASTLSQ_RHS_SOURCE) {
             for (int k = 0; k + 3 < prm.n; k += 4) {

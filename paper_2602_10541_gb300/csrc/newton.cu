@@ -6,7 +6,10 @@
 //   Jacobian   J_ij = L[phi_j](x_i) + N'(u_i) phi_j(x_i), boundary rows
 //              bc_weight phi_j: reassembled with the closed form on the GPU
 //              (FP32 operator kernel with the per-point term N'(u_i) for the
-//              MIXED factor; J64 = L64 + diag(N'(u)) H64 for refinement / FP64)
+//              MIXED factor; J64 = L64 + diag(N'(u)) H64 for refinement / FP64).
+//              Burgers (N = lam u u_x0) adds a second per-point term on the
+//              first-derivative feature: lam u_x0 phi_j + lam u d(phi_j)/dx_0, with
+//              H1 = d(phi_j)/dx_0 at the interior points (FP64, once per call)
 //   step       delta = argmin ||J delta + R||^2 + mu ||delta||^2
 //   line search a = 1, 1/2, ... until ||R(beta + a delta)||^2 <= (1 - 2 c a) ||R||^2
 //   stop       ||u(beta + a delta) - u(beta)|| / ||u(beta + a delta)|| <= tol
@@ -23,28 +26,25 @@ int fl_matvec64(fastlsq_ctx *ctx, const double *A, int64_t ld, int64_t m, int64_
 
 namespace {
 
-__device__ __forceinline__ double nl_val(int kind, double lam, double u)
+__device__ __forceinline__ double nl_val(int kind, double lam, double u, double ux)
 {
     if (kind == FASTLSQ_NL_EXP) return lam * exp(u);
     if (kind == FASTLSQ_NL_CUBIC) return lam * u * u * u;
-    return 0.0;
-}
-__device__ __forceinline__ double nl_der(int kind, double lam, double u)
-{
-    if (kind == FASTLSQ_NL_EXP) return lam * exp(u);
-    if (kind == FASTLSQ_NL_CUBIC) return 3.0 * lam * u * u;
+    if (kind == FASTLSQ_NL_BURGERS) return lam * u * ux;
     return 0.0;
 }
 
-// R_i and u at the collocation rows from Lu = L64 beta (m) and uh = H64 beta (n_int)
+// R_i and u at the collocation rows from Lu = L64 beta (m), uh = H64 beta (n_int) and,
+// for Burgers, uxh = H1 beta (n_int; null otherwise)
 __global__ void k_newton_resid(const double *__restrict__ Lu, const double *__restrict__ uh,
-                               int64_t n_int, int64_t n_bc, int kind, double lam, double bcw,
+                               const double *__restrict__ uxh, int64_t n_int, int64_t n_bc,
+                               int kind, double lam, double bcw,
                                const double *__restrict__ f, const double *__restrict__ g,
                                double *__restrict__ R, double *__restrict__ u_rows)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_int) {
-        R[i] = Lu[i] + nl_val(kind, lam, uh[i]) - f[i];
+        R[i] = Lu[i] + nl_val(kind, lam, uh[i], uxh ? uxh[i] : 0.0) - f[i];
         u_rows[i] = uh[i];
     } else if (i < n_int + n_bc) {
         R[i] = Lu[i] - bcw * g[i - n_int];
@@ -88,23 +88,37 @@ __global__ void k_sum3(const double *__restrict__ part, int nblk, double *__rest
     }
 }
 
-__global__ void k_nl_prime(const double *__restrict__ uh, int64_t n, int kind, double lam,
-                           double *__restrict__ c)
+// derivative of N in the direction phi: c0 phi + c1 d(phi)/dx_0 (c1 only for Burgers)
+__global__ void k_nl_prime(const double *__restrict__ uh, const double *__restrict__ uxh, int64_t n,
+                           int kind, double lam, double *__restrict__ c0, double *__restrict__ c1)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) c[i] = nl_der(kind, lam, uh[i]);
+    if (i >= n) return;
+    const double u = uh[i];
+    double a = 0.0;
+    if (kind == FASTLSQ_NL_EXP) a = lam * exp(u);
+    else if (kind == FASTLSQ_NL_CUBIC) a = 3.0 * lam * u * u;
+    else if (kind == FASTLSQ_NL_BURGERS) {
+        a = lam * uxh[i];
+        c1[i] = lam * u;
+    }
+    c0[i] = a;
 }
 
-// J64 = L64 + diag(c) H64 on the interior rows (boundary rows copied)
+// J64 = L64 + diag(c0) H64 (+ diag(c1) H1) on the interior rows (boundary rows copied)
 __global__ void k_jacobian64(const double *__restrict__ L64, const double *__restrict__ H64,
-                             const double *__restrict__ c, int64_t n_int, int64_t m, int64_t n,
+                             const double *__restrict__ c0, const double *__restrict__ H1,
+                             const double *__restrict__ c1, int64_t n_int, int64_t m, int64_t n,
                              int64_t ld, double *__restrict__ J)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t j = blockIdx.y;
     if (i >= m || j >= n) return;
     double v = L64[i + j * ld];
-    if (i < n_int) v = fma(c[i], H64[i + j * n_int], v);
+    if (i < n_int) {
+        v = fma(c0[i], H64[i + j * n_int], v);
+        if (H1) v = fma(c1[i], H1[i + j * n_int], v);
+    }
     J[i + j * ld] = v;
 }
 
@@ -122,9 +136,9 @@ __global__ void k_neg(const double *__restrict__ x, int64_t n, double *__restric
 }
 
 struct NewtonBufs {
-    double *L64, *H64, *J64;
+    double *L64, *H64, *H1, *J64;   // H1: Burgers only
     float *J32;
-    double *Lu, *uh, *R, *Rn, *u, *un, *c, *delta, *bt, *negR, *part, *sums;
+    double *Lu, *uh, *uxh, *R, *Rn, *u, *un, *c, *c1, *delta, *bt, *negR, *part, *sums;
 };
 
 }  // namespace
@@ -135,9 +149,11 @@ static int newton_residual(fastlsq_ctx *ctx, const fastlsq_newton_problem *p, in
     const int64_t m = p->n_int + p->n_bc;
     FL_TRY(fl_matvec64(ctx, B.L64, m, m, n, beta, B.Lu));
     FL_TRY(fl_matvec64(ctx, B.H64, p->n_int, p->n_int, n, beta, B.uh));
+    if (B.H1) FL_TRY(fl_matvec64(ctx, B.H1, p->n_int, p->n_int, n, beta, B.uxh));
     FL_PROF(ctx, FASTLSQ_K_NEWTON);
     k_newton_resid<<<(unsigned)fl_cdiv(m, 256), 256, 0, ctx->stream>>>(
-        B.Lu, B.uh, p->n_int, p->n_bc, p->nl_kind, p->nl_lam, p->bc_weight, p->f, p->g, R, u_rows);
+        B.Lu, B.uh, B.H1 ? B.uxh : nullptr, p->n_int, p->n_bc, p->nl_kind, p->nl_lam,
+        p->bc_weight, p->f, p->g, R, u_rows);
     FL_CHECK_LAUNCH(ctx, "newton_resid");
     return 0;
 }
@@ -173,6 +189,9 @@ extern "C" int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p,
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "newton: bad options");
     if (o->prec != FASTLSQ_PREC_FP64 && o->prec != FASTLSQ_PREC_MIXED)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "newton: precision");
+    if (p->nl_kind < FASTLSQ_NL_NONE || p->nl_kind > FASTLSQ_NL_BURGERS)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "newton: unknown nonlinearity %d", (int)p->nl_kind);
+    const bool burgers = (p->nl_kind == FASTLSQ_NL_BURGERS);
     fl_op_params opL;
     FL_TRY(fl_pack_op(ctx, &p->op, &opL));
     if (opL.d != p->d) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "newton: op.d != d");
@@ -185,6 +204,9 @@ extern "C" int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p,
     opI.d = d;
     opI.n_terms = 1;
     opI.coef[0] = 1.0;
+    // first derivative along x_0 (Burgers' advection feature)
+    fl_op_params opD = opI;
+    opD.alpha[0][0] = 1;
 
     // buffers
     NewtonBufs B{};
@@ -201,6 +223,9 @@ extern "C" int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p,
     };
     B.L64 = (double *)alloc(sizeof(double) * m * n);
     B.H64 = (double *)alloc(sizeof(double) * n_int * n);
+    B.H1 = burgers ? (double *)alloc(sizeof(double) * n_int * n) : nullptr;
+    B.uxh = burgers ? (double *)alloc(sizeof(double) * n_int) : nullptr;
+    B.c1 = burgers ? (double *)alloc(sizeof(double) * n_int) : nullptr;
     B.J64 = (double *)alloc(sizeof(double) * m * n);
     B.J32 = (o->prec == FASTLSQ_PREC_MIXED) ? (float *)alloc(sizeof(float) * m * n) : nullptr;
     B.Lu = (double *)alloc(sizeof(double) * m);
@@ -237,6 +262,10 @@ extern "C" int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p,
     NT_TRY(fl_launch_assemble_f64(ctx, opI, p->x_bc, n_bc, W, b, n, pref, B.L64, m, n_int, p->bc_weight));
     NT_TRY(fl_prefactors(ctx, opI, W, n, scale, 1.0, pref));
     NT_TRY(fl_launch_assemble_f64(ctx, opI, p->x_int, n_int, W, b, n, pref, B.H64, n_int, 0, 1.0));
+    if (burgers) {
+        NT_TRY(fl_prefactors(ctx, opD, W, n, scale, 1.0, pref));
+        NT_TRY(fl_launch_assemble_f64(ctx, opD, p->x_int, n_int, W, b, n, pref, B.H1, n_int, 0, 1.0));
+    }
     if (cudaMemcpyAsync(beta, beta_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream) !=
         cudaSuccess) {
         rc = fl_cuda(ctx, cudaGetLastError(), "newton copy");
@@ -251,10 +280,10 @@ extern "C" int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p,
         // Jacobian with the per-point coefficient N'(u_i)
         {
         FL_PROF_N(ctx, FASTLSQ_K_NEWTON, 3);
-        k_nl_prime<<<(unsigned)fl_cdiv(n_int, 256), 256, 0, ctx->stream>>>(B.u, n_int, p->nl_kind,
-                                                                          p->nl_lam, B.c);
+        k_nl_prime<<<(unsigned)fl_cdiv(n_int, 256), 256, 0, ctx->stream>>>(
+            B.u, B.uxh, n_int, p->nl_kind, p->nl_lam, B.c, B.c1);
         k_jacobian64<<<dim3((unsigned)fl_cdiv(m, 256), (unsigned)n), 256, 0, ctx->stream>>>(
-            B.L64, B.H64, B.c, n_int, m, n, m, B.J64);
+            B.L64, B.H64, B.c, B.H1, B.c1, n_int, m, n, m, B.J64);
         k_neg<<<(unsigned)fl_cdiv(m, 256), 256, 0, ctx->stream>>>(B.R, m, B.negR);
         }
         if (cudaGetLastError() != cudaSuccess) {
@@ -264,7 +293,13 @@ extern "C" int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p,
         if (o->prec == FASTLSQ_PREC_MIXED) {
             fl_op_params opJ = opL;
             opJ.n_pp = 1;
+            memset(opJ.pp_alpha, 0, sizeof(opJ.pp_alpha));
             opJ.pp_coef[0] = B.c;    // alpha = 0 per-point term N'(u_i) phi_j
+            if (burgers) {           // lam u_i d(phi_j)/dx_0
+                opJ.n_pp = 2;
+                opJ.pp_alpha[1][0] = 1;
+                opJ.pp_coef[1] = B.c1;
+            }
             NT_TRY(fl_prefactors(ctx, opJ, W, n, scale, 1.0, pref));
             NT_TRY(fl_launch_assemble_f32(ctx, opJ, p->x_int, n_int, W, b, n, pref, B.J32, m, 0, 1.0));
             NT_TRY(fl_prefactors(ctx, opI, W, n, scale, p->bc_weight, pref));
@@ -319,13 +354,41 @@ extern "C" int fastlsq_newton(fastlsq_ctx *ctx, const fastlsq_newton_problem *p,
 #undef NT_TRY
 cleanup:
     {
-        void *ptrs[] = {B.L64, B.H64, B.J64, B.J32, B.Lu, B.uh, B.R, B.Rn, B.u, B.un, B.c,
-                        B.delta, B.bt, B.negR, B.part, B.sums, beta, pref};
+        void *ptrs[] = {B.L64, B.H64, B.H1, B.J64, B.J32, B.Lu, B.uh, B.uxh, B.R, B.Rn, B.u, B.un,
+                        B.c, B.c1, B.delta, B.bt, B.negR, B.part, B.sums, beta, pref};
         for (void *q : ptrs)
             if (q) cudaFreeAsync(q, ctx->stream);
     }
     if (rc < 0) return rc;
     int frc = fastlsq_sync(ctx);
     if (frc < 0) return frc;
+    return status;
+}
+
+// Continuation (homotopy) of Sec. 2.4: a sequence of Newton solves whose interior
+// operator coefficients move stage by stage towards the target problem (e.g. the
+// viscosity of steady Burgers 1.0 -> 0.5 -> 0.2 -> 0.1), each warm-started from the
+// previous stage's solution.
+extern "C" int fastlsq_newton_continuation(fastlsq_ctx *ctx, const fastlsq_newton_problem *p,
+                                           const double *W, const double *b, int64_t n_feat,
+                                           double scale, const fastlsq_newton_opts *o,
+                                           int32_t n_stages, const double *stage_coef,
+                                           double *beta_io, fastlsq_newton_stats *stats)
+{
+    if (!ctx || !p) return FASTLSQ_ERR_INVALID;
+    if (n_stages < 1 || n_stages > 64 || !stage_coef)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "newton_continuation: 1..64 stages with coefficients");
+    const int nt = p->op.n_terms;
+    if (nt < 1 || nt > FL_MAX_TERMS)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "newton_continuation: operator terms");
+    std::vector<double> coef((size_t)nt);
+    fastlsq_newton_problem q = *p;
+    q.op.coef = coef.data();
+    int status = 0;
+    for (int k = 0; k < n_stages; ++k) {
+        for (int t = 0; t < nt; ++t) coef[t] = stage_coef[(size_t)k * nt + t];
+        status = fastlsq_newton(ctx, &q, W, b, n_feat, scale, o, beta_io, stats ? &stats[k] : nullptr);
+        if (status < 0 || status == FASTLSQ_WARN_LINESEARCH) break;
+    }
     return status;
 }

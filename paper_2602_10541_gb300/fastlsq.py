@@ -24,7 +24,8 @@ REFINE_CLASSICAL, REFINE_CGLS = 0, 1
 RHS_SOURCE, RHS_EXACT = 0, 1
 POISSON_1D, HELMHOLTZ_2D, POISSON_5D, BRATU_2D, GAUSS_SOURCE_2D = 1, 2, 3, 4, 5
 NLPOISSON_2D, NLHELMHOLTZ_2D = 6, 7
-NL_NONE, NL_EXP, NL_CUBIC = 0, 1, 2
+ALLEN_CAHN_1D, BURGERS_1D = 8, 9
+NL_NONE, NL_EXP, NL_CUBIC, NL_BURGERS = 0, 1, 2, 3
 
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -101,6 +102,9 @@ _SIGNATURES = {
     "fastlsq_newton": [_vp, ctypes.POINTER(fastlsq_newton_problem), _vp, _vp, _i64, _dbl,
                        ctypes.POINTER(fastlsq_newton_opts), _vp,
                        ctypes.POINTER(fastlsq_newton_stats)],
+    "fastlsq_newton_continuation": [_vp, ctypes.POINTER(fastlsq_newton_problem), _vp, _vp, _i64,
+                                    _dbl, ctypes.POINTER(fastlsq_newton_opts), _i32,
+                                    ctypes.POINTER(_dbl), _vp, ctypes.POINTER(fastlsq_newton_stats)],
     "fastlsq_inverse_batch": [_vp, ctypes.POINTER(fastlsq_inverse_instance), _i32,
                               ctypes.POINTER(fastlsq_op), _i32, ctypes.POINTER(fastlsq_inverse_opts)],
     "fastlsq_profile_enable": [_vp, ctypes.c_int],
@@ -361,6 +365,27 @@ def fastlsq_newton(ctx, x_int, x_bc, op, nl_kind, nl_lam, bc_weight, f, g, W, b,
                                 float(scale), ctypes.byref(opts), _ptr(beta), ctypes.byref(st))
     ctx.check(rc)
     return rc, st
+
+
+def fastlsq_newton_continuation(ctx, x_int, x_bc, op, stage_coef, nl_kind, nl_lam, bc_weight, f,
+                                g, W, b, scale, beta, max_iter=12, tol=1e-10, mu=1e-10,
+                                armijo_c=1e-4, max_halvings=20, prec=PREC_MIXED, max_refine=30,
+                                refine_tol=1e-10):
+    """stage_coef: [n_stages][op's n_terms] coefficients per stage.  Returns (status,
+    [stats per stage])."""
+    sc = np.ascontiguousarray(stage_coef, dtype=np.float64).reshape(-1, op.alpha.shape[0])
+    prob = fastlsq_newton_problem(x_int.shape[1], x_int.shape[0], x_bc.shape[0], x_int.data_ptr(),
+                                  x_bc.data_ptr(), op.struct, nl_kind, float(nl_lam),
+                                  float(bc_weight), f.data_ptr(), g.data_ptr())
+    opts = fastlsq_newton_opts(max_iter, float(tol), float(mu), float(armijo_c), max_halvings,
+                               prec, max_refine, float(refine_tol))
+    st = (fastlsq_newton_stats * sc.shape[0])()
+    rc = ctx.lib.fastlsq_newton_continuation(ctx.handle, ctypes.byref(prob), _ptr(W), _ptr(b),
+                                             W.shape[0], float(scale), ctypes.byref(opts),
+                                             sc.shape[0], sc.ctypes.data_as(ctypes.POINTER(_dbl)),
+                                             _ptr(beta), st)
+    ctx.check(rc)
+    return rc, list(st)
 
 
 def fastlsq_profile_enable(ctx, classes=None):

@@ -152,6 +152,32 @@ class ConcurrentSolves:
             origin.wait_event(ev)
 
 
+def newton_solve(ctx, dp: DeviceProblem, f, g, prec=fl.PREC_MIXED, max_iter=30, tol=1e-10,
+                 stage_coef=None, warm=True, max_refine=64, refine_tol=1e-13):
+    """Newton-Raphson with the refinements of Sec. 2.4 on a device problem: warm start
+    from the linear part (one regularised solve with N dropped, i.e. a Newton step with
+    no nonlinearity from beta = 0), then fastlsq_newton, or with stage_coef
+    ([n_stages][n_terms]) fastlsq_newton_continuation with max_iter iterations per
+    stage.  f, g: device sources and Dirichlet data.  Returns (beta, status, stats),
+    stats a list (one per stage)."""
+    w = dp.w
+    beta = torch.zeros(w.n_feat, dtype=torch.float64, device=dp.W.device)
+    first = w.coef if stage_coef is None else np.asarray(stage_coef, dtype=np.float64)[0]
+    common = dict(mu=w.mu, prec=prec, max_refine=max_refine, refine_tol=refine_tol)
+    if warm:
+        fl.fastlsq_newton(ctx, dp.x_int, dp.x_bc, fl.Op(w.alpha, first), fl.NL_NONE, 0.0,
+                          w.lam_bc, f, g, dp.W, dp.b, w.scale, beta, max_iter=1, tol=0.0, **common)
+    if stage_coef is None:
+        rc, st = fl.fastlsq_newton(ctx, dp.x_int, dp.x_bc, dp.op_int, w.nl_kind, w.nl_lam,
+                                   w.lam_bc, f, g, dp.W, dp.b, w.scale, beta, max_iter=max_iter,
+                                   tol=tol, **common)
+        return beta, rc, [st]
+    rc, sts = fl.fastlsq_newton_continuation(ctx, dp.x_int, dp.x_bc, dp.op_int, stage_coef,
+                                             w.nl_kind, w.nl_lam, w.lam_bc, f, g, dp.W, dp.b,
+                                             w.scale, beta, max_iter=max_iter, tol=tol, **common)
+    return beta, rc, sts
+
+
 def rel_l2(a, b) -> float:
     """Relative L2 difference ||a - b|| / ||b||, computed on the host."""
     a = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else np.asarray(a)

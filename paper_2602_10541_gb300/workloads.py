@@ -98,7 +98,7 @@ class Workload:
     params: np.ndarray              # problem parameters (k for Helmholtz, theta for sources)
     seed: int
     mu: float = 0.0
-    nl_kind: int = 0                # 0 none, 1 exp, 2 cubic
+    nl_kind: int = 0                # 0 none, 1 exp, 2 cubic, 3 Burgers (u u_x0)
     nl_lam: float = 0.0
     x_int: np.ndarray = field(default=None, repr=False)
     x_bc: np.ndarray = field(default=None, repr=False)
@@ -213,6 +213,49 @@ def nlhelmholtz2d(n_int=8192, n_bc=1024, n_feat=2048, k=3.0, lam=1.0):
     w.W, w.b = _features(s, n_feat, 2, w.sigma)
     w.x_test = uniform(s + 200, "test", 5000 * 2).reshape(-1, 2)
     return w
+
+
+def allen_cahn1d(n_int=5000, n_feat=1500, eps=0.1):
+    """eps u'' + u - u^3 = 0 on [0,1] (Sec. 3.3 Allen-Cahn, eps = 0.1, sigma = 3) in true
+    solver mode (f = 0), Dirichlet data from the kink u* = tanh((x - 1/2)/sqrt(2 eps))
+    (problem 8); interior points uniform-random, the two ends as boundary rows; Newton
+    warm-started from the linear part, mu = 1e-10, boundary weight 100."""
+    s = SEED0 + 8
+    w = Workload("allen_cahn1d", 8, 1, n_int, 2, n_feat, 3.0, 100.0,
+                 np.array([[2], [0]], np.int32), np.array([eps, 1.0]), np.array([eps]), s,
+                 mu=1e-10, nl_kind=2, nl_lam=-1.0)
+    w.x_int = uniform(s + 100, "x_int", n_int).reshape(n_int, 1)
+    w.x_bc = np.array([[0.0], [1.0]])
+    w.W, w.b = _features(s, n_feat, 1, w.sigma)
+    w.x_test = uniform(s + 200, "test", 5000).reshape(-1, 1)
+    return w
+
+
+BURGERS_STAGES = (1.0, 0.5, 0.2, 0.1)
+
+
+def burgers1d(n_int=5000, n_feat=1500, nu=0.1):
+    """u u' - nu u'' = 0 on [0,1] (Sec. 3.3 steady Burgers, nu = 0.1, sigma = 10) in true
+    solver mode (f = 0), Dirichlet data from the viscous shock u* = -tanh((x - 1/2)/(2 nu))
+    (problem 9); Newton with continuation in nu over BURGERS_STAGES (ending at nu),
+    warm-started from the linear part, mu = 1e-10, boundary weight 100.  coef holds the
+    target -nu of the term D^2."""
+    s = SEED0 + 9
+    w = Workload("burgers1d", 9, 1, n_int, 2, n_feat, 10.0, 100.0,
+                 np.array([[2]], np.int32), np.array([-nu]), np.array([nu]), s,
+                 mu=1e-10, nl_kind=3, nl_lam=1.0)
+    w.x_int = uniform(s + 100, "x_int", n_int).reshape(n_int, 1)
+    w.x_bc = np.array([[0.0], [1.0]])
+    w.W, w.b = _features(s, n_feat, 1, w.sigma)
+    w.x_test = uniform(s + 200, "test", 5000).reshape(-1, 1)
+    return w
+
+
+def burgers_stage_coef(nu=0.1):
+    """Continuation coefficients of the term D^2 per stage: -nu_k for nu_k in
+    BURGERS_STAGES down to nu."""
+    stages = [v for v in BURGERS_STAGES if v > nu] + [nu]
+    return np.array([[-v] for v in stages])
 
 
 def gauss_theta(seed: int, name: str, n_src: int = 4) -> np.ndarray:

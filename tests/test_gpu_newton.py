@@ -130,3 +130,85 @@ def test_newton_nlpoisson_full_size(ctx):
     assert np.linalg.norm(u_d - ue) / np.linalg.norm(ue) <= 1e-6
     assert np.linalg.norm(u_m - ue) / np.linalg.norm(ue) <= 1e-6
     assert np.linalg.norm(u_m - u_d) / np.linalg.norm(u_d) <= 1e-6 + 10 * st_d.step_rel[st_d.iters - 1]
+
+
+# ---------------------------------------------------------------------------
+# 1-D Newton problems of Sec. 3.3: Allen-Cahn (cubic, L = eps D^2 + 1) and steady
+# Burgers (N = u u', whose Jacobian carries a per-point coefficient on the
+# first-derivative feature), with the linear warm start and, for Burgers, the
+# continuation in nu.  The oracle takes the same warm start and stages.
+# ---------------------------------------------------------------------------
+
+def _kink(name, x, c):
+    s = x[:, 0] - 0.5
+    return np.tanh(s / np.sqrt(2 * c)) if name == "allen_cahn1d" else -np.tanh(s / (2 * c))
+
+
+def _oracle_1d(w, stages, iters):
+    f = np.zeros(w.n_int)
+    g = oracle.problem_exact(w.problem, w.x_bc, w.params)
+    beta, *_ = oracle.newton(w.x_int, w.x_bc, w.alpha, stages[0], oracle.NL_NONE, 0.0, w.lam_bc,
+                             f, g, w.W, w.b, w.scale, mu=w.mu, max_iter=1, tol=0.0)
+    hists = []
+    for coef in stages:
+        beta, st, it, hist = oracle.newton(w.x_int, w.x_bc, w.alpha, coef, w.nl_kind, w.nl_lam,
+                                           w.lam_bc, f, g, w.W, w.b, w.scale, mu=w.mu,
+                                           max_iter=iters, tol=0.0, beta0=beta)
+        hists.append(hist)
+    return beta, hists
+
+
+def _gpu_1d(ctx, w, prec, iters, stages=None):
+    from paper_2602_10541_gb300 import pipeline as pl
+    dp = pl.upload(w, DEV)
+    f = torch.zeros(w.n_int, dtype=torch.float64, device=DEV)
+    g = torch.empty(w.n_bc, dtype=torch.float64, device=DEV)
+    fl.fastlsq_rhs(ctx, w.problem, fl.RHS_EXACT, w.params, dp.x_bc, 1.0, g)
+    np.testing.assert_allclose(g.cpu().numpy(), _kink(w.name, w.x_bc, w.params[0]), rtol=0, atol=1e-15)
+    return pl.newton_solve(ctx, dp, f, g, prec=prec, max_iter=iters, tol=0.0, stage_coef=stages)
+
+
+@pytest.mark.parametrize("name", ["allen_cahn1d", "burgers1d"])
+@pytest.mark.parametrize("prec,bar", [(fl.PREC_FP64, 1e-9), (fl.PREC_MIXED, 1e-5)])
+def test_newton_1d_steps_match_oracle(ctx, name, prec, bar):
+    """Warm start plus three Newton steps at the target eps / nu against the oracle's."""
+    w = getattr(wl, name)(n_int=600, n_feat=300)
+    beta_o, (hist_o,) = _oracle_1d(w, [w.coef], 3)
+    beta, rc, (st,) = _gpu_1d(ctx, w, prec, 3)
+    assert st.iters == 3
+    u_o = oracle.eval_u(w.x_test, w.W, w.b, w.scale, beta_o)
+    u = _u(ctx, w, beta)
+    assert np.linalg.norm(u - u_o) / np.linalg.norm(u_o) <= bar
+    np.testing.assert_allclose(st.res_norm[:3], hist_o[:3], rtol=1e-6 if prec == fl.PREC_FP64 else 1e-3)
+
+
+@pytest.mark.parametrize("prec,bar", [(fl.PREC_FP64, 1e-8), (fl.PREC_MIXED, 1e-5)])
+def test_newton_burgers_continuation_matches_oracle(ctx, prec, bar):
+    """fastlsq_newton_continuation over nu = 1, 0.5, 0.2, 0.1 (three steps per stage)
+    against the oracle's stage-by-stage solves."""
+    w = wl.burgers1d(n_int=600, n_feat=300)
+    stages = wl.burgers_stage_coef(0.1)
+    beta_o, hists_o = _oracle_1d(w, list(stages), 3)
+    beta, rc, sts = _gpu_1d(ctx, w, prec, 3, stages=stages)
+    assert len(sts) == 4 and all(s.iters == 3 for s in sts)
+    u_o = oracle.eval_u(w.x_test, w.W, w.b, w.scale, beta_o)
+    u = _u(ctx, w, beta)
+    assert np.linalg.norm(u - u_o) / np.linalg.norm(u_o) <= bar
+    for s, h in zip(sts, hists_o):
+        np.testing.assert_allclose(s.res_norm[0], h[0], rtol=1e-6 if prec == fl.PREC_FP64 else 1e-3)
+
+
+@pytest.mark.parametrize("name", ["allen_cahn1d", "burgers1d"])
+def test_newton_1d_full_size(ctx, name):
+    """The 1-D problems at the paper's sizes (5000 interior points, 1500 features):
+    MIXED and FP64 reach the exact kink to 1e-5 and agree with each other."""
+    w = getattr(wl, name)()
+    stages = wl.burgers_stage_coef(0.1) if name == "burgers1d" else None
+    iters = 12 if stages is not None else 30
+    beta_m, rc_m, st_m = _gpu_1d(ctx, w, fl.PREC_MIXED, iters, stages)
+    beta_d, rc_d, st_d = _gpu_1d(ctx, w, fl.PREC_FP64, iters, stages)
+    u_m, u_d = _u(ctx, w, beta_m), _u(ctx, w, beta_d)
+    ue = _kink(name, w.x_test, w.params[0])
+    assert np.linalg.norm(u_d - ue) / np.linalg.norm(ue) <= 1e-5
+    assert np.linalg.norm(u_m - ue) / np.linalg.norm(ue) <= 1e-5
+    assert np.linalg.norm(u_m - u_d) / np.linalg.norm(u_d) <= 1e-6

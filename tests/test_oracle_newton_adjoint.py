@@ -198,3 +198,89 @@ def test_newton_cubic_recovers_the_manufactured_solution(name):
     ue = _u_star(w.x_test)
     err = np.linalg.norm(u - ue) / np.linalg.norm(ue)
     assert err < 1e-6, (status, iters, err)
+
+
+# ---------------------------------------------------------------------------
+# The 1-D Newton problems of Sec. 3.3 (Allen-Cahn eps = 0.1, steady Burgers nu = 0.1)
+# in true solver mode: f = 0 and the Dirichlet data of a kink that solves each
+# equation exactly, written out here: tanh(s/sqrt(2 eps)) and -tanh(s/(2 nu)).
+# ---------------------------------------------------------------------------
+
+def _kink(name, x, c):
+    s = x[:, 0] - 0.5
+    return np.tanh(s / math.sqrt(2 * c)) if name == "allen_cahn1d" else -np.tanh(s / (2 * c))
+
+
+@pytest.mark.parametrize("name,c", [("allen_cahn1d", 0.1), ("allen_cahn1d", 0.03),
+                                    ("burgers1d", 0.1), ("burgers1d", 0.5)])
+def test_1d_kinks_solve_their_equations(name, c):
+    """The oracle's u* of problems 8 and 9 equals the kink and zeroes the equation:
+    eps u'' + u - u^3 (Allen-Cahn) and u u' - nu u'' (Burgers) by central differences
+    of the oracle's own u* (h = 1e-4), and the source is 0."""
+    w = getattr(wl, name)(n_int=300, n_feat=4)
+    x = w.x_int
+    prob = w.problem
+    u = lambda y: oracle.problem_exact(prob, y, [c])
+    np.testing.assert_allclose(u(x), _kink(name, x, c), rtol=0, atol=1e-15)
+    h = 1e-4
+    e = np.array([[h]])
+    up, u0, um = u(x + e), u(x), u(x - e)
+    d1 = (up - um) / (2 * h)
+    d2 = (up - 2 * u0 + um) / h ** 2
+    res = (c * d2 + u0 - u0 ** 3) if name == "allen_cahn1d" else (u0 * d1 - c * d2)
+    scale = np.abs(c * d2).max()
+    assert np.abs(res).max() < 1e-5 * scale
+    np.testing.assert_array_equal(oracle.problem_source(prob, x, [c]), np.zeros(len(x)))
+
+
+def _solve_1d(w, stages, iters, warm=True):
+    f = np.zeros(w.n_int)
+    g = oracle.problem_exact(w.problem, w.x_bc, w.params)
+    beta = None
+    if warm:   # warm start: the linear part alone (one Newton step with N = 0 is that solve)
+        beta, *_ = oracle.newton(w.x_int, w.x_bc, w.alpha, stages[0], oracle.NL_NONE, 0.0,
+                                 w.lam_bc, f, g, w.W, w.b, w.scale, mu=w.mu, max_iter=1, tol=0.0)
+    hists = []
+    for coef in stages:
+        beta, status, iters_done, hist = oracle.newton(w.x_int, w.x_bc, w.alpha, coef, w.nl_kind,
+                                                       w.nl_lam, w.lam_bc, f, g, w.W, w.b, w.scale,
+                                                       mu=w.mu, max_iter=iters, tol=1e-12, beta0=beta)
+        hists.append(hist)
+    return beta, hists
+
+
+def test_newton_allen_cahn_recovers_the_kink():
+    """Newton (warm start, mu = 1e-10, backtracking) on eps u'' + u - u^3 = 0 converges to
+    the kink; with the cubic's Jacobian term 3 lam u^2 the residual drops by orders of
+    magnitude per step once close (a wrong Jacobian stalls to linear convergence)."""
+    w = wl.allen_cahn1d(n_int=600, n_feat=300)
+    beta, (hist,) = _solve_1d(w, [w.coef], 25)
+    assert np.all(np.diff(hist) <= 0)
+    assert hist[2] < 1e-3 * hist[0], hist       # two quadratic steps reach the floor
+    u = oracle.eval_u(w.x_test, w.W, w.b, w.scale, beta)
+    ue = _kink("allen_cahn1d", w.x_test, 0.1)
+    err = np.linalg.norm(u - ue) / np.linalg.norm(ue)
+    assert err < 2e-5, err
+
+
+def test_newton_burgers_jacobian_converges_quadratically():
+    """At nu = 1 the Burgers step with J = -nu phi'' + u' phi + u phi' (both per-point
+    terms) reaches the approximation floor within two steps from the linear warm
+    start: each accepted step squares the error.  Dropping either term of the
+    Jacobian or flipping its sign leaves a contraction far slower than that."""
+    w = wl.burgers1d(n_int=600, n_feat=300)
+    _, (hist,) = _solve_1d(w, [np.array([-1.0])], 3)
+    assert hist[2] < 1e-6 * hist[0], hist
+
+
+def test_newton_burgers_continuation_recovers_the_shock():
+    """Continuation nu = 1, 0.5, 0.2, 0.1 (Sec. 2.4), each stage warm-started from the
+    previous one, ends at the viscous shock -tanh((x - 1/2)/(2 nu))."""
+    w = wl.burgers1d(n_int=600, n_feat=300)
+    beta, hists = _solve_1d(w, list(wl.burgers_stage_coef(0.1)), 12)
+    for h in hists:
+        assert np.all(np.diff(h) <= 0)
+    u = oracle.eval_u(w.x_test, w.W, w.b, w.scale, beta)
+    ue = _kink("burgers1d", w.x_test, 0.1)
+    err = np.linalg.norm(u - ue) / np.linalg.norm(ue)
+    assert err < 1e-4, err
