@@ -295,6 +295,64 @@ def _secondary(fl, pl, wl, torch, ctx, dev, n_inverse):
                                 f"continuation nu = {', '.join(f'{-c[0]:g}' for c in stages)}, "
                                 f"<= {iters} iterations per stage"))}
 
+    # learnable bandwidth (Alg. 2): the gradient of the outer loss ||A beta* - rhs||^2 in
+    # sigma (W = sigma W_hat) after each solve: residual, adjoint vector v (PCG), the
+    # feature-weight gradient of both row blocks (on the fly, FP64) and the contraction
+    # with W_hat.  Tikhonov mu = 1e-6: with much smaller mu the quantity is not
+    # determined in FP64 at this size.  The whole evaluation (rhs, assembly, MIXED solve
+    # refined by CGLS, gradient) is timed, the gradient alone too, and the gradient is
+    # checked against central differences of the loss (h = 1e-4 sigma)
+    import copy as _copy
+    wbw = wl.helmholtz2d()
+    wbw.mu = 1e-6
+    W_hat = wbw.W / wbw.sigma
+
+    def _bw_solver(sig):
+        wq = _copy.copy(wbw)
+        wq.W = sig * W_hat
+        return pl.LinearSolver(ctx, pl.upload(wq, dev), prec=fl.PREC_MIXED, mu=wbw.mu, max_refine=64,
+                               refine_mode=fl.REFINE_CGLS, refine_tol=1e-13)
+
+    def _bw_once(sb):
+        sb.build_rhs()
+        sb.assemble()
+        fac = sb.solve(keep=True)
+        r, _, gout = sb.outer_grad(W_hat, fac=fac, max_iter=64)
+        fl.fastlsq_factor_destroy(ctx, fac)
+        return r, gout
+
+    sb = _bw_solver(wbw.sigma)
+    for _ in range(2):
+        _bw_once(sb)
+    n_bw = 5
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_bw):
+        r_bw, gout = _bw_once(sb)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / n_bw
+    fac = sb.solve(keep=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_bw):
+        sb.outer_grad(W_hat, fac=fac, max_iter=64)
+    torch.cuda.synchronize()
+    sec_g = (time.perf_counter() - t0) / n_bw
+    fl.fastlsq_factor_destroy(ctx, fac)
+    g_sigma = float(gout[-1].item())
+    hb = 1e-4 * wbw.sigma
+    lp = _bw_once(_bw_solver(wbw.sigma + hb))[0]
+    lm = _bw_once(_bw_solver(wbw.sigma - hb))[0]
+    fd = (float((lp * lp).sum()) - float((lm * lm).sum())) / (2 * hb)
+    out["bandwidth_grad"] = {
+        "seconds_per_eval": sec, "evals_per_s": 1.0 / sec, "gradient_ms": 1e3 * sec_g,
+        "dL_dsigma": g_sigma, "fd_dL_dsigma": fd, "rel_diff_vs_fd": abs(g_sigma - fd) / abs(fd),
+        "workload": ("helmholtz2d (9216 x 2048, sigma = 8, Tikhonov mu = 1e-6): outer loss "
+                     "||A beta* - rhs||^2 of the learnable-bandwidth loop; per evaluation rhs, FP32+FP64 "
+                     "assembly, MIXED solve with CGLS refinement, residual, v by PCG, dL/dW (FP64, on the "
+                     "fly) and dL/dsigma; checked against central differences of the loss")}
+    del sb
+
     # cached re-solves (App. F.4): factor the helmholtz2d operator once, then solve for
     # new right-hand sides (Q^T b, R^{-1}, two refinement steps) against the kept factor
     wr = wl.helmholtz2d()

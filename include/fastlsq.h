@@ -368,6 +368,48 @@ FASTLSQ_API int fastlsq_inverse_batch(fastlsq_ctx *ctx, const fastlsq_inverse_in
                                       int32_t n_inst, const fastlsq_op *op, int32_t n_src,
                                       const fastlsq_inverse_opts *opts);
 
+/*
+ * Feature-weight and bias gradients through the exact inner solve (learnable
+ * bandwidth, App. "Learnable Bandwidth via Reparameterisation", Alg. 2).  For the
+ * block A_ij = row_weight * scale * sum_t coef_t D^{alpha_t} phi_j(x_i) of op (no
+ * per-point terms) and the adjoint weights
+ *   w_ij = r_i (c_v v_j + c_rb beta_j) + c_av (A v)_i beta_j
+ * (r = rhs - A beta on these rows, v = (A^T A + mu I)^{-1} g, Av = (A v) on these rows),
+ * it accumulates
+ *   gW[j*d + k] += sum_i w_ij dA_ij/dW_jk,     gb[j] += sum_i w_ij dA_ij/db_j
+ * with the entries' derivatives formed on the fly in FP64 from eq. cyclic (never
+ * stored).  A loss that sees A only through beta with grad_beta = g takes (c_v, c_rb,
+ * c_av) = (1, 0, -1); the outer loss ||A beta - rhs||^2 of Alg. 2 takes v =
+ * (A^T A + mu I)^{-1} beta and (-2 mu, -2, 2 mu), or v = Av = NULL when mu = 0.  Call
+ * once per row block (interior rows with the PDE operator, boundary rows with the
+ * identity operator and the boundary weight); zero gW and gb first.  x: [n_rows][d];
+ * W: [n_feat][d]; b, beta, v: [n_feat]; r, Av: [n_rows]; gW: [n_feat][d]; gb: [n_feat]
+ * or NULL; v and Av may be NULL (their terms dropped).  All device, stream-ordered.
+ */
+FASTLSQ_API int fastlsq_weight_grad(fastlsq_ctx *ctx, const double *x, int64_t n_rows,
+                                    const fastlsq_op *op, double row_weight, const double *W,
+                                    const double *b, int64_t n_feat, double scale,
+                                    const double *r, const double *beta, const double *v,
+                                    const double *Av, double c_v, double c_rb, double c_av,
+                                    double *gW, double *gb);
+
+/*
+ * Contraction of a feature-weight gradient with the frozen base weights W_hat:
+ *   out[a*d + c] = sum_j gW[j][a] W_hat[j][c],     out[d*d] = sum_a out[a*d + a],
+ * so that for W_j = L W_hat_j (eq. reparam_cholesky) dL/dL_ac = out[a*d + c] (take
+ * the lower triangle) and for W = sigma W_hat (eq. reparam_scalar) dL/dsigma =
+ * out[d*d].  gW, W_hat: [n_feat][d]; out: [d*d + 1]; all device.
+ */
+FASTLSQ_API int fastlsq_bandwidth_grad(fastlsq_ctx *ctx, const double *gW, const double *W_hat,
+                                       int64_t n_feat, int32_t d, double *out);
+
+/*
+ * r = rhs - A beta in FP64 (eq. linear_system's residual), A: m x n column-major
+ * (ld >= m), beta: [n], rhs, r: [m]; all device.
+ */
+FASTLSQ_API int fastlsq_residual(fastlsq_ctx *ctx, const double *A, int64_t ld, int64_t m,
+                                 int64_t n, const double *beta, const double *rhs, double *r);
+
 /* Nonlinearities N(u) of the Newton problems (Sec. 3.3): nl_lam e^u, nl_lam u^3, or the
  * Burgers advection term nl_lam u du/dx_0 (derivative along the first coordinate). */
 typedef enum { FASTLSQ_NL_NONE = 0, FASTLSQ_NL_EXP = 1, FASTLSQ_NL_CUBIC = 2,

@@ -89,6 +89,10 @@ def _load():
         lib.orc_term_coef_grad.argtypes = [_D, _L, ctypes.c_int, _I, _D, _D, _L,
                                            ctypes.c_double, _D, _D, _D, _D]
         lib.orc_term_coef_grad.restype = ctypes.c_double
+        lib.orc_weight_grad.argtypes = [_D, _L, ctypes.c_int, ctypes.c_int, _I, _D,
+                                        ctypes.c_double, _D, _D, _L, ctypes.c_double, _D, _D,
+                                        _D, _D, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, _D, _D]
         _lib = lib
         return lib
 
@@ -267,3 +271,22 @@ def term_coef_grad(x_int, alpha_t, W, b, scale, r, Av, v, beta):
     return lib.orc_term_coef_grad(_d(x_int), n_int, d, _i(_i32(alpha_t)), _d(W), _d(_f64(b)),
                                   W.shape[0], float(scale), _d(_f64(r)), _d(_f64(Av)),
                                   _d(_f64(v)), _d(_f64(beta)))
+
+
+def weight_grad(x, alpha, coef, row_weight, W, b, scale, r, beta, v=None, Av=None, c_v=1.0,
+                c_rb=0.0, c_av=-1.0):
+    """Feature-weight and bias gradients of the bilinear adjoint form (orc_weight_grad).
+    Returns (gW [n_feat][d], gb [n_feat])."""
+    lib = _load()
+    x = _f64(np.atleast_2d(x))
+    n, d = x.shape
+    W = _f64(W).reshape(-1, d)
+    alpha = _i32(alpha).reshape(-1, d)
+    gW = np.zeros_like(W)
+    gb = np.zeros(W.shape[0])
+    nul = ctypes.cast(None, _D)
+    lib.orc_weight_grad(_d(x), n, d, alpha.shape[0], _i(alpha), _d(_f64(coef)), float(row_weight),
+                        _d(W), _d(_f64(b)), W.shape[0], float(scale), _d(_f64(r)), _d(_f64(beta)),
+                        nul if v is None else _d(_f64(v)), nul if Av is None else _d(_f64(Av)),
+                        float(c_v), float(c_rb), float(c_av), _d(gW), _d(gb))
+    return gW, gb

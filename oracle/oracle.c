@@ -609,3 +609,65 @@ double orc_term_coef_grad(const double *x_int, long n_int, int d, const int *alp
     free(At);
     return g;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Learnable bandwidth (App. "Learnable Bandwidth via Reparameterisation",    */
+/* Alg. 2): the gradient of a loss with respect to the feature weights W and  */
+/* biases b through the exact inner solve.                                    */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * dA_ij/dW_jk for the block A_ij = row_weight * scale * sum_t coef_t D^{alpha_t} phi_j(x_i):
+ * each term is coef_t * prod_l W_jl^alpha_tl * Phi_{|alpha_t|}(z) (eq. cyclic), so by the
+ * product rule
+ *   d/dW_jk = coef_t * [alpha_tk W_jk^(alpha_tk - 1) prod_{l != k} W_jl^alpha_tl Phi_{|alpha_t|}(z)
+ *                       + prod_l W_jl^alpha_tl * x_ik * Phi_{|alpha_t| + 1}(z)],
+ * and d/db_j replaces x_ik by 1 in the second part and drops the first.
+ *
+ * Weights of the bilinear form (differentiating the normal equations
+ * (A^T A + mu I) beta = A^T rhs, r = rhs - A beta, v = (A^T A + mu I)^{-1} g):
+ *   w_ij = r_i (c_v v_j + c_rb beta_j) + c_av (A v)_i beta_j.
+ * A loss that sees A only through beta, with grad_beta = g, takes (c_v, c_rb, c_av) =
+ * (1, 0, -1) (as orc_term_coef_grad).  The outer loss ||A beta - rhs||^2 of Alg. 2 has
+ * grad_beta = -2 A^T r = -2 mu beta and an explicit dependence on A (-2 r_i beta_j): with
+ * v = (A^T A + mu I)^{-1} beta it takes (c_v, c_rb, c_av) = (-2 mu, -2, 2 mu).  v and Av
+ * may be NULL (their terms dropped).
+ *   gW[j*d + k] += sum_i w_ij dA_ij/dW_jk,    gb[j] += sum_i w_ij dA_ij/db_j.
+ */
+void orc_weight_grad(const double *x, long n_rows, int d, int n_terms, const int *alpha,
+                     const double *coef, double row_weight, const double *W, const double *b,
+                     long n_feat, double scale, const double *r, const double *beta,
+                     const double *v, const double *Av, double c_v, double c_rb, double c_av,
+                     double *gW, double *gb)
+{
+    for (long j = 0; j < n_feat; ++j) {
+        const double *Wj = W + j * d;
+        for (long i = 0; i < n_rows; ++i) {
+            const double *xi = x + i * d;
+            double wij = r[i] * ((v ? c_v * v[j] : 0.0) + c_rb * beta[j]);
+            if (Av) wij += c_av * Av[i] * beta[j];
+            double z = orc_arg(xi, Wj, b[j], d);
+            for (int t = 0; t < n_terms; ++t) {
+                const int *at = alpha + t * d;
+                double c;
+                int s;
+                orc_term_derivative(at, d, Wj, &c, &s);
+                double f = wij * row_weight * scale * coef[t];
+                double phase_next = orc_phase((s + 1) & 3, z);
+                gb[j] += f * c * phase_next;
+                for (int k = 0; k < d; ++k) {
+                    /* product-rule factor of W_jk: alpha_tk W_jk^(alpha_tk - 1) prod_{l != k} */
+                    double dc = 0.0;
+                    if (at[k] > 0) {
+                        dc = (double)at[k];
+                        for (int l = 0; l < d; ++l) {
+                            int p = (l == k) ? at[l] - 1 : at[l];
+                            for (int q = 0; q < p; ++q) dc *= Wj[l];
+                        }
+                    }
+                    gW[j * d + k] += f * (dc * orc_phase(s, z) + c * xi[k] * phase_next);
+                }
+            }
+        }
+    }
+}

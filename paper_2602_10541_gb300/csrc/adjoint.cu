@@ -93,7 +93,36 @@ k_coef_grad(const double *__restrict__ x, int64_t n_rows, fl_op_params op,
     }
 }
 
+// out[q] = sum over blocks, in block order, of part[blk * stride + q] (q < ncols)
+__global__ void k_sum_blocks(const double *__restrict__ part, int64_t nblk, int stride, int ncols,
+                             double *__restrict__ out)
+{
+    const int q = threadIdx.x;
+    if (q >= ncols) return;
+    double acc = 0.0;
+    for (int64_t blk = 0; blk < nblk; ++blk) acc += part[blk * stride + q];
+    out[q] = acc;
+}
+
 }  // namespace
+
+int fl_reduce_blocks_to_host(fastlsq_ctx *ctx, double *part, int64_t nblk, int stride, int ncols,
+                             double *host_out)
+{
+    // the sums land in the row after the last block's partials (the caller sizes part
+    // for nblk + 1 rows), then one copy of ncols values to the host
+    double *sums = part + nblk * stride;
+    {
+    FL_PROF(ctx, FASTLSQ_K_ADJOINT);
+    k_sum_blocks<<<1, 64, 0, ctx->stream>>>(part, nblk, stride, ncols, sums);
+    FL_CHECK_LAUNCH(ctx, "sum_blocks");
+    }
+    cudaError_t e = cudaMemcpyAsync(host_out, sums, sizeof(double) * ncols, cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fl_cuda(ctx, e, "gradient readback");
+    return 0;
+}
 
 int fl_matvec64(fastlsq_ctx *ctx, const double *A, int64_t ld, int64_t m, int64_t n,
                 const double *v, double *out)
@@ -120,7 +149,7 @@ int fl_launch_coef_grad(fastlsq_ctx *ctx, const double *x, int64_t n_rows, const
     if (n_rows == 0 || op.n_terms == 0) return 0;
     dim3 grid((unsigned)fl_cdiv(n_rows, CG_THREADS), (unsigned)fl_cdiv(n_feat, CG_COLS));
     size_t nblk = (size_t)grid.x * grid.y;
-    double *part = (double *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(double) * nblk * FL_MAX_TERMS);
+    double *part = (double *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(double) * (nblk + 1) * FL_MAX_TERMS);
     if (!part) return FASTLSQ_ERR_NOMEM;
     {
     FL_PROF(ctx, FASTLSQ_K_ADJOINT);
@@ -128,12 +157,5 @@ int fl_launch_coef_grad(fastlsq_ctx *ctx, const double *x, int64_t n_rows, const
                                                       beta, part);
     FL_CHECK_LAUNCH(ctx, "coef_grad");
     }
-    std::vector<double> h(nblk * FL_MAX_TERMS);
-    cudaError_t e = cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(),
-                                    cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return fl_cuda(ctx, e, "coef_grad readback");
-    for (size_t blk = 0; blk < nblk; ++blk)
-        for (int t = 0; t < op.n_terms; ++t) grad_host[t] += h[blk * FL_MAX_TERMS + t];
-    return 0;
+    return fl_reduce_blocks_to_host(ctx, part, (int64_t)nblk, FL_MAX_TERMS, op.n_terms, grad_host);
 }

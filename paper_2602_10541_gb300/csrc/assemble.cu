@@ -631,22 +631,12 @@ int fl_launch_source_grad(fastlsq_ctx *ctx, const double *x, int64_t n, const do
     th.n = 4 * n_src;
     int nblk = (int)std::min<int64_t>(fl_cdiv(n, 256), 304);
     if (nblk < 1) nblk = 1;
-    double *part = (double *)fl_ws(ctx, FL_WS_SCALARS, sizeof(double) * 32 * nblk);
+    double *part = (double *)fl_ws(ctx, FL_WS_SCALARS, sizeof(double) * 32 * (nblk + 1));
     if (!part) return FASTLSQ_ERR_NOMEM;
     {
     FL_PROF(ctx, FASTLSQ_K_ADJOINT);
     k_source_grad<<<nblk, 256, 0, ctx->stream>>>(x, n, th, n_src, w, part);
     FL_CHECK_LAUNCH(ctx, "source_grad");
     }
-    std::vector<double> h((size_t)32 * nblk);
-    cudaError_t e = cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(),
-                                    cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return fl_cuda(ctx, e, "source_grad readback");
-    for (int q = 0; q < 4 * n_src; ++q) {
-        double acc = 0.0;
-        for (int blk = 0; blk < nblk; ++blk) acc += h[(size_t)blk * 32 + q];
-        dtheta_host[q] = acc;
-    }
-    return 0;
+    return fl_reduce_blocks_to_host(ctx, part, nblk, 32, 4 * n_src, dtheta_host);
 }

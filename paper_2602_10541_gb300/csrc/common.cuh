@@ -47,6 +47,7 @@ enum fl_slot {
     FL_WS_ZBUF,            // Z = T^T V^T C of the current trailing update
     FL_WS_COUNTERS,        // completion counters of the trailing-update column tiles
     FL_WS_VIMG,            // the panel's V as the tensor-core update's operand image
+    FL_WS_WGRAD,           // row-chunk partial sums of the feature-weight gradient
     FL_WS_COUNT
 };
 
@@ -148,6 +149,12 @@ struct fl_op_params {
 };
 
 int fl_pack_op(fastlsq_ctx *ctx, const fastlsq_op *op, fl_op_params *out);
+
+// Sums, on the device and in block order, the per-block partials part[blk * stride + q]
+// (q < ncols, ncols <= 64) into part[nblk * stride + q], then copies them to host_out and
+// synchronises the context's stream.  part must hold nblk + 1 rows of stride doubles.
+int fl_reduce_blocks_to_host(fastlsq_ctx *ctx, double *part, int64_t nblk, int stride, int ncols,
+                             double *host_out);
 
 // Kernels / launchers implemented in the .cu files ---------------------------
 int fl_prefactors(fastlsq_ctx *ctx, const fl_op_params &op, const double *W, int64_t n_feat,

@@ -105,6 +105,10 @@ _SIGNATURES = {
     "fastlsq_newton_continuation": [_vp, ctypes.POINTER(fastlsq_newton_problem), _vp, _vp, _i64,
                                     _dbl, ctypes.POINTER(fastlsq_newton_opts), _i32,
                                     ctypes.POINTER(_dbl), _vp, ctypes.POINTER(fastlsq_newton_stats)],
+    "fastlsq_weight_grad": [_vp, _vp, _i64, ctypes.POINTER(fastlsq_op), _dbl, _vp, _vp, _i64, _dbl,
+                            _vp, _vp, _vp, _vp, _dbl, _dbl, _dbl, _vp, _vp],
+    "fastlsq_bandwidth_grad": [_vp, _vp, _vp, _i64, _i32, _vp],
+    "fastlsq_residual": [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp],
     "fastlsq_inverse_batch": [_vp, ctypes.POINTER(fastlsq_inverse_instance), _i32,
                               ctypes.POINTER(fastlsq_op), _i32, ctypes.POINTER(fastlsq_inverse_opts)],
     "fastlsq_profile_enable": [_vp, ctypes.c_int],
@@ -350,6 +354,27 @@ def fastlsq_coef_grad(ctx, x, op, W, b, scale, r, Av, v, beta):
                                         _ptr(Av), _ptr(v), _ptr(beta),
                                         out.ctypes.data_as(ctypes.POINTER(_dbl))))
     return out
+
+
+def fastlsq_weight_grad(ctx, x, op, row_weight, W, b, scale, r, beta, gW, gb=None, v=None, Av=None,
+                        c_v=1.0, c_rb=0.0, c_av=-1.0):
+    """Accumulate the feature-weight (gW [n_feat][d]) and bias (gb) gradients of one row block."""
+    return ctx.check(ctx.lib.fastlsq_weight_grad(
+        ctx.handle, _ptr(x), x.shape[0], ctypes.byref(op.struct), float(row_weight), _ptr(W),
+        _ptr(b), W.shape[0], float(scale), _ptr(r), _ptr(beta), _ptr(v), _ptr(Av), float(c_v),
+        float(c_rb), float(c_av), _ptr(gW), _ptr(gb)))
+
+
+def fastlsq_bandwidth_grad(ctx, gW, W_hat, out):
+    """out [d*d + 1] (device): sum_j gW[j][a] W_hat[j][c], then the trace."""
+    return ctx.check(ctx.lib.fastlsq_bandwidth_grad(ctx.handle, _ptr(gW), _ptr(W_hat), gW.shape[0],
+                                                    gW.shape[1], _ptr(out)))
+
+
+def fastlsq_residual(ctx, A, m, beta, rhs, r):
+    """r = rhs - A beta for the FP64 operator A ([n][ld] storage of an m x n column-major matrix)."""
+    return ctx.check(ctx.lib.fastlsq_residual(ctx.handle, _ptr(A), A.shape[1], m, A.shape[0], _ptr(beta),
+                                              _ptr(rhs), _ptr(r)))
 
 
 def fastlsq_newton(ctx, x_int, x_bc, op, nl_kind, nl_lam, bc_weight, f, g, W, b, scale, beta,

@@ -111,6 +111,38 @@ class LinearSolver:
         self.assemble()
         return self.solve(stats=stats)
 
+    def outer_grad(self, W_hat, fac=None, max_iter=0):
+        """Gradient of the outer loss ||A beta* - rhs||^2 of Alg. 2 (learnable bandwidth)
+        after a solve: r = rhs - A beta (FP64 operator), for mu > 0 the adjoint vector
+        v = (A^T A + mu I)^{-1} beta and A v from the kept factor `fac`, then the
+        feature-weight gradient of both row blocks and its contraction with W_hat.
+        Returns (r [m], gW [n_feat][d], out [d*d + 1]): out[a*d + c] = dL/dL_ac for
+        W_j = L W_hat_j, out[d*d] = dL/dsigma for W = sigma W_hat."""
+        ctx, dp, w = self.ctx, self.dp, self.dp.w
+        dev = dp.W.device
+        beta = self.beta[0]
+        r = torch.empty(self.m, dtype=torch.float64, device=dev)
+        fl.fastlsq_residual(ctx, self.A64, self.m, beta, self.rhs[0], r)
+        v = Av = None
+        if self.mu > 0:
+            if fac is None:
+                raise ValueError("outer_grad: mu > 0 needs the kept factor")
+            v = torch.empty(self.n, dtype=torch.float64, device=dev)
+            Av = torch.empty(self.m, dtype=torch.float64, device=dev)
+            fl.fastlsq_backward(ctx, fac, beta, v, Av, self.A64, max_iter=max_iter)
+        gW = torch.zeros((self.n, w.d), dtype=torch.float64, device=dev)
+        gb = torch.zeros(self.n, dtype=torch.float64, device=dev)
+        cf = dict(c_v=-2.0 * self.mu, c_rb=-2.0, c_av=2.0 * self.mu)
+        ni = w.n_int
+        fl.fastlsq_weight_grad(ctx, dp.x_int, dp.op_int, 1.0, dp.W, dp.b, w.scale, r[:ni], beta, gW, gb,
+                               v=v, Av=None if Av is None else Av[:ni], **cf)
+        fl.fastlsq_weight_grad(ctx, dp.x_bc, dp.op_bc, w.lam_bc, dp.W, dp.b, w.scale, r[ni:], beta, gW,
+                               gb, v=v, Av=None if Av is None else Av[ni:], **cf)
+        out = torch.empty(w.d * w.d + 1, dtype=torch.float64, device=dev)
+        W_hat = torch.as_tensor(np.ascontiguousarray(W_hat), dtype=torch.float64, device=dev)
+        fl.fastlsq_bandwidth_grad(ctx, gW, W_hat, out)
+        return r, gW, out
+
     def u_test(self, beta=None):
         dp = self.dp
         u = torch.empty(dp.x_test.shape[0], dtype=torch.float64, device=dp.W.device)
