@@ -81,16 +81,19 @@ typedef enum { FASTLSQ_REFINE_CLASSICAL = 0, FASTLSQ_REFINE_CGLS = 1 } fastlsq_r
 
 /* A linear operator as a list of terms sum_t coef[t] D^{alpha_t} (the paper's Op,
  * App. B).  alpha: host [n_terms][d] multi-indices; coef: host [n_terms].
- * pp_*: optional per-point terms (at most 4) whose coefficient varies by row:
+ * pp_*: optional per-point terms (at most 8) whose coefficient varies by row:
  * term q adds pp_coef[q][i] * D^{pp_alpha_q} phi_j(x_i), pp_coef[q] a DEVICE
  * double array of n_rows entries (the rows of this call).  This is how the
- * Newton Jacobian's N'(u_i) phi_j enters (eq. newton). */
+ * Newton Jacobian's N'(u_i) phi_j enters (eq. newton), and how a variable-
+ * coefficient operator such as div(nu grad u) = nu Lap u + grad nu . grad u
+ * (Sec. 4.4, coil localisation) is written: 2d per-point terms with coefficients
+ * nu(x_i) on D^{2e_k} and d nu/dx_k(x_i) on D^{e_k}. */
 typedef struct {
     int32_t d;
     int32_t n_terms;
     const int32_t *alpha;          /* host [n_terms * d] */
     const double *coef;            /* host [n_terms]     */
-    int32_t n_pp;                  /* number of per-point terms (0..4) */
+    int32_t n_pp;                  /* number of per-point terms (0..8) */
     const int32_t *pp_alpha;       /* host [n_pp * d]    */
     const double *const *pp_coef;  /* host array of n_pp DEVICE pointers */
 } fastlsq_op;
@@ -153,11 +156,18 @@ typedef enum {
                                        /* Allen-Cahn; f = 0), u* = tanh((x - 1/2) / sqrt(2 eps))     */
     FASTLSQ_PROBLEM_BURGERS_1D = 9,    /* u u' - nu u'' = 0 on [0,1], params[0] = nu (Sec. 3.3 steady */
                                        /* Burgers; f = 0), u* = -tanh((x - 1/2) / (2 nu))            */
+    FASTLSQ_PROBLEM_VARCOEF_2D = 10,   /* div(nu grad u) = f on [0,1]^2 (Sec. 4.4's variable-          */
+                                       /* coefficient form), nu = 1 + a (x^2 + y^2/2), params[0] = a, */
+                                       /* u* = sin(pi x) sin(2 pi y) + x y; kinds COEF / COEF_GRAD    */
+                                       /* give nu and its gradient at points                           */
     FASTLSQ_PROBLEM_GAUSS_SOURCE_2D = 5 /* -Lap u = sum_k a_k exp(-|x-c_k|^2/(2 w_k^2)), params =   */
                                        /* theta [n_src][4] = (c_x, c_y, w, a)                      */
 } fastlsq_problem;
 
-typedef enum { FASTLSQ_RHS_SOURCE = 0, FASTLSQ_RHS_EXACT = 1 } fastlsq_rhs_kind;
+/* SOURCE: f; EXACT: u*; COEF: the variable coefficient nu of the problem's operator;
+ * COEF_GRAD + k: d nu / d x_k (problems with a variable coefficient only). */
+typedef enum { FASTLSQ_RHS_SOURCE = 0, FASTLSQ_RHS_EXACT = 1, FASTLSQ_RHS_COEF = 2,
+               FASTLSQ_RHS_COEF_GRAD = 3 } fastlsq_rhs_kind;
 
 /*
  * Right-hand side entries (eq. linear_system): out[i] = weight * f(x_i)

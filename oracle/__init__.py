@@ -36,6 +36,7 @@ NLPOISSON_2D = 6
 NLHELMHOLTZ_2D = 7
 ALLEN_CAHN_1D = 8
 BURGERS_1D = 9
+VARCOEF_2D = 10
 
 NL_NONE, NL_EXP, NL_CUBIC, NL_BURGERS = 0, 1, 2, 3
 
@@ -89,6 +90,7 @@ def _load():
         lib.orc_term_coef_grad.argtypes = [_D, _L, ctypes.c_int, _I, _D, _D, _L,
                                            ctypes.c_double, _D, _D, _D, _D]
         lib.orc_term_coef_grad.restype = ctypes.c_double
+        lib.orc_problem_coef.argtypes = [ctypes.c_int, ctypes.c_int, _D, _L, ctypes.c_int, _D, _D]
         lib.orc_weight_grad.argtypes = [_D, _L, ctypes.c_int, ctypes.c_int, _I, _D,
                                         ctypes.c_double, _D, _D, _L, ctypes.c_double, _D, _D,
                                         _D, _D, ctypes.c_double, ctypes.c_double,
@@ -188,6 +190,17 @@ def lstsq(A, rhs, mu=0.0):
     if rc != 0:
         raise MemoryError("orc_lstsq")
     return beta
+
+
+def problem_coef(prob, comp, x, params=()):
+    """Variable coefficient nu (comp = -1) or d nu / d x_comp at points (orc_problem_coef)."""
+    lib = _load()
+    x = _f64(np.atleast_2d(x))
+    n, d = x.shape
+    p = _f64(np.asarray(params, dtype=np.float64).reshape(-1) if len(params) else np.zeros(1))
+    out = np.zeros(n)
+    lib.orc_problem_coef(int(prob), int(comp), _d(x), n, d, _d(p), _d(out))
+    return out
 
 
 def problem_exact(prob, x, params=()):

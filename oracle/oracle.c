@@ -260,8 +260,29 @@ enum {
     /* that solves the equation exactly on the real line, Dirichlet data u* at x = 0, 1:  */
     ORC_ALLEN_CAHN_1D = 8, /* eps u'' + u - u^3 = 0; params[0] = eps;                          */
                            /* u* = tanh((x - 1/2) / sqrt(2 eps))                                */
-    ORC_BURGERS_1D = 9     /* u u' - nu u'' = 0; params[0] = nu; u* = -tanh((x - 1/2) / (2 nu))  */
+    ORC_BURGERS_1D = 9,    /* u u' - nu u'' = 0; params[0] = nu; u* = -tanh((x - 1/2) / (2 nu))  */
+    /* the variable-coefficient form of Sec. 4.4 (div(nu grad u), expanded as             */
+    /* nu Lap u + grad nu . grad u), with a manufactured u*:                              */
+    ORC_VARCOEF_2D = 10    /* div(nu grad u) = f on [0,1]^2, nu = 1 + a (x^2 + y^2/2),           */
+                           /* params[0] = a; u* = sin(pi x) sin(2 pi y) + x y                    */
 };
+
+/* The variable coefficient of problem 10 (comp = -1) or its derivative along x_comp. */
+void orc_problem_coef(int prob, int comp, const double *x, long n, int d, const double *params,
+                      double *out)
+{
+    for (long i = 0; i < n; ++i) {
+        const double *p = x + i * d;
+        double v = 0.0;
+        if (prob == ORC_VARCOEF_2D) {
+            const double a = params[0];
+            if (comp < 0) v = 1.0 + a * (p[0] * p[0] + 0.5 * p[1] * p[1]);
+            else if (comp == 0) v = 2.0 * a * p[0];
+            else if (comp == 1) v = a * p[1];
+        }
+        out[i] = v;
+    }
+}
 
 /* s(x; theta) = sum_k a_k exp(-|x - c_k|^2 / (2 w_k^2)), theta_k = (c_kx, c_ky, w_k, a_k). */
 static double orc_gauss(const double *x, const double *theta, int n_src)
@@ -299,6 +320,8 @@ void orc_problem_exact(int prob, const double *x, long n, int d,
         } else if (prob == ORC_BURGERS_1D) {
             /* u = -tanh(k s): u u' = k tanh sech^2 and nu u'' = 2 nu k^2 tanh sech^2, equal at k = 1/(2 nu) */
             v = -tanh((p[0] - 0.5) / (2.0 * params[0]));
+        } else if (prob == ORC_VARCOEF_2D) {
+            v = sin(pi * p[0]) * sin(2 * pi * p[1]) + p[0] * p[1];
         }
         u[i] = v;
     }
@@ -335,6 +358,15 @@ void orc_problem_source(int prob, const double *x, long n, int d,
                 v = 2 * pi * pi * s + params[0] * u * u * u;
             else
                 v = -2 * pi * pi * s + params[0] * params[0] * u + params[1] * u * u * u;
+        } else if (prob == ORC_VARCOEF_2D) {
+            /* nu Lap u* + grad nu . grad u*, with Lap u* = -5 pi^2 sin(pi x) sin(2 pi y) (x y is
+             * harmonic) and grad u* = (pi cos(pi x) sin(2 pi y) + y, 2 pi sin(pi x) cos(2 pi y) + x) */
+            double a = params[0];
+            double s = sin(pi * p[0]) * sin(2 * pi * p[1]);
+            double nu = 1.0 + a * (p[0] * p[0] + 0.5 * p[1] * p[1]);
+            double ux = pi * cos(pi * p[0]) * sin(2 * pi * p[1]) + p[1];
+            double uy = 2 * pi * sin(pi * p[0]) * cos(2 * pi * p[1]) + p[0];
+            v = nu * (-5 * pi * pi * s) + 2.0 * a * p[0] * ux + a * p[1] * uy;
         }
         f[i] = v;
     }

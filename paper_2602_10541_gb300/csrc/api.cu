@@ -389,8 +389,14 @@ extern "C" int fastlsq_rhs(fastlsq_ctx *ctx, fastlsq_problem problem, fastlsq_rh
     if (!ctx) return FASTLSQ_ERR_INVALID;
     if (n < 0 || d < 1 || d > FL_MAX_D || n_params < 0 || (n_params > 0 && !params))
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "rhs: bad arguments");
-    if (problem < FASTLSQ_PROBLEM_POISSON_1D || problem > FASTLSQ_PROBLEM_BURGERS_1D)
+    if (problem < FASTLSQ_PROBLEM_POISSON_1D || problem > FASTLSQ_PROBLEM_VARCOEF_2D)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "rhs: unknown problem %d", (int)problem);
+    if (kind < FASTLSQ_RHS_SOURCE || kind >= FASTLSQ_RHS_COEF_GRAD + d)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "rhs: kind %d", (int)kind);
+    if (kind >= FASTLSQ_RHS_COEF && problem != FASTLSQ_PROBLEM_VARCOEF_2D)
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "rhs: problem %d has no variable coefficient", (int)problem);
+    if (problem == FASTLSQ_PROBLEM_VARCOEF_2D && (n_params < 1 || d != 2))
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "rhs: problem 10 needs d = 2 and params[0] = a");
     if ((problem == FASTLSQ_PROBLEM_ALLEN_CAHN_1D || problem == FASTLSQ_PROBLEM_BURGERS_1D) &&
         kind == FASTLSQ_RHS_EXACT && (n_params < 1 || !(params[0] > 0)))
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "rhs: problem %d needs params[0] > 0", (int)problem);

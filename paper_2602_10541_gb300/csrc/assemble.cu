@@ -67,12 +67,14 @@ struct fl_pp_rows {
 // dimension D is a template parameter, so the inner loop holds exactly D FMAs.
 // CTA tile: 128 rows (32 lanes x 4 rows) x 256 columns; the column data (W, b, P,
 // Q) are converted to float once per CTA into shared memory, the thread's 4 points
-// once per thread into registers.
+// once per thread into registers.  NPP is the number of per-point terms compiled in:
+// 0 for plain operators (no registers or shared memory spent on them), FL_MAX_PP for
+// operators with per-point coefficients (Newton Jacobians, variable coefficients).
 constexpr int AF_ROWS = 128;
 constexpr int AF_COLS = 256;
 constexpr int AF_THREADS = 256;
 
-template <int D, bool NEED_COS>
+template <int D, bool NEED_COS, int NPP>
 __global__ void __launch_bounds__(AF_THREADS)
 k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
                const double *__restrict__ W, const double *__restrict__ b, int64_t n_feat,
@@ -82,7 +84,7 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
 {
     __shared__ float sW[D][AF_COLS];
     __shared__ float sB[AF_COLS], sP[AF_COLS], sQ[NEED_COS ? AF_COLS : 1];
-    __shared__ float sM[FL_MAX_PP][AF_COLS];
+    __shared__ float sM[NPP > 0 ? NPP : 1][AF_COLS];
     __shared__ float sX[AF_ROWS][D];                     // the CTA's points, converted once
 
     const int64_t col0 = (int64_t)blockIdx.y * AF_COLS;
@@ -96,7 +98,8 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
         sB[t] = (float)b[col0 + t];
         sP[t] = (float)pref[col0 + t];
         if (NEED_COS) sQ[t] = (float)pref[n_feat + col0 + t];
-        for (int q = 0; q < n_pp; ++q) sM[q][t] = (float)pref[(2 + q) * n_feat + col0 + t];
+        if constexpr (NPP > 0)
+            for (int q = 0; q < n_pp; ++q) sM[q][t] = (float)pref[(2 + q) * n_feat + col0 + t];
     }
 
     for (int t = threadIdx.x; t < AF_ROWS * D; t += AF_THREADS) {
@@ -108,7 +111,7 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
     const int warp = threadIdx.x >> 5;
     const int64_t r0 = row0 + 4 * lane;
     float xr[4][D];
-    float cpt[FL_MAX_PP][4];
+    float cpt[NPP > 0 ? NPP : 1][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int64_t i = r0 + u;
@@ -116,7 +119,7 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
 #pragma unroll
         for (int k = 0; k < D; ++k) xr[u][k] = sX[4 * lane + u][k];
 #pragma unroll
-        for (int q = 0; q < FL_MAX_PP; ++q) cpt[q][u] = (ok && q < n_pp) ? (float)pp.c[q][i] : 0.f;
+        for (int q = 0; q < NPP; ++q) cpt[q][u] = (ok && q < n_pp) ? (float)pp.c[q][i] : 0.f;
     }
     const bool full = (r0 + 3 < n_rows);
     const int64_t gr = row_offset + r0;
@@ -143,9 +146,9 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
                 cs = __cosf(r);
                 val = fmaf(sQ[c], cs, val);
             }
-            if (n_pp > 0) {                               // uniform: per-point terms (Newton)
+            if constexpr (NPP > 0) {                      // per-point terms
 #pragma unroll
-                for (int q = 0; q < FL_MAX_PP; ++q) {
+                for (int q = 0; q < NPP; ++q) {
                     if (q >= n_pp) break;
                     const float phi = ((pp_cos_mask >> q) & 1) ? (NEED_COS ? cs : __cosf(r)) : sn;
                     val = fmaf(cpt[q][u] * sM[q][c], phi, val);
@@ -165,7 +168,7 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
 }
 
 // FP64 assembly: double FMAs and double-precision sin/cos (CUDA's sin, cos).
-template <bool NEED_COS>
+template <bool NEED_COS, int NPP>
 __global__ void __launch_bounds__(ASM_THREADS)
 k_assemble_f64(const double *__restrict__ x, int64_t n_rows, int d,
                const double *__restrict__ W, const double *__restrict__ b, int64_t n_feat,
@@ -174,7 +177,7 @@ k_assemble_f64(const double *__restrict__ x, int64_t n_rows, int d,
 {
     __shared__ double sW[ASM_COLS][FL_MAX_D];
     __shared__ double sB[ASM_COLS], sP[ASM_COLS], sQ[ASM_COLS];
-    __shared__ double sM[FL_MAX_PP][ASM_COLS];
+    __shared__ double sM[NPP > 0 ? NPP : 1][ASM_COLS];
     const int64_t col0 = (int64_t)blockIdx.y * ASM_COLS;
     const int64_t row0 = (int64_t)blockIdx.x * ASM_ROWS;
     for (int t = threadIdx.x; t < ASM_COLS; t += blockDim.x) {
@@ -184,13 +187,14 @@ k_assemble_f64(const double *__restrict__ x, int64_t n_rows, int d,
         sB[t] = ok ? b[j] : 0.0;
         sP[t] = ok ? pref[j] : 0.0;
         sQ[t] = ok ? pref[n_feat + j] : 0.0;
-        for (int q = 0; q < n_pp; ++q) sM[q][t] = ok ? pref[(2 + q) * n_feat + j] : 0.0;
+        if constexpr (NPP > 0)
+            for (int q = 0; q < n_pp; ++q) sM[q][t] = ok ? pref[(2 + q) * n_feat + j] : 0.0;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     double xr[4][FL_MAX_D];
-    double cpt[FL_MAX_PP][4];
+    double cpt[NPP > 0 ? NPP : 1][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         int64_t i = row0 + lane + 32 * u;
@@ -198,7 +202,7 @@ k_assemble_f64(const double *__restrict__ x, int64_t n_rows, int d,
 #pragma unroll
         for (int k = 0; k < FL_MAX_D; ++k) xr[u][k] = (ok && k < d) ? x[i * d + k] : 0.0;
 #pragma unroll
-        for (int q = 0; q < FL_MAX_PP; ++q) cpt[q][u] = (ok && q < n_pp) ? pp.c[q][i] : 0.0;
+        for (int q = 0; q < NPP; ++q) cpt[q][u] = (ok && q < n_pp) ? pp.c[q][i] : 0.0;
     }
     for (int cc = 0; cc < ASM_COLS / 8; ++cc) {
         const int c = warp * (ASM_COLS / 8) + cc;
@@ -217,7 +221,7 @@ k_assemble_f64(const double *__restrict__ x, int64_t n_rows, int d,
             double val = sP[c] * sn;
             if (NEED_COS) val = fma(sQ[c], cs, val);
 #pragma unroll
-            for (int q = 0; q < FL_MAX_PP; ++q)
+            for (int q = 0; q < NPP; ++q)
                 if (q < n_pp) val = fma(cpt[q][u] * sM[q][c], ((pp_cos_mask >> q) & 1) ? cs : sn, val);
             if (i < n_rows) A[j * ldA + row_offset + i] = val;
         }
@@ -382,6 +386,23 @@ __global__ void k_rhs(int problem, int kind, fl_problem_params prm, const double
         else v = -2 * pi * pi * sp + prm.p[0] * prm.p[0] * us + prm.p[1] * us * us * us;
         break;
     }
+    case FASTLSQ_PROBLEM_VARCOEF_2D: {
+        // div(nu grad u) = nu Lap u + grad nu . grad u with nu = 1 + a (x^2 + y^2/2) and
+        // u* = sin(pi x) sin(2 pi y) + x y (Lap u* = -5 pi^2 sin(pi x) sin(2 pi y))
+        const double a = prm.p[0];
+        const double nu = 1.0 + a * (p[0] * p[0] + 0.5 * p[1] * p[1]);
+        const double s2 = sin(pi * p[0]) * sin(2 * pi * p[1]);
+        if (kind == FASTLSQ_RHS_EXACT) v = s2 + p[0] * p[1];
+        else if (kind == FASTLSQ_RHS_COEF) v = nu;
+        else if (kind == FASTLSQ_RHS_COEF_GRAD) v = 2.0 * a * p[0];
+        else if (kind == FASTLSQ_RHS_COEF_GRAD + 1) v = a * p[1];
+        else if (kind == FASTLSQ_RHS_SOURCE) {
+            const double ux = pi * cos(pi * p[0]) * sin(2 * pi * p[1]) + p[1];
+            const double uy = 2 * pi * sin(pi * p[0]) * cos(2 * pi * p[1]) + p[0];
+            v = nu * (-5 * pi * pi * s2) + 2.0 * a * p[0] * ux + a * p[1] * uy;
+        }
+        break;
+    }
     case FASTLSQ_PROBLEM_ALLEN_CAHN_1D:
         // tanh(k s) with k^2 = 1/(2 eps) solves eps u'' + u - u^3 = 0 (f = 0)
         if (kind == FASTLSQ_RHS_EXACT) v = tanh((p[0] - 0.5) / sqrt(2.0 * prm.p[0]));
@@ -485,20 +506,25 @@ int fl_launch_assemble_f32(fastlsq_ctx *ctx, const fl_op_params &op, const doubl
     const dim3 grid((unsigned)fl_cdiv(n_rows, AF_ROWS), (unsigned)fl_cdiv(n_feat, AF_COLS));
     const float c1 = ctx->cw2pi[0], c2 = ctx->cw2pi[1], c3 = ctx->cw2pi[2];
     FL_PROF(ctx, FASTLSQ_K_ASSEMBLE_F32);
+#define FL_ASM32_PP(DD, COS, NPP)                                                                    \
+    k_assemble_f32<DD, COS, NPP><<<grid, AF_THREADS, 0, ctx->stream>>>(                              \
+        x, n_rows, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset, c1, c2, c3)
 #define FL_ASM32(DD)                                                                                 \
     case DD:                                                                                         \
-        if (need_cos)                                                                                \
-            k_assemble_f32<DD, true><<<grid, AF_THREADS, 0, ctx->stream>>>(                          \
-                x, n_rows, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset, c1, c2, c3);   \
-        else                                                                                         \
-            k_assemble_f32<DD, false><<<grid, AF_THREADS, 0, ctx->stream>>>(                         \
-                x, n_rows, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset, c1, c2, c3);   \
+        if (op.n_pp > 0) {                                                                           \
+            if (need_cos) FL_ASM32_PP(DD, true, FL_MAX_PP);                                          \
+            else FL_ASM32_PP(DD, false, FL_MAX_PP);                                                  \
+        } else {                                                                                     \
+            if (need_cos) FL_ASM32_PP(DD, true, 0);                                                  \
+            else FL_ASM32_PP(DD, false, 0);                                                          \
+        }                                                                                            \
         break;
     switch (op.d) {
         FL_ASM32(1) FL_ASM32(2) FL_ASM32(3) FL_ASM32(4) FL_ASM32(5) FL_ASM32(6) FL_ASM32(7) FL_ASM32(8)
     default: return fl_fail(ctx, FASTLSQ_ERR_INVALID, "assemble: dimension %d", op.d);
     }
 #undef FL_ASM32
+#undef FL_ASM32_PP
     FL_CHECK_LAUNCH(ctx, "assemble_f32");
     return 0;
 }
@@ -515,12 +541,17 @@ int fl_launch_assemble_f64(fastlsq_ctx *ctx, const fl_op_params &op, const doubl
     for (int q = 0; q < op.n_pp; ++q) pp.c[q] = op.pp_coef[q];
     dim3 grid((unsigned)fl_cdiv(n_rows, ASM_ROWS), (unsigned)fl_cdiv(n_feat, ASM_COLS));
     FL_PROF(ctx, FASTLSQ_K_ASSEMBLE_F64);
-    if (need_cos)
-        k_assemble_f64<true><<<grid, ASM_THREADS, 0, ctx->stream>>>(
-            x, n_rows, op.d, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset);
-    else
-        k_assemble_f64<false><<<grid, ASM_THREADS, 0, ctx->stream>>>(
-            x, n_rows, op.d, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset);
+#define FL_ASM64(COS, NPP)                                                                          \
+    k_assemble_f64<COS, NPP><<<grid, ASM_THREADS, 0, ctx->stream>>>(                                \
+        x, n_rows, op.d, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset)
+    if (op.n_pp > 0) {
+        if (need_cos) FL_ASM64(true, FL_MAX_PP);
+        else FL_ASM64(false, FL_MAX_PP);
+    } else {
+        if (need_cos) FL_ASM64(true, 0);
+        else FL_ASM64(false, 0);
+    }
+#undef FL_ASM64
     FL_CHECK_LAUNCH(ctx, "assemble_f64");
     return 0;
 }

@@ -14,7 +14,7 @@
 
 #define FL_MAX_D 8
 #define FL_MAX_TERMS 32
-#define FL_MAX_PP 4
+#define FL_MAX_PP 8
 #define FL_MAX_FEAT 16384
 
 // Device error flag codes (first one raised wins).

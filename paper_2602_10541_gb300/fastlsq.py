@@ -21,10 +21,11 @@ _lib = None
 F32, F64 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 REFINE_CLASSICAL, REFINE_CGLS = 0, 1
-RHS_SOURCE, RHS_EXACT = 0, 1
+RHS_SOURCE, RHS_EXACT, RHS_COEF, RHS_COEF_GRAD = 0, 1, 2, 3
 POISSON_1D, HELMHOLTZ_2D, POISSON_5D, BRATU_2D, GAUSS_SOURCE_2D = 1, 2, 3, 4, 5
 NLPOISSON_2D, NLHELMHOLTZ_2D = 6, 7
 ALLEN_CAHN_1D, BURGERS_1D = 8, 9
+VARCOEF_2D = 10
 NL_NONE, NL_EXP, NL_CUBIC, NL_BURGERS = 0, 1, 2, 3
 
 _vp = ctypes.c_void_p

@@ -27,10 +27,24 @@ class DeviceProblem:
     op_bc: fl.Op
 
 
-def upload(w: Workload, device="cuda:0") -> DeviceProblem:
+def upload(w: Workload, device="cuda:0", ctx=None) -> DeviceProblem:
+    """Copy a workload's inputs to the GPU.  A workload with per-point terms (variable
+    coefficients) needs ctx: their coefficients at the interior points are evaluated
+    on the GPU from the problem catalogue (fastlsq_rhs with the workload's kinds)."""
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
-    return DeviceProblem(w, t(w.x_int), t(w.x_bc), t(w.W), t(w.b), t(w.x_test),
-                         fl.Op(w.alpha, w.coef), fl.Op.identity(w.d))
+    x_int = t(w.x_int)
+    op_int = fl.Op(w.alpha, w.coef)
+    if w.pp_alpha is not None:
+        if ctx is None:
+            raise ValueError("upload: a workload with per-point terms needs a context")
+        pp = []
+        for kind in w.pp_kinds:
+            c = torch.empty(w.n_int, dtype=torch.float64, device=device)
+            fl.fastlsq_rhs(ctx, w.problem, kind, w.params, x_int, 1.0, c)
+            pp.append(c)
+        op_int = fl.Op(w.alpha, w.coef, pp_alpha=w.pp_alpha, pp_coef=pp)
+    return DeviceProblem(w, x_int, t(w.x_bc), t(w.W), t(w.b), t(w.x_test), op_int,
+                         fl.Op.identity(w.d))
 
 
 class LinearSolver:

@@ -100,6 +100,8 @@ class Workload:
     mu: float = 0.0
     nl_kind: int = 0                # 0 none, 1 exp, 2 cubic, 3 Burgers (u u_x0)
     nl_lam: float = 0.0
+    pp_alpha: np.ndarray = None     # [n_pp][d] per-point terms of L (variable coefficients)
+    pp_kinds: tuple = None          # rhs kinds giving each per-point coefficient at x_int
     x_int: np.ndarray = field(default=None, repr=False)
     x_bc: np.ndarray = field(default=None, repr=False)
     W: np.ndarray = field(default=None, repr=False)
@@ -256,6 +258,24 @@ def burgers_stage_coef(nu=0.1):
     BURGERS_STAGES down to nu."""
     stages = [v for v in BURGERS_STAGES if v > nu] + [nu]
     return np.array([[-v] for v in stages])
+
+
+def varcoef2d(n_int=8192, n_bc=1024, n_feat=2048, a=1.0):
+    """div(nu grad u) = f on [0,1]^2 with nu = 1 + a (x^2 + y^2/2) (the variable-coefficient
+    form of Sec. 4.4, expanded as nu Lap u + grad nu . grad u), manufactured
+    u* = sin(pi x) sin(2 pi y) + x y (problem 10); the operator is four per-point terms
+    with coefficients nu, nu, d nu/dx, d nu/dy on D^(2,0), D^(0,2), D^(1,0), D^(0,1);
+    points as helmholtz2d, sigma = 6, boundary weight 100."""
+    s = SEED0 + 10
+    w = Workload("varcoef2d", 10, 2, n_int, n_bc, n_feat, 6.0, 100.0,
+                 np.zeros((1, 2), np.int32), np.zeros(1), np.array([a]), s,
+                 pp_alpha=np.array([[2, 0], [0, 2], [1, 0], [0, 1]], np.int32),
+                 pp_kinds=(2, 2, 3, 4))
+    w.x_int = uniform(s + 100, "x_int", n_int * 2).reshape(n_int, 2)
+    w.x_bc = box_boundary(s + 100, "x_bc", n_bc, 2, per_face=True)
+    w.W, w.b = _features(s, n_feat, 2, w.sigma)
+    w.x_test = uniform(s + 200, "test", 5000 * 2).reshape(-1, 2)
+    return w
 
 
 def gauss_theta(seed: int, name: str, n_src: int = 4) -> np.ndarray:
