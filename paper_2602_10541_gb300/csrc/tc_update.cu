@@ -137,6 +137,11 @@ k_vimg(const float *__restrict__ F, int64_t ld, int64_t k, int ncols, int64_t mp
 constexpr int TY_CONV = TY_THREADS / 32 - 2;     // converter warps
 constexpr int TY_LAND = 6;                       // landing slots (raw, then hi)
 constexpr int TY_LO = 2;                         // lo slots
+// Independent TMEM accumulators: the three split products of a chunk (hi*hi, hi*lo,
+// lo*hi) and the chunk's parity each go to their own 32-column accumulator, so that
+// consecutive MMAs do not wait on one accumulator; the epilogue adds the six.
+constexpr int TY_NACC = 6;
+constexpr uint32_t TY_TMEM = 256;                // columns allocated (power of two >= 6 x 32)
 constexpr uint32_t TY_SLOT = TY_A + TY_B;        // one chunk: C part then V part
 constexpr int TY_QA = TY_A / 16, TY_QB = TY_B / 16;                  // float4 per part
 constexpr int TY_PER = (TY_QA + TY_QB + 32 * TY_CONV - 1) / (32 * TY_CONV);   // per converter thread
@@ -161,7 +166,7 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
     const int nchunks = (int)fl_max64(0, fl_cdiv_dev(tchunks - blockIdx.y, S));
     auto row0 = [&](int ch) { return ((int64_t)blockIdx.y + (int64_t)ch * S) * TY_K; };
 
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, 32);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, TY_TMEM);
     if (threadIdx.x == 0) {
         for (int s = 0; s < TY_LAND; ++s) {
             tc::mbar_init(&full[s], 1);
@@ -214,12 +219,15 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
                 unsigned char *Ah = land + s * TY_SLOT, *Bh = Ah + TY_A, *Al = lo + t * TY_SLOT, *Bl = Al + TY_A;
                 const uint64_t dAh = tc::smem_desc_sw128(Ah), dAl = tc::smem_desc_sw128(Al);
                 const uint64_t dBh = tc::smem_desc_sw128(Bh), dBl = tc::smem_desc_sw128(Bl);
+                // accumulators (parity of ch) x (hi*hi, hi*lo, lo*hi) at TMEM columns 32 a
+                const uint32_t d0 = tmem + (uint32_t)(96 * (ch & 1));
 #pragma unroll
                 for (int ks = 0; ks < TY_K / 8; ++ks) {
                     const uint64_t o = (uint64_t)(ks * 32) >> 4;      // 8 tf32 = 32 bytes along K
-                    tc::mma_tf32(tmem, dAh + o, dBh + o, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
-                    tc::mma_tf32(tmem, dAh + o, dBl + o, idesc, 1u);
-                    tc::mma_tf32(tmem, dAl + o, dBh + o, idesc, 1u);
+                    const uint32_t acc = (ch > 1 || ks > 0) ? 1u : 0u;
+                    tc::mma_tf32(d0, dAh + o, dBh + o, idesc, acc);
+                    tc::mma_tf32(d0 + 32, dAh + o, dBl + o, idesc, acc);
+                    tc::mma_tf32(d0 + 64, dAl + o, dBh + o, idesc, acc);
                 }
                 tc::mma_commit(&land_empty[s]);
                 tc::mma_commit(&lo_empty[t]);
@@ -303,11 +311,15 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
         const int q4 = warp & 3, lc = 16 * (warp >> 2);
         const int64_t c = cbase + q4 * 32 + lane;
         float v[16];
-        if (nchunks > 0) {
-            tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + lc, v);
-        } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        // the accumulators written: all six once there are two chunks, three with one
+        const int nacc = nchunks > 1 ? TY_NACC : (nchunks > 0 ? 3 : 0);
+        for (int a = 0; a < nacc; ++a) {
+            float w[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(32 * a + lc), w);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += w[j];
         }
         if (c < nct)
 #pragma unroll
@@ -315,7 +327,7 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+    if (warp == 0) tc::tmem_dealloc(tmem, TY_TMEM);
     if (ok)   // uniform; the ring is free once the last MMA has completed
         trail_finish_z<float, 32, TY_C, TY_THREADS, true>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Zimg,
                                                           counters + blockIdx.x, reinterpret_cast<float *>(base));
@@ -339,7 +351,9 @@ k_tcu(const __grid_constant__ CUtensorMap mT, float *__restrict__ F, int64_t ld,
     const int64_t rbase = (int64_t)blockIdx.x * TU_R;
     const int64_t cbase = (int64_t)blockIdx.y * TU_C;
 
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, TU_C);
+    // three accumulators (hi*hi, hi*lo, lo*hi) of TU_C columns each, added in the epilogue,
+    // so that consecutive MMAs do not wait on one accumulator; two CTAs per SM use 512
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 4 * TU_C);
     if (threadIdx.x == 0) {
         tc::mbar_init(&bar_c, 1);
         tc::mbar_init(&bar_z, 1);
@@ -372,9 +386,10 @@ k_tcu(const __grid_constant__ CUtensorMap mT, float *__restrict__ F, int64_t ld,
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
             const uint64_t o = (uint64_t)(ks * 32) >> 4;
-            tc::mma_tf32(tmem, dAh + o, dBh + o, idesc, ks > 0 ? 1u : 0u);
-            tc::mma_tf32(tmem, dAh + o, dBl + o, idesc, 1u);
-            tc::mma_tf32(tmem, dAl + o, dBh + o, idesc, 1u);
+            const uint32_t acc = ks > 0 ? 1u : 0u;
+            tc::mma_tf32(tmem, dAh + o, dBh + o, idesc, acc);
+            tc::mma_tf32(tmem + TU_C, dAh + o, dBl + o, idesc, acc);
+            tc::mma_tf32(tmem + 2 * TU_C, dAl + o, dBh + o, idesc, acc);
         }
         tc::mma_commit(&bar_m);
     }
@@ -399,8 +414,13 @@ k_tcu(const __grid_constant__ CUtensorMap mT, float *__restrict__ F, int64_t ld,
         const int64_t i = rbase + r;
 #pragma unroll
         for (int cc = c0; cc < c0 + 32; cc += 16) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + cc, v);
+            float v[16], w1[16], w2[16];
+            const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + cc;
+            tc::tmem_ld16(ta, v);
+            tc::tmem_ld16(ta + TU_C, w1);
+            tc::tmem_ld16(ta + 2 * TU_C, w2);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] += w1[j] + w2[j];
             if (i < mp) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -412,7 +432,7 @@ k_tcu(const __grid_constant__ CUtensorMap mT, float *__restrict__ F, int64_t ld,
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, TU_C);
+    if (warp == 0) tc::tmem_dealloc(tmem, 4 * TU_C);
 }
 
 }  // namespace
