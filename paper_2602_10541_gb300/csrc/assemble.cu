@@ -544,12 +544,15 @@ int fl_launch_assemble_f64(fastlsq_ctx *ctx, const fl_op_params &op, const doubl
 #define FL_ASM64(COS, NPP)                                                                          \
     k_assemble_f64<COS, NPP><<<grid, ASM_THREADS, 0, ctx->stream>>>(                                \
         x, n_rows, op.d, W, b, n_feat, pref, op.n_pp, mask, pp, A, ldA, row_offset)
-    if (op.n_pp > 0) {
+    // FP64: the four-slot form (per-point loop checked at run time) for every operator with
+    // at most four per-point terms, plain operators included -- measured 684 us against 877 us
+    // for a form without the loop on the helmholtz2d interior block -- and eight slots beyond
+    if (op.n_pp > 4) {
         if (need_cos) FL_ASM64(true, FL_MAX_PP);
         else FL_ASM64(false, FL_MAX_PP);
     } else {
-        if (need_cos) FL_ASM64(true, 0);
-        else FL_ASM64(false, 0);
+        if (need_cos) FL_ASM64(true, 4);
+        else FL_ASM64(false, 4);
     }
 #undef FL_ASM64
     FL_CHECK_LAUNCH(ctx, "assemble_f64");
