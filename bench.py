@@ -160,12 +160,17 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def _src_sha(name):
-    with open(os.path.join(ROOT, "paper_2602_10541_gb300", "csrc", name), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+def _src_sha(names):
+    """Hash of a kernel class's sources (the .cu file and the headers its kernels use)."""
+    h = hashlib.sha256()
+    for name in (names,) if isinstance(names, str) else names:
+        with open(os.path.join(ROOT, "paper_2602_10541_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
-KERNEL_SRC = {"panel": "panel_row.cu", "trail_simt": "qr.cu", "trail_tc": "tc_update.cu",
+KERNEL_SRC = {"panel": "panel_row.cu", "trail_simt": "qr.cu",
+              "trail_tc": ("tc_update.cu", "trail_z.cuh", "tc_common.cuh"),
               "apply_q": "apply_q.cu", "trsv": "refine.cu", "residual": "qr.cu",
               "assemble_f32": "assemble.cu", "assemble_f64": "assemble.cu", "copy_in": "qr.cu"}
 

@@ -59,26 +59,37 @@ __device__ __forceinline__ void trail_finish_z(const T *__restrict__ Ypart, int 
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) sY[it * THREADS + threadIdx.x] = acc[it];
     __syncthreads();
+    // Z(l, c) = sum_{q <= l} T(q, l) Y(q, c): the thread keeps its column c of Y in registers
+    // and forms its ITEMS rows l = h + R it at once (R = THREADS / COLS, h = tid / COLS, the
+    // same for a whole warp, so T's entries are broadcast reads)
+    static_assert(THREADS % COLS == 0, "threads cover whole columns");
+    constexpr int R = THREADS / COLS;
+    const int cc = threadIdx.x % COLS, h = threadIdx.x / COLS;
+    const int64_t c = cbase + cc;
+    T y[NB], z[ITEMS];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) y[q] = sY[q * COLS + cc];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) z[it] = T(0);
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+            const int l = h + R * it;
+            if (q <= l) z[it] += sT[q + l * NB] * y[q];
+        }
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
-        const int idx = it * THREADS + threadIdx.x;
-        const int l = idx / COLS, cc = idx % COLS;
-        const int64_t c = cbase + cc;
+        const int l = h + R * it;
         if constexpr (IMG) {
-            T z = T(0);
-            if (c < nct)
-                for (int q = 0; q <= l; ++q) z += sT[q + l * NB] * sY[q * COLS + cc];
-            float h, lo;
-            tc::split_tf32((float)z, h, lo);
+            float hi, lo;
+            tc::split_tf32((float)(c < nct ? z[it] : T(0)), hi, lo);
             float *img = reinterpret_cast<float *>(Z) + (cbase / COLS) * (2 * COLS * 32);
             const uint32_t off = tc::sw128_offset((uint32_t)cc, (uint32_t)l) >> 2;
-            img[off] = h;
+            img[off] = hi;
             img[COLS * 32 + off] = lo;
         } else {
-            if (c >= nct) continue;
-            T z = T(0);
-            for (int q = 0; q <= l; ++q) z += sT[q + l * NB] * sY[q * COLS + cc];
-            Z[(int64_t)l * nct + c] = z;
+            if (c < nct) Z[(int64_t)l * nct + c] = z[it];
         }
     }
     if (threadIdx.x == 0) *counter = 0;
