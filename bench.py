@@ -474,12 +474,15 @@ def main():
                     help="1: FP32 substitution in the triangular solves of classical refinement")
     ap.add_argument("--no-extras", action="store_true", help="skip the Newton and inverse-problem timings")
     ap.add_argument("--inverse-instances", type=int, default=32)
-    ap.add_argument("--instances", type=int, default=4,
+    ap.add_argument("--instances", type=int, default=8,
                     help="independent full-size solves per step, each on its own stream")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
                     help="assemble the FP64 operator on a side stream during the factorisation")
-    ap.add_argument("--lookahead", type=int, default=1, choices=[0, 1],
-                    help="1: factor the next panel on a second stream during the trailing update")
+    ap.add_argument("--lookahead", type=int, default=0, choices=[0, 1],
+                    help="1: factor the next panel on a second stream during the trailing update; "
+                         "0 (default here): with 8 solves in flight the other instances already "
+                         "fill the SMs beside each panel, and the split update costs more than "
+                         "it hides")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -594,13 +597,17 @@ def main():
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tpath):
-        tinfo = json.load(open(tpath)).get(dominant)
-        if tinfo and tinfo.get("src_sha") == _src_sha(KERNEL_SRC.get(dominant, "qr.cu")):
+        tinfo = json.load(open(tpath)).get(f"{dominant}@lookahead{args.lookahead}")
+        # a capture counts only for the same sources and the same split of the update
+        # (with look-ahead the panel kernel updates the next panel's columns itself)
+        if (tinfo and tinfo.get("src_sha") == _src_sha(KERNEL_SRC.get(dominant, "qr.cu"))
+                and tinfo.get("lookahead") == args.lookahead):
             traffic = tinfo.get("bytes_per_launch")
     roofline = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak, "traffic": traffic,
                 "launches": dom_launches, "avg_launch_us": 1e3 * dom_ms / max(1, dom_launches),
-                "peak_source": peak_src}
+                "peak_source": peak_src,
+                "concurrent_instances": B}     # each launch shares the GPU with B - 1 other solves
     breakdown = {k: {"launches_per_step": v[0] / 2.0, "ms_per_step": v[1] / 2.0}
                  for k, v in prof_pre.items() if v[0]}
     # the same roofline arithmetic for every class of the pre-pass (two steps), for context
@@ -624,11 +631,13 @@ def main():
     fl.fastlsq_set_stream(ctx, stream)
     u_mixed = solver.u_test()
     s64 = pl.LinearSolver(ctx, dp, prec=fl.PREC_FP64)
+    fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, 1)   # one solve alone: the library default
     torch.cuda.synchronize()
     t64 = time.perf_counter()
     s64.step()
     torch.cuda.synchronize()
     fp64_ms = 1e3 * (time.perf_counter() - t64)
+    fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, args.lookahead)
     u64 = s64.u_test()
     ue = solver.u_exact_test()
     accuracy = {"rel_l2_vs_fp64_gpu": pl.rel_l2(u_mixed, u64), "rel_l2_vs_exact": pl.rel_l2(u_mixed, ue),
@@ -692,6 +701,8 @@ def main():
 
     extras = None
     if rank == 0 and not args.no_extras:
+        # one solve, Newton run or instance at a time: look-ahead on (the library default)
+        fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, 1)
         extras = _secondary(fl, pl, wl, torch, ctx, dev, args.inverse_instances)
 
     if rank == 0:
@@ -703,7 +714,7 @@ def main():
                            "precision": f"mixed: FP32 assembly and Householder QR, FP64 residual, "
                                         f"{args.refine} refinement steps",
                            "tensor_core_updates": bool(solve_stats.tensor_core),
-                           "panel_nb": nb, "l2": "flushed between steps (256 MiB write outside the step events)",
+                           "panel_nb": nb, "lookahead": bool(args.lookahead), "l2": "flushed between steps (256 MiB write outside the step events)",
                            "instances_per_step": B,
                            "concurrency": (f"{B} independent instances (seeds) of the workload per step, "
                                            "each on its own context and stream"),

@@ -248,9 +248,12 @@ def main(argv=None):
     ap.add_argument("--tensor-core", action="store_true",
                     help="tcgen05 trailing updates (MIXED; the default)")
     ap.add_argument("--simt", action="store_true", help="SIMT FP32 trailing updates instead")
+    ap.add_argument("--lookahead", type=int, default=1, choices=[0, 1],
+                    help="1 (the library default): factor the next panel on a second stream")
     a = ap.parse_args(argv)
     ctx = fl.Context(0)
     fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 0 if a.simt else 1)
+    fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, a.lookahead)
     dp = upload(wl.CONFIGS[a.workload]())
     s = LinearSolver(ctx, dp, prec=fl.PREC_MIXED if a.prec == "mixed" else fl.PREC_FP64,
                      max_refine=a.refine,
