@@ -4,7 +4,7 @@
 // For panel k with Householder block V (m_p x 32, unit lower trapezoidal) and
 // compact-WY factor T, C -= V (T^T (V^T C)) in two kernels:
 //   k_tcy : Y^T = C^T V over interleaved row chunks (MMA M = 128 columns of C, N = 32,
-//           K = rows in chunks of 32).  A ring of 6 landing slots is filled by TMA: a C
+//           K = rows in chunks of 32).  A ring of 3 landing slots is filled by TMA: a C
 //           chunk (32 rows x 128 columns) and a V chunk (32 rows x 32 columns) land in
 //           the K-major 128-byte-swizzled layout the MMA reads (the column-major factor
 //           is already K-major for both).  Six warps split a landed chunk into hi (in
@@ -135,7 +135,11 @@ k_vimg(const float *__restrict__ F, int64_t ld, int64_t k, int ncols, int64_t mp
 // lo_empty (MMAs done); no CTA-wide synchronisation inside the loop.
 // ---------------------------------------------------------------------------
 constexpr int TY_CONV = TY_THREADS / 32 - 2;     // converter warps
-constexpr int TY_LAND = 6;                       // landing slots (raw, then hi)
+// Three landing slots and two lo slots: 100 KB of shared memory, so two CTAs (of one
+// solve or of two solves on other streams) fit on an SM.  One solve at a time, 4 and 6
+// landing slots ran at the same speed; with eight solves in flight, 3 slots gave 296
+// solves/s against 272 with 4 or 6 (one CTA per SM).
+constexpr int TY_LAND = 3;                       // landing slots (raw, then hi)
 constexpr int TY_LO = 2;                         // lo slots
 // Independent TMEM accumulators: the three split products of a chunk (hi*hi, hi*lo,
 // lo*hi) and the chunk's parity each go to their own 32-column accumulator, so that
