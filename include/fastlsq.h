@@ -21,7 +21,8 @@
  *    coefficients are double precision; the operator matrix may be float or
  *    double (fastlsq_dtype).
  *  - Work is queued on the context's stream and is asynchronous unless the call
- *    documents a host read-back (the stats structs).
+ *    documents a host read-back (the stats structs).  Call with the context's
+ *    device current on the calling thread (fastlsq_create leaves it current).
  *  - Return value: 0 success; negative = error (-1 invalid argument, -2 out of
  *    memory, -3 CUDA error, -4 device-side wait timed out, -5 non-finite value);
  *    positive = warning (1 Newton reached max_iter, 2 line search failed,
@@ -203,8 +204,12 @@ FASTLSQ_API int fastlsq_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, 
 
 /*
  * fastlsq_eval without any device allocation.  The paper has no counterpart: this
- * entry serves callers that must not allocate device memory while they run (code
- * under a no-allocation policy, or code being captured into a CUDA graph).
+ * entry serves callers that cannot call cudaMalloc while they run, for example a
+ * service that reserves all of its device memory at start-up and must not fail or
+ * stall on an allocation in the middle of a request, or code running inside a
+ * custom device allocator's own callbacks, where allocating again would re-enter
+ * the allocator.  fastlsq_eval may grow the context's workspace with cudaMalloc;
+ * this call never does.
  *
  * Arguments, layout and result are those of fastlsq_eval, and the result is
  * bitwise the same (the same kernels in the same order).  The only difference is
@@ -217,8 +222,9 @@ FASTLSQ_API int fastlsq_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, 
  * call reads was written earlier in the same call.
  *
  * The array's device address is looked up with cudaGetSymbolAddress on the first
- * call on each device; make that first call before capturing a stream into a
- * graph.  There is one array per device for the whole process: two calls whose
+ * call on each device (with the context's device made current for the lookup, and
+ * the caller's device restored after it); make that first call before any stream
+ * capture begins.  There is one array per device for the whole process: two calls whose
  * executions can overlap (different streams, host threads or contexts on the same
  * device) use the same scratch and give wrong results.  Serialise them.
  */

@@ -12,6 +12,7 @@
 // Per-point terms (the Newton Jacobian's N'(u_i) phi_j) keep their own column
 // multiplier M_qj = s m_qj (+-1) and a per-row coefficient.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "common.cuh"
@@ -610,16 +611,26 @@ int fl_launch_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t n_eval, in
         return fl_fail(ctx, FASTLSQ_ERR_INVALID,
                        "eval_noalloc: ceil(n_feat/%d) * n_eval = %lld exceeds the %lld-entry static scratch",
                        EVAL_SPLIT_COLS, (long long)(nsplit * n_eval), (long long)FL_EVAL_STATIC_DOUBLES);
-    static double *addr[64] = {};            // per device ordinal; every thread writes the same value
+    // the array's device address, per device ordinal; racing first calls store the same value
+    static std::atomic<double *> addr[64];
     if (ctx->device < 0 || ctx->device >= 64)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval_noalloc: device ordinal %d", ctx->device);
-    if (!addr[ctx->device]) {
+    double *part = addr[ctx->device].load(std::memory_order_acquire);
+    if (!part) {
+        // the symbol's address is per device: look it up with the context's device current,
+        // then give the calling thread its own device back
+        int cur = -1;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess) return fl_cuda(ctx, e, "eval_noalloc: current device");
+        if (cur != ctx->device && (e = cudaSetDevice(ctx->device)) != cudaSuccess)
+            return fl_cuda(ctx, e, "eval_noalloc: select the context's device");
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_eval_static);
+        e = cudaGetSymbolAddress(&p, g_eval_static);
+        if (cur != ctx->device) cudaSetDevice(cur);
         if (e != cudaSuccess) return fl_cuda(ctx, e, "eval_noalloc: scratch address");
-        addr[ctx->device] = (double *)p;
+        part = (double *)p;
+        addr[ctx->device].store(part, std::memory_order_release);
     }
-    double *part = addr[ctx->device];
     dim3 grid((unsigned)fl_cdiv(n_eval, 128), (unsigned)nsplit);
     FL_PROF_N(ctx, FASTLSQ_K_EVAL, 2);
     k_eval_partial<<<grid, 128, 0, ctx->stream>>>(x, n_eval, d, W, b, n_feat, beta, part);

@@ -1,5 +1,8 @@
 """fastlsq_eval_noalloc, the evaluation entry point whose scratch is a fixed array
 inside the library (no device allocation), against fastlsq_eval on the same inputs.
+It exists for callers that cannot call cudaMalloc mid-run: a service holding all of its
+device memory from start-up, which must not fail or stall on an allocation during a
+request, or code inside a custom allocator's callbacks, which must not re-enter it.
 
 Collected last (file name) so that it also runs after every other GPU test in the
 same process; it passes alone as well.
