@@ -4,10 +4,11 @@
 Workload: the 2-D Helmholtz problem (Lap u + 16 u = f on [0,1]^2, manufactured
 u* = sin(pi x) sin(2 pi y) + 0.3 cos(3 pi x + pi y), 8192 uniform-random interior
 points + 1024 boundary points (256 per edge, weight 100), 2048 frozen features
-W ~ N(0, 64 I), b ~ U(0, 2 pi)).  One step = one whole linear PDE solve (Alg. 1):
-right-hand side, operator assembly (FP32 for the factor, FP64 for the refinement
-residual), blocked Householder QR, triangular solve and two steps of FP64
-iterative refinement, all in libfastlsq kernels through the C ABI.
+W ~ N(0, 64 I), b ~ U(0, 2 pi)).  One step = 8 independent whole linear PDE solves
+(Alg. 1; seeds 0..7, each on its own context and stream, `--instances`): right-hand
+side, operator assembly (FP32 for the factor, FP64 for the refinement residual),
+blocked Householder QR, triangular solve and two steps of FP64 iterative refinement,
+all in libfastlsq kernels through the C ABI.
 
 `value` is device-timed solves/s with inputs resident in HBM (L2 flushed between
 steps, outside the per-step events); `e2e` is the same metric through the C ABI
