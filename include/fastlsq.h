@@ -514,7 +514,10 @@ typedef enum {
                                       stream while the rest of panel p's trailing update runs
                                       on a second, low-priority stream of the context (joined
                                       back into the caller's stream before the next panel's
-                                      update); 0: everything on the caller's stream */
+                                      update); 0: everything on the caller's stream, one
+                                      update pass per panel (faster when several
+                                      independent solves run on other streams and fill
+                                      the SMs beside each panel) */
     FASTLSQ_OPT_TRSV_FP32 = 3,     /* 1 (default): the triangular solves of classical
                                       refinement (MIXED) substitute in FP32 arithmetic
                                       (backward stable like the FP32 factor); 0: FP64
