@@ -192,11 +192,11 @@ int fl_apply_q_cluster(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, 
     while (CS > 1 && fl_cdiv(m_aug, CS) < 128) CS >>= 1;
     const int64_t threads = std::max<int64_t>(128, fl_round_up(fl_cdiv(m_aug, CS), 32));   // >= 128: T prefetch
     if (threads > AQC_MAX_THREADS) return 1;
-    static bool attr_done = false;
-    if (!attr_done) {
+    static FlOncePerDevice attr_once;
+    if (attr_once.pending(ctx->device)) {
         cudaError_t e = cudaFuncSetAttribute(k_apply_q_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return fl_cuda(ctx, e, "cudaFuncSetAttribute");
-        attr_done = true;
+        attr_once.done(ctx->device);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CS);

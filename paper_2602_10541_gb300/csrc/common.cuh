@@ -5,12 +5,28 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
 #include <vector>
 
 #include "../../include/fastlsq.h"
+
+// Kernel attributes (the dynamic shared-memory limit, non-portable cluster sizes) belong
+// to the kernel's module in one device's context, so they are set once per device, not
+// once per process.  Device ordinals past 63 set them on every call.
+struct FlOncePerDevice {
+    std::atomic<uint64_t> bits{0};
+    bool pending(int dev) const
+    {
+        return dev < 0 || dev >= 64 || !((bits.load(std::memory_order_acquire) >> dev) & 1u);
+    }
+    void done(int dev)
+    {
+        if (dev >= 0 && dev < 64) bits.fetch_or(uint64_t(1) << dev, std::memory_order_acq_rel);
+    }
+};
 
 #define FL_MAX_D 8
 #define FL_MAX_TERMS 32

@@ -556,13 +556,13 @@ int launch_panel_row(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t 
     const size_t smem = L.bytes();
     const size_t cap = (size_t)ctx->max_smem_optin - 1024;          // static shared memory aside
     if (smem > cap) return 2;
-    static bool attr_done = false;   // per process; attributes are per function
-    if (!attr_done) {
+    static FlOncePerDevice attr_once;
+    if (attr_once.pending(ctx->device)) {
         cudaError_t e = cudaFuncSetAttribute(k_panel_row<RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_panel_row<RPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return fl_cuda(ctx, e, "cudaFuncSetAttribute");
-        attr_done = true;
+        attr_once.done(ctx->device);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL);

@@ -714,14 +714,14 @@ cudaError_t set_max_dynamic_smem(K kernel, int optin)
 template <typename T, int NB>
 int set_panel_attrs(fastlsq_ctx *ctx)
 {
-    static bool done = false;   // per process; attributes are per function
-    if (done) return 0;
+    static FlOncePerDevice once;
+    if (!once.pending(ctx->device)) return 0;
     cudaError_t e = set_max_dynamic_smem(k_panel<T, NB>, ctx->max_smem_optin);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_panel<T, NB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 
     if (e != cudaSuccess) return fl_cuda(ctx, e, "cudaFuncSetAttribute");
-    done = true;
+    once.done(ctx->device);
     return 0;
 }
 
@@ -791,16 +791,16 @@ static int launch_trailing(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_
     T *Ypart = (T *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(T) * nsplit * NB * nct);
     T *Z = (T *)fl_ws(ctx, FL_WS_ZBUF, sizeof(T) * NB * nct);
     if (!Ypart || !Z) return FASTLSQ_ERR_NOMEM;
-    static bool attr_done = false;
+    static FlOncePerDevice attr_once;
     const size_t smem_c = sizeof(T) * NB * (TC_COLS + TC_ROWS);
-    if (!attr_done) {
+    if (attr_once.pending(ctx->device)) {
         cudaError_t e = cudaFuncSetAttribute(k_trail_c<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_c);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_trail_y<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)TrailYSmem<T, NB>::bytes);
         if (e != cudaSuccess) return fl_cuda(ctx, e, "trailing-update attributes");
-        attr_done = true;
+        attr_once.done(ctx->device);
     }
     FL_PROF_N(ctx, FASTLSQ_K_TRAIL_SIMT, 2);
     k_trail_y<T, NB><<<dim3((unsigned)ctiles, (unsigned)nsplit), TY_THREADS, TrailYSmem<T, NB>::bytes,

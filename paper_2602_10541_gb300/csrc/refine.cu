@@ -528,15 +528,15 @@ int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const doub
     const size_t smem = TrsvClusterSmem::bytes(nown_max, nblk, elem);
     using K = void (*)(const T *, int64_t, int64_t, const double *, double *, int, int *, const KryScalars *);
     K kern = a32 ? (K)k_trsv_cluster<T, float> : (K)k_trsv_cluster<T, double>;
-    static bool attr_done[2] = {false, false};   // per process; attributes are per function
+    static FlOncePerDevice attr_once[2];
     if (nown_max <= 4 && smem + elem * 2 * 4 * TG_BS <= (size_t)ctx->max_smem_optin) {
-        if (!attr_done[a32]) {
+        if (attr_once[a32].pending(ctx->device)) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  ctx->max_smem_optin - (int)(elem * 2 * 4 * TG_BS));
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return fl_cuda(ctx, e, "cudaFuncSetAttribute");
-            attr_done[a32] = true;
+            attr_once[a32].done(ctx->device);
         }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(CS);

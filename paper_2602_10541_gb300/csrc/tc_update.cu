@@ -521,13 +521,13 @@ int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_
     if (!factor_maps(F, ld, ntot, maps)) return 1;
     const size_t smem_y = (TY_LAND + TY_LO) * TY_SLOT + 1024;
     const size_t smem_u = 2 * TU_V + 2 * TU_Z + TU_CT + 1024;
-    static bool attr_done = false;
-    if (!attr_done) {
+    static FlOncePerDevice attr_once;
+    if (attr_once.pending(ctx->device)) {
         cudaError_t e = cudaFuncSetAttribute(k_tcy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_tcu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u);
         if (e != cudaSuccess) return fl_cuda(ctx, e, "tensor-core attributes");
-        attr_done = true;
+        attr_once.done(ctx->device);
     }
     const int64_t mp = m_aug - k;
     const int64_t ctiles = fl_cdiv(nct, TY_C);
