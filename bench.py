@@ -1,21 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the FastLSQ hot path on GB300 (one JSON line on rank 0).
 
-Workload: the 2-D Helmholtz problem (Lap u + 16 u = f on [0,1]^2, manufactured
-u* = sin(pi x) sin(2 pi y) + 0.3 cos(3 pi x + pi y), 8192 uniform-random interior
-points + 1024 boundary points (256 per edge, weight 100), 2048 frozen features
-W ~ N(0, 64 I), b ~ U(0, 2 pi)).  One step = 8 independent whole linear PDE solves
-(Alg. 1; seeds 0..7, each on its own context and stream, `--instances`): right-hand
-side, operator assembly (FP32 for the factor, FP64 for the refinement residual),
-blocked Householder QR, triangular solve and two steps of FP64 iterative refinement,
-all in libfastlsq kernels through the C ABI.
+Headline workload (default `--workload poisson5d`): the 5-D Poisson problem
+-Lap u = f on [0,1]^5, manufactured u* = sum_k sin(pi x_k) + prod_k x_k, 32768
+uniform-random interior points + 4096 boundary points (uniform over the 10 faces,
+weight 100), 4096 frozen features W ~ N(0, 9 I), b ~ U(0, 2 pi): the largest of the
+linear configurations.  One step = `--instances` independent whole linear PDE solves
+(Alg. 1; other seeds, each on its own context and stream): right-hand side, operator
+assembly (FP32 for the factor, FP64 for the refinement residual), two-level blocked
+Householder QR (tensor-core outer-block updates), triangular solve and two steps of
+FP64 iterative refinement, all in libfastlsq kernels through the C ABI.
+`--workload helmholtz2d` runs the 2-D Helmholtz configuration instead (9216 x 2048).
 
 `value` is device-timed solves/s with inputs resident in HBM (L2 flushed between
 steps, outside the per-step events); `e2e` is the same metric through the C ABI
 with host buffers (H2D of the points and features, D2H of beta inside the timed
-step).  The roofline object describes the kernel class with the largest device
-time, measured with CUDA events inside the timed region.  `--impl reference`
-times the FP64 CPU oracle on a bounded sample of the same workload.
+step).  `roofline` describes the factorisation's trailing update on the tensor
+cores (the Y pass and the update pass of the outer blocks), measured with CUDA
+events inside the timed region; `kernels` gives every kernel class.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload.
 """
 from __future__ import annotations
 
@@ -36,32 +40,65 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "PDE solves/s at <=1e-6 rel L2 err vs FP64 GPU path; assembly Gentries/s"
-WORKLOAD = ("helmholtz2d: Lap u + k^2 u = f, k=4, [0,1]^2, 8192 interior + 1024 boundary rows "
-            "(weight 100), 2048 features sigma=8")
-# the CPU oracle runs a sample with half the rows and half the features (1/8 of the
-# dominant m n^2 QR work) or a quarter of each (1/64); times are scaled by that ratio
-SAMPLE_CPU = dict(n_int=4096, n_bc=512, n_feat=1024)
-SAMPLE_REF = dict(n_int=2048, n_bc=256, n_feat=512)
+WORKLOADS = {
+    "poisson5d": dict(
+        desc=("poisson5d: -Lap u = f, [0,1]^5, 32768 interior + 4096 boundary rows (weight 100), "
+              "4096 features sigma=3"),
+        rows=32768 + 4096, feat=4096, instances=4,
+        # the CPU oracle's bounded samples (same recipe, fewer rows and features); their
+        # times are scaled to the full workload by the QR work ratio m n^2
+        cpu_sample=dict(n_int=4096, n_bc=512, n_feat=1024),
+        ref_sample=dict(n_int=2048, n_bc=256, n_feat=512)),
+    "helmholtz2d": dict(
+        desc=("helmholtz2d: Lap u + k^2 u = f, k=4, [0,1]^2, 8192 interior + 1024 boundary rows "
+              "(weight 100), 2048 features sigma=8"),
+        rows=8192 + 1024, feat=2048, instances=8,
+        cpu_sample=None,                     # the full workload: one solve is about 20 s
+        ref_sample=dict(n_int=2048, n_bc=256, n_feat=512)),
+}
 
 
-def _scale_ratio(sample):
-    full = (8192 + 1024) * 2048 ** 2
-    return full / ((sample["n_int"] + sample["n_bc"]) * sample["n_feat"] ** 2)
+def _scale_ratio(name, sample):
+    """QR work (m n^2) of the full workload over that of the sample (1 for the full size)."""
+    if sample is None:
+        return 1.0
+    cfg = WORKLOADS[name]
+    return cfg["rows"] * cfg["feat"] ** 2 / ((sample["n_int"] + sample["n_bc"]) * sample["n_feat"] ** 2)
 
 
-def _oracle_solve_seconds(sample):
-    """One oracle solve of the sampled Helmholtz problem (assembly, rhs, QR, solve)."""
+def _oracle_solve_seconds(name, sample):
+    """One oracle solve of the workload (or of its sample): assembly, rhs, QR, solve."""
     import oracle
     from paper_2602_10541_gb300 import workloads as wl
-    w = wl.helmholtz2d(**sample)
+    w = getattr(wl, name)(**(sample or {}))
     t0 = time.perf_counter()
     A_int = oracle.assemble(w.x_int, w.alpha, w.coef, w.W, w.b, w.scale)
-    A_bc = oracle.assemble(w.x_bc, np.zeros((1, 2), np.int32), [1.0], w.W, w.b, w.scale,
+    A_bc = oracle.assemble(w.x_bc, np.zeros((1, w.d), np.int32), [1.0], w.W, w.b, w.scale,
                            row_weight=w.lam_bc)
     f = oracle.problem_source(w.problem, w.x_int, w.params)
     g = oracle.problem_exact(w.problem, w.x_bc, w.params)
     oracle.lstsq(np.vstack([A_int, A_bc]), np.concatenate([f, w.lam_bc * g]))
     return time.perf_counter() - t0
+
+
+def _sample_text(name, sample, seconds=None):
+    if sample is None:
+        return f"one oracle solve of the full {name} workload" + (f" ({seconds:.1f} s)" if seconds else "")
+    r = _scale_ratio(name, sample)
+    return (f"{name} with {sample['n_int']}+{sample['n_bc']} rows x {sample['n_feat']} features"
+            + (f" ({seconds:.1f} s)" if seconds else "")
+            + f"; time x{r:.0f}: extrapolated to the full workload by the QR work ratio m n^2")
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def _dist_env():
@@ -89,21 +126,22 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    ratio = _scale_ratio(SAMPLE_REF)
+    name = args.workload
+    sample = WORKLOADS[name]["ref_sample"]
+    ratio = _scale_ratio(name, sample)
     for _ in range(max(0, args.warmup)):
-        _oracle_solve_seconds(SAMPLE_REF)
-    ts = [_oracle_solve_seconds(SAMPLE_REF) for _ in range(args.steps)]
+        _oracle_solve_seconds(name, sample)
+    ts = [_oracle_solve_seconds(name, sample) for _ in range(args.steps)]
     total = sum(ts) * ratio
     value = args.steps / total
-    sample = (f"helmholtz2d with {SAMPLE_REF['n_int']}+{SAMPLE_REF['n_bc']} rows x "
-              f"{SAMPLE_REF['n_feat']} features per step, time x{ratio:.0f} (m n^2 ratio)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (plain C, 1 thread)"},
+            "config": {"workload": WORKLOADS[name]["desc"], "impl": "FP64 CPU oracle (plain C, 1 thread)"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "cpu": _cpu_model(),
+                             "sample": _sample_text(name, sample) + " (per step)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -172,14 +210,47 @@ def _src_sha(names):
 
 KERNEL_SRC = {"panel": "panel_row.cu", "trail_simt": "qr.cu",
               "trail_tc": ("tc_update.cu", "trail_z.cuh", "tc_common.cuh"),
+              "block_prep": ("tc_block.cu", "tc_common.cuh"), "block_y": ("tc_block.cu", "tc_common.cuh"),
+              "block_u": ("tc_block.cu", "tc_common.cuh"),
               "apply_q": "apply_q.cu", "trsv": "refine.cu", "residual": "qr.cu",
               "assemble_f32": "assemble.cu", "assemble_f64": "assemble.cu", "copy_in": "qr.cu"}
 
+BLK = 128          # outer block width of the blocked factorisation
+SPLIT_PRODUCTS = 6  # bf16 products per fp32 product in the three-part split
 
-def _algorithmic(kernel, m, n, m_aug, nb, nrhs, refine, nb_elem):
+
+def _blocked_flops(m_aug, n, nrhs):
+    """Algorithmic flops of the outer-block updates of one factorisation: the Y pass
+    Y = V^T [V | C] (2 m_p nbk n_ext per block, the block's own V^T V included) and the
+    update pass C -= V Z (2 m_p nbk n_tr per block)."""
+    y = u = 0.0
+    for k in range(0, n, BLK):
+        nbk = min(BLK, n - k)
+        mp, n_ext = m_aug - k, n + nrhs - k
+        n_tr = n_ext - nbk
+        if n_tr <= 0:
+            continue
+        y += 2.0 * mp * nbk * n_ext
+        u += 2.0 * mp * nbk * n_tr
+    return y, u
+
+
+def _inner_flops(m_aug, n, nb):
+    """Flops of the SIMT updates inside the outer blocks (4 m_p nb n_c per panel)."""
+    f = 0.0
+    for k in range(0, n, BLK):
+        nbk = min(BLK, n - k)
+        for kp in range(k, k + nbk, nb):
+            c = min(nb, n - kp)
+            f += 4.0 * (m_aug - kp) * c * (k + nbk - (kp + c))
+    return f
+
+
+def _algorithmic(kernel, m, n, m_aug, nb, nrhs, refine, nb_elem, blocked=True):
     """(unit, amount per solve) of the algorithmic cost of one kernel class in one
-    step; bytes for memory-bound kernels (each operand moved once), flops for
-    arithmetic-bound ones: each operand moved once, or 4 (m-k) nb n_c flops per trailing update."""
+    solve: flops for the contractions (the tensor-core classes in bf16 products: six per
+    fp32 product of the three-part split), bytes for memory-bound kernels (each operand
+    moved once)."""
     e = nb_elem
     panels = [(k, min(nb, n - k)) for k in range(0, n, nb)]
     if kernel == "assemble_f32":
@@ -188,13 +259,17 @@ def _algorithmic(kernel, m, n, m_aug, nb, nrhs, refine, nb_elem):
         return "bytes", 8.0 * m * n
     if kernel == "panel":                              # slice read + written once per panel
         return "bytes", sum(2.0 * (m_aug - k) * c * e for k, c in panels)
-    if kernel == "trail_simt":                         # Y = V^T C and C -= V Z: 4 (m-k) c nct
+    if kernel == "block_y":
+        return "flops", SPLIT_PRODUCTS * _blocked_flops(m_aug, n, nrhs)[0]
+    if kernel == "block_u":
+        return "flops", SPLIT_PRODUCTS * _blocked_flops(m_aug, n, nrhs)[1]
+    if kernel == "block_prep":                         # V images written (12 B per V entry)
+        return "bytes", sum(12.0 * (m_aug - k) * min(BLK, n - k) for k in range(0, n, BLK))
+    if kernel == "trail_simt":
+        if blocked:
+            return "flops", _inner_flops(m_aug, n, nb)
         return "flops", sum(4.0 * (m_aug - k) * c * (n + nrhs - (k + c)) for k, c in panels)
-    if kernel == "trail_tc":
-        # 128 TF32x3 products (384 tensor flops) per 12 bytes of C (read twice, written
-        # once) is below the tensor ridge (measured TF32 / HBM, about 140 flop per byte):
-        # HBM is the roof.  Bytes: C read twice and written once, V read once and written
-        # once as the operand image (hi, lo), per panel
+    if kernel == "trail_tc":                           # panel-by-panel TF32x3: C read twice, written once
         return "bytes", sum((12.0 * (n + nrhs - (k + c)) + 4.0 * c + 8.0 * 32) * (m_aug - k)
                             for k, c in panels)
     if kernel == "apply_q":                            # V read twice per application
@@ -461,29 +536,50 @@ def _secondary(fl, pl, wl, torch, ctx, dev, n_inverse):
     return out
 
 
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return p, "of measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "of fallback"
+
+
+def _traffic(cls, workload):
+    """ncu DRAM bytes per launch of a kernel class for the workload, if a capture of the
+    current sources is on record (profiles/ncu_traffic.json)."""
+    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(tpath):
+        return None, None
+    info = json.load(open(tpath)).get(f"{cls}@{workload}")
+    if not info or info.get("src_sha") != _src_sha(KERNEL_SRC.get(cls, "qr.cu")):
+        return None, None
+    return info.get("bytes_per_launch"), info.get("source")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="poisson5d", choices=sorted(WORKLOADS))
     ap.add_argument("--refine", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tensor-core", type=int, default=1, choices=[0, 1],
-                    help="1: trailing QR updates on tcgen05 (TF32x3), 0: SIMT FP32")
+    ap.add_argument("--tensor-core", type=int, default=1, choices=[0, 1, 2],
+                    help="1: two-level blocked QR with tcgen05 outer-block updates (three-part "
+                         "bf16 split); 2: panel-by-panel tcgen05 TF32x3; 0: SIMT FP32")
     ap.add_argument("--trsv-fp32", type=int, default=1, choices=[0, 1],
                     help="1: FP32 substitution in the triangular solves of classical refinement")
-    ap.add_argument("--no-extras", action="store_true", help="skip the Newton and inverse-problem timings")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other rows of the hot path")
     ap.add_argument("--inverse-instances", type=int, default=32)
-    ap.add_argument("--instances", type=int, default=8,
-                    help="independent full-size solves per step, each on its own stream")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="independent full-size solves per step, each on its own stream "
+                         "(0: the workload's default, 4 for poisson5d, 8 for helmholtz2d)")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
                     help="assemble the FP64 operator on a side stream during the factorisation")
     ap.add_argument("--lookahead", type=int, default=0, choices=[0, 1],
-                    help="1: factor the next panel on a second stream during the trailing update; "
-                         "0 (default here): with 8 solves in flight the other instances already "
-                         "fill the SMs beside each panel, and the split update costs more than "
-                         "it hides")
+                    help="panel-by-panel modes: 1 factors the next panel on a second stream")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -503,18 +599,21 @@ def main():
     dev = f"cuda:{local}"
     if not _build.up_to_date():
         _build.build()
+    name = args.workload
+    cfg = WORKLOADS[name]
+    make = getattr(wl, name)
     stream = torch.cuda.current_stream(local)
     # each rank solves its own instances (replicas: a solve does not shard); a step is
-    # args.instances independent full-size solves, one context and stream each
+    # B independent full-size solves, one context and stream each
     _, hi_prio = torch.cuda.Stream.priority_range()
-    B = max(1, args.instances)
+    B = args.instances if args.instances > 0 else cfg["instances"]
     ctxs, solvers = [], []
     for i in range(B):
         c = fl.Context(local, stream=torch.cuda.Stream(device=local, priority=hi_prio))
         fl.fastlsq_set_option(c, fl.OPT_TENSOR_CORE, args.tensor_core)
         fl.fastlsq_set_option(c, fl.OPT_TRSV_FP32, args.trsv_fp32)
         fl.fastlsq_set_option(c, fl.OPT_LOOKAHEAD, args.lookahead)
-        wi = wl.helmholtz2d(seed_offset=rank * B + i)
+        wi = make(seed_offset=rank * B + i)
         with torch.cuda.stream(c.stream):
             dpi = pl.upload(wi, dev)
             solvers.append(pl.LinearSolver(c, dpi, prec=fl.PREC_MIXED, max_refine=args.refine,
@@ -525,18 +624,22 @@ def main():
     dp, w = solver.dp, solver.dp.w
     batch = pl.ConcurrentSolves(solvers)
     m, n = w.n_rows, w.n_feat
+    m_aug = m + (n if w.mu > 0 else 0)
 
     for _ in range(args.warmup):
         batch.step(stream)
     torch.cuda.synchronize()
 
-    # which kernel class dominates (pre-pass with events on every class of instance 0)
+    # per-class device times of instance 0 (a pre-pass with events on every class)
     fl.fastlsq_profile_enable(ctx, None)
     for _ in range(2):
         batch.step(stream)
     prof_pre = fl.fastlsq_profile_read(ctx)
     dominant = max(prof_pre, key=lambda k: prof_pre[k][1])
-    fl.fastlsq_profile_enable(ctx, [dominant])     # only the dominant class inside the timed region
+    # inside the timed region, events on the tensor-core update classes only
+    tc_classes = ["block_y", "block_u"] if args.tensor_core == 1 else (
+        ["trail_tc"] if args.tensor_core == 2 else ["trail_simt"])
+    fl.fastlsq_profile_enable(ctx, tc_classes)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -565,63 +668,74 @@ def main():
     value, total_ms = _job_throughput(total_ms, args.steps, world, dev)
     value *= B
 
-    # roofline of the dominant kernel class (events recorded in the timed region)
-    dom_launches, dom_ms = prof[dominant]
-    elem = 4
     with torch.cuda.stream(ctx.stream):
         solver.solve(stats=True)
     solve_stats = solver.stats
     nb = solve_stats.nb
-    unit_kind, per_step = _algorithmic(dominant, m, n, m + (n if w.mu > 0 else 0), nb, 1,
-                                       args.refine, elem)
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    blocked = args.tensor_core == 1
+    peaks, peak_tag = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    if unit_kind == "flops" and dominant == "trail_simt":
-        # FP32 FMA pipe: SMs x 128 lanes x 2 flop x max SM clock
+
+    # roofline of the factorisation's trailing update (the contraction of Sec. 2.3's QR):
+    # algorithmic flops per launch over the event time of its launches in the timed region
+    units = 0.0
+    for cls in tc_classes:
+        units += _algorithmic(cls, m, n, m_aug, nb, 1, args.refine, 4, blocked)[1]
+    tc_launches = sum(prof[c][0] for c in tc_classes)
+    tc_ms = sum(prof[c][1] for c in tc_classes)
+    if args.tensor_core == 1:
+        bound, unit = "tensor", "TFLOP/s"
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
+        peak_src = f"MEASURED_PEAKS.json bf16_tflops_sustained ({peak_tag}): bf16 operands"
+        work_note = ("bf16 tensor flops: 6 products (three-part split) x 2 m_p nbk n per outer block, "
+                     "Y pass (n = columns right of the block plus the block's own) and update pass")
+    elif args.tensor_core == 2:
+        bound, unit = "tensor", "TFLOP/s"
+        peak = 0.5 * peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
+        peak_src = f"MEASURED_PEAKS.json bf16_tflops_sustained x 0.5 (nominal tf32 : bf16) ({peak_tag})"
+        units = sum(3 * 4.0 * (m_aug - k) * min(nb, n - k) * (n + 1 - (k + min(nb, n - k)))
+                    for k in range(0, n, nb))
+        work_note = "tf32 tensor flops: 3 products (TF32x3) x 4 m_p nb n_c per panel"
+    else:
         bound, unit = "alu", "TFLOP/s"
         peak = 2.0 * 128 * nsm * sm_mhz * 1e6 / 1e12
         peak_src = f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"
-    elif unit_kind == "flops":
-        # tcgen05 kind::tf32: measured bf16 dense peak x 1/2 (nominal TF32 : BF16 ratio)
-        bound, unit = "tensor", "TFLOP/s"
-        peak = peaks.get("bf16_tflops", 1900.0) * 0.5
-        peak_src = ("MEASURED_PEAKS.json bf16_tflops x 0.5 (of measured)" if peaks
-                    else "fallback 1900 TF/s bf16 x 0.5")
-    else:
-        bound, unit, peak = "hbm", "GB/s", hbm
-        peak_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"
-    scale_u = 1e12 if unit == "TFLOP/s" else 1e9
-    achieved = per_step * args.steps / (dom_ms / 1e3) / scale_u if dom_ms > 0 else 0.0
+        work_note = "FP32 flops: 4 m_p nb n_c per panel"
+    per_launch = units * args.steps / max(1, tc_launches)
+    achieved = units * args.steps / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else 0.0
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if os.path.exists(tpath):
-        tinfo = json.load(open(tpath)).get(f"{dominant}@lookahead{args.lookahead}")
-        # a capture counts only for the same sources and the same split of the update
-        # (with look-ahead the panel kernel updates the next panel's columns itself)
-        if (tinfo and tinfo.get("src_sha") == _src_sha(KERNEL_SRC.get(dominant, "qr.cu"))
-                and tinfo.get("lookahead") == args.lookahead):
-            traffic = tinfo.get("bytes_per_launch")
-    roofline = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak, "traffic": traffic,
-                "launches": dom_launches, "avg_launch_us": 1e3 * dom_ms / max(1, dom_launches),
-                "peak_source": peak_src,
+    tsrc = None
+    if args.tensor_core == 1:
+        ty, sy = _traffic("block_y", name)
+        tu, su = _traffic("block_u", name)
+        if ty is not None and tu is not None:
+            traffic = 0.5 * (ty + tu)
+            tsrc = f"{sy}; {su}"
+    roofline = {"kernel": "+".join(tc_classes), "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
+                "launches": tc_launches, "avg_launch_us": 1e3 * tc_ms / max(1, tc_launches),
+                "work_per_launch": per_launch, "work": work_note, "peak_source": peak_src,
+                "algorithmic_fp32_tflops": achieved / (SPLIT_PRODUCTS if args.tensor_core == 1 else
+                                                       (3 if args.tensor_core == 2 else 1)),
+                "dominant_class_of_step": dominant,
                 "concurrent_instances": B}     # each launch shares the GPU with B - 1 other solves
-    breakdown = {k: {"launches_per_step": v[0] / 2.0, "ms_per_step": v[1] / 2.0}
+    breakdown = {k: {"launches_per_solve": v[0] / 2.0, "ms_per_solve": v[1] / 2.0}
                  for k, v in prof_pre.items() if v[0]}
-    # the same roofline arithmetic for every class of the pre-pass (two steps), for context
     for kname, v in breakdown.items():
-        ukind, amount = _algorithmic(kname, m, n, m + (n if w.mu > 0 else 0), nb, 1, args.refine, elem)
-        if amount <= 0 or v["ms_per_step"] <= 0:
+        ukind, amount = _algorithmic(kname, m, n, m_aug, nb, 1, args.refine, 4, blocked)
+        if amount <= 0 or v["ms_per_solve"] <= 0:
             continue
         if ukind == "flops":
-            pk = 2.0 * 128 * nsm * sm_mhz * 1e6 / 1e12 if kname == "trail_simt" else peaks.get("bf16_tflops", 1900.0) * 0.5
-            v["roofline"] = {"achieved": amount / (v["ms_per_step"] / 1e3) / 1e12, "peak": pk, "unit": "TFLOP/s",
-                             "bound": "alu" if kname == "trail_simt" else "tensor"}
+            if kname in ("block_y", "block_u"):
+                pk, bd = peaks.get("bf16_tflops_sustained", 1700.0), "tensor"
+            else:
+                pk, bd = 2.0 * 128 * nsm * sm_mhz * 1e6 / 1e12, "alu"
+            v["roofline"] = {"achieved": amount / (v["ms_per_solve"] / 1e3) / 1e12, "peak": pk,
+                             "unit": "TFLOP/s", "bound": bd}
         else:
-            v["roofline"] = {"achieved": amount / (v["ms_per_step"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            v["roofline"] = {"achieved": amount / (v["ms_per_solve"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                              "bound": "hbm"}
         v["roofline"]["frac"] = v["roofline"]["achieved"] / v["roofline"]["peak"]
 
@@ -631,6 +745,7 @@ def main():
     s0 = ctx.stream
     fl.fastlsq_set_stream(ctx, stream)
     u_mixed = solver.u_test()
+    ue = solver.u_exact_test()
     s64 = pl.LinearSolver(ctx, dp, prec=fl.PREC_FP64)
     fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, 1)   # one solve alone: the library default
     torch.cuda.synchronize()
@@ -640,12 +755,22 @@ def main():
     fp64_ms = 1e3 * (time.perf_counter() - t64)
     fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, args.lookahead)
     u64 = s64.u_test()
-    ue = solver.u_exact_test()
     accuracy = {"rel_l2_vs_fp64_gpu": pl.rel_l2(u_mixed, u64), "rel_l2_vs_exact": pl.rel_l2(u_mixed, ue),
                 "fp64_gpu_rel_l2_vs_exact": pl.rel_l2(u64, ue), "fp64_gpu_ms_per_solve": fp64_ms,
                 "fp64_gpu_solves_per_s": 1e3 / fp64_ms,
                 "resid_norms": list(solve_stats.resid_norm[: args.refine + 1])}
     del s64
+    torch.cuda.empty_cache()
+
+    # one solve alone (instance 0, the library defaults), for the latency of a solve
+    torch.cuda.synchronize()
+    one = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        solver.step()
+        torch.cuda.synchronize()
+        one.append(time.perf_counter() - t0)
+    single = {"ms_per_solve": 1e3 * min(one), "solves_per_s": 1.0 / min(one)}
 
     # assembly alone (FP32 operator, both row blocks), Gentries/s
     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -660,9 +785,11 @@ def main():
         torch.cuda.synchronize()
         asm_ms += ea.elapsed_time(eb)
     asm_rate = args.steps * m * n / (asm_ms / 1e3)
+    sfu = nsm * 16 * sm_mhz * 1e6
     assembly = {"gentries_per_s": asm_rate / 1e9, "entries": m * n,
                 "hbm_write_gbs": 4 * asm_rate / 1e9, "hbm_frac": 4 * asm_rate / 1e9 / hbm,
-                "sfu_bound_gentries_per_s": None}
+                "sfu_bound_gentries_per_s": sfu / 1e9, "sfu_frac": asm_rate / sfu,
+                "sfu_bound_source": f"derived: {nsm} SMs x 16 sin/clk x {sm_mhz:.0f} MHz"}
 
     # end to end through the C ABI with host buffers: every instance's inputs from
     # pinned host memory, its solution back, each step
@@ -688,46 +815,95 @@ def main():
     fl.fastlsq_set_stream(ctx, stream)
     e2e = {"value": world * B * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": bi,
            "d2h_bytes_per_step": bo}
+    del batch, solvers, solver
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        ratio = _scale_ratio(SAMPLE_CPU)
-        t = _oracle_solve_seconds(SAMPLE_CPU)
-        cpu = {"value": 1.0 / (t * ratio), "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": (f"one oracle solve of helmholtz2d with {SAMPLE_CPU['n_int']}+"
-                          f"{SAMPLE_CPU['n_bc']} rows x {SAMPLE_CPU['n_feat']} features "
-                          f"({t:.1f} s), time x{ratio:.0f} (m n^2 ratio to the full workload)")}
+        sample = cfg["cpu_sample"]
+        t = _oracle_solve_seconds(name, sample)
+        cpu = {"value": 1.0 / (t * _scale_ratio(name, sample)), "unit": "solves/s", "cores": 1,
+               "kind": "oracle", "cpu": _cpu_model(), "nproc": os.cpu_count(),
+               "sample": _sample_text(name, sample, t)}
 
     extras = None
     if rank == 0 and not args.no_extras:
         # one solve, Newton run or instance at a time: look-ahead on (the library default)
         fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, 1)
         extras = _secondary(fl, pl, wl, torch, ctx, dev, args.inverse_instances)
+        if name != "helmholtz2d":
+            extras["helmholtz2d_concurrent"] = _helmholtz_row(fl, pl, wl, torch, dev, local, args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_rows": m, "n_feat": n,
-                           "precision": f"mixed: FP32 assembly and Householder QR, FP64 residual, "
-                                        f"{args.refine} refinement steps",
-                           "tensor_core_updates": bool(solve_stats.tensor_core),
-                           "panel_nb": nb, "lookahead": bool(args.lookahead), "l2": "flushed between steps (256 MiB write outside the step events)",
+                "config": {"workload": cfg["desc"], "n_rows": m, "n_feat": n,
+                           "precision": (f"mixed: FP32 assembly and Householder QR (outer-block updates on "
+                                         f"tcgen05, three-part bf16 split), FP64 residual, {args.refine} "
+                                         f"refinement steps"),
+                           "tensor_core_updates": int(solve_stats.tensor_core),
+                           "panel_nb": nb, "outer_block": BLK if blocked else None,
+                           "lookahead": bool(args.lookahead),
+                           "l2": "flushed between steps (256 MiB write outside the step events)",
                            "instances_per_step": B,
                            "concurrency": (f"{B} independent instances (seeds) of the workload per step, "
                                            "each on its own context and stream"),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-                "clocks": clk, "accuracy": accuracy, "assembly": assembly, "kernels": breakdown,
-                "other_rows": extras, "wall_s_timed": wall}
+                "clocks": clk, "accuracy": accuracy, "single_solve": single, "assembly": assembly,
+                "kernels": breakdown, "other_rows": extras, "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _helmholtz_row(fl, pl, wl, torch, dev, local, args):
+    """The 2-D Helmholtz configuration (9216 x 2048) as a row: 8 concurrent solves per
+    step, device-timed, and the MIXED solution against the FP64 GPU path."""
+    _, hi_prio = torch.cuda.Stream.priority_range()
+    ctxs, solvers = [], []
+    for i in range(8):
+        c = fl.Context(local, stream=torch.cuda.Stream(device=local, priority=hi_prio))
+        fl.fastlsq_set_option(c, fl.OPT_TENSOR_CORE, args.tensor_core)
+        fl.fastlsq_set_option(c, fl.OPT_LOOKAHEAD, 0)
+        with torch.cuda.stream(c.stream):
+            solvers.append(pl.LinearSolver(c, pl.upload(wl.helmholtz2d(seed_offset=i), dev),
+                                           prec=fl.PREC_MIXED, max_refine=args.refine))
+        ctxs.append(c)
+    batch = pl.ConcurrentSolves(solvers)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        batch.step(stream)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 10
+    torch.cuda.synchronize()
+    ea.record(stream)
+    for _ in range(steps):
+        batch.step(stream)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    ms = ea.elapsed_time(eb)
+    s0 = solvers[0]
+    torch.cuda.synchronize()
+    fl.fastlsq_set_stream(s0.ctx, stream)
+    um = s0.u_test()
+    s64 = pl.LinearSolver(s0.ctx, s0.dp, prec=fl.PREC_FP64)
+    s64.step()
+    u64 = s64.u_test()
+    ue = s0.u_exact_test()
+    out = {"solves_per_s": 8 * steps / (ms / 1e3), "instances_per_step": 8,
+           "rel_l2_vs_fp64_gpu": pl.rel_l2(um, u64), "rel_l2_vs_exact": pl.rel_l2(um, ue),
+           "workload": WORKLOADS["helmholtz2d"]["desc"]}
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.close()
+    return out
 
 
 if __name__ == "__main__":

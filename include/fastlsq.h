@@ -244,7 +244,9 @@ FASTLSQ_API int fastlsq_eval_adjoint(fastlsq_ctx *ctx, const double *x, int64_t 
 typedef struct {
     int32_t refine_steps;      /* refinement steps / CGLS iterations performed     */
     int32_t nb;                /* panel width used                                 */
-    int32_t tensor_core;       /* 1 if trailing updates ran on tcgen05              */
+    int32_t tensor_core;       /* trailing-update mode of the factor: 0 SIMT, 1 outer
+                                  blocks on tcgen05 (bf16 three-part split), 2 panel
+                                  by panel on tcgen05 (TF32x3); see FASTLSQ_OPT_TENSOR_CORE */
     int32_t status;            /* as the return value of the call                  */
     double resid_norm[65];     /* ||rhs - A beta|| (incl. sqrt(mu) rows) after the  */
                                /* first solve and after each refinement step (FP64) */
@@ -501,12 +503,20 @@ FASTLSQ_API int fastlsq_newton_continuation(fastlsq_ctx *ctx, const fastlsq_newt
 
 /* Context options for fastlsq_set_option. */
 typedef enum {
-    FASTLSQ_OPT_TENSOR_CORE = 0,  /* 1 (default): MIXED trailing updates on tcgen05 (TF32x3,
-                                      operands by TMA) for panel width 32 in factors refined
-                                      classically; factors refined by CGLS (preconditioners
-                                      of ill-conditioned systems) always use the SIMT FP32
-                                      update, whose products are 4x more accurate; 0: SIMT
-                                      FP32 everywhere */
+    FASTLSQ_OPT_TENSOR_CORE = 0,  /* trailing updates of the MIXED (FP32) factorisation.
+                                      1 (default): two-level blocking: outer blocks of 128
+                                      columns, each factored as panels of width 32 (16 for
+                                      panels taller than the register panels hold) with
+                                      SIMT FP32 updates inside the block, then one update
+                                      of every column right of the block on tcgen05 with
+                                      K = 128, operands split into three bf16 parts (six
+                                      products: FP32-level accuracy), FP32 accumulation;
+                                      used for factors refined classically and by CGLS.
+                                      2: panel by panel on tcgen05 with TF32x3 products
+                                      (2^-22 relative, operands by TMA) for panel width 32
+                                      in factors refined classically (CGLS-refined factors
+                                      then use the SIMT update).  0: SIMT FP32 panel by
+                                      panel everywhere. */
     FASTLSQ_OPT_REGISTER_PANEL = 1, /* 1 (default): FP32 panels of width 32 factor with the
                                       slice in registers where rows per warp <= 24;
                                       0: the shared-memory panel kernel everywhere */
@@ -554,6 +564,9 @@ typedef enum {
     FASTLSQ_K_NEWTON,          /* Newton pointwise kernels                        */
     FASTLSQ_K_ADJOINT,         /* adjoint contractions                            */
     FASTLSQ_K_KRYLOV,          /* Krylov refinement (FP64 products, scalars)      */
+    FASTLSQ_K_BLOCK_PREP,      /* outer-block update: operand images of V and Z   */
+    FASTLSQ_K_BLOCK_Y,         /* outer-block update: Y = V^T [V | C], tcgen05    */
+    FASTLSQ_K_BLOCK_U,         /* outer-block update: C -= V Z, tcgen05           */
     FASTLSQ_K_COUNT
 } fastlsq_kernel;
 

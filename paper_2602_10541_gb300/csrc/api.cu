@@ -287,7 +287,9 @@ extern "C" int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value)
 {
     if (!ctx) return FASTLSQ_ERR_INVALID;
     if (option == FASTLSQ_OPT_TENSOR_CORE) {
-        ctx->use_tensor_core = value ? 1 : 0;
+        if (value < FL_TC_SIMT || value > FL_TC_PANEL)
+            return fl_fail(ctx, FASTLSQ_ERR_INVALID, "tensor-core mode %d outside 0..2", value);
+        ctx->use_tensor_core = value;
         return 0;
     }
     if (option == FASTLSQ_OPT_REGISTER_PANEL) {
@@ -594,9 +596,15 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
     f->ld_refine = (prec == FASTLSQ_PREC_MIXED || A_refine) ? ld_refine : ldA;
     // TF32x3 products carry about 2^-22 relative per product, FP32 FMAs 2^-24: where the
     // factor preconditions CGLS (systems with kappa near 1 / eps32), the FP32 update keeps
-    // A R^{-1} well conditioned (measured on Sec. 4.4 instances: cond 2-11 vs 10-170)
-    f->tensor_core = (prec == FASTLSQ_PREC_MIXED && refine_mode == FASTLSQ_REFINE_CLASSICAL)
-                         ? ctx->use_tensor_core : 0;
+    // A R^{-1} well conditioned (measured on Sec. 4.4 instances: cond 2-11 vs 10-170), so
+    // the panel-by-panel TF32x3 mode serves classically refined factors only; the blocked
+    // mode's three-part bf16 products are FP32-accurate and serve both
+    f->tensor_core = 0;
+    if (prec == FASTLSQ_PREC_MIXED) {
+        if (ctx->use_tensor_core == FL_TC_BLOCKED) f->tensor_core = FL_TC_BLOCKED;
+        else if (ctx->use_tensor_core == FL_TC_PANEL && refine_mode == FASTLSQ_REFINE_CLASSICAL)
+            f->tensor_core = FL_TC_PANEL;
+    }
     int rc = 0;
     const int64_t npanels = fl_cdiv(n_feat, nb);
     f->F = fl_alloc(ctx, elem * f->ld * (n_feat + nrhs), &rc);

@@ -28,6 +28,11 @@ struct FlOncePerDevice {
     }
 };
 
+// Trailing-update modes of the FP32 factorisation (values of FASTLSQ_OPT_TENSOR_CORE).
+#define FL_TC_SIMT 0       // SIMT FP32, panel by panel
+#define FL_TC_BLOCKED 1    // outer blocks of 128 columns on tcgen05, three-part bf16 split
+#define FL_TC_PANEL 2      // panel by panel on tcgen05, TF32x3 split
+
 #define FL_MAX_D 8
 #define FL_MAX_TERMS 32
 #define FL_MAX_PP 8
@@ -64,6 +69,10 @@ enum fl_slot {
     FL_WS_COUNTERS,        // completion counters of the trailing-update column tiles
     FL_WS_VIMG,            // the panel's V as the tensor-core update's operand image
     FL_WS_WGRAD,           // row-chunk partial sums of the feature-weight gradient
+    FL_WS_BLK_VY,          // outer-block update: V^T operand image (per 64-row chunk)
+    FL_WS_BLK_VU,          // outer-block update: V operand image (per 128-row tile)
+    FL_WS_BLK_Y,           // outer-block update: Y = V^T [V | C] split partials
+    FL_WS_BLK_Z,           // outer-block update: Z operand image
     FL_WS_COUNT
 };
 
@@ -85,7 +94,7 @@ struct fastlsq_ctx {
     fl_buffer ws[FL_WS_COUNT];
     int *d_flag = nullptr;          // device error flag (int)
     void *d_grid_bar = nullptr;     // grid barrier state (count, generation) of this context
-    int use_tensor_core = 1;        // tcgen05 trailing updates for the MIXED path
+    int use_tensor_core = 1;        // MIXED trailing updates: FL_TC_SIMT, FL_TC_BLOCKED or FL_TC_PANEL
     int panel_reg = 1;              // register-resident FP32 panel (width 32) where it fits
     int row_panel = 1;              // of which the row layout (one or two rows per thread)
     int lookahead = 1;              // panel p+1 beside the rest of panel p's update (on aux_stream)

@@ -362,11 +362,18 @@ k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, 
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
 
+    // two-level sum: each chunk's 32 rows into a fresh partial, the partials into acc,
+    // so a split of many rows is not one long chain of roundings
     if (rs0 < rs1) load(rs0);
     for (int64_t r0 = rs0; r0 < rs1; r0 += TY_ROWS) {
         store();
         __syncthreads();
         if (r0 + TY_ROWS < rs1) load(r0 + TY_ROWS);          // next chunk in flight
+        T cacc[LPW][4];
+#pragma unroll
+        for (int a = 0; a < LPW; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cacc[a][b] = T(0);
 #pragma unroll 8
         for (int r = 0; r < TY_ROWS; ++r) {
             const V4 cv = *reinterpret_cast<const V4 *>(sC + r * CLD + 4 * lane);
@@ -375,12 +382,16 @@ k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, 
             for (int a = 0; a < LPW; ++a) vl[a] = sV[r * VLD + LPW * warp + a];
 #pragma unroll
             for (int a = 0; a < LPW; ++a) {
-                acc[a][0] += vl[a] * cv.x;
-                acc[a][1] += vl[a] * cv.y;
-                acc[a][2] += vl[a] * cv.z;
-                acc[a][3] += vl[a] * cv.w;
+                cacc[a][0] += vl[a] * cv.x;
+                cacc[a][1] += vl[a] * cv.y;
+                cacc[a][2] += vl[a] * cv.z;
+                cacc[a][3] += vl[a] * cv.w;
             }
         }
+#pragma unroll
+        for (int a = 0; a < LPW; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += cacc[a][b];
         __syncthreads();
     }
 #pragma unroll
@@ -783,9 +794,12 @@ static int launch_trailing(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_
     if (nct <= 0) return 0;
     const int64_t mp = m_aug - k;
     const int64_t ctiles = fl_cdiv(nct, TY_COLS);
-    // split the long row dimension so the grid covers the GPU about twice
+    // split the long row dimension so the grid covers the GPU about twice, with at least
+    // 1024 rows per split: the last CTA of a column tile adds the splits' partials one
+    // after another, so a narrow update (the columns inside an outer block) is not held
+    // up by hundreds of them
     int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(fl_cdiv(2 * ctx->num_sms, ctiles),
-                                                            fl_cdiv(mp, 256)));
+                                                            fl_cdiv(mp, 1024)));
     int64_t rows_per_split = fl_round_up(fl_cdiv(mp, nsplit), TY_ROWS);
     nsplit = fl_cdiv(mp, rows_per_split);
     T *Ypart = (T *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(T) * nsplit * NB * nct);
@@ -896,10 +910,56 @@ static int factor_t(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n
     return 0;
 }
 
+// Two-level blocked Householder QR of an FP32 factor: outer blocks of 128 columns,
+// each factored as inner panels of width NB (panel kernel, then the SIMT update of the
+// block's remaining columns, K = NB); the block's reflectors then update every column
+// right of the block at once on the tensor cores (fl_block_update_f32: K = 128, three-part
+// bf16 split).  The factor's storage (reflectors, tau, per-panel T) is the same as the
+// one-level schedule's, so every solve reads it unchanged.
+template <int NB>
+static int factor_blocked(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t m_aug, int64_t n, int nrhs,
+                          float *tau, float *Tall)
+{
+    constexpr int BLK = 128;
+    const int64_t ntot = n + nrhs;
+    const int64_t max_tiles = fl_cdiv(ntot, 32) + 8;
+    int *counters = (int *)fl_ws(ctx, FL_WS_COUNTERS, sizeof(int) * max_tiles);
+    if (!counters) return FASTLSQ_ERR_NOMEM;
+    cudaMemsetAsync(counters, 0, sizeof(int) * max_tiles, ctx->stream);
+    for (int64_t k = 0; k < n; k += BLK) {
+        const int nbk = (int)std::min<int64_t>(BLK, n - k);
+        for (int64_t kp = k; kp < k + nbk; kp += NB) {
+            const int ncols = (int)std::min<int64_t>(NB, n - kp);
+            float *Tblk = Tall + (kp / NB) * NB * NB;
+            FL_TRY((panel_any<float, NB>(ctx, F, ld, kp, m_aug, ncols, tau + kp, Tblk)));
+            const int64_t nin = k + nbk - (kp + ncols);
+            if (nin > 0) FL_TRY((launch_trailing<float, NB>(ctx, F, ld, kp, m_aug, ncols, nin, 0, Tblk, counters)));
+        }
+        if (ntot <= k + nbk) continue;
+        const int rc = fl_block_update_f32(ctx, F, ld, k, m_aug, nbk, ntot, NB, Tall + (k / NB) * NB * NB);
+        if (rc < 0) return rc;
+        if (rc == 1) {      // shape not taken: the block's panels update the columns one by one
+            for (int64_t kp = k; kp < k + nbk; kp += NB) {
+                const int ncols = (int)std::min<int64_t>(NB, n - kp);
+                FL_TRY((launch_trailing<float, NB>(ctx, F, ld, kp, m_aug, ncols, ntot - (k + nbk),
+                                                   (k + nbk) - (kp + ncols), Tall + (kp / NB) * NB * NB,
+                                                   counters)));
+            }
+        }
+    }
+    return 0;
+}
+
 template <typename T>
 int fl_factor(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n, int nrhs, int nb,
               T *tau, T *Tall, int use_tc)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (use_tc == FL_TC_BLOCKED) {
+            if (nb == 32) return factor_blocked<32>(ctx, F, ld, m_aug, n, nrhs, tau, Tall);
+            if (nb == 16) return factor_blocked<16>(ctx, F, ld, m_aug, n, nrhs, tau, Tall);
+        }
+    }
     switch (nb) {
     case 32: return factor_t<T, 32>(ctx, F, ld, m_aug, n, nrhs, tau, Tall, use_tc);
     case 16: return factor_t<T, 16>(ctx, F, ld, m_aug, n, nrhs, tau, Tall, use_tc);

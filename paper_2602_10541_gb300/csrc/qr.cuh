@@ -52,6 +52,13 @@ int fl_panel_reg_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t 
 int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
                        int nb, int64_t nct, int64_t coff, int64_t ntot, const float *Tblk, int *counters);
 
+// Outer-block trailing update on the tensor cores (three-part bf16 split), tc_block.cu:
+// C <- H^T C for the block of nbk <= 128 columns at column k (inner panels of width nb,
+// T factors from Tb on), C = F's columns k + nbk .. ntot.  Returns 1 when the shape is
+// not taken (unaligned factor).
+int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int nbk,
+                        int64_t ntot, int nb, const float *Tb);
+
 // Krylov refinement with the factor's R as preconditioner (refine.cu)
 int fl_refine_cgls(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs64, double *beta64,
                    int max_iter, double tol, double *norms_dev);

@@ -1,0 +1,778 @@
+// Outer-block trailing update of the two-level blocked Householder QR on the tcgen05
+// tensor cores (Sec. 2.3 "via QR"), in a three-part bf16 split with FP32 accumulation:
+//
+//   x = x1 + x2 + x3,  x1 = bf16(x), x2 = bf16(x - x1), x3 = x - x1 - x2 (exact in bf16
+//   for every normal fp32 x: 8 + 8 + 8 significand bits cover fp32's 24), and
+//   a*b ~ a1 b1 + (a1 b2 + a2 b1 + a1 b3 + a3 b1 + a2 b2);
+//
+// the dropped terms (a2 b3, a3 b2, a3 b3) are below 2^-25 |ab|, so the products carry
+// FP32-level accuracy (the TF32x3 split of the per-panel update carries 2^-22).  The
+// tensor core sums at most 64 rows (the Y pass) or 64 block columns (the update pass,
+// with the leading product a1 b1 and the five small ones in separate accumulators)
+// before the sums continue in FP32 registers with round-to-nearest adds.  Six bf16
+// products cost what three tf32 ones do (bf16 runs at twice the tf32 rate).
+//
+// For an outer block of nbk <= 128 columns at column k, already factored as inner
+// panels of width NB (their reflectors V in F below the diagonal, their NB x NB
+// compact-WY factors T_q in the factor's T storage), the trailing columns C (the rest
+// of F, right-hand sides included) get C <- H^T C, H = H_0 H_1 ... H_{nq-1}:
+//   k_bimg : V of the block written once as two bf16 operand images (three parts
+//            each, K-major, 128-byte swizzle): VY (rows of V^T, K = factor rows, per
+//            64-row chunk) for the Y pass and VU (rows of V, K = block columns, per
+//            128-row tile) for the update pass;
+//   k_by   : Y = V^T [V | C] over split row ranges (MMA M = 128 block columns, N = 128
+//            columns, K = 64 rows per stage); the columns of C are loaded from F by
+//            converter warps (coalesced float4 along the rows), split in registers and
+//            stored in the operand layout; the products of each 64-row chunk accumulate
+//            in a fresh TMEM accumulator that the converter warps add into an FP32
+//            total (round-to-nearest) two chunks behind the MMAs; the V^T V
+//            block (Gram matrix) comes out of the same pass from the block's own columns
+//            (unit lower trapezoid applied); k_bsum adds the split partials in order;
+//   k_bz   : Z = the block-triangular T^T applied to Y, inner panel by inner panel:
+//            Z_q = T_q^T (Y_q - sum_{p<q} (V_p^T V_q)^T Z_p)  (the compact-WY product of
+//            the inner panels), written as the update's bf16 operand image;
+//   k_bu   : C -= V Z (M = 128 rows, N = 64 columns, K = 128), persistent CTAs over
+//            (row tile, column tile) units with the VU tile resident, Z tiles in a ring
+//            of two and two TMEM accumulator buffers, so the epilogue (C read, C - D
+//            written, coalesced along the rows) overlaps the next tile's MMAs.
+// Every mbarrier wait is bounded: on timeout the kernel raises the device flag, waits
+// (bounded) for its copies and MMAs in flight, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "qr.cuh"
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int BK = 128;                 // outer block width (MMA M of the Y pass, K of the update)
+constexpr int BY_KC = 64;               // factor rows per Y-pass stage (128 bytes of bf16)
+constexpr int BY_N = 128;               // columns per Y-pass CTA
+constexpr int BU_R = 128;               // rows per update tile
+constexpr int BU_N = 64;                // columns per update tile
+constexpr uint32_t PART128 = 128u * 128u;         // one part of a 128-row operand tile (bytes)
+constexpr uint32_t ZPART = BU_N * 128u;            // one part of a 64-row operand tile
+constexpr uint32_t VY_CHUNK = 3u * PART128;        // VY image of one 64-row chunk
+constexpr uint32_t VU_TILE = 6u * PART128;         // VU image of one 128-row tile (2 K halves)
+constexpr uint32_t Z_TILE = 6u * ZPART;            // Z image of one 64-column tile
+constexpr long long BT_SPIN = 2000000000ll;        // SM cycles (about a second) before a wait gives up
+
+// 10 warps: three share an SM sub-partition's 16K registers, so at most 168 a thread
+constexpr int BY_THREADS = 320;         // warp 0: A loads, warp 1: MMA, warps 2..9: converters, epilogue
+constexpr int BY_CONV = 8;
+constexpr uint32_t BY_STAGE = 2u * VY_CHUNK;       // A parts then B parts
+constexpr size_t BY_SMEM = 2 * BY_STAGE + 1024;
+constexpr int BU_THREADS = 320;         // warp 0: loads, warp 1: MMA, warps 2..9: epilogue
+constexpr int BU_EPI = 8;
+constexpr size_t BU_SMEM = VU_TILE + 2 * Z_TILE + 1024;
+constexpr int BI_LD = 129;              // padded row of the k_bimg staging tile
+constexpr size_t BI_SMEM = sizeof(float) * 128 * BI_LD;
+
+__device__ __forceinline__ unsigned char *bt_align1024(unsigned char *p)
+{
+    const uint32_t a = tc::smem_addr(p);
+    return p + ((1024u - (a & 1023u)) & 1023u);
+}
+
+__device__ __forceinline__ void bt_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                 :: "r"(tc::smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bt_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 :: "r"(tc::smem_addr(dst)), "l"(src), "r"(bytes), "r"(tc::smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bt_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(tc::smem_addr(bar)) : "memory");
+}
+
+// Operand tiles are K-major with 128-byte rows (64 bf16 along K) in the 128-byte
+// swizzle: element (row, kk) sits at row * 128 + (((kk / 8) ^ (row % 8)) * 16) + 2 (kk % 8).
+// three-part bf16 split of one fp32 value
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c)
+{
+    a = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(a);
+    b = __float2bfloat16_rn(r1);
+    c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// 4 consecutive K elements -> three parts of 8 bytes each
+__device__ __forceinline__ void split4(float4 v, uint2 (&p)[3])
+{
+    __nv_bfloat16 a[4], b[4], c[4];
+    split3(v.x, a[0], b[0], c[0]);
+    split3(v.y, a[1], b[1], c[1]);
+    split3(v.z, a[2], b[2], c[2]);
+    split3(v.w, a[3], b[3], c[3]);
+    p[0] = make_uint2(pack2(a[0], a[1]), pack2(a[2], a[3]));
+    p[1] = make_uint2(pack2(b[0], b[1]), pack2(b[2], b[3]));
+    p[2] = make_uint2(pack2(c[0], c[1]), pack2(c[2], c[3]));
+}
+
+// 8 consecutive K elements -> three parts of 16 bytes each
+__device__ __forceinline__ void split8(const float (&v)[8], uint4 (&p)[3])
+{
+    __nv_bfloat16 a[8], b[8], c[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) split3(v[e], a[e], b[e], c[e]);
+    p[0] = make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]), pack2(a[6], a[7]));
+    p[1] = make_uint4(pack2(b[0], b[1]), pack2(b[2], b[3]), pack2(b[4], b[5]), pack2(b[6], b[7]));
+    p[2] = make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), pack2(c[6], c[7]));
+}
+
+// V(i, l) of the block: unit lower trapezoid, zero past the block's nbk columns
+__device__ __forceinline__ float v_mask(float raw, int64_t i, int l, int nbk)
+{
+    if (l >= nbk || i < l) return 0.f;
+    return (i == l) ? 1.f : raw;
+}
+
+// ---------------------------------------------------------------------------
+// k_bimg: one CTA per 128-row tile t of the block's rows (panel-local rows
+// 128 t .. 128 t + 127).  The tile of V (128 rows x 128 columns) is staged in shared
+// memory, then written as the VU tile (row-major operand, K = block column) and as
+// the VY chunks 2t and 2t + 1 (column-major operand, K = row).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_bimg(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, int64_t nch,
+       unsigned char *__restrict__ VY, unsigned char *__restrict__ VU)
+{
+    extern __shared__ float sx[];          // sx[l * BI_LD + r]
+    const int64_t t = blockIdx.x;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < 128 * 32; idx += 256) {
+        const int l = idx >> 5, q4 = idx & 31;
+        const int64_t i = t * 128 + 4 * q4;                 // panel-local row of the quad
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (l < nbk && i < mp && k + i < ld) v = *reinterpret_cast<const float4 *>(F + (k + i) + (k + l) * ld);
+        float *d = sx + l * BI_LD + 4 * q4;
+        d[0] = (i + 0 < mp) ? v_mask(v.x, i + 0, l, nbk) : 0.f;
+        d[1] = (i + 1 < mp) ? v_mask(v.y, i + 1, l, nbk) : 0.f;
+        d[2] = (i + 2 < mp) ? v_mask(v.z, i + 2, l, nbk) : 0.f;
+        d[3] = (i + 3 < mp) ? v_mask(v.w, i + 3, l, nbk) : 0.f;
+    }
+    __syncthreads();
+    // VU: row r, 16 chunks of 8 block columns (two K halves of 8 chunks)
+    unsigned char *vu = VU + t * VU_TILE;
+    for (int idx = tid; idx < 128 * 16; idx += 256) {
+        const int r = idx >> 4, c16 = idx & 15, h = c16 >> 3, cc = c16 & 7;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = sx[(8 * c16 + e) * BI_LD + r];
+        uint4 p[3];
+        split8(v, p);
+        const uint32_t off = (uint32_t)r * 128u + (((uint32_t)cc ^ ((uint32_t)r & 7u)) << 4);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            *reinterpret_cast<uint4 *>(vu + (uint32_t)(h * 3 + q) * PART128 + off) = p[q];
+    }
+    // VY: chunks 2t, 2t + 1; row l of the chunk, 8 chunks of 8 factor rows
+    for (int qq = 0; qq < 2; ++qq) {
+        const int64_t q = 2 * t + qq;
+        if (q >= nch) break;
+        unsigned char *vy = VY + q * VY_CHUNK;
+        for (int idx = tid; idx < 128 * 8; idx += 256) {
+            const int l = idx >> 3, c8 = idx & 7;
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = sx[l * BI_LD + 64 * qq + 8 * c8 + e];
+            uint4 p[3];
+            split8(v, p);
+            const uint32_t off = (uint32_t)l * 128u + (((uint32_t)c8 ^ ((uint32_t)l & 7u)) << 4);
+#pragma unroll
+            for (int pp = 0; pp < 3; ++pp) *reinterpret_cast<uint4 *>(vy + (uint32_t)pp * PART128 + off) = p[pp];
+        }
+    }
+}
+// ---------------------------------------------------------------------------
+// k_by: Ypart[s][e][l] = sum over the split's rows i of V(i, l) X(i, e), X = F's
+// columns k + e (e < nbk: the block's own V, masked; e >= nbk: the trailing columns).
+// CTA (j, s): columns e in [128 j, 128 j + 128), the 64-row chunks s, s + S, ...
+// Roles: warp 0 bulk-loads the VY chunk (A operand, three parts), warps 2..9 load the
+// X chunk from F one chunk ahead, split it and store the three B parts, warp 1 issues
+// the 24 MMAs of the chunk and commits them to the stage's "empty" barrier and to the
+// chunk's accumulator.  Each chunk's six products go to a fresh TMEM accumulator (three
+// buffers in turn); warps 2..9 add a finished accumulator into a running FP32 total
+// kept in TMEM (tcgen05.ld, round-to-nearest add, tcgen05.st) two chunks behind the
+// MMAs, so the long sum over the split's rows is taken with round-to-nearest adds while
+// the tensor core sums 64 rows at a time, and the adds stay off the MMAs' path.
+// ---------------------------------------------------------------------------
+constexpr int BY_NBUF = 3;             // chunk accumulators in TMEM (plus the total)
+
+__global__ void __launch_bounds__(BY_THREADS, 1)
+k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, int64_t n_ext,
+     const unsigned char *__restrict__ VY, int64_t nch, float *__restrict__ Ypart, int *flag)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = bt_align1024(smem_raw);
+    __shared__ uint64_t fullA[2], fullB[2], empty[2], accf[BY_NBUF], acce[BY_NBUF];
+    __shared__ int s_last_load[2], s_last_commit;
+    __shared__ volatile int s_fail;
+    __shared__ uint32_t tmem_slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ebase = (int64_t)blockIdx.x * BY_N;
+    const int64_t S = gridDim.y;
+    const int nloc = (int)fl_max64(0, fl_cdiv_dev(nch - (int64_t)blockIdx.y, S));
+    auto chunk = [&](int ch) { return (int64_t)blockIdx.y + (int64_t)ch * S; };
+
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&fullA[s], 1);
+            tc::mbar_init(&fullB[s], BY_CONV);
+            tc::mbar_init(&empty[s], 1);
+            s_last_load[s] = -1;
+        }
+        for (int b = 0; b < BY_NBUF; ++b) {
+            tc::mbar_init(&accf[b], 1);
+            tc::mbar_init(&acce[b], BY_CONV);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_last_commit = -1;
+        s_fail = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    // TMEM columns: [128 b, 128 b + 128) the chunk accumulator b, [384, 512) the total
+    const uint32_t ttotal = tmem + BY_NBUF * BY_N;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int ch = 0; ch < nloc; ++ch) {
+                const int s = ch & 1;
+                if (ch >= 2 && !tc::mbar_wait(&empty[s], (uint32_t)((ch - 2) >> 1) & 1u, BT_SPIN)) {
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                bt_expect_tx(&fullA[s], VY_CHUNK);
+                bt_bulk_load(base + s * BY_STAGE, VY + chunk(ch) * VY_CHUNK, VY_CHUNK, &fullA[s]);
+                s_last_load[s] = ch;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16(BK, BY_N);
+            for (int ch = 0; ch < nloc; ++ch) {
+                const int s = ch & 1, b = ch % BY_NBUF;
+                if (!tc::mbar_wait(&fullA[s], (uint32_t)(ch >> 1) & 1u, BT_SPIN) ||
+                    !tc::mbar_wait(&fullB[s], (uint32_t)(ch >> 1) & 1u, BT_SPIN) ||
+                    (ch >= BY_NBUF &&
+                     !tc::mbar_wait(&acce[b], (uint32_t)((ch - BY_NBUF) / BY_NBUF) & 1u, BT_SPIN))) {
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                tc::fence_after_sync();
+                const unsigned char *A = base + s * BY_STAGE, *B = A + VY_CHUNK;
+                const uint32_t d = tmem + (uint32_t)(BY_N * b);
+                uint64_t dA[3], dB[3];
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    dA[p] = tc::smem_desc_sw128(A + p * PART128);
+                    dB[p] = tc::smem_desc_sw128(B + p * PART128);
+                }
+                // the small products first, the leading one last
+#pragma unroll
+                for (int ks = 0; ks < BY_KC / 16; ++ks) {
+                    const uint64_t o = (uint64_t)(ks * 32) >> 4;       // 16 bf16 = 32 bytes along K
+                    tc::mma_bf16(d, dA[0] + o, dB[1] + o, idesc, ks > 0 ? 1u : 0u);
+                    tc::mma_bf16(d, dA[1] + o, dB[0] + o, idesc, 1u);
+                    tc::mma_bf16(d, dA[0] + o, dB[2] + o, idesc, 1u);
+                    tc::mma_bf16(d, dA[2] + o, dB[0] + o, idesc, 1u);
+                    tc::mma_bf16(d, dA[1] + o, dB[1] + o, idesc, 1u);
+                    tc::mma_bf16(d, dA[0] + o, dB[0] + o, idesc, 1u);
+                }
+                tc::mma_commit(&empty[s]);
+                tc::mma_commit(&accf[b]);
+                s_last_commit = ch;
+            }
+        }
+    } else {
+        const int ct = threadIdx.x - 64;                       // 0 .. 255
+        // D: TMEM lane = block column l, column = e.  Warp w adds its lane quarter
+        // (w mod 4) and half (w - 2) / 4 of the 128 columns into the total
+        const int qd = warp & 3, hf = (warp - 2) >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
+        float4 x[8];
+        auto load = [&](int ch) {
+            const int64_t r0 = chunk(ch) * BY_KC;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = ct + 256 * u, cc = q >> 4, quad = q & 15;
+                const int64_t i = r0 + 4 * quad;               // panel-local row
+                const int64_t e = ebase + cc;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e < n_ext && i < mp && k + i < ld) v = *reinterpret_cast<const float4 *>(F + (k + i) + (k + e) * ld);
+                if (e < nbk) {
+                    v.x = (i + 0 < mp) ? v_mask(v.x, i + 0, (int)e, nbk) : 0.f;
+                    v.y = (i + 1 < mp) ? v_mask(v.y, i + 1, (int)e, nbk) : 0.f;
+                    v.z = (i + 2 < mp) ? v_mask(v.z, i + 2, (int)e, nbk) : 0.f;
+                    v.w = (i + 3 < mp) ? v_mask(v.w, i + 3, (int)e, nbk) : 0.f;
+                }
+                x[u] = v;
+            }
+        };
+        // total += accumulator of chunk c (the first chunk's is copied)
+        auto drain = [&](int c) -> bool {
+            const int b = c % BY_NBUF;
+            if (!tc::mbar_wait(&accf[b], (uint32_t)(c / BY_NBUF) & 1u, BT_SPIN)) return false;
+            tc::fence_after_sync();
+#pragma unroll
+            for (int rd = 0; rd < 4; ++rd) {
+                uint32_t v0[16], t0[16];
+                const uint32_t col = (uint32_t)(64 * hf + 16 * rd);
+                tc::tmem_ld16_nw(tmem + lane_base + (uint32_t)(BY_N * b) + col, v0);
+                if (c > 0) tc::tmem_ld16_nw(ttotal + lane_base + col, t0);
+                tc::tmem_wait_ld();
+                float a0[16];
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj)
+                    a0[jj] = (c > 0) ? __uint_as_float(t0[jj]) + __uint_as_float(v0[jj]) : __uint_as_float(v0[jj]);
+                tc::tmem_st16(ttotal + lane_base + col, a0);
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) bt_arrive(&acce[b]);
+            return true;
+        };
+        if (nloc > 0) load(0);
+        for (int ch = 0; ch < nloc; ++ch) {
+            const int s = ch & 1;
+            if (ch >= 2 && !tc::mbar_wait(&empty[s], (uint32_t)((ch - 2) >> 1) & 1u, BT_SPIN)) {
+                s_fail = 1;
+                break;
+            }
+            if (s_fail) break;
+            unsigned char *B = base + s * BY_STAGE + VY_CHUNK;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = ct + 256 * u, cc = q >> 4, quad = q & 15;
+                uint2 p[3];
+                split4(x[u], p);
+                const uint32_t off = (uint32_t)cc * 128u + ((((uint32_t)quad >> 1) ^ ((uint32_t)cc & 7u)) << 4) +
+                                     (((uint32_t)quad & 1u) << 3);
+#pragma unroll
+                for (int pp = 0; pp < 3; ++pp) *reinterpret_cast<uint2 *>(B + (uint32_t)pp * PART128 + off) = p[pp];
+            }
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) bt_arrive(&fullB[s]);
+            if (ch + 1 < nloc) load(ch + 1);
+            if (ch >= 2 && !drain(ch - 2)) {
+                s_fail = 1;
+                break;
+            }
+        }
+        for (int c = nloc - 2; c < nloc && !s_fail; ++c)
+            if (c >= 0 && !drain(c)) s_fail = 1;
+        __syncwarp();
+        if (!s_fail) {
+            const int l = 32 * qd + lane;
+#pragma unroll
+            for (int rd = 0; rd < 4; ++rd) {
+                float t[16];
+                const uint32_t col = (uint32_t)(64 * hf + 16 * rd);
+                if (nloc > 0) tc::tmem_ld16(ttotal + lane_base + col, t);
+                else
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) t[jj] = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    const int64_t e = ebase + col + jj;
+                    if (e < n_ext) Ypart[((int64_t)blockIdx.y * n_ext + e) * BK + l] = t[jj];
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (s_fail) {
+        if (threadIdx.x == 0) {
+            atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
+            for (int s = 0; s < 2; ++s)
+                if (s_last_load[s] >= 0) tc::mbar_wait(&fullA[s], (uint32_t)(s_last_load[s] >> 1) & 1u, BT_SPIN);
+            const int lc = s_last_commit;
+            if (lc >= 0) tc::mbar_wait(&accf[lc % BY_NBUF], (uint32_t)(lc / BY_NBUF) & 1u, BT_SPIN);
+        }
+        __syncthreads();
+    }
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------
+// k_bsum: Ysum[e][l] = sum over the splits s (in split order) of Ypart[s][e][l]; one
+// warp per column e, four block columns l per lane.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_bsum(const float *__restrict__ Ypart, int S, int64_t n_ext, float *__restrict__ Ysum)
+{
+    const int64_t e = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= n_ext) return;
+    const float4 *src = reinterpret_cast<const float4 *>(Ypart + e * BK) + lane;
+    const int64_t stride = n_ext * (BK / 4);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int s = 0;
+    for (; s + 4 <= S; s += 4) {
+        const float4 a0 = __ldcg(src + (int64_t)s * stride), a1 = __ldcg(src + (int64_t)(s + 1) * stride);
+        const float4 a2 = __ldcg(src + (int64_t)(s + 2) * stride), a3 = __ldcg(src + (int64_t)(s + 3) * stride);
+        acc.x = (((acc.x + a0.x) + a1.x) + a2.x) + a3.x;
+        acc.y = (((acc.y + a0.y) + a1.y) + a2.y) + a3.y;
+        acc.z = (((acc.z + a0.z) + a1.z) + a2.z) + a3.z;
+        acc.w = (((acc.w + a0.w) + a1.w) + a2.w) + a3.w;
+    }
+    for (; s < S; ++s) {
+        const float4 a = __ldcg(src + (int64_t)s * stride);
+        acc.x += a.x;
+        acc.y += a.y;
+        acc.z += a.z;
+        acc.w += a.w;
+    }
+    reinterpret_cast<float4 *>(Ysum + e * BK)[lane] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// k_bz: one CTA per 64 trailing columns.  Y (block columns x 64) and the Gram matrix
+// G = V^T V come from Ysum; then, inner panel by inner panel, W_q = Y_q - sum_{p<q}
+// (V_p^T V_q)^T Z_p and Z_q = T_q^T W_q; Z is written as the update's B-operand image
+// (64 rows = columns, K = block column, three parts).
+// ---------------------------------------------------------------------------
+template <int NB>
+__global__ void __launch_bounds__(256)
+k_bz(const float *__restrict__ Ysum, int64_t n_ext, int nbk, const float *__restrict__ Tb,
+     unsigned char *__restrict__ Zimg)
+{
+    extern __shared__ float smz[];
+    float *sG = smz;                        // sG[e * 129 + l] = (V^T V)(l, e)
+    float *sY = sG + 128 * 129;             // sY[l * 65 + c]: Y, then Z
+    float *sW = sY + 128 * 65;              // sW[l * 65 + c]
+    float *sT = sW + 128 * 65;              // T_q(a, b) at q NB NB + a + b NB
+    const int tid = threadIdx.x;
+    const int64_t n_tr = n_ext - nbk;
+    const int64_t cbase = (int64_t)blockIdx.x * BU_N;
+    const int nq = (nbk + NB - 1) / NB;
+    for (int idx = tid; idx < 128 * 128; idx += 256) {
+        const int e = idx >> 7, l = idx & 127;
+        sG[e * 129 + l] = (e < nbk && l < e) ? __ldcg(Ysum + (int64_t)e * BK + l) : 0.f;
+    }
+    for (int idx = tid; idx < 128 * BU_N; idx += 256) {
+        const int c = idx >> 7, l = idx & 127;
+        const int64_t cg = cbase + c;
+        sY[l * 65 + c] = (cg < n_tr && l < nbk) ? __ldcg(Ysum + (nbk + cg) * BK + l) : 0.f;
+    }
+    for (int idx = tid; idx < nq * NB * NB; idx += 256) sT[idx] = Tb[idx];
+    __syncthreads();
+    const int c = tid & 63, g = tid >> 6;
+    for (int q = 0; q < nq; ++q) {
+        const int q0 = q * NB;
+#pragma unroll
+        for (int u = 0; u < NB / 4; ++u) {
+            const int lp = q0 + g + 4 * u;
+            float w = sY[lp * 65 + c];
+            for (int l2 = 0; l2 < q0; ++l2) w -= sG[lp * 129 + l2] * sY[l2 * 65 + c];
+            sW[lp * 65 + c] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < NB / 4; ++u) {
+            const int b = g + 4 * u, l = q0 + b;
+            float z = 0.f;
+            for (int a = 0; a <= b; ++a) z += sT[q * NB * NB + a + b * NB] * sW[(q0 + a) * 65 + c];
+            sY[l * 65 + c] = z;
+        }
+        __syncthreads();
+    }
+    unsigned char *zi = Zimg + (int64_t)blockIdx.x * Z_TILE;
+    for (int idx = tid; idx < BU_N * 16; idx += 256) {
+        const int cc = idx >> 4, c16 = idx & 15, h = c16 >> 3, ch = c16 & 7;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int l = 8 * c16 + e;
+            v[e] = (l < nq * NB) ? sY[l * 65 + cc] : 0.f;
+        }
+        uint4 p[3];
+        split8(v, p);
+        const uint32_t off = (uint32_t)cc * 128u + (((uint32_t)ch ^ ((uint32_t)cc & 7u)) << 4);
+#pragma unroll
+        for (int pp = 0; pp < 3; ++pp) *reinterpret_cast<uint4 *>(zi + (uint32_t)(h * 3 + pp) * ZPART + off) = p[pp];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_bu: C(i, c) -= sum_l V(i, l) Z(l, c) for the trailing columns, rows k.. of F.
+// Units (row tile r, column tile j) in row-tile-major order; CTA b takes a contiguous
+// range.  Warp 0 loads the VU tile (when r changes) and the Z tiles (ring of two),
+// warp 1 issues the 48 MMAs of a unit into one of two TMEM buffers (the two K halves
+// and the leading and small products in four accumulators, summed in the epilogue),
+// warps 2..9 (two per lane quarter, 32 columns each) read D, free the buffer, load
+// their 32 elements of C, then store C - D.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(BU_THREADS, 1)
+k_bu(float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, int64_t n_ext,
+     const unsigned char *__restrict__ VU, const unsigned char *__restrict__ Zimg, int64_t n_ct, int64_t n_units,
+     int *flag)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = bt_align1024(smem_raw);
+    unsigned char *VUs = base;
+    __shared__ uint64_t vu_full, vu_empty, z_full[2], z_empty[2], acc_full[2], acc_empty[2];
+    __shared__ int s_vu_loads, s_last_z[2], s_last_commit;
+    __shared__ volatile int s_fail;
+    __shared__ uint32_t tmem_slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t u0 = (int64_t)blockIdx.x * n_units / gridDim.x;
+    const int64_t u1 = ((int64_t)blockIdx.x + 1) * n_units / gridDim.x;
+    const int nloc = (int)(u1 - u0);
+    const int64_t n_tr = n_ext - nbk;
+
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&vu_full, 1);
+        tc::mbar_init(&vu_empty, 1);
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&z_full[s], 1);
+            tc::mbar_init(&z_empty[s], 1);
+            tc::mbar_init(&acc_full[s], 1);
+            tc::mbar_init(&acc_empty[s], BU_EPI);
+            s_last_z[s] = -1;
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_vu_loads = 0;
+        s_last_commit = -1;
+        s_fail = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int64_t prev_r = -1;
+            int loads = 0;
+            for (int lu = 0; lu < nloc; ++lu) {
+                const int64_t u = u0 + lu, r = u / n_ct, j = u % n_ct;
+                if (r != prev_r) {
+                    if (loads > 0 && !tc::mbar_wait(&vu_empty, (uint32_t)(loads - 1) & 1u, BT_SPIN)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    if (s_fail) break;
+                    bt_expect_tx(&vu_full, VU_TILE);
+                    bt_bulk_load(VUs, VU + r * VU_TILE, VU_TILE, &vu_full);
+                    s_vu_loads = ++loads;
+                    prev_r = r;
+                }
+                const int s = lu & 1;
+                if (lu >= 2 && !tc::mbar_wait(&z_empty[s], (uint32_t)((lu - 2) >> 1) & 1u, BT_SPIN)) {
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                bt_expect_tx(&z_full[s], Z_TILE);
+                bt_bulk_load(base + VU_TILE + s * Z_TILE, Zimg + j * Z_TILE, Z_TILE, &z_full[s]);
+                s_last_z[s] = lu;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16(BU_R, BU_N);
+            int64_t prev_r = -1;
+            int vu_idx = 0;
+            uint64_t dA[2][3];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int p = 0; p < 3; ++p) dA[h][p] = tc::smem_desc_sw128(VUs + (h * 3 + p) * PART128);
+            for (int lu = 0; lu < nloc; ++lu) {
+                const int64_t u = u0 + lu, r = u / n_ct;
+                if (r != prev_r) {
+                    if (!tc::mbar_wait(&vu_full, (uint32_t)vu_idx & 1u, BT_SPIN)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    ++vu_idx;
+                    prev_r = r;
+                }
+                const int s = lu & 1, b = lu & 1;
+                if (!tc::mbar_wait(&z_full[s], (uint32_t)(lu >> 1) & 1u, BT_SPIN) ||
+                    (lu >= 2 && !tc::mbar_wait(&acc_empty[b], (uint32_t)((lu - 2) >> 1) & 1u, BT_SPIN))) {
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                tc::fence_after_sync();
+                const unsigned char *Zs = base + VU_TILE + s * Z_TILE;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    // buffer b: [big h0 | big h1 | small h0 | small h1], BU_N columns each
+                    const uint32_t dbig = tmem + (uint32_t)(256 * b + BU_N * h), dsmall = dbig + 2 * BU_N;
+                    uint64_t dB[3];
+#pragma unroll
+                    for (int p = 0; p < 3; ++p) dB[p] = tc::smem_desc_sw128(Zs + (h * 3 + p) * ZPART);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t o = (uint64_t)(ks * 32) >> 4;
+                        const uint32_t acc = ks > 0 ? 1u : 0u;
+                        tc::mma_bf16(dbig, dA[h][0] + o, dB[0] + o, idesc, acc);
+                        tc::mma_bf16(dsmall, dA[h][0] + o, dB[1] + o, idesc, acc);
+                        tc::mma_bf16(dsmall, dA[h][1] + o, dB[0] + o, idesc, 1u);
+                        tc::mma_bf16(dsmall, dA[h][0] + o, dB[2] + o, idesc, 1u);
+                        tc::mma_bf16(dsmall, dA[h][2] + o, dB[0] + o, idesc, 1u);
+                        tc::mma_bf16(dsmall, dA[h][1] + o, dB[1] + o, idesc, 1u);
+                    }
+                }
+                tc::mma_commit(&z_empty[s]);
+                tc::mma_commit(&acc_full[b]);
+                const int64_t rn = (lu + 1 < nloc) ? (u + 1) / n_ct : -1;
+                if (rn != r) tc::mma_commit(&vu_empty);
+                s_last_commit = lu;
+            }
+        }
+    } else {
+        const int qd = warp & 3, hf = (warp - 2) >> 2;    // lane quarter, 32-column half
+        for (int lu = 0; lu < nloc; ++lu) {
+            const int64_t u = u0 + lu, r = u / n_ct, j = u % n_ct;
+            const int b = lu & 1;
+            // the thread's 32 elements of C first: their loads overlap the MMAs
+            const int64_t i = r * BU_R + 32 * qd + lane;          // panel-local row
+            const int64_t c0 = j * BU_N + 32 * hf;
+            float *col = F + (k + i) + (k + nbk + c0) * ld;
+            const int64_t nvalid = (i < mp) ? n_tr - c0 : 0;
+            float cv[32];
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) cv[jj] = (jj < nvalid) ? col[(int64_t)jj * ld] : 0.f;
+            if (!tc::mbar_wait(&acc_full[b], (uint32_t)(lu >> 1) & 1u, BT_SPIN)) {
+                s_fail = 1;
+                break;
+            }
+            if (s_fail) break;
+            tc::fence_after_sync();
+            float d[32];
+#pragma unroll
+            for (int cg = 0; cg < 2; ++cg) {
+                float v0[16], v1[16], w0[16], w1[16];
+                const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(256 * b + 32 * hf + 16 * cg);
+                tc::tmem_ld16(ta, v0);
+                tc::tmem_ld16(ta + BU_N, v1);
+                tc::tmem_ld16(ta + 2 * BU_N, w0);
+                tc::tmem_ld16(ta + 3 * BU_N, w1);
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) d[16 * cg + jj] = (v0[jj] + v1[jj]) + (w0[jj] + w1[jj]);
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) bt_arrive(&acc_empty[b]);
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj)
+                if (jj < nvalid) col[(int64_t)jj * ld] = cv[jj] - d[jj];
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (s_fail) {
+        if (threadIdx.x == 0) {
+            atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
+            if (s_vu_loads > 0) tc::mbar_wait(&vu_full, (uint32_t)(s_vu_loads - 1) & 1u, BT_SPIN);
+            for (int s = 0; s < 2; ++s)
+                if (s_last_z[s] >= 0) tc::mbar_wait(&z_full[s], (uint32_t)(s_last_z[s] >> 1) & 1u, BT_SPIN);
+            const int lc = s_last_commit;
+            if (lc >= 0) tc::mbar_wait(&acc_full[lc & 1], (uint32_t)(lc >> 1) & 1u, BT_SPIN);
+        }
+        __syncthreads();
+    }
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+template <typename K>
+cudaError_t bt_smem_attr(K kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+constexpr size_t bz_smem(int nb) { return sizeof(float) * (128 * 129 + 2 * 128 * 65 + (size_t)128 * nb); }
+
+}  // namespace
+
+// C <- H^T C for the outer block of nbk <= 128 columns at column k (inner panels of
+// width nb in {16, 32}, their T factors from Tb on), C = F's columns k + nbk .. ntot.
+// Returns 1 when the shape is not taken (alignment), the caller then updates panel by
+// panel.
+int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int nbk,
+                        int64_t ntot, int nb, const float *Tb)
+{
+    const int64_t mp = m_aug - k, n_ext = ntot - k, n_tr = n_ext - nbk;
+    if (n_tr <= 0 || mp <= 0) return 0;
+    if (nbk < 1 || nbk > BK || (nb != 16 && nb != 32) || ld % 4 != 0 || k % 4 != 0 ||
+        (reinterpret_cast<uintptr_t>(F) & 15u) != 0)
+        return 1;
+    static FlOncePerDevice attr_once;
+    if (attr_once.pending(ctx->device)) {
+        cudaError_t e = bt_smem_attr(k_bimg, BI_SMEM);
+        if (e == cudaSuccess) e = bt_smem_attr(k_by, BY_SMEM);
+        if (e == cudaSuccess) e = bt_smem_attr(k_bz<16>, bz_smem(16));
+        if (e == cudaSuccess) e = bt_smem_attr(k_bz<32>, bz_smem(32));
+        if (e == cudaSuccess) e = bt_smem_attr(k_bu, BU_SMEM);
+        if (e != cudaSuccess) return fl_cuda(ctx, e, "block-update attributes");
+        attr_once.done(ctx->device);
+    }
+    const int64_t nch = fl_cdiv(mp, BY_KC), n_rt = fl_cdiv(mp, BU_R), n_ct = fl_cdiv(n_tr, BU_N);
+    const int64_t ytiles = fl_cdiv(n_ext, BY_N);
+    // one wave of Y-pass CTAs (one per SM), each streaming at least 4 chunks of rows
+    const int64_t S = std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms / ytiles, nch / 4));
+    unsigned char *VY = (unsigned char *)fl_ws(ctx, FL_WS_BLK_VY, (size_t)nch * VY_CHUNK);
+    unsigned char *VU = (unsigned char *)fl_ws(ctx, FL_WS_BLK_VU, (size_t)n_rt * VU_TILE);
+    float *Ypart = (float *)fl_ws(ctx, FL_WS_BLK_Y, sizeof(float) * (size_t)(S + 1) * n_ext * BK);
+    unsigned char *Zimg = (unsigned char *)fl_ws(ctx, FL_WS_BLK_Z, (size_t)n_ct * Z_TILE);
+    if (!VY || !VU || !Ypart || !Zimg) return FASTLSQ_ERR_NOMEM;
+    float *Ysum = Ypart + (size_t)S * n_ext * BK;
+    {
+        FL_PROF(ctx, FASTLSQ_K_BLOCK_PREP);
+        k_bimg<<<(unsigned)n_rt, 256, BI_SMEM, ctx->stream>>>(F, ld, k, nbk, mp, nch, VY, VU);
+        FL_CHECK_LAUNCH(ctx, "block image");
+    }
+    {
+        FL_PROF(ctx, FASTLSQ_K_BLOCK_Y);
+        k_by<<<dim3((unsigned)ytiles, (unsigned)S), BY_THREADS, BY_SMEM, ctx->stream>>>(
+            F, ld, k, nbk, mp, n_ext, VY, nch, Ypart, ctx->d_flag);
+        FL_CHECK_LAUNCH(ctx, "block Y pass");
+    }
+    {
+        FL_PROF_N(ctx, FASTLSQ_K_BLOCK_PREP, 2);
+        k_bsum<<<(unsigned)fl_cdiv(n_ext, 8), 256, 0, ctx->stream>>>(Ypart, (int)S, n_ext, Ysum);
+        FL_CHECK_LAUNCH(ctx, "block Y sum");
+        if (nb == 32)
+            k_bz<32><<<(unsigned)n_ct, 256, bz_smem(32), ctx->stream>>>(Ysum, n_ext, nbk, Tb, Zimg);
+        else
+            k_bz<16><<<(unsigned)n_ct, 256, bz_smem(16), ctx->stream>>>(Ysum, n_ext, nbk, Tb, Zimg);
+        FL_CHECK_LAUNCH(ctx, "block Z");
+    }
+    {
+        const int64_t units = n_rt * n_ct;
+        const unsigned G = (unsigned)std::min<int64_t>(ctx->num_sms, units);
+        FL_PROF(ctx, FASTLSQ_K_BLOCK_U);
+        k_bu<<<G, BU_THREADS, BU_SMEM, ctx->stream>>>(F, ld, k, nbk, mp, n_ext, VU, Zimg, n_ct, units,
+                                                      ctx->d_flag);
+        FL_CHECK_LAUNCH(ctx, "block update");
+    }
+    return 0;
+}

@@ -118,7 +118,7 @@ _SIGNATURES = {
 
 KERNELS = ["prefactor", "assemble_f32", "assemble_f64", "rhs", "eval", "copy_in", "panel",
            "trail_simt", "trail_tc", "apply_q", "trsv", "residual", "vector", "newton", "adjoint",
-           "krylov"]
+           "krylov", "block_prep", "block_y", "block_u"]
 
 
 def library_path() -> str:

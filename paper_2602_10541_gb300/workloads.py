@@ -159,10 +159,10 @@ def helmholtz2d(n_int=8192, n_bc=1024, n_feat=2048, k=4.0, seed_offset=0):
     return w
 
 
-def poisson5d(n_int=32768, n_bc=4096, n_feat=4096):
+def poisson5d(n_int=32768, n_bc=4096, n_feat=4096, seed_offset=0):
     """-Lap u = f on [0,1]^5, uniform-random interior, boundary points on a face
     chosen uniformly among the 10, sigma = 3, boundary weight 100."""
-    s = SEED0 + 3
+    s = SEED0 + 3 + 1000 * seed_offset
     alpha, coef = _laplacian_terms(5, -1.0)
     w = Workload("poisson5d", 3, 5, n_int, n_bc, n_feat, 3.0, 100.0, alpha, coef,
                  np.zeros(0), s)

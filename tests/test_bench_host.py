@@ -1,7 +1,7 @@
 """Host-side bookkeeping of bench.py (no GPU): the stored ncu traffic is reported only
-for the kernel sources and the look-ahead setting it was captured with, the algorithmic
-byte count of the tensor-core update adds up panel by panel, and the whole-job
-throughput of one rank is its solves over its device time."""
+for the kernel sources and workload it was captured with, the algorithmic work of the
+two-level schedule adds up to the one-level schedule's plus the rows above the inner
+panels, and the whole-job throughput of one rank is its solves over its device time."""
 import json
 import os
 import shutil
@@ -14,19 +14,21 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_traffic_entries_carry_their_capture_keys():
-    d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
-    assert "trail_tc@lookahead0" in d and "trail_tc@lookahead1" in d
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        pytest.skip("no ncu traffic on record")
+    d = json.load(open(path))
     for key, e in d.items():
-        cls, mode = key.split("@lookahead")
+        cls, workload = key.split("@")
         assert cls in bench.KERNEL_SRC
-        assert e["lookahead"] == int(mode)
+        assert workload in bench.WORKLOADS
         assert e["bytes_per_launch"] > 0 and len(e["src_sha"]) == 16
 
 
 def test_source_hash_covers_every_file_of_the_class(tmp_path, monkeypatch):
     csrc = tmp_path / "paper_2602_10541_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    names = bench.KERNEL_SRC["trail_tc"]
+    names = bench.KERNEL_SRC["block_y"]
     for n in names:
         shutil.copy(os.path.join(ROOT, "paper_2602_10541_gb300", "csrc", n), csrc / n)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
@@ -41,18 +43,35 @@ def test_source_hash_covers_every_file_of_the_class(tmp_path, monkeypatch):
     assert bench._src_sha(names) == h0
 
 
-@pytest.mark.parametrize("m,n,nb", [(100, 40, 32), (64, 64, 32), (300, 97, 16)])
-def test_update_bytes_add_up_per_panel(m, n, nb):
-    # element by element: every trailing element of C (right-hand side column included)
-    # is read twice and written once, every element of V read once, and the operand
-    # image of V written as 32 hi/lo pairs per row
-    want = 0.0
-    for k in range(0, n, nb):
-        c = min(nb, n - k)
-        for _row in range(k, m):
-            want += 12.0 * (n + 1 - (k + c)) + 4.0 * c + 8.0 * 32
-    unit, got = bench._algorithmic("trail_tc", m, n, m, nb, 1, 2, 4)
-    assert unit == "bytes" and got == pytest.approx(want, rel=1e-15)
+@pytest.mark.parametrize("m,n,nb", [(1000, 300, 32), (700, 256, 16), (500, 130, 32), (400, 64, 32)])
+def test_two_level_work_adds_up(m, n, nb):
+    """One level: panel kp updates every column right of it with its rows kp.. (4 (m-kp)
+    nb n_c flops).  Two levels: inside the block the same, and the outer update applies
+    the whole block with the block's rows k.. to the columns right of the block, so it
+    also multiplies the zeros above each inner panel's diagonal: the difference is
+    exactly sum over inner panels of 4 (kp - k) nb n_right."""
+    nrhs = 1
+    one = sum(4.0 * (m - kp) * min(nb, n - kp) * (n + nrhs - (kp + min(nb, n - kp)))
+              for kp in range(0, n, nb))
+    y, u = bench._blocked_flops(m, n, nrhs)
+    gram = sum(2.0 * (m - k) * min(128, n - k) * min(128, n - k) for k in range(0, n, 128)
+               if n + nrhs > k + min(128, n - k))
+    two = (y - gram) + u + bench._inner_flops(m, n, nb)
+    extra = 0.0
+    for k in range(0, n, 128):
+        nbk = min(128, n - k)
+        for kp in range(k, k + nbk, nb):
+            extra += 4.0 * (kp - k) * min(nb, n - kp) * (n + nrhs - (k + nbk))
+    assert two == pytest.approx(one + extra, rel=1e-14)
+    unit, amount = bench._algorithmic("block_u", m, n, m, nb, 1, 2, 4)
+    assert unit == "flops" and amount == pytest.approx(bench.SPLIT_PRODUCTS * u)
+
+
+def test_oracle_sample_ratio_is_the_qr_work_ratio():
+    s = bench.WORKLOADS["poisson5d"]["cpu_sample"]
+    r = bench._scale_ratio("poisson5d", s)
+    assert r == pytest.approx((32768 + 4096) * 4096 ** 2 / ((s["n_int"] + s["n_bc"]) * s["n_feat"] ** 2))
+    assert bench._scale_ratio("helmholtz2d", None) == 1.0
 
 
 def test_single_rank_throughput_is_solves_over_device_time():

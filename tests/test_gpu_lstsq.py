@@ -376,7 +376,7 @@ def test_row_panel_matches_oracle_and_column_panel(ctx, m, n):
     assert np.abs(Rs[1] - Rs[0]).max() <= 2e-5 * scale
 
 
-@pytest.mark.parametrize("tc", [0, 1])
+@pytest.mark.parametrize("tc", [0, 2])
 @pytest.mark.parametrize("m,n", [(700, 130), (3000, 257), (9000, 96)])
 def test_lookahead_matches_single_stream(ctx, tc, m, n):
     """Look-ahead (the rest of each trailing update on the auxiliary stream while the

@@ -1,15 +1,21 @@
-"""Trailing updates of the MIXED factorisation on the tcgen05 tensor cores (split
-TF32x3 products, FP32 accumulation in TMEM, operands by TMA; the default) against
-the FP64 oracle and against the SIMT FP32 updates.
+"""Trailing updates of the MIXED factorisation on the tcgen05 tensor cores against
+the FP64 oracle and against the SIMT FP32 updates.  Two modes: the default two-level
+blocking (outer blocks of 128 columns updated with K = 128, operands split into
+three bf16 parts, six products, FP32 accumulation in TMEM) and the panel-by-panel
+TF32x3 update (operands by TMA).
 
-Bars: TF32x3 keeps about FP32 accuracy per product (the dropped lo*lo term is
-2^-22 relative), so R must match the oracle's Householder R to the same 2e-5
-(relative to max |R|) as the SIMT FP32 path; after refinement the solutions meet
-the same bars as the SIMT path (1e-9 on nearly consistent random systems, 1e-6 on
-the PDE test set).
+Bars: both splits keep about FP32 accuracy per product (three bf16 parts: dropped
+terms below 2^-25; TF32x3: 2^-22), so R must match the oracle's Householder R to the
+same 2e-5 (relative to max |R|) as the SIMT FP32 path; after refinement the
+solutions meet the same bars as the SIMT path (1e-9 on nearly consistent random
+systems, 1e-6 on the PDE test set).  Where the factor preconditions CGLS, the
+blocked mode's R must precondition as well as the SIMT FP32 R does.
 """
+import math
+
 import numpy as np
 import pytest
+import scipy.linalg
 import torch
 
 import oracle
@@ -54,14 +60,18 @@ def _factor_r(ctx, A, tc):
     return R.cpu().numpy().T, st
 
 
-# (m, n): several 128 x 128 update tiles with ragged edges; n = 40 at m = 30000 runs
-# the 16-wide panel; 300 columns leave a ragged last panel and trailing tile.
-@pytest.mark.parametrize("m,n", [(700, 130), (3000, 257), (1500, 300), (30000, 40)])
-def test_tensor_core_r_matches_oracle(ctx, m, n):
+# (m, n): several update tiles with ragged edges; n = 40 at m = 30000 runs the 16-wide
+# panel; 300 columns leave a ragged last panel, outer block and trailing tile; 700
+# columns are six outer blocks; m = 30000 with 300 columns is the blocked update over
+# 16-wide inner panels.
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("m,n", [(700, 130), (3000, 257), (1500, 300), (30000, 40), (5001, 700),
+                                 (30000, 300)])
+def test_tensor_core_r_matches_oracle(ctx, m, n, mode):
     rng = np.random.default_rng(7 * m + n)
     A = rng.standard_normal((m, n))
-    Rt, st = _factor_r(ctx, A, 1)
-    assert st.tensor_core == 1
+    Rt, st = _factor_r(ctx, A, mode)
+    assert st.tensor_core == mode
     Rs, st0 = _factor_r(ctx, A, 0)
     assert st0.tensor_core == 0
     packed, _ = oracle.qr(A)
@@ -72,21 +82,22 @@ def test_tensor_core_r_matches_oracle(ctx, m, n):
     assert np.abs(Rt - Rs).max() <= 2e-5 * scale
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("m,n,mu", [(517, 77, 0.0), (2000, 130, 1e-10), (4000, 513, 0.0)])
-def test_tensor_core_mixed_solve_refines_to_fp64(ctx, m, n, mu):
+def test_tensor_core_mixed_solve_refines_to_fp64(ctx, m, n, mu, mode):
     rng = np.random.default_rng(m + 3 * n)
     A = rng.standard_normal((m, n))
     b = A @ rng.standard_normal(n)
     B = (b + 1e-9 * np.linalg.norm(b) / np.sqrt(m) * rng.standard_normal(m))[:, None]
     ref = oracle.lstsq(A, B, mu=mu).reshape(-1)
     beta = torch.zeros((1, n), dtype=torch.float64, device=DEV)
-    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
+    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, mode)
     try:
         _, _, st = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, mu, _rhs(B), beta,
                                     A_refine=_cm(A, torch.float64), max_refine=4, stats=True)
     finally:
         fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
-    assert st.tensor_core == 1
+    assert st.tensor_core == mode
     np.testing.assert_allclose(beta.cpu().numpy()[0], ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
 
 
@@ -108,3 +119,43 @@ def test_tensor_core_helmholtz_matches_oracle(ctx):
         fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
     assert s.stats.tensor_core == 1
     assert pl.rel_l2(s.u_test().cpu().numpy(), u_orc) <= 1e-6
+
+
+def _inverse_operator(w):
+    """FP64 operator of a Sec. 4.4 instance (-Lap rows, Dirichlet rows weighted by lam)
+    with the Tikhonov rows sqrt(mu) I below, from the oracle."""
+    A_int = oracle.assemble(w.x_int, w.alpha, w.coef, w.W, w.b, w.scale)
+    A_bc = oracle.assemble(w.x_bc, np.zeros((1, w.d), np.int32), [1.0], w.W, w.b, w.scale,
+                           row_weight=w.lam_bc)
+    return np.vstack([A_int, A_bc])
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_blocked_factor_preconditions_like_simt(ctx, q):
+    """cond(A_mu R^{-1}) with R from the blocked tensor-core factor against R from the
+    SIMT FP32 factor, on inverse-problem instances whose regularised system has a
+    condition number near 1/eps32 (the systems CGLS refines): the three-part bf16
+    products must not degrade the preconditioner (the TF32x3 update did: 10-170
+    against 2-11)."""
+    w = wl.inverse_instance(q, n_int=1600, n_feat=384)
+    A = _inverse_operator(w)
+    m, n = A.shape
+    Aug = np.vstack([A, math.sqrt(w.mu) * np.eye(n)])
+    conds = {}
+    for mode in (0, 1):
+        fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, mode)
+        try:
+            _, fac, st = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, w.mu, None, None,
+                                          A_refine=_cm(A, torch.float64), keep=True, stats=True,
+                                          refine_mode=fl.REFINE_CGLS)
+        finally:
+            fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
+        assert st.tensor_core == mode
+        R = torch.zeros((n, n), dtype=torch.float64, device=DEV)
+        fl.fastlsq_factor_get_r(ctx, fac, R)
+        fl.fastlsq_factor_destroy(ctx, fac)
+        Rn = R.cpu().numpy().T
+        P = scipy.linalg.solve_triangular(Rn, np.eye(n), lower=False)
+        conds[mode] = np.linalg.cond(Aug @ P)
+    print(f"instance {q}: cond(A R^-1) SIMT {conds[0]:.3g}, blocked tensor core {conds[1]:.3g}")
+    assert conds[1] <= 1.5 * conds[0] + 1.0
