@@ -23,9 +23,10 @@
 //   k_by   : Y = V^T [V | C] over split row ranges (MMA M = 128 block columns, N = 128
 //            columns, K = 64 rows per stage); the columns of C are loaded from F by
 //            converter warps (coalesced float4 along the rows), split in registers and
-//            stored in the operand layout; the products of each 64-row chunk accumulate
-//            in a fresh TMEM accumulator that the converter warps add into an FP32
-//            total (round-to-nearest) two chunks behind the MMAs; the V^T V
+//            stored in the operand layout; the leading products of each 64-row chunk
+//            accumulate in a fresh TMEM accumulator that the converter warps add into
+//            FP32 registers two chunks behind the MMAs (the small products accumulate
+//            over the split in TMEM); the V^T V
 //            block (Gram matrix) comes out of the same pass from the block's own columns
 //            (unit lower trapezoid applied); k_bsum adds the split partials in order;
 //   k_bz   : Z = the block-triangular T^T applied to Y, inner panel by inner panel:
@@ -204,13 +205,15 @@ k_bimg(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, 
 // Roles: warp 0 bulk-loads the VY chunk (A operand, three parts), warps 2..9 load the
 // X chunk from F one chunk ahead, split it and store the three B parts, warp 1 issues
 // the 24 MMAs of the chunk and commits them to the stage's "empty" barrier and to the
-// chunk's accumulator.  Each chunk's six products go to a fresh TMEM accumulator (three
-// buffers in turn); warps 2..9 add a finished accumulator into a running FP32 total
-// kept in TMEM (tcgen05.ld, round-to-nearest add, tcgen05.st) two chunks behind the
-// MMAs, so the long sum over the split's rows is taken with round-to-nearest adds while
-// the tensor core sums 64 rows at a time, and the adds stay off the MMAs' path.
+// chunk's accumulator.  The five small products accumulate over the whole split in one
+// TMEM accumulator; each chunk's leading products go to a fresh TMEM accumulator (three
+// buffers in turn) that warps 2..9 add into FP32 registers two chunks behind the MMAs,
+// so the long sum of the leading products over the split's rows is taken with
+// round-to-nearest adds while the tensor core sums 64 rows at a time, and the adds
+// stay off the MMAs' path.  (Measured: sharing one accumulator between the leading and
+// the small products, even for 64 rows, made R a worse CGLS preconditioner.)
 // ---------------------------------------------------------------------------
-constexpr int BY_NBUF = 3;             // chunk accumulators in TMEM (plus the total)
+constexpr int BY_NBUF = 3;             // leading-product accumulators in TMEM (plus the small one)
 
 __global__ void __launch_bounds__(BY_THREADS, 1)
 k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, int64_t n_ext,
@@ -248,8 +251,9 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
-    // TMEM columns: [128 b, 128 b + 128) the chunk accumulator b, [384, 512) the total
-    const uint32_t ttotal = tmem + BY_NBUF * BY_N;
+    // TMEM columns: [0, 128) the small products of the split, [128 + 128 b, 256 + 128 b)
+    // the leading products of chunk buffer b
+    const uint32_t tsmall = tmem;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -280,23 +284,22 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
                 if (s_fail) break;
                 tc::fence_after_sync();
                 const unsigned char *A = base + s * BY_STAGE, *B = A + VY_CHUNK;
-                const uint32_t d = tmem + (uint32_t)(BY_N * b);
+                const uint32_t dbig = tmem + (uint32_t)(BY_N + BY_N * b);
                 uint64_t dA[3], dB[3];
 #pragma unroll
                 for (int p = 0; p < 3; ++p) {
                     dA[p] = tc::smem_desc_sw128(A + p * PART128);
                     dB[p] = tc::smem_desc_sw128(B + p * PART128);
                 }
-                // the small products first, the leading one last
 #pragma unroll
                 for (int ks = 0; ks < BY_KC / 16; ++ks) {
                     const uint64_t o = (uint64_t)(ks * 32) >> 4;       // 16 bf16 = 32 bytes along K
-                    tc::mma_bf16(d, dA[0] + o, dB[1] + o, idesc, ks > 0 ? 1u : 0u);
-                    tc::mma_bf16(d, dA[1] + o, dB[0] + o, idesc, 1u);
-                    tc::mma_bf16(d, dA[0] + o, dB[2] + o, idesc, 1u);
-                    tc::mma_bf16(d, dA[2] + o, dB[0] + o, idesc, 1u);
-                    tc::mma_bf16(d, dA[1] + o, dB[1] + o, idesc, 1u);
-                    tc::mma_bf16(d, dA[0] + o, dB[0] + o, idesc, 1u);
+                    tc::mma_bf16(dbig, dA[0] + o, dB[0] + o, idesc, ks > 0 ? 1u : 0u);
+                    tc::mma_bf16(tsmall, dA[0] + o, dB[1] + o, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
+                    tc::mma_bf16(tsmall, dA[1] + o, dB[0] + o, idesc, 1u);
+                    tc::mma_bf16(tsmall, dA[0] + o, dB[2] + o, idesc, 1u);
+                    tc::mma_bf16(tsmall, dA[2] + o, dB[0] + o, idesc, 1u);
+                    tc::mma_bf16(tsmall, dA[1] + o, dB[1] + o, idesc, 1u);
                 }
                 tc::mma_commit(&empty[s]);
                 tc::mma_commit(&accf[b]);
@@ -306,9 +309,12 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
     } else {
         const int ct = threadIdx.x - 64;                       // 0 .. 255
         // D: TMEM lane = block column l, column = e.  Warp w adds its lane quarter
-        // (w mod 4) and half (w - 2) / 4 of the 128 columns into the total
+        // (w mod 4) and half (w - 2) / 4 of the 128 columns into its registers
         const int qd = warp & 3, hf = (warp - 2) >> 2;
         const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
+        float y[64];
+#pragma unroll
+        for (int jj = 0; jj < 64; ++jj) y[jj] = 0.f;
         float4 x[8];
         auto load = [&](int ch) {
             const int64_t r0 = chunk(ch) * BY_KC;
@@ -328,23 +334,23 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
                 x[u] = v;
             }
         };
-        // total += accumulator of chunk c (the first chunk's is copied)
+        // y += leading products of chunk c
         auto drain = [&](int c) -> bool {
             const int b = c % BY_NBUF;
             if (!tc::mbar_wait(&accf[b], (uint32_t)(c / BY_NBUF) & 1u, BT_SPIN)) return false;
             tc::fence_after_sync();
 #pragma unroll
-            for (int rd = 0; rd < 4; ++rd) {
-                uint32_t v0[16], t0[16];
-                const uint32_t col = (uint32_t)(64 * hf + 16 * rd);
-                tc::tmem_ld16_nw(tmem + lane_base + (uint32_t)(BY_N * b) + col, v0);
-                if (c > 0) tc::tmem_ld16_nw(ttotal + lane_base + col, t0);
+            for (int rd = 0; rd < 2; ++rd) {
+                uint32_t v0[16], v1[16];
+                const uint32_t src = tmem + lane_base + (uint32_t)(BY_N + BY_N * b + 64 * hf + 32 * rd);
+                tc::tmem_ld16_nw(src, v0);
+                tc::tmem_ld16_nw(src + 16, v1);
                 tc::tmem_wait_ld();
-                float a0[16];
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj)
-                    a0[jj] = (c > 0) ? __uint_as_float(t0[jj]) + __uint_as_float(v0[jj]) : __uint_as_float(v0[jj]);
-                tc::tmem_st16(ttotal + lane_base + col, a0);
+                for (int jj = 0; jj < 16; ++jj) {
+                    y[32 * rd + jj] += __uint_as_float(v0[jj]);
+                    y[32 * rd + 16 + jj] += __uint_as_float(v1[jj]);
+                }
             }
             tc::fence_before_sync();
             __syncwarp();
@@ -383,19 +389,21 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
             if (c >= 0 && !drain(c)) s_fail = 1;
         __syncwarp();
         if (!s_fail) {
+            // the small products of the whole split (every MMA has completed: the last
+            // chunk's commit arrived after all earlier MMAs of the issuing thread)
             const int l = 32 * qd + lane;
 #pragma unroll
             for (int rd = 0; rd < 4; ++rd) {
                 float t[16];
                 const uint32_t col = (uint32_t)(64 * hf + 16 * rd);
-                if (nloc > 0) tc::tmem_ld16(ttotal + lane_base + col, t);
+                if (nloc > 0) tc::tmem_ld16(tsmall + lane_base + col, t);
                 else
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) t[jj] = 0.f;
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {
                     const int64_t e = ebase + col + jj;
-                    if (e < n_ext) Ypart[((int64_t)blockIdx.y * n_ext + e) * BK + l] = t[jj];
+                    if (e < n_ext) Ypart[((int64_t)blockIdx.y * n_ext + e) * BK + l] = y[16 * rd + jj] + t[jj];
                 }
             }
         }
