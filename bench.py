@@ -507,32 +507,54 @@ def _secondary(fl, pl, wl, torch, ctx, dev, n_inverse):
                         "workload": "d u/dx and d u/dy of the helmholtz2d solution (2048 features) at 200,000 points, FP64"}
     del sr, dpr
 
-    op = fl.Op([[2, 0], [0, 2]], [-1.0, -1.0])
-    insts, ws = [], []
-    for q in range(n_inverse):
-        wq = wl.inverse_instance(q)
-        ws.append(wq)
-        insts.append(dict(x_int=t(wq.x_int), x_bc=t(wq.x_bc), W=t(wq.W), b=t(wq.b), sensors=t(wq.sensors),
-                          y_obs=torch.zeros(wq.sensors.shape[0], dtype=torch.float64, device=dev),
-                          theta=t(wq.params), beta=torch.zeros(wq.n_feat, dtype=torch.float64, device=dev),
-                          loss=torch.zeros(1, dtype=torch.float64, device=dev),
-                          dtheta=torch.zeros(16, dtype=torch.float64, device=dev)))
-    fl.fastlsq_inverse_batch(ctx, insts, op, 4)
-    for d, wq in zip(insts, ws):
-        u_s = torch.empty(d["sensors"].shape[0], dtype=torch.float64, device=dev)
-        fl.fastlsq_eval(ctx, d["sensors"], d["W"], d["b"], wq.scale, d["beta"], u_s)
-        d["y_obs"].copy_(u_s + t(wq.noise))
-        d["theta"].copy_(t(wq.theta0))
+    out["inverse"] = _inverse_row(fl, pl, wl, torch, ctx, dev, n_inverse)
+    return out
+
+
+def _inverse_row(fl, pl, wl, torch, ctx, dev, n_inst):
+    """The batched inverse heat-source configuration: n_inst instances drawn with its
+    recipe, factored once (FP64 QR, kept), then gradient evaluations of the whole batch,
+    each one persistent launch, replayed from a captured CUDA graph and timed with
+    events.  Reports factorisations/s of the setup and gradient evaluations/s (one
+    evaluation = loss and dL/dtheta of one instance)."""
+    ws = [wl.inverse_instance(q) for q in range(n_inst)]
+    # a context of its own on a non-default stream (graph capture needs one)
+    ctx = fl.Context(torch.device(dev).index or 0, stream=torch.cuda.Stream(device=dev))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    fl.fastlsq_inverse_batch(ctx, insts, op, 4)
+    batch = pl.InverseBatch(ctx, ws, device=dev)
     torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
-    out["inverse"] = {"instances": n_inverse, "seconds": sec, "gradient_evals_per_s": n_inverse / sec,
-                      "rows_range": [int(min(wq.n_int for wq in ws)), int(max(wq.n_int for wq in ws))],
-                      "features_range": [int(min(wq.n_feat for wq in ws)), int(max(wq.n_feat for wq in ws))],
-                      "workload": ("steady inverse heat source, 4 Gaussians (16 parameters), MIXED factor + "
-                                   "CGLS/PCG refinement, loss and dL/dtheta per instance")}
+    setup_s = time.perf_counter() - t0
+    batch.observe()
+    for _ in range(2):
+        batch.eval()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=ctx.stream):
+        batch.eval()
+    reps = 10
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(ctx.stream):                # replay() runs on the current stream
+        g.replay()
+        a.record(ctx.stream)
+        for _ in range(reps):
+            g.replay()
+        b.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    out = {"instances": n_inst, "setup_s": setup_s, "factorizations_per_s": n_inst / setup_s,
+           "ms_per_batch_eval": ms, "gradient_evals_per_s": n_inst / (ms / 1e3),
+           "launch": batch.launch,
+           "rows_range": [int(min(w.n_int for w in ws)), int(max(w.n_int for w in ws))],
+           "features_range": [int(min(w.n_feat for w in ws)), int(max(w.n_feat for w in ws))],
+           "loss_mean": float(sum(d["loss"].item() for d in batch.inst) / n_inst),
+           "workload": ("steady inverse heat source -Lap u = s(x; theta), 4 Gaussians (16 parameters), "
+                        "n_int ~ U{1024..8192}, n_feat ~ U{512..2048}, sigma = 8, mu = 1e-10, 64 sensors; "
+                        "FP64 factor of [A; sqrt(mu) I] kept, per evaluation Q^T, R^-1, R^-T, Q and the "
+                        "source gradient in one persistent launch (CUDA graph replay)")}
+    batch.close()
+    del g
+    ctx.close()
     return out
 
 
@@ -572,7 +594,7 @@ def main():
     ap.add_argument("--trsv-fp32", type=int, default=1, choices=[0, 1],
                     help="1: FP32 substitution in the triangular solves of classical refinement")
     ap.add_argument("--no-extras", action="store_true", help="skip the other rows of the hot path")
-    ap.add_argument("--inverse-instances", type=int, default=32)
+    ap.add_argument("--inverse-instances", type=int, default=256)
     ap.add_argument("--instances", type=int, default=0,
                     help="independent full-size solves per step, each on its own stream "
                          "(0: the workload's default, 4 for poisson5d, 8 for helmholtz2d)")

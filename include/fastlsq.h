@@ -387,6 +387,45 @@ FASTLSQ_API int fastlsq_inverse_batch(fastlsq_ctx *ctx, const fastlsq_inverse_in
                                       const fastlsq_inverse_opts *opts);
 
 /*
+ * Pre-factored batch of inverse-problem instances (Sec. 4.4: the operator is factored
+ * once and every evaluation of the forward map and its gradient reuses the factor,
+ * two triangular solves per evaluation; Sec. 2.5: gradients through the solve).
+ *
+ * fastlsq_inverse_prepare assembles each instance's FP64 operator (interior rows op,
+ * boundary rows bc_weight * identity), factors [A; sqrt(mu) I] by FP64 Householder QR
+ * (the factor is kept by the plan), tabulates the sensor matrix H_s[s][j] =
+ * scale sin(W_j . x_s + b_j) and records the instances' device pointers.  opts: mu > 0
+ * and bc_weight are used; prec, refine and adjoint fields are ignored (the factor is
+ * FP64).  Limits: n_src <= 8, n_sens <= 256, and n_int + n_bc + n_feat small enough
+ * that one instance's vector of that length plus one of n_feat (FP64) fit in a CTA's
+ * shared memory (about 26,000 in all on GB300), else -1.  Synchronises the context's
+ * stream; returns 0 and *plan, or a negative status (nothing is kept).
+ *
+ * fastlsq_inverse_eval runs one gradient evaluation of every instance in ONE
+ * persistent launch: a grid of min(n_inst, SMs * ctas_per_sm) CTAs of `threads`
+ * threads (256 or 512) takes instances from a device-side queue, longest first
+ * (m_aug n_feat); one CTA evaluates an instance entirely:
+ *   y = Q^T [s(x_int; theta); 0; 0], beta = R^{-1} y[0:n], u_s = H_s beta,
+ *   loss = mean (u_s - y_obs)^2, w = R^{-T} H_s^T dloss/du_s, z = Q [w; 0]
+ *   (= A (A^T A + mu I)^{-1} H_s^T g), dtheta = sum_{i < n_int} z_i ds(x_i)/dtheta,
+ * writing beta, loss and dtheta through the instances' pointers.  It reads theta and
+ * y_obs at run time, allocates nothing and does not synchronise, so it can be captured
+ * in a CUDA graph and replayed after the caller updates theta or y_obs in place.  No
+ * CTA waits on another (the queue is one atomic counter).  -1 for other threads or
+ * ctas_per_sm values (1..4) whose shared memory does not fit.
+ *
+ * fastlsq_inverse_plan_destroy synchronises the plan's stream and frees the factors,
+ * the sensor matrices and the tables.
+ */
+typedef struct fastlsq_inverse_plan fastlsq_inverse_plan;
+FASTLSQ_API int fastlsq_inverse_prepare(fastlsq_ctx *ctx, const fastlsq_inverse_instance *inst,
+                                        int32_t n_inst, const fastlsq_op *op, int32_t n_src,
+                                        const fastlsq_inverse_opts *opts, fastlsq_inverse_plan **plan);
+FASTLSQ_API int fastlsq_inverse_eval(fastlsq_ctx *ctx, const fastlsq_inverse_plan *plan,
+                                     int32_t threads, int32_t ctas_per_sm);
+FASTLSQ_API int fastlsq_inverse_plan_destroy(fastlsq_inverse_plan *plan);
+
+/*
  * Feature-weight and bias gradients through the exact inner solve (learnable
  * bandwidth, App. "Learnable Bandwidth via Reparameterisation", Alg. 2).  For the
  * block A_ij = row_weight * scale * sum_t coef_t D^{alpha_t} phi_j(x_i) of op (no

@@ -112,6 +112,11 @@ _SIGNATURES = {
     "fastlsq_residual": [_vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp],
     "fastlsq_inverse_batch": [_vp, ctypes.POINTER(fastlsq_inverse_instance), _i32,
                               ctypes.POINTER(fastlsq_op), _i32, ctypes.POINTER(fastlsq_inverse_opts)],
+    "fastlsq_inverse_prepare": [_vp, ctypes.POINTER(fastlsq_inverse_instance), _i32,
+                                ctypes.POINTER(fastlsq_op), _i32, ctypes.POINTER(fastlsq_inverse_opts),
+                                ctypes.POINTER(_vp)],
+    "fastlsq_inverse_eval": [_vp, _vp, _i32, _i32],
+    "fastlsq_inverse_plan_destroy": [_vp],
     "fastlsq_profile_enable": [_vp, ctypes.c_int],
     "fastlsq_profile_read": [_vp, ctypes.c_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)],
 }
@@ -434,6 +439,58 @@ def fastlsq_profile_read(ctx):
         ctx.check(ctx.lib.fastlsq_profile_read(ctx.handle, k, ctypes.byref(n), ctypes.byref(ms)))
         out[name] = (int(n.value), float(ms.value))
     return out
+
+
+def fastlsq_sync(ctx):
+    """Wait for the context's stream and report a device-side error flag (raises)."""
+    return ctx.check(ctx.lib.fastlsq_sync(ctx.handle))
+
+
+def _inverse_instances(instances):
+    arr = (fastlsq_inverse_instance * len(instances))()
+    for q, d in enumerate(instances):
+        arr[q] = fastlsq_inverse_instance(
+            d["x_int"].shape[0], d["x_bc"].shape[0], d["W"].shape[0], d["sensors"].shape[0],
+            d["x_int"].data_ptr(), d["x_bc"].data_ptr(), d["W"].data_ptr(), d["b"].data_ptr(),
+            d["sensors"].data_ptr(), d["y_obs"].data_ptr(), d["theta"].data_ptr(),
+            d["beta"].data_ptr(), d["loss"].data_ptr(), d["dtheta"].data_ptr())
+    return arr
+
+
+class InversePlan:
+    """fastlsq_inverse_prepare / fastlsq_inverse_plan_destroy: the instances' factors
+    and sensor matrices, kept for repeated evaluations (the instance tensors must stay
+    alive and at the same addresses while the plan is used)."""
+
+    def __init__(self, ctx, instances, op, n_src, mu=1e-10, bc_weight=100.0):
+        self.ctx = ctx
+        self.instances = list(instances)
+        arr = _inverse_instances(self.instances)
+        opts = fastlsq_inverse_opts(PREC_FP64, 0, 0.0, 0, 0.0, float(mu), float(bc_weight))
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.fastlsq_inverse_prepare(ctx.handle, arr, len(self.instances), ctypes.byref(op.struct),
+                                                  n_src, ctypes.byref(opts), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.fastlsq_inverse_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fastlsq_inverse_prepare(ctx, instances, op, n_src, mu=1e-10, bc_weight=100.0):
+    return InversePlan(ctx, instances, op, n_src, mu=mu, bc_weight=bc_weight)
+
+
+def fastlsq_inverse_eval(ctx, plan, threads=256, ctas_per_sm=1):
+    """One gradient evaluation of every instance of the plan (one persistent launch)."""
+    return ctx.check(ctx.lib.fastlsq_inverse_eval(ctx.handle, plan.handle, threads, ctas_per_sm))
 
 
 def fastlsq_inverse_batch(ctx, instances, op, n_src, prec=PREC_MIXED, refine_iters=64,

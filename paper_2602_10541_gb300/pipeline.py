@@ -202,6 +202,58 @@ class ConcurrentSolves:
             origin.wait_event(ev)
 
 
+def tuned(kernel: str, default: dict) -> dict:
+    """The launch shape the autotuner recorded for a kernel (tuning.json next to this
+    module, written by ``python -m paper_2602_10541_gb300.tune``), else `default`."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+    if os.path.exists(path):
+        entry = json.load(open(path)).get(kernel)
+        if entry:
+            return {k: entry[k] for k in default}
+    return dict(default)
+
+
+class InverseBatch:
+    """Instances of the batched inverse heat-source problem (Sec. 4.4, steady form) on
+    the GPU behind one pre-factored plan: setup factors every operator once (FP64),
+    each evaluation is one persistent launch over all instances (loss, beta, dL/dtheta
+    per instance).  Observations come from the forward map at the instances' true
+    parameters plus their noise; evaluations start at their perturbed parameters."""
+
+    def __init__(self, ctx, workloads, device="cuda:0", mu=1e-10, bc_weight=100.0, launch=None):
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+        self.ctx, self.ws = ctx, list(workloads)
+        self.inst = [dict(x_int=t(w.x_int), x_bc=t(w.x_bc), W=t(w.W), b=t(w.b), sensors=t(w.sensors),
+                          y_obs=torch.zeros(w.sensors.shape[0], dtype=torch.float64, device=device),
+                          theta=t(w.params), beta=torch.zeros(w.n_feat, dtype=torch.float64, device=device),
+                          loss=torch.zeros(1, dtype=torch.float64, device=device),
+                          dtheta=torch.zeros(w.params.size, dtype=torch.float64, device=device))
+                     for w in self.ws]
+        self.n_src = self.ws[0].params.size // 4
+        self.launch = launch or tuned("inverse_eval", {"threads": 256, "ctas_per_sm": 1})
+        self.plan = fl.fastlsq_inverse_prepare(ctx, self.inst, fl.Op(self.ws[0].alpha, self.ws[0].coef),
+                                               self.n_src, mu=mu, bc_weight=bc_weight)
+        self.device = device
+
+    def eval(self):
+        fl.fastlsq_inverse_eval(self.ctx, self.plan, **self.launch)
+
+    def observe(self):
+        """y_obs = u(sensors) at the true parameters + the instance's noise; theta set to
+        the perturbed evaluation point theta_0."""
+        self.eval()
+        for d, w in zip(self.inst, self.ws):
+            u_s = torch.empty(d["sensors"].shape[0], dtype=torch.float64, device=self.device)
+            fl.fastlsq_eval(self.ctx, d["sensors"], d["W"], d["b"], w.scale, d["beta"], u_s)
+            d["y_obs"].copy_(u_s + torch.as_tensor(w.noise, device=self.device))
+            d["theta"].copy_(torch.as_tensor(w.theta0, device=self.device))
+
+    def close(self):
+        self.plan.close()
+
+
 def newton_solve(ctx, dp: DeviceProblem, f, g, prec=fl.PREC_MIXED, max_iter=30, tol=1e-10,
                  stage_coef=None, warm=True, max_refine=64, refine_tol=1e-13):
     """Newton-Raphson with the refinements of Sec. 2.4 on a device problem: warm start
