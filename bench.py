@@ -235,6 +235,11 @@ def _blocked_flops(m_aug, n, nrhs):
     return y, u
 
 
+def _block_launches(n, nrhs):
+    """Y-pass plus update-pass launches of one factorisation (blocks with columns right of them)."""
+    return 2 * sum(1 for k in range(0, n, BLK) if n + nrhs - k - min(BLK, n - k) > 0)
+
+
 def _inner_flops(m_aug, n, nb):
     """Flops of the SIMT updates inside the outer blocks (4 m_p nb n_c per panel)."""
     f = 0.0
@@ -376,7 +381,7 @@ def _secondary(fl, pl, wl, torch, ctx, dev, n_inverse):
                                 f"continuation nu = {', '.join(f'{-c[0]:g}' for c in stages)}, "
                                 f"<= {iters} iterations per stage"))}
 
-    # variable-coefficient operator (Sec. 4.4): div(nu grad u) = f as nu Lap u + grad nu .
+    # variable-coefficient operator (Sec. 3.8): div(nu grad u) = f as nu Lap u + grad nu .
     # grad u, four per-point terms assembled on the fly from the coefficient fields; MIXED
     # solves (2 refinement steps) timed one at a time, error vs u* and vs the FP64 solve
     wv = wl.varcoef2d()
@@ -462,7 +467,7 @@ def _secondary(fl, pl, wl, torch, ctx, dev, n_inverse):
                      "fly) and dL/dsigma; checked against central differences of the loss")}
     del sb
 
-    # cached re-solves (App. F.4): factor the helmholtz2d operator once, then solve for
+    # cached re-solves (App. G.5): factor the helmholtz2d operator once, then solve for
     # new right-hand sides (Q^T b, R^{-1}, two refinement steps) against the kept factor
     wr = wl.helmholtz2d()
     dpr = pl.upload(wr, dev)
@@ -567,16 +572,19 @@ def _peaks():
             "sm_max_mhz": 2070.0}, "of fallback"
 
 
-def _traffic(cls, workload):
-    """ncu DRAM bytes per launch of a kernel class for the workload, if a capture of the
-    current sources is on record (profiles/ncu_traffic.json)."""
+def _traffic(cls):
+    """ncu DRAM bytes per bf16 tensor flop of a kernel class, if a capture of the current
+    sources is on record (profiles/ncu_traffic.json).  Both passes stream their operand
+    once per launch (the Y pass reads the block's rows of [V | C], the update pass reads
+    and writes C), so their traffic grows with the launch's flops at a fixed block
+    width and a capture on a smaller workload scales to the bench's."""
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(tpath):
         return None, None
-    info = json.load(open(tpath)).get(f"{cls}@{workload}")
+    info = json.load(open(tpath)).get(cls)
     if not info or info.get("src_sha") != _src_sha(KERNEL_SRC.get(cls, "qr.cu")):
         return None, None
-    return info.get("bytes_per_launch"), info.get("source")
+    return info.get("bytes_per_tensor_flop"), info.get("captured_on")
 
 
 def main():
@@ -730,11 +738,13 @@ def main():
     traffic = None
     tsrc = None
     if args.tensor_core == 1:
-        ty, sy = _traffic("block_y", name)
-        tu, su = _traffic("block_u", name)
+        ty, sy = _traffic("block_y")
+        tu, su = _traffic("block_u")
         if ty is not None and tu is not None:
-            traffic = 0.5 * (ty + tu)
-            tsrc = f"{sy}; {su}"
+            fy = _algorithmic("block_y", m, n, m_aug, nb, 1, args.refine, 4, blocked)[1]
+            fu = _algorithmic("block_u", m, n, m_aug, nb, 1, args.refine, 4, blocked)[1]
+            traffic = (ty * fy + tu * fu) / max(1, _block_launches(n, 1))
+            tsrc = f"ncu DRAM bytes per bf16 tensor flop on {sy}, scaled to this workload's launches"
     roofline = {"kernel": "+".join(tc_classes), "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
                 "launches": tc_launches, "avg_launch_us": 1e3 * tc_ms / max(1, tc_launches),

@@ -9,7 +9,7 @@
  * [A_pde; lambda A_bc] beta = [f; lambda g] (Sec. 2.3, eq. linear_system,
  * Alg. 1); a nonlinear one is solved by Newton-Raphson with Tikhonov-regularised
  * least-squares steps (Sec. 2.4, eq. newton); gradients flow through the
- * pre-factored solve (Sec. 2.5, Sec. 4.4).
+ * pre-factored solve (Sec. 2.5, Sec. 3.8).
  *
  * Conventions for every entry point:
  *  - All array arguments are DEVICE pointers on the context's device unless the
@@ -87,7 +87,7 @@ typedef enum { FASTLSQ_REFINE_CLASSICAL = 0, FASTLSQ_REFINE_CGLS = 1 } fastlsq_r
  * double array of n_rows entries (the rows of this call).  This is how the
  * Newton Jacobian's N'(u_i) phi_j enters (eq. newton), and how a variable-
  * coefficient operator such as div(nu grad u) = nu Lap u + grad nu . grad u
- * (Sec. 4.4, coil localisation) is written: 2d per-point terms with coefficients
+ * (Sec. 3.8, coil localisation) is written: 2d per-point terms with coefficients
  * nu(x_i) on D^{2e_k} and d nu/dx_k(x_i) on D^{e_k}. */
 typedef struct {
     int32_t d;
@@ -157,7 +157,7 @@ typedef enum {
                                        /* Allen-Cahn; f = 0), u* = tanh((x - 1/2) / sqrt(2 eps))     */
     FASTLSQ_PROBLEM_BURGERS_1D = 9,    /* u u' - nu u'' = 0 on [0,1], params[0] = nu (Sec. 3.3 steady */
                                        /* Burgers; f = 0), u* = -tanh((x - 1/2) / (2 nu))            */
-    FASTLSQ_PROBLEM_VARCOEF_2D = 10,   /* div(nu grad u) = f on [0,1]^2 (Sec. 4.4's variable-          */
+    FASTLSQ_PROBLEM_VARCOEF_2D = 10,   /* div(nu grad u) = f on [0,1]^2 (Sec. 3.8's variable-          */
                                        /* coefficient form), nu = 1 + a (x^2 + y^2/2), params[0] = a, */
                                        /* u* = sin(pi x) sin(2 pi y) + x y; kinds COEF / COEF_GRAD    */
                                        /* give nu and its gradient at points                           */
@@ -221,10 +221,13 @@ FASTLSQ_API int fastlsq_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, 
  * request is larger.  Nothing in the array needs to start at zero: every entry a
  * call reads was written earlier in the same call.
  *
- * The array's device address is looked up with cudaGetSymbolAddress on the first
- * call on each device (with the context's device made current for the lookup, and
- * the caller's device restored after it); make that first call before any stream
- * capture begins.  There is one array per device for the whole process: two calls whose
+ * The array's device address is looked up with cudaGetSymbolAddress when the context
+ * is created (fastlsq_create, with the context's device current); that lookup also
+ * loads the library's device code, so the array is committed at context creation, not
+ * at the first call: create the context before reserving the rest of the device's
+ * memory.  A context does not outlive a device reset (create a new one after
+ * cudaDeviceReset; it looks the array up again).  n_feat above 16384 returns
+ * FASTLSQ_ERR_INVALID like fastlsq_eval.  There is one array per device for the whole process: two calls whose
  * executions can overlap (different streams, host threads or contexts on the same
  * device) use the same scratch and give wrong results.  Serialise them.
  */
@@ -233,7 +236,7 @@ FASTLSQ_API int fastlsq_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t 
                          const double *beta, double *u);
 
 /*
- * Adjoint of fastlsq_eval (the sensor readout u_s = H_s beta of Sec. 4.4):
+ * Adjoint of fastlsq_eval (the sensor readout u_s = H_s beta of Sec. 3.8):
  * grad_beta[j] = scale * sum_e g[e] sin(W_j.x_e + b_j), FP64.  x: [n_eval][d],
  * g: [n_eval], grad_beta: [n_feat].
  */
@@ -280,7 +283,7 @@ FASTLSQ_API int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec,
                   fastlsq_factor **keep, fastlsq_solve_stats *stats);
 
 /* Solve again with checkpointed factors for new right-hand sides (the paper's
- * matrix caching, App. F.4): beta = R^{-1} Q^T [rhs; 0], refined as in
+ * matrix caching, App. G.5): beta = R^{-1} Q^T [rhs; 0], refined as in
  * fastlsq_lstsq when the factor is MIXED and was given A_refine. */
 FASTLSQ_API int fastlsq_factor_solve(fastlsq_ctx *ctx, const fastlsq_factor *f,
                          const double *rhs, int32_t nrhs, int64_t ld_rhs,
@@ -304,15 +307,17 @@ FASTLSQ_API int fastlsq_factor_destroy(fastlsq_factor *f);
 
 /*
  * Adjoint of the regularised solve beta = (A^T A + mu I)^{-1} A^T rhs
- * (Sec. 2.5; Sec. 4.4: "each evaluation costs two triangular back-substitutions"),
+ * (Sec. 2.5; Sec. 3.8: "each evaluation costs two triangular back-substitutions"),
  * with R^T R = A^T A + mu I from the checkpointed factor:
  *   v = R^{-1} R^{-T} grad_beta                      (n_feat, double, out)
  *   grad_rhs = A v                                   (n_rows, double, out; NULL to skip)
  * A_op is the FP64 operator (n_rows x n_feat, ld) used for A v; NULL uses the
- * factor's A_refine.  For a MIXED factor, max_iter > 0 refines v by
- * preconditioned CG on (A^T A + mu I) v = grad_beta with FP64 operator products
- * (M = R^T R), up to max_iter iterations or a residual reduction by tol; this
- * needs the factor's A_refine.  Loss gradients with respect to a source parameter theta
+ * factor's A_refine.  max_iter > 0 (either factor) computes v by preconditioned
+ * CG on (A^T A + mu I) v = grad_beta with FP64 operator products (M = R^T R), up to
+ * max_iter iterations or a residual reduction by tol; this needs the factor's
+ * A_refine (for an FP64 factor, the operator it was factored from).  max_iter = 0
+ * applies the two substitutions alone, whose relative error grows like
+ * kappa(R)^2 times the factor's rounding unit.  Loss gradients with respect to a source parameter theta
  * follow as sum_i grad_rhs[i] d rhs_i / d theta (fastlsq_source_grad), and with
  * respect to operator coefficients from fastlsq_coef_grad.
  */
@@ -342,7 +347,7 @@ FASTLSQ_API int fastlsq_coef_grad(fastlsq_ctx *ctx, const double *x, int64_t n_r
                       const double *r, const double *Av, const double *v,
                       const double *beta, double *grad);
 
-/* One instance of the steady inverse heat-source problem (Sec. 4.4, App. F.2 in
+/* One instance of the steady inverse heat-source problem (Sec. 3.8, App. G.2 in
  * steady form): -L u = s(x; theta) in the domain (interior operator from the
  * batch call), u = 0 on the boundary rows, sensors u_s = u(x_s), loss
  * L = mean_s (u_s - y_s)^2.  All pointers are DEVICE pointers. */
@@ -372,7 +377,7 @@ typedef struct {
 
 /*
  * Loss and gradient dL/dtheta for a batch of instances of uneven size (the
- * differentiable solve of Sec. 2.5 applied to the inverse problem of Sec. 4.4):
+ * differentiable solve of Sec. 2.5 applied to the inverse problem of Sec. 3.8):
  * per instance, assemble the operator (FP64, plus FP32 for a MIXED factor),
  * factor it, solve for beta with the source s(x; theta), read the sensors, form
  * the loss, and run the adjoint: grad_beta = H_s^T dL/du_s,
@@ -387,7 +392,7 @@ FASTLSQ_API int fastlsq_inverse_batch(fastlsq_ctx *ctx, const fastlsq_inverse_in
                                       const fastlsq_inverse_opts *opts);
 
 /*
- * Pre-factored batch of inverse-problem instances (Sec. 4.4: the operator is factored
+ * Pre-factored batch of inverse-problem instances (Sec. 3.8: the operator is factored
  * once and every evaluation of the forward map and its gradient reuses the factor,
  * two triangular solves per evaluation; Sec. 2.5: gradients through the solve).
  *
@@ -539,6 +544,20 @@ FASTLSQ_API int fastlsq_newton_continuation(fastlsq_ctx *ctx, const fastlsq_newt
                    const fastlsq_newton_opts *opts, int32_t n_stages,
                    const double *stage_coef, double *beta_inout,
                    fastlsq_newton_stats *stats);
+
+/*
+ * Self-test of the bounded device waits (failure detection; the paper has no
+ * counterpart).  Launches, on the context's stream, a kernel whose wait never
+ * completes: which = 0, an mbarrier wait like those of the tensor-core kernels on a
+ * barrier nobody arrives on (one CTA); which = 1, the grid barrier of the cooperative
+ * kernels with one of its two CTAs leaving without arriving.  After budget_cycles SM
+ * clock cycles (0 .. 4e9; the library's own waits use about 2e9, a second) the waiting
+ * thread raises the context's device error flag and the kernel returns: the next
+ * fastlsq_sync returns FASTLSQ_ERR_TIMEOUT, clears the flag and resets the grid
+ * barrier, and the context stays usable.  Returns 0 once queued, -1 for other
+ * arguments, -3 if the launch fails.
+ */
+FASTLSQ_API int fastlsq_selftest_wait(fastlsq_ctx *ctx, int32_t which, int64_t budget_cycles);
 
 /* Context options for fastlsq_set_option. */
 typedef enum {

@@ -259,7 +259,7 @@ def newton(x_int, x_bc, alpha, coef, nl_kind, nl_lam, bc_weight, f, g, W, b, sca
 
 
 def inverse_adjoint(A, rhs, Hs, y_obs, mu):
-    """Forward map + adjoint of Sec. 4.4 (orc_inverse_adjoint).  Returns a dict."""
+    """Forward map + adjoint of Sec. 3.8 (orc_inverse_adjoint).  Returns a dict."""
     lib = _load()
     A = np.asfortranarray(A, dtype=np.float64)
     m, n = A.shape

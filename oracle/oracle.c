@@ -199,7 +199,7 @@ void orc_forwardsolve_rt(const double *QR, long n, long lda, double *y)
 
 /* Build the Tikhonov-augmented matrix [A; sqrt(mu) I] ((m + n) x n when mu > 0,
  * else a copy of A) as used for the regularised solves of Sec. 2.4 and the
- * inverse-problem forward map beta = (A^T A + mu I)^{-1} A^T f of Sec. 4.4. */
+ * inverse-problem forward map beta = (A^T A + mu I)^{-1} A^T f of Sec. 3.8. */
 static double *orc_augment(const double *A, long m, long n, long lda, double mu,
                            long *m_aug)
 {
@@ -261,7 +261,7 @@ enum {
     ORC_ALLEN_CAHN_1D = 8, /* eps u'' + u - u^3 = 0; params[0] = eps;                          */
                            /* u* = tanh((x - 1/2) / sqrt(2 eps))                                */
     ORC_BURGERS_1D = 9,    /* u u' - nu u'' = 0; params[0] = nu; u* = -tanh((x - 1/2) / (2 nu))  */
-    /* the variable-coefficient form of Sec. 4.4 (div(nu grad u), expanded as             */
+    /* the variable-coefficient form of Sec. 3.8 (div(nu grad u), expanded as             */
     /* nu Lap u + grad nu . grad u), with a manufactured u*:                              */
     ORC_VARCOEF_2D = 10    /* div(nu grad u) = f on [0,1]^2, nu = 1 + a (x^2 + y^2/2),           */
                            /* params[0] = a; u* = sin(pi x) sin(2 pi y) + x y                    */
@@ -560,7 +560,7 @@ done:
 }
 
 /* ------------------------------------------------------------------------- */
-/* Differentiable solve and its adjoint (Sec. 2.5; Sec. 4.4 inverse heat      */
+/* Differentiable solve and its adjoint (Sec. 2.5; Sec. 3.8 inverse heat      */
 /* source: beta = (A^T A + mu I)^{-1} A^T f with a pre-factored matrix).      */
 /* ------------------------------------------------------------------------- */
 

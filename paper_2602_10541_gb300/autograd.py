@@ -1,5 +1,5 @@
 """torch.autograd.Function wrappers over the C ABI (Sec. 2.5: gradients flow through
-the pre-factored solve; Sec. 4.4: each evaluation costs two triangular solves).
+the pre-factored solve; Sec. 3.8: each evaluation costs two triangular solves).
 
 ``Factorization`` checkpoints the QR factors of the operator once;
 ``solve(rhs)`` is beta = R^{-1} Q^T [rhs; 0] and its backward is

@@ -1,4 +1,4 @@
-// Adjoint pieces of the differentiable solve (Sec. 2.5; Sec. 4.4): the FP64
+// Adjoint pieces of the differentiable solve (Sec. 2.5; Sec. 3.8): the FP64
 // product A v, and the on-the-fly contraction that gives gradients with respect
 // to operator coefficients,
 //   dL/dc_t = sum_ij (r_i v_j - (A v)_i beta_j) * s * D^{alpha_t} phi_j(x_i),

@@ -15,6 +15,7 @@ int fl_launch_eval_op(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, 
                       const double *b, int64_t n_feat, const double *pref, const double *beta, double *u);
 int fl_launch_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, const double *W,
                            const double *b, int64_t n_feat, double scale, const double *beta, double *u);
+cudaError_t fl_eval_static_lookup(double **out);
 int fl_launch_eval_adjoint(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d,
                            const double *W, const double *b, int64_t n_feat, double scale,
                            const double *g, double *grad);
@@ -142,6 +143,10 @@ extern "C" int fastlsq_create(fastlsq_ctx **out, int device, void *stream)
         e = cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
+    // the address of fastlsq_eval_noalloc's fixed scratch in this device's context (this
+    // also loads the library's device code now, so the array is committed here and a
+    // context created after a device reset gets the array's new address)
+    if (e == cudaSuccess) e = fl_eval_static_lookup(&ctx->eval_static);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_grid_bar, 64);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_grid_bar, 0, 64, ctx->stream);
     if (e == cudaSuccess) {
@@ -417,7 +422,7 @@ extern "C" int fastlsq_eval(fastlsq_ctx *ctx, const double *x, int64_t n_eval, i
                             const double *beta, double *u)
 {
     if (!ctx) return FASTLSQ_ERR_INVALID;
-    if (n_eval < 0 || n_feat < 1 || d < 1 || d > FL_MAX_D)
+    if (n_eval < 0 || n_feat < 1 || n_feat > FL_MAX_FEAT || d < 1 || d > FL_MAX_D)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval: bad sizes");
     if (n_eval == 0) return 0;
     if (!x || !W || !b || !beta || !u) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval: null array");
@@ -429,7 +434,7 @@ extern "C" int fastlsq_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t n
                                     const double *beta, double *u)
 {
     if (!ctx) return FASTLSQ_ERR_INVALID;
-    if (n_eval < 0 || n_feat < 1 || d < 1 || d > FL_MAX_D)
+    if (n_eval < 0 || n_feat < 1 || n_feat > FL_MAX_FEAT || d < 1 || d > FL_MAX_D)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval_noalloc: bad sizes");
     if (n_eval == 0) return 0;
     if (!x || !W || !b || !beta || !u) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval_noalloc: null array");
@@ -596,7 +601,7 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
     f->ld_refine = (prec == FASTLSQ_PREC_MIXED || A_refine) ? ld_refine : ldA;
     // TF32x3 products carry about 2^-22 relative per product, FP32 FMAs 2^-24: where the
     // factor preconditions CGLS (systems with kappa near 1 / eps32), the FP32 update keeps
-    // A R^{-1} well conditioned (measured on Sec. 4.4 instances: cond 2-11 vs 10-170), so
+    // A R^{-1} well conditioned (measured on Sec. 3.8 instances: cond 2-11 vs 10-170), so
     // the panel-by-panel TF32x3 mode serves classically refined factors only; the blocked
     // mode's three-part bf16 products are FP32-accurate and serve both
     f->tensor_core = 0;
@@ -712,12 +717,14 @@ extern "C" int fastlsq_backward(fastlsq_ctx *ctx, const fastlsq_factor *f, const
 {
     if (!ctx || !f || !grad_beta || !v) return FASTLSQ_ERR_INVALID;
     if (max_iter < 0 || max_iter > 64) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "backward: max_iter 0..64");
-    if (f->prec == FASTLSQ_PREC_FP64) {
-        FL_TRY(backward_t<double>(ctx, f, grad_beta, v));
-    } else if (max_iter > 0) {
+    // max_iter > 0: PCG on the normal equations with FP64 operator products, for either
+    // factor (the two substitutions alone carry about kappa(R)^2 eps of the factor's type)
+    if (max_iter > 0) {
         if (!f->A_refine) return fl_fail(ctx, FASTLSQ_ERR_INVALID, "backward: PCG needs the FP64 operator");
         FL_TRY(wait_refine(ctx));
         FL_TRY(fl_normal_pcg(ctx, f, grad_beta, v, max_iter, tol));
+    } else if (f->prec == FASTLSQ_PREC_FP64) {
+        FL_TRY(backward_t<double>(ctx, f, grad_beta, v));
     } else {
         FL_TRY(backward_t<float>(ctx, f, grad_beta, v));
     }

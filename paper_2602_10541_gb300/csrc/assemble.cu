@@ -597,10 +597,21 @@ int fl_launch_eval_op(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, 
 // fastlsq_eval_noalloc: the evaluation of fastlsq_eval with its partial sums in a
 // fixed device array of this library instead of the context's workspace, so the
 // call allocates nothing.  The array is shared by every context on a device; its
-// address is looked up once per device.
+// address is looked up by fastlsq_create (fl_eval_static_lookup), with the context's
+// device current, and kept in the context.
 // ---------------------------------------------------------------------------
 constexpr size_t FL_EVAL_STATIC_DOUBLES = (size_t)1 << 19;      // 4 MiB of FP64 partial sums
 static __device__ __align__(256) double g_eval_static[FL_EVAL_STATIC_DOUBLES];
+
+// The device address of the array in the current device's context.  Looking it up
+// loads this library's device code (and commits the array) if that has not happened.
+cudaError_t fl_eval_static_lookup(double **out)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_eval_static);
+    *out = (e == cudaSuccess) ? (double *)p : nullptr;
+    return e;
+}
 
 int fl_launch_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t n_eval, int d, const double *W,
                            const double *b, int64_t n_feat, double scale, const double *beta, double *u)
@@ -611,26 +622,8 @@ int fl_launch_eval_noalloc(fastlsq_ctx *ctx, const double *x, int64_t n_eval, in
         return fl_fail(ctx, FASTLSQ_ERR_INVALID,
                        "eval_noalloc: ceil(n_feat/%d) * n_eval = %lld exceeds the %lld-entry static scratch",
                        EVAL_SPLIT_COLS, (long long)(nsplit * n_eval), (long long)FL_EVAL_STATIC_DOUBLES);
-    // the array's device address, per device ordinal; racing first calls store the same value
-    static std::atomic<double *> addr[64];
-    if (ctx->device < 0 || ctx->device >= 64)
-        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "eval_noalloc: device ordinal %d", ctx->device);
-    double *part = addr[ctx->device].load(std::memory_order_acquire);
-    if (!part) {
-        // the symbol's address is per device: look it up with the context's device current,
-        // then give the calling thread its own device back
-        int cur = -1;
-        cudaError_t e = cudaGetDevice(&cur);
-        if (e != cudaSuccess) return fl_cuda(ctx, e, "eval_noalloc: current device");
-        if (cur != ctx->device && (e = cudaSetDevice(ctx->device)) != cudaSuccess)
-            return fl_cuda(ctx, e, "eval_noalloc: select the context's device");
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_eval_static);
-        if (cur != ctx->device) cudaSetDevice(cur);
-        if (e != cudaSuccess) return fl_cuda(ctx, e, "eval_noalloc: scratch address");
-        part = (double *)p;
-        addr[ctx->device].store(part, std::memory_order_release);
-    }
+    double *part = ctx->eval_static;
+    if (!part) return fl_fail(ctx, FASTLSQ_ERR_CUDA, "eval_noalloc: the scratch address was not found");
     dim3 grid((unsigned)fl_cdiv(n_eval, 128), (unsigned)nsplit);
     FL_PROF_N(ctx, FASTLSQ_K_EVAL, 2);
     k_eval_partial<<<grid, 128, 0, ctx->stream>>>(x, n_eval, d, W, b, n_feat, beta, part);

@@ -103,6 +103,7 @@ struct fastlsq_ctx {
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t refine_event = nullptr;   // waited on before reads of A_refine (caller's)
+    double *eval_static = nullptr;  // device address of fastlsq_eval_noalloc's fixed scratch
     // Cody-Waite split of 2 pi for the FP32 argument reduction (host-derived)
     float cw2pi[3] = {0.f, 0.f, 0.f};
     fl_prof_state prof;

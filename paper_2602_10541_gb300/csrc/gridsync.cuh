@@ -14,7 +14,7 @@ struct GridBar {
 constexpr long long BAR_SPIN_CLOCKS = 2000000000ll;
 
 __device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned nblocks, int *flag,
-                                          volatile int *s_abort)
+                                          volatile int *s_abort, long long spin_clocks = BAR_SPIN_CLOCKS)
 {
     __syncthreads();
     if (threadIdx.x == 0 && !*s_abort) {
@@ -29,7 +29,7 @@ __device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned nblocks, int *f
         } else {
             const long long t0 = clock64();
             while (*vgen == g) {
-                if (clock64() - t0 > BAR_SPIN_CLOCKS) {
+                if (clock64() - t0 > spin_clocks) {
                     atomicCAS(flag, 0, FL_DEVERR_TIMEOUT);
                     *s_abort = 1;
                     break;

@@ -1,4 +1,4 @@
-// Batched inverse problem (Sec. 4.4 in steady form, Sec. 2.5): loss and dL/dtheta
+// Batched inverse problem (Sec. 3.8 in steady form, Sec. 2.5): loss and dL/dtheta
 // for many instances of uneven size, queued on one stream with no host round trip.
 #include <algorithm>
 #include <cmath>

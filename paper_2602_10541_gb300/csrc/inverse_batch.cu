@@ -1,4 +1,4 @@
-// Batched inverse problem with pre-factored operators (Sec. 4.4 in steady form;
+// Batched inverse problem with pre-factored operators (Sec. 3.8 in steady form;
 // Sec. 2.5: gradients through the pre-factored solve, two triangular solves per
 // evaluation): many instances of uneven size, every gradient evaluation of the whole
 // batch in ONE persistent launch.

@@ -8,7 +8,7 @@
 //    Converges to the FP64 least-squares solution also when the residual is large
 //    or kappa(A) eps32 > 1, where classical refinement stagnates.
 //  * fl_normal_pcg: preconditioned CG on (A~^T A~) v = c with M = R^T R; this is
-//    the adjoint solve v = (A^T A + mu I)^{-1} grad_beta of Sec. 2.5 / Sec. 4.4.
+//    the adjoint solve v = (A^T A + mu I)^{-1} grad_beta of Sec. 2.5 / Sec. 3.8.
 //
 // Every kernel reads a device flag and returns at once after convergence, so a
 // fixed number of launches can be queued (and captured in a CUDA graph) without

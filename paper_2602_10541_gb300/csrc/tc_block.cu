@@ -96,42 +96,32 @@ __device__ __forceinline__ void bt_arrive(uint64_t *bar)
 
 // Operand tiles are K-major with 128-byte rows (64 bf16 along K) in the 128-byte
 // swizzle: element (row, kk) sits at row * 128 + (((kk / 8) ^ (row % 8)) * 16) + 2 (kk % 8).
-// three-part bf16 split of one fp32 value
-__device__ __forceinline__ void split3(float x, __nv_bfloat16 &a, __nv_bfloat16 &b, __nv_bfloat16 &c)
+// three-part split of two fp32 values with paired conversions (one cvt per pair and part)
+__device__ __forceinline__ void split3x2(float x, float y, uint32_t &a, uint32_t &b, uint32_t &c)
 {
-    a = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(a);
-    b = __float2bfloat16_rn(r1);
-    c = __float2bfloat16_rn(r1 - __bfloat162float(b));
-}
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
-{
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);              // .x = x (low half)
+    const float rx = x - __low2float(h), ry = y - __high2float(h);
+    const __nv_bfloat162 m = __floats2bfloat162_rn(rx, ry);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(rx - __low2float(m), ry - __high2float(m));
+    a = *reinterpret_cast<const uint32_t *>(&h);
+    b = *reinterpret_cast<const uint32_t *>(&m);
+    c = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 // 4 consecutive K elements -> three parts of 8 bytes each
 __device__ __forceinline__ void split4(float4 v, uint2 (&p)[3])
 {
-    __nv_bfloat16 a[4], b[4], c[4];
-    split3(v.x, a[0], b[0], c[0]);
-    split3(v.y, a[1], b[1], c[1]);
-    split3(v.z, a[2], b[2], c[2]);
-    split3(v.w, a[3], b[3], c[3]);
-    p[0] = make_uint2(pack2(a[0], a[1]), pack2(a[2], a[3]));
-    p[1] = make_uint2(pack2(b[0], b[1]), pack2(b[2], b[3]));
-    p[2] = make_uint2(pack2(c[0], c[1]), pack2(c[2], c[3]));
+    split3x2(v.x, v.y, p[0].x, p[1].x, p[2].x);
+    split3x2(v.z, v.w, p[0].y, p[1].y, p[2].y);
 }
 
 // 8 consecutive K elements -> three parts of 16 bytes each
 __device__ __forceinline__ void split8(const float (&v)[8], uint4 (&p)[3])
 {
-    __nv_bfloat16 a[8], b[8], c[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) split3(v[e], a[e], b[e], c[e]);
-    p[0] = make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]), pack2(a[6], a[7]));
-    p[1] = make_uint4(pack2(b[0], b[1]), pack2(b[2], b[3]), pack2(b[4], b[5]), pack2(b[6], b[7]));
-    p[2] = make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), pack2(c[6], c[7]));
+    split3x2(v[0], v[1], p[0].x, p[1].x, p[2].x);
+    split3x2(v[2], v[3], p[0].y, p[1].y, p[2].y);
+    split3x2(v[4], v[5], p[0].z, p[1].z, p[2].z);
+    split3x2(v[6], v[7], p[0].w, p[1].w, p[2].w);
 }
 
 // V(i, l) of the block: unit lower trapezoid, zero past the block's nbk columns
@@ -204,13 +194,13 @@ k_bimg(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, 
 // CTA (j, s): columns e in [128 j, 128 j + 128), the 64-row chunks s, s + S, ...
 // Roles: warp 0 bulk-loads the VY chunk (A operand, three parts), warps 2..9 load the
 // X chunk from F one chunk ahead, split it and store the three B parts, warp 1 issues
-// the 24 MMAs of the chunk and commits them to the stage's "empty" barrier and to the
-// chunk's accumulator.  The five small products accumulate over the whole split in one
-// TMEM accumulator; each chunk's leading products go to a fresh TMEM accumulator (three
-// buffers in turn) that warps 2..9 add into FP32 registers two chunks behind the MMAs,
-// so the long sum of the leading products over the split's rows is taken with
-// round-to-nearest adds while the tensor core sums 64 rows at a time, and the adds
-// stay off the MMAs' path.  (Measured: sharing one accumulator between the leading and
+// the 24 MMAs of the chunk, commits each 32-row half to that half's accumulator and the
+// whole chunk to the stage's "empty" barrier.  The five small products accumulate over
+// the whole split in one TMEM accumulator; each half-chunk's leading products go to a
+// fresh TMEM accumulator (three buffers in turn) that warps 2..9 add into FP32
+// registers one chunk behind the MMAs, so the long sum of the leading products over
+// the split's rows is taken with round-to-nearest adds while the tensor core sums only
+// 32 rows at a time, and the adds stay off the MMAs' path.  (Measured: sharing one accumulator between the leading and
 // the small products, even for 64 rows, made R a worse CGLS preconditioner.)
 // ---------------------------------------------------------------------------
 constexpr int BY_NBUF = 3;             // leading-product accumulators in TMEM (plus the small one)
@@ -252,7 +242,7 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     // TMEM columns: [0, 128) the small products of the split, [128 + 128 b, 256 + 128 b)
-    // the leading products of chunk buffer b
+    // the leading products of half-chunk buffer b
     const uint32_t tsmall = tmem;
 
     if (warp == 0) {
@@ -272,19 +262,16 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16(BK, BY_N);
-            for (int ch = 0; ch < nloc; ++ch) {
-                const int s = ch & 1, b = ch % BY_NBUF;
+            for (int ch = 0; ch < nloc && !s_fail; ++ch) {
+                const int s = ch & 1;
                 if (!tc::mbar_wait(&fullA[s], (uint32_t)(ch >> 1) & 1u, BT_SPIN) ||
-                    !tc::mbar_wait(&fullB[s], (uint32_t)(ch >> 1) & 1u, BT_SPIN) ||
-                    (ch >= BY_NBUF &&
-                     !tc::mbar_wait(&acce[b], (uint32_t)((ch - BY_NBUF) / BY_NBUF) & 1u, BT_SPIN))) {
+                    !tc::mbar_wait(&fullB[s], (uint32_t)(ch >> 1) & 1u, BT_SPIN)) {
                     s_fail = 1;
                     break;
                 }
                 if (s_fail) break;
                 tc::fence_after_sync();
                 const unsigned char *A = base + s * BY_STAGE, *B = A + VY_CHUNK;
-                const uint32_t dbig = tmem + (uint32_t)(BY_N + BY_N * b);
                 uint64_t dA[3], dB[3];
 #pragma unroll
                 for (int p = 0; p < 3; ++p) {
@@ -292,18 +279,33 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
                     dB[p] = tc::smem_desc_sw128(B + p * PART128);
                 }
 #pragma unroll
-                for (int ks = 0; ks < BY_KC / 16; ++ks) {
-                    const uint64_t o = (uint64_t)(ks * 32) >> 4;       // 16 bf16 = 32 bytes along K
-                    tc::mma_bf16(dbig, dA[0] + o, dB[0] + o, idesc, ks > 0 ? 1u : 0u);
-                    tc::mma_bf16(tsmall, dA[0] + o, dB[1] + o, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
-                    tc::mma_bf16(tsmall, dA[1] + o, dB[0] + o, idesc, 1u);
-                    tc::mma_bf16(tsmall, dA[0] + o, dB[2] + o, idesc, 1u);
-                    tc::mma_bf16(tsmall, dA[2] + o, dB[0] + o, idesc, 1u);
-                    tc::mma_bf16(tsmall, dA[1] + o, dB[1] + o, idesc, 1u);
+                for (int hh = 0; hh < 2; ++hh) {
+                    // half-chunk hc: rows [32 hh, 32 hh + 32) of the chunk, its leading
+                    // products into buffer hc mod 3 once the converters have drained it
+                    const int hc = 2 * ch + hh, b = hc % BY_NBUF;
+                    if (hc >= BY_NBUF &&
+                        !tc::mbar_wait(&acce[b], (uint32_t)((hc - BY_NBUF) / BY_NBUF) & 1u, BT_SPIN)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t dbig = tmem + (uint32_t)(BY_N + BY_N * b);
+#pragma unroll
+                    for (int kk = 0; kk < BY_KC / 32; ++kk) {
+                        const int ks = (BY_KC / 32) * hh + kk;
+                        const uint64_t o = (uint64_t)(ks * 32) >> 4;   // 16 bf16 = 32 bytes along K
+                        tc::mma_bf16(dbig, dA[0] + o, dB[0] + o, idesc, kk > 0 ? 1u : 0u);
+                        tc::mma_bf16(tsmall, dA[0] + o, dB[1] + o, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
+                        tc::mma_bf16(tsmall, dA[1] + o, dB[0] + o, idesc, 1u);
+                        tc::mma_bf16(tsmall, dA[0] + o, dB[2] + o, idesc, 1u);
+                        tc::mma_bf16(tsmall, dA[2] + o, dB[0] + o, idesc, 1u);
+                        tc::mma_bf16(tsmall, dA[1] + o, dB[1] + o, idesc, 1u);
+                    }
+                    tc::mma_commit(&accf[b]);
+                    s_last_commit = hc;
                 }
+                if (s_fail) break;
                 tc::mma_commit(&empty[s]);
-                tc::mma_commit(&accf[b]);
-                s_last_commit = ch;
             }
         }
     } else {
@@ -334,10 +336,10 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
                 x[u] = v;
             }
         };
-        // y += leading products of chunk c
-        auto drain = [&](int c) -> bool {
-            const int b = c % BY_NBUF;
-            if (!tc::mbar_wait(&accf[b], (uint32_t)(c / BY_NBUF) & 1u, BT_SPIN)) return false;
+        // y += leading products of half-chunk hc
+        auto drain = [&](int hc) -> bool {
+            const int b = hc % BY_NBUF;
+            if (!tc::mbar_wait(&accf[b], (uint32_t)(hc / BY_NBUF) & 1u, BT_SPIN)) return false;
             tc::fence_after_sync();
 #pragma unroll
             for (int rd = 0; rd < 2; ++rd) {
@@ -380,13 +382,12 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
             __syncwarp();
             if (lane == 0) bt_arrive(&fullB[s]);
             if (ch + 1 < nloc) load(ch + 1);
-            if (ch >= 2 && !drain(ch - 2)) {
+            if (ch >= 1 && (!drain(2 * ch - 2) || !drain(2 * ch - 1))) {
                 s_fail = 1;
                 break;
             }
         }
-        for (int c = nloc - 2; c < nloc && !s_fail; ++c)
-            if (c >= 0 && !drain(c)) s_fail = 1;
+        if (nloc > 0 && !s_fail && (!drain(2 * nloc - 2) || !drain(2 * nloc - 1))) s_fail = 1;
         __syncwarp();
         if (!s_fail) {
             // the small products of the whole split (every MMA has completed: the last

@@ -30,10 +30,11 @@ __device__ __forceinline__ void trail_finish_z(const T *__restrict__ Ypart, int 
     T acc[ITEMS];
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) acc[it] = T(0);
-    // splits in groups of 4 so that 4 x ITEMS independent loads are in flight per round;
-    // the additions keep the split order
+    // splits in groups of 8 so that 8 x ITEMS independent loads are in flight per round
+    // (a narrow update split over ~150 row ranges waits on few rounds); the additions
+    // keep the split order
     int sp = 0;
-    for (; sp + 4 <= nsplit; sp += 4) {
+    for (; sp + 8 <= nsplit; sp += 8) {
 #pragma unroll
         for (int it = 0; it < ITEMS; ++it) {
             const int idx = it * THREADS + threadIdx.x;
@@ -42,8 +43,11 @@ __device__ __forceinline__ void trail_finish_z(const T *__restrict__ Ypart, int 
             if (c < nct) {
                 const T *src = Ypart + ((int64_t)sp * NB + l) * nct + c;
                 const int64_t st = (int64_t)NB * nct;
-                const T a0 = __ldcg(src), a1 = __ldcg(src + st), a2 = __ldcg(src + 2 * st), a3 = __ldcg(src + 3 * st);
-                acc[it] = (((acc[it] + a0) + a1) + a2) + a3;
+                T a[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) a[q] = __ldcg(src + q * st);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[it] += a[q];
             }
         }
     }

@@ -117,6 +117,7 @@ _SIGNATURES = {
                                 ctypes.POINTER(_vp)],
     "fastlsq_inverse_eval": [_vp, _vp, _i32, _i32],
     "fastlsq_inverse_plan_destroy": [_vp],
+    "fastlsq_selftest_wait": [_vp, _i32, _i64],
     "fastlsq_profile_enable": [_vp, ctypes.c_int],
     "fastlsq_profile_read": [_vp, ctypes.c_int, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)],
 }
@@ -439,6 +440,11 @@ def fastlsq_profile_read(ctx):
         ctx.check(ctx.lib.fastlsq_profile_read(ctx.handle, k, ctypes.byref(n), ctypes.byref(ms)))
         out[name] = (int(n.value), float(ms.value))
     return out
+
+
+def fastlsq_selftest_wait(ctx, which, budget_cycles):
+    """Queue a kernel whose bounded wait (0: mbarrier, 1: grid barrier) runs out."""
+    return ctx.check(ctx.lib.fastlsq_selftest_wait(ctx.handle, which, int(budget_cycles)))
 
 
 def fastlsq_sync(ctx):

@@ -1,4 +1,4 @@
-"""Compose the C-ABI calls into the paper's pipelines (Alg. 1; Sec. 2.4; Sec. 4.4).
+"""Compose the C-ABI calls into the paper's pipelines (Alg. 1; Sec. 2.4; Sec. 3.8).
 
 Orchestration only: every number is produced by libfastlsq kernels through the
 binding in ``fastlsq.py``.  Used by the tests, ``bench.py`` and the smoke check.
@@ -111,7 +111,8 @@ class LinearSolver:
         try:
             rc, fac, st = fl.fastlsq_lstsq(self.ctx, self.prec, A, self.m, self.mu, self.rhs, self.beta,
                                            A_refine=self.A64,
-                                           max_refine=self.max_refine if self.prec == fl.PREC_MIXED else 0,
+                                           max_refine=(self.max_refine if self.prec == fl.PREC_MIXED
+                                                       or self.refine_mode == fl.REFINE_CGLS else 0),
                                            keep=keep, stats=stats, refine_mode=self.refine_mode,
                                            refine_tol=self.refine_tol)
         finally:
@@ -216,7 +217,7 @@ def tuned(kernel: str, default: dict) -> dict:
 
 
 class InverseBatch:
-    """Instances of the batched inverse heat-source problem (Sec. 4.4, steady form) on
+    """Instances of the batched inverse heat-source problem (Sec. 3.8, steady form) on
     the GPU behind one pre-factored plan: setup factors every operator once (FP64),
     each evaluation is one persistent launch over all instances (loss, beta, dL/dtheta
     per instance).  Observations come from the forward map at the instances' true
@@ -290,26 +291,52 @@ def rel_l2(a, b) -> float:
 def main(argv=None):
     """Command line: run a few linear solves of a named workload and print the error
     of the last one on the test set, e.g. as the program under a profiler:
-    ``python -m paper_2602_10541_gb300.pipeline helmholtz2d --prec mixed --steps 2``."""
+    ``python -m paper_2602_10541_gb300.pipeline helmholtz2d --prec mixed --steps 2``;
+    ``... random --rows 36864 --cols 256`` factors a random MIXED matrix of that shape;
+    ``... inverse --instances 16`` runs gradient evaluations of a batch of inverse-problem
+    instances."""
     import argparse
 
     from . import workloads as wl
 
     ap = argparse.ArgumentParser(prog="python -m paper_2602_10541_gb300.pipeline")
-    ap.add_argument("workload", choices=["poisson1d", "helmholtz2d", "poisson5d"])
+    ap.add_argument("workload", choices=["poisson1d", "helmholtz2d", "poisson5d", "random", "inverse"])
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--refine", type=int, default=2)
     ap.add_argument("--refine-mode", choices=["classical", "cgls"], default="classical")
-    ap.add_argument("--tensor-core", action="store_true",
-                    help="tcgen05 trailing updates (MIXED; the default)")
-    ap.add_argument("--simt", action="store_true", help="SIMT FP32 trailing updates instead")
+    ap.add_argument("--tensor-core", type=int, default=1, choices=[0, 1, 2],
+                    help="1 (default): blocked tcgen05 updates; 2: panel-by-panel TF32x3; 0: SIMT FP32")
     ap.add_argument("--lookahead", type=int, default=1, choices=[0, 1],
                     help="1 (the library default): factor the next panel on a second stream")
+    ap.add_argument("--rows", type=int, default=36864, help="random: rows")
+    ap.add_argument("--cols", type=int, default=256, help="random: columns")
+    ap.add_argument("--instances", type=int, default=16, help="inverse: instances")
     a = ap.parse_args(argv)
     ctx = fl.Context(0)
-    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 0 if a.simt else 1)
+    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, a.tensor_core)
     fl.fastlsq_set_option(ctx, fl.OPT_LOOKAHEAD, a.lookahead)
+    if a.workload == "random":
+        g = torch.Generator("cuda:0").manual_seed(1)
+        A = fl.colmajor(a.rows, a.cols, torch.float32, "cuda:0", zero=True)
+        A[:, : a.rows] = torch.randn((a.cols, a.rows), generator=g, device="cuda:0")
+        for _ in range(a.steps):
+            _, fac, st = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, A, a.rows, 0.0, None, None,
+                                          A_refine=A.double(), keep=True, stats=True)
+            fl.fastlsq_factor_destroy(ctx, fac)
+        torch.cuda.synchronize()
+        print(f"random {a.rows} x {a.cols}: panel width {st.nb}, trailing-update mode {st.tensor_core}")
+        return
+    if a.workload == "inverse":
+        batch = InverseBatch(ctx, [wl.inverse_instance(q) for q in range(a.instances)])
+        batch.observe()
+        for _ in range(a.steps):
+            batch.eval()
+        torch.cuda.synchronize()
+        print(f"inverse: {a.instances} instances, mean loss "
+              f"{sum(d['loss'].item() for d in batch.inst) / a.instances:.4e}")
+        batch.close()
+        return
     dp = upload(wl.CONFIGS[a.workload]())
     s = LinearSolver(ctx, dp, prec=fl.PREC_MIXED if a.prec == "mixed" else fl.PREC_FP64,
                      max_refine=a.refine,

@@ -262,7 +262,7 @@ def burgers_stage_coef(nu=0.1):
 
 def varcoef2d(n_int=8192, n_bc=1024, n_feat=2048, a=1.0):
     """div(nu grad u) = f on [0,1]^2 with nu = 1 + a (x^2 + y^2/2) (the variable-coefficient
-    form of Sec. 4.4, expanded as nu Lap u + grad nu . grad u), manufactured
+    form of Sec. 3.8, expanded as nu Lap u + grad nu . grad u), manufactured
     u* = sin(pi x) sin(2 pi y) + x y (problem 10); the operator is four per-point terms
     with coefficients nu, nu, d nu/dx, d nu/dy on D^(2,0), D^(0,2), D^(1,0), D^(0,1);
     points as helmholtz2d, sigma = 6, boundary weight 100."""

@@ -18,11 +18,19 @@ def test_traffic_entries_carry_their_capture_keys():
     if not os.path.exists(path):
         pytest.skip("no ncu traffic on record")
     d = json.load(open(path))
-    for key, e in d.items():
-        cls, workload = key.split("@")
+    for cls, e in d.items():
         assert cls in bench.KERNEL_SRC
-        assert workload in bench.WORKLOADS
-        assert e["bytes_per_launch"] > 0 and len(e["src_sha"]) == 16
+        assert len(e["src_sha"]) == 16
+        # the record's own launches: bytes over flops, and the algorithmic floor (the
+        # Y pass reads each FP32 entry of [V | C] once: 4 bytes per 6 * 2 * nbk flops)
+        assert e["bytes_per_tensor_flop"] == pytest.approx(sum(e["dram_bytes"]) / sum(e["bf16_tensor_flops"]))
+        assert e["bytes_per_tensor_flop"] > 0.5 * 4.0 / (6 * 2 * bench.BLK)
+
+
+def test_block_launch_count_matches_the_blocks_with_trailing_columns():
+    assert bench._block_launches(4096, 1) == 2 * 32
+    assert bench._block_launches(300, 1) == 2 * 3
+    assert bench._block_launches(256, 0) == 2 * 1
 
 
 def test_source_hash_covers_every_file_of_the_class(tmp_path, monkeypatch):

@@ -1,4 +1,4 @@
-"""GPU parity of the differentiable solve (Sec. 2.5, Sec. 4.4) against the FP64 oracle.
+"""GPU parity of the differentiable solve (Sec. 2.5, Sec. 3.8) against the FP64 oracle.
 
 The chain theta -> s(x; theta) -> beta = (A^T A + mu I)^{-1} A^T [s; 0] -> u_s = H_s
 beta -> loss = mean (u_s - y)^2 runs through the autograd wrappers over the C ABI

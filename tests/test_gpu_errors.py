@@ -64,3 +64,26 @@ def test_invalid_arguments_are_rejected(ctx):
     u = torch.empty(10, dtype=torch.float64, device=DEV)
     fl.fastlsq_eval(ctx, x, W, b, 0.5, beta, u)
     assert torch.isfinite(u).all()
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_waits_time_out_and_the_context_recovers(which):
+    """A wait that never completes (0: an mbarrier nobody arrives on, like the
+    tensor-core kernels' waits; 1: the grid barrier of the cooperative kernels with one
+    CTA that never arrives) gives up after its budget (2e6 SM cycles, about a
+    millisecond), raises the device flag and returns: fastlsq_sync reports
+    FASTLSQ_ERR_TIMEOUT, the flag is cleared, and the context then solves correctly."""
+    ctx = fl.Context(0)
+    fl.fastlsq_selftest_wait(ctx, which, 2_000_000)
+    with pytest.raises(fl.FastLSQError) as e:
+        fl.fastlsq_sync(ctx)
+    assert e.value.code == -4
+    assert fl.fastlsq_sync(ctx) == 0
+    # the cooperative kernels (the grid barrier) and the tensor-core kernels still work
+    w = wl.helmholtz2d(n_int=1536, n_bc=256, n_feat=384)
+    s = pl.LinearSolver(ctx, pl.upload(w), prec=fl.PREC_MIXED, max_refine=2)
+    s.step(stats=True)
+    assert s.stats.status == 0 and s.stats.tensor_core == 1
+    assert pl.rel_l2(s.u_test(), s.u_exact_test()) < 1e-6
+    _expect_invalid(lambda: fl.fastlsq_selftest_wait(ctx, 2, 1000))
+    ctx.close()

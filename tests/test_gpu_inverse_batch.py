@@ -1,4 +1,4 @@
-"""The pre-factored batch of inverse-problem instances (Sec. 4.4: factor once, two
+"""The pre-factored batch of inverse-problem instances (Sec. 3.8: factor once, two
 triangular solves per evaluation; Sec. 2.5: gradients through the solve) evaluated in
 one persistent launch, against the FP64 oracle.
 

@@ -199,7 +199,44 @@ def test_pde_solutions_match_oracle(ctx, name, kw):
         u = s.u_test().cpu().numpy()
         assert pl.rel_l2(u, u_orc) <= bar, (prec, pl.rel_l2(u, u_orc))
         err = pl.rel_l2(u, ue)
-        assert err <= 2 * err_orc + (1e-12 if prec == fl.PREC_FP64 else 1e-6), (prec, err, err_orc)
+        # within 2x the oracle's error, plus a floor for rounding: FP64 1e-12; MIXED
+        # 1e-7, the distance two classical refinement steps leave between the FP32-factor
+        # solution and the FP64 one (measured 5e-9 on helmholtz2d and 2.5e-8 on
+        # poisson5d at full size, 4x below this floor)
+        assert err <= 2 * err_orc + (1e-12 if prec == fl.PREC_FP64 else 1e-7), (prec, err, err_orc)
+
+
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    out = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()[:2]
+            out[k] = float(v)
+    return out
+
+
+def test_poisson5d_full_size(ctx):
+    """The 5-D Poisson configuration at full size (32,768 + 4,096 rows x 4,096 features,
+    16-wide inner panels at 36,864 rows, two-level tensor-core updates): MIXED within 1e-6
+    of the FP64 GPU path, both within 2x the FP64 oracle's own error against u* at this
+    size (tests/golden/poisson5d_full.txt, written by the oracle alone)."""
+    err_orc = _golden("poisson5d_full.txt")["oracle_rel_l2_vs_exact"]
+    w = wl.poisson5d()
+    dp = pl.upload(w)
+    s64 = pl.LinearSolver(ctx, dp, prec=fl.PREC_FP64)
+    s64.step()
+    u64 = s64.u_test()
+    del s64
+    smx = pl.LinearSolver(ctx, dp, prec=fl.PREC_MIXED, max_refine=2)
+    smx.step(stats=True)
+    umx = smx.u_test()
+    ue = smx.u_exact_test()
+    assert smx.stats.tensor_core == 1 and smx.stats.nb == 16
+    assert pl.rel_l2(umx, u64) <= 1e-6
+    assert pl.rel_l2(u64, ue) <= 2 * err_orc + 1e-12, (pl.rel_l2(u64, ue), err_orc)
+    assert pl.rel_l2(umx, ue) <= 2 * err_orc + 1e-7, (pl.rel_l2(umx, ue), err_orc)
 
 
 def test_helmholtz2d_full_size(ctx):
@@ -254,7 +291,7 @@ def test_concurrent_solves_are_bit_identical():
 
 
 def test_cached_resolves_of_a_pde_system(ctx):
-    """Re-solves against a kept factor (App. F.4) for several right-hand sides at once:
+    """Re-solves against a kept factor (App. G.5) for several right-hand sides at once:
     u is linear in the right-hand side (checked on the test set; beta itself is not
     determined elementwise for these condition numbers)."""
     w = wl.helmholtz2d(n_int=3000, n_bc=512, n_feat=640)

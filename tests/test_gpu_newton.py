@@ -12,6 +12,7 @@ import torch
 import oracle
 from paper_2602_10541_gb300 import fastlsq as fl
 from paper_2602_10541_gb300 import workloads as wl
+from tests.golden import bratu as golden_bratu
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -64,17 +65,30 @@ def test_newton_steps_match_oracle(ctx, prec, bar):
 
 
 def test_newton_bratu_full_size(ctx):
+    """The Bratu configuration at full size (8192 + 1024 rows, 2048 features, Newton
+    from beta = 0, step test 1e-10, at most 15 iterations).  Both precisions must end on
+    the step test or the iteration cap, never on a failed line search; the MIXED field
+    must match the FP64 GPU field and both must match an independent finite-difference
+    solution (Richardson-extrapolated 5-point scheme) on the test set."""
     w = wl.bratu2d()
     beta_m, rc_m, st_m = _gpu_newton(ctx, w, fl.PREC_MIXED, 15)
     beta_d, rc_d, st_d = _gpu_newton(ctx, w, fl.PREC_FP64, 15)
-    assert rc_m in (0, 1, 2) and rc_d in (0, 1, 2)
+    assert rc_m in (0, 1) and rc_d in (0, 1), (rc_m, rc_d)
     assert st_m.res_norm[2] < 1e-2 * st_m.res_norm[0]
+    # whether the config's step criterion (relative step <= 1e-10) was met
+    print(f"bratu: MIXED status {rc_m}, {st_m.iters} iterations, last step {st_m.step_rel[st_m.iters - 1]:.2e}; "
+          f"FP64 status {rc_d}, {st_d.iters} iterations, last step {st_d.step_rel[st_d.iters - 1]:.2e}")
+    assert (rc_m == 0) == (st_m.step_rel[st_m.iters - 1] <= 1e-10)
     u_m, u_d = _u(ctx, w, beta_m), _u(ctx, w, beta_d)
-    # neither run meets the 1e-10 step test in 15 iterations (the residual plateau of
-    # Sec. 3.3), so the comparison is bounded by what the FP64 iteration itself
-    # still changes: 1e-6 plus ten times its last relative step
+    # the comparison is bounded by what the FP64 iteration itself still changes: 1e-6
+    # plus ten times its last relative step
     bar = 1e-6 + 10 * st_d.step_rel[st_d.iters - 1]
     assert np.linalg.norm(u_m - u_d) / np.linalg.norm(u_d) <= bar
+    ref = golden_bratu.bratu_reference(128)(w.x_test)
+    for u in (u_m, u_d):
+        err = np.linalg.norm(u - ref) / np.linalg.norm(ref)
+        print(f"bratu: rel L2 vs finite differences {err:.2e}")
+        assert err <= 1e-4, err
     # the classical lambda = 1 Bratu solution peaks near 0.0784
     uc = torch.empty(1, dtype=torch.float64, device=DEV)
     fl.fastlsq_eval(ctx, _t([[0.5, 0.5]]), _t(w.W), _t(w.b), w.scale, beta_m, uc)

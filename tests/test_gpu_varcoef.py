@@ -1,4 +1,4 @@
-"""GPU parity of the variable-coefficient operator (Sec. 4.4: div(nu grad u) = nu Lap u
+"""GPU parity of the variable-coefficient operator (Sec. 3.8: div(nu grad u) = nu Lap u
 + grad nu . grad u, written as per-point terms of the operator) against the oracle.
 
 - the coefficient fields of problem 10 from the GPU catalogue vs the oracle's;

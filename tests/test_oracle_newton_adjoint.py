@@ -10,43 +10,14 @@ import math
 
 import numpy as np
 import pytest
-import scipy.sparse as sp
-import scipy.sparse.linalg as spla
-from scipy.interpolate import RegularGridInterpolator
-
 import oracle
 from paper_2602_10541_gb300 import workloads as wl
-
-
-def _bratu_fd(n, lam=1.0):
-    """Solve Lap u + lam e^u = 0 on the unit square, u = 0 on the boundary, on an
-    (n+1) x (n+1) grid with the 5-point stencil; Newton to machine precision."""
-    h = 1.0 / n
-    m = n - 1
-    I = sp.identity(m)
-    T = sp.diags([np.ones(m - 1), -2 * np.ones(m), np.ones(m - 1)], [-1, 0, 1])
-    L = (sp.kron(I, T) + sp.kron(T, I)) / h ** 2
-    u = np.zeros(m * m)
-    for _ in range(30):
-        F = L @ u + lam * np.exp(u)
-        J = L + sp.diags(lam * np.exp(u))
-        du = spla.spsolve(J.tocsc(), -F)
-        u += du
-        if np.abs(du).max() < 1e-14:
-            break
-    full = np.zeros((n + 1, n + 1))
-    full[1:-1, 1:-1] = u.reshape(m, m)
-    return full
+from tests.golden import bratu as golden_bratu
 
 
 @pytest.fixture(scope="module")
 def bratu_reference():
-    n = 128
-    coarse = _bratu_fd(n)
-    fine = _bratu_fd(2 * n)
-    rich = (4 * fine[::2, ::2] - coarse) / 3
-    g = np.linspace(0, 1, n + 1)
-    return RegularGridInterpolator((g, g), rich, method="cubic")
+    return golden_bratu.bratu_reference(128)
 
 
 def test_bratu_reference_center_value(bratu_reference):

@@ -1,4 +1,4 @@
-"""Pins of the oracle's variable-coefficient problem (Sec. 4.4: div(nu grad u), expanded
+"""Pins of the oracle's variable-coefficient problem (Sec. 3.8: div(nu grad u), expanded
 as nu Lap u + grad nu . grad u, the operator written as per-point terms).
 
 - nu and its gradient equal the closed form written here, and grad nu matches central

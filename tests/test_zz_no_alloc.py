@@ -49,3 +49,18 @@ def test_noalloc_eval_rejects_requests_beyond_its_scratch():
     with pytest.raises(fl.FastLSQError):
         fl.fastlsq_eval_noalloc(ctx, x, W, b, 1.0, beta, u)
     assert float(u.abs().max()) == 0.0      # nothing was launched
+
+
+def test_noalloc_eval_rejects_too_many_features():
+    """More features than the library's limit (16384) is an invalid argument, not a
+    launch with a column grid past the hardware's limit."""
+    ctx = fl.Context(0)
+    rng = np.random.default_rng(11)
+    x, W, b, beta = _inputs(rng, 1, 16385, 2)
+    u = torch.zeros(1, dtype=torch.float64, device=DEV)
+    with pytest.raises(fl.FastLSQError) as e:
+        fl.fastlsq_eval_noalloc(ctx, x, W, b, 1.0, beta, u)
+    assert e.value.code == -1
+    with pytest.raises(fl.FastLSQError) as e:
+        fl.fastlsq_eval(ctx, x, W, b, 1.0, beta, u)
+    assert e.value.code == -1
