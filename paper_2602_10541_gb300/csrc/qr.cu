@@ -401,8 +401,9 @@ k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, 
             const int64_t c = cbase + 4 * lane + b;
             if (c < nct) Ypart[((int64_t)blockIdx.y * NB + LPW * warp + a) * nct + c] = acc[a][b];
         }
-    trail_finish_z<T, NB, TY_COLS, TY_THREADS>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Z,
-                                               counters + blockIdx.x, reinterpret_cast<T *>(ty_raw));
+    int *cnt = counters + (int64_t)blockIdx.x * TREE_STRIDE;
+    trail_finish_z<T, NB, TY_COLS, TY_THREADS>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Z, cnt, cnt + 1,
+                                               reinterpret_cast<T *>(ty_raw));
 }
 
 // C(i, c) -= sum_l V(i, l) Z(l, c).  CTA tile TC_ROWS x TC_COLS; each thread owns 4
@@ -799,6 +800,7 @@ static int launch_trailing(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_
     // 256-row splits, 73 us per narrow update inside an outer block, 1024-row splits 100 us)
     int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(fl_cdiv(2 * ctx->num_sms, ctiles),
                                                             fl_cdiv(mp, 256)));
+    nsplit = std::min<int64_t>(nsplit, TREE_MAX_SPLITS);
     int64_t rows_per_split = fl_round_up(fl_cdiv(mp, nsplit), TY_ROWS);
     nsplit = fl_cdiv(mp, rows_per_split);
     T *Ypart = (T *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(T) * nsplit * NB * nct);
@@ -833,6 +835,10 @@ static int panel_any(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m_au
         if (ctx->panel_reg && fl_panel_reg_fits(m_aug - k))
             return fl_panel_reg_f32(ctx, F, ld, k, m_aug, ncols, tau, Tblk);
     }
+    if constexpr (std::is_same<T, float>::value && NB == 16) {
+        if (ctx->panel_reg && fl_panel_tall_fits(ctx, m_aug - k, false))
+            return fl_panel_tall_f32(ctx, F, ld, k, m_aug, ncols, tau, Tblk);
+    }
     return launch_panel<T, NB>(ctx, F, ld, k, m_aug, ncols, tau, Tblk);
 }
 
@@ -863,9 +869,10 @@ static int factor_t(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n
     const int64_t ntot = n + nrhs;
     // one completion counter per column tile of the trailing updates, zero between panels
     const int64_t max_tiles = fl_cdiv(ntot, 32) + 8;
-    int *counters = (int *)fl_ws(ctx, FL_WS_COUNTERS, sizeof(int) * max_tiles);
+    const size_t cbytes = sizeof(int) * (size_t)max_tiles * TREE_STRIDE;
+    int *counters = (int *)fl_ws(ctx, FL_WS_COUNTERS, cbytes);
     if (!counters) return FASTLSQ_ERR_NOMEM;
-    cudaMemsetAsync(counters, 0, sizeof(int) * max_tiles, ctx->stream);
+    cudaMemsetAsync(counters, 0, cbytes, ctx->stream);
     const int64_t npan = fl_cdiv(n, NB);
     const bool la = ctx->lookahead && ctx->aux_stream && npan > 1;
     for (int64_t p = 0; p < npan; ++p) {
@@ -922,17 +929,53 @@ static int factor_blocked(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t m_aug,
     constexpr int BLK = 128;
     const int64_t ntot = n + nrhs;
     const int64_t max_tiles = fl_cdiv(ntot, 32) + 8;
-    int *counters = (int *)fl_ws(ctx, FL_WS_COUNTERS, sizeof(int) * max_tiles);
+    const size_t cbytes = sizeof(int) * (size_t)max_tiles * TREE_STRIDE;
+    int *counters = (int *)fl_ws(ctx, FL_WS_COUNTERS, cbytes);
     if (!counters) return FASTLSQ_ERR_NOMEM;
-    cudaMemsetAsync(counters, 0, sizeof(int) * max_tiles, ctx->stream);
+    cudaMemsetAsync(counters, 0, cbytes, ctx->stream);
+    const bool la = ctx->lookahead && ctx->aux_stream && ctx->panel_reg && ctx->fuse_next;
     for (int64_t k = 0; k < n; k += BLK) {
         const int nbk = (int)std::min<int64_t>(BLK, n - k);
+        bool factored = false;        // this inner panel was factored by the previous step's look-ahead
         for (int64_t kp = k; kp < k + nbk; kp += NB) {
             const int ncols = (int)std::min<int64_t>(NB, n - kp);
             float *Tblk = Tall + (kp / NB) * NB * NB;
-            FL_TRY((panel_any<float, NB>(ctx, F, ld, kp, m_aug, ncols, tau + kp, Tblk)));
+            if (!factored) FL_TRY((panel_any<float, NB>(ctx, F, ld, kp, m_aug, ncols, tau + kp, Tblk)));
+            factored = false;
             const int64_t nin = k + nbk - (kp + ncols);
-            if (nin > 0) FL_TRY((launch_trailing<float, NB>(ctx, F, ld, kp, m_aug, ncols, nin, 0, Tblk, counters)));
+            if (nin <= 0) continue;
+            // look-ahead (tall 16-wide panels): the next panel applies this panel's update
+            // to its own columns in its prologue, and the rest of the update runs on the
+            // auxiliary stream beside it; the two join before the panel after next
+            bool fuse = false;
+            if constexpr (NB == 16) fuse = la && fl_panel_tall_fits(ctx, m_aug - (kp + NB), true);
+            if (!fuse) {
+                FL_TRY((launch_trailing<float, NB>(ctx, F, ld, kp, m_aug, ncols, nin, 0, Tblk, counters)));
+                continue;
+            }
+            const int ncn = (int)std::min<int64_t>(NB, nin);
+            const bool rest = nin > ncn;
+            if (rest) {
+                cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0);
+                if (e != cudaSuccess) return fl_cuda(ctx, e, "look-ahead fork");
+            }
+            // the panel is submitted first (and its stream has the higher priority), so
+            // that its cluster is placed before the update's CTAs fill the GPU
+            FL_TRY(fl_panel_tall_f32(ctx, F, ld, kp + NB, m_aug, ncn, tau + kp + NB, Tblk + NB * NB, kp, Tblk));
+            if (rest) {
+                cudaStream_t main_stream = ctx->stream;
+                ctx->stream = ctx->aux_stream;
+                const int rc = launch_trailing<float, NB>(ctx, F, ld, kp, m_aug, ncols, nin - ncn, ncn, Tblk,
+                                                          counters);
+                cudaError_t e = cudaSuccess;
+                if (rc == 0) e = cudaEventRecord(ctx->ev_join, ctx->aux_stream);
+                ctx->stream = main_stream;
+                FL_TRY(rc);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+                if (e != cudaSuccess) return fl_cuda(ctx, e, "look-ahead join");
+            }
+            factored = true;
         }
         if (ntot <= k + nbk) continue;
         const int rc = fl_block_update_f32(ctx, F, ld, k, m_aug, nbk, ntot, NB, Tall + (k / NB) * NB * NB);

@@ -37,6 +37,13 @@ int fl_from_f64(fastlsq_ctx *ctx, const double *src, int64_t n, int64_t n_total,
 // its T in Tprev) to this panel's columns, rows kp.. (the look-ahead update fused in).
 // Returns 1 when the panel is too tall for registers, 2 when the fused form does not fit.
 bool fl_panel_reg_fits(int64_t mp);
+// Shared-memory panel of width 16 for tall FP32 panels (panel_tall.cu): 0 on launch,
+// 1 when the panel is too short (the register kernels) or too tall for it.  With
+// kp >= 0 the kernel first applies the previous panel (reflectors at columns kp = k - 16,
+// T in Tprev) to this panel's columns, rows kp.. (the look-ahead update).
+bool fl_panel_tall_fits(fastlsq_ctx *ctx, int64_t mp, bool fused);
+int fl_panel_tall_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,
+                      float *tau, float *Tblk, int64_t kp = -1, const float *Tprev = nullptr);
 // Row-layout register panel (panel_row.cu), tried first by fl_panel_reg_f32 when the
 // context's row_panel option is on: 1 = too tall, 2 = fused form does not fit.
 int fl_panel_row_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int ncols,

@@ -334,7 +334,9 @@ k_tcy(const __grid_constant__ CUtensorMap mC, const __grid_constant__ CUtensorMa
     if (warp == 0) tc::tmem_dealloc(tmem, TY_TMEM);
     if (ok)   // uniform; the ring is free once the last MMA has completed
         trail_finish_z<float, 32, TY_C, TY_THREADS, true>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Zimg,
-                                                          counters + blockIdx.x, reinterpret_cast<float *>(base));
+                                                          counters + (int64_t)blockIdx.x * TREE_STRIDE,
+                                                          counters + (int64_t)blockIdx.x * TREE_STRIDE + 1,
+                                                          reinterpret_cast<float *>(base));
 }
 
 // ---------------------------------------------------------------------------
@@ -534,7 +536,8 @@ int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_
     // one wave of k_tcy CTAs (one per SM) beside the 16-SM cluster of the next panel,
     // each streaming at least 16 chunks of rows
     const int64_t free_sms = std::max<int64_t>(1, ctx->num_sms - 16);
-    const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(free_sms / ctiles, fl_cdiv(mp, 16 * TY_K)));
+    const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>({free_sms / ctiles, fl_cdiv(mp, 16 * TY_K),
+                                                                    (int64_t)TREE_MAX_SPLITS}));
     const int64_t rblocks = fl_cdiv(mp, TU_R);
     float *Vimg = (float *)fl_ws(ctx, FL_WS_VIMG, (size_t)rblocks * 2 * TU_R * 32 * sizeof(float));
     float *Ypart = (float *)fl_ws(ctx, FL_WS_PARTIAL, sizeof(float) * nsplit * 32 * nct);

@@ -420,6 +420,22 @@ def test_lookahead_matches_single_stream(ctx, tc, m, n):
     next panel is factored, that panel applying the previous update to its own columns
     in its prologue, or with separate kernels) gives the same factor as one stream up to
     FP32 summation order, and the same refined solution."""
+    _lookahead_case(ctx, tc, m, n)
+
+
+@pytest.mark.parametrize("m,n", [(13000, 160), (20000, 300)])
+def test_tall_blocked_lookahead_matches_single_stream(ctx, m, n):
+    """Tall matrices on the two-level factor (16-wide shared-memory panels): with
+    look-ahead each inner panel of an outer block after the first applies the previous
+    panel's update to its own columns in its prologue while the rest of that update
+    runs on the auxiliary stream.  Same factor as the single-stream schedule and the
+    oracle's R up to FP32 summation order; same refined solution.  (160 columns: a
+    ragged second block of two panels; 300: three blocks, the last of three panels,
+    the final one 12 wide.)"""
+    _lookahead_case(ctx, 1, m, n)
+
+
+def _lookahead_case(ctx, tc, m, n):
     rng = np.random.default_rng(5 * m + n)
     A = rng.standard_normal((m, n))
     B = _nearly_consistent(rng, A)
