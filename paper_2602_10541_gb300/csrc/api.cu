@@ -463,6 +463,7 @@ static void factor_free(fastlsq_factor *f)
     if (f->F) cudaFreeAsync(f->F, s);
     if (f->tau) cudaFreeAsync(f->tau, s);
     if (f->T) cudaFreeAsync(f->T, s);
+    if (f->Tb) cudaFreeAsync(f->Tb, s);
     delete f;
 }
 
@@ -483,7 +484,8 @@ static int solve_one(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, i
         FL_TRY(fl_extract_rhs<T>(ctx, F, f->ld, n, r, y));
     } else {
         FL_TRY(fl_from_f64<T>(ctx, rhs64, m, m_aug, y));
-        FL_TRY(fl_apply_q<T>(ctx, F, f->ld, m_aug, n, f->nb, (const T *)f->T, y, 1));
+        FL_TRY(fl_apply_q<T>(ctx, F, f->ld, m_aug, n, f->nb, (const T *)f->T, y, 1,
+                             f->has_tb ? (const float *)f->Tb : nullptr));
     }
     FL_TRY(fl_to_f64<T>(ctx, y, n, y64, 0));
     // FP32 substitution (backward stable, like the FP32 factor itself) is an option for
@@ -500,7 +502,8 @@ static int solve_one(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, i
     for (int it = 0; it < max_refine; ++it) {
         FL_TRY(fl_residual<T>(ctx, f->A_refine, f->ld_refine, m, n, f->mu, m_aug, rhs64, beta64, y,
                               norms_dev ? norms_dev + it : nullptr));
-        FL_TRY(fl_apply_q<T>(ctx, F, f->ld, m_aug, n, f->nb, (const T *)f->T, y, 1));
+        FL_TRY(fl_apply_q<T>(ctx, F, f->ld, m_aug, n, f->nb, (const T *)f->T, y, 1,
+                             f->has_tb ? (const float *)f->Tb : nullptr));
         FL_TRY(fl_to_f64<T>(ctx, y, n, y64, 0));
         FL_TRY(fl_trsv_grid<T>(ctx, F, f->ld, n, y64, dx64, work, 0, nullptr, a32));
         FL_TRY(fl_to_f64<double>(ctx, dx64, n, beta64, 1));
@@ -615,7 +618,9 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
     f->F = fl_alloc(ctx, elem * f->ld * (n_feat + nrhs), &rc);
     if (f->F) f->tau = fl_alloc(ctx, elem * npanels * nb, &rc);
     if (f->tau) f->T = fl_alloc(ctx, elem * npanels * nb * nb, &rc);
-    if (!f->T) {
+    if (f->T && f->tensor_core == FL_TC_BLOCKED)
+        f->Tb = fl_alloc(ctx, sizeof(float) * (size_t)fl_cdiv(n_feat, 128) * 128 * 128, &rc);
+    if (!f->T || (f->tensor_core == FL_TC_BLOCKED && !f->Tb)) {
         factor_free(f);
         return rc ? rc : FASTLSQ_ERR_NOMEM;
     }
@@ -634,7 +639,7 @@ extern "C" int fastlsq_lstsq(fastlsq_ctx *ctx, fastlsq_prec prec, const void *A,
                                            rhs, ld_rhs, nrhs, (float *)f->F, f->ld);
         if (rc == 0)
             rc = fl_factor<float>(ctx, (float *)f->F, f->ld, m_aug, n_feat, nrhs, nb,
-                                  (float *)f->tau, (float *)f->T, f->tensor_core);
+                                  (float *)f->tau, (float *)f->T, f->tensor_core, (float *)f->Tb, &f->has_tb);
     }
     if (rc == 0 && nrhs > 0)
         rc = solve_all(ctx, f, nrhs, rhs, nrhs, ld_rhs, beta, ld_beta,

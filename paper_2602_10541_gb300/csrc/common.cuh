@@ -73,6 +73,7 @@ enum fl_slot {
     FL_WS_BLK_VU,          // outer-block update: V operand image (per 128-row tile)
     FL_WS_BLK_Y,           // outer-block update: Y = V^T [V | C] split partials
     FL_WS_BLK_Z,           // outer-block update: Z operand image
+    FL_WS_BLK_G,           // outer blocks' Gram matrices V_b^T V_b (for their block reflectors' T)
     FL_WS_COUNT
 };
 
@@ -132,6 +133,8 @@ struct fastlsq_factor {
     void *F = nullptr;         // factor storage m_aug x n (float or double)
     void *tau = nullptr;       // n
     void *T = nullptr;         // (n / nb) blocks of nb x nb (column-major)
+    void *Tb = nullptr;        // two-level factor: per outer block its 128 x 128 T_b (row-major)
+    int has_tb = 0;            // Tb holds every outer block's T_b
     const double *A_refine = nullptr;
     int64_t ld_refine = 0;
     int tensor_core = 0;

@@ -924,9 +924,16 @@ static int factor_t(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n
 // one-level schedule's, so every solve reads it unchanged.
 template <int NB>
 static int factor_blocked(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t m_aug, int64_t n, int nrhs,
-                          float *tau, float *Tall)
+                          float *tau, float *Tall, float *Tball, int *tb_ok)
 {
     constexpr int BLK = 128;
+    if (tb_ok) *tb_ok = 0;
+    float *Gall = nullptr;
+    if (Tball) {
+        Gall = (float *)fl_ws(ctx, FL_WS_BLK_G, sizeof(float) * (size_t)fl_cdiv(n, BLK) * BLK * BLK);
+        if (!Gall) return FASTLSQ_ERR_NOMEM;
+    }
+    bool all_g = Gall != nullptr;
     const int64_t ntot = n + nrhs;
     const int64_t max_tiles = fl_cdiv(ntot, 32) + 8;
     const size_t cbytes = sizeof(int) * (size_t)max_tiles * TREE_STRIDE;
@@ -977,10 +984,15 @@ static int factor_blocked(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t m_aug,
             }
             factored = true;
         }
-        if (ntot <= k + nbk) continue;
-        const int rc = fl_block_update_f32(ctx, F, ld, k, m_aug, nbk, ntot, NB, Tall + (k / NB) * NB * NB);
+        if (ntot <= k + nbk) {
+            all_g = false;
+            continue;
+        }
+        const int rc = fl_block_update_f32(ctx, F, ld, k, m_aug, nbk, ntot, NB, Tall + (k / NB) * NB * NB,
+                                           Gall ? Gall + (k / BLK) * BLK * BLK : nullptr);
         if (rc < 0) return rc;
         if (rc == 1) {      // shape not taken: the block's panels update the columns one by one
+            all_g = false;
             for (int64_t kp = k; kp < k + nbk; kp += NB) {
                 const int ncols = (int)std::min<int64_t>(NB, n - kp);
                 FL_TRY((launch_trailing<float, NB>(ctx, F, ld, kp, m_aug, ncols, ntot - (k + nbk),
@@ -989,17 +1001,22 @@ static int factor_blocked(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t m_aug,
             }
         }
     }
+    if (all_g) {
+        FL_TRY(fl_block_t_f32(ctx, Gall, Tall, n, NB, Tball));
+        if (tb_ok) *tb_ok = 1;
+    }
     return 0;
 }
 
 template <typename T>
 int fl_factor(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n, int nrhs, int nb,
-              T *tau, T *Tall, int use_tc)
+              T *tau, T *Tall, int use_tc, float *Tball, int *tb_ok)
 {
+    if (tb_ok) *tb_ok = 0;
     if constexpr (std::is_same<T, float>::value) {
         if (use_tc == FL_TC_BLOCKED) {
-            if (nb == 32) return factor_blocked<32>(ctx, F, ld, m_aug, n, nrhs, tau, Tall);
-            if (nb == 16) return factor_blocked<16>(ctx, F, ld, m_aug, n, nrhs, tau, Tall);
+            if (nb == 32) return factor_blocked<32>(ctx, F, ld, m_aug, n, nrhs, tau, Tall, Tball, tb_ok);
+            if (nb == 16) return factor_blocked<16>(ctx, F, ld, m_aug, n, nrhs, tau, Tall, Tball, tb_ok);
         }
     }
     switch (nb) {
@@ -1010,15 +1027,19 @@ int fl_factor(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n, int 
     }
 }
 template int fl_factor<float>(fastlsq_ctx *, float *, int64_t, int64_t, int64_t, int, int, float *,
-                              float *, int);
+                              float *, int, float *, int *);
 template int fl_factor<double>(fastlsq_ctx *, double *, int64_t, int64_t, int64_t, int, int,
-                               double *, double *, int);
+                               double *, double *, int, float *, int *);
 
 template <typename T>
 int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
-               const T *Tall, T *y, int transpose)
+               const T *Tall, T *y, int transpose, const float *Tball)
 {
     if constexpr (std::is_same<T, float>::value) {
+        if (Tball) {
+            const int rc = fl_apply_qb_f32(ctx, F, ld, m_aug, n, Tball, y, transpose);
+            if (rc <= 0) return rc;      // 1: shape not taken by the block-reflector kernel
+        }
         const int rc = fl_apply_q_cluster<float>(ctx, F, ld, m_aug, n, nb, Tall, y, transpose);
         if (rc <= 0) return rc;          // 1: shape not taken by the cluster kernel
     }
@@ -1043,9 +1064,9 @@ int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t 
     return 0;
 }
 template int fl_apply_q<float>(fastlsq_ctx *, const float *, int64_t, int64_t, int64_t, int,
-                               const float *, float *, int);
+                               const float *, float *, int, const float *);
 template int fl_apply_q<double>(fastlsq_ctx *, const double *, int64_t, int64_t, int64_t, int,
-                                const double *, double *, int);
+                                const double *, double *, int, const float *);
 
 template <typename TA, typename T>
 int fl_copy_in(fastlsq_ctx *ctx, const TA *A, int64_t ldA, int64_t m, int64_t n, double mu,

@@ -6,17 +6,27 @@ __host__ __device__ __forceinline__ int64_t fl_cdiv_dev(int64_t a, int64_t b) { 
 
 int fl_panel_capacity_nb(fastlsq_ctx *ctx, int64_t m_aug, size_t elem);
 
+// Tball (two-level FP32 factor, may be null): receives every outer block's T_b; *tb_ok
+// tells whether all of them were formed (a block whose update was not taken has none)
 template <typename T>
 int fl_factor(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t m_aug, int64_t n, int nrhs, int nb,
-              T *tau, T *Tall, int use_tc);
+              T *tau, T *Tall, int use_tc, float *Tball = nullptr, int *tb_ok = nullptr);
 // Q^T y / Q y on one cluster, FP32 factor with panel width 32 (apply_q.cu); returns 1
 // when the shape is not taken (more than 16 x 640 rows or another panel width)
 template <typename T>
 int fl_apply_q_cluster(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
                        const T *Tall, T *y, int transpose);
+// Tball: the two-level factor's block reflectors' T (or null): then one grid barrier
+// per outer block (apply_qb.cu) where the shape fits
 template <typename T>
 int fl_apply_q(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t m_aug, int64_t n, int nb,
-               const T *Tall, T *y, int transpose);
+               const T *Tall, T *y, int transpose, const float *Tball = nullptr);
+// Block reflectors of the two-level FP32 factor (apply_qb.cu): T_b of every outer block
+// from the blocks' Gram matrices and the inner panels' T, and Q^T y with them (returns
+// 1 when not taken: Q y, or more than 160 x 296 rows)
+int fl_block_t_f32(fastlsq_ctx *ctx, const float *Gall, const float *Tall, int64_t n, int nb, float *Tball);
+int fl_apply_qb_f32(fastlsq_ctx *ctx, const float *F, int64_t ld, int64_t m_aug, int64_t n, const float *Tball,
+                    float *y, int transpose);
 template <typename TA, typename T>
 int fl_copy_in(fastlsq_ctx *ctx, const TA *A, int64_t ldA, int64_t m, int64_t n, double mu,
                int64_t m_aug, const double *rhs, int64_t ld_rhs, int nrhs, T *F, int64_t ld);
@@ -62,9 +72,10 @@ int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_
 // Outer-block trailing update on the tensor cores (three-part bf16 split), tc_block.cu:
 // C <- H^T C for the block of nbk <= 128 columns at column k (inner panels of width nb,
 // T factors from Tb on), C = F's columns k + nbk .. ntot.  Returns 1 when the shape is
-// not taken (unaligned factor).
+// not taken (unaligned factor).  Gout (may be null) receives the block's Gram matrix
+// V^T V, G[e * 128 + l] = v_l^T v_e for l, e < nbk.
 int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int nbk,
-                        int64_t ntot, int nb, const float *Tb);
+                        int64_t ntot, int nb, const float *Tb, float *Gout = nullptr);
 
 // Krylov refinement with the factor's R as preconditioner (refine.cu)
 int fl_refine_cgls(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs64, double *beta64,

@@ -727,7 +727,7 @@ constexpr size_t bz_smem(int nb) { return sizeof(float) * (128 * 129 + 2 * 128 *
 // Returns 1 when the shape is not taken (alignment), the caller then updates panel by
 // panel.
 int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int nbk,
-                        int64_t ntot, int nb, const float *Tb)
+                        int64_t ntot, int nb, const float *Tb, float *Gout)
 {
     const int64_t mp = m_aug - k, n_ext = ntot - k, n_tr = n_ext - nbk;
     if (n_tr <= 0 || mp <= 0) return 0;
@@ -769,6 +769,11 @@ int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64
         FL_PROF_N(ctx, FASTLSQ_K_BLOCK_PREP, 2);
         k_bsum<<<(unsigned)fl_cdiv(n_ext, 8), 256, 0, ctx->stream>>>(Ypart, (int)S, n_ext, Ysum);
         FL_CHECK_LAUNCH(ctx, "block Y sum");
+        if (Gout) {      // the block's own columns of Y: its Gram matrix
+            const cudaError_t e = cudaMemcpyAsync(Gout, Ysum, sizeof(float) * (size_t)nbk * BK,
+                                                  cudaMemcpyDeviceToDevice, ctx->stream);
+            if (e != cudaSuccess) return fl_cuda(ctx, e, "block Gram copy");
+        }
         if (nb == 32)
             k_bz<32><<<(unsigned)n_ct, 256, bz_smem(32), ctx->stream>>>(Ysum, n_ext, nbk, Tb, Zimg);
         else

@@ -464,3 +464,29 @@ def _lookahead_case(ctx, tc, m, n):
     for key in ((1, 1), (1, 0)):
         assert np.abs(Rs[key] - Ro).max() <= 2e-5 * scale, key
         assert np.abs(Rs[key] - Rs[(0, 0)]).max() <= 2e-5 * scale, key
+
+
+@pytest.mark.parametrize("m,n", [(700, 130), (3000, 257), (13000, 300)])
+def test_block_reflector_qt_matches_factorisation_and_oracle(ctx, m, n):
+    """Q^T b by the block-reflector kernel (a re-solve of a kept two-level factor: one
+    grid barrier per outer block, T_b formed from the block's Gram matrix and its inner
+    panels' T) against Q^T b carried through the factorisation itself (the right-hand
+    side as an extra column of every trailing update), both followed by the same R^{-1}
+    and no refinement, and against the oracle's least-squares solution.  257 columns:
+    a last outer block of one column; 13,000 rows: 16-wide inner panels."""
+    rng = np.random.default_rng(11 * m + n)
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal((m, 1))
+    ref = oracle.lstsq(A, b).reshape(-1)
+    scale = np.abs(ref).max()
+    fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, 1)
+    beta_f = torch.zeros((1, n), dtype=torch.float64, device=DEV)
+    _, fac, st = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, 0.0, _rhs(b), beta_f,
+                                  A_refine=_cm(A, torch.float64), max_refine=0, keep=True, stats=True)
+    assert st.tensor_core == 1
+    beta_r = torch.zeros((1, n), dtype=torch.float64, device=DEV)
+    fl.fastlsq_factor_solve(ctx, fac, _rhs(b), beta_r, max_refine=0)
+    fl.fastlsq_factor_destroy(ctx, fac)
+    bf, br = beta_f.cpu().numpy()[0], beta_r.cpu().numpy()[0]
+    assert np.abs(br - bf).max() <= 2e-5 * scale
+    assert np.abs(br - ref).max() <= 2e-5 * scale
