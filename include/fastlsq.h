@@ -594,10 +594,15 @@ typedef enum {
                                       applies the previous panel's update to its own columns
                                       in its prologue (no separate kernels for it) where its
                                       shared memory allows; 0: separate update kernels */
-    FASTLSQ_OPT_ROW_PANEL = 5       /* 1 (default): the register panel keeps one or two
+    FASTLSQ_OPT_ROW_PANEL = 5,      /* 1 (default): the register panel keeps one or two
                                       panel rows per thread (updates without shuffles),
                                       where the panel has at most 768 rows per CTA; 0: one
                                       column per lane (32 rows per thread at most) */
+    FASTLSQ_OPT_SPLIT_ROWS = 6      /* least rows per split of the SIMT trailing updates'
+                                      Y pass (a multiple of 32, 32 .. 1048576; default 256).
+                                      Small splits give one solve the shortest latency;
+                                      larger ones launch fewer CTAs per update, leaving
+                                      more of the GPU to other solves running beside it */
 } fastlsq_option;
 
 /* Set a context option (see fastlsq_option).  Returns 0 or -1 for an unknown option. */

@@ -100,6 +100,7 @@ struct fastlsq_ctx {
     int row_panel = 1;              // of which the row layout (one or two rows per thread)
     int lookahead = 1;              // panel p+1 beside the rest of panel p's update (on aux_stream)
     int fuse_next = 1;              // look-ahead: next panel applies the previous update itself
+    int split_rows = 256;           // least rows per split of the SIMT trailing updates' Y pass
     int trsv32 = 1;                 // FP32 arithmetic in the triangular solves of classical refinement
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

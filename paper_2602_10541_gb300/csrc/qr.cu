@@ -796,10 +796,10 @@ static int launch_trailing(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_
     const int64_t mp = m_aug - k;
     const int64_t ctiles = fl_cdiv(nct, TY_COLS);
     // split the long row dimension so the grid covers the GPU about twice, with at least
-    // 256 rows per split (measured on the 36,864-row panels of the 5-D Poisson system:
-    // 256-row splits, 73 us per narrow update inside an outer block, 1024-row splits 100 us)
+    // ctx->split_rows rows per split (256 by default: the shortest latency of one narrow
+    // update inside an outer block at 36,864 rows; larger splits use fewer CTAs)
     int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(fl_cdiv(2 * ctx->num_sms, ctiles),
-                                                            fl_cdiv(mp, 256)));
+                                                            fl_cdiv(mp, ctx->split_rows)));
     nsplit = std::min<int64_t>(nsplit, TREE_MAX_SPLITS);
     int64_t rows_per_split = fl_round_up(fl_cdiv(mp, nsplit), TY_ROWS);
     nsplit = fl_cdiv(mp, rows_per_split);

@@ -202,6 +202,7 @@ OPT_LOOKAHEAD = 2
 OPT_TRSV_FP32 = 3
 OPT_FUSED_LOOKAHEAD = 4
 OPT_ROW_PANEL = 5
+OPT_SPLIT_ROWS = 6
 
 
 def fastlsq_set_option(ctx, option, value):
