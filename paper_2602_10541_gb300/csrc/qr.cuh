@@ -1,5 +1,7 @@
 // Launchers of the blocked Householder QR and its solves (qr.cu, tc_update.cu).
 #pragma once
+#include <cuda.h>
+
 #include "common.cuh"
 
 __host__ __device__ __forceinline__ int64_t fl_cdiv_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -76,6 +78,12 @@ int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_
 // V^T V, G[e * 128 + l] = v_l^T v_e for l, e < nbk.
 int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int nbk,
                         int64_t ntot, int nb, const float *Tb, float *Gout = nullptr);
+
+// TMA descriptor of the factor F (ld rows x ntot columns, column-major fp32) as a 2-D
+// tensor with boxes of box_r rows x box_c columns, out-of-range elements read as zero
+// (tc_update.cu); false when the driver's encoder is unavailable or rejects the shape
+bool fl_encode_f32_map(CUtensorMap *m, const float *F, int64_t ld, int64_t ntot, uint32_t box_r, uint32_t box_c,
+                       bool swizzle128);
 
 // Krylov refinement with the factor's R as preconditioner (refine.cu)
 int fl_refine_cgls(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs64, double *beta64,

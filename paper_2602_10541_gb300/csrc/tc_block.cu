@@ -38,6 +38,7 @@
 //            written, coalesced along the rows) overlaps the next tile's MMAs.
 // Every mbarrier wait is bounded: on timeout the kernel raises the device flag, waits
 // (bounded) for its copies and MMAs in flight, frees its TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -64,8 +65,9 @@ constexpr long long BT_SPIN = 2000000000ll;        // SM cycles (about a second)
 constexpr int BY_THREADS = 320;         // warp 0: A loads, warp 1: MMA, warps 2..9: converters, epilogue
 constexpr int BY_CONV = 8;
 constexpr uint32_t BY_STAGE = 2u * VY_CHUNK;       // A parts then B parts
-constexpr size_t BY_SMEM = 2 * BY_STAGE + 1024;
-constexpr int BY_PF = 2;                // chunks ahead that the converters prefetch into L2
+constexpr uint32_t BY_RAW = 64u * BY_N * 4u;       // one chunk of F as fp32 (64 rows x 128 columns)
+constexpr size_t BY_SMEM = 2 * BY_STAGE + BY_RAW + 1024;
+constexpr int BY_PF = 3;                // chunks ahead that the converters prefetch into L2
 constexpr int BU_THREADS = 320;         // warp 0: loads, warp 1: MMA, warps 2..9: epilogue
 constexpr int BU_EPI = 8;
 constexpr size_t BU_SMEM = VU_TILE + 2 * Z_TILE + 1024;
@@ -93,6 +95,17 @@ __device__ __forceinline__ void bt_bulk_load(void *dst, const void *src, uint32_
 __device__ __forceinline__ void bt_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(tc::smem_addr(bar)) : "memory");
+}
+
+// 2-D tile of F (x = row, y = column) into shared memory, counted on bar; rows and
+// columns outside F read as zero
+__device__ __forceinline__ void bt_tma_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                 "[%0], [%1, {%2, %3}], [%4];\n"
+                 :: "r"(tc::smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y),
+                    "r"(tc::smem_addr(bar))
+                 : "memory");
 }
 
 // Operand tiles are K-major with 128-byte rows (64 bf16 along K) in the 128-byte
@@ -193,9 +206,11 @@ k_bimg(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, 
 // k_by: Ypart[s][e][l] = sum over the split's rows i of V(i, l) X(i, e), X = F's
 // columns k + e (e < nbk: the block's own V, masked; e >= nbk: the trailing columns).
 // CTA (j, s): columns e in [128 j, 128 j + 128), the 64-row chunks s, s + S, ...
-// Roles: warp 0 bulk-loads the VY chunk (A operand, three parts), warps 2..9 load the
-// X chunk from F one chunk ahead (and the chunk after next into L2: measured 19% faster
-// on a 36,864 x 1024 factor than without), split it and store the three B parts, warp 1 issues
+// Roles: warp 0 bulk-loads the VY chunk (A operand, three parts) (lane 0) and the raw
+// fp32 X chunk of F by TMA into one raw buffer (lane 1) as soon as the converters have
+// read the previous one, warps 2..9 read the X chunk into registers one chunk ahead
+// (so a chunk of F is requested two chunks before its parts are stored; and three
+// ahead into L2), split it and store the three B parts, warp 1 issues
 // the 24 MMAs of the chunk, commits each 32-row half to that half's accumulator and the
 // whole chunk to the stage's "empty" barrier.  The five small products accumulate over
 // the whole split in one TMEM accumulator; each half-chunk's leading products go to a
@@ -208,13 +223,15 @@ k_bimg(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, 
 constexpr int BY_NBUF = 3;             // leading-product accumulators in TMEM (plus the small one)
 
 __global__ void __launch_bounds__(BY_THREADS, 1)
-k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, int64_t n_ext,
-     const unsigned char *__restrict__ VY, int64_t nch, float *__restrict__ Ypart, int *flag)
+k_by(const __grid_constant__ CUtensorMap mF, const float *__restrict__ F, int64_t ld, int64_t k, int nbk,
+     int64_t mp, int64_t n_ext, const unsigned char *__restrict__ VY, int64_t nch, float *__restrict__ Ypart,
+     int *flag)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = bt_align1024(smem_raw);
-    __shared__ uint64_t fullA[2], fullB[2], empty[2], accf[BY_NBUF], acce[BY_NBUF];
-    __shared__ int s_last_load[2], s_last_commit;
+    const float *raw = reinterpret_cast<const float *>(base + 2 * BY_STAGE);   // [128 columns][64 rows]
+    __shared__ uint64_t fullA[2], fullB[2], empty[2], accf[BY_NBUF], acce[BY_NBUF], rawFull, rawEmpty;
+    __shared__ int s_last_load[2], s_last_commit, s_last_raw;
     __shared__ volatile int s_fail;
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -235,8 +252,11 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
             tc::mbar_init(&accf[b], 1);
             tc::mbar_init(&acce[b], BY_CONV);
         }
+        tc::mbar_init(&rawFull, 1);
+        tc::mbar_init(&rawEmpty, BY_CONV);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_last_commit = -1;
+        s_last_raw = -1;
         s_fail = 0;
     }
     tc::fence_before_sync();
@@ -259,6 +279,19 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
                 bt_expect_tx(&fullA[s], VY_CHUNK);
                 bt_bulk_load(base + s * BY_STAGE, VY + chunk(ch) * VY_CHUNK, VY_CHUNK, &fullA[s]);
                 s_last_load[s] = ch;
+            }
+        } else if (lane == 1) {
+            // the raw chunks of F by TMA into the one raw buffer, once the converters have
+            // read the previous chunk out of it
+            for (int ch = 0; ch < nloc; ++ch) {
+                if (ch >= 1 && !tc::mbar_wait(&rawEmpty, (uint32_t)(ch - 1) & 1u, BT_SPIN)) {
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                bt_expect_tx(&rawFull, BY_RAW);
+                bt_tma_2d(base + 2 * BY_STAGE, &mF, (int)(k + chunk(ch) * BY_KC), (int)(k + ebase), &rawFull);
+                s_last_raw = ch;
             }
         }
     } else if (warp == 1) {
@@ -320,15 +353,16 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
 #pragma unroll
         for (int jj = 0; jj < 64; ++jj) y[jj] = 0.f;
         float4 x[8];
-        auto load = [&](int ch) {
+        // chunk ch from the raw buffer (TMA-loaded; rows and columns outside F are zero)
+        auto load = [&](int ch) -> bool {
+            if (!tc::mbar_wait(&rawFull, (uint32_t)ch & 1u, BT_SPIN)) return false;
             const int64_t r0 = chunk(ch) * BY_KC;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int q = ct + 256 * u, cc = q >> 4, quad = q & 15;
                 const int64_t i = r0 + 4 * quad;               // panel-local row
                 const int64_t e = ebase + cc;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (e < n_ext && i < mp && k + i < ld) v = *reinterpret_cast<const float4 *>(F + (k + i) + (k + e) * ld);
+                float4 v = *reinterpret_cast<const float4 *>(raw + cc * BY_KC + 4 * quad);
                 if (e < nbk) {
                     v.x = (i + 0 < mp) ? v_mask(v.x, i + 0, (int)e, nbk) : 0.f;
                     v.y = (i + 1 < mp) ? v_mask(v.y, i + 1, (int)e, nbk) : 0.f;
@@ -337,6 +371,9 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
                 }
                 x[u] = v;
             }
+            __syncwarp();
+            if (lane == 0) bt_arrive(&rawEmpty);
+            return true;
         };
         // y += leading products of half-chunk hc
         auto drain = [&](int hc) -> bool {
@@ -361,7 +398,7 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
             if (lane == 0) bt_arrive(&acce[b]);
             return true;
         };
-        if (nloc > 0) load(0);
+        if (nloc > 0 && !load(0)) s_fail = 1;
         for (int ch = 0; ch < nloc; ++ch) {
             const int s = ch & 1;
             if (ch >= 2 && !tc::mbar_wait(&empty[s], (uint32_t)((ch - 2) >> 1) & 1u, BT_SPIN)) {
@@ -383,8 +420,11 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
             tc::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) bt_arrive(&fullB[s]);
-            if (ch + 1 < nloc) load(ch + 1);
-            if (ch + BY_PF < nloc) {   // the chunk after next into L2: thread (column ct / 2, half ct % 2)
+            if (ch + 1 < nloc && !load(ch + 1)) {
+                s_fail = 1;
+                break;
+            }
+            if (ch + BY_PF < nloc) {   // the chunk BY_PF ahead into L2: thread (column ct / 2, half ct % 2)
                 const int64_t ip = chunk(ch + BY_PF) * BY_KC + 32 * (ct & 1);
                 const int64_t ep = ebase + (ct >> 1);
                 if (ep < n_ext && ip < mp)
@@ -427,6 +467,7 @@ k_by(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, in
                 if (s_last_load[s] >= 0) tc::mbar_wait(&fullA[s], (uint32_t)(s_last_load[s] >> 1) & 1u, BT_SPIN);
             const int lc = s_last_commit;
             if (lc >= 0) tc::mbar_wait(&accf[lc % BY_NBUF], (uint32_t)(lc / BY_NBUF) & 1u, BT_SPIN);
+            if (s_last_raw >= 0) tc::mbar_wait(&rawFull, (uint32_t)s_last_raw & 1u, BT_SPIN);
         }
         __syncthreads();
     }
@@ -762,6 +803,8 @@ int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64
     unsigned char *Zimg = (unsigned char *)fl_ws(ctx, FL_WS_BLK_Z, (size_t)n_ct * Z_TILE);
     if (!VY || !VU || !Ypart || !Zimg) return FASTLSQ_ERR_NOMEM;
     float *Ysum = Ypart + (size_t)S * n_ext * BK;
+    CUtensorMap mF;
+    if (!fl_encode_f32_map(&mF, F, ld, ntot, BY_KC, BY_N, false)) return 1;
     {
         FL_PROF(ctx, FASTLSQ_K_BLOCK_PREP);
         k_bimg<<<(unsigned)n_rt, 256, BI_SMEM, ctx->stream>>>(F, ld, k, nbk, mp, nch, VY, VU);
@@ -770,7 +813,7 @@ int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64
     {
         FL_PROF(ctx, FASTLSQ_K_BLOCK_Y);
         k_by<<<dim3((unsigned)ytiles, (unsigned)S), BY_THREADS, BY_SMEM, ctx->stream>>>(
-            F, ld, k, nbk, mp, n_ext, VY, nch, Ypart, ctx->d_flag);
+            mF, F, ld, k, nbk, mp, n_ext, VY, nch, Ypart, ctx->d_flag);
         FL_CHECK_LAUNCH(ctx, "block Y pass");
     }
     {

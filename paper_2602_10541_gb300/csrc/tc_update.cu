@@ -445,6 +445,7 @@ k_tcu(const __grid_constant__ CUtensorMap mT, float *__restrict__ F, int64_t ld,
 
 namespace {
 
+// the driver's tensor-map encoder, looked up once
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -462,12 +463,13 @@ EncodeTiled encode_fn()
     });
     return fn;
 }
+}  // namespace
 
 // The factor F (ld rows x ntot columns, column-major fp32) seen as a 2-D tensor
 // (dimension 0 = rows): boxes of box_r rows x box_c columns; out-of-range elements
 // read as zero.
-bool encode_map(CUtensorMap *m, const float *F, int64_t ld, int64_t ntot, uint32_t box_r, uint32_t box_c,
-                bool swizzle128)
+bool fl_encode_f32_map(CUtensorMap *m, const float *F, int64_t ld, int64_t ntot, uint32_t box_r, uint32_t box_c,
+                       bool swizzle128)
 {
     EncodeTiled fn = encode_fn();
     if (!fn) return false;
@@ -479,6 +481,8 @@ bool encode_map(CUtensorMap *m, const float *F, int64_t ld, int64_t ntot, uint32
               CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+namespace {
 
 // the three maps of one factor, cached (a factorisation launches two updates per panel)
 struct FactorMaps {
@@ -502,8 +506,8 @@ bool factor_maps(const float *F, int64_t ld, int64_t ntot, FactorMaps &out)
     e.F = F;
     e.ld = ld;
     e.ntot = ntot;
-    if (!encode_map(&e.c, F, ld, ntot, TY_K, TY_C, true) || !encode_map(&e.v, F, ld, ntot, TY_K, 32, true) ||
-        !encode_map(&e.t, F, ld, ntot, TU_R, TU_C, false))
+    if (!fl_encode_f32_map(&e.c, F, ld, ntot, TY_K, TY_C, true) || !fl_encode_f32_map(&e.v, F, ld, ntot, TY_K, 32, true) ||
+        !fl_encode_f32_map(&e.t, F, ld, ntot, TU_R, TU_C, false))
         return false;
     cache[next] = e;
     next = (next + 1) % 8;
