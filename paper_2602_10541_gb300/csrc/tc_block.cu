@@ -70,7 +70,8 @@ constexpr size_t BY_SMEM = 2 * BY_STAGE + BY_RAW + 1024;
 constexpr int BY_PF = 3;                // chunks ahead that the converters prefetch into L2
 constexpr int BU_THREADS = 320;         // warp 0: loads, warp 1: MMA, warps 2..9: epilogue
 constexpr int BU_EPI = 8;
-constexpr size_t BU_SMEM = VU_TILE + 2 * Z_TILE + 1024;
+constexpr uint32_t BU_CT = (uint32_t)BU_R * BU_N * 4u;   // one tile of C as fp32 (128 rows x 64 columns)
+constexpr size_t BU_SMEM = VU_TILE + 2 * Z_TILE + BU_CT + 1024;
 constexpr int BI_LD = 129;              // padded row of the k_bimg staging tile
 constexpr size_t BI_SMEM = sizeof(float) * 128 * BI_LD;
 
@@ -577,22 +578,25 @@ k_bz(const float *__restrict__ Ysum, int64_t n_ext, int nbk, const float *__rest
 // ---------------------------------------------------------------------------
 // k_bu: C(i, c) -= sum_l V(i, l) Z(l, c) for the trailing columns, rows k.. of F.
 // Units (row tile r, column tile j) in row-tile-major order; CTA b takes a contiguous
-// range.  Warp 0 loads the VU tile (when r changes) and the Z tiles (ring of two),
-// warp 1 issues the 48 MMAs of a unit into one of two TMEM buffers (the two K halves
-// and the leading and small products in four accumulators, summed in the epilogue),
-// warps 2..9 (two per lane quarter, 32 columns each) read D, free the buffer, load
-// their 32 elements of C, then store C - D.
+// range.  Warp 0 loads the VU tile (when r changes) and the Z tiles (ring of two)
+// (lane 0), and the unit's tile of C by TMA into one C buffer as soon as the epilogue
+// has read the previous tile (lane 1); warp 1 issues the 48 MMAs of a unit into one of
+// two TMEM buffers (the two K halves and the leading and small products in four
+// accumulators, summed in the epilogue); warps 2..9 (two per lane quarter, 32 columns
+// each) read their 32 elements of C from the C buffer and free it, read D, free the
+// TMEM buffer, then store C - D.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(BU_THREADS, 1)
-k_bu(float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, int64_t n_ext,
-     const unsigned char *__restrict__ VU, const unsigned char *__restrict__ Zimg, int64_t n_ct, int64_t n_units,
-     int *flag)
+k_bu(const __grid_constant__ CUtensorMap mC, float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp,
+     int64_t n_ext, const unsigned char *__restrict__ VU, const unsigned char *__restrict__ Zimg, int64_t n_ct,
+     int64_t n_units, int *flag)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = bt_align1024(smem_raw);
     unsigned char *VUs = base;
-    __shared__ uint64_t vu_full, vu_empty, z_full[2], z_empty[2], acc_full[2], acc_empty[2];
-    __shared__ int s_vu_loads, s_last_z[2], s_last_commit;
+    const float *Cs = reinterpret_cast<const float *>(base + VU_TILE + 2 * Z_TILE);   // [64 columns][128 rows]
+    __shared__ uint64_t vu_full, vu_empty, z_full[2], z_empty[2], acc_full[2], acc_empty[2], c_full, c_empty;
+    __shared__ int s_vu_loads, s_last_z[2], s_last_commit, s_last_c;
     __shared__ volatile int s_fail;
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -612,9 +616,12 @@ k_bu(float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, int64_t 
             tc::mbar_init(&acc_empty[s], BU_EPI);
             s_last_z[s] = -1;
         }
+        tc::mbar_init(&c_full, 1);
+        tc::mbar_init(&c_empty, BU_EPI);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_vu_loads = 0;
         s_last_commit = -1;
+        s_last_c = -1;
         s_fail = 0;
     }
     tc::fence_before_sync();
@@ -648,6 +655,20 @@ k_bu(float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, int64_t 
                 bt_expect_tx(&z_full[s], Z_TILE);
                 bt_bulk_load(base + VU_TILE + s * Z_TILE, Zimg + j * Z_TILE, Z_TILE, &z_full[s]);
                 s_last_z[s] = lu;
+            }
+        } else if (lane == 1) {
+            // the units' tiles of C by TMA into the one C buffer, once the epilogue has read
+            // the previous tile out of it
+            for (int lu = 0; lu < nloc; ++lu) {
+                const int64_t u = u0 + lu, r = u / n_ct, j = u % n_ct;
+                if (lu >= 1 && !tc::mbar_wait(&c_empty, (uint32_t)(lu - 1) & 1u, BT_SPIN)) {
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                bt_expect_tx(&c_full, BU_CT);
+                bt_tma_2d(base + VU_TILE + 2 * Z_TILE, &mC, (int)(k + r * BU_R), (int)(k + nbk + j * BU_N), &c_full);
+                s_last_c = lu;
             }
         }
     } else if (warp == 1) {
@@ -710,14 +731,21 @@ k_bu(float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, int64_t 
         for (int lu = 0; lu < nloc; ++lu) {
             const int64_t u = u0 + lu, r = u / n_ct, j = u % n_ct;
             const int b = lu & 1;
-            // the thread's 32 elements of C first: their loads overlap the MMAs
+            // the thread's 32 elements of C first, from the TMA-loaded tile (which then
+            // goes back to the loader for the next unit): they overlap the MMAs
             const int64_t i = r * BU_R + 32 * qd + lane;          // panel-local row
             const int64_t c0 = j * BU_N + 32 * hf;
             float *col = F + (k + i) + (k + nbk + c0) * ld;
             const int64_t nvalid = (i < mp) ? n_tr - c0 : 0;
+            if (!tc::mbar_wait(&c_full, (uint32_t)lu & 1u, BT_SPIN)) {
+                s_fail = 1;
+                break;
+            }
             float cv[32];
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) cv[jj] = (jj < nvalid) ? col[(int64_t)jj * ld] : 0.f;
+            for (int jj = 0; jj < 32; ++jj) cv[jj] = Cs[(32 * hf + jj) * BU_R + 32 * qd + lane];
+            __syncwarp();
+            if (lane == 0) bt_arrive(&c_empty);
             if (!tc::mbar_wait(&acc_full[b], (uint32_t)(lu >> 1) & 1u, BT_SPIN)) {
                 s_fail = 1;
                 break;
@@ -755,6 +783,7 @@ k_bu(float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, int64_t 
                 if (s_last_z[s] >= 0) tc::mbar_wait(&z_full[s], (uint32_t)(s_last_z[s] >> 1) & 1u, BT_SPIN);
             const int lc = s_last_commit;
             if (lc >= 0) tc::mbar_wait(&acc_full[lc & 1], (uint32_t)(lc >> 1) & 1u, BT_SPIN);
+            if (s_last_c >= 0) tc::mbar_wait(&c_full, (uint32_t)s_last_c & 1u, BT_SPIN);
         }
         __syncthreads();
     }
@@ -803,8 +832,10 @@ int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64
     unsigned char *Zimg = (unsigned char *)fl_ws(ctx, FL_WS_BLK_Z, (size_t)n_ct * Z_TILE);
     if (!VY || !VU || !Ypart || !Zimg) return FASTLSQ_ERR_NOMEM;
     float *Ysum = Ypart + (size_t)S * n_ext * BK;
-    CUtensorMap mF;
-    if (!fl_encode_f32_map(&mF, F, ld, ntot, BY_KC, BY_N, false)) return 1;
+    CUtensorMap mF, mC;
+    if (!fl_encode_f32_map(&mF, F, ld, ntot, BY_KC, BY_N, false) ||
+        !fl_encode_f32_map(&mC, F, ld, ntot, BU_R, BU_N, false))
+        return 1;
     {
         FL_PROF(ctx, FASTLSQ_K_BLOCK_PREP);
         k_bimg<<<(unsigned)n_rt, 256, BI_SMEM, ctx->stream>>>(F, ld, k, nbk, mp, nch, VY, VU);
@@ -835,7 +866,7 @@ int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64
         const int64_t units = n_rt * n_ct;
         const unsigned G = (unsigned)std::min<int64_t>(ctx->num_sms, units);
         FL_PROF(ctx, FASTLSQ_K_BLOCK_U);
-        k_bu<<<G, BU_THREADS, BU_SMEM, ctx->stream>>>(F, ld, k, nbk, mp, n_ext, VU, Zimg, n_ct, units,
+        k_bu<<<G, BU_THREADS, BU_SMEM, ctx->stream>>>(mC, F, ld, k, nbk, mp, n_ext, VU, Zimg, n_ct, units,
                                                       ctx->d_flag);
         FL_CHECK_LAUNCH(ctx, "block update");
     }
