@@ -306,10 +306,27 @@ k_panel_tall(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_abort = 0;
     }
-    // the CTA's rows (columns past the panel zero), read along F's columns
-    for (int idx = threadIdx.x; idx < nown * PT_NB; idx += PT_NT) {
-        const int c = idx / nown, r = idx - c * nown;
-        P[r * PT_LD + c] = (c < ncols) ? F[(k + c0 + r) + (k + c) * ld] : 0.f;
+    // the CTA's rows (columns past the panel zero), read along F's columns: a thread's
+    // rows r, r + 768, .. of all 16 columns, their loads in flight together, then each
+    // row as 16-byte stores
+    for (int r0 = threadIdx.x; r0 < nown; r0 += 2 * PT_NT) {
+        float a[2][PT_NB];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = r0 + h * PT_NT;
+#pragma unroll
+            for (int c = 0; c < PT_NB; ++c)
+                a[h][c] = (r < nown && c < ncols) ? F[(k + c0 + r) + (k + c) * ld] : 0.f;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = r0 + h * PT_NT;
+            if (r < nown)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<float4 *>(P + r * PT_LD + 4 * q) =
+                        make_float4(a[h][4 * q], a[h][4 * q + 1], a[h][4 * q + 2], a[h][4 * q + 3]);
+        }
     }
     for (int idx = threadIdx.x; idx < 16 * 17; idx += PT_NT) G[idx] = 0.f;
     if (threadIdx.x < 16) tauv[threadIdx.x] = 0.f;
@@ -478,9 +495,12 @@ k_panel_tall(float *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols,
     __syncthreads();
 
     // the factored rows: R on and above the diagonal, V below
-    for (int idx = threadIdx.x; idx < nown * PT_NB; idx += PT_NT) {
-        const int c = idx / nown, r = idx - c * nown;
-        if (c < ncols) F[(k + c0 + r) + (k + c) * ld] = P[r * PT_LD + c];
+    for (int r = threadIdx.x; r < nown; r += PT_NT) {
+        float a[PT_NB];
+        pt_load_row(P + r * PT_LD, a);
+#pragma unroll
+        for (int c = 0; c < PT_NB; ++c)
+            if (c < ncols) F[(k + c0 + r) + (k + c) * ld] = a[c];
     }
     if (rank == 0 && warp == 0) {
         // T = (I + D N)^{-1} D with N = striu(V^T V), D = diag(tau): lane c solves the
