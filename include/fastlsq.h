@@ -582,7 +582,10 @@ typedef enum {
                                       stream while the rest of panel p's trailing update runs
                                       on a second, low-priority stream of the context (joined
                                       back into the caller's stream before the next panel's
-                                      update); 0: everything on the caller's stream, one
+                                      update); in the two-level factor the outer-block
+                                      update pass also does the next block's columns first
+                                      and the rest on a third stream beside that block's
+                                      panels; 0: everything on the caller's stream, one
                                       update pass per panel (faster when several
                                       independent solves run on other streams and fill
                                       the SMs beside each panel) */

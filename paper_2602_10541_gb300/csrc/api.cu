@@ -164,12 +164,18 @@ extern "C" int fastlsq_create(fastlsq_ctx **out, int device, void *stream)
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->aux_stream, cudaStreamNonBlocking, lo);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->aux2_stream, cudaStreamNonBlocking, lo);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming);
     }
     if (e != cudaSuccess) {
         int rc = (e == cudaErrorMemoryAllocation) ? FASTLSQ_ERR_NOMEM : FASTLSQ_ERR_CUDA;
         if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
         if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
         if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+        if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
+        if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
+        if (ctx->aux2_stream) cudaStreamDestroy(ctx->aux2_stream);
         if (ctx->d_flag) cudaFree(ctx->d_flag);
         if (ctx->d_grid_bar) cudaFree(ctx->d_grid_bar);
         delete ctx;
@@ -213,6 +219,7 @@ static void prof_collect(fastlsq_ctx *ctx)
 {
     cudaStreamSynchronize(ctx->stream);
     if (ctx->aux_stream) cudaStreamSynchronize(ctx->aux_stream);
+    if (ctx->aux2_stream) cudaStreamSynchronize(ctx->aux2_stream);
     for (int k = 0; k < FASTLSQ_K_COUNT; ++k) {
         for (size_t i = 0; i + 1 < ctx->prof.used[k]; i += 2) {
             float ms = 0.f;
@@ -253,9 +260,13 @@ extern "C" int fastlsq_destroy(fastlsq_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->aux_stream) cudaStreamSynchronize(ctx->aux_stream);
+    if (ctx->aux2_stream) cudaStreamSynchronize(ctx->aux2_stream);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
+    if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
+    if (ctx->aux2_stream) cudaStreamDestroy(ctx->aux2_stream);
     for (int k = 0; k < FASTLSQ_K_COUNT; ++k)
         for (cudaEvent_t e : ctx->prof.ev[k]) cudaEventDestroy(e);
     for (int s = 0; s < FL_WS_COUNT; ++s)

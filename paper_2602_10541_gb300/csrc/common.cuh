@@ -104,6 +104,9 @@ struct fastlsq_ctx {
     int trsv32 = 1;                 // FP32 arithmetic in the triangular solves of classical refinement
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t aux2_stream = nullptr;   // the rest of an outer block's update pass (look-ahead)
+    cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
+    int join2_pending = 0;                // ev_join2 recorded and not yet waited for
     cudaEvent_t refine_event = nullptr;   // waited on before reads of A_refine (caller's)
     double *eval_static = nullptr;  // device address of fastlsq_eval_noalloc's fixed scratch
     // Cody-Waite split of 2 pi for the FP32 argument reduction (host-derived)

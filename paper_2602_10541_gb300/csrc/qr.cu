@@ -941,6 +941,7 @@ static int factor_blocked(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t m_aug,
     if (!counters) return FASTLSQ_ERR_NOMEM;
     cudaMemsetAsync(counters, 0, cbytes, ctx->stream);
     const bool la = ctx->lookahead && ctx->aux_stream && ctx->panel_reg && ctx->fuse_next;
+    const int split = (ctx->lookahead && ctx->aux2_stream) ? 1 : 0;
     for (int64_t k = 0; k < n; k += BLK) {
         const int nbk = (int)std::min<int64_t>(BLK, n - k);
         bool factored = false;        // this inner panel was factored by the previous step's look-ahead
@@ -988,9 +989,14 @@ static int factor_blocked(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t m_aug,
             all_g = false;
             continue;
         }
+        // with look-ahead, the next block's columns are updated first and its panels start
+        // while the rest of this block's update pass runs beside them
         const int rc = fl_block_update_f32(ctx, F, ld, k, m_aug, nbk, ntot, NB, Tall + (k / NB) * NB * NB,
-                                           Gall ? Gall + (k / BLK) * BLK * BLK : nullptr);
-        if (rc < 0) return rc;
+                                           Gall ? Gall + (k / BLK) * BLK * BLK : nullptr, split);
+        if (rc < 0) {
+            fl_block_join(ctx);
+            return rc;
+        }
         if (rc == 1) {      // shape not taken: the block's panels update the columns one by one
             all_g = false;
             for (int64_t kp = k; kp < k + nbk; kp += NB) {
@@ -1001,6 +1007,7 @@ static int factor_blocked(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t m_aug,
             }
         }
     }
+    FL_TRY(fl_block_join(ctx));
     if (all_g) {
         FL_TRY(fl_block_t_f32(ctx, Gall, Tall, n, NB, Tball));
         if (tb_ok) *tb_ok = 1;

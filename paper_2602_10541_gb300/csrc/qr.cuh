@@ -75,9 +75,12 @@ int fl_trailing_tc_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_
 // C <- H^T C for the block of nbk <= 128 columns at column k (inner panels of width nb,
 // T factors from Tb on), C = F's columns k + nbk .. ntot.  Returns 1 when the shape is
 // not taken (unaligned factor).  Gout (may be null) receives the block's Gram matrix
-// V^T V, G[e * 128 + l] = v_l^T v_e for l, e < nbk.
+// V^T V, G[e * 128 + l] = v_l^T v_e for l, e < nbk.  With split_next the update pass of
+// the next block's 128 columns runs on the caller's stream and the rest on the context's
+// second auxiliary stream, to be joined by fl_block_join (the next call joins first).
 int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int nbk,
-                        int64_t ntot, int nb, const float *Tb, float *Gout = nullptr);
+                        int64_t ntot, int nb, const float *Tb, float *Gout = nullptr, int split_next = 0);
+int fl_block_join(fastlsq_ctx *ctx);
 
 // TMA descriptor of the factor F (ld rows x ntot columns, column-major fp32) as a 2-D
 // tensor with boxes of box_r rows x box_c columns, out-of-range elements read as zero

@@ -588,8 +588,8 @@ k_bz(const float *__restrict__ Ysum, int64_t n_ext, int nbk, const float *__rest
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(BU_THREADS, 1)
 k_bu(const __grid_constant__ CUtensorMap mC, float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp,
-     int64_t n_ext, const unsigned char *__restrict__ VU, const unsigned char *__restrict__ Zimg, int64_t n_ct,
-     int64_t n_units, int *flag)
+     int64_t n_ext, const unsigned char *__restrict__ VU, const unsigned char *__restrict__ Zimg, int64_t j0,
+     int64_t nj, int64_t n_units, int *flag)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = bt_align1024(smem_raw);
@@ -634,7 +634,7 @@ k_bu(const __grid_constant__ CUtensorMap mC, float *__restrict__ F, int64_t ld, 
             int64_t prev_r = -1;
             int loads = 0;
             for (int lu = 0; lu < nloc; ++lu) {
-                const int64_t u = u0 + lu, r = u / n_ct, j = u % n_ct;
+                const int64_t u = u0 + lu, r = u / nj, j = j0 + u % nj;
                 if (r != prev_r) {
                     if (loads > 0 && !tc::mbar_wait(&vu_empty, (uint32_t)(loads - 1) & 1u, BT_SPIN)) {
                         s_fail = 1;
@@ -660,7 +660,7 @@ k_bu(const __grid_constant__ CUtensorMap mC, float *__restrict__ F, int64_t ld, 
             // the units' tiles of C by TMA into the one C buffer, once the epilogue has read
             // the previous tile out of it
             for (int lu = 0; lu < nloc; ++lu) {
-                const int64_t u = u0 + lu, r = u / n_ct, j = u % n_ct;
+                const int64_t u = u0 + lu, r = u / nj, j = j0 + u % nj;
                 if (lu >= 1 && !tc::mbar_wait(&c_empty, (uint32_t)(lu - 1) & 1u, BT_SPIN)) {
                     s_fail = 1;
                     break;
@@ -682,7 +682,7 @@ k_bu(const __grid_constant__ CUtensorMap mC, float *__restrict__ F, int64_t ld, 
 #pragma unroll
                 for (int p = 0; p < 3; ++p) dA[h][p] = tc::smem_desc_sw128(VUs + (h * 3 + p) * PART128);
             for (int lu = 0; lu < nloc; ++lu) {
-                const int64_t u = u0 + lu, r = u / n_ct;
+                const int64_t u = u0 + lu, r = u / nj;
                 if (r != prev_r) {
                     if (!tc::mbar_wait(&vu_full, (uint32_t)vu_idx & 1u, BT_SPIN)) {
                         s_fail = 1;
@@ -721,7 +721,7 @@ k_bu(const __grid_constant__ CUtensorMap mC, float *__restrict__ F, int64_t ld, 
                 }
                 tc::mma_commit(&z_empty[s]);
                 tc::mma_commit(&acc_full[b]);
-                const int64_t rn = (lu + 1 < nloc) ? (u + 1) / n_ct : -1;
+                const int64_t rn = (lu + 1 < nloc) ? (u + 1) / nj : -1;
                 if (rn != r) tc::mma_commit(&vu_empty);
                 s_last_commit = lu;
             }
@@ -729,7 +729,7 @@ k_bu(const __grid_constant__ CUtensorMap mC, float *__restrict__ F, int64_t ld, 
     } else {
         const int qd = warp & 3, hf = (warp - 2) >> 2;    // lane quarter, 32-column half
         for (int lu = 0; lu < nloc; ++lu) {
-            const int64_t u = u0 + lu, r = u / n_ct, j = u % n_ct;
+            const int64_t u = u0 + lu, r = u / nj, j = j0 + u % nj;
             const int b = lu & 1;
             // the thread's 32 elements of C first, from the TMA-loaded tile (which then
             // goes back to the loader for the next unit): they overlap the MMAs
@@ -805,8 +805,9 @@ constexpr size_t bz_smem(int nb) { return sizeof(float) * (128 * 129 + 2 * 128 *
 // Returns 1 when the shape is not taken (alignment), the caller then updates panel by
 // panel.
 int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64_t m_aug, int nbk,
-                        int64_t ntot, int nb, const float *Tb, float *Gout)
+                        int64_t ntot, int nb, const float *Tb, float *Gout, int split_next)
 {
+    FL_TRY(fl_block_join(ctx));           // the previous block's split update pass
     const int64_t mp = m_aug - k, n_ext = ntot - k, n_tr = n_ext - nbk;
     if (n_tr <= 0 || mp <= 0) return 0;
     if (nbk < 1 || nbk > BK || (nb != 16 && nb != 32) || ld % 4 != 0 || k % 4 != 0 ||
@@ -862,13 +863,40 @@ int fl_block_update_f32(fastlsq_ctx *ctx, float *F, int64_t ld, int64_t k, int64
             k_bz<16><<<(unsigned)n_ct, 256, bz_smem(16), ctx->stream>>>(Ysum, n_ext, nbk, Tb, Zimg);
         FL_CHECK_LAUNCH(ctx, "block Z");
     }
-    {
-        const int64_t units = n_rt * n_ct;
+    // the update pass over column tiles [j0, j0 + nj)
+    auto update = [&](int64_t j0, int64_t nj) -> int {
+        const int64_t units = n_rt * nj;
         const unsigned G = (unsigned)std::min<int64_t>(ctx->num_sms, units);
         FL_PROF(ctx, FASTLSQ_K_BLOCK_U);
-        k_bu<<<G, BU_THREADS, BU_SMEM, ctx->stream>>>(mC, F, ld, k, nbk, mp, n_ext, VU, Zimg, n_ct, units,
+        k_bu<<<G, BU_THREADS, BU_SMEM, ctx->stream>>>(mC, F, ld, k, nbk, mp, n_ext, VU, Zimg, j0, nj, units,
                                                       ctx->d_flag);
         FL_CHECK_LAUNCH(ctx, "block update");
-    }
+        return 0;
+    };
+    const int64_t nj_next = BK / BU_N;            // the next outer block's columns
+    if (!split_next || n_ct <= nj_next) return update(0, n_ct);
+    // the next block's columns first, on the caller's stream; the rest on the second
+    // auxiliary stream, joined back before the next block's update (fl_block_join)
+    FL_TRY(update(0, nj_next));
+    cudaError_t e = cudaEventRecord(ctx->ev_fork2, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux2_stream, ctx->ev_fork2, 0);
+    if (e != cudaSuccess) return fl_cuda(ctx, e, "block update fork");
+    cudaStream_t main_stream = ctx->stream;
+    ctx->stream = ctx->aux2_stream;
+    const int rc = update(nj_next, n_ct - nj_next);
+    if (rc == 0) e = cudaEventRecord(ctx->ev_join2, ctx->aux2_stream);
+    ctx->stream = main_stream;
+    FL_TRY(rc);
+    if (e != cudaSuccess) return fl_cuda(ctx, e, "block update join");
+    ctx->join2_pending = 1;
+    return 0;
+}
+
+int fl_block_join(fastlsq_ctx *ctx)
+{
+    if (!ctx->join2_pending) return 0;
+    ctx->join2_pending = 0;
+    const cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join2, 0);
+    if (e != cudaSuccess) return fl_cuda(ctx, e, "block update join");
     return 0;
 }
