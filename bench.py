@@ -608,6 +608,8 @@ def main():
                          "(0: the workload's default, 4 for poisson5d, 8 for helmholtz2d)")
     ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
                     help="assemble the FP64 operator on a side stream during the factorisation")
+    ap.add_argument("--fused-lookahead", type=int, default=1, choices=[0, 1],
+                    help="with look-ahead, 1: panels apply the previous panel's update in their prologue")
     ap.add_argument("--split-rows", type=int, default=256,
                     help="least rows per split of the SIMT updates inside an outer block")
     ap.add_argument("--lookahead", type=int, default=0, choices=[0, 1],
@@ -646,6 +648,7 @@ def main():
         fl.fastlsq_set_option(c, fl.OPT_TRSV_FP32, args.trsv_fp32)
         fl.fastlsq_set_option(c, fl.OPT_LOOKAHEAD, args.lookahead)
         fl.fastlsq_set_option(c, fl.OPT_SPLIT_ROWS, args.split_rows)
+        fl.fastlsq_set_option(c, fl.OPT_FUSED_LOOKAHEAD, args.fused_lookahead)
         wi = make(seed_offset=rank * B + i)
         with torch.cuda.stream(c.stream):
             dpi = pl.upload(wi, dev)
@@ -886,6 +889,7 @@ def main():
                            "tensor_core_updates": int(solve_stats.tensor_core),
                            "panel_nb": nb, "outer_block": BLK if blocked else None,
                            "lookahead": bool(args.lookahead), "split_rows": args.split_rows,
+                           "fused_lookahead": bool(args.fused_lookahead),
                            "l2": "flushed between steps (256 MiB write outside the step events)",
                            "instances_per_step": B,
                            "concurrency": (f"{B} independent instances (seeds) of the workload per step, "
