@@ -547,8 +547,17 @@ def _inverse_row(fl, pl, wl, torch, ctx, dev, n_inst):
         b.record(ctx.stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
+    # FP64 FMAs of one evaluation of the batch: Q^T and Q each a dot pass and an update
+    # pass over the reflectors (2 (m_aug n - n^2 / 2) each), two triangular solves (n^2 / 2
+    # each): 4 m_aug n per instance, m_aug = interior + boundary + Tikhonov rows
+    fma = sum(4.0 * (w.n_int + w.n_bc + w.n_feat) * w.n_feat for w in ws)
+    tfma = fma / (ms / 1e3) / 1e12
     out = {"instances": n_inst, "setup_s": setup_s, "factorizations_per_s": n_inst / setup_s,
            "ms_per_batch_eval": ms, "gradient_evals_per_s": n_inst / (ms / 1e3),
+           "roofline": {"bound": "fp64", "achieved": tfma, "unit": "TFMA/s", "peak": 0.625,
+                        "frac": tfma / 0.625, "work_fma_per_eval": fma,
+                        "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (0.625 TFMA/s); a cuBLAS DGEMM "
+                                       "on this pool measured 1.10 TFLOP/s"},
            "launch": batch.launch,
            "rows_range": [int(min(w.n_int for w in ws)), int(max(w.n_int for w in ws))],
            "features_range": [int(min(w.n_feat for w in ws)), int(max(w.n_feat for w in ws))],
