@@ -401,23 +401,29 @@ FASTLSQ_API int fastlsq_inverse_batch(fastlsq_ctx *ctx, const fastlsq_inverse_in
  * (the factor is kept by the plan), tabulates the sensor matrix H_s[s][j] =
  * scale sin(W_j . x_s + b_j) and records the instances' device pointers.  opts: mu > 0
  * and bc_weight are used; prec, refine and adjoint fields are ignored (the factor is
- * FP64).  Limits: n_src <= 8, n_sens <= 256, and n_int + n_bc + n_feat small enough
- * that one instance's vector of that length plus one of n_feat (FP64) fit in a CTA's
- * shared memory (about 26,000 in all on GB300), else -1.  Synchronises the context's
- * stream; returns 0 and *plan, or a negative status (nothing is kept).
+ * FP64).  The factorisations run a few at a time on worker streams of the library's
+ * own, after the work already queued on the context's stream.  Limits: n_src <= 8,
+ * n_sens <= 256, and n_int + n_bc + n_feat small enough that a quarter of one
+ * instance's vector of that length plus one of n_feat (FP64) fit in a CTA's shared
+ * memory, else -1 (the evaluation's configuration must fit too).  Synchronises the
+ * context's stream; returns 0 and *plan, or a negative status (nothing is kept).
  *
  * fastlsq_inverse_eval runs one gradient evaluation of every instance in ONE
- * persistent launch: a grid of min(n_inst, SMs * ctas_per_sm) CTAs of `threads`
- * threads (256 or 512) takes instances from a device-side queue, longest first
- * (m_aug n_feat); one CTA evaluates an instance entirely:
+ * persistent launch: a grid of min(n_inst, SMs * ctas_per_sm / cluster) clusters of
+ * `cluster` CTAs (1, 2 or 4) of `threads` threads (256 or 512) takes instances from a
+ * device-side queue, longest first (m_aug n_feat); one cluster evaluates an instance
+ * entirely, its m_aug-vectors dealt over the ranks in stripes of 32 rows:
  *   y = Q^T [s(x_int; theta); 0; 0], beta = R^{-1} y[0:n], u_s = H_s beta,
  *   loss = mean (u_s - y_obs)^2, w = R^{-T} H_s^T dloss/du_s, z = Q [w; 0]
  *   (= A (A^T A + mu I)^{-1} H_s^T g), dtheta = sum_{i < n_int} z_i ds(x_i)/dtheta,
  * writing beta, loss and dtheta through the instances' pointers.  It reads theta and
  * y_obs at run time, allocates nothing and does not synchronise, so it can be captured
  * in a CUDA graph and replayed after the caller updates theta or y_obs in place.  No
- * CTA waits on another (the queue is one atomic counter).  -1 for other threads or
- * ctas_per_sm values (1..4) whose shared memory does not fit.
+ * cluster waits on another (the queue is one atomic counter); the ranks of a cluster
+ * meet at hardware cluster barriers.  Results are deterministic for a given cluster
+ * size (fixed summation orders); other cluster sizes sum in another order.  -1 for
+ * other threads, cluster or ctas_per_sm values (1..4), or a shape whose shared memory
+ * does not fit.
  *
  * fastlsq_inverse_plan_destroy synchronises the plan's stream and frees the factors,
  * the sensor matrices and the tables.
@@ -427,7 +433,7 @@ FASTLSQ_API int fastlsq_inverse_prepare(fastlsq_ctx *ctx, const fastlsq_inverse_
                                         int32_t n_inst, const fastlsq_op *op, int32_t n_src,
                                         const fastlsq_inverse_opts *opts, fastlsq_inverse_plan **plan);
 FASTLSQ_API int fastlsq_inverse_eval(fastlsq_ctx *ctx, const fastlsq_inverse_plan *plan,
-                                     int32_t threads, int32_t ctas_per_sm);
+                                     int32_t threads, int32_t ctas_per_sm, int32_t cluster);
 FASTLSQ_API int fastlsq_inverse_plan_destroy(fastlsq_inverse_plan *plan);
 
 /*

@@ -4,21 +4,29 @@
 // batch in ONE persistent launch.
 //
 // fastlsq_inverse_prepare factors each instance once (FP64 Householder QR of
-// [A; sqrt(mu) I], kept: the checkpoint the evaluations reuse) and tabulates its
-// sensor matrix H_s (n_sens x n_feat, FP64).  fastlsq_inverse_eval launches
-// k_inv_eval: a grid of persistent CTAs that take instances from a device-side queue
-// (one atomic counter, instances in decreasing order of m_aug n, so the longest start
-// first); one CTA runs an instance's whole evaluation with its vectors in shared memory:
+// [A; sqrt(mu) I], kept: the checkpoint the evaluations reuse; several instances at a
+// time on worker streams) and tabulates its sensor matrix H_s (n_sens x n_feat, FP64).
+// fastlsq_inverse_eval launches k_inv_eval: a grid of persistent clusters of C CTAs
+// (C = 1, 2 or 4) that take instances from a device-side queue (one atomic counter,
+// instances in decreasing order of m_aug n, so the longest start first); a cluster runs
+// an instance's whole evaluation with its vectors in shared memory, the m_aug-vectors
+// dealt over the ranks in stripes of 32 rows:
 //   y   = [s(x_int; theta); 0 (u = 0 rows); 0 (sqrt(mu) rows)]
-//   y  <- Q^T y                       (the factor's reflectors, panel by panel)
-//   beta = R^{-1} y[0:n]              (blocked substitution)
+//   y  <- Q^T y                       (the factor's reflectors, panel by panel; per
+//                                      panel the ranks' partial V^T y exchanged
+//                                      through distributed shared memory)
+//   beta = R^{-1} y[0:n]              (blocked substitution, rank 0)
 //   u_s = H_s beta, L = mean (u_s - y_obs)^2, g = dL/du_s
-//   w   = R^{-T} (H_s^T g)
+//   w   = R^{-T} (H_s^T g)            (rank 0)
 //   z   = Q [w; 0]                    (= A (A^T A + mu I)^{-1} H_s^T g = dL/d rhs)
-//   dL/dtheta = sum_{i < n_int} z_i ds(x_i; theta)/dtheta
-// No CTA waits on another: the queue is the only shared state, so nothing needs a
-// timeout.  The launch allocates nothing and synchronises nothing on the host, so a
-// caller can capture it in a CUDA graph and replay it with new theta and y_obs.
+//   dL/dtheta = sum_{i < n_int} z_i ds(x_i; theta)/dtheta   (ranks' sums in rank order)
+// Clusters do not wait on one another: the queue is their only shared state; inside a
+// cluster the ranks meet at hardware cluster barriers, which the ranks, launched
+// together, always reach.  The launch allocates nothing and synchronises nothing on the
+// host, so a caller can capture it in a CUDA graph and replay it with new theta and
+// y_obs.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -29,11 +37,14 @@
 #include "common.cuh"
 #include "qr.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace {
 
 constexpr int IB_MAX_SRC = 8;
 constexpr int IB_MAX_SENS = 256;
 constexpr int IB_NB = 32;              // largest panel width of an FP64 factor
+constexpr int IB_SETUP_WORKERS = 4;    // concurrent factorisations in the setup
 
 struct InvDesc {
     int64_t n_int, n_feat, n_sens, m_aug, ld;
@@ -71,11 +82,43 @@ __device__ __forceinline__ double ib_reduce_scatter(double (&vals)[IB_NB], int l
     return vals[0];
 }
 
-// y <- Q^T y (transpose) or Q y on the CTA's shared vector y[0, m_aug), FP64.  Per
-// panel: s = V^T y (each thread its rows, warp reduce-scatter, warps summed in order),
-// w = T^T s or T s, y -= V w.
-template <int THREADS>
-__device__ void ib_apply_q(const InvDesc &D, double *y, double *red, double *wv, bool transpose)
+// Rows of an instance's m_aug-vectors held by one CTA of a cluster of C: stripes of 32
+// rows dealt round-robin (stripe t of rank r is rows 32 (t C + r) .. + 31), kept at local
+// index 32 t + (row & 31).  Every panel's rows [k, m_aug) are then shared almost evenly
+// by the cluster, and a warp's 32 consecutive local rows are 32 consecutive rows of the
+// factor (coalesced).  C = 1 is the identity.
+template <int C>
+struct IbRows {
+    int rank;
+    __device__ __forceinline__ int64_t glob(int64_t lr) const
+    {
+        return (C == 1) ? lr : (((lr >> 5) * C + rank) << 5) + (lr & 31);
+    }
+    // first local index whose row is >= k
+    __device__ __forceinline__ int64_t first(int64_t k) const
+    {
+        if (C == 1) return k;
+        const int64_t sk = k >> 5;
+        const int64_t t = (sk >= rank) ? (sk - rank + C - 1) / C : 0;
+        return (t * C + rank == sk) ? (t << 5) + (k & 31) : (t << 5);
+    }
+};
+
+// The cluster's shared state of one CTA: the exchange buffers written by the other
+// ranks through distributed shared memory.
+struct IbXchg {
+    double *xs;        // [2][C][32]  per-panel partial sums s = V^T y, double-buffered
+    double *xd;        // [C][4 IB_MAX_SRC]  per-rank partial gradients
+    int flip;          // which half of xs the next exchange uses
+};
+
+// y <- Q^T y (transpose) or Q y on the cluster's distributed vector y (this CTA's rows,
+// local indices), FP64.  Per panel: s = V^T y (each thread its rows, warp
+// reduce-scatter, warps summed in order; with C > 1 the ranks' sums exchanged and
+// added in rank order, so every rank holds the same s), w = T^T s or T s, y -= V w.
+template <int THREADS, int C>
+__device__ void ib_apply_q(const InvDesc &D, const IbRows<C> &rows, double *y, double *red, double *wv,
+                           IbXchg &xc, bool transpose)
 {
     constexpr int NW = THREADS / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -86,11 +129,14 @@ __device__ void ib_apply_q(const InvDesc &D, double *y, double *red, double *wv,
         const int p = transpose ? step : P - 1 - step;
         const int64_t k = (int64_t)p * nb;
         const int nc = (int)fl_min64(nb, n - k);
+        const int64_t lr0 = rows.first(k);
         double acc[IB_NB];
 #pragma unroll
         for (int l = 0; l < IB_NB; ++l) acc[l] = 0.0;
-        for (int64_t i = k + tid; i < m_aug; i += THREADS) {
-            const double yi = y[i];
+        for (int64_t lr = lr0 + tid;; lr += THREADS) {
+            const int64_t i = rows.glob(lr);
+            if (i >= m_aug) break;
+            const double yi = y[lr];
             const int64_t li = i - k;
             const double *row = D.F + i + k * ld;
             if (li >= IB_NB) {
@@ -108,10 +154,25 @@ __device__ void ib_apply_q(const InvDesc &D, double *y, double *red, double *wv,
         const double part = ib_reduce_scatter(acc, lane);
         red[warp * IB_NB + lane] = part;
         __syncthreads();
+        double s = 0.0;
         if (warp == 0) {
-            double s = 0.0;
 #pragma unroll
             for (int w = 0; w < NW; ++w) s += red[w * IB_NB + lane];
+        }
+        if constexpr (C > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            double *buf = xc.xs + xc.flip * C * IB_NB;
+            if (warp == 0)
+                for (int r = 0; r < C; ++r) cl.map_shared_rank(buf, r)[rows.rank * IB_NB + lane] = s;
+            cl.sync();
+            if (warp == 0) {
+                s = 0.0;
+#pragma unroll
+                for (int r = 0; r < C; ++r) s += buf[r * IB_NB + lane];
+            }
+            xc.flip ^= 1;
+        }
+        if (warp == 0) {
             const double *T = D.T + (int64_t)p * nb * nb;      // T(q, l) at q + l nb
             double wl = 0.0;
             for (int q = 0; q < nc; ++q) {
@@ -124,22 +185,24 @@ __device__ void ib_apply_q(const InvDesc &D, double *y, double *red, double *wv,
             wv[lane] = (lane < nc) ? wl : 0.0;
         }
         __syncthreads();
-        for (int64_t i = k + tid; i < m_aug; i += THREADS) {
+        for (int64_t lr = lr0 + tid;; lr += THREADS) {
+            const int64_t i = rows.glob(lr);
+            if (i >= m_aug) break;
             const int64_t li = i - k;
             const double *row = D.F + i + k * ld;
-            double s = 0.0;
+            double t = 0.0;
             if (li >= IB_NB) {
 #pragma unroll
                 for (int l = 0; l < IB_NB; ++l)
-                    if (l < nc) s = fma(row[(int64_t)l * ld], wv[l], s);
+                    if (l < nc) t = fma(row[(int64_t)l * ld], wv[l], t);
             } else {
 #pragma unroll
                 for (int l = 0; l < IB_NB; ++l) {
                     const double v = (l >= nc || li < l) ? 0.0 : (li == l ? 1.0 : row[(int64_t)l * ld]);
-                    s = fma(v, wv[l], s);
+                    t = fma(v, wv[l], t);
                 }
             }
-            y[i] -= s;
+            y[lr] -= t;
         }
         __syncthreads();
     }
@@ -229,32 +292,52 @@ __device__ double ib_block_sum(double v, double *red)
     return s;
 }
 
-template <int THREADS>
+// One gradient evaluation of every instance: clusters of C CTAs take instances from the
+// queue (rank 0 draws, the others read its draw); each rank holds its stripes of y.
+template <int THREADS, int C>
 __global__ void __launch_bounds__(THREADS)
 k_inv_eval(const InvDesc *__restrict__ descs, const int *__restrict__ order, int n_inst,
-           int *__restrict__ queue, int n_src, int64_t m_aug_max, int64_t n_max)
+           int *__restrict__ queue, int n_src, int64_t y_rows, int64_t n_max)
 {
     constexpr int NW = THREADS / 32;
     extern __shared__ double ib_sm[];
-    double *y = ib_sm;                          // [m_aug_max]
-    double *xv = y + m_aug_max;                 // [n_max]
+    double *y = ib_sm;                          // [y_rows]: this rank's stripes
+    double *xv = y + y_rows;                    // [n_max]   (rank 0)
     double *red = xv + n_max;                   // [NW][32]
     double *wv = red + NW * IB_NB;              // [32]
     double *gs = wv + IB_NB;                    // [IB_MAX_SENS]
     double *th = gs + IB_MAX_SENS;              // [4 IB_MAX_SRC]
+    IbXchg xc;
+    xc.xs = th + 4 * IB_MAX_SRC;                // [2][C][32]
+    xc.xd = xc.xs + 2 * C * IB_NB;              // [C][4 IB_MAX_SRC]
+    xc.flip = 0;
     __shared__ int s_q;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    IbRows<C> rows;
+    rows.rank = 0;
+    if constexpr (C > 1) rows.rank = (int)cg::this_cluster().block_rank();
+    const bool lead = rows.rank == 0;
     for (;;) {
-        if (tid == 0) s_q = atomicAdd(queue, 1);
-        __syncthreads();
-        const int q = s_q;
+        if (lead && tid == 0) s_q = atomicAdd(queue, 1);
+        int q;
+        if constexpr (C > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            cl.sync();
+            q = *cl.map_shared_rank(&s_q, 0);
+            cl.sync();                          // rank 0 keeps its shared memory until read
+        } else {
+            __syncthreads();
+            q = s_q;
+        }
         if (q >= n_inst) break;
         const InvDesc D = descs[order[q]];
         const int64_t n = D.n_feat;
         for (int t = tid; t < 4 * n_src; t += THREADS) th[t] = D.theta[t];
         __syncthreads();
         // source at the interior rows, zero elsewhere
-        for (int64_t i = tid; i < D.m_aug; i += THREADS) {
+        for (int64_t lr = tid;; lr += THREADS) {
+            const int64_t i = rows.glob(lr);
+            if (i >= D.m_aug) break;
             double v = 0.0;
             if (i < D.n_int) {
                 const double px = D.x_int[2 * i], py = D.x_int[2 * i + 1];
@@ -263,48 +346,76 @@ k_inv_eval(const InvDesc *__restrict__ descs, const int *__restrict__ order, int
                     v += th[4 * s + 3] * exp(-(dx * dx + dy * dy) / (2.0 * w * w));
                 }
             }
-            y[i] = v;
+            y[lr] = v;
         }
         __syncthreads();
-        ib_apply_q<THREADS>(D, y, red, wv, true);
-        for (int64_t j = tid; j < n; j += THREADS) xv[j] = y[j];
-        __syncthreads();
-        ib_trsv<THREADS>(D, xv, false);                          // beta
-        for (int64_t j = tid; j < n; j += THREADS) D.beta[j] = xv[j];
-        // sensors: warp per sensor, lanes over features
-        for (int64_t s = warp; s < D.n_sens; s += NW) {
-            const double *h = D.H + s * n;
-            double u = 0.0;
-            for (int64_t j = lane; j < n; j += 32) u = fma(h[j], xv[j], u);
+        ib_apply_q<THREADS, C>(D, rows, y, red, wv, xc, true);
+        // (Q^T y)[0, n] to rank 0
+        if constexpr (C > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            double *xv0 = cl.map_shared_rank(xv, 0);
+            for (int64_t lr = tid;; lr += THREADS) {
+                const int64_t i = rows.glob(lr);
+                if (i >= n) break;
+                xv0[i] = y[lr];
+            }
+            cl.sync();
+        } else {
+            for (int64_t j = tid; j < n; j += THREADS) xv[j] = y[j];
+            __syncthreads();
+        }
+        if (lead) {
+            ib_trsv<THREADS>(D, xv, false);                          // beta
+            for (int64_t j = tid; j < n; j += THREADS) D.beta[j] = xv[j];
+            // sensors: warp per sensor, lanes over features
+            for (int64_t s = warp; s < D.n_sens; s += NW) {
+                const double *h = D.H + s * n;
+                double u = 0.0;
+                for (int64_t j = lane; j < n; j += 32) u = fma(h[j], xv[j], u);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-            if (lane == 0) gs[s] = u - D.y_obs[s];
+                for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+                if (lane == 0) gs[s] = u - D.y_obs[s];
+            }
+            __syncthreads();
+            double l2 = 0.0;
+            for (int64_t s = tid; s < D.n_sens; s += THREADS) l2 += gs[s] * gs[s];
+            l2 = ib_block_sum<THREADS>(l2, red);
+            if (tid == 0) *D.loss = l2 / (double)D.n_sens;
+            for (int64_t s = tid; s < D.n_sens; s += THREADS) gs[s] *= 2.0 / (double)D.n_sens;
+            __syncthreads();
+            // grad_beta = H_s^T g, then w = R^{-T} grad_beta
+            for (int64_t j = tid; j < n; j += THREADS) {
+                double a = 0.0;
+                for (int64_t s = 0; s < D.n_sens; ++s) a = fma(D.H[s * n + j], gs[s], a);
+                xv[j] = a;
+            }
+            __syncthreads();
+            ib_trsv<THREADS>(D, xv, true);
         }
-        __syncthreads();
-        double l2 = 0.0;
-        for (int64_t s = tid; s < D.n_sens; s += THREADS) l2 += gs[s] * gs[s];
-        l2 = ib_block_sum<THREADS>(l2, red);
-        if (tid == 0) *D.loss = l2 / (double)D.n_sens;
-        for (int64_t s = tid; s < D.n_sens; s += THREADS) gs[s] *= 2.0 / (double)D.n_sens;
-        __syncthreads();
-        // grad_beta = H_s^T g, then w = R^{-T} grad_beta
-        for (int64_t j = tid; j < n; j += THREADS) {
-            double a = 0.0;
-            for (int64_t s = 0; s < D.n_sens; ++s) a = fma(D.H[s * n + j], gs[s], a);
-            xv[j] = a;
-        }
-        __syncthreads();
-        ib_trsv<THREADS>(D, xv, true);
         // z = Q [w; 0]
-        for (int64_t i = tid; i < D.m_aug; i += THREADS) y[i] = (i < n) ? xv[i] : 0.0;
+        {
+            const double *w0 = xv;
+            if constexpr (C > 1) {
+                cg::cluster_group cl = cg::this_cluster();
+                cl.sync();                                           // w complete on rank 0
+                w0 = cl.map_shared_rank(xv, 0);
+            }
+            for (int64_t lr = tid;; lr += THREADS) {
+                const int64_t i = rows.glob(lr);
+                if (i >= D.m_aug) break;
+                y[lr] = (i < n) ? w0[i] : 0.0;
+            }
+        }
         __syncthreads();
-        ib_apply_q<THREADS>(D, y, red, wv, false);
+        ib_apply_q<THREADS, C>(D, rows, y, red, wv, xc, false);
         // dL/dtheta = sum over the interior rows of z_i ds(x_i)/dtheta
         double acc[4 * IB_MAX_SRC];
 #pragma unroll
         for (int t = 0; t < 4 * IB_MAX_SRC; ++t) acc[t] = 0.0;
-        for (int64_t i = tid; i < D.n_int; i += THREADS) {
-            const double px = D.x_int[2 * i], py = D.x_int[2 * i + 1], zi = y[i];
+        for (int64_t lr = tid;; lr += THREADS) {
+            const int64_t i = rows.glob(lr);
+            if (i >= D.n_int) break;
+            const double px = D.x_int[2 * i], py = D.x_int[2 * i + 1], zi = y[lr];
 #pragma unroll
             for (int s = 0; s < IB_MAX_SRC; ++s) {
                 if (s >= n_src) break;
@@ -322,16 +433,36 @@ k_inv_eval(const InvDesc *__restrict__ descs, const int *__restrict__ order, int
         for (int t = 0; t < 4 * IB_MAX_SRC; ++t) {
             if (t >= 4 * n_src) break;                   // uniform over the CTA
             const double v = ib_block_sum<THREADS>(acc[t], red);
-            if (tid == 0) D.dtheta[t] = v;
+            if constexpr (C > 1) {
+                if (tid == 0) *(cg::this_cluster().map_shared_rank(xc.xd, 0) + rows.rank * 4 * IB_MAX_SRC + t) = v;
+            } else {
+                if (tid == 0) D.dtheta[t] = v;
+            }
+        }
+        if constexpr (C > 1) {
+            cg::this_cluster().sync();
+            if (lead)                                    // the ranks' sums in rank order
+                for (int t = tid; t < 4 * n_src; t += THREADS) {
+                    double v = 0.0;
+                    for (int r = 0; r < C; ++r) v += xc.xd[r * 4 * IB_MAX_SRC + t];
+                    D.dtheta[t] = v;
+                }
         }
         __syncthreads();
     }
 }
 
-size_t ib_smem(int threads, int64_t m_aug_max, int64_t n_max)
+// rows of y one rank holds: its stripes of the tallest instance
+int64_t ib_rows(int64_t m_aug_max, int cluster)
 {
-    return sizeof(double) * ((size_t)m_aug_max + (size_t)n_max + (size_t)(threads / 32) * IB_NB + IB_NB +
-                             IB_MAX_SENS + 4 * IB_MAX_SRC);
+    return 32 * ((fl_cdiv(m_aug_max, 32) + cluster - 1) / cluster);
+}
+
+size_t ib_smem(int threads, int64_t m_aug_max, int64_t n_max, int cluster)
+{
+    return sizeof(double) * ((size_t)ib_rows(m_aug_max, cluster) + (size_t)n_max + (size_t)(threads / 32) * IB_NB +
+                             IB_NB + IB_MAX_SENS + 4 * IB_MAX_SRC + 2 * (size_t)cluster * IB_NB +
+                             (size_t)cluster * 4 * IB_MAX_SRC);
 }
 
 }  // namespace
@@ -352,24 +483,34 @@ struct fastlsq_inverse_plan {
 
 namespace {
 
-template <int THREADS>
+template <int THREADS, int C>
 cudaError_t ib_launch(const fastlsq_inverse_plan *P, cudaStream_t st, int grid, size_t smem)
 {
     static FlOncePerDevice once;
     if (once.pending(P->device)) {
-        cudaError_t e = cudaFuncSetAttribute(k_inv_eval<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        // a later plan may need more: set the largest the device allows
+        // the largest the device allows, so that a later plan with taller instances fits
         int optin = 0;
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
-        e = cudaFuncSetAttribute(k_inv_eval<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
+        cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_inv_eval<THREADS, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - 1024);
         if (e != cudaSuccess) return e;
         once.done(P->device);
     }
-    k_inv_eval<THREADS><<<grid, THREADS, smem, st>>>(P->d_desc, P->d_order, P->n_inst, P->d_queue, P->n_src,
-                                                     P->m_aug_max, P->n_max);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_inv_eval<THREADS, C>, (const InvDesc *)P->d_desc, (const int *)P->d_order,
+                              P->n_inst, P->d_queue, P->n_src, ib_rows(P->m_aug_max, C), P->n_max);
 }
 
 void plan_free(fastlsq_inverse_plan *P)
@@ -416,8 +557,9 @@ extern "C" int fastlsq_inverse_prepare(fastlsq_ctx *ctx, const fastlsq_inverse_i
         n_max = std::max<int64_t>(n_max, I.n_feat);
         maug_max = std::max<int64_t>(maug_max, I.n_int + I.n_bc + I.n_feat);
     }
-    // the evaluation keeps y [m_aug] and one n-vector per CTA in shared memory
-    if (ib_smem(512, maug_max, n_max) > (size_t)ctx->max_smem_optin - 1024)
+    // the evaluation keeps y [m_aug] (split over a cluster's ranks) and one n-vector per
+    // CTA in shared memory: the plan must fit at least the smallest configuration
+    if (ib_smem(256, maug_max, n_max, 4) > (size_t)ctx->max_smem_optin - 1024)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID,
                        "inverse_prepare: %lld rows + features exceed the evaluation's shared memory",
                        (long long)maug_max);
@@ -433,60 +575,151 @@ extern "C" int fastlsq_inverse_prepare(fastlsq_ctx *ctx, const fastlsq_inverse_i
     P->h_desc.resize(n_inst);
     size_t h_total = 0;
     for (int q = 0; q < n_inst; ++q) h_total += (size_t)inst[q].n_sens * inst[q].n_feat;
-    double *A64 = nullptr, *pref = nullptr;
-    cudaError_t e = cudaMallocAsync(&A64, sizeof(double) * m_max * n_max, ctx->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&pref, sizeof(double) * (2 + FL_MAX_PP) * n_max, ctx->stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(&P->H, sizeof(double) * h_total, ctx->stream);
+    cudaError_t e = cudaMallocAsync(&P->H, sizeof(double) * h_total, ctx->stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&P->d_desc, sizeof(InvDesc) * n_inst, ctx->stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&P->d_order, sizeof(int) * n_inst, ctx->stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&P->d_queue, sizeof(int), ctx->stream);
     int rc = (e == cudaSuccess) ? 0 : fl_cuda(ctx, e, "inverse_prepare buffers");
     size_t h_off = 0;
-    for (int q = 0; q < n_inst && rc >= 0; ++q) {
-        const fastlsq_inverse_instance &I = inst[q];
-        const int64_t n = I.n_feat, m = I.n_int + I.n_bc, ld = fl_round_up(m, 4);
-        const double scale = 1.0 / sqrt((double)n);
-        do {
-            if ((rc = fl_prefactors(ctx, opL, I.W, n, scale, 1.0, pref)) < 0) break;
-            if ((rc = fl_launch_assemble_f64(ctx, opL, I.x_int, I.n_int, I.W, I.b, n, pref, A64, ld, 0, 1.0)) < 0) break;
-            if (I.n_bc) {
-                if ((rc = fl_prefactors(ctx, opI, I.W, n, scale, o->bc_weight, pref)) < 0) break;
-                if ((rc = fl_launch_assemble_f64(ctx, opI, I.x_bc, I.n_bc, I.W, I.b, n, pref, A64, ld, I.n_int,
-                                                 o->bc_weight)) < 0) break;
-            }
-            rc = fastlsq_lstsq(ctx, FASTLSQ_PREC_FP64, A64, FASTLSQ_F64, ld, m, n, o->mu, nullptr, 0, ld, nullptr, n,
-                               nullptr, 0, 0, FASTLSQ_REFINE_CLASSICAL, 0.0, &P->factors[q], nullptr);
-            if (rc < 0) break;
-            double *H = P->H + h_off;
-            k_sensor_matrix<<<dim3((unsigned)fl_cdiv(n, 256), (unsigned)I.n_sens), 256, 0, ctx->stream>>>(
-                I.sensors, I.n_sens, I.W, I.b, n, scale, H);
-            if (cudaGetLastError() != cudaSuccess) {
-                rc = fl_fail(ctx, FASTLSQ_ERR_CUDA, "sensor matrix");
-                break;
-            }
-            const fastlsq_factor *f = P->factors[q];
-            InvDesc &D = P->h_desc[q];
-            D.n_int = I.n_int;
-            D.n_feat = n;
-            D.n_sens = I.n_sens;
-            D.m_aug = f->m_aug;
-            D.ld = f->ld;
-            D.nb = f->nb;
-            D.scale = scale;
-            D.x_int = I.x_int;
-            D.theta = I.theta;
-            D.y_obs = I.y_obs;
-            D.H = H;
-            D.F = (const double *)f->F;
-            D.T = (const double *)f->T;
-            D.beta = I.beta;
-            D.loss = I.loss;
-            D.dtheta = I.dtheta;
-            h_off += (size_t)I.n_sens * n;
-        } while (0);
+    std::vector<size_t> h_at(n_inst);
+    for (int q = 0; q < n_inst; ++q) {
+        h_at[q] = h_off;
+        h_off += (size_t)inst[q].n_sens * inst[q].n_feat;
     }
-    if (A64) cudaFreeAsync(A64, ctx->stream);
-    if (pref) cudaFreeAsync(pref, ctx->stream);
+    // The factorisations are independent: they are spread over a few worker contexts,
+    // each on a stream of its own, so that the panel chains of small instances (which
+    // leave most SMs idle) overlap.  Instances go to the worker with the least work so
+    // far, largest first (m n^2 each), so every worker's workspace reaches its size on
+    // its first instance.  Each worker has its own operator and prefactor buffers.
+    struct Worker {
+        fastlsq_ctx *c = nullptr;
+        cudaStream_t s = nullptr;
+        double *A64 = nullptr, *pref = nullptr;
+        std::vector<int> todo;
+        double load = 0.0;
+    };
+    const int n_work = std::min<int>(IB_SETUP_WORKERS, n_inst);
+    std::vector<Worker> wk(n_work);
+    {
+        std::vector<int> by_cost(n_inst);
+        std::iota(by_cost.begin(), by_cost.end(), 0);
+        auto cost = [&](int q) {
+            return (double)(inst[q].n_int + inst[q].n_bc + inst[q].n_feat) * (double)inst[q].n_feat *
+                   (double)inst[q].n_feat;
+        };
+        std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return cost(a) > cost(b); });
+        for (int q : by_cost) {
+            Worker *lo = &wk[0];
+            for (Worker &w : wk)
+                if (w.load < lo->load) lo = &w;
+            lo->todo.push_back(q);
+            lo->load += cost(q);
+        }
+    }
+    cudaEvent_t ready = nullptr;
+    if (rc >= 0) {
+        e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ready, ctx->stream);     // inputs and P->H
+        if (e != cudaSuccess) rc = fl_cuda(ctx, e, "inverse_prepare event");
+    }
+    for (Worker &w : wk) {
+        if (rc < 0) break;
+        e = cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            rc = fl_cuda(ctx, e, "inverse_prepare stream");
+            break;
+        }
+        const int crc = fastlsq_create(&w.c, ctx->device, (void *)w.s);
+        if (crc < 0) {
+            rc = fl_fail(ctx, crc, "inverse_prepare: worker context");
+            break;
+        }
+        w.c->panel_reg = ctx->panel_reg;
+        w.c->row_panel = ctx->row_panel;
+        w.c->lookahead = ctx->lookahead;
+        w.c->fuse_next = ctx->fuse_next;
+        w.c->split_rows = ctx->split_rows;
+        e = cudaStreamWaitEvent(w.s, ready, 0);
+        if (e == cudaSuccess) e = cudaMallocAsync(&w.A64, sizeof(double) * m_max * n_max, w.s);
+        if (e == cudaSuccess) e = cudaMallocAsync(&w.pref, sizeof(double) * (2 + FL_MAX_PP) * n_max, w.s);
+        if (e != cudaSuccess) rc = fl_cuda(ctx, e, "inverse_prepare worker buffers");
+    }
+    // issue round-robin over the workers (the host never waits inside the loop)
+    for (size_t r = 0; rc >= 0; ++r) {
+        bool any = false;
+        for (Worker &w : wk) {
+            if (rc < 0 || r >= w.todo.size()) continue;
+            any = true;
+            const int q = w.todo[r];
+            fastlsq_ctx *c = w.c;
+            const fastlsq_inverse_instance &I = inst[q];
+            const int64_t n = I.n_feat, m = I.n_int + I.n_bc, ld = fl_round_up(m, 4);
+            const double scale = 1.0 / sqrt((double)n);
+            double *A64 = w.A64, *pref = w.pref;
+            int wrc = 0;
+            do {
+                if ((wrc = fl_prefactors(c, opL, I.W, n, scale, 1.0, pref)) < 0) break;
+                if ((wrc = fl_launch_assemble_f64(c, opL, I.x_int, I.n_int, I.W, I.b, n, pref, A64, ld, 0,
+                                                  1.0)) < 0) break;
+                if (I.n_bc) {
+                    if ((wrc = fl_prefactors(c, opI, I.W, n, scale, o->bc_weight, pref)) < 0) break;
+                    if ((wrc = fl_launch_assemble_f64(c, opI, I.x_bc, I.n_bc, I.W, I.b, n, pref, A64, ld, I.n_int,
+                                                      o->bc_weight)) < 0) break;
+                }
+                wrc = fastlsq_lstsq(c, FASTLSQ_PREC_FP64, A64, FASTLSQ_F64, ld, m, n, o->mu, nullptr, 0, ld, nullptr,
+                                    n, nullptr, 0, 0, FASTLSQ_REFINE_CLASSICAL, 0.0, &P->factors[q], nullptr);
+                if (wrc < 0) break;
+                double *H = P->H + h_at[q];
+                k_sensor_matrix<<<dim3((unsigned)fl_cdiv(n, 256), (unsigned)I.n_sens), 256, 0, w.s>>>(
+                    I.sensors, I.n_sens, I.W, I.b, n, scale, H);
+                if (cudaGetLastError() != cudaSuccess) {
+                    wrc = fl_fail(c, FASTLSQ_ERR_CUDA, "sensor matrix");
+                    break;
+                }
+                const fastlsq_factor *f = P->factors[q];
+                InvDesc &D = P->h_desc[q];
+                D.n_int = I.n_int;
+                D.n_feat = n;
+                D.n_sens = I.n_sens;
+                D.m_aug = f->m_aug;
+                D.ld = f->ld;
+                D.nb = f->nb;
+                D.scale = scale;
+                D.x_int = I.x_int;
+                D.theta = I.theta;
+                D.y_obs = I.y_obs;
+                D.H = H;
+                D.F = (const double *)f->F;
+                D.T = (const double *)f->T;
+                D.beta = I.beta;
+                D.loss = I.loss;
+                D.dtheta = I.dtheta;
+            } while (0);
+            if (wrc < 0) rc = fl_fail(ctx, wrc, "inverse_prepare: instance %d: %s", q, c->last_error.c_str());
+        }
+        if (!any) break;
+    }
+    // join the workers: their kernels' error flags, then their buffers; the kept factors
+    // move to the plan's stream (their memory is stream-ordered and complete here)
+    for (Worker &w : wk) {
+        if (w.c) {
+            const int src = fastlsq_sync(w.c);
+            if (src < 0 && rc >= 0) rc = fl_fail(ctx, src, "inverse_prepare: %s", w.c->last_error.c_str());
+        }
+        if (w.A64) cudaFreeAsync(w.A64, w.s);
+        if (w.pref) cudaFreeAsync(w.pref, w.s);
+        if (w.s) cudaStreamSynchronize(w.s);
+    }
+    for (fastlsq_factor *f : P->factors) {
+        if (!f) continue;
+        f->ctx = ctx;
+        f->stream = ctx->stream;
+    }
+    for (Worker &w : wk) {
+        if (w.c) fastlsq_destroy(w.c);
+        if (w.s) cudaStreamDestroy(w.s);
+    }
+    if (ready) cudaEventDestroy(ready);
     if (rc >= 0) {
         for (const InvDesc &D : P->h_desc)
             if (D.nb > IB_NB) rc = fl_fail(ctx, FASTLSQ_ERR_INVALID, "inverse_prepare: panel width %d", D.nb);
@@ -517,20 +750,31 @@ extern "C" int fastlsq_inverse_prepare(fastlsq_ctx *ctx, const fastlsq_inverse_i
 }
 
 extern "C" int fastlsq_inverse_eval(fastlsq_ctx *ctx, const fastlsq_inverse_plan *P, int32_t threads,
-                                    int32_t ctas_per_sm)
+                                    int32_t ctas_per_sm, int32_t cluster)
 {
     if (!ctx || !P) return FASTLSQ_ERR_INVALID;
-    if ((threads != 256 && threads != 512) || ctas_per_sm < 1 || ctas_per_sm > 4)
-        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "inverse_eval: threads 256 or 512, 1..4 CTAs per SM");
-    const size_t smem = ib_smem(threads, P->m_aug_max, P->n_max);
+    if ((threads != 256 && threads != 512) || ctas_per_sm < 1 || ctas_per_sm > 4 ||
+        (cluster != 1 && cluster != 2 && cluster != 4))
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID,
+                       "inverse_eval: threads 256 or 512, 1..4 CTAs per SM, clusters of 1, 2 or 4");
+    const size_t smem = ib_smem(threads, P->m_aug_max, P->n_max, cluster);
     if (smem * ctas_per_sm > (size_t)ctx->max_smem_optin)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "inverse_eval: %d CTAs per SM do not fit in shared memory",
                        ctas_per_sm);
-    const int grid = std::min<int>(P->n_inst, ctx->num_sms * ctas_per_sm);
+    // one cluster per instance at most; whole clusters only
+    const int clusters = std::max(1, std::min<int>(P->n_inst, ctx->num_sms * ctas_per_sm / cluster));
+    const int grid = clusters * cluster;
     cudaError_t e = cudaMemsetAsync(P->d_queue, 0, sizeof(int), ctx->stream);
     if (e != cudaSuccess) return fl_cuda(ctx, e, "inverse_eval queue");
     FL_PROF(ctx, FASTLSQ_K_ADJOINT);
-    e = (threads == 256) ? ib_launch<256>(P, ctx->stream, grid, smem) : ib_launch<512>(P, ctx->stream, grid, smem);
+    if (threads == 256)
+        e = (cluster == 1)   ? ib_launch<256, 1>(P, ctx->stream, grid, smem)
+            : (cluster == 2) ? ib_launch<256, 2>(P, ctx->stream, grid, smem)
+                             : ib_launch<256, 4>(P, ctx->stream, grid, smem);
+    else
+        e = (cluster == 1)   ? ib_launch<512, 1>(P, ctx->stream, grid, smem)
+            : (cluster == 2) ? ib_launch<512, 2>(P, ctx->stream, grid, smem)
+                             : ib_launch<512, 4>(P, ctx->stream, grid, smem);
     if (e != cudaSuccess) return fl_cuda(ctx, e, "inverse_eval launch");
     return 0;
 }

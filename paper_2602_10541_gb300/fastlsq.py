@@ -115,7 +115,7 @@ _SIGNATURES = {
     "fastlsq_inverse_prepare": [_vp, ctypes.POINTER(fastlsq_inverse_instance), _i32,
                                 ctypes.POINTER(fastlsq_op), _i32, ctypes.POINTER(fastlsq_inverse_opts),
                                 ctypes.POINTER(_vp)],
-    "fastlsq_inverse_eval": [_vp, _vp, _i32, _i32],
+    "fastlsq_inverse_eval": [_vp, _vp, _i32, _i32, _i32],
     "fastlsq_inverse_plan_destroy": [_vp],
     "fastlsq_selftest_wait": [_vp, _i32, _i64],
     "fastlsq_profile_enable": [_vp, ctypes.c_int],
@@ -495,9 +495,10 @@ def fastlsq_inverse_prepare(ctx, instances, op, n_src, mu=1e-10, bc_weight=100.0
     return InversePlan(ctx, instances, op, n_src, mu=mu, bc_weight=bc_weight)
 
 
-def fastlsq_inverse_eval(ctx, plan, threads=256, ctas_per_sm=1):
-    """One gradient evaluation of every instance of the plan (one persistent launch)."""
-    return ctx.check(ctx.lib.fastlsq_inverse_eval(ctx.handle, plan.handle, threads, ctas_per_sm))
+def fastlsq_inverse_eval(ctx, plan, threads=256, ctas_per_sm=1, cluster=1):
+    """One gradient evaluation of every instance of the plan (one persistent launch of
+    clusters of `cluster` CTAs, one cluster per instance at a time)."""
+    return ctx.check(ctx.lib.fastlsq_inverse_eval(ctx.handle, plan.handle, threads, ctas_per_sm, cluster))
 
 
 def fastlsq_inverse_batch(ctx, instances, op, n_src, prec=PREC_MIXED, refine_iters=64,

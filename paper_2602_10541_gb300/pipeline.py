@@ -212,7 +212,7 @@ def tuned(kernel: str, default: dict) -> dict:
     if os.path.exists(path):
         entry = json.load(open(path)).get(kernel)
         if entry:
-            return {k: entry[k] for k in default}
+            return {k: entry.get(k, v) for k, v in default.items()}
     return dict(default)
 
 
@@ -233,7 +233,7 @@ class InverseBatch:
                           dtheta=torch.zeros(w.params.size, dtype=torch.float64, device=device))
                      for w in self.ws]
         self.n_src = self.ws[0].params.size // 4
-        self.launch = launch or tuned("inverse_eval", {"threads": 256, "ctas_per_sm": 1})
+        self.launch = launch or tuned("inverse_eval", {"threads": 256, "ctas_per_sm": 1, "cluster": 1})
         self.plan = fl.fastlsq_inverse_prepare(ctx, self.inst, fl.Op(self.ws[0].alpha, self.ws[0].coef),
                                                self.n_src, mu=mu, bc_weight=bc_weight)
         self.device = device

@@ -2,9 +2,10 @@
 fastest in tuning.json next to this module (read by pipeline.tuned()).
 
 Tuned today: the persistent evaluation of the batched inverse problem
-(fastlsq_inverse_eval), threads per CTA in {256, 512} x CTAs per SM in {1, 2}, on
-instances drawn with the batched configuration's recipe (uneven points and
-features).  ``python -m paper_2602_10541_gb300.tune [--instances N] [--reps R]``.
+(fastlsq_inverse_eval), threads per CTA in {256, 512} x CTAs per SM in {1, 2} x CTAs
+per cluster (one instance each) in {1, 2, 4}, on the batched configuration's 256
+instances (uneven points and features).
+``python -m paper_2602_10541_gb300.tune [--instances N] [--reps R]``.
 """
 from __future__ import annotations
 
@@ -20,10 +21,11 @@ from . import pipeline as pl
 from . import workloads as wl
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
-CANDIDATES = [{"threads": t, "ctas_per_sm": c} for t in (256, 512) for c in (1, 2)]
+CANDIDATES = [{"threads": t, "ctas_per_sm": c, "cluster": k} for t in (256, 512) for c in (1, 2)
+              for k in (1, 2, 4)]
 
 
-def tune_inverse(n_inst=64, reps=5, device="cuda:0"):
+def tune_inverse(n_inst=256, reps=5, device="cuda:0"):
     ctx = fl.Context(0)
     batch = pl.InverseBatch(ctx, [wl.inverse_instance(q) for q in range(n_inst)], device=device)
     batch.observe()
@@ -53,7 +55,7 @@ def tune_inverse(n_inst=64, reps=5, device="cuda:0"):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2602_10541_gb300.tune")
-    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--reps", type=int, default=5)
     a = ap.parse_args(argv)
     table = json.load(open(TABLE)) if os.path.exists(TABLE) else {}

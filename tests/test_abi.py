@@ -37,6 +37,16 @@ def test_binding_covers_every_declared_symbol():
     assert set(_declared()) <= set(fl._SIGNATURES)
 
 
+def test_binding_signatures_match_header_arity():
+    """Every binding passes as many arguments as the header's declaration takes."""
+    from paper_2602_10541_gb300 import fastlsq as fl
+    src = open(os.path.join(ROOT, "include", "fastlsq.h")).read()
+    for name, params in re.findall(r"FASTLSQ_API\s+[\w\s\*]*?\b(fastlsq_\w+)\s*\(([^)]*)\)", src):
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(fl._SIGNATURES[name]) == n, (name, n, len(fl._SIGNATURES[name]))
+
+
 def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
     from paper_2602_10541_gb300 import _build
     from paper_2602_10541_gb300 import fastlsq as fl

@@ -69,14 +69,15 @@ def batch():
     return cases, dev
 
 
-@pytest.mark.parametrize("threads,ctas", [(256, 1), (512, 1), (256, 2)])
-def test_persistent_batch_matches_oracle(ctx, batch, threads, ctas):
+@pytest.mark.parametrize("threads,ctas,cluster", [(256, 1, 1), (512, 1, 1), (256, 2, 1), (256, 1, 2),
+                                                  (512, 1, 2), (512, 2, 4)])
+def test_persistent_batch_matches_oracle(ctx, batch, threads, ctas, cluster):
     cases, dev = batch
     plan = fl.fastlsq_inverse_prepare(ctx, dev, OP, 4, mu=MU)
     for d in dev:
         d["loss"].zero_()
         d["dtheta"].zero_()
-    fl.fastlsq_inverse_eval(ctx, plan, threads=threads, ctas_per_sm=ctas)
+    fl.fastlsq_inverse_eval(ctx, plan, threads=threads, ctas_per_sm=ctas, cluster=cluster)
     torch.cuda.synchronize()
     for (w, y, ref), d in zip(cases, dev):
         assert abs(d["loss"].item() - ref["loss"]) <= 1e-6 * ref["loss"], (w.name, d["loss"].item(), ref["loss"])
@@ -114,22 +115,24 @@ def test_persistent_batch_gradient_matches_central_differences(ctx, batch):
     assert np.abs(g - fd).max() <= 1e-4 * np.abs(fd).max(), (g, fd)
 
 
-def test_persistent_batch_replays_from_a_cuda_graph(ctx, batch):
+@pytest.mark.parametrize("cluster", [1, 2])
+def test_persistent_batch_replays_from_a_cuda_graph(ctx, batch, cluster):
     """The evaluation allocates nothing and never synchronises: captured once, a replay
-    after theta changes gives the eager results bit for bit."""
+    after theta changes gives the eager results bit for bit (at a fixed cluster size
+    the sums run in a fixed order)."""
     cases, dev = batch
     s = torch.cuda.Stream()
     gctx = fl.Context(0, stream=s)
     sub = dev[:4]
     with torch.cuda.stream(s):
         plan = fl.fastlsq_inverse_prepare(gctx, sub, OP, 4, mu=MU)
-        fl.fastlsq_inverse_eval(gctx, plan)            # kernel attributes set before capture
+        fl.fastlsq_inverse_eval(gctx, plan, cluster=cluster)   # kernel attributes set before capture
     torch.cuda.synchronize()
     theta_b = [d["theta"].clone() * 1.01 for d in sub]
     for d, tb in zip(sub, theta_b):
         d["theta"].copy_(tb)
     with torch.cuda.stream(s):
-        fl.fastlsq_inverse_eval(gctx, plan)
+        fl.fastlsq_inverse_eval(gctx, plan, cluster=cluster)
     torch.cuda.synchronize()
     eager = [(d["loss"].clone(), d["dtheta"].clone(), d["beta"].clone()) for d in sub]
     for d in sub:
@@ -138,7 +141,7 @@ def test_persistent_batch_replays_from_a_cuda_graph(ctx, batch):
         d["beta"].zero_()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
-        fl.fastlsq_inverse_eval(gctx, plan)
+        fl.fastlsq_inverse_eval(gctx, plan, cluster=cluster)
     g.replay()
     torch.cuda.synchronize()
     for d, (l, dt, b) in zip(sub, eager):
@@ -160,6 +163,9 @@ def test_inverse_plan_rejects_bad_arguments(ctx, batch):
     plan = fl.fastlsq_inverse_prepare(ctx, dev[:1], OP, 4, mu=MU)
     with pytest.raises(fl.FastLSQError) as e:
         fl.fastlsq_inverse_eval(ctx, plan, threads=128)
+    assert e.value.code == -1
+    with pytest.raises(fl.FastLSQError) as e:
+        fl.fastlsq_inverse_eval(ctx, plan, cluster=3)
     assert e.value.code == -1
     plan.close()
     fl.fastlsq_sync(ctx)
