@@ -547,13 +547,20 @@ def _inverse_row(fl, pl, wl, torch, ctx, dev, n_inst):
         b.record(ctx.stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
-    # FP64 FMAs of one evaluation of the batch: Q^T and Q each a dot pass and an update
-    # pass over the reflectors (2 (m_aug n - n^2 / 2) each), two triangular solves (n^2 / 2
-    # each): 4 m_aug n per instance, m_aug = interior + boundary + Tikhonov rows
-    fma = sum(4.0 * (w.n_int + w.n_bc + w.n_feat) * w.n_feat for w in ws)
+    # FP64 FMAs of one evaluation of the batch.  Thin-Q plan (the default): Qi^T s and
+    # Qi w over the interior rows (n_int n each) and two triangular solves (n^2 / 2 each):
+    # 2 n_int n + n^2 per instance.  Reflector plan: Q^T and Q each a dot pass and an
+    # update pass over the reflectors (2 (m_aug n - n^2 / 2) each) and the two solves:
+    # 4 m_aug n, m_aug = interior + boundary + Tikhonov rows.
+    thin_q = batch.thin_q
+    if thin_q:
+        fma = sum(2.0 * w.n_int * w.n_feat + float(w.n_feat) ** 2 for w in ws)
+    else:
+        fma = sum(4.0 * (w.n_int + w.n_bc + w.n_feat) * w.n_feat for w in ws)
     tfma = fma / (ms / 1e3) / 1e12
     out = {"instances": n_inst, "setup_s": setup_s, "factorizations_per_s": n_inst / setup_s,
            "ms_per_batch_eval": ms, "gradient_evals_per_s": n_inst / (ms / 1e3),
+           "plan": "thin Q of the interior rows" if thin_q else "reflectors",
            "roofline": {"bound": "fp64", "achieved": tfma, "unit": "TFMA/s", "peak": 0.625,
                         "frac": tfma / 0.625, "work_fma_per_eval": fma,
                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (0.625 TFMA/s); a cuBLAS DGEMM "
@@ -564,8 +571,9 @@ def _inverse_row(fl, pl, wl, torch, ctx, dev, n_inst):
            "loss_mean": float(sum(d["loss"].item() for d in batch.inst) / n_inst),
            "workload": ("steady inverse heat source -Lap u = s(x; theta), 4 Gaussians (16 parameters), "
                         "n_int ~ U{1024..8192}, n_feat ~ U{512..2048}, sigma = 8, mu = 1e-10, 64 sensors; "
-                        "FP64 factor of [A; sqrt(mu) I] kept, per evaluation Q^T, R^-1, R^-T, Q and the "
-                        "source gradient in one persistent launch (CUDA graph replay)")}
+                        "FP64 factor of [A; sqrt(mu) I] kept with the thin Q of its interior rows, per "
+                        "evaluation Qi^T s, R^-1, R^-T, Qi w and the source gradient in one persistent "
+                        "launch (CUDA graph replay)")}
     batch.close()
     del g
     ctx.close()

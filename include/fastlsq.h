@@ -398,14 +398,15 @@ FASTLSQ_API int fastlsq_inverse_batch(fastlsq_ctx *ctx, const fastlsq_inverse_in
  *
  * fastlsq_inverse_prepare assembles each instance's FP64 operator (interior rows op,
  * boundary rows bc_weight * identity), factors [A; sqrt(mu) I] by FP64 Householder QR
- * (the factor is kept by the plan), tabulates the sensor matrix H_s[s][j] =
+ * (the factor is kept by the plan; with FASTLSQ_OPT_INVERSE_THIN_Q set, the default,
+ * also Qi = the interior rows of Q [I; 0]), tabulates the sensor matrix H_s[s][j] =
  * scale sin(W_j . x_s + b_j) and records the instances' device pointers.  opts: mu > 0
  * and bc_weight are used; prec, refine and adjoint fields are ignored (the factor is
  * FP64).  The factorisations run a few at a time on worker streams of the library's
  * own, after the work already queued on the context's stream.  Limits: n_src <= 8,
- * n_sens <= 256, and n_int + n_bc + n_feat small enough that a quarter of one
- * instance's vector of that length plus one of n_feat (FP64) fit in a CTA's shared
- * memory, else -1 (the evaluation's configuration must fit too).  Synchronises the
+ * n_sens <= 256, and a quarter of n_int + n_bc + n_feat (thin-Q plans: n_int) plus
+ * n_feat FP64 values fitting in a CTA's shared memory, else -1 (the evaluation's
+ * configuration must fit too).  Synchronises the
  * context's stream; returns 0 and *plan, or a negative status (nothing is kept).
  *
  * fastlsq_inverse_eval runs one gradient evaluation of every instance in ONE
@@ -415,7 +416,8 @@ FASTLSQ_API int fastlsq_inverse_batch(fastlsq_ctx *ctx, const fastlsq_inverse_in
  * entirely, its m_aug-vectors dealt over the ranks in stripes of 32 rows:
  *   y = Q^T [s(x_int; theta); 0; 0], beta = R^{-1} y[0:n], u_s = H_s beta,
  *   loss = mean (u_s - y_obs)^2, w = R^{-T} H_s^T dloss/du_s, z = Q [w; 0]
- *   (= A (A^T A + mu I)^{-1} H_s^T g), dtheta = sum_{i < n_int} z_i ds(x_i)/dtheta,
+ *   (= A (A^T A + mu I)^{-1} H_s^T g), dtheta = sum_{i < n_int} z_i ds(x_i)/dtheta
+ *   (thin-Q plans: y[0:n] = Qi^T s and z[0:n_int] = Qi w, the same quantities),
  * writing beta, loss and dtheta through the instances' pointers.  It reads theta and
  * y_obs at run time, allocates nothing and does not synchronise, so it can be captured
  * in a CUDA graph and replayed after the caller updates theta or y_obs in place.  No
@@ -607,11 +609,19 @@ typedef enum {
                                       panel rows per thread (updates without shuffles),
                                       where the panel has at most 768 rows per CTA; 0: one
                                       column per lane (32 rows per thread at most) */
-    FASTLSQ_OPT_SPLIT_ROWS = 6      /* least rows per split of the SIMT trailing updates'
+    FASTLSQ_OPT_SPLIT_ROWS = 6,     /* least rows per split of the SIMT trailing updates'
                                       Y pass (a multiple of 32, 32 .. 1048576; default 256).
                                       Small splits give one solve the shortest latency;
                                       larger ones launch fewer CTAs per update, leaving
                                       more of the GPU to other solves running beside it */
+    FASTLSQ_OPT_INVERSE_THIN_Q = 7  /* 1 (default): fastlsq_inverse_prepare also forms each
+                                      instance's thin Q restricted to its interior rows,
+                                      Qi = (Q [I; 0])[0:n_int] (n_int x n FP64, about the
+                                      factorisation's FP64 work again), and the evaluations
+                                      use Qi^T s and Qi w: 2 n_int n FMAs per instance
+                                      instead of 4 m_aug n with the reflectors; 0: the
+                                      plan keeps the reflectors only (faster setup, less
+                                      memory). Read when a plan is prepared. */
 } fastlsq_option;
 
 /* Set a context option (see fastlsq_option).  Returns 0 or -1 for an unknown option. */

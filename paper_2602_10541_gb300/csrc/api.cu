@@ -328,6 +328,10 @@ extern "C" int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value)
         ctx->trsv32 = value ? 1 : 0;
         return 0;
     }
+    if (option == FASTLSQ_OPT_INVERSE_THIN_Q) {
+        ctx->inverse_thin_q = value ? 1 : 0;
+        return 0;
+    }
     if (option == FASTLSQ_OPT_SPLIT_ROWS) {
         if (value < 32 || value > (1 << 20) || value % 32 != 0)
             return fl_fail(ctx, FASTLSQ_ERR_INVALID, "split rows %d: a multiple of 32 in 32 .. 1048576", value);

@@ -102,6 +102,7 @@ struct fastlsq_ctx {
     int fuse_next = 1;              // look-ahead: next panel applies the previous update itself
     int split_rows = 256;           // least rows per split of the SIMT trailing updates' Y pass
     int trsv32 = 1;                 // FP32 arithmetic in the triangular solves of classical refinement
+    int inverse_thin_q = 1;         // inverse plans keep the thin Q of the interior rows
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t aux2_stream = nullptr;   // the rest of an outer block's update pass (look-ahead)

@@ -52,6 +52,8 @@ struct InvDesc {
     double scale;
     const double *x_int, *theta, *y_obs, *H;      // H: [n_sens][n_feat]
     const double *F, *T;                          // factor (V below, R above), T blocks
+    const double *Q;                              // thin-Q form: rows [0, n_int) of Q [I; 0]
+    int64_t ldq;
     double *beta, *loss, *dtheta;
 };
 
@@ -452,6 +454,206 @@ k_inv_eval(const InvDesc *__restrict__ descs, const int *__restrict__ order, int
     }
 }
 
+// The evaluation with the explicit thin Q of the interior rows, Qi = rows [0, n_int) of
+// Q [I_n; 0] (n_int x n, kept by the plan): since y = [s; 0; 0] is zero below the
+// interior rows and the gradient reads z on them only,
+//   (Q^T y)[0, n] = Qi^T s      and      z[0, n_int) = (Q [w; 0])[0, n_int) = Qi w,
+// 2 n_int n FP64 FMAs per evaluation instead of the reflectors' 4 m_aug n.  With a
+// cluster, s is computed in row stripes and gathered into every rank, the columns of
+// Qi^T s are dealt in groups of four over the ranks (results into rank 0), rank 0 runs
+// the substitutions and the sensor products, and each rank forms z on its row stripes.
+template <int THREADS, int C>
+__global__ void __launch_bounds__(THREADS)
+k_inv_eval_q(const InvDesc *__restrict__ descs, const int *__restrict__ order, int n_inst,
+             int *__restrict__ queue, int n_src, int64_t nint_max, int64_t n_max)
+{
+    constexpr int NW = THREADS / 32;
+    extern __shared__ double ib_sm[];
+    double *sv = ib_sm;                         // [nint_max]  s at the interior rows
+    double *xv = sv + nint_max;                 // [n_max]     Qi^T s, then w
+    double *red = xv + n_max;                   // [NW][32]
+    double *gs = red + NW * IB_NB;              // [IB_MAX_SENS]
+    double *th = gs + IB_MAX_SENS;              // [4 IB_MAX_SRC]
+    double *xd = th + 4 * IB_MAX_SRC;           // [C][4 IB_MAX_SRC]
+    __shared__ int s_q;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    IbRows<C> rows;
+    rows.rank = 0;
+    if constexpr (C > 1) rows.rank = (int)cg::this_cluster().block_rank();
+    const bool lead = rows.rank == 0;
+    for (;;) {
+        if (lead && tid == 0) s_q = atomicAdd(queue, 1);
+        int q;
+        if constexpr (C > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            cl.sync();
+            q = *cl.map_shared_rank(&s_q, 0);
+            cl.sync();                          // rank 0 keeps its shared memory until read
+        } else {
+            __syncthreads();
+            q = s_q;
+        }
+        if (q >= n_inst) break;
+        const InvDesc D = descs[order[q]];
+        const int64_t n = D.n_feat, n_int = D.n_int, ldq = D.ldq;
+        const double *Qi = D.Q;
+        for (int t = tid; t < 4 * n_src; t += THREADS) th[t] = D.theta[t];
+        __syncthreads();
+        // s at the interior rows (this rank's stripes), into every rank
+        for (int64_t lr = tid;; lr += THREADS) {
+            const int64_t i = rows.glob(lr);
+            if (i >= n_int) break;
+            const double px = D.x_int[2 * i], py = D.x_int[2 * i + 1];
+            double v = 0.0;
+            for (int s = 0; s < n_src; ++s) {
+                const double dx = px - th[4 * s], dy = py - th[4 * s + 1], w = th[4 * s + 2];
+                v += th[4 * s + 3] * exp(-(dx * dx + dy * dy) / (2.0 * w * w));
+            }
+            if constexpr (C > 1) {
+                cg::cluster_group cl = cg::this_cluster();
+                for (int r = 0; r < C; ++r) cl.map_shared_rank(sv, r)[i] = v;
+            } else {
+                sv[i] = v;
+            }
+        }
+        if constexpr (C > 1) cg::this_cluster().sync();
+        else __syncthreads();
+        // t = Qi^T s: a warp per group of four columns, lanes over the rows (coalesced)
+        {
+            double *t_out = xv;
+            if constexpr (C > 1) t_out = cg::this_cluster().map_shared_rank(xv, 0);
+            const int64_t ngrp = (n + 3) / 4;
+            for (int64_t g = rows.rank + (int64_t)C * warp; g < ngrp; g += (int64_t)C * NW) {
+                const int64_t j0 = 4 * g;
+                const int nc = (int)fl_min64(4, n - j0);
+                const double *q0 = Qi + j0 * ldq;
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                if (nc == 4) {
+#pragma unroll 4
+                    for (int64_t i = lane; i < n_int; i += 32) {
+                        const double si = sv[i];
+                        a0 = fma(q0[i], si, a0);
+                        a1 = fma(q0[i + ldq], si, a1);
+                        a2 = fma(q0[i + 2 * ldq], si, a2);
+                        a3 = fma(q0[i + 3 * ldq], si, a3);
+                    }
+                } else {
+                    for (int64_t i = lane; i < n_int; i += 32) {
+                        const double si = sv[i];
+                        a0 = fma(q0[i], si, a0);
+                        if (nc > 1) a1 = fma(q0[i + ldq], si, a1);
+                        if (nc > 2) a2 = fma(q0[i + 2 * ldq], si, a2);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+                    a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+                }
+                if (lane < nc) t_out[j0 + lane] = (lane == 0) ? a0 : (lane == 1) ? a1 : (lane == 2) ? a2 : a3;
+            }
+        }
+        if constexpr (C > 1) cg::this_cluster().sync();
+        else __syncthreads();
+        if (lead) {
+            ib_trsv<THREADS>(D, xv, false);                          // beta
+            for (int64_t j = tid; j < n; j += THREADS) D.beta[j] = xv[j];
+            for (int64_t s = warp; s < D.n_sens; s += NW) {
+                const double *h = D.H + s * n;
+                double u = 0.0;
+                for (int64_t j = lane; j < n; j += 32) u = fma(h[j], xv[j], u);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+                if (lane == 0) gs[s] = u - D.y_obs[s];
+            }
+            __syncthreads();
+            double l2 = 0.0;
+            for (int64_t s = tid; s < D.n_sens; s += THREADS) l2 += gs[s] * gs[s];
+            l2 = ib_block_sum<THREADS>(l2, red);
+            if (tid == 0) *D.loss = l2 / (double)D.n_sens;
+            for (int64_t s = tid; s < D.n_sens; s += THREADS) gs[s] *= 2.0 / (double)D.n_sens;
+            __syncthreads();
+            for (int64_t j = tid; j < n; j += THREADS) {
+                double a = 0.0;
+                for (int64_t s = 0; s < D.n_sens; ++s) a = fma(D.H[s * n + j], gs[s], a);
+                xv[j] = a;
+            }
+            __syncthreads();
+            ib_trsv<THREADS>(D, xv, true);                           // w
+        }
+        if constexpr (C > 1) {                                       // w into every rank
+            cg::cluster_group cl = cg::this_cluster();
+            cl.sync();
+            if (!lead) {
+                const double *w0 = cl.map_shared_rank(xv, 0);
+                for (int64_t j = tid; j < n; j += THREADS) xv[j] = w0[j];
+            }
+            __syncthreads();
+        }
+        // z_i = (Qi w)_i on this rank's row stripes, and dL/dtheta from it
+        double acc[4 * IB_MAX_SRC];
+#pragma unroll
+        for (int t = 0; t < 4 * IB_MAX_SRC; ++t) acc[t] = 0.0;
+        for (int64_t lr = tid;; lr += THREADS) {
+            const int64_t i = rows.glob(lr);
+            if (i >= n_int) break;
+            const double *qr = Qi + i;
+            double z0 = 0.0, z1 = 0.0, z2 = 0.0, z3 = 0.0;
+            int64_t j = 0;
+#pragma unroll 2
+            for (; j + 4 <= n; j += 4) {
+                z0 = fma(qr[j * ldq], xv[j], z0);
+                z1 = fma(qr[(j + 1) * ldq], xv[j + 1], z1);
+                z2 = fma(qr[(j + 2) * ldq], xv[j + 2], z2);
+                z3 = fma(qr[(j + 3) * ldq], xv[j + 3], z3);
+            }
+            for (; j < n; ++j) z0 = fma(qr[j * ldq], xv[j], z0);
+            const double zi = (z0 + z1) + (z2 + z3);
+            const double px = D.x_int[2 * i], py = D.x_int[2 * i + 1];
+#pragma unroll
+            for (int s = 0; s < IB_MAX_SRC; ++s) {
+                if (s >= n_src) break;
+                const double *t = th + 4 * s;
+                const double dx = px - t[0], dy = py - t[1];
+                const double r2 = dx * dx + dy * dy, w2 = t[2] * t[2];
+                const double e = exp(-r2 / (2.0 * w2));
+                acc[4 * s + 0] = fma(zi * t[3] * e, dx / w2, acc[4 * s + 0]);
+                acc[4 * s + 1] = fma(zi * t[3] * e, dy / w2, acc[4 * s + 1]);
+                acc[4 * s + 2] = fma(zi * t[3] * e, r2 / (w2 * t[2]), acc[4 * s + 2]);
+                acc[4 * s + 3] = fma(zi, e, acc[4 * s + 3]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4 * IB_MAX_SRC; ++t) {
+            if (t >= 4 * n_src) break;                   // uniform over the CTA
+            const double v = ib_block_sum<THREADS>(acc[t], red);
+            if constexpr (C > 1) {
+                if (tid == 0) *(cg::this_cluster().map_shared_rank(xd, 0) + rows.rank * 4 * IB_MAX_SRC + t) = v;
+            } else {
+                if (tid == 0) D.dtheta[t] = v;
+            }
+        }
+        if constexpr (C > 1) {
+            cg::this_cluster().sync();
+            if (lead)                                    // the ranks' sums in rank order
+                for (int t = tid; t < 4 * n_src; t += THREADS) {
+                    double v = 0.0;
+                    for (int r = 0; r < C; ++r) v += xd[r * 4 * IB_MAX_SRC + t];
+                    D.dtheta[t] = v;
+                }
+        }
+        __syncthreads();
+    }
+}
+
+size_t ib_q_smem(int threads, int64_t nint_max, int64_t n_max, int cluster)
+{
+    return sizeof(double) * ((size_t)nint_max + (size_t)n_max + (size_t)(threads / 32) * IB_NB + IB_MAX_SENS +
+                             4 * IB_MAX_SRC + (size_t)cluster * 4 * IB_MAX_SRC);
+}
+
 // rows of y one rank holds: its stripes of the tallest instance
 int64_t ib_rows(int64_t m_aug_max, int cluster)
 {
@@ -471,8 +673,10 @@ struct fastlsq_inverse_plan {
     int device = 0;
     cudaStream_t stream = nullptr;
     int n_inst = 0, n_src = 0;
-    int64_t m_aug_max = 0, n_max = 0;
+    int64_t m_aug_max = 0, n_max = 0, nint_max = 0;
+    int thin_q = 0;               // evaluations use the explicit thin Q of the interior rows
     std::vector<fastlsq_factor *> factors;
+    std::vector<double *> Qbuf;   // thin-Q form: per instance rows [0, n_int) of Q [I; 0]
     double *H = nullptr;          // sensor matrices, all instances
     InvDesc *d_desc = nullptr;
     int *d_order = nullptr;
@@ -494,6 +698,9 @@ cudaError_t ib_launch(const fastlsq_inverse_plan *P, cudaStream_t st, int grid, 
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_inv_eval<THREADS, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      optin - 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_inv_eval_q<THREADS, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - 1024);
         if (e != cudaSuccess) return e;
         once.done(P->device);
     }
@@ -509,6 +716,9 @@ cudaError_t ib_launch(const fastlsq_inverse_plan *P, cudaStream_t st, int grid, 
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    if (P->thin_q)
+        return cudaLaunchKernelEx(&cfg, k_inv_eval_q<THREADS, C>, (const InvDesc *)P->d_desc,
+                                  (const int *)P->d_order, P->n_inst, P->d_queue, P->n_src, P->nint_max, P->n_max);
     return cudaLaunchKernelEx(&cfg, k_inv_eval<THREADS, C>, (const InvDesc *)P->d_desc, (const int *)P->d_order,
                               P->n_inst, P->d_queue, P->n_src, ib_rows(P->m_aug_max, C), P->n_max);
 }
@@ -517,6 +727,8 @@ void plan_free(fastlsq_inverse_plan *P)
 {
     if (!P) return;
     for (fastlsq_factor *f : P->factors) fastlsq_factor_destroy(f);
+    for (double *q : P->Qbuf)
+        if (q) cudaFreeAsync(q, P->stream);
     if (P->H) cudaFreeAsync(P->H, P->stream);
     if (P->d_desc) cudaFreeAsync(P->d_desc, P->stream);
     if (P->d_order) cudaFreeAsync(P->d_order, P->stream);
@@ -546,7 +758,7 @@ extern "C" int fastlsq_inverse_prepare(fastlsq_ctx *ctx, const fastlsq_inverse_i
     opI.d = 2;
     opI.n_terms = 1;
     opI.coef[0] = 1.0;
-    int64_t m_max = 0, n_max = 0, maug_max = 0;
+    int64_t m_max = 0, n_max = 0, maug_max = 0, nint_max = 0;
     for (int q = 0; q < n_inst; ++q) {
         const fastlsq_inverse_instance &I = inst[q];
         if (I.n_int < 1 || I.n_bc < 0 || I.n_feat < 1 || I.n_feat > FL_MAX_FEAT || I.n_sens < 1 ||
@@ -556,10 +768,14 @@ extern "C" int fastlsq_inverse_prepare(fastlsq_ctx *ctx, const fastlsq_inverse_i
         m_max = std::max<int64_t>(m_max, fl_round_up(I.n_int + I.n_bc, 4));
         n_max = std::max<int64_t>(n_max, I.n_feat);
         maug_max = std::max<int64_t>(maug_max, I.n_int + I.n_bc + I.n_feat);
+        nint_max = std::max<int64_t>(nint_max, I.n_int);
     }
-    // the evaluation keeps y [m_aug] (split over a cluster's ranks) and one n-vector per
-    // CTA in shared memory: the plan must fit at least the smallest configuration
-    if (ib_smem(256, maug_max, n_max, 4) > (size_t)ctx->max_smem_optin - 1024)
+    // the evaluation keeps y [m_aug] (split over a cluster's ranks; thin-Q form: s at the
+    // interior rows) and one n-vector per CTA in shared memory: the plan must fit at
+    // least the smallest configuration
+    const int thin_q = ctx->inverse_thin_q;
+    if ((thin_q ? ib_q_smem(256, nint_max, n_max, 4) : ib_smem(256, maug_max, n_max, 4)) >
+        (size_t)ctx->max_smem_optin - 1024)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID,
                        "inverse_prepare: %lld rows + features exceed the evaluation's shared memory",
                        (long long)maug_max);
@@ -571,7 +787,10 @@ extern "C" int fastlsq_inverse_prepare(fastlsq_ctx *ctx, const fastlsq_inverse_i
     P->n_src = n_src;
     P->m_aug_max = maug_max;
     P->n_max = n_max;
+    P->nint_max = nint_max;
+    P->thin_q = thin_q;
     P->factors.assign(n_inst, nullptr);
+    P->Qbuf.assign(n_inst, nullptr);
     P->h_desc.resize(n_inst);
     size_t h_total = 0;
     for (int q = 0; q < n_inst; ++q) h_total += (size_t)inst[q].n_sens * inst[q].n_feat;
@@ -677,6 +896,32 @@ extern "C" int fastlsq_inverse_prepare(fastlsq_ctx *ctx, const fastlsq_inverse_i
                     break;
                 }
                 const fastlsq_factor *f = P->factors[q];
+                // thin-Q form: Q [I; 0] into a copy of the factor's storage with n more
+                // columns, then its interior rows kept (ldq rows, a multiple of 4)
+                const int64_t ldq = fl_round_up(I.n_int, 4);
+                if (thin_q) {
+                    double *G = nullptr;
+                    cudaError_t ge = cudaMallocAsync(&G, sizeof(double) * f->ld * 2 * n, w.s);
+                    if (ge == cudaSuccess)
+                        ge = cudaMemcpyAsync(G, f->F, sizeof(double) * f->ld * n, cudaMemcpyDeviceToDevice, w.s);
+                    if (ge != cudaSuccess) {
+                        if (G) cudaFreeAsync(G, w.s);
+                        wrc = fl_cuda(c, ge, "thin Q buffer");
+                        break;
+                    }
+                    wrc = fl_form_q_f64(c, G, f->ld, f->m_aug, n, f->nb, (const double *)f->T, n);
+                    if (wrc >= 0) {
+                        ge = cudaMallocAsync(&P->Qbuf[q], sizeof(double) * ldq * n, w.s);
+                        if (ge == cudaSuccess) ge = cudaMemsetAsync(P->Qbuf[q], 0, sizeof(double) * ldq * n, w.s);
+                        if (ge == cudaSuccess)
+                            ge = cudaMemcpy2DAsync(P->Qbuf[q], sizeof(double) * ldq, G + n * f->ld,
+                                                   sizeof(double) * f->ld, sizeof(double) * I.n_int, n,
+                                                   cudaMemcpyDeviceToDevice, w.s);
+                        if (ge != cudaSuccess) wrc = fl_cuda(c, ge, "thin Q copy");
+                    }
+                    cudaFreeAsync(G, w.s);
+                    if (wrc < 0) break;
+                }
                 InvDesc &D = P->h_desc[q];
                 D.n_int = I.n_int;
                 D.n_feat = n;
@@ -691,6 +936,8 @@ extern "C" int fastlsq_inverse_prepare(fastlsq_ctx *ctx, const fastlsq_inverse_i
                 D.H = H;
                 D.F = (const double *)f->F;
                 D.T = (const double *)f->T;
+                D.Q = P->Qbuf[q];
+                D.ldq = ldq;
                 D.beta = I.beta;
                 D.loss = I.loss;
                 D.dtheta = I.dtheta;
@@ -757,7 +1004,8 @@ extern "C" int fastlsq_inverse_eval(fastlsq_ctx *ctx, const fastlsq_inverse_plan
         (cluster != 1 && cluster != 2 && cluster != 4))
         return fl_fail(ctx, FASTLSQ_ERR_INVALID,
                        "inverse_eval: threads 256 or 512, 1..4 CTAs per SM, clusters of 1, 2 or 4");
-    const size_t smem = ib_smem(threads, P->m_aug_max, P->n_max, cluster);
+    const size_t smem = P->thin_q ? ib_q_smem(threads, P->nint_max, P->n_max, cluster)
+                                  : ib_smem(threads, P->m_aug_max, P->n_max, cluster);
     if (smem * ctas_per_sm > (size_t)ctx->max_smem_optin)
         return fl_fail(ctx, FASTLSQ_ERR_INVALID, "inverse_eval: %d CTAs per SM do not fit in shared memory",
                        ctas_per_sm);

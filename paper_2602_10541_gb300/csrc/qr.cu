@@ -300,7 +300,7 @@ struct TrailYSmem {
     static constexpr size_t bytes = stage > zscr ? stage : zscr;
 };
 
-template <typename T, int NB>
+template <typename T, int NB, bool TFWD = false>
 __global__ void __launch_bounds__(TY_THREADS)
 k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, int64_t nct, int64_t coff,
           int64_t rows_per_split, T *__restrict__ Ypart, T *__restrict__ Z, const T *__restrict__ Tblk,
@@ -402,8 +402,8 @@ k_trail_y(const T *__restrict__ F, int64_t ld, int64_t k, int64_t m, int ncols, 
             if (c < nct) Ypart[((int64_t)blockIdx.y * NB + LPW * warp + a) * nct + c] = acc[a][b];
         }
     int *cnt = counters + (int64_t)blockIdx.x * TREE_STRIDE;
-    trail_finish_z<T, NB, TY_COLS, TY_THREADS>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Z, cnt, cnt + 1,
-                                               reinterpret_cast<T *>(ty_raw));
+    trail_finish_z<T, NB, TY_COLS, TY_THREADS, false, TFWD>(Ypart, (int)gridDim.y, nct, cbase, Tblk, Z, cnt,
+                                                            cnt + 1, reinterpret_cast<T *>(ty_raw));
 }
 
 // C(i, c) -= sum_l V(i, l) Z(l, c).  CTA tile TC_ROWS x TC_COLS; each thread owns 4
@@ -788,7 +788,7 @@ static int launch_panel(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m
     return 0;
 }
 
-template <typename T, int NB>
+template <typename T, int NB, bool TFWD = false>
 static int launch_trailing(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_t m_aug,
                            int ncols, int64_t nct, int64_t coff, const T *Tblk, int *counters)
 {
@@ -812,14 +812,14 @@ static int launch_trailing(fastlsq_ctx *ctx, T *F, int64_t ld, int64_t k, int64_
         cudaError_t e = cudaFuncSetAttribute(k_trail_c<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_c);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trail_y<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_trail_y<T, NB, TFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)TrailYSmem<T, NB>::bytes);
         if (e != cudaSuccess) return fl_cuda(ctx, e, "trailing-update attributes");
         attr_once.done(ctx->device);
     }
     FL_PROF_N(ctx, FASTLSQ_K_TRAIL_SIMT, 2);
-    k_trail_y<T, NB><<<dim3((unsigned)ctiles, (unsigned)nsplit), TY_THREADS, TrailYSmem<T, NB>::bytes,
-                       ctx->stream>>>(F, ld, k, m_aug, ncols, nct, coff, rows_per_split, Ypart, Z, Tblk, counters);
+    k_trail_y<T, NB, TFWD><<<dim3((unsigned)ctiles, (unsigned)nsplit), TY_THREADS, TrailYSmem<T, NB>::bytes,
+                             ctx->stream>>>(F, ld, k, m_aug, ncols, nct, coff, rows_per_split, Ypart, Z, Tblk, counters);
     FL_CHECK_LAUNCH(ctx, "trail_y");
     k_trail_c<T, NB><<<dim3((unsigned)fl_cdiv(mp, TC_ROWS), (unsigned)fl_cdiv(nct, TC_COLS)), 256, smem_c,
                        ctx->stream>>>(F, ld, k, m_aug, ncols, nct, coff, Z);
@@ -1074,6 +1074,57 @@ template int fl_apply_q<float>(fastlsq_ctx *, const float *, int64_t, int64_t, i
                                const float *, float *, int, const float *);
 template int fl_apply_q<double>(fastlsq_ctx *, const double *, int64_t, int64_t, int64_t, int,
                                 const double *, double *, int, const float *);
+
+// E = [I_n; 0] (ld rows, the padding rows included, n columns)
+__global__ void k_eye(double *__restrict__ E, int64_t ld, int64_t n)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ld * n) return;
+    const int64_t i = idx % ld, j = idx / ld;
+    E[idx] = (i == j) ? 1.0 : 0.0;
+}
+
+// The thin Q of an FP64 factor: columns [col0, col0 + n) of F (which holds the factor
+// in its first n columns, leading dimension ld) become Q [I_n; 0] = H_0 H_1 ... H_{P-1}
+// [I_n; 0].  The panels are applied last to first by the SIMT narrow update with Z = T Y
+// (each H_p = I - V_p T_p V_p^T); panel p touches rows [k_p, m_aug) and only the
+// columns [k_p, n) of E, since E's columns left of k_p are still unit vectors above
+// row k_p there (as in LAPACK's orgqr).  About m n^2 - n^3 / 3 FMAs, the work of the
+// factorisation's own updates.
+template <int NB>
+static int form_q_nb(fastlsq_ctx *ctx, double *F, int64_t ld, int64_t m_aug, int64_t n, const double *Tall,
+                     int64_t col0)
+{
+    const int64_t max_tiles = fl_cdiv(n, 32) + 8;
+    const size_t cbytes = sizeof(int) * (size_t)max_tiles * TREE_STRIDE;
+    int *counters = (int *)fl_ws(ctx, FL_WS_COUNTERS, cbytes);
+    if (!counters) return FASTLSQ_ERR_NOMEM;
+    cudaError_t e = cudaMemsetAsync(counters, 0, cbytes, ctx->stream);
+    if (e != cudaSuccess) return fl_cuda(ctx, e, "form_q counters");
+    k_eye<<<(unsigned)fl_cdiv(ld * n, 256), 256, 0, ctx->stream>>>(F + col0 * ld, ld, n);
+    FL_CHECK_LAUNCH(ctx, "form_q eye");
+    const int64_t npan = fl_cdiv(n, NB);
+    for (int64_t p = npan - 1; p >= 0; --p) {
+        const int64_t k = p * NB;
+        const int ncols = (int)std::min<int64_t>(NB, n - k);
+        FL_TRY((launch_trailing<double, NB, true>(ctx, F, ld, k, m_aug, ncols, n - k, col0 - ncols,
+                                                  Tall + p * NB * NB, counters)));
+    }
+    return 0;
+}
+
+int fl_form_q_f64(fastlsq_ctx *ctx, double *F, int64_t ld, int64_t m_aug, int64_t n, int nb, const double *Tall,
+                  int64_t col0)
+{
+    if (col0 < n || m_aug < n || ld < m_aug || (ld & 3))
+        return fl_fail(ctx, FASTLSQ_ERR_INVALID, "form_q: shape");
+    switch (nb) {
+    case 32: return form_q_nb<32>(ctx, F, ld, m_aug, n, Tall, col0);
+    case 16: return form_q_nb<16>(ctx, F, ld, m_aug, n, Tall, col0);
+    case 8: return form_q_nb<8>(ctx, F, ld, m_aug, n, Tall, col0);
+    default: return fl_fail(ctx, FASTLSQ_ERR_INVALID, "panel width %d", nb);
+    }
+}
 
 template <typename TA, typename T>
 int fl_copy_in(fastlsq_ctx *ctx, const TA *A, int64_t ldA, int64_t m, int64_t n, double mu,

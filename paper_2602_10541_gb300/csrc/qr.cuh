@@ -88,6 +88,11 @@ int fl_block_join(fastlsq_ctx *ctx);
 bool fl_encode_f32_map(CUtensorMap *m, const float *F, int64_t ld, int64_t ntot, uint32_t box_r, uint32_t box_c,
                        bool swizzle128);
 
+// Thin Q of an FP64 factor: columns [col0, col0 + n) of F (ld rows, col0 >= n, F's
+// first n columns the factor, T blocks Tall) set to Q [I_n; 0] (qr.cu)
+int fl_form_q_f64(fastlsq_ctx *ctx, double *F, int64_t ld, int64_t m_aug, int64_t n, int nb, const double *Tall,
+                  int64_t col0);
+
 // Krylov refinement with the factor's R as preconditioner (refine.cu)
 int fl_refine_cgls(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs64, double *beta64,
                    int max_iter, double tol, double *norms_dev);

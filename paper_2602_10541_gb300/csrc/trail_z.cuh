@@ -4,7 +4,8 @@
 // per group) adds the group's partials in split order and stores the sum in the
 // group's first slot; the last group to finish (an atomic per tile) adds the group
 // sums in group order, so the result does not depend on which CTAs finish last, and
-// forms Z = T^T Y (T upper triangular) for the tile.  The counters are reset for the
+// forms Z = T^T Y (T upper triangular) for the tile -- or, with TFWD, Z = T Y (the
+// reflectors applied as Q = H_0 ... H_{P-1}, H_p = I - V T V^T, instead of Q^T).  The counters are reset for the
 // next panel.  Z is stored [l][c] with row stride nct, or (Zimg) as the tensor-core
 // operand image of the tile: Z^T split into tf32 hi and lo parts, each 128 rows (c)
 // of 128 bytes (l) in the K-major 128-byte-swizzled layout.
@@ -18,7 +19,7 @@ constexpr int TREE_MAXG = 32;      // groups per column tile (splits <= 512)
 constexpr int TREE_STRIDE = 1 + TREE_MAXG;
 constexpr int TREE_MAX_SPLITS = TREE_GS * TREE_MAXG;
 
-template <typename T, int NB, int COLS, int THREADS, bool IMG = false>
+template <typename T, int NB, int COLS, int THREADS, bool IMG = false, bool TFWD = false>
 __device__ __forceinline__ void trail_finish_z(T *__restrict__ Ypart, int nsplit, int64_t nct,
                                                int64_t cbase, const T *__restrict__ Tblk,
                                                T *__restrict__ Z, int *counter, int *gcounter, T *scratch)
@@ -95,7 +96,8 @@ __device__ __forceinline__ void trail_finish_z(T *__restrict__ Ypart, int nsplit
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) sY[it * THREADS + threadIdx.x] = acc[it];
     __syncthreads();
-    // Z(l, c) = sum_{q <= l} T(q, l) Y(q, c): the thread keeps its column c of Y in registers
+    // Z(l, c) = sum_{q <= l} T(q, l) Y(q, c) (TFWD: sum_{q >= l} T(l, q) Y(q, c)): the
+    // thread keeps its column c of Y in registers
     // and forms its ITEMS rows l = h + R it at once (R = THREADS / COLS, h = tid / COLS, the
     // same for a whole warp, so T's entries are broadcast reads)
     static_assert(THREADS % COLS == 0, "threads cover whole columns");
@@ -112,7 +114,11 @@ __device__ __forceinline__ void trail_finish_z(T *__restrict__ Ypart, int nsplit
 #pragma unroll
         for (int it = 0; it < ITEMS; ++it) {
             const int l = h + R * it;
-            if (q <= l) z[it] += sT[q + l * NB] * y[q];
+            if constexpr (TFWD) {
+                if (q >= l) z[it] += sT[l + q * NB] * y[q];
+            } else {
+                if (q <= l) z[it] += sT[q + l * NB] * y[q];
+            }
         }
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {

@@ -223,7 +223,7 @@ class InverseBatch:
     per instance).  Observations come from the forward map at the instances' true
     parameters plus their noise; evaluations start at their perturbed parameters."""
 
-    def __init__(self, ctx, workloads, device="cuda:0", mu=1e-10, bc_weight=100.0, launch=None):
+    def __init__(self, ctx, workloads, device="cuda:0", mu=1e-10, bc_weight=100.0, launch=None, thin_q=True):
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
         self.ctx, self.ws = ctx, list(workloads)
         self.inst = [dict(x_int=t(w.x_int), x_bc=t(w.x_bc), W=t(w.W), b=t(w.b), sensors=t(w.sensors),
@@ -234,6 +234,8 @@ class InverseBatch:
                      for w in self.ws]
         self.n_src = self.ws[0].params.size // 4
         self.launch = launch or tuned("inverse_eval", {"threads": 256, "ctas_per_sm": 1, "cluster": 1})
+        self.thin_q = bool(thin_q)
+        fl.fastlsq_set_option(ctx, fl.OPT_INVERSE_THIN_Q, int(self.thin_q))
         self.plan = fl.fastlsq_inverse_prepare(ctx, self.inst, fl.Op(self.ws[0].alpha, self.ws[0].coef),
                                                self.n_src, mu=mu, bc_weight=bc_weight)
         self.device = device

@@ -69,11 +69,18 @@ def batch():
     return cases, dev
 
 
+@pytest.mark.parametrize("thin_q", [1, 0])
 @pytest.mark.parametrize("threads,ctas,cluster", [(256, 1, 1), (512, 1, 1), (256, 2, 1), (256, 1, 2),
                                                   (512, 1, 2), (512, 2, 4)])
-def test_persistent_batch_matches_oracle(ctx, batch, threads, ctas, cluster):
+def test_persistent_batch_matches_oracle(ctx, batch, threads, ctas, cluster, thin_q):
+    """Both forms of the plan: the explicit thin Q of the interior rows (default) and
+    the reflectors alone."""
     cases, dev = batch
-    plan = fl.fastlsq_inverse_prepare(ctx, dev, OP, 4, mu=MU)
+    fl.fastlsq_set_option(ctx, fl.OPT_INVERSE_THIN_Q, thin_q)
+    try:
+        plan = fl.fastlsq_inverse_prepare(ctx, dev, OP, 4, mu=MU)
+    finally:
+        fl.fastlsq_set_option(ctx, fl.OPT_INVERSE_THIN_Q, 1)
     for d in dev:
         d["loss"].zero_()
         d["dtheta"].zero_()
@@ -115,14 +122,15 @@ def test_persistent_batch_gradient_matches_central_differences(ctx, batch):
     assert np.abs(g - fd).max() <= 1e-4 * np.abs(fd).max(), (g, fd)
 
 
-@pytest.mark.parametrize("cluster", [1, 2])
-def test_persistent_batch_replays_from_a_cuda_graph(ctx, batch, cluster):
+@pytest.mark.parametrize("thin_q,cluster", [(1, 1), (1, 2), (0, 2)])
+def test_persistent_batch_replays_from_a_cuda_graph(ctx, batch, thin_q, cluster):
     """The evaluation allocates nothing and never synchronises: captured once, a replay
     after theta changes gives the eager results bit for bit (at a fixed cluster size
     the sums run in a fixed order)."""
     cases, dev = batch
     s = torch.cuda.Stream()
     gctx = fl.Context(0, stream=s)
+    fl.fastlsq_set_option(gctx, fl.OPT_INVERSE_THIN_Q, thin_q)
     sub = dev[:4]
     with torch.cuda.stream(s):
         plan = fl.fastlsq_inverse_prepare(gctx, sub, OP, 4, mu=MU)
