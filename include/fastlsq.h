@@ -404,10 +404,10 @@ FASTLSQ_API int fastlsq_inverse_batch(fastlsq_ctx *ctx, const fastlsq_inverse_in
  * and bc_weight are used; prec, refine and adjoint fields are ignored (the factor is
  * FP64).  The factorisations run a few at a time on worker streams of the library's
  * own, after the work already queued on the context's stream.  Limits: n_src <= 8,
- * n_sens <= 256, and a quarter of n_int + n_bc + n_feat (thin-Q plans: n_int) plus
- * n_feat FP64 values fitting in a CTA's shared memory, else -1 (the evaluation's
- * configuration must fit too).  Synchronises the
- * context's stream; returns 0 and *plan, or a negative status (nothing is kept).
+ * n_sens <= 256, and a quarter of n_int + n_bc + n_feat (thin-Q plans: all of n_int)
+ * plus n_feat FP64 values fitting in a CTA's shared memory, else -1 (the evaluation's
+ * configuration must fit too).  Synchronises the context's stream; returns 0 and
+ * *plan, or a negative status (nothing is kept).
  *
  * fastlsq_inverse_eval runs one gradient evaluation of every instance in ONE
  * persistent launch: a grid of min(n_inst, SMs * ctas_per_sm / cluster) clusters of
