@@ -235,12 +235,15 @@ __device__ void ib_trsv(const InvDesc &D, double *x, bool transpose)
                 if (lane < bw && i < bw)
                     rr[i] = transpose ? F[(c0 + i) + (c0 + lane) * ld] : F[(c0 + lane) + (c0 + i) * ld];
             }
+            // the block's 32 reciprocals of the diagonal at once (one division per lane),
+            // so that the sequential chain below is a multiply and an FMA per step
+            const double rinv = 1.0 / ((lane < bw) ? F[(c0 + lane) + (c0 + lane) * ld] : 1.0);
             if (!transpose) {
 #pragma unroll
                 for (int c = 31; c >= 0; --c) {
                     if (c >= bw) continue;
                     double xc = 0.0;
-                    if (lane == c) xc = xv / rr[c];
+                    if (lane == c) xc = xv * rinv;
                     xc = __shfl_sync(0xffffffffu, xc, c);
                     if (lane == c) xv = xc;
                     if (lane < c) xv = fma(-rr[c], xc, xv);
@@ -250,7 +253,7 @@ __device__ void ib_trsv(const InvDesc &D, double *x, bool transpose)
                 for (int r = 0; r < 32; ++r) {
                     if (r >= bw) continue;
                     double xr = 0.0;
-                    if (lane == r) xr = xv / rr[r];
+                    if (lane == r) xr = xv * rinv;
                     xr = __shfl_sync(0xffffffffu, xr, r);
                     if (lane == r) xv = xr;
                     if (lane > r) xv = fma(-rr[r], xr, xv);

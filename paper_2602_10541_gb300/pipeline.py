@@ -314,6 +314,8 @@ def main(argv=None):
     ap.add_argument("--rows", type=int, default=36864, help="random: rows")
     ap.add_argument("--cols", type=int, default=256, help="random: columns")
     ap.add_argument("--instances", type=int, default=16, help="inverse: instances")
+    ap.add_argument("--cluster", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="inverse: CTAs per instance (0: the tuned launch)")
     a = ap.parse_args(argv)
     ctx = fl.Context(0)
     fl.fastlsq_set_option(ctx, fl.OPT_TENSOR_CORE, a.tensor_core)
@@ -331,6 +333,8 @@ def main(argv=None):
         return
     if a.workload == "inverse":
         batch = InverseBatch(ctx, [wl.inverse_instance(q) for q in range(a.instances)])
+        if a.cluster:
+            batch.launch = {**batch.launch, "cluster": a.cluster}
         batch.observe()
         for _ in range(a.steps):
             batch.eval()
