@@ -631,6 +631,8 @@ def main():
                     help="least rows per split of the SIMT updates inside an outer block")
     ap.add_argument("--lookahead", type=int, default=0, choices=[0, 1],
                     help="panel-by-panel modes: 1 factors the next panel on a second stream")
+    ap.add_argument("--asm64-ctas", type=int, default=0, choices=range(0, 9),
+                    help="FP64 assembly: 0 one CTA per tile; k a persistent grid of k CTAs per SM")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -666,6 +668,7 @@ def main():
         fl.fastlsq_set_option(c, fl.OPT_LOOKAHEAD, args.lookahead)
         fl.fastlsq_set_option(c, fl.OPT_SPLIT_ROWS, args.split_rows)
         fl.fastlsq_set_option(c, fl.OPT_FUSED_LOOKAHEAD, args.fused_lookahead)
+        fl.fastlsq_set_option(c, fl.OPT_FP64_ASSEMBLY_CTAS, args.asm64_ctas)
         wi = make(seed_offset=rank * B + i)
         with torch.cuda.stream(c.stream):
             dpi = pl.upload(wi, dev)
@@ -906,6 +909,7 @@ def main():
                            "tensor_core_updates": int(solve_stats.tensor_core),
                            "panel_nb": nb, "outer_block": BLK if blocked else None,
                            "lookahead": bool(args.lookahead), "split_rows": args.split_rows,
+                           "fp64_assembly_ctas_per_sm": args.asm64_ctas,
                            "fused_lookahead": bool(args.fused_lookahead),
                            "l2": "flushed between steps (256 MiB write outside the step events)",
                            "instances_per_step": B,

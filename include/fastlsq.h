@@ -614,7 +614,7 @@ typedef enum {
                                       Small splits give one solve the shortest latency;
                                       larger ones launch fewer CTAs per update, leaving
                                       more of the GPU to other solves running beside it */
-    FASTLSQ_OPT_INVERSE_THIN_Q = 7  /* 1 (default): fastlsq_inverse_prepare also forms each
+    FASTLSQ_OPT_INVERSE_THIN_Q = 7, /* 1 (default): fastlsq_inverse_prepare also forms each
                                       instance's thin Q restricted to its interior rows,
                                       Qi = (Q [I; 0])[0:n_int] (n_int x n FP64, about the
                                       factorisation's FP64 work again), and the evaluations
@@ -622,6 +622,11 @@ typedef enum {
                                       instead of 4 m_aug n with the reflectors; 0: the
                                       plan keeps the reflectors only (faster setup, less
                                       memory). Read when a plan is prepared. */
+    FASTLSQ_OPT_FP64_ASSEMBLY_CTAS = 8 /* FP64 operator assembly launch: 0 (default) one CTA
+                                      of 256 threads per 128 x 64 tile of entries; k = 1..8
+                                      a persistent grid of k CTAs per SM looping over the
+                                      tiles (a smaller footprint beside kernels of other
+                                      streams).  The entries are the same either way. */
 } fastlsq_option;
 
 /* Set a context option (see fastlsq_option).  Returns 0 or -1 for an unknown option. */

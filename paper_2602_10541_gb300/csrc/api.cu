@@ -328,6 +328,12 @@ extern "C" int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value)
         ctx->trsv32 = value ? 1 : 0;
         return 0;
     }
+    if (option == FASTLSQ_OPT_FP64_ASSEMBLY_CTAS) {
+        if (value < 0 || value > 8)
+            return fl_fail(ctx, FASTLSQ_ERR_INVALID, "FP64 assembly CTAs per SM %d outside 0..8", value);
+        ctx->asm64_ctas_per_sm = value;
+        return 0;
+    }
     if (option == FASTLSQ_OPT_INVERSE_THIN_Q) {
         ctx->inverse_thin_q = value ? 1 : 0;
         return 0;

@@ -168,7 +168,12 @@ k_assemble_f32(const double *__restrict__ x, int64_t n_rows,
     }
 }
 
-// FP64 assembly: double FMAs and double-precision sin/cos (CUDA's sin, cos).
+// FP64 assembly: double FMAs and double-precision sin/cos (CUDA's sin, cos).  Tiles of
+// ASM_ROWS x ASM_COLS entries, tile t at row block t % row blocks and column block
+// t / row blocks; a CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... (one tile
+// per CTA when the grid covers them all, else a persistent grid whose small footprint
+// leaves the SMs' other warp slots to kernels of other streams: the kernel is bound by
+// the FP64 pipe, which the FP32 and tensor-core kernels beside it do not use).
 template <bool NEED_COS, int NPP>
 __global__ void __launch_bounds__(ASM_THREADS)
 k_assemble_f64(const double *__restrict__ x, int64_t n_rows, int d,
@@ -179,52 +184,57 @@ k_assemble_f64(const double *__restrict__ x, int64_t n_rows, int d,
     __shared__ double sW[ASM_COLS][FL_MAX_D];
     __shared__ double sB[ASM_COLS], sP[ASM_COLS], sQ[ASM_COLS];
     __shared__ double sM[NPP > 0 ? NPP : 1][ASM_COLS];
-    const int64_t col0 = (int64_t)blockIdx.y * ASM_COLS;
-    const int64_t row0 = (int64_t)blockIdx.x * ASM_ROWS;
-    for (int t = threadIdx.x; t < ASM_COLS; t += blockDim.x) {
-        int64_t j = col0 + t;
-        bool ok = j < n_feat;
-        for (int k = 0; k < FL_MAX_D; ++k) sW[t][k] = (ok && k < d) ? W[j * d + k] : 0.0;
-        sB[t] = ok ? b[j] : 0.0;
-        sP[t] = ok ? pref[j] : 0.0;
-        sQ[t] = ok ? pref[n_feat + j] : 0.0;
-        if constexpr (NPP > 0)
-            for (int q = 0; q < n_pp; ++q) sM[q][t] = ok ? pref[(2 + q) * n_feat + j] : 0.0;
-    }
-    __syncthreads();
+    const int64_t nrb = (n_rows + ASM_ROWS - 1) / ASM_ROWS;
+    const int64_t ntiles = nrb * ((n_feat + ASM_COLS - 1) / ASM_COLS);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    double xr[4][FL_MAX_D];
-    double cpt[NPP > 0 ? NPP : 1][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        int64_t i = row0 + lane + 32 * u;
-        bool ok = i < n_rows;
-#pragma unroll
-        for (int k = 0; k < FL_MAX_D; ++k) xr[u][k] = (ok && k < d) ? x[i * d + k] : 0.0;
-#pragma unroll
-        for (int q = 0; q < NPP; ++q) cpt[q][u] = (ok && q < n_pp) ? pp.c[q][i] : 0.0;
-    }
-    for (int cc = 0; cc < ASM_COLS / 8; ++cc) {
-        const int c = warp * (ASM_COLS / 8) + cc;
-        const int64_t j = col0 + c;
-        if (j >= n_feat) break;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t col0 = (tile / nrb) * ASM_COLS;
+        const int64_t row0 = (tile % nrb) * ASM_ROWS;
+        __syncthreads();                        // the previous tile's reads of the staging
+        for (int t = threadIdx.x; t < ASM_COLS; t += blockDim.x) {
+            int64_t j = col0 + t;
+            bool ok = j < n_feat;
+            for (int k = 0; k < FL_MAX_D; ++k) sW[t][k] = (ok && k < d) ? W[j * d + k] : 0.0;
+            sB[t] = ok ? b[j] : 0.0;
+            sP[t] = ok ? pref[j] : 0.0;
+            sQ[t] = ok ? pref[n_feat + j] : 0.0;
+            if constexpr (NPP > 0)
+                for (int q = 0; q < n_pp; ++q) sM[q][t] = ok ? pref[(2 + q) * n_feat + j] : 0.0;
+        }
+        __syncthreads();
+        double xr[4][FL_MAX_D];
+        double cpt[NPP > 0 ? NPP : 1][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             int64_t i = row0 + lane + 32 * u;
-            double z = sB[c];
+            bool ok = i < n_rows;
 #pragma unroll
-            for (int k = 0; k < FL_MAX_D; ++k)
-                if (k < d) z = fma(sW[c][k], xr[u][k], z);
-            double sn, cs = 0.0;
-            if (NEED_COS) sincos(z, &sn, &cs);
-            else sn = sin(z);
-            double val = sP[c] * sn;
-            if (NEED_COS) val = fma(sQ[c], cs, val);
+            for (int k = 0; k < FL_MAX_D; ++k) xr[u][k] = (ok && k < d) ? x[i * d + k] : 0.0;
 #pragma unroll
-            for (int q = 0; q < NPP; ++q)
-                if (q < n_pp) val = fma(cpt[q][u] * sM[q][c], ((pp_cos_mask >> q) & 1) ? cs : sn, val);
-            if (i < n_rows) A[j * ldA + row_offset + i] = val;
+            for (int q = 0; q < NPP; ++q) cpt[q][u] = (ok && q < n_pp) ? pp.c[q][i] : 0.0;
+        }
+        for (int cc = 0; cc < ASM_COLS / 8; ++cc) {
+            const int c = warp * (ASM_COLS / 8) + cc;
+            const int64_t j = col0 + c;
+            if (j >= n_feat) break;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int64_t i = row0 + lane + 32 * u;
+                double z = sB[c];
+#pragma unroll
+                for (int k = 0; k < FL_MAX_D; ++k)
+                    if (k < d) z = fma(sW[c][k], xr[u][k], z);
+                double sn, cs = 0.0;
+                if (NEED_COS) sincos(z, &sn, &cs);
+                else sn = sin(z);
+                double val = sP[c] * sn;
+                if (NEED_COS) val = fma(sQ[c], cs, val);
+#pragma unroll
+                for (int q = 0; q < NPP; ++q)
+                    if (q < n_pp) val = fma(cpt[q][u] * sM[q][c], ((pp_cos_mask >> q) & 1) ? cs : sn, val);
+                if (i < n_rows) A[j * ldA + row_offset + i] = val;
+            }
         }
     }
 }
@@ -540,7 +550,11 @@ int fl_launch_assemble_f64(fastlsq_ctx *ctx, const fl_op_params &op, const doubl
     bool need_cos = op_needs_cos(op, &mask);
     fl_pp_rows pp{};
     for (int q = 0; q < op.n_pp; ++q) pp.c[q] = op.pp_coef[q];
-    dim3 grid((unsigned)fl_cdiv(n_rows, ASM_ROWS), (unsigned)fl_cdiv(n_feat, ASM_COLS));
+    const int64_t ntiles = fl_cdiv(n_rows, ASM_ROWS) * fl_cdiv(n_feat, ASM_COLS);
+    int64_t g = ntiles;
+    if (ctx->asm64_ctas_per_sm > 0) g = std::min<int64_t>(g, (int64_t)ctx->num_sms * ctx->asm64_ctas_per_sm);
+    if (g > INT32_MAX) g = INT32_MAX;
+    const unsigned grid = (unsigned)g;
     FL_PROF(ctx, FASTLSQ_K_ASSEMBLE_F64);
 #define FL_ASM64(COS, NPP)                                                                          \
     k_assemble_f64<COS, NPP><<<grid, ASM_THREADS, 0, ctx->stream>>>(                                \

@@ -204,6 +204,7 @@ OPT_FUSED_LOOKAHEAD = 4
 OPT_ROW_PANEL = 5
 OPT_SPLIT_ROWS = 6
 OPT_INVERSE_THIN_Q = 7
+OPT_FP64_ASSEMBLY_CTAS = 8
 
 
 def fastlsq_set_option(ctx, option, value):

@@ -85,6 +85,33 @@ def test_assemble_matches_oracle(ctx, dtype, case, row_offset):
     assert np.all(got[row_offset + n_rows:] == SENTINEL)
 
 
+@pytest.mark.parametrize("ctas", [1, 2])
+def test_fp64_assembly_persistent_grid_is_identical(ctx, ctas):
+    """The persistent FP64 assembly grid (k CTAs per SM looping over the 128 x 64 tiles)
+    writes the same entries as one CTA per tile, bit for bit, on a ragged operator
+    with more tiles than the grid (2,000 + 300 rows x 700 features) and a per-point term."""
+    d, n_rows, n_feat = 3, 2300, 700
+    rng = np.random.default_rng(11)
+    x = rng.random((n_rows, d))
+    W = 4 * rng.standard_normal((n_feat, d))
+    b = rng.uniform(0, 2 * math.pi, n_feat)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=DEV)
+    op = fl.Op([[2, 0, 0], [0, 2, 0], [0, 0, 1]], [1.0, 1.0, -0.5], pp_alpha=[[0, 0, 0]],
+               pp_coef=[t(rng.standard_normal(n_rows))])
+    out = []
+    for k in (0, ctas):
+        fl.fastlsq_set_option(ctx, fl.OPT_FP64_ASSEMBLY_CTAS, k)
+        A = torch.full((n_feat, n_rows + 5), SENTINEL, dtype=torch.float64, device=DEV)
+        try:
+            fl.fastlsq_assemble(ctx, fl.F64, t(x), op, 2.0, t(W), t(b), 0.1, A, 5)
+        finally:
+            fl.fastlsq_set_option(ctx, fl.OPT_FP64_ASSEMBLY_CTAS, 0)
+        torch.cuda.synchronize()
+        out.append(A.cpu())
+    assert torch.equal(out[0], out[1])
+    assert torch.all(out[1][:, :5] == SENTINEL)
+
+
 @pytest.mark.parametrize("dtype", [fl.F32, fl.F64])
 def test_per_point_terms(ctx, dtype):
     # Newton Jacobian form: L = Lap plus per-point terms c_i phi_j (alpha = 0) and
