@@ -139,6 +139,29 @@ def test_eval_u_matches_definition():
     np.testing.assert_allclose(u, 0.25 * np.sin(x @ W.T + b) @ beta, rtol=1e-13)
 
 
+def test_eval_u_agrees_with_the_identity_operator_and_central_differences():
+    """u = sum_j beta_j scale sin(W_j . x + b_j) evaluated by eval_u equals the identity
+    operator's assembled rows times beta (a separate code path, pinned by the closed
+    forms above), and central differences of eval_u in x (h = 1e-4, error O(h^2))
+    reproduce the assembled Laplacian rows times beta: a wrong scale, sign or argument
+    in eval_u fails one of the two."""
+    d = 3
+    x, W, b = _setup(d)
+    beta = rng.standard_normal(W.shape[0])
+    u = oracle.eval_u(x, W, b, 0.25, beta)
+    A_id = oracle.assemble(x, np.zeros((1, d), np.int32), [1.0], W, b, 0.25)
+    np.testing.assert_allclose(u, A_id @ beta, rtol=1e-12, atol=1e-14)
+    h = 1e-4
+    lap_fd = np.zeros(x.shape[0])
+    for k in range(d):
+        e = np.zeros(d)
+        e[k] = h
+        lap_fd += (oracle.eval_u(x + e, W, b, 0.25, beta) - 2 * u + oracle.eval_u(x - e, W, b, 0.25, beta)) / h ** 2
+    A_lap = oracle.assemble(x, (2 * np.eye(d, dtype=np.int32)), [1.0] * d, W, b, 0.25)
+    ref = A_lap @ beta
+    assert np.abs(lap_fd - ref).max() <= 1e-5 * np.abs(ref).max() + 1e-9
+
+
 def test_workload_generators_are_deterministic_and_shaped():
     a = wl.helmholtz2d(n_int=64, n_bc=16, n_feat=8)
     c = wl.helmholtz2d(n_int=64, n_bc=16, n_feat=8)
