@@ -159,16 +159,30 @@ k_bimg(const float *__restrict__ F, int64_t ld, int64_t k, int nbk, int64_t mp, 
     extern __shared__ float sx[];          // sx[l * BI_LD + r]
     const int64_t t = blockIdx.x;
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < 128 * 32; idx += 256) {
-        const int l = idx >> 5, q4 = idx & 31;
-        const int64_t i = t * 128 + 4 * q4;                 // panel-local row of the quad
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (l < nbk && i < mp && k + i < ld) v = *reinterpret_cast<const float4 *>(F + (k + i) + (k + l) * ld);
-        float *d = sx + l * BI_LD + 4 * q4;
-        d[0] = (i + 0 < mp) ? v_mask(v.x, i + 0, l, nbk) : 0.f;
-        d[1] = (i + 1 < mp) ? v_mask(v.y, i + 1, l, nbk) : 0.f;
-        d[2] = (i + 2 < mp) ? v_mask(v.z, i + 2, l, nbk) : 0.f;
-        d[3] = (i + 3 < mp) ? v_mask(v.w, i + 3, l, nbk) : 0.f;
+    // the tile's 128 rows x 128 block columns: every load of a thread issued before its
+    // stores, in two halves of eight (a loop of dependent load-store pairs left one memory
+    // round trip per iteration exposed)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        float4 v[8];
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int idx = tid + (half * 8 + it) * 256, l = idx >> 5, q4 = idx & 31;
+            const int64_t i = t * 128 + 4 * q4;             // panel-local row of the quad
+            v[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (l < nbk && i < mp && k + i < ld) v[it] = *reinterpret_cast<const float4 *>(F + (k + i) + (k + l) * ld);
+        }
+        asm volatile("" ::: "memory");                   // the loads above stay ahead of the stores
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int idx = tid + (half * 8 + it) * 256, l = idx >> 5, q4 = idx & 31;
+            const int64_t i = t * 128 + 4 * q4;
+            float *d = sx + l * BI_LD + 4 * q4;
+            d[0] = (i + 0 < mp) ? v_mask(v[it].x, i + 0, l, nbk) : 0.f;
+            d[1] = (i + 1 < mp) ? v_mask(v[it].y, i + 1, l, nbk) : 0.f;
+            d[2] = (i + 2 < mp) ? v_mask(v[it].z, i + 2, l, nbk) : 0.f;
+            d[3] = (i + 3 < mp) ? v_mask(v[it].w, i + 3, l, nbk) : 0.f;
+        }
     }
     __syncthreads();
     // VU: row r, 16 chunks of 8 block columns (two K halves of 8 chunks)
@@ -527,35 +541,84 @@ k_bz(const float *__restrict__ Ysum, int64_t n_ext, int nbk, const float *__rest
     const int64_t n_tr = n_ext - nbk;
     const int64_t cbase = (int64_t)blockIdx.x * BU_N;
     const int nq = (nbk + NB - 1) / NB;
-    for (int idx = tid; idx < 128 * 128; idx += 256) {
-        const int e = idx >> 7, l = idx & 127;
-        sG[e * 129 + l] = (e < nbk && l < e) ? __ldcg(Ysum + (int64_t)e * BK + l) : 0.f;
+    // G and Y as 16-byte vectors of Ysum (row e of the Gram matrix and column cg of Y are
+    // 128 consecutive floats), each thread's loads all issued before its stores (a loop of
+    // dependent load-store pairs left one L2 round trip per iteration exposed)
+    {
+        constexpr int GIT = 128 * 32 / 256;              // float4 of G per thread
+        float4 gv[GIT];
+#pragma unroll
+        for (int it = 0; it < GIT; ++it) {
+            const int idx = tid + it * 256, e = idx >> 5, l4 = (idx & 31) * 4;
+            gv[it] = (e < nbk) ? __ldcg(reinterpret_cast<const float4 *>(Ysum + (int64_t)e * BK + l4))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        constexpr int YIT = BU_N * 32 / 256;             // float4 of Y per thread
+        float4 yv[YIT];
+#pragma unroll
+        for (int it = 0; it < YIT; ++it) {
+            const int idx = tid + it * 256, c = idx >> 5, l4 = (idx & 31) * 4;
+            const int64_t cg = cbase + c;
+            yv[it] = (cg < n_tr) ? __ldcg(reinterpret_cast<const float4 *>(Ysum + (nbk + cg) * BK + l4))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        asm volatile("" ::: "memory");                   // the loads above stay ahead of the stores
+#pragma unroll
+        for (int it = 0; it < GIT; ++it) {
+            const int idx = tid + it * 256, e = idx >> 5, l4 = (idx & 31) * 4;
+            float *d = sG + e * 129 + l4;
+            d[0] = (l4 + 0 < e) ? gv[it].x : 0.f;
+            d[1] = (l4 + 1 < e) ? gv[it].y : 0.f;
+            d[2] = (l4 + 2 < e) ? gv[it].z : 0.f;
+            d[3] = (l4 + 3 < e) ? gv[it].w : 0.f;
+        }
+#pragma unroll
+        for (int it = 0; it < YIT; ++it) {
+            const int idx = tid + it * 256, c = idx >> 5, l4 = (idx & 31) * 4;
+            sY[(l4 + 0) * 65 + c] = (l4 + 0 < nbk) ? yv[it].x : 0.f;
+            sY[(l4 + 1) * 65 + c] = (l4 + 1 < nbk) ? yv[it].y : 0.f;
+            sY[(l4 + 2) * 65 + c] = (l4 + 2 < nbk) ? yv[it].z : 0.f;
+            sY[(l4 + 3) * 65 + c] = (l4 + 3 < nbk) ? yv[it].w : 0.f;
+        }
+        const int nt4 = nq * NB * NB / 4;                // T blocks, a multiple of 4 floats
+#pragma unroll 4
+        for (int idx = tid; idx < nt4; idx += 256)
+            reinterpret_cast<float4 *>(sT)[idx] = __ldg(reinterpret_cast<const float4 *>(Tb) + idx);
     }
-    for (int idx = tid; idx < 128 * BU_N; idx += 256) {
-        const int c = idx >> 7, l = idx & 127;
-        const int64_t cg = cbase + c;
-        sY[l * 65 + c] = (cg < n_tr && l < nbk) ? __ldcg(Ysum + (nbk + cg) * BK + l) : 0.f;
-    }
-    for (int idx = tid; idx < nq * NB * NB; idx += 256) sT[idx] = Tb[idx];
     __syncthreads();
+    // a thread's NB / 4 rows (l = q0 + g + 4 u) advance together, so that each step of
+    // the sums reads Y (or W) once for all of them and the chains hide one another's
+    // shared-memory latency (one chain at a time left about 30 us of exposed latency)
     const int c = tid & 63, g = tid >> 6;
+    constexpr int NU = NB / 4;
     for (int q = 0; q < nq; ++q) {
         const int q0 = q * NB;
+        float w[NU];
 #pragma unroll
-        for (int u = 0; u < NB / 4; ++u) {
-            const int lp = q0 + g + 4 * u;
-            float w = sY[lp * 65 + c];
-            for (int l2 = 0; l2 < q0; ++l2) w -= sG[lp * 129 + l2] * sY[l2 * 65 + c];
-            sW[lp * 65 + c] = w;
+        for (int u = 0; u < NU; ++u) w[u] = sY[(q0 + g + 4 * u) * 65 + c];
+#pragma unroll 4
+        for (int l2 = 0; l2 < q0; ++l2) {
+            const float y = sY[l2 * 65 + c];
+#pragma unroll
+            for (int u = 0; u < NU; ++u) w[u] -= sG[(q0 + g + 4 * u) * 129 + l2] * y;
         }
+#pragma unroll
+        for (int u = 0; u < NU; ++u) sW[(q0 + g + 4 * u) * 65 + c] = w[u];
         __syncthreads();
+        float z[NU];
 #pragma unroll
-        for (int u = 0; u < NB / 4; ++u) {
-            const int b = g + 4 * u, l = q0 + b;
-            float z = 0.f;
-            for (int a = 0; a <= b; ++a) z += sT[q * NB * NB + a + b * NB] * sW[(q0 + a) * 65 + c];
-            sY[l * 65 + c] = z;
+        for (int u = 0; u < NU; ++u) z[u] = 0.f;
+#pragma unroll
+        for (int a = 0; a < NB; ++a) {
+            const float wa = sW[(q0 + a) * 65 + c];
+#pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                const int b = g + 4 * u;
+                if (a <= b) z[u] += sT[q * NB * NB + a + b * NB] * wa;
+            }
         }
+#pragma unroll
+        for (int u = 0; u < NU; ++u) sY[(q0 + g + 4 * u) * 65 + c] = z[u];
         __syncthreads();
     }
     unsigned char *zi = Zimg + (int64_t)blockIdx.x * Z_TILE;
