@@ -600,7 +600,8 @@ typedef enum {
     FASTLSQ_OPT_TRSV_FP32 = 3,     /* 1 (default): the triangular solves of classical
                                       refinement (MIXED) substitute in FP32 arithmetic
                                       (backward stable like the FP32 factor); 0: FP64
-                                      arithmetic.  CGLS and the adjoint always use FP64. */
+                                      arithmetic.  CGLS and the adjoint: see
+                                      FASTLSQ_OPT_KRYLOV_DF. */
     FASTLSQ_OPT_FUSED_LOOKAHEAD = 4,/* 1 (default): with look-ahead, the register panel
                                       applies the previous panel's update to its own columns
                                       in its prologue (no separate kernels for it) where its
@@ -622,11 +623,18 @@ typedef enum {
                                       instead of 4 m_aug n with the reflectors; 0: the
                                       plan keeps the reflectors only (faster setup, less
                                       memory). Read when a plan is prepared. */
-    FASTLSQ_OPT_FP64_ASSEMBLY_CTAS = 8 /* FP64 operator assembly launch: 0 (default) one CTA
+    FASTLSQ_OPT_FP64_ASSEMBLY_CTAS = 8, /* FP64 operator assembly launch: 0 (default) one CTA
                                       of 256 threads per 128 x 64 tile of entries; k = 1..8
                                       a persistent grid of k CTAs per SM looping over the
                                       tiles (a smaller footprint beside kernels of other
                                       streams).  The entries are the same either way. */
+    FASTLSQ_OPT_KRYLOV_DF = 9       /* 1 (default): the preconditioner solves R^{-1}, R^{-T}
+                                      of CGLS refinement and of the PCG adjoint with an FP32
+                                      factor run in double-float arithmetic (pairs of FP32
+                                      values, about 48 bits) on the FP32 pipes; 0: FP64
+                                      arithmetic.  The Krylov vectors, products and
+                                      residuals stay FP64, and fastlsq_factor_trsv is always
+                                      FP64. */
 } fastlsq_option;
 
 /* Set a context option (see fastlsq_option).  Returns 0 or -1 for an unknown option. */

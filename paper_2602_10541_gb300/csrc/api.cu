@@ -328,6 +328,10 @@ extern "C" int fastlsq_set_option(fastlsq_ctx *ctx, int option, int value)
         ctx->trsv32 = value ? 1 : 0;
         return 0;
     }
+    if (option == FASTLSQ_OPT_KRYLOV_DF) {
+        ctx->krylov_df = value ? 1 : 0;
+        return 0;
+    }
     if (option == FASTLSQ_OPT_FP64_ASSEMBLY_CTAS) {
         if (value < 0 || value > 8)
             return fl_fail(ctx, FASTLSQ_ERR_INVALID, "FP64 assembly CTAs per SM %d outside 0..8", value);
@@ -517,7 +521,7 @@ static int solve_one(fastlsq_ctx *ctx, const fastlsq_factor *f, int nrhs_in_F, i
     FL_TRY(fl_to_f64<T>(ctx, y, n, y64, 0));
     // FP32 substitution (backward stable, like the FP32 factor itself) is an option for
     // classical refinement; CGLS needs R^{-1} as a fixed linear operator: FP64
-    const int a32 = (mode == FASTLSQ_REFINE_CLASSICAL) ? ctx->trsv32 : 0;
+    const int a32 = (mode == FASTLSQ_REFINE_CLASSICAL && ctx->trsv32) ? FL_ARITH_F32 : 0;
     FL_TRY(fl_trsv_grid<T>(ctx, F, f->ld, n, y64, beta64, work, 0, nullptr, a32));
     if ((max_refine > 0 || norms_dev) && f->A_refine) FL_TRY(wait_refine(ctx));
     if (mode == FASTLSQ_REFINE_CGLS) {

@@ -104,6 +104,7 @@ struct fastlsq_ctx {
     int trsv32 = 1;                 // FP32 arithmetic in the triangular solves of classical refinement
     int inverse_thin_q = 1;         // inverse plans keep the thin Q of the interior rows
     int asm64_ctas_per_sm = 0;      // FP64 assembly: 0 one CTA per tile, k a persistent grid
+    int krylov_df = 1;              // double-float preconditioner solves in CGLS / PCG (FP32 factors)
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t aux2_stream = nullptr;   // the rest of an outer block's update pass (look-ahead)

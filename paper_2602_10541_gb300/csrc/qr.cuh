@@ -99,7 +99,10 @@ int fl_refine_cgls(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *rhs6
 int fl_normal_pcg(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *c64, double *v64,
                   int max_iter, double tol);
 
-// grid-wide FP64 triangular solve with R of type T (refine.cu)
+// triangular solve with R of type T (refine.cu): FP64 arithmetic, or for an FP32 factor
+// FP32 (FL_ARITH_F32) or double-float (FL_ARITH_DF) arithmetic in the cluster kernel
+constexpr int FL_ARITH_F32 = 1;
+constexpr int FL_ARITH_DF = 2;
 template <typename T>
 int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const double *y, double *x,
-                 double *work, int transpose, const void *skip_scalars = nullptr, int arith32 = 0);
+                 double *work, int transpose, const void *skip_scalars = nullptr, int arith = 0);

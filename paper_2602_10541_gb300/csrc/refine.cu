@@ -20,6 +20,7 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "gridsync.cuh"
 #include "qr.cuh"
 
@@ -385,7 +386,7 @@ k_trsv_cluster(const T *__restrict__ F, int64_t ld, int64_t n, const double *__r
     for (int lb = 0; lb < nown; ++lb) {
         const int64_t r0 = (int64_t)(rank + lb * CS) * TG_BS;
         for (int i = tid; i < TG_BS; i += TC_THREADS)
-            if (r0 + i < n) x[r0 + i] = xs[r0 + i];
+            if (r0 + i < n) x[r0 + i] = (double)xs[r0 + i];
     }
 }
 
@@ -514,7 +515,7 @@ int kry_dot(fastlsq_ctx *ctx, const double *a, const double *b, int64_t n, const
 // makes the call a no-op.
 template <typename T>
 int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const double *y, double *x,
-                 double *work, int transpose, const void *skip_scalars, int arith32)
+                 double *work, int transpose, const void *skip_scalars, int arith)
 {
     FL_PROF(ctx, FASTLSQ_K_TRSV);
     int *flag = ctx->d_flag;
@@ -522,21 +523,22 @@ int fl_trsv_grid(fastlsq_ctx *ctx, const T *F, int64_t ld, int64_t n, const doub
     const int64_t nblk = fl_cdiv(n, TG_BS);
     const int CS = (int)std::min<int64_t>(TC_MAX_CS, nblk);
     const int nown_max = (int)fl_cdiv(nblk, CS);
-    // FP32 arithmetic only on request and only for an FP32 factor
-    const bool a32 = arith32 && std::is_same<T, float>::value;
-    const size_t elem = a32 ? sizeof(float) : sizeof(double);
+    // FP32 or double-float arithmetic only on request and only for an FP32 factor
+    const int mode = std::is_same<T, float>::value ? ((arith == FL_ARITH_F32 || arith == FL_ARITH_DF) ? arith : 0) : 0;
+    const size_t elem = (mode == FL_ARITH_F32) ? sizeof(float) : sizeof(double);
     const size_t smem = TrsvClusterSmem::bytes(nown_max, nblk, elem);
     using K = void (*)(const T *, int64_t, int64_t, const double *, double *, int, int *, const KryScalars *);
-    K kern = a32 ? (K)k_trsv_cluster<T, float> : (K)k_trsv_cluster<T, double>;
-    static FlOncePerDevice attr_once[2];
+    K kern = (mode == FL_ARITH_F32) ? (K)k_trsv_cluster<T, float>
+             : (mode == FL_ARITH_DF) ? (K)k_trsv_cluster<T, dfl> : (K)k_trsv_cluster<T, double>;
+    static FlOncePerDevice attr_once[3];
     if (nown_max <= 4 && smem + elem * 2 * 4 * TG_BS <= (size_t)ctx->max_smem_optin) {
-        if (attr_once[a32].pending(ctx->device)) {
+        if (attr_once[mode].pending(ctx->device)) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  ctx->max_smem_optin - (int)(elem * 2 * 4 * TG_BS));
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return fl_cuda(ctx, e, "cudaFuncSetAttribute");
-            attr_once[a32].done(ctx->device);
+            attr_once[mode].done(ctx->device);
         }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(CS);
@@ -571,12 +573,17 @@ template int fl_trsv_grid<double>(fastlsq_ctx *, const double *, int64_t, int64_
 
 namespace {
 
-// out = R^{-1} in (transpose = 0) or R^{-T} in, in FP64 with the factor's R
+// out = R^{-1} in (transpose = 0) or R^{-T} in with the factor's R: in FP64, or, as the
+// preconditioner of CGLS and PCG with an FP32 factor (precond), in double-float
+// arithmetic when the context allows it (about 48 bits: the preconditioner need only
+// stay the same linear map to well below the FP32 factor's own error, and the FP64
+// residuals and products of the Krylov method set the accuracy of the result)
 template <typename T>
 int kry_prec(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *in, double *out, int transpose,
-             const KryBufs &B)
+             const KryBufs &B, bool precond = true)
 {
-    return fl_trsv_grid<T>(ctx, (const T *)f->F, f->ld, f->n, in, out, B.work, transpose, B.st);
+    const int arith = (precond && ctx->krylov_df && std::is_same<T, float>::value) ? FL_ARITH_DF : 0;
+    return fl_trsv_grid<T>(ctx, (const T *)f->F, f->ld, f->n, in, out, B.work, transpose, B.st, arith);
 }
 
 template <typename T>
@@ -697,6 +704,6 @@ int fl_factor_trsv64(fastlsq_ctx *ctx, const fastlsq_factor *f, const double *y,
     KryBufs B;
     FL_TRY(kry_bufs(ctx, f, &B));
     cudaMemsetAsync(B.st, 0, sizeof(KryScalars), ctx->stream);
-    if (f->prec == FASTLSQ_PREC_FP64) return kry_prec<double>(ctx, f, y, x, transpose, B);
-    return kry_prec<float>(ctx, f, y, x, transpose, B);
+    if (f->prec == FASTLSQ_PREC_FP64) return kry_prec<double>(ctx, f, y, x, transpose, B, false);
+    return kry_prec<float>(ctx, f, y, x, transpose, B, false);
 }

@@ -205,6 +205,7 @@ OPT_ROW_PANEL = 5
 OPT_SPLIT_ROWS = 6
 OPT_INVERSE_THIN_Q = 7
 OPT_FP64_ASSEMBLY_CTAS = 8
+OPT_KRYLOV_DF = 9
 
 
 def fastlsq_set_option(ctx, option, value):

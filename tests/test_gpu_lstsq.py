@@ -127,18 +127,54 @@ def test_mixed_refinement_on_large_residual_problem_never_hurts(ctx):
     assert errs[1] <= errs[0] * 1.5 and errs[1] < 1e-5, errs
 
 
+@pytest.mark.parametrize("krylov_df", [1, 0])
 @pytest.mark.parametrize("mu", [0.0, 1e-2])
-def test_mixed_cgls_refinement_reaches_fp64_on_large_residual(ctx, mu):
+def test_mixed_cgls_refinement_reaches_fp64_on_large_residual(ctx, mu, krylov_df):
+    """CGLS with the FP32 factor's R as preconditioner, its substitutions in double-float
+    (the default) or FP64 arithmetic."""
     rng = np.random.default_rng(23)
     m, n = 517, 77
     A = rng.standard_normal((m, n))
     B = rng.standard_normal((m, 1))
     ref = oracle.lstsq(A, B, mu=mu).reshape(-1)
     beta = torch.zeros((1, n), dtype=torch.float64, device=DEV)
-    _, _, st = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, mu, _rhs(B), beta,
-                                A_refine=_cm(A, torch.float64), max_refine=30,
-                                refine_mode=fl.REFINE_CGLS, refine_tol=1e-14, stats=True)
+    fl.fastlsq_set_option(ctx, fl.OPT_KRYLOV_DF, krylov_df)
+    try:
+        _, _, st = fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, mu, _rhs(B), beta,
+                                    A_refine=_cm(A, torch.float64), max_refine=30,
+                                    refine_mode=fl.REFINE_CGLS, refine_tol=1e-14, stats=True)
+    finally:
+        fl.fastlsq_set_option(ctx, fl.OPT_KRYLOV_DF, 1)
     np.testing.assert_allclose(beta.cpu().numpy()[0], ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+
+
+def test_cgls_double_float_preconditioner_on_an_ill_conditioned_system(ctx):
+    """A system with singular values from 1 down to 1e-6 (900 x 200: four 64-row blocks of
+    the substitution, the last ragged) and a large residual: CGLS preconditioned by the
+    FP32 factor reaches the oracle's FP64 least-squares solution with the substitutions in
+    double-float and in FP64 arithmetic, and the two agree with each other."""
+    rng = np.random.default_rng(29)
+    m, n = 900, 200
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (U * np.logspace(0, -6, n)) @ V.T
+    B = rng.standard_normal((m, 1))
+    ref = oracle.lstsq(A, B).reshape(-1)
+    out = []
+    for df in (1, 0):
+        beta = torch.zeros((1, n), dtype=torch.float64, device=DEV)
+        fl.fastlsq_set_option(ctx, fl.OPT_KRYLOV_DF, df)
+        try:
+            fl.fastlsq_lstsq(ctx, fl.PREC_MIXED, _cm(A, torch.float32), m, 0.0, _rhs(B), beta,
+                             A_refine=_cm(A, torch.float64), max_refine=64, refine_mode=fl.REFINE_CGLS,
+                             refine_tol=1e-15)
+        finally:
+            fl.fastlsq_set_option(ctx, fl.OPT_KRYLOV_DF, 1)
+        out.append(beta.cpu().numpy()[0])
+    scale = np.abs(ref).max()
+    for b in out:
+        assert np.abs(b - ref).max() <= 1e-7 * scale, np.abs(b - ref).max() / scale
+    assert np.abs(out[0] - out[1]).max() <= 1e-7 * scale
 
 
 @pytest.mark.parametrize("prec,dt,tol", [(fl.PREC_FP64, torch.float64, 1e-11),
