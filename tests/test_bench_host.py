@@ -1,7 +1,8 @@
 """Host-side bookkeeping of bench.py (no GPU): the stored ncu traffic is reported only
 for the kernel sources and workload it was captured with, the algorithmic work of the
 two-level schedule adds up to the one-level schedule's plus the rows above the inner
-panels, and the whole-job throughput of one rank is its solves over its device time."""
+panels, the whole-job throughput of one rank is its solves over its device time, and the
+autotuner's launch table is read with defaults for keys it lacks."""
 import json
 import os
 import shutil
@@ -85,3 +86,25 @@ def test_oracle_sample_ratio_is_the_qr_work_ratio():
 def test_single_rank_throughput_is_solves_over_device_time():
     value, total = bench._job_throughput(2500.0, 20, 1)
     assert total == 2500.0 and value == pytest.approx(8.0)
+
+
+def test_tuned_launch_fills_keys_the_table_lacks(tmp_path, monkeypatch):
+    """pipeline.tuned() takes the recorded launch shape and falls back to the default for
+    any key the table does not hold (a table written before a key existed)."""
+    import json
+    from paper_2602_10541_gb300 import pipeline as pl
+    table = tmp_path / "tuning.json"
+    table.write_text(json.dumps({"inverse_eval": {"threads": 512, "ctas_per_sm": 2, "ms": 1.0}}))
+    real_join = os.path.join
+    pkg = os.path.dirname(os.path.abspath(pl.__file__))
+    monkeypatch.setattr(os.path, "join",
+                        lambda *a: str(table) if a == (pkg, "tuning.json") else real_join(*a))
+    got = pl.tuned("inverse_eval", {"threads": 256, "ctas_per_sm": 1, "cluster": 1})
+    assert got == {"threads": 512, "ctas_per_sm": 2, "cluster": 1}
+    assert pl.tuned("other_kernel", {"a": 1}) == {"a": 1}
+
+
+def test_tuner_candidates_cover_every_launch_shape():
+    from paper_2602_10541_gb300 import tune
+    shapes = {(c["threads"], c["ctas_per_sm"], c["cluster"]) for c in tune.CANDIDATES}
+    assert shapes == {(t, k, c) for t in (256, 512) for k in (1, 2) for c in (1, 2, 4)}
