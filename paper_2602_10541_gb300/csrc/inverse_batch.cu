@@ -5,7 +5,9 @@
 //
 // fastlsq_inverse_prepare factors each instance once (FP64 Householder QR of
 // [A; sqrt(mu) I], kept: the checkpoint the evaluations reuse; several instances at a
-// time on worker streams) and tabulates its sensor matrix H_s (n_sens x n_feat, FP64).
+// time on worker streams), by default forms Qi = the interior rows of Q [I; 0] from the
+// kept factor (thin-Q plan, evaluated by k_inv_eval_q below), and tabulates the sensor
+// matrix H_s (n_sens x n_feat, FP64).  With the reflector plan,
 // fastlsq_inverse_eval launches k_inv_eval: a grid of persistent clusters of C CTAs
 // (C = 1, 2 or 4) that take instances from a device-side queue (one atomic counter,
 // instances in decreasing order of m_aug n, so the longest start first); a cluster runs
