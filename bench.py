@@ -516,6 +516,17 @@ def _secondary(fl, pl, wl, torch, ctx, dev, n_inverse):
     return out
 
 
+def _inverse_eval_fma(shapes, thin_q):
+    """FP64 FMAs of one evaluation of a batch of (n_int, n_bc, n_feat) instances.  Thin-Q
+    plan (the default): Qi^T s and Qi w over the interior rows (n_int n each) and two
+    triangular solves (n^2 / 2 each): 2 n_int n + n^2 per instance.  Reflector plan: Q^T
+    and Q each a dot pass and an update pass over the reflectors (2 (m_aug n - n^2 / 2)
+    each) and the two solves: 4 m_aug n, m_aug = interior + boundary + Tikhonov rows."""
+    if thin_q:
+        return sum(2.0 * ni * n + float(n) ** 2 for ni, nb, n in shapes)
+    return sum(4.0 * (ni + nb + n) * n for ni, nb, n in shapes)
+
+
 def _inverse_row(fl, pl, wl, torch, ctx, dev, n_inst):
     """The batched inverse heat-source configuration: n_inst instances drawn with its
     recipe, factored once (FP64 QR, kept), then gradient evaluations of the whole batch,
@@ -547,16 +558,8 @@ def _inverse_row(fl, pl, wl, torch, ctx, dev, n_inst):
         b.record(ctx.stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
-    # FP64 FMAs of one evaluation of the batch.  Thin-Q plan (the default): Qi^T s and
-    # Qi w over the interior rows (n_int n each) and two triangular solves (n^2 / 2 each):
-    # 2 n_int n + n^2 per instance.  Reflector plan: Q^T and Q each a dot pass and an
-    # update pass over the reflectors (2 (m_aug n - n^2 / 2) each) and the two solves:
-    # 4 m_aug n, m_aug = interior + boundary + Tikhonov rows.
     thin_q = batch.thin_q
-    if thin_q:
-        fma = sum(2.0 * w.n_int * w.n_feat + float(w.n_feat) ** 2 for w in ws)
-    else:
-        fma = sum(4.0 * (w.n_int + w.n_bc + w.n_feat) * w.n_feat for w in ws)
+    fma = _inverse_eval_fma([(w.n_int, w.n_bc, w.n_feat) for w in ws], thin_q)
     tfma = fma / (ms / 1e3) / 1e12
     out = {"instances": n_inst, "setup_s": setup_s, "factorizations_per_s": n_inst / setup_s,
            "ms_per_batch_eval": ms, "gradient_evals_per_s": n_inst / (ms / 1e3),

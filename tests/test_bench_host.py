@@ -108,3 +108,16 @@ def test_tuner_candidates_cover_every_launch_shape():
     from paper_2602_10541_gb300 import tune
     shapes = {(c["threads"], c["ctas_per_sm"], c["cluster"]) for c in tune.CANDIDATES}
     assert shapes == {(t, k, c) for t in (256, 512) for k in (1, 2) for c in (1, 2, 4)}
+
+
+def test_inverse_evaluation_work_of_both_plans():
+    """The thin-Q plan's FMAs per instance are 2 n_int n + n^2 (two passes over the
+    interior rows of Q and two substitutions); the reflector plan's are 4 m_aug n.  For
+    the batched configuration's largest instance the thin plan does 2.5x less."""
+    shapes = [(8192, 1024, 2048), (1024, 128, 512)]
+    thin = bench._inverse_eval_fma(shapes, True)
+    refl = bench._inverse_eval_fma(shapes, False)
+    assert thin == 2 * 8192 * 2048 + 2048 ** 2 + 2 * 1024 * 512 + 512 ** 2
+    assert refl == 4 * (8192 + 1024 + 2048) * 2048 + 4 * (1024 + 128 + 512) * 512
+    big_t, big_r = bench._inverse_eval_fma(shapes[:1], True), bench._inverse_eval_fma(shapes[:1], False)
+    assert 2.4 < big_r / big_t < 2.6
